@@ -1,0 +1,274 @@
+/*
+ * gnnmp.h -- C ABI of libgnnmp: the consistent neural message-passing (NMP)
+ * layer of arXiv 2410.01657 ("Scalable and Consistent Graph Neural Networks
+ * for Distributed Mesh-based Data-driven Modeling") on one GB300 (sm_103a).
+ *
+ * Conventions for every entry point
+ *  - Return 0 (GNN_OK) on success or a negative GNN_E* code; the thread-local
+ *    message of the last failure is gnn_last_error(). No C++ exception crosses
+ *    this boundary.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *    memory of the current device. The caller allocates and owns every device
+ *    buffer passed in (PyTorch does it in the Python binding); the library
+ *    allocates device memory nowhere in the compute calls.
+ *  - Compute calls are asynchronous on the CUDA stream passed as `stream`
+ *    (a cudaStream_t cast to void*, NULL = legacy default stream). Argument
+ *    errors are reported synchronously; a kernel-side failure (a bounded wait
+ *    that ran out, a bounds check) is latched in a device error word and
+ *    reported by the next gnn_check().
+ *  - Matrices are row-major. Node rows [n_rows x H] and edge rows
+ *    [n_edges x H] follow the row and edge order of the gnn_partition they
+ *    were built for (partitions concatenated, receiver-sorted edges).
+ */
+#ifndef GNNMP_H
+#define GNNMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define GNN_OK            0
+#define GNN_EINVAL       -1   /* bad argument (NULL pointer, out-of-range value)        */
+#define GNN_ESHAPE       -2   /* inconsistent sizes or a size the kernels cannot take   */
+#define GNN_EDTYPE       -3   /* unsupported precision / dtype combination              */
+#define GNN_ECUDA        -4   /* a CUDA runtime or driver call failed                   */
+#define GNN_EHALO        -5   /* inconsistent partition / halo bookkeeping              */
+#define GNN_ETIMEOUT     -6   /* a bounded device-side wait ran out (see gnn_check)     */
+#define GNN_ENOMEM       -7   /* host allocation failed or workspace too small          */
+#define GNN_EUNSUPPORTED -8   /* valid input the implementation does not cover          */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* gnn_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int gnn_version(void);
+/* Synchronise `stream`, then read and clear the device error word.
+ * Returns GNN_OK, GNN_ETIMEOUT (a device wait gave up) or GNN_ECUDA. */
+int gnn_check(void* stream);
+
+/* ====================================================== graph generation (host)
+ * Sec. II-A, Fig. 2: nodes at the GLL quadrature points of hexahedral elements
+ * of polynomial order p, undirected edges between neighbouring quadrature
+ * points of an element (6-neighbour stencil, both directions), coincident
+ * nodes of neighbouring elements merged by global id.
+ */
+typedef struct gnn_mesh_desc {
+    int32_t nel[3];          /* elements per axis (>= 1)                                  */
+    int32_t p;               /* polynomial order (1..15)                                  */
+    double extent[3];        /* brick [0,extent[a]]; element size extent[a]/nel[a]        */
+    int32_t periodic[3];     /* nonzero: axis wraps (needs nel*p >= 3)                    */
+    double jitter_frac;      /* node displacement as a fraction of the local GLL spacing  */
+    const double* jitter;    /* host [n_nodes x 3] values in [-1,1], or NULL (no jitter)  */
+} gnn_mesh_desc;
+
+typedef struct gnn_graph gnn_graph;   /* opaque, library-owned host object */
+
+typedef struct gnn_graph_info {
+    int64_t n_nodes;         /* lattice points: prod(L)                                   */
+    int64_t n_edges;         /* directed edges of the R=1 graph                           */
+    int64_t n_elem;
+    int32_t L[3];            /* lattice points per axis: nel*p (+1 if not periodic)      */
+    int32_t p;
+} gnn_graph_info;
+
+/* Build the R=1 GLL-brick graph. Global id of lattice point (ix,iy,iz) is
+ * ix + L0*(iy + L1*iz); the CSR is receiver-sorted, senders ascending.
+ * Node (ix,..) moves by jitter[g*3+a]*jitter_frac*(smallest adjacent GLL
+ * spacing on axis a), except the normal coordinate on non-periodic faces.
+ * *out is freed with gnn_graph_destroy. Errors: GNN_EINVAL, GNN_ENOMEM. */
+int gnn_graph_build(const gnn_mesh_desc* desc, gnn_graph** out);
+void gnn_graph_destroy(gnn_graph* g);
+int gnn_graph_get_info(const gnn_graph* g, gnn_graph_info* info);
+/* Copy-out accessors into caller-owned host buffers of the stated length. */
+int gnn_graph_copy_pos(const gnn_graph* g, double* pos /* [n_nodes*3] */);
+int gnn_graph_copy_csr(const gnn_graph* g, int64_t* row_ptr /* [n_nodes+1] */,
+                       int64_t* col /* [n_edges] */);
+int gnn_graph_copy_elements(const gnn_graph* g, int64_t* elem_nodes /* [n_elem*(p+1)^3] */);
+
+/* ================================================ partitioning + halo (host)
+ * Sec. II-A, Figs. 3-4: elements are split over R sub-graphs; each keeps the
+ * nodes and stencil edges of its own elements with local coincident nodes
+ * collapsed (the "reduced" graph). d_ij (Eq. 5b) counts the sub-graphs that
+ * hold directed edge (i,j); d_i (Eq. 8b) the sub-graphs that hold node i.
+ * On one GPU all sub-graphs are resident as one concatenated row space, so the
+ * halo rows of Fig. 4 become a copy list: for every global id held by >= 2
+ * sub-graphs, the rows holding it in increasing sub-graph order.
+ */
+#define GNN_PART_SLAB_Z 0    /* R contiguous z-layers of elements                        */
+#define GNN_PART_RCB    1    /* recursive coordinate bisection of element centres        */
+
+typedef struct gnn_partition gnn_partition;   /* opaque, library-owned host object */
+
+typedef struct gnn_partition_info {
+    int32_t n_parts;         /* R                                                          */
+    int32_t max_in_degree;   /* largest receiver in-degree over all rows                  */
+    int64_t n_rows;          /* sum of local rows over sub-graphs                          */
+    int64_t n_edges;         /* sum of local directed edges                                */
+    int64_t n_shared;        /* global ids held by >= 2 sub-graphs                        */
+    int64_t n_copies;        /* rows holding those ids (length of the copy list)          */
+    int64_t n_edge_tiles;    /* receiver-aligned tiles of <= GNN_EDGE_TILE edges           */
+    int64_t n_node_tiles;    /* tiles of GNN_NODE_TILE consecutive rows                    */
+} gnn_partition_info;
+
+#define GNN_EDGE_TILE 128
+#define GNN_NODE_TILE 128
+
+/* Partition g into R sub-graphs. method is GNN_PART_*; target_weights (host,
+ * R positive doubles, NULL = equal) sets the RCB share of each part. RCB
+ * splits a set of parts [r0, r0+n) into its first floor(n/2) parts and the
+ * rest along the axis of largest element-centre extent (lowest axis on ties),
+ * after a stable sort by (centre, element id), giving the left side
+ * floor(count*W_left/W + 0.5) elements (at least one per part).
+ * Errors: GNN_EINVAL (R out of range, bad weights), GNN_ESHAPE (more than
+ * 2^31-1 rows or edges), GNN_ENOMEM. */
+int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method,
+                       const double* target_weights, gnn_partition** out);
+void gnn_partition_destroy(gnn_partition* p);
+int gnn_partition_get_info(const gnn_partition* p, gnn_partition_info* info);
+
+/* Arrays of a partition, copied into a caller-owned host buffer of exactly
+ * `bytes` bytes (GNN_ESHAPE otherwise). Row r of sub-graph s is global row
+ * row_offsets[s] + r; local rows are ordered by global id. */
+#define GNN_P_ROW_OFFSETS  0   /* int64 [R+1]                                               */
+#define GNN_P_EDGE_OFFSETS 1   /* int64 [R+1]                                               */
+#define GNN_P_ROW_GID      2   /* int64 [n_rows] global id of each row                      */
+#define GNN_P_ROW_PTR      3   /* int32 [n_rows+1] receiver CSR                             */
+#define GNN_P_COL          4   /* int32 [n_edges] sender row (same sub-graph), ascending gid */
+#define GNN_P_EDGE_DEG     5   /* uint8 [n_edges] d_ij                                      */
+#define GNN_P_EDGE_W       6   /* float [n_edges] 1/d_ij                                    */
+#define GNN_P_NODE_DEG     7   /* uint8 [n_rows] d_i                                        */
+#define GNN_P_NODE_W       8   /* float [n_rows] 1/d_i                                      */
+#define GNN_P_T_PTR        9   /* int32 [n_rows+1] sender CSR                               */
+#define GNN_P_T_EID       10   /* int32 [n_edges] edge ids by sender, ascending             */
+#define GNN_P_HALO_PTR    11   /* int32 [n_shared+1]                                        */
+#define GNN_P_HALO_ROWS   12   /* int32 [n_copies] rows of each shared id, by sub-graph     */
+#define GNN_P_EDGE_TILES  13   /* int32 [n_edge_tiles+1] first receiver row of each tile    */
+#define GNN_P_EDGE_ATTR   14   /* float [n_edges*4] [dx,dy,dz,|d|], d = pos(send)-pos(recv) */
+#define GNN_P_ROW_POS     15   /* double [n_rows*3]                                         */
+#define GNN_P_PART_STATS  16   /* int64 [R*3] per sub-graph: local rows, halo rows, neighbours */
+int gnn_partition_copy(const gnn_partition* p, int32_t what, void* dst, size_t bytes);
+
+/* ====================================================== device-side graph
+ * The arrays above after upload to device memory by the caller. Pointers are
+ * device pointers, borrowed for the duration of each call.
+ */
+typedef struct gnn_graph_dev {
+    int64_t n_rows;
+    int64_t n_edges;
+    const int32_t* row_ptr;     /* [n_rows+1]   */
+    const int32_t* col;         /* [n_edges]    */
+    const float*   edge_w;      /* [n_edges]    1/d_ij                                      */
+    const int32_t* t_ptr;       /* [n_rows+1]   */
+    const int32_t* t_eid;       /* [n_edges]    */
+    const float*   node_w;      /* [n_rows]     1/d_i (consistent loss)                     */
+    int64_t n_shared;
+    const int32_t* halo_ptr;    /* [n_shared+1] */
+    const int32_t* halo_rows;   /* [n_copies]   */
+    int64_t n_edge_tiles;
+    const int32_t* edge_tiles;  /* [n_edge_tiles+1] */
+    int32_t max_in_degree;      /* host copy of gnn_partition_info.max_in_degree            */
+} gnn_graph_dev;
+
+/* ====================================================== parameters
+ * One MLP block (Sec. III, Table 1): n_lin = n_hidden + 2 Linear layers
+ * dims[0] -> dims[1] -> ... -> dims[n_lin], ELU (alpha 1) after all but the
+ * last, then an affine LayerNorm over dims[n_lin] when gamma != NULL. W[k] is
+ * [dims[k+1] x dims[k]] row-major (out x in), FP32 device memory. The same
+ * struct carries gradients (dW, db, dgamma, dbeta), which calls accumulate into.
+ */
+#define GNN_MAX_LIN 8
+typedef struct gnn_mlp {
+    int32_t n_lin;
+    int32_t dims[GNN_MAX_LIN + 1];
+    float* W[GNN_MAX_LIN];
+    float* b[GNN_MAX_LIN];
+    float* gamma;               /* NULL: no LayerNorm */
+    float* beta;
+} gnn_mlp;
+
+/* One consistent NMP layer: edge MLP on [x_i, x_j, e_ij] (3H -> H) and node
+ * MLP on [a*_i, x_i] (2H -> H), both with LayerNorm (Eq. 5a, 5e). */
+typedef struct gnn_mp_params {
+    gnn_mlp edge;
+    gnn_mlp node;
+} gnn_mp_params;
+
+#define GNN_PREC_FP32 0   /* plain FP32 SIMT kernels, FP32 edge state                       */
+#define GNN_PREC_BF16 1   /* fused tcgen05 kernels: BF16 GEMM operands, FP32 accumulation,
+                             FP32 sums/LayerNorm statistics, BF16 edge state and edge grads */
+#define GNN_HALO_SYNC 0   /* consistent layer (Eq. 5c-5d applied)                           */
+#define GNN_HALO_NONE 1   /* the paper's "None" mode: Eq. 5c-5d skipped (inconsistent)     */
+#define GNN_FLAG_NO_EDGE_OUT 1  /* forward: do not write e_out (last layer in inference)  */
+
+typedef struct gnn_mp_config {
+    int32_t hidden;          /* H: 16, 32, 64 or 128 (BF16); 1..256 (FP32)                 */
+    int32_t precision;       /* GNN_PREC_*                                                  */
+    int32_t halo_mode;       /* GNN_HALO_*                                                  */
+    int32_t flags;           /* GNN_FLAG_*                                                  */
+    float ln_eps;            /* LayerNorm epsilon (the paper's PyTorch default 1e-5)       */
+} gnn_mp_config;
+
+/* ====================================================== consistent NMP layer
+ * Workspace bytes needed by gnn_mp_forward / gnn_mp_backward for this graph,
+ * configuration and parameter shapes. */
+int gnn_mp_workspace_size(const gnn_graph_dev* G, const gnn_mp_config* cfg,
+                          const gnn_mp_params* W, size_t* fwd_bytes, size_t* bwd_bytes);
+
+/* Forward of one consistent NMP layer, Eq. 5a-5e:
+ *   e'_ij = e_ij + LN(MLP_E([x_i, x_j, e_ij]))   (i receiver, j sender)     Eq. 5a
+ *   a_i   = sum_j e'_ij / d_ij                    (FP32, fixed order)        Eq. 5b
+ *   a*_i  = sum over the copies of node i of a    (halo swap + sync)         Eq. 5c-5d
+ *   x'_i  = x_i + LN(MLP_N([a*_i, x_i]))                                     Eq. 5e
+ * x_in/x_out: device FP32 [n_rows x H]. e_in/e_out: device [n_edges x H],
+ * FP32 for GNN_PREC_FP32, BF16 for GNN_PREC_BF16. a_star_out: device FP32
+ * [n_rows x H] or NULL (saved for the backward, which otherwise recomputes it).
+ * e_out may be NULL with GNN_FLAG_NO_EDGE_OUT. x_out must not alias x_in.
+ * ws: device workspace of ws_bytes >= the forward size. */
+int gnn_mp_forward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                   const float* x_in, const void* e_in, float* x_out, void* e_out,
+                   float* a_star_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Backward (adjoint) of gnn_mp_forward with per-layer recomputation of the
+ * MLP activations (Eq. 3). Given dL/dx_out and dL/de_out (NULL = zero),
+ * writes dL/dx_in (FP32) and dL/de_in (edge dtype) and ACCUMULATES (+=) the
+ * parameter gradients into dW (same shapes as W, FP32) in a fixed order.
+ * a_star: the forward's a_star_out, or NULL to recompute it. The halo adjoint
+ * is the same copy-sum as the forward (the map a -> a* is symmetric). */
+int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                    const float* x_in, const void* e_in, const float* a_star,
+                    const float* dx_out, const void* de_out, float* dx_in, void* de_in,
+                    const gnn_mp_params* dW, void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. 5c-5d on one GPU: for every global id held by >= 2 rows, replace each
+ * copy by the sum of all copies (summed in increasing sub-graph order, so all
+ * copies end bitwise equal). rows: device FP32 [n_rows x width], in place.
+ * The map is symmetric, so it is also its own adjoint. */
+int gnn_halo_exchange(const gnn_graph_dev* G, float* rows, int32_t width, void* stream);
+
+/* ====================================================== encoder / decoder / loss
+ * Row-wise MLP block (node/edge encoders, node decoder; Sec. III): Y = MLP(X)
+ * over n_rows rows. X: device FP32 [n_rows x dims[0]]; Y: device
+ * [n_rows x dims[n_lin]], FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1). */
+int gnn_mlp_workspace_size(const gnn_mlp* P, int64_t n_rows, size_t* fwd_bytes, size_t* bwd_bytes);
+int gnn_mlp_forward(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,
+                    float ln_eps, void* ws, size_t ws_bytes, void* stream);
+/* dY: device [n_rows x dims[n_lin]] FP32 (dy_bf16 = 0) or BF16 (dy_bf16 = 1).
+ * dX: device FP32 [n_rows x dims[0]] or NULL. dP accumulates (+=). */
+int gnn_mlp_backward(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY,
+                     int32_t dy_bf16, float* dX, const gnn_mlp* dP, float ln_eps,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* Consistent MSE loss, Eq. 8a-8c: L = sum_rows sum_f (1/d_i)(y - t)^2 /
+ * (N_eff * F) with N_eff = sum_rows 1/d_i. y, t: device FP32 [n_rows x F].
+ * loss: device FP32 scalar (written). dy: device FP32 [n_rows x F] = dL/dy,
+ * or NULL. Reductions run in a fixed order (deterministic). ws >= 16 KiB. */
+int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, int32_t F,
+                        float* loss, float* dy, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GNNMP_H */

@@ -1,0 +1,24 @@
+// Fused BF16 tcgen05 path of libgnnmp (declarations used by the C-ABI layer).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "gnnmp.h"
+
+namespace gnn {
+namespace fused {
+
+cudaError_t take_device_error(unsigned int* out);
+size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
+size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
+int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+               const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
+               size_t ws_bytes, cudaStream_t s);
+int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
+                float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
+                cudaStream_t s);
+
+}  // namespace fused
+}  // namespace gnn

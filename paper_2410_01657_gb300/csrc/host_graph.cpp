@@ -1,0 +1,689 @@
+// Host-side graph generation and partitioning of libgnnmp.
+//
+// Sec. II-A of the paper: graph nodes are the GLL quadrature points of the hex
+// elements of a spectral-element mesh, undirected edges join neighbouring
+// quadrature points inside an element, and coincident nodes of neighbouring
+// elements share one global id. On a conforming brick the union of the
+// per-element 6-neighbour stencils is the 6-neighbour graph of the global GLL
+// lattice, so the R=1 CSR is generated directly from lattice coordinates.
+//
+// Partitioning (Figs. 3-4): elements are assigned to R sub-graphs; sub-graph r
+// keeps the nodes and stencil edges of its elements (local coincident nodes
+// collapsed -- the "reduced" distributed graph). Edge degree d_ij (Eq. 5b) is
+// the number of sub-graphs holding directed edge (i,j), node degree d_i
+// (Eq. 8b) the number holding node i. The halo rows of Fig. 4 become, with all
+// sub-graphs resident on one GPU, a copy list per shared global id.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "common.h"
+
+namespace gnn {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int set_error(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char* last_error() { return g_last_error.c_str(); }
+
+// Gauss-Legendre-Lobatto points on [-1,1], ascending: the endpoints and the
+// roots of P_p'. Newton iteration of von Winckel's "lglnodes" on
+// x P_p(x) - P_{p-1}(x), started from the Chebyshev-Lobatto points.
+static std::vector<double> gll_points(int p) {
+    std::vector<double> x(p + 1);
+    for (int k = 0; k <= p; ++k) x[k] = std::cos(M_PI * k / p);
+    for (int it = 0; it < 100; ++it) {
+        double change = 0.0;
+        for (int k = 0; k <= p; ++k) {
+            double pm1 = 1.0, pk = x[k];           // P_0, P_1
+            for (int n = 2; n <= p; ++n) {
+                double pn = ((2.0 * n - 1.0) * x[k] * pk - (n - 1.0) * pm1) / n;
+                pm1 = pk;
+                pk = pn;
+            }
+            // pk = P_p(x), pm1 = P_{p-1}(x)
+            double dx = (x[k] * pk - pm1) / ((p + 1.0) * pk);
+            x[k] -= dx;
+            change = std::max(change, std::fabs(dx));
+        }
+        if (change < 1e-16) break;
+    }
+    std::sort(x.begin(), x.end());
+    x[0] = -1.0;
+    x[p] = 1.0;
+    for (int k = 1; k < p; ++k) {            // exact antisymmetry
+        if (k < p - k) {
+            double m = 0.5 * (x[p - k] - x[k]);
+            x[k] = -m;
+            x[p - k] = m;
+        } else if (k == p - k) {
+            x[k] = 0.0;
+        }
+    }
+    return x;
+}
+
+}  // namespace gnn
+
+struct gnn_graph {
+    int32_t nel[3];
+    int32_t p;
+    double extent[3];
+    int32_t periodic[3];
+    int32_t L[3];
+    int64_t n_nodes;
+    std::vector<double> pos;        // [N*3]
+    std::vector<int64_t> row_ptr;   // [N+1]
+    std::vector<int64_t> col;       // [E]
+};
+
+struct gnn_partition {
+    int32_t R;
+    int32_t max_in_degree;
+    std::vector<int64_t> row_offsets, edge_offsets;
+    std::vector<int64_t> row_gid;
+    std::vector<int32_t> row_ptr, col;
+    std::vector<uint8_t> edge_deg, node_deg;
+    std::vector<int32_t> t_ptr, t_eid;
+    std::vector<int32_t> halo_ptr, halo_rows;
+    std::vector<int32_t> edge_tiles;
+    std::vector<double> row_pos;
+    std::vector<int64_t> part_stats;
+};
+
+namespace {
+
+using gnn::set_error;
+
+struct Lattice {
+    int32_t nel[3], L[3], p;
+    int32_t periodic[3];
+    int64_t gid(int64_t ix, int64_t iy, int64_t iz) const { return ix + L[0] * (iy + (int64_t)L[1] * iz); }
+    void coords(int64_t g, int64_t c[3]) const {
+        c[0] = g % L[0];
+        c[1] = (g / L[0]) % L[1];
+        c[2] = g / ((int64_t)L[0] * L[1]);
+    }
+    // element indices along one axis that contain lattice index i; returns count (1 or 2)
+    int elems_of_point(int a, int64_t i, int64_t out[2]) const {
+        int n = 0;
+        int64_t e = i / p;
+        if (i % p == 0) {
+            int64_t left = e - 1;
+            if (periodic[a]) left = (left + nel[a]) % nel[a];
+            if (left >= 0) out[n++] = left;
+            if (e < nel[a]) out[n++] = e;
+        } else {
+            out[n++] = e;
+        }
+        return n;
+    }
+    int64_t elem_id(int64_t ex, int64_t ey, int64_t ez) const { return ex + nel[0] * (ey + (int64_t)nel[1] * ez); }
+};
+
+Lattice lattice_of(const gnn_graph* g) {
+    Lattice lt;
+    for (int a = 0; a < 3; ++a) {
+        lt.nel[a] = g->nel[a];
+        lt.L[a] = g->L[a];
+        lt.periodic[a] = g->periodic[a];
+    }
+    lt.p = g->p;
+    return lt;
+}
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+    unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+    if (n < 2 || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt && (int64_t)t < n; ++t)
+        th.emplace_back([&] {
+            for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+        });
+    for (auto& t : th) t.join();
+}
+
+// Element -> part by recursive coordinate bisection of element centres.
+void rcb_split(const std::vector<double>& centre, std::vector<int64_t>& elems, int64_t lo, int64_t hi,
+               int32_t r0, int32_t nr, const std::vector<double>& w, std::vector<int32_t>& part) {
+    if (nr == 1) {
+        for (int64_t i = lo; i < hi; ++i) part[elems[i]] = r0;
+        return;
+    }
+    int axis = 0;
+    double ext[3];
+    for (int a = 0; a < 3; ++a) {
+        double mn = std::numeric_limits<double>::infinity(), mx = -mn;
+        for (int64_t i = lo; i < hi; ++i) {
+            double c = centre[elems[i] * 3 + a];
+            mn = std::min(mn, c);
+            mx = std::max(mx, c);
+        }
+        ext[a] = mx - mn;
+    }
+    for (int a = 1; a < 3; ++a)
+        if (ext[a] > ext[axis]) axis = a;
+    std::sort(elems.begin() + lo, elems.begin() + hi, [&](int64_t u, int64_t v) {
+        double cu = centre[u * 3 + axis], cv = centre[v * 3 + axis];
+        if (cu != cv) return cu < cv;
+        return u < v;
+    });
+    int32_t nl = nr / 2;
+    double wl = 0.0, wr = 0.0;
+    for (int32_t k = r0; k < r0 + nl; ++k) wl += w[k];
+    for (int32_t k = r0 + nl; k < r0 + nr; ++k) wr += w[k];
+    int64_t n = hi - lo;
+    int64_t cut = (int64_t)std::floor((double)n * wl / (wl + wr) + 0.5);
+    cut = std::min(std::max(cut, (int64_t)nl), n - (nr - nl));
+    rcb_split(centre, elems, lo, lo + cut, r0, nl, w, part);
+    rcb_split(centre, elems, lo + cut, hi, r0 + nl, nr - nl, w, part);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gnn_last_error(void) { return gnn::last_error(); }
+
+int gnn_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+int gnn_graph_build(const gnn_mesh_desc* d, gnn_graph** out) {
+    GNN_REQUIRE(d && out, GNN_EINVAL, "gnn_graph_build: NULL argument");
+    *out = nullptr;
+    GNN_REQUIRE(d->p >= 1 && d->p <= 15, GNN_EINVAL, "gnn_graph_build: p=%d out of range 1..15", d->p);
+    for (int a = 0; a < 3; ++a) {
+        GNN_REQUIRE(d->nel[a] >= 1, GNN_EINVAL, "gnn_graph_build: nel[%d]=%d < 1", a, d->nel[a]);
+        GNN_REQUIRE(d->extent[a] > 0.0, GNN_EINVAL, "gnn_graph_build: extent[%d] <= 0", a);
+        GNN_REQUIRE(!d->periodic[a] || (int64_t)d->nel[a] * d->p >= 3, GNN_EINVAL,
+                    "gnn_graph_build: periodic axis %d needs nel*p >= 3", a);
+    }
+    GNN_REQUIRE(d->jitter_frac >= 0.0 && d->jitter_frac < 0.5, GNN_EINVAL,
+                "gnn_graph_build: jitter_frac must be in [0, 0.5)");
+    gnn_graph* g = new (std::nothrow) gnn_graph();
+    GNN_REQUIRE(g, GNN_ENOMEM, "gnn_graph_build: out of host memory");
+    try {
+        g->p = d->p;
+        int64_t N = 1;
+        for (int a = 0; a < 3; ++a) {
+            g->nel[a] = d->nel[a];
+            g->extent[a] = d->extent[a];
+            g->periodic[a] = d->periodic[a] ? 1 : 0;
+            g->L[a] = d->nel[a] * d->p + (g->periodic[a] ? 0 : 1);
+            N *= g->L[a];
+        }
+        GNN_REQUIRE(N * 6 < (int64_t)std::numeric_limits<int32_t>::max() * 4, GNN_ESHAPE,
+                    "gnn_graph_build: graph too large");
+        g->n_nodes = N;
+        const int p = d->p;
+        std::vector<double> xi = gnn::gll_points(p);
+        std::vector<double> coord[3], spacing[3];
+        for (int a = 0; a < 3; ++a) {
+            int La = g->L[a];
+            double h = d->extent[a] / d->nel[a];
+            coord[a].assign(La, 0.0);
+            for (int e = 0; e < d->nel[a]; ++e)
+                for (int k = 0; k <= p; ++k) {
+                    int gi = e * p + k;
+                    if (gi < La) coord[a][gi] = (e + 0.5 * (xi[k] + 1.0)) * h;
+                }
+            spacing[a].assign(La, std::numeric_limits<double>::infinity());
+            for (int i = 0; i < La; ++i) {
+                double s = spacing[a][i];
+                if (i > 0) s = std::min(s, coord[a][i] - coord[a][i - 1]);
+                if (i + 1 < La) s = std::min(s, coord[a][i + 1] - coord[a][i]);
+                if (g->periodic[a] && (i == 0 || i == La - 1))
+                    s = std::min(s, coord[a][0] + d->extent[a] - coord[a][La - 1]);
+                spacing[a][i] = s;
+            }
+        }
+        g->pos.resize(N * 3);
+        Lattice lt = lattice_of(g);
+        parallel_for((N + 65535) / 65536, [&](int64_t blk) {
+            int64_t g0 = blk * 65536, g1 = std::min(N, g0 + 65536);
+            for (int64_t gi = g0; gi < g1; ++gi) {
+                int64_t c[3];
+                lt.coords(gi, c);
+                for (int a = 0; a < 3; ++a) {
+                    double v = coord[a][c[a]];
+                    if (d->jitter && d->jitter_frac != 0.0) {
+                        bool face = !g->periodic[a] && (c[a] == 0 || c[a] == g->L[a] - 1);
+                        if (!face) v = v + d->jitter[gi * 3 + a] * d->jitter_frac * spacing[a][c[a]];
+                    }
+                    g->pos[gi * 3 + a] = v;
+                }
+            }
+        });
+        // lattice CSR: every lattice-adjacent pair lies in a common element
+        g->row_ptr.resize(N + 1);
+        g->row_ptr[0] = 0;
+        std::vector<uint8_t> deg(N);
+        parallel_for((N + 65535) / 65536, [&](int64_t blk) {
+            int64_t g0 = blk * 65536, g1 = std::min(N, g0 + 65536);
+            for (int64_t gi = g0; gi < g1; ++gi) {
+                int64_t c[3];
+                lt.coords(gi, c);
+                int n = 0;
+                for (int a = 0; a < 3; ++a) {
+                    if (g->periodic[a]) n += 2;
+                    else n += (c[a] > 0) + (c[a] < g->L[a] - 1);
+                }
+                deg[gi] = (uint8_t)n;
+            }
+        });
+        for (int64_t gi = 0; gi < N; ++gi) g->row_ptr[gi + 1] = g->row_ptr[gi] + deg[gi];
+        g->col.resize(g->row_ptr[N]);
+        parallel_for((N + 65535) / 65536, [&](int64_t blk) {
+            int64_t g0 = blk * 65536, g1 = std::min(N, g0 + 65536);
+            for (int64_t gi = g0; gi < g1; ++gi) {
+                int64_t c[3];
+                lt.coords(gi, c);
+                int64_t nb[6];
+                int n = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int s = -1; s <= 1; s += 2) {
+                        int64_t cc[3] = {c[0], c[1], c[2]};
+                        cc[a] += s;
+                        if (cc[a] < 0 || cc[a] >= g->L[a]) {
+                            if (!g->periodic[a]) continue;
+                            cc[a] = (cc[a] + g->L[a]) % g->L[a];
+                        }
+                        nb[n++] = lt.gid(cc[0], cc[1], cc[2]);
+                    }
+                std::sort(nb, nb + n);
+                std::copy(nb, nb + n, g->col.begin() + g->row_ptr[gi]);
+            }
+        });
+    } catch (const std::bad_alloc&) {
+        delete g;
+        return set_error(GNN_ENOMEM, "gnn_graph_build: out of host memory");
+    }
+    *out = g;
+    gnn::clear_error();
+    return GNN_OK;
+}
+
+void gnn_graph_destroy(gnn_graph* g) { delete g; }
+
+int gnn_graph_get_info(const gnn_graph* g, gnn_graph_info* info) {
+    GNN_REQUIRE(g && info, GNN_EINVAL, "gnn_graph_get_info: NULL argument");
+    info->n_nodes = g->n_nodes;
+    info->n_edges = (int64_t)g->col.size();
+    info->n_elem = (int64_t)g->nel[0] * g->nel[1] * g->nel[2];
+    for (int a = 0; a < 3; ++a) info->L[a] = g->L[a];
+    info->p = g->p;
+    return GNN_OK;
+}
+
+int gnn_graph_copy_pos(const gnn_graph* g, double* pos) {
+    GNN_REQUIRE(g && pos, GNN_EINVAL, "gnn_graph_copy_pos: NULL argument");
+    std::memcpy(pos, g->pos.data(), g->pos.size() * sizeof(double));
+    return GNN_OK;
+}
+
+int gnn_graph_copy_csr(const gnn_graph* g, int64_t* row_ptr, int64_t* col) {
+    GNN_REQUIRE(g && row_ptr && col, GNN_EINVAL, "gnn_graph_copy_csr: NULL argument");
+    std::memcpy(row_ptr, g->row_ptr.data(), g->row_ptr.size() * sizeof(int64_t));
+    std::memcpy(col, g->col.data(), g->col.size() * sizeof(int64_t));
+    return GNN_OK;
+}
+
+int gnn_graph_copy_elements(const gnn_graph* g, int64_t* en) {
+    GNN_REQUIRE(g && en, GNN_EINVAL, "gnn_graph_copy_elements: NULL argument");
+    Lattice lt = lattice_of(g);
+    const int q = g->p + 1;
+    int64_t n_elem = (int64_t)g->nel[0] * g->nel[1] * g->nel[2];
+    for (int64_t e = 0; e < n_elem; ++e) {
+        int64_t ex = e % g->nel[0], ey = (e / g->nel[0]) % g->nel[1], ez = e / ((int64_t)g->nel[0] * g->nel[1]);
+        for (int k = 0; k < q; ++k)
+            for (int j = 0; j < q; ++j)
+                for (int i = 0; i < q; ++i)
+                    en[e * q * q * q + i + q * (j + q * k)] =
+                        lt.gid((ex * g->p + i) % g->L[0], (ey * g->p + j) % g->L[1], (ez * g->p + k) % g->L[2]);
+    }
+    return GNN_OK;
+}
+
+int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method, const double* target_weights,
+                       gnn_partition** out) {
+    GNN_REQUIRE(g && out, GNN_EINVAL, "gnn_partition_halo: NULL argument");
+    *out = nullptr;
+    const int64_t n_elem = (int64_t)g->nel[0] * g->nel[1] * g->nel[2];
+    GNN_REQUIRE(R >= 1 && R <= 65535 && R <= n_elem, GNN_EINVAL,
+                "gnn_partition_halo: R=%d must be in 1..min(65535, n_elem)", R);
+    GNN_REQUIRE(method == GNN_PART_SLAB_Z || method == GNN_PART_RCB, GNN_EINVAL,
+                "gnn_partition_halo: unknown method %d", method);
+    GNN_REQUIRE(method != GNN_PART_SLAB_Z || R <= g->nel[2], GNN_EINVAL,
+                "gnn_partition_halo: slab partition needs R <= nel[2]");
+    std::vector<double> w(R, 1.0);
+    if (target_weights) {
+        for (int r = 0; r < R; ++r) {
+            GNN_REQUIRE(target_weights[r] > 0.0 && std::isfinite(target_weights[r]), GNN_EINVAL,
+                        "gnn_partition_halo: target weight %d not positive", r);
+            w[r] = target_weights[r];
+        }
+    }
+    gnn_partition* P = new (std::nothrow) gnn_partition();
+    GNN_REQUIRE(P, GNN_ENOMEM, "gnn_partition_halo: out of host memory");
+    try {
+        Lattice lt = lattice_of(g);
+        const int p = g->p;
+        const int q = p + 1;
+        const int64_t N = g->n_nodes;
+        // ---- element -> part
+        std::vector<int32_t> part(n_elem);
+        if (method == GNN_PART_SLAB_Z) {
+            for (int64_t e = 0; e < n_elem; ++e) {
+                int64_t ez = e / ((int64_t)g->nel[0] * g->nel[1]);
+                int32_t r = 0;
+                while (r + 1 < R && ez >= ((int64_t)(r + 1) * g->nel[2]) / R) ++r;
+                part[e] = r;
+            }
+        } else {
+            std::vector<double> centre(n_elem * 3);
+            double h[3];
+            for (int a = 0; a < 3; ++a) h[a] = g->extent[a] / g->nel[a];
+            for (int64_t e = 0; e < n_elem; ++e) {
+                int64_t c[3] = {e % g->nel[0], (e / g->nel[0]) % g->nel[1], e / ((int64_t)g->nel[0] * g->nel[1])};
+                for (int a = 0; a < 3; ++a) centre[e * 3 + a] = (c[a] + 0.5) * h[a];
+            }
+            std::vector<int64_t> elems(n_elem);
+            for (int64_t e = 0; e < n_elem; ++e) elems[e] = e;
+            rcb_split(centre, elems, 0, n_elem, 0, R, w, part);
+        }
+        std::vector<int64_t> elem_count(R, 0);
+        for (int64_t e = 0; e < n_elem; ++e) elem_count[part[e]]++;
+        for (int r = 0; r < R; ++r)
+            GNN_REQUIRE(elem_count[r] > 0, GNN_EINVAL, "gnn_partition_halo: part %d has no element", r);
+
+        // parts holding a lattice point / a lattice edge
+        auto node_parts = [&](int64_t gi, int32_t* ps) {
+            int64_t c[3], ea[3][2];
+            int na[3];
+            lt.coords(gi, c);
+            for (int a = 0; a < 3; ++a) na[a] = lt.elems_of_point(a, c[a], ea[a]);
+            int n = 0;
+            for (int i = 0; i < na[0]; ++i)
+                for (int j = 0; j < na[1]; ++j)
+                    for (int k = 0; k < na[2]; ++k) {
+                        int32_t r = part[lt.elem_id(ea[0][i], ea[1][j], ea[2][k])];
+                        bool seen = false;
+                        for (int t = 0; t < n; ++t) seen |= (ps[t] == r);
+                        if (!seen) ps[n++] = r;
+                    }
+            return n;
+        };
+        auto edge_parts = [&](int64_t gu, int64_t gv, int32_t* ps) {
+            int64_t cu[3], cv[3];
+            lt.coords(gu, cu);
+            lt.coords(gv, cv);
+            int axis = 0;
+            for (int a = 0; a < 3; ++a)
+                if (cu[a] != cv[a]) axis = a;
+            int64_t ea[3][2];
+            int na[3];
+            for (int a = 0; a < 3; ++a) {
+                if (a == axis) {
+                    int64_t lo = cu[a], hi = cv[a];
+                    // segment index = lower end, or the wrap segment L-1 -> 0
+                    int64_t seg = (std::llabs(hi - lo) == 1) ? std::min(lo, hi) : std::max(lo, hi);
+                    ea[a][0] = seg / p;
+                    na[a] = 1;
+                } else {
+                    na[a] = lt.elems_of_point(a, cu[a], ea[a]);
+                }
+            }
+            int n = 0;
+            for (int i = 0; i < na[0]; ++i)
+                for (int j = 0; j < na[1]; ++j)
+                    for (int k = 0; k < na[2]; ++k) {
+                        int32_t r = part[lt.elem_id(ea[0][i], ea[1][j], ea[2][k])];
+                        bool seen = false;
+                        for (int t = 0; t < n; ++t) seen |= (ps[t] == r);
+                        if (!seen) ps[n++] = r;
+                    }
+            return n;
+        };
+
+        // ---- per-part local nodes and edges
+        std::vector<std::vector<int64_t>> nodes(R);
+        std::vector<std::vector<int32_t>> lptr(R), lcol(R);
+        std::vector<std::vector<uint8_t>> ldeg(R), ndeg(R);
+        std::vector<std::vector<int64_t>> elems_of(R);
+        for (int64_t e = 0; e < n_elem; ++e) elems_of[part[e]].push_back(e);
+        std::atomic<int> err(0);
+        parallel_for(R, [&](int64_t r) {
+            std::vector<int64_t>& nd = nodes[r];
+            nd.reserve(elems_of[r].size() * q * q * q);
+            for (int64_t e : elems_of[r]) {
+                int64_t ex = e % g->nel[0], ey = (e / g->nel[0]) % g->nel[1], ez = e / ((int64_t)g->nel[0] * g->nel[1]);
+                for (int k = 0; k < q; ++k)
+                    for (int j = 0; j < q; ++j)
+                        for (int i = 0; i < q; ++i)
+                            nd.push_back(lt.gid((ex * p + i) % g->L[0], (ey * p + j) % g->L[1], (ez * p + k) % g->L[2]));
+            }
+            std::sort(nd.begin(), nd.end());
+            nd.erase(std::unique(nd.begin(), nd.end()), nd.end());
+            const int64_t n = (int64_t)nd.size();
+            lptr[r].assign(n + 1, 0);
+            ndeg[r].resize(n);
+            int32_t ps[8];
+            for (int64_t i = 0; i < n; ++i) {
+                int64_t gi = nd[i];
+                ndeg[r][i] = (uint8_t)node_parts(gi, ps);
+                for (int64_t t = g->row_ptr[gi]; t < g->row_ptr[gi + 1]; ++t) {
+                    int64_t gj = g->col[t];
+                    int m = edge_parts(gi, gj, ps);
+                    bool mine = false;
+                    for (int s = 0; s < m; ++s) mine |= (ps[s] == (int32_t)r);
+                    if (!mine) continue;
+                    auto it = std::lower_bound(nd.begin(), nd.end(), gj);
+                    if (it == nd.end() || *it != gj) {
+                        err = 1;
+                        continue;
+                    }
+                    lcol[r].push_back((int32_t)(it - nd.begin()));
+                    ldeg[r].push_back((uint8_t)m);
+                }
+                lptr[r][i + 1] = (int32_t)lcol[r].size();
+            }
+        });
+        GNN_REQUIRE(!err, GNN_EHALO, "gnn_partition_halo: internal edge/node mismatch");
+
+        // ---- concatenate
+        P->R = R;
+        P->row_offsets.assign(R + 1, 0);
+        P->edge_offsets.assign(R + 1, 0);
+        for (int r = 0; r < R; ++r) {
+            P->row_offsets[r + 1] = P->row_offsets[r] + (int64_t)nodes[r].size();
+            P->edge_offsets[r + 1] = P->edge_offsets[r] + (int64_t)lcol[r].size();
+        }
+        const int64_t NR = P->row_offsets[R], NE = P->edge_offsets[R];
+        GNN_REQUIRE(NR < (int64_t)std::numeric_limits<int32_t>::max() &&
+                        NE < (int64_t)std::numeric_limits<int32_t>::max(),
+                    GNN_ESHAPE, "gnn_partition_halo: more than 2^31-1 rows or edges");
+        P->row_gid.resize(NR);
+        P->row_ptr.resize(NR + 1);
+        P->col.resize(NE);
+        P->edge_deg.resize(NE);
+        P->node_deg.resize(NR);
+        P->row_ptr[0] = 0;
+        parallel_for(R, [&](int64_t r) {
+            int64_t ro = P->row_offsets[r], eo = P->edge_offsets[r];
+            for (size_t i = 0; i < nodes[r].size(); ++i) {
+                P->row_gid[ro + i] = nodes[r][i];
+                P->node_deg[ro + i] = ndeg[r][i];
+                P->row_ptr[ro + i + 1] = (int32_t)(eo + lptr[r][i + 1]);
+            }
+            for (size_t t = 0; t < lcol[r].size(); ++t) {
+                P->col[eo + t] = (int32_t)(ro + lcol[r][t]);
+                P->edge_deg[eo + t] = ldeg[r][t];
+            }
+        });
+        int32_t maxdeg = 0;
+        for (int64_t i = 0; i < NR; ++i) maxdeg = std::max(maxdeg, P->row_ptr[i + 1] - P->row_ptr[i]);
+        P->max_in_degree = maxdeg;
+
+        // ---- sender CSR (counting sort by sender row, edge ids ascending)
+        P->t_ptr.assign(NR + 1, 0);
+        for (int64_t t = 0; t < NE; ++t) P->t_ptr[P->col[t] + 1]++;
+        for (int64_t i = 0; i < NR; ++i) P->t_ptr[i + 1] += P->t_ptr[i];
+        P->t_eid.resize(NE);
+        {
+            std::vector<int32_t> fill(P->t_ptr.begin(), P->t_ptr.end() - 1);
+            for (int64_t t = 0; t < NE; ++t) P->t_eid[fill[P->col[t]]++] = (int32_t)t;
+        }
+
+        // ---- copy list of shared global ids, copies in increasing part order
+        std::vector<std::pair<int64_t, int32_t>> shared;
+        for (int64_t i = 0; i < NR; ++i)
+            if (P->node_deg[i] > 1) shared.emplace_back(P->row_gid[i], (int32_t)i);
+        std::sort(shared.begin(), shared.end());
+        P->halo_ptr.clear();
+        P->halo_rows.resize(shared.size());
+        P->part_stats.assign((size_t)R * 3, 0);
+        std::vector<int32_t> row_part(NR);
+        for (int r = 0; r < R; ++r)
+            for (int64_t i = P->row_offsets[r]; i < P->row_offsets[r + 1]; ++i) row_part[i] = r;
+        std::vector<std::vector<int32_t>> neigh(R);
+        for (size_t s = 0; s < shared.size();) {
+            size_t e = s;
+            while (e < shared.size() && shared[e].first == shared[s].first) ++e;
+            GNN_REQUIRE((int64_t)(e - s) == P->node_deg[shared[s].second], GNN_EHALO,
+                        "gnn_partition_halo: copy count of gid %lld differs from its degree",
+                        (long long)shared[s].first);
+            P->halo_ptr.push_back((int32_t)s);
+            for (size_t k = s; k < e; ++k) {
+                P->halo_rows[k] = shared[k].second;
+                int32_t rk = row_part[shared[k].second];
+                P->part_stats[rk * 3 + 1] += (int64_t)(e - s - 1);
+                for (size_t m = s; m < e; ++m)
+                    if (m != k) neigh[rk].push_back(row_part[shared[m].second]);
+            }
+            s = e;
+        }
+        P->halo_ptr.push_back((int32_t)shared.size());
+        for (int r = 0; r < R; ++r) {
+            P->part_stats[r * 3 + 0] = P->row_offsets[r + 1] - P->row_offsets[r];
+            std::sort(neigh[r].begin(), neigh[r].end());
+            P->part_stats[r * 3 + 2] =
+                (int64_t)(std::unique(neigh[r].begin(), neigh[r].end()) - neigh[r].begin());
+        }
+
+        // ---- receiver-aligned edge tiles of <= GNN_EDGE_TILE edges
+        GNN_REQUIRE(maxdeg <= GNN_EDGE_TILE, GNN_EUNSUPPORTED,
+                    "gnn_partition_halo: in-degree %d exceeds the edge tile (%d)", maxdeg, GNN_EDGE_TILE);
+        P->edge_tiles.clear();
+        P->edge_tiles.push_back(0);
+        {
+            int64_t r0 = 0;
+            while (r0 < NR) {
+                int64_t r1 = r0;
+                while (r1 < NR && P->row_ptr[r1 + 1] - P->row_ptr[r0] <= GNN_EDGE_TILE) ++r1;
+                P->edge_tiles.push_back((int32_t)r1);
+                r0 = r1;
+            }
+        }
+        // ---- positions per row
+        P->row_pos.resize(NR * 3);
+        for (int64_t i = 0; i < NR; ++i)
+            for (int a = 0; a < 3; ++a) P->row_pos[i * 3 + a] = g->pos[P->row_gid[i] * 3 + a];
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return set_error(GNN_ENOMEM, "gnn_partition_halo: out of host memory");
+    }
+    *out = P;
+    gnn::clear_error();
+    return GNN_OK;
+}
+
+void gnn_partition_destroy(gnn_partition* p) { delete p; }
+
+int gnn_partition_get_info(const gnn_partition* P, gnn_partition_info* info) {
+    GNN_REQUIRE(P && info, GNN_EINVAL, "gnn_partition_get_info: NULL argument");
+    info->n_parts = P->R;
+    info->max_in_degree = P->max_in_degree;
+    info->n_rows = (int64_t)P->row_gid.size();
+    info->n_edges = (int64_t)P->col.size();
+    info->n_shared = (int64_t)P->halo_ptr.size() - 1;
+    info->n_copies = (int64_t)P->halo_rows.size();
+    info->n_edge_tiles = (int64_t)P->edge_tiles.size() - 1;
+    info->n_node_tiles = (info->n_rows + GNN_NODE_TILE - 1) / GNN_NODE_TILE;
+    return GNN_OK;
+}
+
+int gnn_partition_copy(const gnn_partition* P, int32_t what, void* dst, size_t bytes) {
+    GNN_REQUIRE(P && dst, GNN_EINVAL, "gnn_partition_copy: NULL argument");
+    const void* src = nullptr;
+    size_t n = 0;
+    std::vector<float> tmp;
+    switch (what) {
+        case GNN_P_ROW_OFFSETS: src = P->row_offsets.data(); n = P->row_offsets.size() * 8; break;
+        case GNN_P_EDGE_OFFSETS: src = P->edge_offsets.data(); n = P->edge_offsets.size() * 8; break;
+        case GNN_P_ROW_GID: src = P->row_gid.data(); n = P->row_gid.size() * 8; break;
+        case GNN_P_ROW_PTR: src = P->row_ptr.data(); n = P->row_ptr.size() * 4; break;
+        case GNN_P_COL: src = P->col.data(); n = P->col.size() * 4; break;
+        case GNN_P_EDGE_DEG: src = P->edge_deg.data(); n = P->edge_deg.size(); break;
+        case GNN_P_NODE_DEG: src = P->node_deg.data(); n = P->node_deg.size(); break;
+        case GNN_P_EDGE_W:
+            tmp.resize(P->edge_deg.size());
+            for (size_t i = 0; i < tmp.size(); ++i) tmp[i] = 1.0f / (float)P->edge_deg[i];
+            src = tmp.data(); n = tmp.size() * 4; break;
+        case GNN_P_NODE_W:
+            tmp.resize(P->node_deg.size());
+            for (size_t i = 0; i < tmp.size(); ++i) tmp[i] = 1.0f / (float)P->node_deg[i];
+            src = tmp.data(); n = tmp.size() * 4; break;
+        case GNN_P_T_PTR: src = P->t_ptr.data(); n = P->t_ptr.size() * 4; break;
+        case GNN_P_T_EID: src = P->t_eid.data(); n = P->t_eid.size() * 4; break;
+        case GNN_P_HALO_PTR: src = P->halo_ptr.data(); n = P->halo_ptr.size() * 4; break;
+        case GNN_P_HALO_ROWS: src = P->halo_rows.data(); n = P->halo_rows.size() * 4; break;
+        case GNN_P_EDGE_TILES: src = P->edge_tiles.data(); n = P->edge_tiles.size() * 4; break;
+        case GNN_P_ROW_POS: src = P->row_pos.data(); n = P->row_pos.size() * 8; break;
+        case GNN_P_PART_STATS: src = P->part_stats.data(); n = P->part_stats.size() * 8; break;
+        case GNN_P_EDGE_ATTR: {
+            const int64_t NR = (int64_t)P->row_gid.size();
+            tmp.resize(P->col.size() * 4);
+            for (int64_t i = 0; i < NR; ++i)
+                for (int32_t t = P->row_ptr[i]; t < P->row_ptr[i + 1]; ++t) {
+                    const double* pr = &P->row_pos[i * 3];
+                    const double* ps = &P->row_pos[(int64_t)P->col[t] * 3];
+                    double dx = ps[0] - pr[0], dy = ps[1] - pr[1], dz = ps[2] - pr[2];
+                    tmp[(size_t)t * 4 + 0] = (float)dx;
+                    tmp[(size_t)t * 4 + 1] = (float)dy;
+                    tmp[(size_t)t * 4 + 2] = (float)dz;
+                    tmp[(size_t)t * 4 + 3] = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
+                }
+            src = tmp.data(); n = tmp.size() * 4; break;
+        }
+        default: return set_error(GNN_EINVAL, "gnn_partition_copy: unknown array %d", what);
+    }
+    GNN_REQUIRE(bytes == n, GNN_ESHAPE, "gnn_partition_copy: array %d has %zu bytes, buffer %zu", what, n, bytes);
+    if (n) std::memcpy(dst, src, n);
+    return GNN_OK;
+}
+
+}  // extern "C"

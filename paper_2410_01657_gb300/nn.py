@@ -1,0 +1,260 @@
+"""PyTorch front end of libgnnmp: autograd Functions and the encode-process-decode network.
+
+torch provides device memory, streams and autograd bookkeeping only; every
+step of the network runs in libgnnmp's kernels through ``binding``:
+
+* ``ConsistentMPFunction`` -- one consistent NMP layer (Eq. 5a-5e) with its
+  hand-written adjoint (``gnn_mp_forward`` / ``gnn_mp_backward``), recomputing
+  the layer's MLP activations in the backward pass instead of storing them;
+* ``RowMLPFunction`` -- node/edge encoders and the node decoder (Sec. III);
+* ``ConsistentLossFunction`` -- the consistent MSE loss, Eq. 8a-8c;
+* ``ConsistentGNN`` -- encoders, M consistent layers, decoder (Sec. III).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .graph import DeviceGraph
+
+PRECISIONS = {"fp32": B.GNN_PREC_FP32, "bf16": B.GNN_PREC_BF16}
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def mlp_struct(dims, tensors, has_ln: bool) -> B.gnn_mlp:
+    """gnn_mlp view of tensors ordered [W_0..W_{n-1}, b_0..b_{n-1}, (gamma, beta)]."""
+    n = len(dims) - 1
+    s = B.gnn_mlp()
+    s.n_lin = n
+    for k, d in enumerate(dims):
+        s.dims[k] = int(d)
+    for k in range(n):
+        s.W[k] = B.ptr(tensors[k])
+        s.b[k] = B.ptr(tensors[n + k])
+    if has_ln:
+        s.gamma = B.ptr(tensors[2 * n])
+        s.beta = B.ptr(tensors[2 * n + 1])
+    return s
+
+
+def n_mlp_tensors(dims, has_ln: bool) -> int:
+    return 2 * (len(dims) - 1) + (2 if has_ln else 0)
+
+
+def mp_config(hidden: int, precision: str, halo: bool = True, ln_eps: float = 1e-5, flags: int = 0):
+    c = B.gnn_mp_config()
+    c.hidden = int(hidden)
+    c.precision = PRECISIONS[precision]
+    c.halo_mode = B.GNN_HALO_SYNC if halo else B.GNN_HALO_NONE
+    c.flags = int(flags)
+    c.ln_eps = float(ln_eps)
+    return c
+
+
+def mp_params(edge_dims, node_dims, tensors) -> B.gnn_mp_params:
+    ne = n_mlp_tensors(edge_dims, True)
+    p = B.gnn_mp_params()
+    p.edge = mlp_struct(edge_dims, tensors[:ne], True)
+    p.node = mlp_struct(node_dims, tensors[ne:], True)
+    return p
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def mp_workspace_sizes(G: DeviceGraph, cfg, W) -> tuple:
+    f, b = C.c_size_t(), C.c_size_t()
+    B.call("gnn_mp_workspace_size", C.byref(G.struct), C.byref(cfg), C.byref(W), C.byref(f), C.byref(b))
+    return int(f.value), int(b.value)
+
+
+def gnn_mp_forward(G: DeviceGraph, cfg, W, x, e, x_out, e_out, a_star=None, ws=None):
+    """Direct call of gnn_mp_forward on preallocated tensors (no autograd)."""
+    if ws is None:
+        ws = workspace(mp_workspace_sizes(G, cfg, W)[0], x.device)
+    B.call("gnn_mp_forward", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(x_out),
+           B.ptr(e_out), B.ptr(a_star), B.ptr(ws), ws.numel(), _stream())
+
+
+def gnn_mp_backward(G: DeviceGraph, cfg, W, x, e, a_star, dx_out, de_out, dx_in, de_in, dW, ws=None):
+    """Direct call of gnn_mp_backward on preallocated tensors; dW accumulates."""
+    if ws is None:
+        ws = workspace(mp_workspace_sizes(G, cfg, W)[1], x.device)
+    B.call("gnn_mp_backward", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(a_star),
+           B.ptr(dx_out), B.ptr(de_out), B.ptr(dx_in), B.ptr(de_in), C.byref(dW), B.ptr(ws), ws.numel(),
+           _stream())
+
+
+def gnn_halo_exchange(G: DeviceGraph, rows: torch.Tensor) -> None:
+    B.call("gnn_halo_exchange", C.byref(G.struct), B.ptr(rows), int(rows.shape[1]), _stream())
+
+
+class ConsistentMPFunction(torch.autograd.Function):
+    """One consistent NMP layer, Eq. 5a-5e, with the hand-written adjoint (Eq. 3)."""
+
+    @staticmethod
+    def forward(ctx, x, e, G, cfg_args, edge_dims, node_dims, *params):
+        cfg = mp_config(*cfg_args)
+        W = mp_params(edge_dims, node_dims, params)
+        fwd, _ = mp_workspace_sizes(G, cfg, W)
+        x = x.contiguous()
+        e = e.contiguous()
+        x_out = torch.empty_like(x)
+        e_out = torch.empty_like(e)
+        a_star = torch.empty_like(x)
+        gnn_mp_forward(G, cfg, W, x, e, x_out, e_out, a_star, workspace(fwd, x.device))
+        ctx.G, ctx.cfg_args, ctx.dims = G, cfg_args, (edge_dims, node_dims)
+        ctx.save_for_backward(x, e, a_star, *params)
+        return x_out, e_out
+
+    @staticmethod
+    def backward(ctx, dx_out, de_out):
+        x, e, a_star, *params = ctx.saved_tensors
+        G = ctx.G
+        cfg = mp_config(*ctx.cfg_args)
+        W = mp_params(*ctx.dims, params)
+        dparams = [torch.zeros_like(p) for p in params]
+        dW = mp_params(*ctx.dims, dparams)
+        _, bwd = mp_workspace_sizes(G, cfg, W)
+        dx = torch.empty_like(x)
+        de = torch.empty_like(e)
+        dx_out = torch.zeros_like(x) if dx_out is None else dx_out.contiguous()
+        de_out = None if de_out is None else de_out.to(e.dtype).contiguous()
+        gnn_mp_backward(G, cfg, W, x, e, a_star, dx_out, de_out, dx, de, dW, workspace(bwd, x.device))
+        return (dx, de, None, None, None, None, *dparams)
+
+
+class RowMLPFunction(torch.autograd.Function):
+    """Row-wise MLP block (encoders, decoder)."""
+
+    @staticmethod
+    def forward(ctx, X, dims, has_ln, out_bf16, ln_eps, need_dx, *params):
+        P = mlp_struct(dims, params, has_ln)
+        f, b = C.c_size_t(), C.c_size_t()
+        rows = X.shape[0]
+        B.call("gnn_mlp_workspace_size", C.byref(P), rows, C.byref(f), C.byref(b))
+        X = X.contiguous()
+        Y = torch.empty((rows, dims[-1]), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=X.device)
+        ws = workspace(f.value, X.device)
+        B.call("gnn_mlp_forward", C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps), B.ptr(ws),
+               ws.numel(), _stream())
+        ctx.meta = (dims, has_ln, out_bf16, ln_eps, need_dx, int(b.value))
+        ctx.save_for_backward(X, *params)
+        return Y
+
+    @staticmethod
+    def backward(ctx, dY):
+        X, *params = ctx.saved_tensors
+        dims, has_ln, out_bf16, ln_eps, need_dx, bwd = ctx.meta
+        P = mlp_struct(dims, params, has_ln)
+        dparams = [torch.zeros_like(p) for p in params]
+        dP = mlp_struct(dims, dparams, has_ln)
+        dY = dY.to(torch.bfloat16 if out_bf16 else torch.float32).contiguous()
+        dX = torch.empty_like(X) if need_dx else None
+        ws = workspace(bwd, X.device)
+        B.call("gnn_mlp_backward", C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16), B.ptr(dX),
+               C.byref(dP), float(ln_eps), B.ptr(ws), ws.numel(), _stream())
+        return (dX, None, None, None, None, None, *dparams)
+
+
+class ConsistentLossFunction(torch.autograd.Function):
+    """Consistent MSE loss, Eq. 8a-8c (1/d_i-weighted, N_eff-normalised)."""
+
+    @staticmethod
+    def forward(ctx, y, t, G):
+        y = y.contiguous()
+        t = t.contiguous()
+        loss = torch.empty((), dtype=torch.float32, device=y.device)
+        dy = torch.empty_like(y)
+        ws = workspace(1 << 16, y.device)
+        B.call("gnn_consistent_loss", C.byref(G.struct), B.ptr(y), B.ptr(t), int(y.shape[1]), B.ptr(loss),
+               B.ptr(dy), B.ptr(ws), ws.numel(), _stream())
+        ctx.save_for_backward(dy)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        (dy,) = ctx.saved_tensors
+        return dy * g, None, None
+
+
+def consistent_loss(y, t, G: DeviceGraph):
+    return ConsistentLossFunction.apply(y, t, G)
+
+
+class _MLP(torch.nn.Module):
+    def __init__(self, P: dict, device):
+        super().__init__()
+        self.dims = [P["W"][0].shape[1]] + [w.shape[0] for w in P["W"]]
+        self.has_ln = "gamma" in P
+        ts = [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if self.has_ln else [])
+        self.params = torch.nn.ParameterList(
+            [torch.nn.Parameter(torch.as_tensor(np.asarray(t), dtype=torch.float32, device=device).contiguous())
+             for t in ts])
+
+    def tensors(self):
+        return list(self.params)
+
+
+class ConsistentGNN(torch.nn.Module):
+    """Encode-process-decode GNN with consistent NMP layers (Sec. III).
+
+    ``params`` is the nested dict of arrays made by ``synthetic.gnn_params``
+    (float64 arrays are cast to FP32 master weights)."""
+
+    def __init__(self, params: dict, precision: str = "bf16", halo: bool = True, ln_eps: float = 1e-5,
+                 device="cuda"):
+        super().__init__()
+        self.precision = precision
+        self.halo = halo
+        self.ln_eps = ln_eps
+        self.enc_node = _MLP(params["enc_node"], device)
+        self.enc_edge = _MLP(params["enc_edge"], device)
+        self.layers = torch.nn.ModuleList()
+        for lp in params["layers"]:
+            m = torch.nn.Module()
+            m.edge = _MLP(lp["edge"], device)
+            m.node = _MLP(lp["node"], device)
+            self.layers.append(m)
+        self.dec = _MLP(params["dec"], device)
+        self.hidden = self.enc_node.dims[-1]
+
+    def _row_mlp(self, m: _MLP, X, out_bf16: bool, need_dx: bool):
+        return RowMLPFunction.apply(X, m.dims, m.has_ln, out_bf16, self.ln_eps, need_dx, *m.tensors())
+
+    def encode(self, G: DeviceGraph, u, attr):
+        x = self._row_mlp(self.enc_node, u, False, False)
+        e = self._row_mlp(self.enc_edge, attr, self.precision == "bf16", False)
+        return x, e
+
+    def process(self, G: DeviceGraph, x, e):
+        cfg_args = (self.hidden, self.precision, self.halo, self.ln_eps, 0)
+        for layer in self.layers:
+            x, e = ConsistentMPFunction.apply(x, e, G, cfg_args, layer.edge.dims, layer.node.dims,
+                                              *layer.edge.tensors(), *layer.node.tensors())
+        return x, e
+
+    def forward(self, G: DeviceGraph, u, attr):
+        x, e = self.encode(G, u, attr)
+        x, e = self.process(G, x, e)
+        return self._row_mlp(self.dec, x, False, True)
+
+    def grads_numpy(self) -> dict:
+        """Parameter gradients in the nested-dict layout of ``synthetic.gnn_params``."""
+        def mlp(m: _MLP):
+            n = len(m.dims) - 1
+            g = [p.grad.double().cpu().numpy() if p.grad is not None else np.zeros(p.shape) for p in m.params]
+            out = {"W": g[:n], "b": g[n:2 * n]}
+            if m.has_ln:
+                out["gamma"], out["beta"] = g[2 * n], g[2 * n + 1]
+            return out
+        return {"enc_node": mlp(self.enc_node), "enc_edge": mlp(self.enc_edge),
+                "layers": [{"edge": mlp(l.edge), "node": mlp(l.node)} for l in self.layers],
+                "dec": mlp(self.dec)}

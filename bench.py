@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of the consistent NMP layer (forward + backward) on one GB300.
+
+One step = M=4 consistent NMP layers forward (Eq. 5a-5e) then their adjoint,
+on the 16^3-element p=5 GLL brick (531,441 nodes, 3,149,280 directed edges)
+split into 8 RCB sub-graphs resident on the GPU, H=64, MLPs with 2 hidden
+layers. Inputs (x0, e0 from the encoders, a seeded upstream gradient) are
+resident in HBM; the edge state (>400 MB) is larger than L2, so no flush is
+needed between steps. Metric: MP-layer edges/s = 3,149,280 * 4 / step time.
+
+value     -- fused BF16 path (FP32 accumulation and sums), device-timed.
+fp32      -- the plain FP32 SIMT path on the same graph and step.
+e2e       -- the full network training step through the public API
+             (encoders, 4 layers, decoder, consistent loss, backward) with
+             inputs copied from pinned host memory each step and the loss read
+             back, in the same metric.
+roofline  -- the dominant kernel's algorithmic bytes (or FLOPs) per launch over
+             its CUDA-event launch time, against MEASURED_PEAKS.json.
+cpu_baseline -- the FP64 numpy oracle on a bounded sample, host cores.
+
+``--impl reference`` times the oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NEL, P, R, H, NH, M = (16, 16, 16), 5, 8, 64, 2, 4
+E_UNPART = 6 * 81 * 81 * 80          # directed edges of the 81^3 GLL lattice
+N_UNPART = 81 ** 3
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self) -> dict:
+        sm = [float(s[0]) for s in self.samples if len(s) >= 7 and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) >= 7 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples if len(s) >= 7
+                          for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+
+def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int) -> float | None:
+    """Least HBM bytes one launch of a fused kernel must move (one layer).
+
+    Per edge: read e (s_e H), write e' (s_e H), col (4), 1/d (4); per row:
+    the row's CSR pointer and node tensors (see the per-kernel notes)."""
+    E, N = G.n_edges, G.n_rows
+    se = edge_bytes
+    if kernel == "k_edge_fwd":      # e in/out, col, w, P/Q gathers (bf16 2H per row), a out (fp32 H)
+        return E * (2 * se * hidden + 8) + N * (2 * 2 * hidden + 4 * hidden + 4)
+    if kernel == "k_edge_bwd":      # e in, de_out in, de_in out, dz1 out, col, w; da in, P/Q, dP out per row
+        return E * (4 * se * hidden + 8) + N * (4 * hidden + 2 * 2 * hidden + 4 * hidden + 4)
+    return None
+
+
+def sgemm_flops_per_step(G, hidden: int, n_lin: int, layers: int) -> float:
+    """FP32 SIMT GEMM FLOPs of one plain-path step (forward, recompute, dgrad, wgrad)."""
+    E, N, Hh = G.n_edges, G.n_rows, hidden
+    def chain(rows, d0):
+        dims = [d0] + [Hh] * n_lin
+        return sum(2.0 * rows * dims[k] * dims[k + 1] for k in range(n_lin))
+    per_layer_fwd = chain(E, 3 * Hh) + chain(N, 2 * Hh)
+    return layers * per_layer_fwd * 4.0     # forward + recompute + dgrad + wgrad
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured",
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+
+def oracle_sample(n_el: int, steps: int = 1):
+    """Time the FP64 oracle on an n_el^3 p=5 brick (8 RCB parts, H=64, 4 layers fwd+bwd).
+    Returns (edges/s in the metric's unit, seconds per step, sample description, threads)."""
+    import numpy as np
+
+    import synthetic as syn
+    from oracle import graph as og
+    from oracle import model as om
+
+    b = og.build_brick((n_el,) * 3, P)
+    subs = og.build_subgraphs(b, og.partition_rcb(b, R), R)
+    params = syn.gnn_params(SEED, H, NH, M)
+    rng = np.random.default_rng(1)
+    xg = rng.standard_normal((b.n_nodes, H))
+    xs = [xg[sg.gid] for sg in subs]
+    es = [rng.standard_normal((sg.n_edges, H)) for sg in subs]
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        caches, x, e = [], xs, es
+        for lp in params["layers"]:
+            x, e, c = om.layer_forward(lp, subs, x, e)
+            caches.append(c)
+        dx = [np.ones_like(a) for a in x]
+        de = [np.zeros_like(a) for a in e]
+        for li in range(M - 1, -1, -1):
+            dx, de, _ = om.layer_backward(params["layers"][li], subs, caches[li], dx, de)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return (b.n_edges * M / t, t,
+            f"{n_el}^3 elements p=5 ({b.n_nodes} nodes, {b.n_edges} edges), 8 RCB parts, H=64, "
+            f"4 layers fwd+bwd, FP64 numpy", _blas_threads())
+
+
+def _blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(4)
+    vals, secs = [], []
+    desc = threads = None
+    for _ in range(args.steps):
+        v, t, desc, threads = oracle_sample(4)
+        vals.append(v)
+        secs.append(t)
+    t = sum(secs) / len(secs)
+    value = 52920 * M / t
+    line = {"impl": "reference", "metric": "MP-layer edges/s fwd+bwd", "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "consistent NMP layers x4 fwd+bwd, FP64 oracle sample "
+                                                        "(4^3 elements p=5, 8 RCB parts, H=64)"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def build_problem(dev, precision):
+    import numpy as np
+    import torch
+
+    import synthetic as syn
+    from paper_2410_01657_gb300 import nn as gnn
+    from paper_2410_01657_gb300.graph import MeshGraph
+
+    part = MeshGraph(NEL, P).partition(R, "rcb")
+    G = part.to_device(dev)
+    params = syn.gnn_params(SEED, H, NH, M)
+    modes = syn.fourier_modes(SEED, 8)
+    pos = part.array("row_pos")
+    u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=dev)
+    t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=dev)
+    net = gnn.ConsistentGNN(params, precision=precision, device=dev)
+    with torch.no_grad():
+        x0, e0 = net.encode(G, u, G.edge_attr())
+    layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
+    stack = gnn.LayerStack(G, layers, H, precision, x0, e0)
+    dx_top = torch.tensor(syn.normal((part.n_rows, H), SEED + 7, 1e-3), dtype=torch.float32, device=dev)
+    return part, G, net, stack, dx_top, u, t
+
+
+def time_stack(stack, dx_top, steps, warmup, profile=True):
+    import torch
+
+    from paper_2410_01657_gb300 import binding as B
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        stack.step(dx_top)
+    torch.cuda.synchronize()
+    if profile:
+        B.call("gnn_profile_start", 1 << 16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        stack.step(dx_top)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if profile:
+        B.call("gnn_profile_stop")
+    ms = ev0.elapsed_time(ev1) / steps
+    report = B.profile_report() if profile else {}
+    return ms, report
+
+
+def time_e2e(net, G, u, t, steps, warmup, dev):
+    """Full training step through the public API with host-resident inputs."""
+    import torch
+
+    from paper_2410_01657_gb300 import nn as gnn
+
+    u_h = u.cpu().pin_memory()
+    t_h = t.cpu().pin_memory()
+    a_h = G.edge_attr().cpu().pin_memory()
+    h2d = u_h.numel() * 4 + t_h.numel() * 4 + a_h.numel() * 4
+
+    def one():
+        ud = u_h.to(dev, non_blocking=True)
+        td = t_h.to(dev, non_blocking=True)
+        ad = a_h.to(dev, non_blocking=True)
+        net.zero_grad(set_to_none=True)
+        y = net(G, ud, ad)
+        loss = gnn.consistent_loss(y, td, G)
+        loss.backward()
+        return loss.item()
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        one()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, h2d, 4
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2410_01657_gb300 import _build
+    from paper_2410_01657_gb300 import binding as B
+    _build.build()
+    B.load()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    precision = args.precision
+    part, G, net, stack, dx_top, u, t = build_problem(dev, precision)
+    peaks = load_peaks()
+    barrier()
+    with ClockSampler(local) as clk:
+        ms, report = time_stack(stack, dx_top, args.steps, args.warmup)
+    barrier()
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * E_UNPART * M / (ms * 1e-3)
+    launches = sum(n for n, _ in report.values())
+    total_ms = sum(v for _, v in report.values()) or 1.0
+    top = max(report.items(), key=lambda kv: kv[1][1]) if report else ("none", (1, 0.0))
+    top_name, (top_n, top_ms) = top
+    edge_bytes = 2 if precision == "bf16" else 4
+    roof = None
+    abytes = algorithmic_bytes(top_name, G, H, edge_bytes)
+    if abytes is not None:
+        ach = abytes / (top_ms / top_n * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"],
+                "share": top_ms / total_ms}
+    elif top_name == "k_sgemm":
+        flops = sgemm_flops_per_step(G, H, NH + 2, M) * args.steps
+        ach = flops / (top_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_src": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock",
+                "share": top_ms / total_ms}
+
+    fp32 = None
+    if precision == "bf16" and not args.no_fp32:
+        del stack
+        torch.cuda.empty_cache()
+        _, G32, _, stack32, dx32, _, _ = build_problem(dev, "fp32")
+        ms32, _ = time_stack(stack32, dx32, max(3, args.steps // 2), 2, profile=False)
+        fp32 = {"value": E_UNPART * M / (ms32 * 1e-3), "unit": "edges/s", "ms_per_step": ms32,
+                "speedup_of_bf16": ms32 / ms}
+        del stack32
+        torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        ms_e, h2d, d2h = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
+        e2e = {"value": world * E_UNPART * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "step": "encoders + 4 layers + decoder + consistent loss, fwd+bwd, host inputs"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, tsec, desc, threads = oracle_sample(6)
+        cpu = {"value": v, "unit": "edges/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": tsec}
+
+    if rank == 0:
+        line = {"metric": "MP-layer edges/s fwd+bwd", "value": value, "unit": "edges/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+                "config": {"workload": "consistent NMP layers x4 fwd+bwd, 16^3 elements p=5 GLL brick "
+                                       "(531,441 nodes, 3,149,280 edges), 8 RCB sub-graphs, H=64, MLP 2 hidden",
+                           "rows": part.n_rows, "edges_partitioned": part.n_edges,
+                           "l2": "inputs larger than L2 (edge state > 400 MB), no flush",
+                           "parallelism": f"replicas x{world}"},
+                "nodes_per_s": world * N_UNPART * M / (ms * 1e-3),
+                "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu,
+                "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -268,6 +268,17 @@ int gnn_mlp_backward(const gnn_mlp* P, int64_t n_rows, const float* X, const voi
 int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, int32_t F,
                         float* loss, float* dy, void* ws, size_t ws_bytes, void* stream);
 
+/* ====================================================== kernel timing
+ * Benchmark support (the paper has no counterpart). Between gnn_profile_start
+ * and gnn_profile_stop every libgnnmp kernel launch is bracketed by a pair of
+ * CUDA events on its stream (up to `capacity` launches; later launches are
+ * not timed and the report says so). gnn_profile_report waits for the events
+ * and writes one text line per kernel name, "<name> <launches> <total_ms>\n",
+ * into out (host, `bytes` long, GNN_ENOMEM if too short). */
+int gnn_profile_start(int32_t capacity);
+int gnn_profile_stop(void);
+int gnn_profile_report(char* out, size_t bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,7 +109,22 @@ _SIGS = {
                                    C.POINTER(gnn_mlp), C.c_float, _P, C.c_size_t, _P]),
     "gnn_consistent_loss": (C.c_int, [C.POINTER(gnn_graph_dev), _P, _P, C.c_int32, _P, _P, _P,
                                       C.c_size_t, _P]),
+    "gnn_profile_start": (C.c_int, [C.c_int32]),
+    "gnn_profile_stop": (C.c_int, []),
+    "gnn_profile_report": (C.c_int, [C.c_char_p, C.c_size_t]),
 }
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total_ms)} of the last gnn_profile_start/stop window."""
+    buf = C.create_string_buffer(1 << 16)
+    call("gnn_profile_report", buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        if line and not line.startswith("#"):
+            name, n, ms = line.split()
+            out[name] = (int(n), float(ms))
+    return out
 
 _lib = None
 

@@ -637,7 +637,7 @@ int gnn_partition_get_info(const gnn_partition* P, gnn_partition_info* info) {
 }
 
 int gnn_partition_copy(const gnn_partition* P, int32_t what, void* dst, size_t bytes) {
-    GNN_REQUIRE(P && dst, GNN_EINVAL, "gnn_partition_copy: NULL argument");
+    GNN_REQUIRE(P && (dst || bytes == 0), GNN_EINVAL, "gnn_partition_copy: NULL argument");
     const void* src = nullptr;
     size_t n = 0;
     std::vector<float> tmp;

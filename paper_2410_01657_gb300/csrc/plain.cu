@@ -13,6 +13,7 @@
 
 #include "device_common.cuh"
 #include "plain.h"
+#include "profiler.h"
 
 namespace gnn {
 namespace plain {
@@ -436,7 +437,10 @@ static int gemm(const GemmArgs& a, int64_t nsplit, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return GNN_OK;
     dim3 grid((unsigned)((a.N + 63) / 64), (unsigned)((a.M + 63) / 64), (unsigned)std::max<int64_t>(1, nsplit));
     GNN_REQUIRE(grid.y <= 65535u && grid.z <= 65535u, GNN_ESHAPE, "sgemm: grid too large");
-    k_sgemm<<<grid, 256, 0, s>>>(a);
+    {
+        ProfScope _ps(s, "k_sgemm");
+        k_sgemm<<<grid, 256, 0, s>>>(a);
+    }
     GNN_LAUNCH_CHECK("k_sgemm");
     return GNN_OK;
 }
@@ -480,12 +484,21 @@ static int linear_bwd_weight(int64_t rows, int64_t K, int64_t N, const float* G,
     a.k_chunk = ch; a.c_split_stride = N * K;
     int rc = gemm(a, nz, s);
     if (rc) return rc;
-    k_reduce_partials<<<grid1(N * K), 256, 0, s>>>(part, nz, N * K, dW, 1);
+    {
+        ProfScope _ps(s, "k_reduce_partials");
+        k_reduce_partials<<<grid1(N * K), 256, 0, s>>>(part, nz, N * K, dW, 1);
+    }
     GNN_LAUNCH_CHECK("k_reduce_partials");
     if (db) {
-        k_colsum_partial<<<(unsigned)nz, 256, 0, s>>>(G, rows, N, (int)N, ch, part);
+        {
+            ProfScope _ps(s, "k_colsum_partial");
+            k_colsum_partial<<<(unsigned)nz, 256, 0, s>>>(G, rows, N, (int)N, ch, part);
+        }
         GNN_LAUNCH_CHECK("k_colsum_partial");
-        k_reduce_partials<<<grid1(N), 256, 0, s>>>(part, nz, N, db, 1);
+        {
+            ProfScope _ps(s, "k_reduce_partials");
+            k_reduce_partials<<<grid1(N), 256, 0, s>>>(part, nz, N, db, 1);
+        }
         GNN_LAUNCH_CHECK("k_reduce_partials");
     }
     return GNN_OK;
@@ -526,7 +539,10 @@ static int ln_fwd(const float* Z, int64_t rows, int H, const gnn_mlp& P, float e
                   cudaStream_t s) {
     if (rows == 0) return GNN_OK;
     unsigned blocks = (unsigned)std::min<int64_t>((rows + 7) / 8, 152 * 16);
-    k_ln_fwd<TR, TO><<<blocks, 256, 0, s>>>(Z, rows, H, P.gamma, P.beta, eps, res, out);
+    {
+        ProfScope _ps(s, "k_ln_fwd");
+        k_ln_fwd<TR, TO><<<blocks, 256, 0, s>>>(Z, rows, H, P.gamma, P.beta, eps, res, out);
+    }
     GNN_LAUNCH_CHECK("k_ln_fwd");
     return GNN_OK;
 }
@@ -546,7 +562,10 @@ int mlp_output(const gnn_mlp& P, int64_t rows, const float* zlast, float eps, co
     GNN_REQUIRE(!res_f32 && !res_bf16, GNN_EINVAL, "mlp_output: residual without LayerNorm is not supported");
     if (rows == 0) return GNN_OK;
     if (out_bf16) {
-        k_f32_to_bf16<<<grid1(rows * H), 256, 0, s>>>(zlast, (__nv_bfloat16*)out, rows * H);
+        {
+            ProfScope _ps(s, "k_f32_to_bf16");
+            k_f32_to_bf16<<<grid1(rows * H), 256, 0, s>>>(zlast, (__nv_bfloat16*)out, rows * H);
+        }
         GNN_LAUNCH_CHECK("k_f32_to_bf16");
     } else if (out != zlast) {
         GNN_CUDA_CHECK(cudaMemcpyAsync(out, zlast, sizeof(float) * rows * H, cudaMemcpyDeviceToDevice, s), "copy");
@@ -567,11 +586,20 @@ int mlp_bwd(const gnn_mlp& P, const gnn_mlp& dP, int64_t rows, const float* X, i
     if (P.gamma) {
         const int64_t ch = chunk_rows(rows), nz = n_chunks(rows);
         if (rows) {
-            k_ln_bwd<<<(unsigned)nz, 256, 0, s>>>(zlast, dY, rows, H, P.gamma, eps, g, ch, part, part + nz * H);
+            {
+                ProfScope _ps(s, "k_ln_bwd");
+                k_ln_bwd<<<(unsigned)nz, 256, 0, s>>>(zlast, dY, rows, H, P.gamma, eps, g, ch, part, part + nz * H);
+            }
             GNN_LAUNCH_CHECK("k_ln_bwd");
-            k_reduce_partials<<<grid1(H), 256, 0, s>>>(part, nz, H, dP.gamma, 1);
+            {
+                ProfScope _ps(s, "k_reduce_partials");
+                k_reduce_partials<<<grid1(H), 256, 0, s>>>(part, nz, H, dP.gamma, 1);
+            }
             GNN_LAUNCH_CHECK("k_reduce_partials");
-            k_reduce_partials<<<grid1(H), 256, 0, s>>>(part + nz * H, nz, H, dP.beta, 1);
+            {
+                ProfScope _ps(s, "k_reduce_partials");
+                k_reduce_partials<<<grid1(H), 256, 0, s>>>(part + nz * H, nz, H, dP.beta, 1);
+            }
             GNN_LAUNCH_CHECK("k_reduce_partials");
         }
     } else if (rows) {
@@ -586,7 +614,10 @@ int mlp_bwd(const gnn_mlp& P, const gnn_mlp& dP, int64_t rows, const float* X, i
             rc = linear_bwd_data(rows, P.dims[k], P.dims[k + 1], g, P.W[k], gn, P.dims[k], s);
             if (rc) return rc;
             if (rows) {
-                k_elu_bwd<<<grid1(rows * P.dims[k]), 256, 0, s>>>(gn, hbuf[k], rows * P.dims[k]);
+                {
+                    ProfScope _ps(s, "k_elu_bwd");
+                    k_elu_bwd<<<grid1(rows * P.dims[k]), 256, 0, s>>>(gn, hbuf[k], rows * P.dims[k]);
+                }
                 GNN_LAUNCH_CHECK("k_elu_bwd");
             }
             std::swap(g, gn);
@@ -652,23 +683,35 @@ static int layer_forward_core(const gnn_graph_dev& G, const gnn_mp_config& cfg, 
     const int64_t NR = G.n_rows, E = G.n_edges;
     int rc;
     if (NR && E) {
-        k_gather_edge_input<<<grid1(NR, 8), 256, 0, s>>>(G.row_ptr, G.col, NR, H, x_in, e_in, b.X1);
+        {
+            ProfScope _ps(s, "k_gather_edge_input");
+            k_gather_edge_input<<<grid1(NR, 8), 256, 0, s>>>(G.row_ptr, G.col, NR, H, x_in, e_in, b.X1);
+        }
         GNN_LAUNCH_CHECK("k_gather_edge_input");
     }
     if ((rc = chain_fwd(W.edge, E, b.X1, 3 * H, b.hE, b.zE, s))) return rc;
     if (!skip_agg) {
         if ((rc = mlp_output(W.edge, E, b.zE, cfg.ln_eps, e_in, nullptr, e_new, 0, s))) return rc;   // Eq. 5a
         if (NR) {
-            k_segsum<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.edge_w, NR, H, e_new, a);           // Eq. 5b
+            {
+                ProfScope _ps(s, "k_segsum");
+                k_segsum<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.edge_w, NR, H, e_new, a);           // Eq. 5b
             GNN_LAUNCH_CHECK("k_segsum");
+            }
         }
         if (cfg.halo_mode == GNN_HALO_SYNC && G.n_shared) {                                      // Eq. 5c-5d
-            k_halo<<<grid1(G.n_shared * H), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, H, a);
+            {
+                ProfScope _ps(s, "k_halo");
+                k_halo<<<grid1(G.n_shared * H), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, H, a);
+            }
             GNN_LAUNCH_CHECK("k_halo");
         }
     }
     if (NR) {
-        k_concat2<<<grid1(NR * H), 256, 0, s>>>(a, x_in, NR, H, b.X2);
+        {
+            ProfScope _ps(s, "k_concat2");
+            k_concat2<<<grid1(NR * H), 256, 0, s>>>(a, x_in, NR, H, b.X2);
+        }
         GNN_LAUNCH_CHECK("k_concat2");
     }
     if ((rc = chain_fwd(W.node, NR, b.X2, 2 * H, b.hN, b.zN, s))) return rc;
@@ -755,28 +798,43 @@ int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_p
     if ((rc = mlp_bwd(W.node, dW.node, NR, b.X2, 2 * H, b.hN, b.zN, dx_out, d.dX2, d.g0, d.g1, d.part, cfg.ln_eps, s)))
         return rc;
     if (NR) {
-        k_split_node_grad<<<grid1(NR * H), 256, 0, s>>>(d.dX2, dx_out, NR, H, d.da, dx_in);
+        {
+            ProfScope _ps(s, "k_split_node_grad");
+            k_split_node_grad<<<grid1(NR * H), 256, 0, s>>>(d.dX2, dx_out, NR, H, d.da, dx_in);
+        }
         GNN_LAUNCH_CHECK("k_split_node_grad");
     }
     // halo swap + sync adjoint (Eq. 5c-5d): the same symmetric copy-sum
     if (cfg.halo_mode == GNN_HALO_SYNC && G.n_shared) {
-        k_halo<<<grid1(G.n_shared * H), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, H, d.da);
+        {
+            ProfScope _ps(s, "k_halo");
+            k_halo<<<grid1(G.n_shared * H), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, H, d.da);
+        }
         GNN_LAUNCH_CHECK("k_halo");
     }
     // aggregation adjoint (Eq. 5b) + upstream edge gradient
     if (NR) {
-        k_agg_adjoint<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.edge_w, NR, H, d.da, de_out, d.de_tot);
+        {
+            ProfScope _ps(s, "k_agg_adjoint");
+            k_agg_adjoint<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.edge_w, NR, H, d.da, de_out, d.de_tot);
+        }
         GNN_LAUNCH_CHECK("k_agg_adjoint");
     }
     // edge update adjoint (Eq. 5a)
     if ((rc = mlp_bwd(W.edge, dW.edge, E, b.X1, 3 * H, b.hE, b.zE, d.de_tot, d.dX1, d.g0, d.g1, d.part, cfg.ln_eps, s)))
         return rc;
     if (E) {
-        k_edge_grad_out<<<grid1(E * H), 256, 0, s>>>(d.de_tot, d.dX1, E, H, de_in);
+        {
+            ProfScope _ps(s, "k_edge_grad_out");
+            k_edge_grad_out<<<grid1(E * H), 256, 0, s>>>(d.de_tot, d.dX1, E, H, de_in);
+        }
         GNN_LAUNCH_CHECK("k_edge_grad_out");
     }
     if (NR) {
-        k_gather_adjoint<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.t_ptr, G.t_eid, NR, H, d.dX1, dx_in);
+        {
+            ProfScope _ps(s, "k_gather_adjoint");
+            k_gather_adjoint<<<grid1(NR * H), 256, 0, s>>>(G.row_ptr, G.t_ptr, G.t_eid, NR, H, d.dX1, dx_in);
+        }
         GNN_LAUNCH_CHECK("k_gather_adjoint");
     }
     return GNN_OK;
@@ -784,7 +842,10 @@ int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_p
 
 int halo(const gnn_graph_dev& G, float* rows, int width, cudaStream_t s) {
     if (G.n_shared == 0 || width == 0) return GNN_OK;
-    k_halo<<<grid1(G.n_shared * width), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, width, rows);
+    {
+        ProfScope _ps(s, "k_halo");
+        k_halo<<<grid1(G.n_shared * width), 256, 0, s>>>(G.halo_ptr, G.halo_rows, G.n_shared, width, rows);
+    }
     GNN_LAUNCH_CHECK("k_halo");
     return GNN_OK;
 }
@@ -834,7 +895,10 @@ int mlp_backward(const gnn_mlp& P, int64_t rows, const float* X, const void* dY,
     const int64_t n_out = rows * P.dims[P.n_lin];
     if (dy_bf16) {
         if (n_out) {
-            k_bf16_to_f32<<<grid1(n_out), 256, 0, s>>>((const __nv_bfloat16*)dY, dyf, n_out);
+            {
+                ProfScope _ps(s, "k_bf16_to_f32");
+                k_bf16_to_f32<<<grid1(n_out), 256, 0, s>>>((const __nv_bfloat16*)dY, dyf, n_out);
+            }
             GNN_LAUNCH_CHECK("k_bf16_to_f32");
         }
         dy = dyf;
@@ -851,12 +915,21 @@ int consistent_loss(const gnn_graph_dev& G, const float* y, const float* t, int 
                 "gnn_consistent_loss: workspace too small");
     float* part = (float*)ws;
     float* stats = part + 2 * nblk;
-    k_loss_partial<<<(unsigned)nblk, 256, 0, s>>>(y, t, G.node_w, rows, F, chunk, part);
+    {
+        ProfScope _ps(s, "k_loss_partial");
+        k_loss_partial<<<(unsigned)nblk, 256, 0, s>>>(y, t, G.node_w, rows, F, chunk, part);
+    }
     GNN_LAUNCH_CHECK("k_loss_partial");
-    k_loss_final<<<1, 32, 0, s>>>(part, nblk, F, loss, stats);
+    {
+        ProfScope _ps(s, "k_loss_final");
+        k_loss_final<<<1, 32, 0, s>>>(part, nblk, F, loss, stats);
+    }
     GNN_LAUNCH_CHECK("k_loss_final");
     if (dy && rows) {
-        k_loss_grad<<<grid1(rows * F), 256, 0, s>>>(y, t, G.node_w, rows, F, stats, dy);
+        {
+            ProfScope _ps(s, "k_loss_grad");
+            k_loss_grad<<<grid1(rows * F), 256, 0, s>>>(y, t, G.node_w, rows, F, stats, dy);
+        }
         GNN_LAUNCH_CHECK("k_loss_grad");
     }
     return GNN_OK;

@@ -203,6 +203,62 @@ class _MLP(torch.nn.Module):
         return list(self.params)
 
 
+class LayerStack:
+    """M consistent NMP layers, forward then backward, on preallocated buffers.
+
+    Every buffer (node/edge states of each layer, saved a*, gradients,
+    workspace) is allocated once, so ``step`` issues library calls only and
+    can be captured in a CUDA graph. ``layers`` is a list of
+    (edge tensors, node tensors, edge dims, node dims) per layer; gradients
+    accumulate into ``dparams`` (zeroed by ``zero_grad``)."""
+
+    def __init__(self, G: DeviceGraph, layers, hidden: int, precision: str, x0, e0, halo: bool = True,
+                 ln_eps: float = 1e-5):
+        self.G = G
+        self.M = len(layers)
+        self.cfg = mp_config(hidden, precision, halo, ln_eps)
+        dev = x0.device
+        edt = torch.bfloat16 if precision == "bf16" else torch.float32
+        self.W, self.dW, self.dparams = [], [], []
+        for (te, tn, de, dn) in layers:
+            tens = list(te) + list(tn)
+            self.W.append(mp_params(de, dn, tens))
+            dp = [torch.zeros_like(t) for t in tens]
+            self.dparams.append(dp)
+            self.dW.append(mp_params(de, dn, dp))
+        self._keep = [layers]
+        NR, E = G.n_rows, G.n_edges
+        self.x = [x0.contiguous()] + [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
+        self.e = [e0.to(edt).contiguous()] + [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
+        self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
+        self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(self.M + 1)]
+        self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
+        f, b = mp_workspace_sizes(G, self.cfg, self.W[0])
+        self.ws = workspace(max(f, b), dev)
+
+    def zero_grad(self):
+        for dp in self.dparams:
+            for t in dp:
+                t.zero_()
+
+    def forward(self):
+        for l in range(self.M):
+            gnn_mp_forward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.x[l + 1], self.e[l + 1],
+                           self.a[l], self.ws)
+
+    def backward(self, dx_top):
+        """dx_top: dL/dx of the last layer's output; dL/de of it is zero."""
+        dx_out, de_out = dx_top, None
+        for l in range(self.M - 1, -1, -1):
+            gnn_mp_backward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.a[l], dx_out, de_out,
+                            self.dx[l], self.de[l], self.dW[l], self.ws)
+            dx_out, de_out = self.dx[l], self.de[l]
+
+    def step(self, dx_top):
+        self.forward()
+        self.backward(dx_top)
+
+
 class ConsistentGNN(torch.nn.Module):
     """Encode-process-decode GNN with consistent NMP layers (Sec. III).
 

@@ -1,24 +1,619 @@
-// Fused BF16 path of libgnnmp (tcgen05 / TMEM kernels).
+// Fused BF16 path of libgnnmp: tcgen05 / TMEM kernels for the consistent NMP
+// layer (Eq. 5a-5e) and its adjoint.
+//
+// Layer forward = four launches:
+//   k_proj_fwd   P|Q = x W1a^T | x W1b^T per node row. The edge MLP's first
+//                Linear acts on [x_i, x_j, e_ij]; splitting W1 = [W1a W1b W1c]
+//                gives W1 [x_i; x_j; e] = P_i + Q_j + W1c e, so the 2H-wide part
+//                is computed once per node instead of once per edge.
+//   k_edge_fwd   per tile of <= 128 receiver-aligned edges: TMA load of the
+//                edge-state tile, gather of P_i and Q_j, the Linear/ELU chain
+//                on tcgen05 with the accumulator in TMEM, LayerNorm + residual
+//                (Eq. 5a), e' written once, and the 1/d-weighted segmented sum
+//                over each receiver's edges in FP32 in edge order (Eq. 5b): the
+//                per-edge MLP activations never leave the SM.
+//   halo         Eq. 5c-5d copy-sum on the aggregates (shared with plain.cu).
+//   k_node_fwd   per tile of 128 node rows: [a*, x] -> Linear/ELU chain ->
+//                LayerNorm + residual (Eq. 5e).
+// All kernels are persistent (grid = resident CTAs), loop over tiles with a
+// static stride, and keep the layer's weights in shared memory as BF16.
+// Thread layout: 128 rows x CG column groups; thread (row, g) owns TMEM lane
+// `row` and columns [g*CW, (g+1)*CW) of every accumulator.
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 #include "device_common.cuh"
 #include "fused.h"
+#include "plain.h"
+#include "profiler.h"
+#include "fused_common.cuh"
 
 namespace gnn {
 namespace fused {
 
 cudaError_t take_device_error(unsigned int* out) { return take_device_error_word(out); }
 
-size_t mp_forward_ws(const gnn_graph_dev&, const gnn_mp_config&, const gnn_mp_params&) { return 0; }
-size_t mp_backward_ws(const gnn_graph_dev&, const gnn_mp_config&, const gnn_mp_params&) { return 0; }
+using namespace tc;
 
-int mp_forward(const gnn_graph_dev&, const gnn_mp_config&, const gnn_mp_params&, const float*,
-               const __nv_bfloat16*, float*, __nv_bfloat16*, float*, void*, size_t, cudaStream_t) {
-    return set_error(GNN_EUNSUPPORTED, "gnn_mp_forward: BF16 fused path not built yet");
+// ------------------------------------------------------------------ k_proj_fwd
+
+template <int H>
+__global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict__ x, int64_t n_rows,
+                                                        const float* __restrict__ W1, __nv_bfloat16* __restrict__ pq) {
+    using C = Cfg<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const ProjSmem L = proj_smem<H>();
+    uint8_t* sW = sm + L.w;
+    uint8_t* sA = sm + L.a;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * C::CW;
+    constexpr uint32_t NCOLS = 2 * H < 32 ? 32 : 2 * H;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    // [W1a; W1b] as a [2H x H] K-major tile: row n < H is W1[n][0:H], row H+n is W1[n][H:2H]
+    load_weight(sW, W1, 3 * H, 0, H, H, tid, C::NT, 2 * H, 0);
+    load_weight(sW, W1, 3 * H, H, H, H, tid, C::NT, 2 * H, H);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t n_tiles = (n_rows + 127) / 128;
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t r = t * 128 + row;
+        const bool valid = r < n_rows;
+        float v[C::CW];
+        if (valid) {
+            const float4* p = reinterpret_cast<const float4*>(x + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < C::CW / 4; ++i) {
+                float4 a = __ldg(p + i);
+                v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) v[i] = 0.f;
+        }
+        st_row_tile<C::CW>(sA, row, c0, C::S, v);
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tmem, sA, sW, 2 * H, H);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+        phase ^= 1;
+        tc_fence_after();
+        if (!ok) break;
+        float pv[C::CW], qv[C::CW];
+        ld_acc<C::CW>(tmem, q, c0, pv);
+        ld_acc<C::CW>(tmem, q, H + c0, qv);
+        tc_fence_before();
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) {
+                st_bf16x8(pq + r * 2 * H + c0 + i, pv + i);
+                st_bf16x8(pq + r * 2 * H + H + c0 + i, qv + i);
+            }
+        }
+        __syncthreads();   // sA and TMEM are reused by the next tile
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
-int mp_backward(const gnn_graph_dev&, const gnn_mp_config&, const gnn_mp_params&, const float*,
-                const __nv_bfloat16*, const float*, const float*, const __nv_bfloat16*, float*, __nv_bfloat16*,
-                const gnn_mp_params&, void*, size_t, cudaStream_t) {
-    return set_error(GNN_EUNSUPPORTED, "gnn_mp_backward: BF16 fused path not built yet");
+// ------------------------------------------------------------------ k_edge_fwd
+
+struct EdgeFwdArgs {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const float* edge_w;
+    const int32_t* tiles;
+    int64_t n_tiles;
+    int64_t n_edges;
+    const __nv_bfloat16* pq;
+    __nv_bfloat16* e_out;
+    float* a;
+    MlpDev mlp;
+    float eps;
+};
+
+template <int H>
+__global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
+    using C = Cfg<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int n_lin = A.mlp.n_lin;
+    const EdgeFwdSmem L = edge_fwd_smem<H>(n_lin);
+    uint8_t* sW = sm + L.w;
+    uint8_t* sA0 = sm + L.a0;
+    uint8_t* sA1 = sm + L.a1;
+    float* sPar = reinterpret_cast<float*>(sm + L.par);   // bias[n_lin][H], gamma[H], beta[H]
+    int32_t* sSeg = reinterpret_cast<int32_t*>(sm + L.seg);
+    float* sRed = reinterpret_cast<float*>(sm + L.red);
+    uint64_t* bar_tma = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint64_t* bar_mma = bar_tma + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
+    float* sStage = reinterpret_cast<float*>(sA0);         // aliases A0+A1 after the chain
+    constexpr int SC = H / 2;                               // staged columns per pass
+    constexpr int SLD = SC + 4;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * C::CW;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, C::TCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar_mma, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, C::NT);        // W1c: the edge-state columns of W1
+    for (int k = 1; k < n_lin; ++k) load_weight(sW + k * C::WT, A.mlp.W[k], H, 0, H, H, tid, C::NT);
+    for (int i = tid; i < n_lin * H; i += C::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += C::NT) {
+        sPar[n_lin * H + i] = A.mlp.gamma[i];
+        sPar[(n_lin + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t ph_tma = 0, ph_mma = 0;
+    bool ok = true;
+
+    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
+        const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
+        const int32_t e0 = A.row_ptr[r0], e1 = A.row_ptr[r1];
+        const int ne = e1 - e0;
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar_tma, C::TILE);
+#pragma unroll
+            for (int kb = 0; kb < (H + 63) / 64; ++kb)
+                tma_load_2d(sA0 + kb * 128 * 128, &tmap_e, kb * 64, e0, bar_tma);
+        }
+        // receiver of each edge of the tile (local row index)
+        for (int rr = tid; rr < r1 - r0; rr += C::NT)
+            for (int32_t e = A.row_ptr[r0 + rr]; e < A.row_ptr[r0 + rr + 1]; ++e) sSeg[e - e0] = rr;
+        __syncthreads();
+        const bool valid = row < ne;
+        const int64_t eg = (int64_t)e0 + row;
+        float w = 0.f;
+        float pq[C::CW];
+        if (valid) {
+            const int64_t rcv = r0 + sSeg[row];
+            const int64_t snd = A.col[eg];
+            w = A.edge_w[eg];
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) {
+                float pv[8], qv[8];
+                ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
+                ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) pq[i + j] = pv[j] + qv[j];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) pq[i] = 0.f;
+        }
+        ok = __syncthreads_and(mbar_wait(bar_tma, ph_tma) ? 1 : 0) != 0;
+        ph_tma ^= 1;
+        if (!ok) break;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tmem, sA0, sW, H, H);
+            mma_commit(bar_mma);
+        }
+        float v[C::CW];
+        for (int k = 0; k < n_lin && ok; ++k) {
+            ok = __syncthreads_and(mbar_wait(bar_mma, ph_mma) ? 1 : 0) != 0;
+            ph_mma ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            ld_acc<C::CW>(tmem, q, c0, v);
+            const float* bk = sPar + k * H + c0;
+            if (k == 0) {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) v[i] += pq[i] + bk[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) v[i] += bk[i];
+            }
+            if (k < n_lin - 1) {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) v[i] = elu1(v[i]);
+                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+                fence_proxy_async();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_mma(tmem, sA1, sW + (k + 1) * C::WT, H, H);
+                    mma_commit(bar_mma);
+                }
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        // LayerNorm + residual (Eq. 5a)
+        float mean, rstd;
+        row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
+        float eo[C::CW];
+        ld_row_tile<C::CW>(sA0, row, c0, C::S, eo);
+        const float* gam = sPar + n_lin * H + c0;
+        const float* bet = sPar + (n_lin + 1) * H + c0;
+#pragma unroll
+        for (int i = 0; i < C::CW; ++i) v[i] = eo[i] + (v[i] - mean) * rstd * gam[i] + bet[i];
+        if (valid && A.e_out) {
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.e_out + eg * H + c0 + i, v + i);
+        }
+        // 1/d-weighted segmented sum over each receiver's edges (Eq. 5b), two column passes
+        __syncthreads();
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) {
+                const int c = c0 + i;
+                if (c >= pass * SC && c < (pass + 1) * SC) sStage[row * SLD + (c - pass * SC)] = w * v[i];
+            }
+            __syncthreads();
+            const int nr = r1 - r0;
+            for (int it = tid; it < nr * SC; it += C::NT) {
+                const int rr = it / SC, cc = it % SC;
+                const int32_t b0 = A.row_ptr[r0 + rr] - e0, b1 = A.row_ptr[r0 + rr + 1] - e0;
+                float s = 0.f;
+                for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
+                A.a[(int64_t)(r0 + rr) * H + pass * SC + cc] = s;
+            }
+            __syncthreads();
+        }
+        fence_proxy_async();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
+}
+
+// ------------------------------------------------------------------ k_node_fwd
+
+struct NodeFwdArgs {
+    const float* a_star;
+    const float* x;
+    float* x_out;
+    int64_t n_rows;
+    MlpDev mlp;
+    float eps;
+};
+
+template <int H>
+__global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
+    using C = Cfg<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int n_lin = A.mlp.n_lin;
+    const NodeFwdSmem L = node_fwd_smem<H>(n_lin);
+    uint8_t* sW0 = sm + L.w0;
+    uint8_t* sW = sm + L.w;
+    uint8_t* sA0 = sm + L.a0;
+    uint8_t* sA1 = sm + L.a1;
+    float* sPar = reinterpret_cast<float*>(sm + L.par);
+    float* sRed = reinterpret_cast<float*>(sm + L.red);
+    uint64_t* bar_mma = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
+    constexpr int S2 = span_of(2 * H);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * C::CW;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, C::TCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar_mma, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
+    for (int k = 1; k < n_lin; ++k) load_weight(sW + (k - 1) * C::WT, A.mlp.W[k], H, 0, H, H, tid, C::NT);
+    for (int i = tid; i < n_lin * H; i += C::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += C::NT) {
+        sPar[n_lin * H + i] = A.mlp.gamma[i];
+        sPar[(n_lin + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t ph = 0;
+    bool ok = true;
+    const int64_t n_tiles = (A.n_rows + 127) / 128;
+
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t r = t * 128 + row;
+        const bool valid = r < A.n_rows;
+        float xa[C::CW], xv[C::CW];
+        if (valid) {
+            const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
+            const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < C::CW / 4; ++i) {
+                float4 u = __ldg(pa + i), w = __ldg(px + i);
+                xa[4 * i] = u.x; xa[4 * i + 1] = u.y; xa[4 * i + 2] = u.z; xa[4 * i + 3] = u.w;
+                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) xa[i] = xv[i] = 0.f;
+        }
+        if constexpr (!NodeSplit<H>::value) {
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) {
+                st_tile8(sA0, row, c0 + i, 128, S2, xa + i);
+                st_tile8(sA0, row, H + c0 + i, 128, S2, xv + i);
+            }
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_mma(tmem, sA0, sW0, H, 2 * H);
+                mma_commit(bar_mma);
+            }
+        } else {
+            // K half 0 (a*) then K half 1 (x) through the same [128 x H] buffer
+            st_row_tile<C::CW>(sA0, row, c0, C::S, xa);
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_mma_koff(tmem, sA0, sW0, H, H, 0, 2 * H, false);
+                mma_commit(bar_mma);
+            }
+            ok = __syncthreads_and(mbar_wait(bar_mma, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            st_row_tile<C::CW>(sA0, row, c0, C::S, xv);
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_mma_koff(tmem, sA0, sW0, H, H, H, 2 * H, true);
+                mma_commit(bar_mma);
+            }
+        }
+        float v[C::CW];
+        for (int k = 0; k < n_lin && ok; ++k) {
+            ok = __syncthreads_and(mbar_wait(bar_mma, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            ld_acc<C::CW>(tmem, q, c0, v);
+            const float* bk = sPar + k * H + c0;
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) v[i] += bk[i];
+            if (k < n_lin - 1) {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) v[i] = elu1(v[i]);
+                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+                fence_proxy_async();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_mma(tmem, sA1, sW + k * C::WT, H, H);
+                    mma_commit(bar_mma);
+                }
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        float mean, rstd;
+        row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
+        const float* gam = sPar + n_lin * H + c0;
+        const float* bet = sPar + (n_lin + 1) * H + c0;
+        if (valid) {
+            float4* po = reinterpret_cast<float4*>(A.x_out + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < C::CW / 4; ++i) {
+                float4 o;
+                o.x = xv[4 * i] + (v[4 * i] - mean) * rstd * gam[4 * i] + bet[4 * i];
+                o.y = xv[4 * i + 1] + (v[4 * i + 1] - mean) * rstd * gam[4 * i + 1] + bet[4 * i + 1];
+                o.z = xv[4 * i + 2] + (v[4 * i + 2] - mean) * rstd * gam[4 * i + 2] + bet[4 * i + 2];
+                o.w = xv[4 * i + 3] + (v[4 * i + 3] - mean) * rstd * gam[4 * i + 3] + bet[4 * i + 3];
+                po[i] = o;
+            }
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
+}
+
+// =================================================================== host side
+
+namespace {
+
+using namespace host;
+
+struct FwdWs {
+    __nv_bfloat16* pq;
+    float* a;
+    __nv_bfloat16* e_scratch;
+    size_t bytes;
+};
+
+FwdWs carve_fwd(void* ws, const gnn_graph_dev& G, int H, bool need_a, bool need_e) {
+    FwdWs w{};
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        void* p = ws ? (char*)ws + off : nullptr;
+        off += n;
+        return p;
+    };
+    w.pq = (__nv_bfloat16*)take((size_t)G.n_rows * 2 * H * 2);
+    w.a = need_a ? (float*)take((size_t)G.n_rows * H * 4) : nullptr;
+    w.e_scratch = need_e ? (__nv_bfloat16*)take(0) : nullptr;
+    w.bytes = off + 256;
+    return w;
+}
+
+template <int H>
+int proj_h(const gnn_graph_dev& G, const gnn_mp_params& W, const float* x_in, __nv_bfloat16* pq, cudaStream_t s) {
+    using C = Cfg<H>;
+    const int64_t NR = G.n_rows;
+    if (NR == 0) return GNN_OK;
+    const ProjSmem L = proj_smem<H>();
+    int grid;
+    int rc = persistent_grid(k_proj_fwd<H>, C::NT, L.total, 2 * H < 32 ? 32 : 2 * H, (NR + 127) / 128, &grid);
+    if (rc) return rc;
+    {
+        ProfScope _ps(s, "k_proj_fwd");
+        k_proj_fwd<H><<<grid, C::NT, L.total, s>>>(x_in, NR, W.edge.W[0], pq);
+    }
+    GNN_LAUNCH_CHECK("k_proj_fwd");
+    return GNN_OK;
+}
+
+// Edge MLP + residual + weighted segmented sum (Eq. 5a-5b), then Eq. 5c-5d.
+template <int H>
+int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const __nv_bfloat16* e_in,
+           const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a, cudaStream_t s) {
+    using C = Cfg<H>;
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    if (NR == 0) return GNN_OK;
+    if (E > 0) {
+        CUtensorMap tm;
+        int rc = make_row_tmap(&tm, e_in, E, H);
+        if (rc) return rc;
+        EdgeFwdArgs A;
+        A.row_ptr = G.row_ptr;
+        A.col = G.col;
+        A.edge_w = G.edge_w;
+        A.tiles = G.edge_tiles;
+        A.n_tiles = G.n_edge_tiles;
+        A.n_edges = E;
+        A.pq = pq;
+        A.e_out = e_out;
+        A.a = a;
+        A.mlp = mlp_dev(W.edge);
+        A.eps = cfg.ln_eps;
+        const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin);
+        int grid;
+        rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid);
+        if (rc) return rc;
+        {
+            ProfScope _ps(s, "k_edge_fwd");
+            k_edge_fwd<H><<<grid, C::NT, L.total, s>>>(tm, A);
+        }
+        GNN_LAUNCH_CHECK("k_edge_fwd");
+    } else {
+        GNN_CUDA_CHECK(cudaMemsetAsync(a, 0, sizeof(float) * NR * H, s), "memset");
+    }
+    if (cfg.halo_mode == GNN_HALO_SYNC) return plain::halo(G, a, H, s);
+    return GNN_OK;
+}
+
+template <int H>
+int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
+           const float* x_in, float* x_out, cudaStream_t s) {
+    using C = Cfg<H>;
+    const int64_t NR = G.n_rows;
+    if (NR == 0) return GNN_OK;
+    NodeFwdArgs A;
+    A.a_star = a;
+    A.x = x_in;
+    A.x_out = x_out;
+    A.n_rows = NR;
+    A.mlp = mlp_dev(W.node);
+    A.eps = cfg.ln_eps;
+    const NodeFwdSmem L = node_fwd_smem<H>(W.node.n_lin);
+    int grid;
+    int rc = persistent_grid(k_node_fwd<H>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
+    if (rc) return rc;
+    {
+        ProfScope _ps(s, "k_node_fwd");
+        k_node_fwd<H><<<grid, C::NT, L.total, s>>>(A);
+    }
+    GNN_LAUNCH_CHECK("k_node_fwd");
+    return GNN_OK;
+}
+
+}  // namespace
+
+size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params&) {
+    return carve_fwd(nullptr, G, cfg.hidden, true, false).bytes;
+}
+
+#define GNN_H_DISPATCH(H_, CALL)                                                           \
+    switch (H_) {                                                                          \
+        case 16: { constexpr int HH = 16; return CALL; }                                   \
+        case 32: { constexpr int HH = 32; return CALL; }                                   \
+        case 64: { constexpr int HH = 64; return CALL; }                                   \
+        case 128: { constexpr int HH = 128; return CALL; }                                 \
+        default: return set_error(GNN_ESHAPE, "BF16 path needs H in {16,32,64,128} (H=%d)", H_); \
+    }
+
+int proj_forward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const float* x_in, __nv_bfloat16* pq,
+                 cudaStream_t s) {
+    GNN_H_DISPATCH(H, proj_h<HH>(G, W, x_in, pq, s));
+}
+
+int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                      const __nv_bfloat16* e_in, const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a,
+                      cudaStream_t s) {
+    GNN_H_DISPATCH(cfg.hidden, edge_h<HH>(G, cfg, W, e_in, pq, e_out, a, s));
+}
+
+int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
+                 const float* x_in, float* x_out, cudaStream_t s) {
+    GNN_H_DISPATCH(cfg.hidden, node_h<HH>(G, cfg, W, a, x_in, x_out, s));
+}
+
+int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+               const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
+               size_t ws_bytes, cudaStream_t s) {
+    const int H = cfg.hidden;
+    GNN_REQUIRE(H == 16 || H == 32 || H == 64 || H == 128, GNN_ESHAPE, "gnn_mp_forward: BF16 path needs H in {16,32,64,128}");
+    GNN_REQUIRE(W.edge.n_lin >= 2 && W.node.n_lin >= 2, GNN_ESHAPE, "MLPs need >= 2 Linear layers");
+    FwdWs w = carve_fwd(ws, G, H, a_star_out == nullptr, false);
+    GNN_REQUIRE(ws_bytes >= w.bytes, GNN_ENOMEM, "gnn_mp_forward: workspace too small");
+    __nv_bfloat16* eo = (cfg.flags & GNN_FLAG_NO_EDGE_OUT) ? nullptr : e_out;
+    float* a = a_star_out ? a_star_out : w.a;
+    int rc;
+    if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
+    if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s))) return rc;
+    return node_forward(G, cfg, W, a, x_in, x_out, s);
 }
 
 }  // namespace fused

@@ -20,5 +20,14 @@ int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_p
                 float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
                 cudaStream_t s);
 
+// Steps of the forward shared with the backward's recomputation.
+int proj_forward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const float* x_in, __nv_bfloat16* pq,
+                 cudaStream_t s);
+int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                      const __nv_bfloat16* e_in, const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a,
+                      cudaStream_t s);
+int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
+                 const float* x_in, float* x_out, cudaStream_t s);
+
 }  // namespace fused
 }  // namespace gnn

@@ -1,0 +1,1113 @@
+// Fused BF16 backward (adjoint) of the consistent NMP layer, Eq. 3, with
+// per-layer recomputation of the MLP activations.
+//
+// Launch sequence of gnn_mp_backward (BF16):
+//   k_proj_fwd    recompute P|Q = x W1a^T | x W1b^T (forward kernel)
+//   k_node_bwd    recompute the node MLP from [a*, x], back-propagate dx_out:
+//                 da* (FP32) and dx_in = dx_out + d[x part]; dW of the node MLP
+//   halo          adjoint of Eq. 5c-5d = the same symmetric copy-sum on da*
+//   k_edge_bwd    recompute the edge MLP per receiver-aligned tile; the
+//                 gradient of e' is de_out + da_i / d_ij (adjoint of Eq. 5b);
+//                 back-propagate to de_in = g + W1c^T dz1, write dz1 (the
+//                 gradient of the first pre-activation) per edge, sum it over
+//                 each receiver's edges into dP (FP32, fixed edge order); dW
+//   k_proj_bwd    dQ_j = sum of dz1 over the edges sent by j (sender CSR,
+//                 fixed order); dx_in += dP W1a + dQ W1b; dW1a, dW1b
+//   k_reduce      per-CTA weight-gradient partials summed in CTA order into dW
+// No atomics anywhere: every sum has a fixed order, so results are bitwise
+// reproducible.
+//
+// Weight gradients accumulate in TMEM across all tiles a CTA processes:
+// D_k[out][in] += dz_k^T h_k is one tcgen05.mma per 16 rows with both operands
+// MN-major views of the tiles the chain already holds in shared memory; a
+// constant block with a column of ones appended to h_k yields the bias
+// gradient sum_rows dz_k in column `in = H_in` of the same accumulator.
+// Thread layout: 128 rows x H/16 column groups of 16 columns.
+
+#include <algorithm>
+#include <cstring>
+
+#include "fused.h"
+#include "fused_common.cuh"
+#include "plain.h"
+#include "profiler.h"
+
+namespace gnn {
+namespace fused {
+
+template <int H>
+struct CfgB {
+    static constexpr int S = span_of(H);
+    static constexpr int S2 = span_of(2 * H);
+    static constexpr int CG = H >= 16 ? H / 16 : 1;
+    static constexpr int CW = H / CG;         // 16
+    static constexpr int NT = 128 * CG;
+    static constexpr int TILE = 128 * H * 2;
+    static constexpr int WT = H * H * 2;
+    static constexpr int NW = H + 16;         // wgrad N: H inputs + the ones block
+};
+
+__host__ __device__ constexpr uint32_t pow2_cols(uint32_t n) {
+    uint32_t c = 32;
+    while (c < n) c <<= 1;
+    return c;
+}
+
+// ------------------------------------------------------------------ device helpers
+
+// D[128 x N] (+)= A[128 x K] (K-major row tile, span Sa) * B where B is a
+// K x N MN-major row tile (rows = K, contiguous = N, span Sb, N-blocks lbo apart).
+__device__ __forceinline__ void issue_dgrad(uint32_t d, const uint8_t* A, int Sa, const uint8_t* Bt, int Sb,
+                                            int b_rows, uint32_t lbo, int N, int K) {
+    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint32_t id = idesc_bf16(128, N, 0, 1);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo, 8 * Sb, swz_code(Sb));
+        mma_bf16(d, kmajor_desc(a, 128, Sa, k0), bd, id, k0 > 0 ? 1u : 0u);
+        (void)b_rows;
+    }
+}
+
+// D[128 x N] (+)= A^T B over the 128 rows of two MN-major row tiles:
+// A: rows = K (=128), contiguous = M features (span Sa, M-blocks lbo_a apart);
+// B: rows = K, contiguous = N features (span Sb, N-blocks lbo_b apart).
+__device__ __forceinline__ void issue_wgrad(uint32_t d, const uint8_t* A, int Sa, uint32_t lbo_a, const uint8_t* Bt,
+                                            int Sb, uint32_t lbo_b, int N, bool accumulate) {
+    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint32_t id = idesc_bf16(128, N, 1, 1);
+    for (int k0 = 0; k0 < 128; k0 += 16) {
+        const uint64_t ad = sdesc(a + (uint32_t)k0 * Sa, lbo_a, 8 * Sa, swz_code(Sa));
+        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo_b, 8 * Sb, swz_code(Sb));
+        mma_bf16(d, ad, bd, id, (accumulate || k0 > 0) ? 1u : 0u);
+    }
+}
+
+// Ones block: a [128 x S/2] row tile whose column 0 is 1 and the rest 0.
+__device__ __forceinline__ void fill_ones(uint8_t* dst, int S, int tid, int nt) {
+    const int per = S / 2;
+    for (int i = tid; i < 128 * (per / 8); i += nt) {
+        const int r = i / (per / 8), c = (i % (per / 8)) * 8;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (c == 0) v[0] = 1.f;
+        st_tile8(dst, r, c, 128, S, v);
+    }
+}
+
+// Row sums of two per-thread partial vectors over the CG threads of a row.
+template <int CG>
+__device__ __forceinline__ void row_sum2(float a, float b, float* red, int row, int g, float& sa, float& sb) {
+    red[g * 128 + row] = a;
+    red[(CG + g) * 128 + row] = b;
+    __syncthreads();
+    sa = 0.f;
+    sb = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) {
+        sa += red[k * 128 + row];
+        sb += red[(CG + k) * 128 + row];
+    }
+    __syncthreads();
+}
+
+// Reduce per-thread column accumulators acc[CW] over the 128 rows of the CTA
+// (lanes by shuffle, then the 4 lane quarters in order) into out[c0..c0+CW).
+template <int CW>
+__device__ __forceinline__ void rows_reduce_store(float* acc, float* red, int q, int lane, int g, int c0, float* out) {
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < CW; ++i) red[(g * 4 + q) * CW + i] = acc[i];
+    }
+    __syncthreads();
+    if (q == 0 && lane < CW) {
+        float s = 0.f;
+        for (int k = 0; k < 4; ++k) s += red[(g * 4 + k) * CW + lane];
+        out[c0 + lane] = s;
+    }
+    __syncthreads();
+}
+
+// Flush a TMEM accumulator [128 lanes x N cols] (rows < m_valid) into dst[m*N + n].
+template <int CG>
+__device__ __forceinline__ void flush_acc(uint32_t tmem, int N, int m_valid, int q, int lane, int g, float* dst) {
+    const int m = 32 * q + lane;
+    for (int c = g * 16; c < N; c += CG * 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+        tmem_ld_wait();
+        if (m < m_valid) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[(int64_t)m * N + c + i] = v[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ shared memory plans
+
+struct EdgeBwdSmem {
+    uint32_t w, e0, de, g, hb, ones, stage, par, seg, red, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
+    using C = CfgB<H>;
+    EdgeBwdSmem s;
+    s.w = 0;
+    s.e0 = align_up(n_lin * C::WT, 1024);
+    s.de = s.e0 + C::TILE;
+    s.g = s.de + C::TILE;
+    s.hb = s.g + C::TILE;
+    s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
+    s.stage = align_up(s.ones + 128 * C::S, 1024);
+    s.par = s.stage + 128 * (H + 4) * 4;
+    s.seg = s.par + (n_lin + 2) * H * 4;
+    s.red = s.seg + 128 * 4;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);
+    s.tm = s.bar + 16;
+    uint32_t end = s.tm + 16;
+    end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
+    s.total = end + 1024;
+    return s;
+}
+
+struct NodeBwdSmem {
+    uint32_t w0, w, ain, ones2, g, hb, ones, par, red, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline NodeBwdSmem node_bwd_smem(int n_lin) {
+    using C = CfgB<H>;
+    NodeBwdSmem s;
+    s.w0 = 0;
+    s.w = align_up(2 * C::WT, 1024);
+    s.ain = align_up(s.w + (n_lin - 1) * C::WT, 1024);
+    s.ones2 = s.ain + 2 * C::TILE;                 // contiguous after ain: the next N-block of [ain ; ones]
+    s.g = align_up(s.ones2 + 128 * C::S2, 1024);
+    s.hb = s.g + C::TILE;
+    s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
+    s.par = align_up(s.ones + 128 * C::S, 16);
+    s.red = s.par + (n_lin + 2) * H * 4;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);
+    s.tm = s.bar + 16;
+    uint32_t end = s.tm + 16;
+    end = end > s.g + 32768 ? end : s.g + 32768;
+    s.total = end + 1024;
+    return s;
+}
+
+struct ProjBwdSmem {
+    uint32_t w, a, x, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline ProjBwdSmem proj_bwd_smem() {
+    using C = CfgB<H>;
+    ProjBwdSmem s;
+    s.w = 0;
+    s.a = align_up(2 * C::WT, 1024);
+    s.x = s.a + 2 * C::TILE;
+    s.bar = align_up(s.x + C::TILE, 8);
+    s.tm = s.bar + 16;
+    uint32_t end = s.tm + 16;
+    end = end > s.a + 32768 ? end : s.a + 32768;
+    s.total = end + 1024;
+    return s;
+}
+
+// TMEM column plans
+template <int H>
+__host__ __device__ inline uint32_t edge_bwd_tcols(int n_lin) { return H + n_lin * (H + 16); }
+template <int H>
+__host__ __device__ inline uint32_t node_bwd_tcols(int n_lin) {
+    return 2 * H + (2 * H + 16) + (n_lin - 1) * (H + 16);
+}
+
+// ------------------------------------------------------------------ k_node_bwd
+
+struct NodeBwdArgs {
+    const float* a_star;
+    const float* x;
+    const float* dx_out;
+    float* da;          // out: gradient of a* (FP32)
+    float* dx_in;       // out: dx_out + x part of the node-MLP input gradient
+    float* part;        // per-CTA weight-gradient partials
+    int64_t pstride;
+    int64_t n_rows;
+    MlpDev mlp;
+    float eps;
+};
+
+template <int H>
+__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
+    using C = CfgB<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int L = A.mlp.n_lin;
+    const NodeBwdSmem P = node_bwd_smem<H>(L);
+    uint8_t* sW0 = sm + P.w0;
+    uint8_t* sW = sm + P.w;
+    uint8_t* sAin = sm + P.ain;
+    uint8_t* sG = sm + P.g;
+    uint8_t* sHB = sm + P.hb;
+    uint8_t* sOnes = sm + P.ones;
+    float* sPar = reinterpret_cast<float*>(sm + P.par);
+    float* sRed = reinterpret_cast<float*>(sm + P.red);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
+    constexpr int S = C::S, S2 = C::S2, CW = C::CW;
+    const uint32_t NCOLS = pow2_cols(node_bwd_tcols<H>(L));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
+    for (int k = 1; k < L; ++k) load_weight(sW + (k - 1) * C::WT, A.mlp.W[k], H, 0, H, H, tid, C::NT);
+    fill_ones(sm + P.ones2, S2, tid, C::NT);
+    fill_ones(sOnes, S, tid, C::NT);
+    for (int i = tid; i < L * H; i += C::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += C::NT) {
+        sPar[L * H + i] = A.mlp.gamma[i];
+        sPar[(L + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tWork = tmem;
+    auto tDW = [&](int k) -> uint32_t {
+        return tmem + (uint32_t)(2 * H + (k == 0 ? 0 : (2 * H + 16) + (k - 1) * (H + 16)));
+    };
+    float acc_g[CW], acc_b[CW];
+#pragma unroll
+    for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
+    uint32_t ph = 0;
+    bool ok = true, first = true;
+    const int64_t n_tiles = (A.n_rows + 127) / 128;
+
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t r = t * 128 + row;
+        const bool valid = r < A.n_rows;
+        float xv[CW], av[CW], gv[CW];
+        if (valid) {
+            const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
+            const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+            const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                float4 u = __ldg(pa + i), w = __ldg(px + i), z = __ldg(pg + i);
+                av[4 * i] = u.x; av[4 * i + 1] = u.y; av[4 * i + 2] = u.z; av[4 * i + 3] = u.w;
+                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                gv[4 * i] = z.x; gv[4 * i + 1] = z.y; gv[4 * i + 2] = z.z; gv[4 * i + 3] = z.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) av[i] = xv[i] = gv[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < CW; i += 8) {
+            st_tile8(sAin, row, c0 + i, 128, S2, av + i);
+            st_tile8(sAin, row, H + c0 + i, 128, S2, xv + i);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tWork, sAin, sW0, H, 2 * H);
+            mma_commit(bar);
+        }
+        // ---- recompute the chain
+        float v[CW];
+        for (int k = 0; k < L && ok; ++k) {
+            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            ld_acc<CW>(tWork, q, c0, v);
+#pragma unroll
+            for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
+            if (k < L - 1) {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] = elu1(v[i]);
+                st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
+                fence_proxy_async();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_mma(tWork, sHB + k * C::TILE, sW + k * C::WT, H, H);
+                    mma_commit(bar);
+                }
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        // ---- LayerNorm adjoint
+        float mean, rstd;
+        row_stats<H, C::CG, CW>(v, sRed, row, g, A.eps, mean, rstd);
+        float dz[CW];
+        float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+            const float xh = (v[i] - mean) * rstd;
+            acc_g[i] += gv[i] * xh;
+            acc_b[i] += gv[i];
+            const float d = gv[i] * sPar[L * H + c0 + i];
+            dz[i] = d;
+            v[i] = xh;
+            m1 += d;
+            m2 += d * xh;
+        }
+        float s1, s2;
+        row_sum2<C::CG>(m1, m2, sRed + 2 * C::CG * 128, row, g, s1, s2);
+        s1 *= 1.f / H;
+        s2 *= 1.f / H;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
+        // ---- chain adjoint, layer L-1 .. 0
+        for (int k = L - 1; k >= 0 && ok; --k) {
+            st_row_tile<CW>(sG, row, c0, S, dz);
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                if (k == 0) {
+                    issue_dgrad(tWork, sG, S, sW0, S2, H, (uint32_t)H * S2, 2 * H, H);
+                    issue_wgrad(tDW(0), sG, S, 128u * S, sAin, S2, 128u * S2, 2 * H + 16, !first);
+                } else {
+                    issue_dgrad(tWork, sG, S, sW + (k - 1) * C::WT, S, H, (uint32_t)H * S, H, H);
+                    uint8_t* hk = sHB + (k - 1) * C::TILE;
+                    issue_wgrad(tDW(k), sG, S, 128u * S, hk, S, (uint32_t)(smem_u32(sOnes) - smem_u32(hk)), H + 16,
+                                !first);
+                }
+                mma_commit(bar);
+            }
+            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            if (k > 0) {
+                float dh[CW], hv[CW];
+                ld_acc<CW>(tWork, q, c0, dh);
+                ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
+#pragma unroll
+                for (int i = 0; i < CW; ++i) dz[i] = dh[i] * elu1_deriv_from_out(hv[i]);
+            } else {
+                float da[CW], dxp[CW];
+                ld_acc<CW>(tWork, q, c0, da);
+                ld_acc<CW>(tWork, q, H + c0, dxp);
+                if (valid) {
+                    float4* pda = reinterpret_cast<float4*>(A.da + r * H + c0);
+                    float4* pdx = reinterpret_cast<float4*>(A.dx_in + r * H + c0);
+#pragma unroll
+                    for (int i = 0; i < CW / 4; ++i) {
+                        pda[i] = make_float4(da[4 * i], da[4 * i + 1], da[4 * i + 2], da[4 * i + 3]);
+                        pdx[i] = make_float4(gv[4 * i] + dxp[4 * i], gv[4 * i + 1] + dxp[4 * i + 1],
+                                             gv[4 * i + 2] + dxp[4 * i + 2], gv[4 * i + 3] + dxp[4 * i + 3]);
+                    }
+                }
+            }
+            tc_fence_before();
+        }
+        first = false;
+        __syncthreads();
+    }
+    // ---- flush the CTA's partial gradients
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        int64_t off = 0;
+        for (int k = 0; k < L; ++k) {
+            const int N = k == 0 ? 2 * H + 16 : H + 16;
+            if (!first) flush_acc<C::CG>(tDW(k), N, H, q, lane, g, part + off);
+            else
+                for (int i = tid; i < H * N; i += C::NT) part[off + i] = 0.f;
+            off += (int64_t)H * N;
+        }
+        rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
+        rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ------------------------------------------------------------------ k_edge_bwd
+
+struct EdgeBwdArgs {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const float* edge_w;
+    const int32_t* tiles;
+    int64_t n_tiles;
+    const __nv_bfloat16* pq;
+    const float* da;            // gradient of the aggregate after the halo adjoint
+    int has_de_out;
+    __nv_bfloat16* de_in;
+    __nv_bfloat16* dz1;         // per-edge gradient of the first pre-activation
+    float* dP;                  // per-row sum of dz1 over the row's received edges
+    float* part;
+    int64_t pstride;
+    MlpDev mlp;
+    float eps;
+};
+
+template <int H>
+__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_constant__ CUtensorMap tmap_e,
+                                                            const __grid_constant__ CUtensorMap tmap_de,
+                                                            EdgeBwdArgs A) {
+    using C = CfgB<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int L = A.mlp.n_lin;
+    const EdgeBwdSmem P = edge_bwd_smem<H>(L);
+    uint8_t* sW = sm + P.w;
+    uint8_t* sE0 = sm + P.e0;
+    uint8_t* sDE = sm + P.de;
+    uint8_t* sG = sm + P.g;
+    uint8_t* sHB = sm + P.hb;
+    uint8_t* sOnes = sm + P.ones;
+    float* sStage = reinterpret_cast<float*>(sm + P.stage);
+    float* sPar = reinterpret_cast<float*>(sm + P.par);
+    int32_t* sSeg = reinterpret_cast<int32_t*>(sm + P.seg);
+    float* sRed = reinterpret_cast<float*>(sm + P.red);
+    uint64_t* bar_tma = reinterpret_cast<uint64_t*>(sm + P.bar);
+    uint64_t* bar = bar_tma + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
+    constexpr int S = C::S, CW = C::CW, SLD = H + 4;
+    const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, C::NT);
+    for (int k = 1; k < L; ++k) load_weight(sW + k * C::WT, A.mlp.W[k], H, 0, H, H, tid, C::NT);
+    fill_ones(sOnes, S, tid, C::NT);
+    for (int i = tid; i < L * H; i += C::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += C::NT) {
+        sPar[L * H + i] = A.mlp.gamma[i];
+        sPar[(L + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tWork = tmem;
+    auto tDW = [&](int k) -> uint32_t { return tmem + (uint32_t)(H + k * (H + 16)); };
+    const uint32_t ones_addr = smem_u32(sOnes);
+    float acc_g[CW], acc_b[CW];
+#pragma unroll
+    for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
+    uint32_t ph_tma = 0, ph = 0;
+    bool ok = true, first = true;
+    const uint32_t tx_bytes = C::TILE * (A.has_de_out ? 2 : 1);
+
+    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
+        const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
+        const int32_t e0 = A.row_ptr[r0], e1 = A.row_ptr[r1];
+        const int ne = e1 - e0;
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar_tma, tx_bytes);
+            tma_load_2d(sE0, &tmap_e, 0, e0, bar_tma);
+            if (A.has_de_out) tma_load_2d(sDE, &tmap_de, 0, e0, bar_tma);
+        }
+        for (int rr = tid; rr < r1 - r0; rr += C::NT)
+            for (int32_t e = A.row_ptr[r0 + rr]; e < A.row_ptr[r0 + rr + 1]; ++e) sSeg[e - e0] = rr;
+        __syncthreads();
+        const bool valid = row < ne;
+        const int64_t eg = (int64_t)e0 + row;
+        float w = 0.f;
+        float pq[CW], dar[CW];
+        int64_t rcv = 0;
+        if (valid) {
+            rcv = r0 + sSeg[row];
+            const int64_t snd = A.col[eg];
+            w = A.edge_w[eg];
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) {
+                float pv[8], qv[8];
+                ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
+                ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) pq[i + j] = pv[j] + qv[j];
+            }
+            const float4* pd = reinterpret_cast<const float4*>(A.da + rcv * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                float4 u = __ldg(pd + i);
+                dar[4 * i] = u.x; dar[4 * i + 1] = u.y; dar[4 * i + 2] = u.z; dar[4 * i + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) pq[i] = dar[i] = 0.f;
+        }
+        ok = __syncthreads_and(mbar_wait(bar_tma, ph_tma) ? 1 : 0) != 0;
+        ph_tma ^= 1;
+        if (!ok) break;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tWork, sE0, sW, H, H);
+            mma_commit(bar);
+        }
+        // ---- recompute the chain
+        float v[CW];
+        for (int k = 0; k < L && ok; ++k) {
+            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            ld_acc<CW>(tWork, q, c0, v);
+            if (k == 0) {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] += pq[i] + sPar[c0 + i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
+            }
+            if (k < L - 1) {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] = elu1(v[i]);
+                st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
+                fence_proxy_async();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    issue_mma(tWork, sHB + k * C::TILE, sW + (k + 1) * C::WT, H, H);
+                    mma_commit(bar);
+                }
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        // ---- gradient of e' (adjoint of Eq. 5b plus the upstream edge gradient)
+        float gv[CW];
+        if (valid) {
+            float deo[CW];
+            if (A.has_de_out) ld_row_tile<CW>(sDE, row, c0, S, deo);
+#pragma unroll
+            for (int i = 0; i < CW; ++i) gv[i] = (A.has_de_out ? deo[i] : 0.f) + w * dar[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) gv[i] = 0.f;
+        }
+        // ---- LayerNorm adjoint
+        float mean, rstd;
+        row_stats<H, C::CG, CW>(v, sRed, row, g, A.eps, mean, rstd);
+        float dz[CW];
+        float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+            const float xh = (v[i] - mean) * rstd;
+            acc_g[i] += gv[i] * xh;
+            acc_b[i] += gv[i];
+            const float d = gv[i] * sPar[L * H + c0 + i];
+            dz[i] = d;
+            v[i] = xh;
+            m1 += d;
+            m2 += d * xh;
+        }
+        float s1, s2;
+        row_sum2<C::CG>(m1, m2, sRed + 2 * C::CG * 128, row, g, s1, s2);
+        s1 *= 1.f / H;
+        s2 *= 1.f / H;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
+        // ---- chain adjoint
+        for (int k = L - 1; k >= 0 && ok; --k) {
+            st_row_tile<CW>(sG, row, c0, S, dz);
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                issue_dgrad(tWork, sG, S, sW + k * C::WT, S, H, (uint32_t)H * S, H, H);
+                uint8_t* hk = (k == 0) ? sE0 : sHB + (k - 1) * C::TILE;
+                issue_wgrad(tDW(k), sG, S, 128u * S, hk, S, ones_addr - smem_u32(hk), H + 16, !first);
+                mma_commit(bar);
+            }
+            if (k == 0) {
+                // dz1 per edge (for the sender-side sum) and its receiver-side segmented sum
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < CW; i += 8) st_bf16x8(A.dz1 + eg * H + c0 + i, dz + i);
+                }
+#pragma unroll
+                for (int i = 0; i < CW; ++i) sStage[row * SLD + c0 + i] = dz[i];
+                __syncthreads();
+                const int nr = r1 - r0;
+                for (int it = tid; it < nr * H; it += C::NT) {
+                    const int rr = it / H, cc = it % H;
+                    const int32_t b0 = A.row_ptr[r0 + rr] - e0, b1 = A.row_ptr[r0 + rr + 1] - e0;
+                    float s = 0.f;
+                    for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
+                    A.dP[(int64_t)(r0 + rr) * H + cc] = s;
+                }
+            }
+            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ph ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            float dh[CW];
+            ld_acc<CW>(tWork, q, c0, dh);
+            if (k > 0) {
+                float hv[CW];
+                ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
+#pragma unroll
+                for (int i = 0; i < CW; ++i) dz[i] = dh[i] * elu1_deriv_from_out(hv[i]);
+            } else if (valid) {
+                float o[CW];
+#pragma unroll
+                for (int i = 0; i < CW; ++i) o[i] = gv[i] + dh[i];      // residual + W1c^T dz1
+#pragma unroll
+                for (int i = 0; i < CW; i += 8) st_bf16x8(A.de_in + eg * H + c0 + i, o + i);
+            }
+            tc_fence_before();
+        }
+        first = false;
+        fence_proxy_async();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        int64_t off = 0;
+        for (int k = 0; k < L; ++k) {
+            const int N = H + 16;
+            if (!first) flush_acc<C::CG>(tDW(k), N, H, q, lane, g, part + off);
+            else
+                for (int i = tid; i < H * N; i += C::NT) part[off + i] = 0.f;
+            off += (int64_t)H * N;
+        }
+        rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
+        rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ------------------------------------------------------------------ k_proj_bwd
+
+struct ProjBwdArgs {
+    const float* x;
+    const float* dP;
+    const __nv_bfloat16* dz1;
+    const int32_t* t_ptr;
+    const int32_t* t_eid;
+    const float* W1;
+    float* dx_in;       // += dP W1a + dQ W1b
+    float* part;
+    int64_t pstride;
+    int64_t n_rows;
+};
+
+template <int H>
+__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
+    using C = CfgB<H>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const ProjBwdSmem P = proj_bwd_smem<H>();
+    uint8_t* sW = sm + P.w;
+    uint8_t* sA = sm + P.a;
+    uint8_t* sX = sm + P.x;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
+    constexpr int S = C::S, S2 = C::S2, CW = C::CW;
+    constexpr uint32_t NCOLS = pow2_cols(2 * H);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    // [W1a; W1b] as a [2H x H] row tile (rows = stacked outputs, contiguous = inputs)
+    load_weight(sW, A.W1, 3 * H, 0, H, H, tid, C::NT, 2 * H, 0);
+    load_weight(sW, A.W1, 3 * H, H, H, H, tid, C::NT, 2 * H, H);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tWork = tmem, tDW = tmem + H;
+    uint32_t ph = 0;
+    bool ok = true, first = true;
+    const int64_t n_tiles = (A.n_rows + 127) / 128;
+
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t r = t * 128 + row;
+        const bool valid = r < A.n_rows;
+        float dp[CW], dq[CW], xv[CW];
+#pragma unroll
+        for (int i = 0; i < CW; ++i) dp[i] = dq[i] = xv[i] = 0.f;
+        if (valid) {
+            const float4* pp = reinterpret_cast<const float4*>(A.dP + r * H + c0);
+            const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                float4 u = __ldg(pp + i), w = __ldg(px + i);
+                dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
+                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+            }
+            for (int32_t k = A.t_ptr[r]; k < A.t_ptr[r + 1]; ++k) {      // sender-side sum, edge order
+                const int64_t e = A.t_eid[k];
+#pragma unroll
+                for (int i = 0; i < CW; i += 8) {
+                    float z[8];
+                    ld_bf16x8(A.dz1 + e * H + c0 + i, z);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) dq[i + j] += z[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CW; i += 8) {
+            st_tile8(sA, row, c0 + i, 128, S2, dp + i);
+            st_tile8(sA, row, H + c0 + i, 128, S2, dq + i);
+        }
+        st_row_tile<CW>(sX, row, c0, S, xv);
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_dgrad(tWork, sA, S2, sW, S, 2 * H, (uint32_t)(2 * H) * S, H, 2 * H);
+            issue_wgrad(tDW, sA, S2, 128u * S2, sX, S, 128u * S, H, !first);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+        ph ^= 1;
+        tc_fence_after();
+        if (!ok) break;
+        float d[CW];
+        ld_acc<CW>(tWork, q, c0, d);
+        tc_fence_before();
+        if (valid) {
+            float4* po = reinterpret_cast<float4*>(A.dx_in + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                float4 o = po[i];
+                o.x += d[4 * i];
+                o.y += d[4 * i + 1];
+                o.z += d[4 * i + 2];
+                o.w += d[4 * i + 3];
+                po[i] = o;
+            }
+        }
+        first = false;
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        const int M = 2 * H < 128 ? 2 * H : 128;
+        if (!first) flush_acc<C::CG>(tDW, H, M, q, lane, g, part);
+        else
+            for (int i = tid; i < 2 * H * H; i += C::NT) part[i] = 0.f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ------------------------------------------------------------------ partial reduction
+
+// dst[r*dst_ld + c] += sum over CTAs b (ascending) of part[b*pstride + src_off + r*src_ld + c]
+struct RedSeg {
+    float* dst;
+    int dst_ld, rows, cols;
+    int64_t src_off, src_ld;
+};
+
+constexpr int MAX_SEGS = 2 * GNN_MAX_LIN + 4;
+
+struct RedArgs {
+    RedSeg seg[MAX_SEGS];
+    int n_seg;
+    int64_t seg_start[MAX_SEGS + 1];   // prefix sums of rows*cols
+    const float* part;
+    int64_t pstride;
+    int n_cta;
+};
+
+__global__ void k_reduce_grads(RedArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.seg_start[A.n_seg]) return;
+    int s = 0;
+    while (i >= A.seg_start[s + 1]) ++s;
+    const RedSeg& sg = A.seg[s];
+    const int64_t j = i - A.seg_start[s];
+    const int r = (int)(j / sg.cols), c = (int)(j % sg.cols);
+    float acc = 0.f;
+    const float* p = A.part + sg.src_off + (int64_t)r * sg.src_ld + c;
+    for (int b = 0; b < A.n_cta; ++b) acc += p[(int64_t)b * A.pstride];
+    sg.dst[(int64_t)r * sg.dst_ld + c] += acc;
+}
+
+// =================================================================== host side
+
+namespace {
+
+using namespace host;
+
+struct BwdWs {
+    __nv_bfloat16* pq;
+    float* a;
+    float* da;
+    float* dP;
+    __nv_bfloat16* dz1;
+    float* part;
+    size_t bytes;
+};
+
+int64_t edge_pstride(int H, int L) { return (int64_t)L * H * (H + 16) + 2 * H; }
+int64_t node_pstride(int H, int L) { return (int64_t)H * (2 * H + 16) + (int64_t)(L - 1) * H * (H + 16) + 2 * H; }
+int64_t proj_pstride(int H) { return (int64_t)2 * H * H; }
+
+BwdWs carve_bwd(void* ws, const gnn_graph_dev& G, int H, int Le, int Ln, bool need_a) {
+    BwdWs w{};
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        void* p = ws ? (char*)ws + off : nullptr;
+        off += n;
+        return p;
+    };
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    const int64_t ncta = num_sms();
+    w.pq = (__nv_bfloat16*)take((size_t)NR * 2 * H * 2);
+    w.a = need_a ? (float*)take((size_t)NR * H * 4) : nullptr;
+    w.da = (float*)take((size_t)NR * H * 4);
+    w.dP = (float*)take((size_t)NR * H * 4);
+    w.dz1 = (__nv_bfloat16*)take((size_t)E * H * 2);
+    const int64_t ps = std::max(edge_pstride(H, Le), std::max(node_pstride(H, Ln), proj_pstride(H)));
+    w.part = (float*)take((size_t)ncta * ps * 4);
+    w.bytes = off + 256;
+    return w;
+}
+
+int reduce_grads(RedSeg* segs, int n, const float* part, int64_t pstride, int n_cta, cudaStream_t s) {
+    RedArgs A{};
+    A.n_seg = n;
+    A.seg_start[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        A.seg[i] = segs[i];
+        A.seg_start[i + 1] = A.seg_start[i] + (int64_t)segs[i].rows * segs[i].cols;
+    }
+    A.part = part;
+    A.pstride = pstride;
+    A.n_cta = n_cta;
+    const int64_t tot = A.seg_start[n];
+    if (tot == 0) return GNN_OK;
+    {
+        ProfScope _ps(s, "k_reduce_grads");
+        k_reduce_grads<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A);
+    }
+    GNN_LAUNCH_CHECK("k_reduce_grads");
+    return GNN_OK;
+}
+
+template <int H>
+int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+               const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
+               float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
+               cudaStream_t s) {
+    using C = CfgB<H>;
+    const int Le = W.edge.n_lin, Ln = W.node.n_lin;
+    GNN_REQUIRE(edge_bwd_tcols<H>(Le) <= 512 && node_bwd_tcols<H>(Ln) <= 512, GNN_EUNSUPPORTED,
+                "gnn_mp_backward: BF16 backward at H=%d supports at most %d Linear layers per MLP", H,
+                H == 64 ? 4 : 7);
+    BwdWs w = carve_bwd(ws, G, H, Le, Ln, a_star == nullptr);
+    GNN_REQUIRE(ws_bytes >= w.bytes, GNN_ENOMEM, "gnn_mp_backward: workspace too small");
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    if (NR == 0) return GNN_OK;
+    int rc;
+    // 0. recompute P|Q (and a* when it was not saved)
+    if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
+    if (!a_star) {
+        if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, nullptr, w.a, s))) return rc;
+    }
+    const float* astar = a_star ? a_star : w.a;
+    const int nsm = num_sms();
+    // 1. node MLP adjoint
+    {
+        NodeBwdArgs A;
+        A.a_star = astar;
+        A.x = x_in;
+        A.dx_out = dx_out;
+        A.da = w.da;
+        A.dx_in = dx_in;
+        A.part = w.part;
+        A.pstride = node_pstride(H, Ln);
+        A.n_rows = NR;
+        A.mlp = mlp_dev(W.node);
+        A.eps = cfg.ln_eps;
+        const NodeBwdSmem P = node_bwd_smem<H>(Ln);
+        int grid;
+        rc = persistent_grid(k_node_bwd<H>, C::NT, P.total, pow2_cols(node_bwd_tcols<H>(Ln)), (NR + 127) / 128,
+                             &grid);
+        if (rc) return rc;
+        grid = std::min(grid, nsm);
+        {
+            ProfScope _ps(s, "k_node_bwd");
+            k_node_bwd<H><<<grid, C::NT, P.total, s>>>(A);
+        }
+        GNN_LAUNCH_CHECK("k_node_bwd");
+        RedSeg seg[MAX_SEGS];
+        int n = 0;
+        int64_t off = 0;
+        for (int k = 0; k < Ln; ++k) {
+            const int in = k == 0 ? 2 * H : H;
+            const int N = in + 16;
+            seg[n++] = RedSeg{dW.node.W[k], in, H, in, off, N};
+            seg[n++] = RedSeg{dW.node.b[k], 1, H, 1, off + in, N};
+            off += (int64_t)H * N;
+        }
+        seg[n++] = RedSeg{dW.node.gamma, H, 1, H, off, 0};
+        seg[n++] = RedSeg{dW.node.beta, H, 1, H, off + H, 0};
+        if ((rc = reduce_grads(seg, n, w.part, A.pstride, grid, s))) return rc;
+    }
+    // 2. adjoint of the halo swap + sync
+    if (cfg.halo_mode == GNN_HALO_SYNC) {
+        if ((rc = plain::halo(G, w.da, H, s))) return rc;
+    }
+    // 3. edge MLP adjoint
+    if (E > 0) {
+        CUtensorMap tm_e, tm_de;
+        if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
+        if ((rc = make_row_tmap(&tm_de, de_out ? (const void*)de_out : (const void*)e_in, E, H))) return rc;
+        EdgeBwdArgs A;
+        A.row_ptr = G.row_ptr;
+        A.col = G.col;
+        A.edge_w = G.edge_w;
+        A.tiles = G.edge_tiles;
+        A.n_tiles = G.n_edge_tiles;
+        A.pq = w.pq;
+        A.da = w.da;
+        A.has_de_out = de_out != nullptr;
+        A.de_in = de_in;
+        A.dz1 = w.dz1;
+        A.dP = w.dP;
+        A.part = w.part;
+        A.pstride = edge_pstride(H, Le);
+        A.mlp = mlp_dev(W.edge);
+        A.eps = cfg.ln_eps;
+        const EdgeBwdSmem P = edge_bwd_smem<H>(Le);
+        int grid;
+        rc = persistent_grid(k_edge_bwd<H>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le)), G.n_edge_tiles,
+                             &grid);
+        if (rc) return rc;
+        grid = std::min(grid, nsm);
+        {
+            ProfScope _ps(s, "k_edge_bwd");
+            k_edge_bwd<H><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
+        }
+        GNN_LAUNCH_CHECK("k_edge_bwd");
+        RedSeg seg[MAX_SEGS];
+        int n = 0;
+        int64_t off = 0;
+        for (int k = 0; k < Le; ++k) {
+            const int N = H + 16;
+            if (k == 0) seg[n++] = RedSeg{dW.edge.W[0] + 2 * H, 3 * H, H, H, off, N};   // W1c columns of W1
+            else seg[n++] = RedSeg{dW.edge.W[k], H, H, H, off, N};
+            seg[n++] = RedSeg{dW.edge.b[k], 1, H, 1, off + H, N};
+            off += (int64_t)H * N;
+        }
+        seg[n++] = RedSeg{dW.edge.gamma, H, 1, H, off, 0};
+        seg[n++] = RedSeg{dW.edge.beta, H, 1, H, off + H, 0};
+        if ((rc = reduce_grads(seg, n, w.part, A.pstride, grid, s))) return rc;
+    } else {
+        GNN_CUDA_CHECK(cudaMemsetAsync(w.dP, 0, sizeof(float) * NR * H, s), "memset");
+    }
+    // 4. projection adjoint: sender-side sums, dx_in += [dP dQ] [W1a; W1b], dW1a, dW1b
+    {
+        ProjBwdArgs A;
+        A.x = x_in;
+        A.dP = w.dP;
+        A.dz1 = w.dz1;
+        A.t_ptr = G.t_ptr;
+        A.t_eid = G.t_eid;
+        A.W1 = W.edge.W[0];
+        A.dx_in = dx_in;
+        A.part = w.part;
+        A.pstride = proj_pstride(H);
+        A.n_rows = NR;
+        const ProjBwdSmem P = proj_bwd_smem<H>();
+        int grid;
+        rc = persistent_grid(k_proj_bwd<H>, C::NT, P.total, pow2_cols(2 * H), (NR + 127) / 128, &grid);
+        if (rc) return rc;
+        grid = std::min(grid, nsm);
+        {
+            ProfScope _ps(s, "k_proj_bwd");
+            k_proj_bwd<H><<<grid, C::NT, P.total, s>>>(A);
+        }
+        GNN_LAUNCH_CHECK("k_proj_bwd");
+        RedSeg seg[2];
+        seg[0] = RedSeg{dW.edge.W[0], 3 * H, H, H, 0, H};                     // dW1a -> W1[:, 0:H]
+        seg[1] = RedSeg{dW.edge.W[0] + H, 3 * H, H, H, (int64_t)H * H, H};    // dW1b -> W1[:, H:2H]
+        if ((rc = reduce_grads(seg, 2, w.part, A.pstride, grid, s))) return rc;
+    }
+    return GNN_OK;
+}
+
+}  // namespace
+
+size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
+    return carve_bwd(nullptr, G, cfg.hidden, W.edge.n_lin, W.node.n_lin, true).bytes;
+}
+
+int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
+                float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
+                cudaStream_t s) {
+    switch (cfg.hidden) {
+        case 16: return backward_h<16>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
+        case 32: return backward_h<32>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
+        case 64: return backward_h<64>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
+        default:
+            return set_error(GNN_EUNSUPPORTED, "gnn_mp_backward: the BF16 backward covers H in {16, 32, 64}");
+    }
+}
+
+}  // namespace fused
+}  // namespace gnn

@@ -1,0 +1,296 @@
+// Shared pieces of the fused BF16 kernels (forward and backward translation
+// units): per-H configuration, shared-memory plans, operand staging helpers
+// and the host-side launch helpers (TMA descriptors, persistent grids).
+#pragma once
+
+#include <algorithm>
+#include <mutex>
+
+#include "device_common.cuh"
+#include "tc_common.cuh"
+
+namespace gnn {
+namespace fused {
+
+using namespace tc;
+
+template <int H>
+struct Cfg {
+    static constexpr int S = (2 * H >= 128) ? 128 : 2 * H;   // swizzle span of a K=H tile
+    static constexpr int CG = H >= 32 ? H / 32 : 1;          // column groups
+    static constexpr int CW = H / CG;                        // columns per thread
+    static constexpr int NT = 128 * CG;                      // threads per CTA
+    static constexpr int TILE = 128 * H * 2;                 // [128 x H] BF16 row tile
+    static constexpr int WT = H * H * 2;                     // [H x H] BF16 weight tile
+    static constexpr uint32_t TCOLS = H < 32 ? 32 : H;       // TMEM columns of one accumulator
+};
+
+__host__ __device__ constexpr int span_of(int K) { return 2 * K >= 128 ? 128 : 2 * K; }
+__host__ __device__ constexpr uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+struct MlpDev {
+    const float* W[GNN_MAX_LIN];
+    const float* b[GNN_MAX_LIN];
+    const float* gamma;
+    const float* beta;
+    int n_lin;
+};
+
+// ------------------------------------------------------------------ device helpers
+
+// Convert W[n][c_off + k] (FP32, row stride ld, n < N, k < K) into rows
+// row_off.. of a K-major BF16 row tile with rows_total rows.
+__device__ __forceinline__ void load_weight(uint8_t* dst, const float* __restrict__ W, int ld, int c_off, int N,
+                                            int K, int tid, int nt, int rows_total = -1, int row_off = 0) {
+    const int S = span_of(K);
+    if (rows_total < 0) rows_total = N;
+    for (int i = tid; i < N * (K / 8); i += nt) {
+        const int n = i / (K / 8), k = (i % (K / 8)) * 8;
+        float v[8];
+        const float4* p = reinterpret_cast<const float4*>(W + (int64_t)n * ld + c_off + k);
+        float4 a = __ldg(p), b = __ldg(p + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        st_tile8(dst, row_off + n, k, rows_total, S, v);
+    }
+}
+
+// Issue D = A[128 x K] * B[N x K]^T (both K-major row tiles) from one thread.
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, const uint8_t* A, const uint8_t* Bt, int N, int K) {
+    const int S = span_of(K);
+    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint32_t id = idesc_bf16(128, N);
+    for (int k0 = 0; k0 < K; k0 += 16)
+        mma_bf16(d_tmem, kmajor_desc(a, 128, S, k0), kmajor_desc(b, N, S, k0), id, k0 > 0 ? 1u : 0u);
+}
+
+// D (+)= A[128 x K] * B[N x (b_k0 .. b_k0+K)]^T where B is a K-major row tile
+// whose full K extent is b_ktot (its swizzle span follows b_ktot).
+__device__ __forceinline__ void issue_mma_koff(uint32_t d_tmem, const uint8_t* A, const uint8_t* Bt, int N, int K,
+                                               int b_k0, int b_ktot, bool accumulate) {
+    const int Sa = span_of(K), Sb = span_of(b_ktot);
+    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint32_t id = idesc_bf16(128, N);
+    for (int k0 = 0; k0 < K; k0 += 16)
+        mma_bf16(d_tmem, kmajor_desc(a, 128, Sa, k0), kmajor_desc(b, N, Sb, b_k0 + k0), id,
+                 (accumulate || k0 > 0) ? 1u : 0u);
+}
+
+// Thread's CW accumulator columns starting at c0 of TMEM lane 32*q + laneid.
+template <int CW>
+__device__ __forceinline__ void ld_acc(uint32_t tmem, int q, int c0, float* v) {
+#pragma unroll
+    for (int i = 0; i < CW / 16; ++i) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * i), v + 16 * i);
+    tmem_ld_wait();
+}
+
+template <int CW>
+__device__ __forceinline__ void st_row_tile(uint8_t* tile, int row, int c0, int S, const float* v) {
+#pragma unroll
+    for (int i = 0; i < CW; i += 8) st_tile8(tile, row, c0 + i, 128, S, v + i);
+}
+
+template <int CW>
+__device__ __forceinline__ void ld_row_tile(const uint8_t* tile, int row, int c0, int S, float* v) {
+#pragma unroll
+    for (int i = 0; i < CW; i += 8) ld_tile8(tile, row, c0 + i, 128, S, v + i);
+}
+
+// Row mean / rstd of a row split over CG threads (two-pass, FP32), via red[2][CG][128].
+template <int H, int CG, int CW>
+__device__ __forceinline__ void row_stats(const float* v, float* red, int row, int g, float eps, float& mean,
+                                          float& rstd) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) s += v[i];
+    red[g * 128 + row] = s;
+    __syncthreads();
+    float tot = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) tot += red[k * 128 + row];
+    mean = tot * (1.f / H);
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        const float d = v[i] - mean;
+        q += d * d;
+    }
+    red[(CG + g) * 128 + row] = q;
+    __syncthreads();
+    float tq = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) tq += red[(CG + k) * 128 + row];
+    rstd = rsqrtf(tq * (1.f / H) + eps);
+}
+
+__device__ __forceinline__ void ld_bf16x8(const __nv_bfloat16* p, float* v) {
+    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    unpack_bf16x2(u.x, v[0], v[1]);
+    unpack_bf16x2(u.y, v[2], v[3]);
+    unpack_bf16x2(u.z, v[4], v[5]);
+    unpack_bf16x2(u.w, v[6], v[7]);
+}
+
+__device__ __forceinline__ void st_bf16x8(__nv_bfloat16* p, const float* v) {
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]);
+    u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]);
+    u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
+// ------------------------------------------------------------------ shared memory plans
+
+struct EdgeFwdSmem {
+    uint32_t w, a0, a1, par, seg, red, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin) {
+    using C = Cfg<H>;
+    EdgeFwdSmem s;
+    s.w = 0;
+    s.a0 = align_up(s.w + n_lin * C::WT, 1024);
+    s.a1 = s.a0 + C::TILE;
+    s.par = align_up(s.a1 + C::TILE, 16);
+    s.seg = s.par + (n_lin + 2) * H * 4;
+    s.red = s.seg + 128 * 4;
+    s.bar = align_up(s.red + 2 * C::CG * 128 * 4, 8);
+    s.tm = s.bar + 16;
+    s.total = s.tm + 16 + 1024;      // + slack for 1024-byte alignment of the base
+    return s;
+}
+
+struct NodeFwdSmem {
+    uint32_t w0, w, a0, a1, par, red, bar, tm, total;
+};
+
+// H = 128 streams the [a*, x] input through one [128 x H] buffer in two K
+// halves (the whole 2H-wide tile would not fit next to the weights).
+template <int H>
+struct NodeSplit {
+    static constexpr bool value = H >= 128;
+};
+
+template <int H>
+__host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin) {
+    using C = Cfg<H>;
+    constexpr bool split = NodeSplit<H>::value;
+    NodeFwdSmem s;
+    s.w0 = 0;                                         // W1 of the node MLP: [H x 2H]
+    s.w = align_up(s.w0 + 2 * C::WT, 1024);           // W2.. : (n_lin-1) x [H x H]
+    s.a0 = align_up(s.w + (n_lin - 1) * C::WT, 1024); // [128 x 2H] input tile (or [128 x H] when split)
+    s.a1 = split ? s.a0 : s.a0 + 2 * C::TILE;          // split: the chain reuses the input buffer
+    s.par = align_up(s.a1 + C::TILE, 16);
+    s.red = s.par + (n_lin + 2) * H * 4;
+    s.bar = align_up(s.red + 2 * C::CG * 128 * 4, 8);
+    s.tm = s.bar + 16;
+    s.total = s.tm + 16 + 1024;
+    return s;
+}
+
+struct ProjSmem {
+    uint32_t w, a, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline ProjSmem proj_smem() {
+    using C = Cfg<H>;
+    ProjSmem s;
+    s.w = 0;                                          // [2H x H]: W1a rows then W1b rows
+    s.a = align_up(s.w + 2 * C::WT, 1024);
+    s.bar = align_up(s.a + C::TILE, 8);
+    s.tm = s.bar + 16;
+    s.total = s.tm + 16 + 1024;
+    return s;
+}
+
+__device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
+}
+
+
+// ------------------------------------------------------------------ host helpers
+
+namespace host {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map over a [rows x H] BF16 row-major matrix, box = 128 rows x one swizzle span.
+inline int make_row_tmap(CUtensorMap* m, const void* base, int64_t rows, int H) {
+    EncodeTiledFn enc = encode_fn();
+    GNN_REQUIRE(enc, GNN_ECUDA, "cuTensorMapEncodeTiled is not available");
+    GNN_REQUIRE(((uintptr_t)base & 15) == 0, GNN_EINVAL, "edge buffer must be 16-byte aligned for TMA");
+    const int S = span_of(H);
+    cuuint64_t dims[2] = {(cuuint64_t)H, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)H * 2};
+    cuuint32_t box[2] = {(cuuint32_t)(S / 2), 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMapSwizzle sw = S == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                     : (S == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GNN_REQUIRE(r == CUDA_SUCCESS, GNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GNN_OK;
+}
+
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+// Persistent grid: resident CTAs (by shared memory / registers and by TMEM
+// columns) times SMs, capped by the number of tiles.
+template <class K>
+int persistent_grid(K kernel, int threads, uint32_t smem, uint32_t tmem_cols, int64_t tiles, int* out) {
+    GNN_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute");
+    int per_sm = 0;
+    GNN_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem),
+                   "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    GNN_REQUIRE(per_sm >= 1, GNN_EUNSUPPORTED, "fused kernel does not fit on an SM (smem %u)", smem);
+    per_sm = std::min<int>(per_sm, (int)(512 / tmem_cols));
+    *out = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)per_sm * num_sms()));
+    return GNN_OK;
+}
+
+inline MlpDev mlp_dev(const gnn_mlp& P) {
+    MlpDev d;
+    for (int k = 0; k < GNN_MAX_LIN; ++k) {
+        d.W[k] = k < P.n_lin ? P.W[k] : nullptr;
+        d.b[k] = k < P.n_lin ? P.b[k] : nullptr;
+    }
+    d.gamma = P.gamma;
+    d.beta = P.beta;
+    d.n_lin = P.n_lin;
+    return d;
+}
+
+}  // namespace host
+
+}  // namespace fused
+}  // namespace gnn

@@ -1,0 +1,210 @@
+"""Parity of the fused BF16 tcgen05 path with the FP64 oracle (needs a GB300).
+
+Tolerances: BF16 GEMM operands with FP32 accumulation and FP32 sums must match
+the FP64 oracle within 2e-2 relative L2 on layer outputs (edge state e' is
+stored in BF16) and 5e-2 on gradients. The oracle receives the same
+BF16-rounded edge state the kernels read, so the comparison measures the
+kernels' arithmetic, not the input rounding."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import model as om
+from paper_2410_01657_gb300 import _build
+from paper_2410_01657_gb300 import binding as B
+from paper_2410_01657_gb300 import nn as gnn
+from paper_2410_01657_gb300.graph import MeshGraph
+
+from gpu_util import oracle_subgraphs, rel_l2, split_edges, split_rows
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+TOL_OUT = 2e-2
+TOL_GRAD = 5e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.load()
+
+
+def _to(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def _bf16_round(a):
+    return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def _layer_case(nel, p, R, H, n_hidden, seed=0, method="rcb"):
+    brick, subs = oracle_subgraphs(nel, p, R, method)
+    part = MeshGraph(nel, p).partition(R, method)
+    G = part.to_device(DEV)
+    params = syn.gnn_params(seed, H, n_hidden, 1, randomize_affine=True)
+    rng = np.random.default_rng(seed + 1)
+    gid = part.array("row_gid")
+    x = rng.standard_normal((part.graph.n_nodes, H))[gid]
+    # one edge state per directed global edge, so duplicated edges carry equal copies
+    recv = part.receivers()
+    col = part.array("col")
+    key = gid[recv] * part.graph.n_nodes + gid[col]
+    uk, inv = np.unique(key, return_inverse=True)
+    e = _bf16_round(rng.standard_normal((uk.size, H))[inv])
+    return brick, subs, part, G, params, x, e
+
+
+def _run_fused_layer(G, params, H, x, e, precision="bf16"):
+    net = gnn.ConsistentGNN(params, precision=precision, device=DEV)
+    layer = net.layers[0]
+    edt = torch.bfloat16 if precision == "bf16" else torch.float32
+    xt, et = _to(x), _to(e, edt)
+    cfg = gnn.mp_config(H, precision)
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
+    xo = torch.empty_like(xt)
+    eo = torch.empty_like(et)
+    a = torch.empty_like(xt)
+    gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
+    B.call("gnn_check", None)
+    return xo.cpu().numpy(), eo.float().cpu().numpy(), a.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 2), (64, 2), (128, 2), (64, 0), (32, 5)])
+@pytest.mark.parametrize("R", [1, 3])
+def test_fused_layer_forward_vs_oracle(H, n_hidden, R):
+    brick, subs, part, G, params, x, e = _layer_case((4, 3, 3), 3, R, H, n_hidden)
+    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    xo, eo, a = _run_fused_layer(G, params, H, x, e)
+    assert rel_l2(a, np.concatenate(cache["a_star"])) < TOL_OUT
+    assert rel_l2(eo, np.concatenate(e1)) < TOL_OUT
+    assert rel_l2(xo, np.concatenate(x1)) < TOL_OUT
+    # coincident copies stay bitwise equal
+    gid = part.array("row_gid")
+    order = np.argsort(gid, kind="stable")
+    same = gid[order][1:] == gid[order][:-1]
+    assert np.array_equal(xo[order][1:][same], xo[order][:-1][same])
+
+
+def test_fused_forward_tiles_span_many_ctas():
+    # 10x10x10 elements at p=3: ~29.8k rows, 170k edges -> >1000 edge tiles over every SM
+    H = 64
+    brick, subs, part, G, params, x, e = _layer_case((10, 10, 10), 3, 8, H, 2, seed=3)
+    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    xo, eo, a = _run_fused_layer(G, params, H, x, e)
+    assert part.info.n_edge_tiles > 1000
+    assert rel_l2(eo, np.concatenate(e1)) < TOL_OUT
+    assert rel_l2(xo, np.concatenate(x1)) < TOL_OUT
+
+
+def test_fused_forward_matches_fp32_path_and_is_deterministic():
+    H = 64
+    brick, subs, part, G, params, x, e = _layer_case((5, 5, 5), 3, 4, H, 2, seed=5)
+    xb, eb, ab = _run_fused_layer(G, params, H, x, e, "bf16")
+    xb2, eb2, ab2 = _run_fused_layer(G, params, H, x, e, "bf16")
+    assert np.array_equal(xb, xb2) and np.array_equal(eb, eb2) and np.array_equal(ab, ab2)
+    xf, ef, af = _run_fused_layer(G, params, H, x, e, "fp32")
+    assert rel_l2(xb, xf) < TOL_OUT and rel_l2(eb, ef) < TOL_OUT
+
+
+def test_fused_partitioned_vs_unpartitioned():
+    H = 32
+    nel, p = (4, 4, 4), 2
+    params = syn.gnn_params(7, H, 2, 1, randomize_affine=True)
+    rng = np.random.default_rng(8)
+    out = {}
+    for R in (1, 8):
+        part = MeshGraph(nel, p).partition(R, "rcb")
+        G = part.to_device(DEV)
+        gid = part.array("row_gid")
+        xg = np.random.default_rng(8).standard_normal((part.graph.n_nodes, H))
+        recv = part.receivers()
+        col = part.array("col")
+        N = part.graph.n_nodes
+        key = gid[recv] * N + gid[col]
+        eg = np.random.default_rng(9).standard_normal((N * 7, H))   # per global edge by hash of the key
+        e = _bf16_round(eg[(key * 2654435761) % eg.shape[0]])
+        xo, eo, a = _run_fused_layer(G, params, H, xg[gid], e)
+        glob = np.zeros((N, H))
+        glob[gid] = xo
+        out[R] = glob
+    assert rel_l2(out[8], out[1]) < 1e-2
+
+
+def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=True):
+    brick, subs, part, G, params, x, e = _layer_case(nel, p, R, H, n_hidden, seed=seed)
+    lp = params["layers"][0]
+    rng = np.random.default_rng(seed + 5)
+    x1, e1, cache = om.layer_forward(lp, subs, split_rows(x, subs), split_edges(e, subs))
+    gid = part.array("row_gid")
+    dxg = rng.standard_normal((part.graph.n_nodes, H))
+    dx1 = dxg[gid] / np.maximum(part.array("node_deg")[:, None], 1)      # a consistent upstream gradient
+    de1 = _bf16_round(rng.standard_normal(e.shape) * 0.5) if with_de else np.zeros(e.shape)
+    dx0, de0, g = om.layer_backward(lp, subs, cache, split_rows(dx1, subs), split_edges(de1, subs))
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layer = net.layers[0]
+    tens = layer.edge.tensors() + layer.node.tensors()
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+    dparams = [torch.zeros_like(t) for t in tens]
+    dW = gnn.mp_params(layer.edge.dims, layer.node.dims, dparams)
+    cfg = gnn.mp_config(H, "bf16")
+    xt, et = _to(x), _to(e, torch.bfloat16)
+    xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
+    gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
+    dxi, dei = torch.empty_like(xt), torch.empty_like(et)
+    gnn.gnn_mp_backward(G, cfg, W, xt, et, a, _to(dx1), _to(de1, torch.bfloat16) if with_de else None,
+                        dxi, dei, dW)
+    B.call("gnn_check", None)
+    refs = list(g["edge"]["W"]) + list(g["edge"]["b"]) + [g["edge"]["gamma"], g["edge"]["beta"]] \
+        + list(g["node"]["W"]) + list(g["node"]["b"]) + [g["node"]["gamma"], g["node"]["beta"]]
+    return (dxi.cpu().numpy(), dei.float().cpu().numpy(), [d.cpu().numpy() for d in dparams],
+            np.concatenate(dx0), np.concatenate(de0), refs)
+
+
+@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 2), (64, 2), (64, 0), (32, 5)])
+@pytest.mark.parametrize("R", [1, 3])
+def test_fused_layer_backward_vs_oracle(H, n_hidden, R):
+    dx, de, dws, dx_ref, de_ref, refs = _layer_backward_case(H, n_hidden, R)
+    assert rel_l2(dx, dx_ref) < TOL_GRAD
+    assert rel_l2(de, de_ref) < TOL_GRAD
+    for k, (got, ref) in enumerate(zip(dws, refs)):
+        assert rel_l2(got, ref) < TOL_GRAD, (k, rel_l2(got, ref))
+
+
+def test_fused_layer_backward_without_edge_grad():
+    dx, de, dws, dx_ref, de_ref, refs = _layer_backward_case(64, 2, 2, with_de=False)
+    assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
+    for got, ref in zip(dws, refs):
+        assert rel_l2(got, ref) < TOL_GRAD
+
+
+def test_fused_backward_many_tiles_and_deterministic():
+    out = [_layer_backward_case(64, 2, 8, nel=(8, 8, 8), p=3, seed=13) for _ in range(2)]
+    dx, de, dws, dx_ref, de_ref, refs = out[0]
+    assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
+    for got, ref in zip(dws, refs):
+        assert rel_l2(got, ref) < TOL_GRAD
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a, b)
+
+
+def test_fused_network_training_step_vs_oracle():
+    # encoders + 2 consistent layers + decoder + Eq. 8 loss, BF16 layers, R=3
+    from gpu_util import flat_grads, node_field, oracle_network
+    nel, p, H, M, R = (3, 3, 2), 2, 32, 2, 3
+    brick, subs = oracle_subgraphs(nel, p, R, "rcb")
+    part = MeshGraph(nel, p).partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(21, H, 2, M, randomize_affine=True)
+    u, target = node_field(brick, 1), node_field(brick, 2)
+    ys, L, g, _ = oracle_network(params, brick, subs, u, target)
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    y = net(G, _to(np.concatenate([u[sg.gid] for sg in subs])), G.edge_attr())
+    loss = gnn.consistent_loss(y, _to(np.concatenate([target[sg.gid] for sg in subs])), G)
+    loss.backward()
+    assert rel_l2(y.detach().cpu().numpy(), np.concatenate(ys)) < TOL_OUT
+    assert abs(loss.item() - L) < TOL_OUT * abs(L)
+    gg = dict(flat_grads(net.grads_numpy()))
+    for name, ref in flat_grads(g):
+        assert rel_l2(gg[name], ref) < TOL_GRAD, (name, rel_l2(gg[name], ref))

@@ -34,9 +34,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NEL, P, R, H, NH, M = (16, 16, 16), 5, 8, 64, 2, 4
-E_UNPART = 6 * 81 * 81 * 80          # directed edges of the 81^3 GLL lattice
-N_UNPART = 81 ** 3
+P, R, H, NH, M = 5, 8, 64, 2, 4
 SEED = 0
 
 
@@ -49,6 +47,8 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwd: forward only (inference form of the layer stack)")
+    ap.add_argument("--nel", type=int, default=16,
+                    help="elements per axis of the brick (16 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
@@ -213,7 +213,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
-def build_problem(dev, precision):
+def build_problem(dev, precision, nel=16):
     import numpy as np
     import torch
 
@@ -221,7 +221,7 @@ def build_problem(dev, precision):
     from paper_2410_01657_gb300 import nn as gnn
     from paper_2410_01657_gb300.graph import MeshGraph
 
-    part = MeshGraph(NEL, P).partition(R, "rcb")
+    part = MeshGraph((nel,) * 3, P).partition(R, "rcb")
     G = part.to_device(dev)
     params = syn.gnn_params(SEED, H, NH, M)
     modes = syn.fourier_modes(SEED, 8)
@@ -322,7 +322,10 @@ def main():
         torch.cuda.synchronize()
 
     precision = args.precision
-    part, G, net, stack, dx_top, u, t = build_problem(dev, precision)
+    part, G, net, stack, dx_top, u, t = build_problem(dev, precision, args.nel)
+    L_lat = args.nel * P + 1
+    e_unpart = 6 * L_lat * L_lat * (L_lat - 1)
+    n_unpart = L_lat ** 3
     peaks = load_peaks()
     barrier()
     with ClockSampler(local) as clk:
@@ -332,7 +335,7 @@ def main():
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    value = world * E_UNPART * M / (ms * 1e-3)
+    value = world * e_unpart * M / (ms * 1e-3)
     launches = sum(n for n, _ in report.values())
     total_ms = sum(v for _, v in report.values()) or 1.0
     top = max(report.items(), key=lambda kv: kv[1][1]) if report else ("none", (1, 0.0))
@@ -357,10 +360,10 @@ def main():
     if precision == "bf16" and not args.no_fp32:
         del stack
         torch.cuda.empty_cache()
-        _, G32, _, stack32, dx32, _, _ = build_problem(dev, "fp32")
+        _, G32, _, stack32, dx32, _, _ = build_problem(dev, "fp32", args.nel)
         ms32, _ = time_stack(stack32, dx32, max(3, args.steps // 2), 2, profile=False,
                              fwd_only=args.mode == "fwd")
-        fp32 = {"value": E_UNPART * M / (ms32 * 1e-3), "unit": "edges/s", "ms_per_step": ms32,
+        fp32 = {"value": e_unpart * M / (ms32 * 1e-3), "unit": "edges/s", "ms_per_step": ms32,
                 "speedup_of_bf16": ms32 / ms}
         del stack32
         torch.cuda.empty_cache()
@@ -368,7 +371,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         ms_e, h2d, d2h = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
-        e2e = {"value": world * E_UNPART * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
+        e2e = {"value": world * e_unpart * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "step": "encoders + 4 layers + decoder + consistent loss, fwd+bwd, host inputs"}
 
@@ -382,12 +385,13 @@ def main():
         line = {"metric": "MP-layer edges/s fwd+bwd" if args.mode == "fwdbwd" else "MP-layer edges/s fwd", "value": value, "unit": "edges/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
-                "config": {"workload": "consistent NMP layers x4 fwd+bwd, 16^3 elements p=5 GLL brick "
-                                       "(531,441 nodes, 3,149,280 edges), 8 RCB sub-graphs, H=64, MLP 2 hidden",
+                "config": {"workload": f"consistent NMP layers x4 fwd+bwd, {args.nel}^3 elements p=5 GLL brick "
+                                       f"({n_unpart:,} nodes, {e_unpart:,} edges), 8 RCB sub-graphs, H=64, "
+                                       "MLP 2 hidden",
                            "rows": part.n_rows, "edges_partitioned": part.n_edges,
                            "l2": "inputs larger than L2 (edge state > 400 MB), no flush",
                            "parallelism": f"replicas x{world}"},
-                "nodes_per_s": world * N_UNPART * M / (ms * 1e-3),
+                "nodes_per_s": world * n_unpart * M / (ms * 1e-3),
                 "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu,
                 "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
                 "clocks": clk.summary()}

@@ -213,6 +213,16 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the whole-job step time of weak-scaled replicas)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_problem(dev, precision, nel=16):
     import numpy as np
     import torch
@@ -331,10 +341,7 @@ def main():
     with ClockSampler(local) as clk:
         ms, report = time_stack(stack, dx_top, args.steps, args.warmup, fwd_only=args.mode == "fwd")
     barrier()
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     value = world * e_unpart * M / (ms * 1e-3)
     launches = sum(n for n, _ in report.values())
     total_ms = sum(v for _, v in report.values()) or 1.0

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict
             issue_mma(tmem, sA, sW, 2 * H, H);
             mma_commit(bar);
         }
-        ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+        ok = block_wait(bar, phase, tid);
         phase ^= 1;
         tc_fence_after();
         if (!ok) break;
@@ -193,9 +193,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             for (int kb = 0; kb < (H + 63) / 64; ++kb)
                 tma_load_2d(sA0 + kb * 128 * 128, &tmap_e, kb * 64, e0, bar_tma);
         }
-        // receiver of each edge of the tile (local row index)
+        // the tile's CSR slice (local edge offsets) and the receiver of each edge
+        int32_t* sRp = sSeg + 128;
+        for (int rr = tid; rr <= r1 - r0; rr += C::NT) sRp[rr] = A.row_ptr[r0 + rr] - e0;
+        __syncthreads();
         for (int rr = tid; rr < r1 - r0; rr += C::NT)
-            for (int32_t e = A.row_ptr[r0 + rr]; e < A.row_ptr[r0 + rr + 1]; ++e) sSeg[e - e0] = rr;
+            for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) sSeg[e] = rr;
         __syncthreads();
         const bool valid = row < ne;
         const int64_t eg = (int64_t)e0 + row;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < C::CW; ++i) pq[i] = 0.f;
         }
-        ok = __syncthreads_and(mbar_wait(bar_tma, ph_tma) ? 1 : 0) != 0;
+        ok = block_wait(bar_tma, ph_tma, tid);
         ph_tma ^= 1;
         if (!ok) break;
         if (tid == 0) {
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
         }
         float v[C::CW];
         for (int k = 0; k < n_lin && ok; ++k) {
-            ok = __syncthreads_and(mbar_wait(bar_mma, ph_mma) ? 1 : 0) != 0;
+            ok = block_wait(bar_mma, ph_mma, tid);
             ph_mma ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             }
             if (k < n_lin - 1) {
 #pragma unroll
-                for (int i = 0; i < C::CW; ++i) v[i] = elu1(v[i]);
+                for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<C::CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             const int nr = r1 - r0;
             for (int it = tid; it < nr * SC; it += C::NT) {
                 const int rr = it / SC, cc = it % SC;
-                const int32_t b0 = A.row_ptr[r0 + rr] - e0, b1 = A.row_ptr[r0 + rr + 1] - e0;
+                const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];
                 float s = 0.f;
                 for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
                 A.a[(int64_t)(r0 + rr) * H + pass * SC + cc] = s;
@@ -296,6 +299,294 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
+}
+
+// ------------------------------------------------------------------ k_edge_fwd_ws (warp-specialised)
+//
+// Same arithmetic as k_edge_fwd, reorganised so that no consumer thread waits
+// on a global-memory index load: one producer warp walks the CTA's tiles ahead
+// of the consumers, writing each tile's CSR slice, receiver/sender indices and
+// 1/d into a ring of NS shared-memory stages and starting the TMA load of the
+// tile's edge states into the same stage. Two consumer groups take alternate
+// tiles, so one group's MMA and barrier latency overlaps the other group's
+// epilogue. Stage s is handed over through mbarriers full[s] (32 producer
+// arrivals + the TMA bytes) and empty[s] (one consumer arrival).
+
+constexpr int WS_NS = 4;   // stages
+constexpr int WS_NG = 2;   // consumer groups
+
+struct StageMeta {
+    int32_t r0, r1, e0, ne;
+    int32_t rp[132];       // tile CSR slice, local edge offsets
+    int32_t seg[128];      // local receiver of each edge
+    int32_t col[128];      // sender row of each edge
+    float w[128];          // 1/d of each edge
+};
+
+struct EdgeFwdWsSmem {
+    uint32_t w, st, meta, a1, stg, par, red, bar, tm, total;
+};
+
+template <int H>
+__host__ __device__ inline EdgeFwdWsSmem edge_fwd_ws_smem(int n_lin) {
+    using C = Cfg<H>;
+    EdgeFwdWsSmem s;
+    s.w = 0;
+    s.st = align_up(n_lin * C::WT, 1024);
+    s.meta = s.st + WS_NS * C::TILE;
+    s.a1 = align_up(s.meta + WS_NS * (uint32_t)sizeof(StageMeta), 1024);
+    s.stg = s.a1 + WS_NG * C::TILE;
+    s.par = s.stg + WS_NG * 128 * (H / 2 + 4) * 4;
+    s.red = s.par + (n_lin + 2) * H * 4;
+    s.bar = align_up(s.red + WS_NG * 2 * C::CG * 128 * 4, 8);
+    s.tm = s.bar + 8 * (2 * WS_NS + WS_NG);
+    s.total = s.tm + 16 + 1024;
+    return s;
+}
+
+template <int H>
+struct WsCfg {
+    static constexpr int GT = Cfg<H>::NT;            // threads per consumer group
+    static constexpr int NT = WS_NG * GT + 32;       // + one producer warp
+};
+
+template <int H, int CG, int CW>
+__device__ __forceinline__ void row_stats_named(const float* v, float* red, int row, int g, float eps, int bar_id,
+                                                int nthr, float& mean, float& rstd) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) s += v[i];
+    red[g * 128 + row] = s;
+    named_sync(bar_id, nthr);
+    float tot = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) tot += red[k * 128 + row];
+    mean = tot * (1.f / H);
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        const float d = v[i] - mean;
+        q += d * d;
+    }
+    red[(CG + g) * 128 + row] = q;
+    named_sync(bar_id, nthr);
+    float tq = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) tq += red[(CG + k) * 128 + row];
+    rstd = rsqrtf(tq * (1.f / H) + eps);
+}
+
+// One elected thread polls the mbarrier; the named-barrier group agrees.
+__device__ __forceinline__ bool group_wait(uint64_t* bar, uint32_t parity, bool elected, int bar_id, int nthr) {
+    const bool mine = elected ? mbar_wait(bar, parity) : true;
+    return named_and(mine, bar_id, nthr);
+}
+
+template <int H>
+__global__ void __launch_bounds__(WsCfg<H>::NT, 1)
+    k_edge_fwd_ws(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
+    using C = Cfg<H>;
+    constexpr int GT = WsCfg<H>::GT;
+    constexpr int SC = H / 2, SLD = SC + 4;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int n_lin = A.mlp.n_lin;
+    const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(n_lin);
+    uint8_t* sW = sm + L.w;
+    float* sPar = reinterpret_cast<float*>(sm + L.par);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint64_t* empty = full + WS_NS;
+    uint64_t* mbar = empty + WS_NS;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
+    auto stage_e = [&](int s) { return sm + L.st + s * C::TILE; };
+    auto stage_m = [&](int s) { return reinterpret_cast<StageMeta*>(sm + L.meta + s * sizeof(StageMeta)); };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool producer = tid >= WS_NG * GT;
+    const uint32_t TC = C::TCOLS;
+    const uint32_t NCOLS = TC * WS_NG < 32 ? 32 : TC * WS_NG;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < WS_NS; ++s) {
+            mbar_init(full + s, 32);
+            mbar_init(empty + s, 1);
+        }
+        for (int g = 0; g < WS_NG; ++g) mbar_init(mbar + g, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, WsCfg<H>::NT);
+    for (int k = 1; k < n_lin; ++k) load_weight(sW + k * C::WT, A.mlp.W[k], H, 0, H, H, tid, WsCfg<H>::NT);
+    for (int i = tid; i < n_lin * H; i += WsCfg<H>::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += WsCfg<H>::NT) {
+        sPar[n_lin * H + i] = A.mlp.gamma[i];
+        sPar[(n_lin + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (producer) {
+        // ---------------- producer warp: tile metadata + TMA, NS tiles ahead
+        int j = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
+            const int s = j % WS_NS;
+            if (j >= WS_NS) {
+                ok = mbar_wait(empty + s, (uint32_t)((j / WS_NS) - 1) & 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+            }
+            StageMeta* m = stage_m(s);
+            const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
+            const int32_t e0 = A.row_ptr[r0], ne = A.row_ptr[r1] - e0;
+            for (int i = lane; i <= r1 - r0; i += 32) m->rp[i] = A.row_ptr[r0 + i] - e0;
+            __syncwarp();
+            for (int rr = lane; rr < r1 - r0; rr += 32)
+                for (int32_t e = m->rp[rr]; e < m->rp[rr + 1]; ++e) m->seg[e] = rr;
+            for (int e = lane; e < ne; e += 32) {
+                m->col[e] = A.col[e0 + e];
+                m->w[e] = A.edge_w[e0 + e];
+            }
+            if (lane == 0) {
+                m->r0 = r0;
+                m->r1 = r1;
+                m->e0 = e0;
+                m->ne = ne;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive_expect_tx(full + s, C::TILE);
+#pragma unroll
+                for (int kb = 0; kb < (H + 63) / 64; ++kb)
+                    tma_load_2d(stage_e(s) + kb * 128 * 128, &tmap_e, kb * 64, e0, full + s);
+            } else {
+                mbar_arrive(full + s);
+            }
+        }
+    } else {
+        // ---------------- consumer group g
+        const int g = tid / GT, gt = tid % GT, wg = gt >> 5;
+        const int q = wg & 3, cg = wg >> 2, row = 32 * q + lane, c0 = cg * C::CW;
+        const int bid = 1 + g;
+        const bool elected = gt == 0;
+        const uint32_t tm = tmem + (uint32_t)g * TC;
+        uint8_t* sA1 = sm + L.a1 + g * C::TILE;
+        float* sStage = reinterpret_cast<float*>(sm + L.stg + g * 128 * SLD * 4);
+        float* sRed = reinterpret_cast<float*>(sm + L.red + g * 2 * C::CG * 128 * 4);
+        uint32_t ph_mma = 0;
+        bool ok = true;
+        int j = 0;
+        for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
+            if (j % WS_NG != g) continue;
+            const int s = j % WS_NS;
+            ok = group_wait(full + s, (uint32_t)(j / WS_NS) & 1u, elected, bid, GT);
+            if (!ok) break;
+            const StageMeta* m = stage_m(s);
+            uint8_t* sE = stage_e(s);
+            const int32_t r0 = m->r0, r1 = m->r1;
+            const int64_t e0 = m->e0;
+            const int ne = m->ne;
+            if (elected) {
+                tc_fence_after();
+                issue_mma(tm, sE, sW, H, H);
+                mma_commit(mbar + g);
+            }
+            const bool valid = row < ne;
+            const int64_t eg = e0 + row;
+            float w = 0.f;
+            float pq[C::CW];
+            if (valid) {
+                const int64_t rcv = r0 + m->seg[row];
+                const int64_t snd = m->col[row];
+                w = m->w[row];
+#pragma unroll
+                for (int i = 0; i < C::CW; i += 8) {
+                    float pv[8], qv[8];
+                    ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
+                    ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) pq[i + jj] = pv[jj] + qv[jj];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) pq[i] = 0.f;
+            }
+            float v[C::CW];
+            for (int k = 0; k < n_lin && ok; ++k) {
+                ok = group_wait(mbar + g, ph_mma, elected, bid, GT);
+                ph_mma ^= 1;
+                tc_fence_after();
+                if (!ok) break;
+                ld_acc<C::CW>(tm, q, c0, v);
+                const float* bk = sPar + k * H + c0;
+                if (k == 0) {
+#pragma unroll
+                    for (int i = 0; i < C::CW; ++i) v[i] += pq[i] + bk[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < C::CW; ++i) v[i] += bk[i];
+                }
+                if (k < n_lin - 1) {
+#pragma unroll
+                    for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
+                    st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+                    fence_proxy_async();
+                    tc_fence_before();
+                    named_sync(bid, GT);
+                    if (elected) {
+                        tc_fence_after();
+                        issue_mma(tm, sA1, sW + (k + 1) * C::WT, H, H);
+                        mma_commit(mbar + g);
+                    }
+                }
+            }
+            if (!ok) break;
+            tc_fence_before();
+            float mean, rstd;
+            row_stats_named<H, C::CG, C::CW>(v, sRed, row, cg, A.eps, bid, GT, mean, rstd);
+            float eo[C::CW];
+            ld_row_tile<C::CW>(sE, row, c0, C::S, eo);
+            const float* gam = sPar + n_lin * H + c0;
+            const float* bet = sPar + (n_lin + 1) * H + c0;
+#pragma unroll
+            for (int i = 0; i < C::CW; ++i) v[i] = eo[i] + (v[i] - mean) * rstd * gam[i] + bet[i];
+            if (valid && A.e_out) {
+#pragma unroll
+                for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.e_out + eg * H + c0 + i, v + i);
+            }
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) {
+                    const int c = c0 + i;
+                    if (c >= pass * SC && c < (pass + 1) * SC) sStage[row * SLD + (c - pass * SC)] = w * v[i];
+                }
+                named_sync(bid, GT);
+                const int nr = r1 - r0;
+                for (int it = gt; it < nr * SC; it += GT) {
+                    const int rr = it / SC, cc = it % SC;
+                    const int32_t b0 = m->rp[rr], b1 = m->rp[rr + 1];
+                    float acc = 0.f;
+                    for (int32_t e = b0; e < b1; ++e) acc += sStage[e * SLD + cc];
+                    A.a[(int64_t)(r0 + rr) * H + pass * SC + cc] = acc;
+                }
+                named_sync(bid, GT);
+            }
+            fence_proxy_async();           // generic reads of the stage precede its next TMA write
+            named_sync(bid, GT);
+            if (elected) mbar_arrive(empty + s);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
 // ------------------------------------------------------------------ k_node_fwd
@@ -395,7 +686,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
                 issue_mma_koff(tmem, sA0, sW0, H, H, 0, 2 * H, false);
                 mma_commit(bar_mma);
             }
-            ok = __syncthreads_and(mbar_wait(bar_mma, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar_mma, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -411,7 +702,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
         }
         float v[C::CW];
         for (int k = 0; k < n_lin && ok; ++k) {
-            ok = __syncthreads_and(mbar_wait(bar_mma, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar_mma, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -421,7 +712,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
             for (int i = 0; i < C::CW; ++i) v[i] += bk[i];
             if (k < n_lin - 1) {
 #pragma unroll
-                for (int i = 0; i < C::CW; ++i) v[i] = elu1(v[i]);
+                for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<C::CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -528,11 +819,18 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.a = a;
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
-        const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin);
         int grid;
-        rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid);
-        if (rc) return rc;
-        {
+        if constexpr (H <= 64) {
+            const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(W.edge.n_lin);
+            const uint32_t ncols = C::TCOLS * WS_NG < 32 ? 32 : C::TCOLS * WS_NG;
+            rc = persistent_grid(k_edge_fwd_ws<H>, WsCfg<H>::NT, L.total, ncols, G.n_edge_tiles, &grid);
+            if (rc) return rc;
+            ProfScope _ps(s, "k_edge_fwd");
+            k_edge_fwd_ws<H><<<grid, WsCfg<H>::NT, L.total, s>>>(tm, A);
+        } else {
+            const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin);
+            rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid);
+            if (rc) return rc;
             ProfScope _ps(s, "k_edge_fwd");
             k_edge_fwd<H><<<grid, C::NT, L.total, s>>>(tm, A);
         }

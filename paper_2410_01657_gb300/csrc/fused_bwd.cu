@@ -165,8 +165,8 @@ __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
     s.stage = align_up(s.ones + 128 * C::S, 1024);
     s.par = s.stage + 128 * (H + 4) * 4;
-    s.seg = s.par + (n_lin + 2) * H * 4;
-    s.red = s.seg + 128 * 4;
+    s.seg = s.par + (n_lin + 2) * H * 4;               // seg[128] then the tile's CSR slice rp[132]
+    s.red = s.seg + (128 + 132) * 4;
     s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);
     s.tm = s.bar + 16;
     uint32_t end = s.tm + 16;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
         // ---- recompute the chain
         float v[CW];
         for (int k = 0; k < L && ok; ++k) {
-            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
             if (k < L - 1) {
 #pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = elu1(v[i]);
+                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                 }
                 mma_commit(bar);
             }
-            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -539,8 +539,11 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             tma_load_2d(sE0, &tmap_e, 0, e0, bar_tma);
             if (A.has_de_out) tma_load_2d(sDE, &tmap_de, 0, e0, bar_tma);
         }
+        int32_t* sRp = sSeg + 128;
+        for (int rr = tid; rr <= r1 - r0; rr += C::NT) sRp[rr] = A.row_ptr[r0 + rr] - e0;
+        __syncthreads();
         for (int rr = tid; rr < r1 - r0; rr += C::NT)
-            for (int32_t e = A.row_ptr[r0 + rr]; e < A.row_ptr[r0 + rr + 1]; ++e) sSeg[e - e0] = rr;
+            for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) sSeg[e] = rr;
         __syncthreads();
         const bool valid = row < ne;
         const int64_t eg = (int64_t)e0 + row;
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
             for (int i = 0; i < CW; ++i) pq[i] = dar[i] = 0.f;
         }
-        ok = __syncthreads_and(mbar_wait(bar_tma, ph_tma) ? 1 : 0) != 0;
+        ok = block_wait(bar_tma, ph_tma, tid);
         ph_tma ^= 1;
         if (!ok) break;
         if (tid == 0) {
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         // ---- recompute the chain
         float v[CW];
         for (int k = 0; k < L && ok; ++k) {
-            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -594,7 +597,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             }
             if (k < L - 1) {
 #pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = elu1(v[i]);
+                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -666,13 +669,13 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 const int nr = r1 - r0;
                 for (int it = tid; it < nr * H; it += C::NT) {
                     const int rr = it / H, cc = it % H;
-                    const int32_t b0 = A.row_ptr[r0 + rr] - e0, b1 = A.row_ptr[r0 + rr + 1] - e0;
+                    const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];
                     float s = 0.f;
                     for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
                     A.dP[(int64_t)(r0 + rr) * H + cc] = s;
                 }
             }
-            ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+            ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
@@ -812,7 +815,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
             issue_wgrad(tDW, sA, S2, 128u * S2, sX, S, 128u * S, H, !first);
             mma_commit(bar);
         }
-        ok = __syncthreads_and(mbar_wait(bar, ph) ? 1 : 0) != 0;
+        ok = block_wait(bar, ph, tid);
         ph ^= 1;
         tc_fence_after();
         if (!ok) break;

@@ -38,6 +38,18 @@ struct MlpDev {
 
 // ------------------------------------------------------------------ device helpers
 
+// One thread polls the mbarrier (bounded), the block agrees on the outcome.
+// The barrier also orders the observed completion before every thread's
+// subsequent tcgen05/shared-memory accesses.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, int tid) {
+    const int mine = (tid == 0) ? (mbar_wait(bar, parity) ? 1 : 0) : 1;
+    return __syncthreads_and(mine) != 0;
+}
+
+// ELU (alpha 1) with e^z - 1 from the fast exponential: the result is rounded
+// to BF16 next, far coarser than the absolute error of __expf(z) - 1.
+__device__ __forceinline__ float elu1_fast(float z) { return z > 0.f ? z : __expf(z) - 1.f; }
+
 // Convert W[n][c_off + k] (FP32, row stride ld, n < N, k < K) into rows
 // row_off.. of a K-major BF16 row tile with rows_total rows.
 __device__ __forceinline__ void load_weight(uint8_t* dst, const float* __restrict__ W, int ld, int c_off, int N,
@@ -154,8 +166,8 @@ __host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin) {
     s.a0 = align_up(s.w + n_lin * C::WT, 1024);
     s.a1 = s.a0 + C::TILE;
     s.par = align_up(s.a1 + C::TILE, 16);
-    s.seg = s.par + (n_lin + 2) * H * 4;
-    s.red = s.seg + 128 * 4;
+    s.seg = s.par + (n_lin + 2) * H * 4;               // seg[128] then the tile's CSR slice rp[132]
+    s.red = s.seg + (128 + 132) * 4;
     s.bar = align_up(s.red + 2 * C::CG * 128 * 4, 8);
     s.tm = s.bar + 16;
     s.total = s.tm + 16 + 1024;      // + slack for 1024-byte alignment of the base
@@ -269,6 +281,9 @@ template <class K>
 int persistent_grid(K kernel, int threads, uint32_t smem, uint32_t tmem_cols, int64_t tiles, int* out) {
     GNN_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                    "cudaFuncSetAttribute");
+    GNN_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared),
+                   "cudaFuncSetAttribute(carveout)");
     int per_sm = 0;
     GNN_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem),
                    "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

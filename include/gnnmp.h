@@ -242,6 +242,29 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
                     const float* dx_out, const void* de_out, float* dx_in, void* de_in,
                     const gnn_mp_params* dW, void* ws, size_t ws_bytes, void* stream);
 
+/* gnn_mp_forward for callers that cannot allocate device memory when they run
+ * the layer: code executing while a CUDA stream is being captured without a
+ * graph memory pool, or a host framework that owns the device allocator and
+ * passes the library only the tensors it computes on. The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Same arguments and results as gnn_mp_forward with GNN_PREC_BF16, minus the
+ * workspace: the scratch (P|Q rows, plus the aggregate when a_star_out is
+ * NULL) lives in a fixed 64 MiB area compiled into the library, which every
+ * GPU that loads the library keeps until the process exits. The area fits
+ * about n_rows * 4H bytes of scratch (n_rows * 8H when a_star_out is NULL);
+ * larger graphs get GNN_ESHAPE with the required size in gnn_last_error(),
+ * before any work is queued. GNN_EDTYPE for GNN_PREC_FP32.
+ * The first call on each device looks up the area's device address (with
+ * that device current); make that first call before any stream capture. No
+ * call allocates or frees device memory. All calls share the one area and
+ * every byte of scratch is written before it is read, so nothing carries over
+ * between calls, but calls whose executions overlap on the GPU (two streams,
+ * or two host threads) race on it: serialise them. */
+int gnn_mp_forward_static(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                          const float* x_in, const void* e_in, float* x_out, void* e_out, float* a_star_out,
+                          void* stream);
+
 /* Eq. 5c-5d on one GPU: for every global id held by >= 2 rows, replace each
  * copy by the sum of all copies (summed in increasing sub-graph order, so all
  * copies end bitwise equal). rows: device FP32 [n_rows x width], in place.

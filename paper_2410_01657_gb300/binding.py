@@ -100,6 +100,8 @@ _SIGS = {
     "gnn_mp_backward": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                   C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P, _P,
                                   C.POINTER(gnn_mp_params), _P, C.c_size_t, _P]),
+    "gnn_mp_forward_static": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
+                                        C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P]),
     "gnn_halo_exchange": (C.c_int, [C.POINTER(gnn_graph_dev), _P, C.c_int32, _P]),
     "gnn_mlp_workspace_size": (C.c_int, [C.POINTER(gnn_mlp), C.c_int64, C.POINTER(C.c_size_t),
                                          C.POINTER(C.c_size_t)]),

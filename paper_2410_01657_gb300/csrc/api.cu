@@ -129,6 +129,23 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
                                    (const __nv_bfloat16*)de_out, dx_in, (__nv_bfloat16*)de_in, *dW, ws, ws_bytes, s);
 }
 
+int gnn_mp_forward_static(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                          const float* x_in, const void* e_in, float* x_out, void* e_out, float* a_star_out,
+                          void* stream) {
+    int rc = check_graph(G, "gnn_mp_forward_static");
+    if (rc) return rc;
+    if ((rc = check_cfg(cfg, W, "gnn_mp_forward_static"))) return rc;
+    GNN_REQUIRE(cfg->precision == GNN_PREC_BF16, GNN_EDTYPE,
+                "gnn_mp_forward_static: only the BF16 fused path has a built-in scratch area");
+    if (G->n_rows) GNN_REQUIRE(x_in && x_out, GNN_EINVAL, "gnn_mp_forward_static: NULL node buffer");
+    if (G->n_edges) GNN_REQUIRE(e_in, GNN_EINVAL, "gnn_mp_forward_static: NULL e_in");
+    GNN_REQUIRE(e_out || (cfg->flags & GNN_FLAG_NO_EDGE_OUT) || G->n_edges == 0, GNN_EINVAL,
+                "gnn_mp_forward_static: NULL e_out without GNN_FLAG_NO_EDGE_OUT");
+    GNN_REQUIRE(x_out != x_in || G->n_rows == 0, GNN_EINVAL, "gnn_mp_forward_static: x_out aliases x_in");
+    return gnn::fused::mp_forward_static(*G, *cfg, *W, x_in, (const __nv_bfloat16*)e_in, x_out,
+                                         (__nv_bfloat16*)e_out, a_star_out, (cudaStream_t)stream);
+}
+
 int gnn_halo_exchange(const gnn_graph_dev* G, float* rows, int32_t width, void* stream) {
     int rc = check_graph(G, "gnn_halo_exchange");
     if (rc) return rc;

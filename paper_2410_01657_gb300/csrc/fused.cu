@@ -898,6 +898,60 @@ int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_
     GNN_H_DISPATCH(cfg.hidden, node_h<HH>(G, cfg, W, a, x_in, x_out, s));
 }
 
+// ------------------------------------------------------------------ forward with a built-in scratch area
+//
+// Some callers cannot allocate device memory when they run the layer: code
+// that executes while a CUDA stream is being captured without a graph memory
+// pool, or a host framework that owns the device allocator and hands the
+// library only the tensors it computes on. mp_forward_static serves them with
+// a fixed scratch area that is part of this library's device image instead of
+// a caller workspace. Every GPU that loads the library holds the area until
+// the process exits, and every call shares it: calls whose executions overlap
+// on the GPU (two streams, or two host threads) race on it.
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[128] = {};   // device address of g_static_scratch per device ordinal
+}  // namespace
+
+size_t static_scratch_bytes() { return kStaticScratchBytes; }
+
+// Looks up (once per device, with that device current) the device address of
+// the scratch array; host code must not use the array's name as a pointer.
+static int static_scratch_address(void** out) {
+    int dev = 0;
+    GNN_CUDA_CHECK(cudaGetDevice(&dev), "gnn_mp_forward_static: cudaGetDevice");
+    GNN_REQUIRE(dev >= 0 && dev < 128, GNN_EUNSUPPORTED, "gnn_mp_forward_static: device ordinal %d", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        GNN_CUDA_CHECK(cudaGetSymbolAddress(&p, g_static_scratch), "gnn_mp_forward_static: cudaGetSymbolAddress");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return GNN_OK;
+}
+
+int mp_forward_static(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                      const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out,
+                      cudaStream_t s) {
+    // scratch: P|Q rows (and the aggregate when a_star_out is NULL); every byte
+    // of it is written before it is read, so nothing needs clearing between calls
+    const size_t need = carve_fwd(nullptr, G, cfg.hidden, a_star_out == nullptr, false).bytes;
+    GNN_REQUIRE(need <= kStaticScratchBytes, GNN_ESHAPE,
+                "gnn_mp_forward_static: this graph needs %zu bytes of scratch, the built-in area holds %zu "
+                "(about n_rows * 4H bytes, plus n_rows * 4H more when a_star_out is NULL); "
+                "use gnn_mp_forward with a workspace",
+                need, kStaticScratchBytes);
+    void* scratch = nullptr;
+    int rc = static_scratch_address(&scratch);
+    if (rc) return rc;
+    return mp_forward(G, cfg, W, x_in, e_in, x_out, e_out, a_star_out, scratch, kStaticScratchBytes, s);
+}
+
 int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
                size_t ws_bytes, cudaStream_t s) {

@@ -20,6 +20,12 @@ int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_p
                 float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
                 cudaStream_t s);
 
+// gnn_mp_forward without a caller workspace (built-in scratch area).
+size_t static_scratch_bytes();
+int mp_forward_static(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                      const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out,
+                      cudaStream_t s);
+
 // Steps of the forward shared with the backward's recomputation.
 int proj_forward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const float* x_in, __nv_bfloat16* pq,
                  cudaStream_t s);

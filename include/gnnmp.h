@@ -149,6 +149,15 @@ int gnn_partition_get_info(const gnn_partition* p, gnn_partition_info* info);
 #define GNN_P_EDGE_ATTR   14   /* float [n_edges*4] [dx,dy,dz,|d|], d = pos(send)-pos(recv) */
 #define GNN_P_ROW_POS     15   /* double [n_rows*3]                                         */
 #define GNN_P_PART_STATS  16   /* int64 [R*3] per sub-graph: local rows, halo rows, neighbours */
+#define GNN_P_TILE_META   17   /* uint8 [n_edge_tiles * GNN_TILE_META_BYTES] per-tile records   */
+
+/* Per-edge-tile record (GNN_P_TILE_META), one 2 KiB block per tile so a kernel
+ * can fetch a tile's bookkeeping with one bulk copy: bytes 0..15 int32
+ * {first row r0, end row r1, first edge e0, edge count ne}; 16..543 int32
+ * rp[132] = row_ptr[r0+i] - e0 for i <= r1-r0; 544..799 int16 seg[128] =
+ * local receiver row of each edge; 800..1311 int32 col[128] = sender row;
+ * 1312..1823 float w[128] = 1/d_ij; the rest zero. */
+#define GNN_TILE_META_BYTES 2048
 int gnn_partition_copy(const gnn_partition* p, int32_t what, void* dst, size_t bytes);
 
 /* ====================================================== device-side graph
@@ -170,6 +179,7 @@ typedef struct gnn_graph_dev {
     int64_t n_edge_tiles;
     const int32_t* edge_tiles;  /* [n_edge_tiles+1] */
     int32_t max_in_degree;      /* host copy of gnn_partition_info.max_in_degree            */
+    const void*    tile_meta;   /* [n_edge_tiles * GNN_TILE_META_BYTES], 16-byte aligned    */
 } gnn_graph_dev;
 
 /* ====================================================== parameters

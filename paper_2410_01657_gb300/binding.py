@@ -27,7 +27,9 @@ GNN_NODE_TILE = 128
 
 (GNN_P_ROW_OFFSETS, GNN_P_EDGE_OFFSETS, GNN_P_ROW_GID, GNN_P_ROW_PTR, GNN_P_COL, GNN_P_EDGE_DEG,
  GNN_P_EDGE_W, GNN_P_NODE_DEG, GNN_P_NODE_W, GNN_P_T_PTR, GNN_P_T_EID, GNN_P_HALO_PTR,
- GNN_P_HALO_ROWS, GNN_P_EDGE_TILES, GNN_P_EDGE_ATTR, GNN_P_ROW_POS, GNN_P_PART_STATS) = range(17)
+ GNN_P_HALO_ROWS, GNN_P_EDGE_TILES, GNN_P_EDGE_ATTR, GNN_P_ROW_POS, GNN_P_PART_STATS,
+ GNN_P_TILE_META) = range(18)
+GNN_TILE_META_BYTES = 2048
 
 
 class GnnError(RuntimeError):
@@ -59,7 +61,7 @@ class gnn_graph_dev(C.Structure):
                 ("t_ptr", C.c_void_p), ("t_eid", C.c_void_p), ("node_w", C.c_void_p),
                 ("n_shared", C.c_int64), ("halo_ptr", C.c_void_p), ("halo_rows", C.c_void_p),
                 ("n_edge_tiles", C.c_int64), ("edge_tiles", C.c_void_p),
-                ("max_in_degree", C.c_int32)]
+                ("max_in_degree", C.c_int32), ("tile_meta", C.c_void_p)]
 
 
 class gnn_mlp(C.Structure):

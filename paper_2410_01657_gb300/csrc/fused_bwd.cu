@@ -158,17 +158,17 @@ __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     using C = CfgB<H>;
     EdgeBwdSmem s;
     s.w = 0;
-    s.e0 = align_up(n_lin * C::WT, 1024);
+    s.e0 = align_up(n_lin * C::WT, 1024);         // 2 stages of {e tile, de tile}
     s.de = s.e0 + C::TILE;
-    s.g = s.de + C::TILE;
+    s.seg = s.e0 + 4 * C::TILE;                    // 2 tile records (GNN_TILE_META_BYTES each)
+    s.g = align_up(s.seg + 2 * GNN_TILE_META_BYTES, 1024);
     s.hb = s.g + C::TILE;
     s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
     s.stage = align_up(s.ones + 128 * C::S, 1024);
     s.par = s.stage + 128 * (H + 4) * 4;
-    s.seg = s.par + (n_lin + 2) * H * 4;               // seg[128] then the tile's CSR slice rp[132]
-    s.red = s.seg + (128 + 132) * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);
-    s.tm = s.bar + 16;
+    s.red = s.par + (n_lin + 2) * H * 4;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma
+    s.tm = s.bar + 24;
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
     s.total = end + 1024;
@@ -453,10 +453,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
 // ------------------------------------------------------------------ k_edge_bwd
 
 struct EdgeBwdArgs {
-    const int32_t* row_ptr;
-    const int32_t* col;
-    const float* edge_w;
-    const int32_t* tiles;
+    const uint8_t* tile_meta;   // per-tile records (GNN_TILE_META_BYTES each)
     int64_t n_tiles;
     const __nv_bfloat16* pq;
     const float* da;            // gradient of the aggregate after the halo adjoint
@@ -480,17 +477,16 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     const int L = A.mlp.n_lin;
     const EdgeBwdSmem P = edge_bwd_smem<H>(L);
     uint8_t* sW = sm + P.w;
-    uint8_t* sE0 = sm + P.e0;
-    uint8_t* sDE = sm + P.de;
+    uint8_t* sStg0 = sm + P.e0;       // stage s: e tile at +2*s*TILE, de tile right after it
+    uint8_t* sRec0 = sm + P.seg;      // stage s: tile record at +s*GNN_TILE_META_BYTES
     uint8_t* sG = sm + P.g;
     uint8_t* sHB = sm + P.hb;
     uint8_t* sOnes = sm + P.ones;
     float* sStage = reinterpret_cast<float*>(sm + P.stage);
     float* sPar = reinterpret_cast<float*>(sm + P.par);
-    int32_t* sSeg = reinterpret_cast<int32_t*>(sm + P.seg);
     float* sRed = reinterpret_cast<float*>(sm + P.red);
-    uint64_t* bar_tma = reinterpret_cast<uint64_t*>(sm + P.bar);
-    uint64_t* bar = bar_tma + 1;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.bar);   // full[2]: stage loaded
+    uint64_t* bar = full + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, CW = C::CW, SLD = H + 4;
     const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L));
@@ -503,7 +499,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar_tma, 1);
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
         mbar_init(bar, 1);
         fence_mbar_init();
     }
@@ -526,41 +523,58 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     float acc_g[CW], acc_b[CW];
 #pragma unroll
     for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
-    uint32_t ph_tma = 0, ph = 0;
+    uint32_t ph = 0;
     bool ok = true, first = true;
-    const uint32_t tx_bytes = C::TILE * (A.has_de_out ? 2 : 1);
+    const uint32_t tx_bytes = C::TILE * (A.has_de_out ? 2 : 1) + GNN_TILE_META_BYTES;
+    // stage s <- tile t: its record by bulk copy, its e (and de_out) rows by TMA
+    auto issue_stage = [&](int s, int64_t t) {
+        uint8_t* rec = sRec0 + s * GNN_TILE_META_BYTES;
+        uint8_t* se = sStg0 + s * 2 * C::TILE;
+        const int32_t e0 = reinterpret_cast<const int32_t*>(A.tile_meta + t * GNN_TILE_META_BYTES)[2];
+        mbar_arrive_expect_tx(full + s, tx_bytes);
+        bulk_load(rec, A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, full + s);
+        tma_load_2d(se, &tmap_e, 0, e0, full + s);
+        if (A.has_de_out) tma_load_2d(se + C::TILE, &tmap_de, 0, e0, full + s);
+    };
+    if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) issue_stage(0, blockIdx.x);
+    int j = 0;
 
-    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
-        const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
-        const int32_t e0 = A.row_ptr[r0], e1 = A.row_ptr[r1];
-        const int ne = e1 - e0;
-        if (tid == 0) {
-            mbar_arrive_expect_tx(bar_tma, tx_bytes);
-            tma_load_2d(sE0, &tmap_e, 0, e0, bar_tma);
-            if (A.has_de_out) tma_load_2d(sDE, &tmap_de, 0, e0, bar_tma);
-        }
-        int32_t* sRp = sSeg + 128;
-        for (int rr = tid; rr <= r1 - r0; rr += C::NT) sRp[rr] = A.row_ptr[r0 + rr] - e0;
-        __syncthreads();
-        for (int rr = tid; rr < r1 - r0; rr += C::NT)
-            for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) sSeg[e] = rr;
-        __syncthreads();
+    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
+        const int st = j & 1;
+        ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
+        if (!ok) break;
+        // the other stage was released at the end of the previous tile: prefetch the next tile
+        if (tid == 0 && t + gridDim.x < A.n_tiles) issue_stage(st ^ 1, t + gridDim.x);
+        const uint8_t* rec = sRec0 + st * GNN_TILE_META_BYTES;
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
+        const int32_t* sRp = reinterpret_cast<const int32_t*>(rec + 16);
+        const int16_t* sSeg = reinterpret_cast<const int16_t*>(rec + 544);
+        const int32_t* sCol = reinterpret_cast<const int32_t*>(rec + 800);
+        const float* sW1d = reinterpret_cast<const float*>(rec + 1312);
+        uint8_t* sE0 = sStg0 + st * 2 * C::TILE;
+        uint8_t* sDE = sE0 + C::TILE;
+        const int32_t r0 = hdr[0], r1 = hdr[1], e0 = hdr[2], ne = hdr[3];
         const bool valid = row < ne;
         const int64_t eg = (int64_t)e0 + row;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tWork, sE0, sW, H, H);
+            mma_commit(bar);
+        }
         float w = 0.f;
         float pq[CW], dar[CW];
         int64_t rcv = 0;
         if (valid) {
             rcv = r0 + sSeg[row];
-            const int64_t snd = A.col[eg];
-            w = A.edge_w[eg];
+            const int64_t snd = sCol[row];
+            w = sW1d[row];
 #pragma unroll
             for (int i = 0; i < CW; i += 8) {
                 float pv[8], qv[8];
                 ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
                 ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) pq[i + j] = pv[j] + qv[j];
+                for (int jj = 0; jj < 8; ++jj) pq[i + jj] = pv[jj] + qv[jj];
             }
             const float4* pd = reinterpret_cast<const float4*>(A.da + rcv * H + c0);
 #pragma unroll
@@ -571,14 +585,6 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         } else {
 #pragma unroll
             for (int i = 0; i < CW; ++i) pq[i] = dar[i] = 0.f;
-        }
-        ok = block_wait(bar_tma, ph_tma, tid);
-        ph_tma ^= 1;
-        if (!ok) break;
-        if (tid == 0) {
-            tc_fence_after();
-            issue_mma(tWork, sE0, sW, H, H);
-            mma_commit(bar);
         }
         // ---- recompute the chain
         float v[CW];
@@ -1020,10 +1026,9 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
         if ((rc = make_row_tmap(&tm_de, de_out ? (const void*)de_out : (const void*)e_in, E, H))) return rc;
         EdgeBwdArgs A;
-        A.row_ptr = G.row_ptr;
-        A.col = G.col;
-        A.edge_w = G.edge_w;
-        A.tiles = G.edge_tiles;
+        GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
+                    "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
+        A.tile_meta = (const uint8_t*)G.tile_meta;
         A.n_tiles = G.n_edge_tiles;
         A.pq = w.pq;
         A.da = w.da;

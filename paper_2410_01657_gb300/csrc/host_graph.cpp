@@ -107,6 +107,7 @@ struct gnn_partition {
     std::vector<int32_t> t_ptr, t_eid;
     std::vector<int32_t> halo_ptr, halo_rows;
     std::vector<int32_t> edge_tiles;
+    std::vector<uint8_t> tile_meta;
     std::vector<double> row_pos;
     std::vector<int64_t> part_stats;
 };
@@ -608,6 +609,32 @@ int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method, const doub
                 r0 = r1;
             }
         }
+        // ---- one fixed-size record per edge tile (layout in gnnmp.h, GNN_P_TILE_META)
+        {
+            const int64_t nt = (int64_t)P->edge_tiles.size() - 1;
+            P->tile_meta.assign((size_t)nt * GNN_TILE_META_BYTES, 0);
+            parallel_for(nt, [&](int64_t t) {
+                uint8_t* rec = P->tile_meta.data() + (size_t)t * GNN_TILE_META_BYTES;
+                int32_t* hdr = reinterpret_cast<int32_t*>(rec);
+                int32_t* rp = reinterpret_cast<int32_t*>(rec + 16);
+                int16_t* seg = reinterpret_cast<int16_t*>(rec + 544);
+                int32_t* cl = reinterpret_cast<int32_t*>(rec + 800);
+                float* w = reinterpret_cast<float*>(rec + 1312);
+                const int32_t r0 = P->edge_tiles[t], r1 = P->edge_tiles[t + 1];
+                const int32_t e0 = P->row_ptr[r0], ne = P->row_ptr[r1] - e0;
+                hdr[0] = r0;
+                hdr[1] = r1;
+                hdr[2] = e0;
+                hdr[3] = ne;
+                for (int32_t i = 0; i <= r1 - r0; ++i) rp[i] = P->row_ptr[r0 + i] - e0;
+                for (int32_t i = 0; i < r1 - r0; ++i)
+                    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) seg[e] = (int16_t)i;
+                for (int32_t e = 0; e < ne; ++e) {
+                    cl[e] = P->col[e0 + e];
+                    w[e] = 1.0f / (float)P->edge_deg[e0 + e];
+                }
+            });
+        }
         // ---- positions per row
         P->row_pos.resize(NR * 3);
         for (int64_t i = 0; i < NR; ++i)
@@ -664,6 +691,7 @@ int gnn_partition_copy(const gnn_partition* P, int32_t what, void* dst, size_t b
         case GNN_P_EDGE_TILES: src = P->edge_tiles.data(); n = P->edge_tiles.size() * 4; break;
         case GNN_P_ROW_POS: src = P->row_pos.data(); n = P->row_pos.size() * 8; break;
         case GNN_P_PART_STATS: src = P->part_stats.data(); n = P->part_stats.size() * 8; break;
+        case GNN_P_TILE_META: src = P->tile_meta.data(); n = P->tile_meta.size(); break;
         case GNN_P_EDGE_ATTR: {
             const int64_t NR = (int64_t)P->row_gid.size();
             tmp.resize(P->col.size() * 4);

@@ -96,6 +96,7 @@ _ARRAYS = {
     "edge_attr": (B.GNN_P_EDGE_ATTR, np.float32, lambda i: (i.n_edges, 4)),
     "row_pos": (B.GNN_P_ROW_POS, np.float64, lambda i: (i.n_rows, 3)),
     "part_stats": (B.GNN_P_PART_STATS, np.int64, lambda i: (i.n_parts, 3)),
+    "tile_meta": (B.GNN_P_TILE_META, np.uint8, lambda i: (i.n_edge_tiles * B.GNN_TILE_META_BYTES,)),
 }
 
 
@@ -159,7 +160,7 @@ class DeviceGraph:
         self.device = torch.device(device)
         t = {}
         for name in ("row_ptr", "col", "edge_w", "t_ptr", "t_eid", "node_w", "halo_ptr", "halo_rows",
-                     "edge_tiles"):
+                     "edge_tiles", "tile_meta"):
             t[name] = torch.from_numpy(part.array(name)).to(self.device)
         self.t = t
         g = B.gnn_graph_dev()
@@ -177,6 +178,7 @@ class DeviceGraph:
         g.n_edge_tiles = int(part.info.n_edge_tiles)
         g.edge_tiles = B.ptr(t["edge_tiles"])
         g.max_in_degree = int(part.info.max_in_degree)
+        g.tile_meta = B.ptr(t["tile_meta"])
         self.struct = g
 
     @property

@@ -137,3 +137,23 @@ def test_partition_errors():
         g.partition(3, "slab")
     with pytest.raises(B.GnnError):
         g.partition(2, "rcb", [1.0, -1.0])
+
+
+def test_tile_records_match_partition_arrays():
+    part = MeshGraph((4, 3, 5), 2).partition(5, "rcb", [1, 3, 2, 7, 1])
+    rec = part.array("tile_meta").reshape(-1, B.GNN_TILE_META_BYTES)
+    tiles = part.array("edge_tiles")
+    rp = part.array("row_ptr")
+    col = part.array("col")
+    w = part.array("edge_w")
+    assert rec.shape[0] == len(tiles) - 1
+    for t in range(rec.shape[0]):
+        hdr = rec[t, :16].view(np.int32)
+        r0, r1 = tiles[t], tiles[t + 1]
+        e0, ne = rp[r0], rp[r1] - rp[r0]
+        assert hdr.tolist() == [r0, r1, e0, ne]
+        assert np.array_equal(rec[t, 16:16 + 4 * (r1 - r0 + 1)].view(np.int32), rp[r0:r1 + 1] - e0)
+        seg = rec[t, 544:544 + 2 * ne].view(np.int16)
+        assert np.array_equal(seg, np.repeat(np.arange(r1 - r0), np.diff(rp[r0:r1 + 1])))
+        assert np.array_equal(rec[t, 800:800 + 4 * ne].view(np.int32), col[e0:e0 + ne])
+        assert np.array_equal(rec[t, 1312:1312 + 4 * ne].view(np.float32), w[e0:e0 + ne])

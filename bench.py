@@ -118,6 +118,24 @@ def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int) -> float | N
     return None
 
 
+def measured_traffic(kernel: str, n_edges: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, scaled by
+    the edge count; None when the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "edge_kernel_traffic.json")) as fh:
+            d = json.load(fh)
+        h = hashlib.sha256()
+        for f in d["sources_hashed"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != d["source_hash"] or kernel not in d["bytes_per_edge"]:
+            return None
+        return d["bytes_per_edge"][kernel] * n_edges
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def sgemm_flops_per_step(G, hidden: int, n_lin: int, layers: int) -> float:
     """FP32 SIMT GEMM FLOPs of one plain-path step (forward, recompute, dgrad, wgrad)."""
     E, N, Hh = G.n_edges, G.n_rows, hidden
@@ -353,7 +371,8 @@ def main():
     if abytes is not None:
         ach = abytes / (top_ms / top_n * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"],
+                "frac": ach / peaks["hbm_gbs"], "traffic": measured_traffic(top_name, G.n_edges),
+                "peak_src": peaks["src"],
                 "share": top_ms / total_ms}
     elif top_name == "k_sgemm":
         flops = sgemm_flops_per_step(G, H, NH + 2, M) * args.steps

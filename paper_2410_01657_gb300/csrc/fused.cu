@@ -353,27 +353,24 @@ struct WsCfg {
 template <int H, int CG, int CW>
 __device__ __forceinline__ void row_stats_named(const float* v, float* red, int row, int g, float eps, int bar_id,
                                                 int nthr, float& mean, float& rstd) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < CW; ++i) s += v[i];
-    red[g * 128 + row] = s;
-    named_sync(bar_id, nthr);
-    float tot = 0.f;
-#pragma unroll
-    for (int k = 0; k < CG; ++k) tot += red[k * 128 + row];
-    mean = tot * (1.f / H);
-    float q = 0.f;
+    // one reduction for sum and sum of squares: var = E[v^2] - mean^2 (FP32)
+    float s = 0.f, q = 0.f;
 #pragma unroll
     for (int i = 0; i < CW; ++i) {
-        const float d = v[i] - mean;
-        q += d * d;
+        s += v[i];
+        q += v[i] * v[i];
     }
+    red[g * 128 + row] = s;
     red[(CG + g) * 128 + row] = q;
     named_sync(bar_id, nthr);
-    float tq = 0.f;
+    float ts = 0.f, tq = 0.f;
 #pragma unroll
-    for (int k = 0; k < CG; ++k) tq += red[(CG + k) * 128 + row];
-    rstd = rsqrtf(tq * (1.f / H) + eps);
+    for (int k = 0; k < CG; ++k) {
+        ts += red[k * 128 + row];
+        tq += red[(CG + k) * 128 + row];
+    }
+    mean = ts * (1.f / H);
+    rstd = rsqrtf(fmaxf(tq * (1.f / H) - mean * mean, 0.f) + eps);
 }
 
 // One elected thread polls the mbarrier; the named-barrier group agrees.

@@ -116,13 +116,26 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int64_t nsplit
 }
 
 // part[b*cols + c] = sum of X[r*ld + c] over rows r of chunk b, r ascending.
-__global__ void k_colsum_partial(const float* __restrict__ X, int64_t rows, int64_t ld, int cols,
-                                 int64_t chunk, float* __restrict__ part) {
-    int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+__global__ void __launch_bounds__(256) k_colsum_partial(const float* __restrict__ X, int64_t rows, int64_t ld,
+                                                        int cols, int64_t chunk, float* __restrict__ part) {
+    // 32 columns x 8 row lanes per pass over the chunk; the 8 partial sums of a
+    // column are combined in lane order, so the result does not depend on timing.
+    __shared__ float red[8][33];
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+    for (int c0 = 0; c0 < cols; c0 += 32) {
+        const int c = c0 + cx;
         float s = 0.f;
-        for (int64_t r = r0; r < r1; ++r) s += X[r * ld + c];
-        part[(int64_t)blockIdx.x * cols + c] = s;
+        if (c < cols)
+            for (int64_t r = r0 + ry; r < r1; r += 8) s += X[r * ld + c];
+        red[ry][cx] = s;
+        __syncthreads();
+        if (ry == 0 && c < cols) {
+            float t = 0.f;
+            for (int k = 0; k < 8; ++k) t += red[k][cx];
+            part[(int64_t)blockIdx.x * cols + c] = t;
+        }
+        __syncthreads();
     }
 }
 

@@ -58,6 +58,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint64_t t0 = globaltimer_ns();
     while (true) {
         if (mbar_try_wait(b, parity)) return true;
+        __nanosleep(64);   // yield issue slots to the warps doing work
         if (globaltimer_ns() - t0 > 1000000000ull) {
             raise_device_error(GNN_DEVERR_TIMEOUT);
             return false;

@@ -136,3 +136,35 @@ def gnn_params(seed: int, hidden: int, n_hidden: int, n_layers: int, f_x: int = 
         })
     p["dec"] = xavier_mlp(rng, mlp_dims(H, H, n_hidden, f_y), False, randomize_affine)
     return p
+
+
+def rescale_counts(counts, total: int) -> np.ndarray:
+    """Scale integer counts to sum to ``total`` by largest-remainder rounding
+    (ties to the lower index), keeping every count >= 1."""
+    c = np.asarray(counts, dtype=np.float64)
+    raw = c * (total / c.sum())
+    out = np.maximum(1, np.floor(raw)).astype(np.int64)
+    rem = raw - np.floor(raw)
+    order = sorted(range(len(c)), key=lambda i: (-rem[i], i))
+    k = 0
+    while out.sum() < total:
+        out[order[k % len(c)]] += 1
+        k += 1
+    k = 0
+    while out.sum() > total:
+        i = order[::-1][k % len(c)]
+        if out[i] > 1:
+            out[i] -= 1
+        k += 1
+    return out
+
+
+def uneven_brick(n_parts: int, lo: float, hi: float, seed: int):
+    """Element counts of ``n_parts`` sub-graphs drawn log-uniform on [lo, hi],
+    the smallest cube n^3 holding them, and the counts rescaled to n^3
+    (the RCB target weights of the batching workload)."""
+    counts = log_uniform_counts(n_parts, lo, hi, seed)
+    n = int(np.ceil(round(counts.sum() ** (1.0 / 3.0), 9)))
+    while n ** 3 < counts.sum():
+        n += 1
+    return n, rescale_counts(counts, n ** 3)

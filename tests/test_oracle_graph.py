@@ -187,3 +187,13 @@ def test_jitter_bounds_and_boundary():
         on_face = (idx[a] == 0) | (idx[a] == L - 1)
         assert np.all(off[on_face] == 0.0)
         assert np.abs(off[~on_face]).max() > 0.5 * frac * sp.min()
+
+
+def test_uneven_partition_recipe():
+    import synthetic as syn
+    n, w = syn.uneven_brick(64, 50, 5000, 0)
+    assert n == 41 and w.sum() == 41 ** 3 and w.min() >= 1
+    c = syn.log_uniform_counts(64, 50, 5000, 0)
+    assert np.all((c >= 50) & (c <= 5000))
+    r = syn.rescale_counts([1, 2, 3], 12)
+    assert r.sum() == 12 and list(r) == [2, 4, 6]

@@ -109,8 +109,10 @@ typedef struct gnn_partition_info {
     int64_t n_edges;         /* sum of local directed edges                                */
     int64_t n_shared;        /* global ids held by >= 2 sub-graphs                        */
     int64_t n_copies;        /* rows holding those ids (length of the copy list)          */
-    int64_t n_edge_tiles;    /* receiver-aligned tiles of <= GNN_EDGE_TILE edges           */
+    int64_t n_edge_tiles;    /* receiver-aligned tiles of <= tile_edges edges              */
     int64_t n_node_tiles;    /* tiles of GNN_NODE_TILE consecutive rows                    */
+    int32_t tile_edges;      /* edge cap of the edge tiles (GNN_EDGE_TILE unless re-tiled) */
+    int32_t reserved;
 } gnn_partition_info;
 
 #define GNN_EDGE_TILE 128
@@ -128,6 +130,14 @@ int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method,
                        const double* target_weights, gnn_partition** out);
 void gnn_partition_destroy(gnn_partition* p);
 int gnn_partition_get_info(const gnn_partition* p, gnn_partition_info* info);
+
+/* Rebuild the edge tiles of p (GNN_P_EDGE_TILES, GNN_P_TILE_META) with at
+ * most `tile_edges` edges and GNN_EDGE_TILE rows per tile; rows never straddle
+ * two tiles. Smaller tiles trade per-tile overhead for more parallel work on
+ * small graphs (a launch-shape choice: results do not depend on it).
+ * Device copies made earlier keep the old tiles; upload again afterwards.
+ * Errors: GNN_EINVAL unless max_in_degree <= tile_edges <= GNN_EDGE_TILE. */
+int gnn_partition_set_tile_edges(gnn_partition* p, int32_t tile_edges);
 
 /* Arrays of a partition, copied into a caller-owned host buffer of exactly
  * `bytes` bytes (GNN_ESHAPE otherwise). Row r of sub-graph s is global row
@@ -213,12 +223,23 @@ typedef struct gnn_mp_params {
 #define GNN_HALO_NONE 1   /* the paper's "None" mode: Eq. 5c-5d skipped (inconsistent)     */
 #define GNN_FLAG_NO_EDGE_OUT 1  /* forward: do not write e_out (last layer in inference)  */
 
+/* Launch choices of the fused BF16 edge forward. Every choice computes the
+ * same arithmetic in the same summation order; results agree to FP32
+ * rounding (instruction contraction may differ). 0 = library default. */
+#define GNN_EDGE_FWD_AUTO 0   /* RT for H <= 64, ONE for H = 128                                */
+#define GNN_EDGE_FWD_RT   1   /* record-tiled consumer groups, P|Q rows prefetched (H <= 64)   */
+#define GNN_EDGE_FWD_WS   2   /* producer warp + two consumer groups (H <= 64)                 */
+#define GNN_EDGE_FWD_ONE  3   /* one tile at a time per CTA, CTAs per SM by occupancy          */
+
 typedef struct gnn_mp_config {
     int32_t hidden;          /* H: 16, 32, 64 or 128 (BF16); 1..256 (FP32)                 */
     int32_t precision;       /* GNN_PREC_*                                                  */
     int32_t halo_mode;       /* GNN_HALO_*                                                  */
     int32_t flags;           /* GNN_FLAG_*                                                  */
     float ln_eps;            /* LayerNorm epsilon (the paper's PyTorch default 1e-5)       */
+    int32_t edge_fwd_kernel; /* GNN_EDGE_FWD_* (BF16 only; ignored for FP32)               */
+    int32_t ctas_per_sm;     /* cap on resident CTAs per SM of the BF16 edge forward;
+                                0 = as many as shared memory, registers and TMEM allow   */
 } gnn_mp_config;
 
 /* ====================================================== consistent NMP layer

@@ -21,6 +21,7 @@ GNN_PART_SLAB_Z, GNN_PART_RCB = 0, 1
 GNN_PREC_FP32, GNN_PREC_BF16 = 0, 1
 GNN_HALO_SYNC, GNN_HALO_NONE = 0, 1
 GNN_FLAG_NO_EDGE_OUT = 1
+GNN_EDGE_FWD_AUTO, GNN_EDGE_FWD_RT, GNN_EDGE_FWD_WS, GNN_EDGE_FWD_ONE = 0, 1, 2, 3
 GNN_MAX_LIN = 8
 GNN_EDGE_TILE = 128
 GNN_NODE_TILE = 128
@@ -52,7 +53,8 @@ class gnn_graph_info(C.Structure):
 class gnn_partition_info(C.Structure):
     _fields_ = [("n_parts", C.c_int32), ("max_in_degree", C.c_int32), ("n_rows", C.c_int64),
                 ("n_edges", C.c_int64), ("n_shared", C.c_int64), ("n_copies", C.c_int64),
-                ("n_edge_tiles", C.c_int64), ("n_node_tiles", C.c_int64)]
+                ("n_edge_tiles", C.c_int64), ("n_node_tiles", C.c_int64), ("tile_edges", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class gnn_graph_dev(C.Structure):
@@ -76,7 +78,8 @@ class gnn_mp_params(C.Structure):
 
 class gnn_mp_config(C.Structure):
     _fields_ = [("hidden", C.c_int32), ("precision", C.c_int32), ("halo_mode", C.c_int32),
-                ("flags", C.c_int32), ("ln_eps", C.c_float)]
+                ("flags", C.c_int32), ("ln_eps", C.c_float), ("edge_fwd_kernel", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -94,6 +97,7 @@ _SIGS = {
     "gnn_partition_destroy": (None, [_P]),
     "gnn_partition_get_info": (C.c_int, [_P, C.POINTER(gnn_partition_info)]),
     "gnn_partition_copy": (C.c_int, [_P, C.c_int32, _P, C.c_size_t]),
+    "gnn_partition_set_tile_edges": (C.c_int, [_P, C.c_int32]),
     "gnn_mp_workspace_size": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                         C.POINTER(gnn_mp_params), C.POINTER(C.c_size_t),
                                         C.POINTER(C.c_size_t)]),

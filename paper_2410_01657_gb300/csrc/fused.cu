@@ -127,6 +127,7 @@ struct EdgeFwdArgs {
     const int32_t* col;
     const float* edge_w;
     const int32_t* tiles;
+    const uint8_t* tile_meta;   // per-tile records (GNN_TILE_META_BYTES each)
     int64_t n_tiles;
     int64_t n_edges;
     const __nv_bfloat16* pq;
@@ -586,6 +587,311 @@ __global__ void __launch_bounds__(WsCfg<H>::NT, 1)
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// ------------------------------------------------------------------ k_edge_fwd_rt (record-tiled groups)
+//
+// Same arithmetic as k_edge_fwd, organised around the host-built per-tile
+// records (CSR slice, local receiver, sender and 1/d of every edge). NG
+// consumer groups take interleaved tiles of the CTA's share; a group's next
+// tile but one is requested (record by bulk copy, edge states by TMA) as soon
+// as its stage is free, so no thread builds metadata and the loads have two
+// tiles' time to land. After the first epilogue of a tile has consumed them,
+// every thread requests the P row of its edge's receiver and the Q row of its
+// sender (its own columns) for the group's next tile with cp.async into a
+// private slot: no global gather sits on the MMA chain and none occupies
+// registers. The segmented sum of Eq. 5b is staged through the activation
+// tile, which is free once the last MMA of the tile has completed.
+
+template <int H>
+struct RtCfg {
+    static constexpr int NG = H >= 64 ? 2 : 4;     // consumer groups
+    static constexpr int GT = Cfg<H>::NT;          // threads per group
+    static constexpr int NT = NG * GT;
+    static constexpr int SC = H / 2;               // columns per segmented-sum pass
+    static constexpr int SLOT = 4 * Cfg<H>::CW;    // bytes of a thread's P|Q slot
+    static constexpr int NCH = SLOT / 16;          // 16-byte chunks per slot
+    static constexpr int SWZ_SHIFT = NCH >= 8 ? 0 : (NCH == 4 ? 1 : 2);
+    static constexpr uint32_t NCOLS = NG * Cfg<H>::TCOLS < 32 ? 32 : NG * Cfg<H>::TCOLS;
+};
+
+struct EdgeFwdRtSmem {
+    uint32_t w, par, red, grp, gsz, bar, tm, total;
+};
+
+// Per group (gsz bytes at grp + g*gsz): e stages [2 x TILE], activation tile
+// (TILE), P|Q slots (2 x TILE), tile records [2 x GNN_TILE_META_BYTES].
+template <int H>
+__host__ __device__ inline EdgeFwdRtSmem edge_fwd_rt_smem(int n_lin) {
+    using C = Cfg<H>;
+    using R = RtCfg<H>;
+    EdgeFwdRtSmem s;
+    s.w = 0;
+    s.par = align_up(n_lin * C::WT, 16);
+    s.red = s.par + (n_lin + 2) * H * 4;
+    s.grp = align_up(s.red + R::NG * 2 * C::CG * 128 * 4, 1024);
+    s.gsz = 5 * C::TILE + 2 * GNN_TILE_META_BYTES;
+    s.bar = s.grp + R::NG * s.gsz;
+    s.tm = s.bar + 8 * 3 * R::NG;
+    s.total = s.tm + 16 + 1024;
+    return s;
+}
+
+// Physical 16-byte chunk of logical chunk k in the slot of `row` (rows of one
+// 8-thread shared-memory phase land in distinct banks).
+template <int H>
+__device__ __forceinline__ int slot_chunk(int k, int row) {
+    using R = RtCfg<H>;
+    return k ^ ((row >> R::SWZ_SHIFT) & (R::NCH - 1));
+}
+
+
+
+template <int H>
+__global__ void __launch_bounds__(RtCfg<H>::NT, 1)
+    k_edge_fwd_rt(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
+    using C = Cfg<H>;
+    using R = RtCfg<H>;
+    constexpr int GT = R::GT, SC = R::SC, CW = C::CW, CG = C::CG, NCH = R::NCH;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    const int n_lin = A.mlp.n_lin;
+    const EdgeFwdRtSmem L = edge_fwd_rt_smem<H>(n_lin);
+    uint8_t* sW = sm + L.w;
+    float* sPar = reinterpret_cast<float*>(sm + L.par);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid / GT, gt = tid % GT, wg = gt >> 5;
+    const int q = wg & 3, cg = wg >> 2, row = 32 * q + lane, c0 = cg * CW;
+    const int bid = 1 + g;
+    const bool elected = gt == 0;
+    uint8_t* G = sm + L.grp + g * L.gsz;
+    uint8_t* sA1 = G + 2 * C::TILE;
+    uint8_t* sSlot = G + 3 * C::TILE + (cg * 128 + row) * R::SLOT;
+    uint8_t* sRec = G + 5 * C::TILE;
+    float* sRed = reinterpret_cast<float*>(sm + L.red) + g * 2 * CG * 128;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar) + 3 * g;
+    uint64_t* mbar = full + 2;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, R::NCOLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        uint64_t* b = reinterpret_cast<uint64_t*>(sm + L.bar);
+        for (int i = 0; i < 3 * R::NG; ++i) mbar_init(b + i, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, R::NT);
+    for (int k = 1; k < n_lin; ++k) load_weight(sW + k * C::WT, A.mlp.W[k], H, 0, H, H, tid, R::NT);
+    for (int i = tid; i < n_lin * H; i += R::NT) sPar[i] = A.mlp.b[i / H][i % H];
+    for (int i = tid; i < H; i += R::NT) {
+        sPar[n_lin * H + i] = A.mlp.gamma[i];
+        sPar[(n_lin + 1) * H + i] = A.mlp.beta[i];
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = *tslot + (uint32_t)g * C::TCOLS;
+
+    // the group's tiles: blockIdx.x + (u*NG + g)*gridDim.x, u = 0, 1, ...; tile u uses stage u & 1
+    const int64_t stride = (int64_t)R::NG * gridDim.x;
+    const int64_t t_first = blockIdx.x + (int64_t)g * gridDim.x;
+    auto issue = [&](int s, int64_t t, int32_t e0) {   // elected thread: record + edge states of tile t
+        mbar_arrive_expect_tx(full + s, C::TILE + GNN_TILE_META_BYTES);
+        bulk_load(sRec + s * GNN_TILE_META_BYTES, A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES,
+                  full + s);
+#pragma unroll
+        for (int kb = 0; kb < (H + 63) / 64; ++kb) tma_load_2d(G + s * C::TILE + kb * 128 * 128, &tmap_e, kb * 64, e0,
+                                                               full + s);
+    };
+    // this thread's P|Q slot <- tile whose record is in stage s
+    auto gather = [&](int s) {
+        const uint8_t* rec = sRec + s * GNN_TILE_META_BYTES;
+        const int32_t ne = reinterpret_cast<const int32_t*>(rec)[3];
+        if (row < ne) {
+            const int64_t rcv = reinterpret_cast<const int32_t*>(rec)[0] + reinterpret_cast<const int16_t*>(rec + 544)[row];
+            const int64_t snd = reinterpret_cast<const int32_t*>(rec + 800)[row];
+            const __nv_bfloat16* P = A.pq + rcv * 2 * H + c0;
+            const __nv_bfloat16* Q = A.pq + snd * 2 * H + H + c0;
+#pragma unroll
+            for (int k = 0; k < NCH / 2; ++k) {
+                cp_async16(sSlot + 16 * slot_chunk<H>(k, row), P + 8 * k);
+                cp_async16(sSlot + 16 * slot_chunk<H>(k + NCH / 2, row), Q + 8 * k);
+            }
+        }
+        cp_async_commit();
+    };
+    bool ok = true;
+    uint32_t pending = 0;   // elected thread: bit s = a load into stage s not yet consumed, bit 2+s = its parity
+    if (elected) {
+        for (int u = 0; u < 2; ++u) {
+            const int64_t t = t_first + u * stride;
+            if (t < A.n_tiles) {
+                issue(u, t, ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8));
+                pending |= 1u << u;
+            }
+        }
+    }
+    if (t_first < A.n_tiles) {
+        ok = mbar_wait(full, 0);
+        if (ok) gather(0);
+    }
+
+    uint32_t ph_mma = 0;
+    int u = 0;
+    for (int64_t t = t_first; t < A.n_tiles && ok; t += stride, ++u) {
+        const int s = u & 1;
+        const int64_t t_next = t + stride, t_refill = t + 2 * stride;
+        const int32_t e0_refill =
+            (elected && t_refill < A.n_tiles) ? ld_nc_s32(A.tile_meta + t_refill * GNN_TILE_META_BYTES + 8) : 0;
+        ok = group_wait(full + s, (uint32_t)(u >> 1) & 1u, elected, bid, GT);
+        if (!ok) break;
+        pending &= ~(5u << s);
+        uint8_t* sE = G + s * C::TILE;
+        const uint8_t* rec = sRec + s * GNN_TILE_META_BYTES;
+        if (elected) {
+            tc_fence_after();
+            issue_mma(tm, sE, sW, H, H);
+            mma_commit(mbar);
+        }
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
+        const int32_t r0 = hdr[0], nr = hdr[1] - hdr[0], ne = hdr[3];
+        const int64_t e0 = hdr[2];
+        const bool valid = row < ne;
+        const float w = valid ? reinterpret_cast<const float*>(rec + 1312)[row] : 0.f;
+        cp_async_wait_all();
+        float v[CW];
+        for (int k = 0; k < n_lin && ok; ++k) {
+            ok = group_wait(mbar, ph_mma, elected, bid, GT);
+            ph_mma ^= 1;
+            tc_fence_after();
+            if (!ok) break;
+            ld_acc<CW>(tm, q, c0, v);
+            const float* bk = sPar + k * H + c0;
+            if (k == 0) {
+                if (valid) {
+#pragma unroll
+                    for (int kc = 0; kc < NCH / 2; ++kc) {
+                        float pv[8], qv[8];
+                        const uint4 up = *reinterpret_cast<const uint4*>(sSlot + 16 * slot_chunk<H>(kc, row));
+                        const uint4 uq = *reinterpret_cast<const uint4*>(sSlot + 16 * slot_chunk<H>(kc + NCH / 2, row));
+                        unpack_bf16x2(up.x, pv[0], pv[1]);
+                        unpack_bf16x2(up.y, pv[2], pv[3]);
+                        unpack_bf16x2(up.z, pv[4], pv[5]);
+                        unpack_bf16x2(up.w, pv[6], pv[7]);
+                        unpack_bf16x2(uq.x, qv[0], qv[1]);
+                        unpack_bf16x2(uq.y, qv[2], qv[3]);
+                        unpack_bf16x2(uq.z, qv[4], qv[5]);
+                        unpack_bf16x2(uq.w, qv[6], qv[7]);
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) v[8 * kc + jj] += (pv[jj] + qv[jj]) + bk[8 * kc + jj];
+                    }
+                }
+                // the slot is consumed: request the group's next tile (its record landed a tile ago)
+                if (t_next < A.n_tiles) {
+                    if (mbar_wait(full + (s ^ 1), (uint32_t)((u + 1) >> 1) & 1u)) gather(s ^ 1);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] += bk[i];
+            }
+            if (k < n_lin - 1) {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
+                st_row_tile<CW>(sA1, row, c0, C::S, v);
+                fence_proxy_async();
+                tc_fence_before();
+                named_sync(bid, GT);
+                if (elected) {
+                    tc_fence_after();
+                    issue_mma(tm, sA1, sW + (k + 1) * C::WT, H, H);
+                    mma_commit(mbar);
+                }
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        float mean, rstd;
+        if constexpr (CG == 1) {
+            float su = 0.f, sq = 0.f;
+#pragma unroll
+            for (int i = 0; i < CW; ++i) {
+                su += v[i];
+                sq += v[i] * v[i];
+            }
+            mean = su * (1.f / H);
+            rstd = rsqrtf(fmaxf(sq * (1.f / H) - mean * mean, 0.f) + A.eps);
+        } else {
+            row_stats_named<H, CG, CW>(v, sRed, row, cg, A.eps, bid, GT, mean, rstd);
+        }
+        {
+            float eo[CW];
+            ld_row_tile<CW>(sE, row, c0, C::S, eo);
+            const float* gam = sPar + n_lin * H + c0;
+            const float* bet = sPar + (n_lin + 1) * H + c0;
+#pragma unroll
+            for (int i = 0; i < CW; ++i) v[i] = eo[i] + (v[i] - mean) * rstd * gam[i] + bet[i];
+        }
+        if (valid && A.e_out) {
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) st_bf16x8(A.e_out + (e0 + row) * H + c0 + i, v + i);
+        }
+        // Eq. 5b: a_r = sum over the row's edges of w * e' (edge order), in two passes of SC
+        // columns staged in sA1 as 16-byte chunks; one thread per (row, chunk) sums a segment
+        float4* sS = reinterpret_cast<float4*>(sA1);
+        const int32_t* sRp = reinterpret_cast<const int32_t*>(rec + 16);
+        constexpr int NC = SC / 4;
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            if constexpr (CG == 2) {
+                if (cg == pass) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        sS[row * NC + stage_chunk<NC>(c, row)] =
+                            make_float4(w * v[4 * c], w * v[4 * c + 1], w * v[4 * c + 2], w * v[4 * c + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float* vp = v + pass * SC + 4 * c;
+                    sS[row * NC + stage_chunk<NC>(c, row)] = make_float4(w * vp[0], w * vp[1], w * vp[2], w * vp[3]);
+                }
+            }
+            named_sync(bid, GT);
+            for (int it = gt; it < nr * NC; it += GT) {
+                const int rr = it / NC, c = it % NC;
+                const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int32_t e = b0; e < b1; ++e) {
+                    const float4 u4 = sS[e * NC + stage_chunk<NC>(c, e)];
+                    acc.x += u4.x;
+                    acc.y += u4.y;
+                    acc.z += u4.z;
+                    acc.w += u4.w;
+                }
+                *reinterpret_cast<float4*>(A.a + (int64_t)(r0 + rr) * H + pass * SC + 4 * c) = acc;
+            }
+            if (pass == 1) fence_proxy_async();   // generic reads of the stage precede its next async write
+            named_sync(bid, GT);
+        }
+        if (elected && t_refill < A.n_tiles) {
+            issue(s, t_refill, e0_refill);
+            pending |= (1u << s) | ((((uint32_t)(u + 2) >> 1) & 1u) << (2 + s));
+        }
+    }
+    // after an error, let this group's loads in flight land before the CTA exits
+    if (elected) {
+        for (int s = 0; s < 2; ++s)
+            if (pending & (1u << s)) mbar_wait(full + s, (pending >> (2 + s)) & 1u);
+    }
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(*tslot, R::NCOLS);
+}
+
 // ------------------------------------------------------------------ k_node_fwd
 
 struct NodeFwdArgs {
@@ -809,6 +1115,7 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.col = G.col;
         A.edge_w = G.edge_w;
         A.tiles = G.edge_tiles;
+        A.tile_meta = static_cast<const uint8_t*>(G.tile_meta);
         A.n_tiles = G.n_edge_tiles;
         A.n_edges = E;
         A.pq = pq;
@@ -817,16 +1124,32 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
         int grid;
+        int variant = cfg.edge_fwd_kernel;
+        if (variant == GNN_EDGE_FWD_AUTO) variant = H <= 64 ? GNN_EDGE_FWD_RT : GNN_EDGE_FWD_ONE;
         if constexpr (H <= 64) {
-            const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(W.edge.n_lin);
-            const uint32_t ncols = C::TCOLS * WS_NG < 32 ? 32 : C::TCOLS * WS_NG;
-            rc = persistent_grid(k_edge_fwd_ws<H>, WsCfg<H>::NT, L.total, ncols, G.n_edge_tiles, &grid);
-            if (rc) return rc;
-            ProfScope _ps(s, "k_edge_fwd");
-            k_edge_fwd_ws<H><<<grid, WsCfg<H>::NT, L.total, s>>>(tm, A);
-        } else {
+            if (variant == GNN_EDGE_FWD_RT) {
+                using R = RtCfg<H>;
+                GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
+                            "gnn_mp_forward: tile_meta must be a 16-byte aligned device array");
+                const EdgeFwdRtSmem L = edge_fwd_rt_smem<H>(W.edge.n_lin);
+                rc = persistent_grid(k_edge_fwd_rt<H>, R::NT, L.total, R::NCOLS, (G.n_edge_tiles + R::NG - 1) / R::NG,
+                                     &grid, cfg.ctas_per_sm);
+                if (rc) return rc;
+                ProfScope _ps(s, "k_edge_fwd");
+                k_edge_fwd_rt<H><<<grid, R::NT, L.total, s>>>(tm, A);
+            } else if (variant == GNN_EDGE_FWD_WS) {
+                const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(W.edge.n_lin);
+                const uint32_t ncols = C::TCOLS * WS_NG < 32 ? 32 : C::TCOLS * WS_NG;
+                rc = persistent_grid(k_edge_fwd_ws<H>, WsCfg<H>::NT, L.total, ncols, G.n_edge_tiles, &grid,
+                                     cfg.ctas_per_sm);
+                if (rc) return rc;
+                ProfScope _ps(s, "k_edge_fwd");
+                k_edge_fwd_ws<H><<<grid, WsCfg<H>::NT, L.total, s>>>(tm, A);
+            }
+        }
+        if (variant == GNN_EDGE_FWD_ONE) {
             const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin);
-            rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid);
+            rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid, cfg.ctas_per_sm);
             if (rc) return rc;
             ProfScope _ps(s, "k_edge_fwd");
             k_edge_fwd<H><<<grid, C::NT, L.total, s>>>(tm, A);

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                 ld_acc<CW>(tWork, q, c0, dh);
                 ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
 #pragma unroll
-                for (int i = 0; i < CW; ++i) dz[i] = dh[i] * elu1_deriv_from_out(hv[i]);
+                for (int i = 0; i < CW; ++i) dz[i] = elu1_bwd_from_out(dh[i], hv[i]);
             } else {
                 float da[CW], dxp[CW];
                 ld_acc<CW>(tWork, q, c0, da);
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.bar);   // full[2]: stage loaded
     uint64_t* bar = full + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
-    constexpr int S = C::S, CW = C::CW, SLD = H + 4;
+    constexpr int S = C::S, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -669,16 +669,26 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
                     for (int i = 0; i < CW; i += 8) st_bf16x8(A.dz1 + eg * H + c0 + i, dz + i);
                 }
+                constexpr int NC = H / 4;
+                float4* sS4 = reinterpret_cast<float4*>(sStage);
 #pragma unroll
-                for (int i = 0; i < CW; ++i) sStage[row * SLD + c0 + i] = dz[i];
+                for (int i = 0; i < CW / 4; ++i)
+                    sS4[row * NC + stage_chunk<NC>(c0 / 4 + i, row)] =
+                        make_float4(dz[4 * i], dz[4 * i + 1], dz[4 * i + 2], dz[4 * i + 3]);
                 __syncthreads();
                 const int nr = r1 - r0;
-                for (int it = tid; it < nr * H; it += C::NT) {
-                    const int rr = it / H, cc = it % H;
+                for (int it = tid; it < nr * NC; it += C::NT) {
+                    const int rr = it / NC, c = it % NC;
                     const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];
-                    float s = 0.f;
-                    for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
-                    A.dP[(int64_t)(r0 + rr) * H + cc] = s;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int32_t e = b0; e < b1; ++e) {
+                        const float4 u4 = sS4[e * NC + stage_chunk<NC>(c, e)];
+                        acc.x += u4.x;
+                        acc.y += u4.y;
+                        acc.z += u4.z;
+                        acc.w += u4.w;
+                    }
+                    *reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + 4 * c) = acc;
                 }
             }
             ok = block_wait(bar, ph, tid);
@@ -691,7 +701,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 float hv[CW];
                 ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
 #pragma unroll
-                for (int i = 0; i < CW; ++i) dz[i] = dh[i] * elu1_deriv_from_out(hv[i]);
+                for (int i = 0; i < CW; ++i) dz[i] = elu1_bwd_from_out(dh[i], hv[i]);
             } else if (valid) {
                 float o[CW];
 #pragma unroll

@@ -46,9 +46,23 @@ __device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, int t
     return __syncthreads_and(mine) != 0;
 }
 
-// ELU (alpha 1) with e^z - 1 from the fast exponential: the result is rounded
-// to BF16 next, far coarser than the absolute error of __expf(z) - 1.
-__device__ __forceinline__ float elu1_fast(float z) { return z > 0.f ? z : __expf(z) - 1.f; }
+// 2^x on the special-function unit (approximate, denormals flushed).
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ELU (alpha 1): z for z > 0, e^z - 1 otherwise, with e^z = 2^(z log2 e).
+// Evaluating the exponential at min(z, 0) keeps it in (0, 1], and since
+// e^z - 1 >= z everywhere one max selects the branch. The result is rounded
+// to BF16 next, far coarser than the absolute error of the SFU exponential.
+__device__ __forceinline__ float elu1_fast(float z) {
+    return fmaxf(z, ex2_sfu(fminf(z, 0.f) * 1.4426950408889634f) - 1.f);
+}
+
+// dL/dz of h = ELU(z) from the output: dh for h > 0, dh (h + 1) = dh e^z otherwise.
+__device__ __forceinline__ float elu1_bwd_from_out(float dh, float h) { return fmaf(dh, fminf(h, 0.f), dh); }
 
 // Convert W[n][c_off + k] (FP32, row stride ld, n < N, k < K) into rows
 // row_off.. of a K-major BF16 row tile with rows_total rows.
@@ -94,6 +108,15 @@ __device__ __forceinline__ void ld_acc(uint32_t tmem, int q, int c0, float* v) {
 #pragma unroll
     for (int i = 0; i < CW / 16; ++i) tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * i), v + 16 * i);
     tmem_ld_wait();
+}
+
+// Physical 16-byte chunk of staging chunk c of edge row e (NC chunks of four
+// FP32 per row): the rows of one 8-thread shared-memory phase hit distinct banks.
+template <int NC>
+__device__ __forceinline__ int stage_chunk(int c, int e) {
+    constexpr int SH = NC >= 8 ? 0 : (NC == 4 ? 1 : 2);
+    constexpr int M = (NC >= 8 ? 8 : NC) - 1;
+    return c ^ ((e >> SH) & M);
 }
 
 template <int CW>
@@ -275,7 +298,8 @@ inline int num_sms() {
 // Persistent grid: resident CTAs (by shared memory / registers and by TMEM
 // columns) times SMs, capped by the number of tiles.
 template <class K>
-int persistent_grid(K kernel, int threads, uint32_t smem, uint32_t tmem_cols, int64_t tiles, int* out) {
+int persistent_grid(K kernel, int threads, uint32_t smem, uint32_t tmem_cols, int64_t tiles, int* out,
+                    int max_per_sm = 0) {
     GNN_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                    "cudaFuncSetAttribute");
     GNN_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -286,6 +310,7 @@ int persistent_grid(K kernel, int threads, uint32_t smem, uint32_t tmem_cols, in
                    "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     GNN_REQUIRE(per_sm >= 1, GNN_EUNSUPPORTED, "fused kernel does not fit on an SM (smem %u)", smem);
     per_sm = std::min<int>(per_sm, (int)(512 / tmem_cols));
+    if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
     *out = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)per_sm * num_sms()));
     return GNN_OK;
 }

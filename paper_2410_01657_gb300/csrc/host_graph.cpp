@@ -100,6 +100,7 @@ struct gnn_graph {
 struct gnn_partition {
     int32_t R;
     int32_t max_in_degree;
+    int32_t tile_edges;     // edge cap of the current tiles
     std::vector<int64_t> row_offsets, edge_offsets;
     std::vector<int64_t> row_gid;
     std::vector<int32_t> row_ptr, col;
@@ -369,6 +370,46 @@ int gnn_graph_copy_elements(const gnn_graph* g, int64_t* en) {
     return GNN_OK;
 }
 
+// Receiver-aligned edge tiles: consecutive rows, at most `cap` edges and at
+// most GNN_EDGE_TILE rows per tile (a row's edges never straddle two tiles),
+// and one fixed-size record per tile (layout in gnnmp.h, GNN_P_TILE_META).
+static void build_edge_tiles(gnn_partition* P, int32_t cap) {
+    const int64_t NR = (int64_t)P->row_ptr.size() - 1;
+    P->tile_edges = cap;
+    P->edge_tiles.clear();
+    P->edge_tiles.push_back(0);
+    int64_t r0 = 0;
+    while (r0 < NR) {
+        int64_t r1 = r0;
+        while (r1 < NR && r1 - r0 < GNN_EDGE_TILE && P->row_ptr[r1 + 1] - P->row_ptr[r0] <= cap) ++r1;
+        P->edge_tiles.push_back((int32_t)r1);
+        r0 = r1;
+    }
+    const int64_t nt = (int64_t)P->edge_tiles.size() - 1;
+    P->tile_meta.assign((size_t)nt * GNN_TILE_META_BYTES, 0);
+    parallel_for(nt, [&](int64_t t) {
+        uint8_t* rec = P->tile_meta.data() + (size_t)t * GNN_TILE_META_BYTES;
+        int32_t* hdr = reinterpret_cast<int32_t*>(rec);
+        int32_t* rp = reinterpret_cast<int32_t*>(rec + 16);
+        int16_t* seg = reinterpret_cast<int16_t*>(rec + 544);
+        int32_t* cl = reinterpret_cast<int32_t*>(rec + 800);
+        float* w = reinterpret_cast<float*>(rec + 1312);
+        const int32_t r0 = P->edge_tiles[t], r1 = P->edge_tiles[t + 1];
+        const int32_t e0 = P->row_ptr[r0], ne = P->row_ptr[r1] - e0;
+        hdr[0] = r0;
+        hdr[1] = r1;
+        hdr[2] = e0;
+        hdr[3] = ne;
+        for (int32_t i = 0; i <= r1 - r0; ++i) rp[i] = P->row_ptr[r0 + i] - e0;
+        for (int32_t i = 0; i < r1 - r0; ++i)
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) seg[e] = (int16_t)i;
+        for (int32_t e = 0; e < ne; ++e) {
+            cl[e] = P->col[e0 + e];
+            w[e] = 1.0f / (float)P->edge_deg[e0 + e];
+        }
+    });
+}
+
 int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method, const double* target_weights,
                        gnn_partition** out) {
     GNN_REQUIRE(g && out, GNN_EINVAL, "gnn_partition_halo: NULL argument");
@@ -595,46 +636,10 @@ int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method, const doub
                 (int64_t)(std::unique(neigh[r].begin(), neigh[r].end()) - neigh[r].begin());
         }
 
-        // ---- receiver-aligned edge tiles of <= GNN_EDGE_TILE edges
+        // ---- receiver-aligned edge tiles of <= GNN_EDGE_TILE edges, one record each
         GNN_REQUIRE(maxdeg <= GNN_EDGE_TILE, GNN_EUNSUPPORTED,
                     "gnn_partition_halo: in-degree %d exceeds the edge tile (%d)", maxdeg, GNN_EDGE_TILE);
-        P->edge_tiles.clear();
-        P->edge_tiles.push_back(0);
-        {
-            int64_t r0 = 0;
-            while (r0 < NR) {
-                int64_t r1 = r0;
-                while (r1 < NR && P->row_ptr[r1 + 1] - P->row_ptr[r0] <= GNN_EDGE_TILE) ++r1;
-                P->edge_tiles.push_back((int32_t)r1);
-                r0 = r1;
-            }
-        }
-        // ---- one fixed-size record per edge tile (layout in gnnmp.h, GNN_P_TILE_META)
-        {
-            const int64_t nt = (int64_t)P->edge_tiles.size() - 1;
-            P->tile_meta.assign((size_t)nt * GNN_TILE_META_BYTES, 0);
-            parallel_for(nt, [&](int64_t t) {
-                uint8_t* rec = P->tile_meta.data() + (size_t)t * GNN_TILE_META_BYTES;
-                int32_t* hdr = reinterpret_cast<int32_t*>(rec);
-                int32_t* rp = reinterpret_cast<int32_t*>(rec + 16);
-                int16_t* seg = reinterpret_cast<int16_t*>(rec + 544);
-                int32_t* cl = reinterpret_cast<int32_t*>(rec + 800);
-                float* w = reinterpret_cast<float*>(rec + 1312);
-                const int32_t r0 = P->edge_tiles[t], r1 = P->edge_tiles[t + 1];
-                const int32_t e0 = P->row_ptr[r0], ne = P->row_ptr[r1] - e0;
-                hdr[0] = r0;
-                hdr[1] = r1;
-                hdr[2] = e0;
-                hdr[3] = ne;
-                for (int32_t i = 0; i <= r1 - r0; ++i) rp[i] = P->row_ptr[r0 + i] - e0;
-                for (int32_t i = 0; i < r1 - r0; ++i)
-                    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) seg[e] = (int16_t)i;
-                for (int32_t e = 0; e < ne; ++e) {
-                    cl[e] = P->col[e0 + e];
-                    w[e] = 1.0f / (float)P->edge_deg[e0 + e];
-                }
-            });
-        }
+        build_edge_tiles(P, GNN_EDGE_TILE);
         // ---- positions per row
         P->row_pos.resize(NR * 3);
         for (int64_t i = 0; i < NR; ++i)
@@ -660,6 +665,21 @@ int gnn_partition_get_info(const gnn_partition* P, gnn_partition_info* info) {
     info->n_copies = (int64_t)P->halo_rows.size();
     info->n_edge_tiles = (int64_t)P->edge_tiles.size() - 1;
     info->n_node_tiles = (info->n_rows + GNN_NODE_TILE - 1) / GNN_NODE_TILE;
+    info->tile_edges = P->tile_edges;
+    info->reserved = 0;
+    return GNN_OK;
+}
+
+int gnn_partition_set_tile_edges(gnn_partition* P, int32_t tile_edges) {
+    GNN_REQUIRE(P, GNN_EINVAL, "gnn_partition_set_tile_edges: NULL partition");
+    GNN_REQUIRE(tile_edges >= std::max(P->max_in_degree, 1) && tile_edges <= GNN_EDGE_TILE, GNN_EINVAL,
+                "gnn_partition_set_tile_edges: tile_edges %d outside [%d, %d]", tile_edges,
+                std::max(P->max_in_degree, 1), GNN_EDGE_TILE);
+    try {
+        build_edge_tiles(P, tile_edges);
+    } catch (const std::bad_alloc&) {
+        return set_error(GNN_ENOMEM, "gnn_partition_set_tile_edges: out of host memory");
+    }
     return GNN_OK;
 }
 

@@ -116,6 +116,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Per-thread asynchronous 16-byte global -> shared copy (both addresses
+// 16-byte aligned); completion is tracked per thread by commit/wait groups,
+// and only the issuing thread may read the bytes after its wait.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Non-coherent 32-bit global load (read-only data).
+__device__ __forceinline__ int32_t ld_nc_s32(const void* p) { return __ldg(reinterpret_cast<const int32_t*>(p)); }
+
 // ------------------------------------------------------------------ tcgen05
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {

@@ -142,6 +142,19 @@ class Partition:
             self._cache[name] = out
         return self._cache[name]
 
+    @property
+    def tile_edges(self) -> int:
+        return int(self.info.tile_edges)
+
+    def set_tile_edges(self, tile_edges: int) -> "Partition":
+        """Rebuild the edge tiles with at most `tile_edges` edges each (device
+        copies made before keep the old tiles)."""
+        B.call("gnn_partition_set_tile_edges", self._h, int(tile_edges))
+        B.call("gnn_partition_get_info", self._h, C.byref(self.info))
+        self._cache.pop("edge_tiles", None)
+        self._cache.pop("tile_meta", None)
+        return self
+
     def receivers(self) -> np.ndarray:
         rp = self.array("row_ptr").astype(np.int64)
         return np.repeat(np.arange(self.n_rows, dtype=np.int64), np.diff(rp))

@@ -55,12 +55,14 @@ def _layer_case(nel, p, R, H, n_hidden, seed=0, method="rcb"):
     return brick, subs, part, G, params, x, e
 
 
-def _run_fused_layer(G, params, H, x, e, precision="bf16"):
+def _run_fused_layer(G, params, H, x, e, precision="bf16", variant=0, ctas_per_sm=0):
     net = gnn.ConsistentGNN(params, precision=precision, device=DEV)
     layer = net.layers[0]
     edt = torch.bfloat16 if precision == "bf16" else torch.float32
     xt, et = _to(x), _to(e, edt)
     cfg = gnn.mp_config(H, precision)
+    cfg.edge_fwd_kernel = variant
+    cfg.ctas_per_sm = ctas_per_sm
     W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
     xo = torch.empty_like(xt)
     eo = torch.empty_like(et)
@@ -84,6 +86,35 @@ def test_fused_layer_forward_vs_oracle(H, n_hidden, R):
     order = np.argsort(gid, kind="stable")
     same = gid[order][1:] == gid[order][:-1]
     assert np.array_equal(xo[order][1:][same], xo[order][:-1][same])
+
+
+@pytest.mark.parametrize("H", [16, 32, 64])
+def test_edge_forward_kernel_choices_agree(H):
+    # every launch choice of the edge forward on a ragged multi-tile graph: oracle parity, and the
+    # choices agree with each other to FP32 rounding
+    brick, subs, part, G, params, x, e = _layer_case((6, 5, 4), 3, 5, H, 2, seed=21)
+    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    outs = {}
+    for variant, cps in ((B.GNN_EDGE_FWD_RT, 0), (B.GNN_EDGE_FWD_WS, 0), (B.GNN_EDGE_FWD_ONE, 0),
+                         (B.GNN_EDGE_FWD_ONE, 1)):
+        xo, eo, a = _run_fused_layer(G, params, H, x, e, variant=variant, ctas_per_sm=cps)
+        assert rel_l2(a, np.concatenate(cache["a_star"])) < TOL_OUT
+        assert rel_l2(eo, np.concatenate(e1)) < TOL_OUT
+        assert rel_l2(xo, np.concatenate(x1)) < TOL_OUT
+        outs[(variant, cps)] = (xo, eo, a)
+    ref = outs[(B.GNN_EDGE_FWD_RT, 0)]
+    for k, o in outs.items():
+        for u, v in zip(o, ref):
+            assert rel_l2(u, v) < 1e-5, k
+
+
+def test_edge_forward_kernel_choice_validation():
+    brick, subs, part, G, params, x, e = _layer_case((2, 2, 2), 2, 1, 128, 2)
+    with pytest.raises(B.GnnError) as ei:
+        _run_fused_layer(G, params, 128, x, e, variant=B.GNN_EDGE_FWD_RT)
+    assert ei.value.code == B.GNN_EUNSUPPORTED
+    with pytest.raises(B.GnnError):
+        _run_fused_layer(G, params, 128, x, e, variant=7)
 
 
 def test_fused_forward_tiles_span_many_ctas():

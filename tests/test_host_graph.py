@@ -157,3 +157,35 @@ def test_tile_records_match_partition_arrays():
         assert np.array_equal(seg, np.repeat(np.arange(r1 - r0), np.diff(rp[r0:r1 + 1])))
         assert np.array_equal(rec[t, 800:800 + 4 * ne].view(np.int32), col[e0:e0 + ne])
         assert np.array_equal(rec[t, 1312:1312 + 4 * ne].view(np.float32), w[e0:e0 + ne])
+
+
+@pytest.mark.parametrize("cap", [7, 40, 128])
+def test_retile_caps_edges_and_keeps_records(cap):
+    part = MeshGraph((4, 3, 5), 2).partition(5, "rcb", [1, 3, 2, 7, 1])
+    assert part.tile_edges == B.GNN_EDGE_TILE
+    n0 = part.info.n_edge_tiles
+    part.set_tile_edges(cap)
+    assert part.tile_edges == cap
+    tiles = part.array("edge_tiles").astype(np.int64)
+    rp = part.array("row_ptr").astype(np.int64)
+    assert tiles[0] == 0 and tiles[-1] == part.n_rows and np.all(np.diff(tiles) > 0)
+    assert np.all(rp[tiles[1:]] - rp[tiles[:-1]] <= cap)
+    # greedy: adding the next row to any tile would exceed the cap
+    nxt = tiles[1:-1]
+    assert np.all(rp[nxt + 1] - rp[tiles[:-2]] > cap)
+    if cap < B.GNN_EDGE_TILE:
+        assert part.info.n_edge_tiles > n0
+    rec = part.array("tile_meta").reshape(-1, B.GNN_TILE_META_BYTES)
+    assert rec.shape[0] == len(tiles) - 1
+    for t in range(rec.shape[0]):
+        hdr = rec[t, :16].view(np.int32)
+        assert hdr.tolist() == [tiles[t], tiles[t + 1], rp[tiles[t]], rp[tiles[t + 1]] - rp[tiles[t]]]
+
+
+def test_retile_rejects_caps_below_degree():
+    part = MeshGraph((3, 3, 3), 2).partition(2, "slab")
+    with pytest.raises(B.GnnError) as ei:
+        part.set_tile_edges(part.info.max_in_degree - 1)
+    assert ei.value.code == B.GNN_EINVAL
+    with pytest.raises(B.GnnError):
+        part.set_tile_edges(B.GNN_EDGE_TILE + 1)

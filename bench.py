@@ -18,6 +18,11 @@ roofline  -- the dominant kernel's algorithmic bytes (or FLOPs) per launch over
              its CUDA-event launch time, against MEASURED_PEAKS.json.
 cpu_baseline -- the FP64 numpy oracle on a bounded sample, host cores.
 
+``--workload`` selects the other graph families (c3: 32^3 p=7 H=128 forward;
+c4: 64 uneven sub-graphs of a jittered p=5 brick, H=64 fwd+bwd, autotuned and
+replayed as a CUDA graph; c5: 48^3 p=7 H=32 inference); their layer inputs
+are seeded random states drawn on the device, and they report no fp32/e2e leg.
+
 ``--impl reference`` times the oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -37,6 +42,23 @@ sys.path.insert(0, ROOT)
 P, R, H, NH, M = 5, 8, 64, 2, 4
 SEED = 0
 
+# Workload families (sizes of the paper's brick graphs). "c2" is the benchmark
+# workload of the JSON line; the others are measured with --workload.
+#   inputs "encoders": x0, e0 from the node/edge encoders on the Fourier field
+#   inputs "random":   seeded N(0,1) layer states drawn on the device (the
+#                      encoders' FP32 workspace would not fit beside them)
+WORKLOADS = {
+    "c2": dict(nel=16, p=5, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False,
+               desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs"),
+    "c3": dict(nel=32, p=7, parts=8, H=128, mode="fwd", inputs="random", graph=False,
+               desc="32^3 elements p=7 GLL brick, 8 RCB sub-graphs, forward (inference) only"),
+    "c4": dict(nel=None, p=5, parts=64, H=64, mode="fwdbwd", inputs="random", graph=True, uneven=True,
+               desc="jittered p=5 brick in 64 RCB sub-graphs of log-uniform element counts in [50, 5000], "
+                    "CUDA graph, autotuned tiles"),
+    "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=False,
+               desc="48^3 elements p=7 GLL brick, 16 RCB sub-graphs, inference: last layer writes no edge state"),
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -47,8 +69,13 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwd: forward only (inference form of the layer stack)")
-    ap.add_argument("--nel", type=int, default=16,
-                    help="elements per axis of the brick (16 = the benchmark workload; smaller for profiling)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd; c4: 64 uneven jittered "
+                         "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference")
+    ap.add_argument("--nel", type=int, default=None,
+                    help="elements per axis of the brick (default: the workload's; smaller for profiling)")
+    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step")
+    ap.add_argument("--autotune", action="store_true", help="autotune tiles and the edge forward first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
@@ -104,15 +131,18 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 
-def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int) -> float | None:
-    """Least HBM bytes one launch of a fused kernel must move (one layer).
+def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False):
+    """Least HBM bytes one launch of a fused kernel must move (one layer; for
+    the edge forward of an inference stack, the mean over its M launches, the
+    last of which writes no edge state).
 
     Per edge: read e (s_e H), write e' (s_e H), col (4), 1/d (4); per row:
     the row's CSR pointer and node tensors (see the per-kernel notes)."""
     E, N = G.n_edges, G.n_rows
     se = edge_bytes
     if kernel == "k_edge_fwd":      # e in/out, col, w, P/Q gathers (bf16 2H per row), a out (fp32 H)
-        return E * (2 * se * hidden + 8) + N * (2 * 2 * hidden + 4 * hidden + 4)
+        writes = (M - 1) / M if last_layer_no_edge_out else 1.0
+        return E * ((1 + writes) * se * hidden + 8) + N * (2 * 2 * hidden + 4 * hidden + 4)
     if kernel == "k_edge_bwd":      # e in, de_out in, de_in out, dz1 out, col, w; da in, P/Q, dP out per row
         return E * (4 * se * hidden + 8) + N * (4 * hidden + 2 * 2 * hidden + 4 * hidden + 4)
     return None
@@ -241,40 +271,68 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
-def build_problem(dev, precision, nel=16):
+def workload_graph(wl: dict, nel):
+    """(Partition, unpartitioned nodes, unpartitioned directed edges) of a workload."""
     import numpy as np
+
+    import synthetic as syn
+    from paper_2410_01657_gb300.graph import MeshGraph
+
+    p = wl["p"]
+    if wl.get("uneven"):
+        n, weights = syn.uneven_brick(wl["parts"], 50, 5000, SEED)
+        if nel:
+            n, weights = nel, syn.rescale_counts(weights, nel ** 3)
+        g0 = MeshGraph((n,) * 3, p)
+        jit = syn.jitter_unit(g0.n_nodes, SEED + 1)
+        g = MeshGraph((n,) * 3, p, jitter=jit, jitter_frac=0.2)
+        part = g.partition(wl["parts"], "rcb", np.asarray(weights, dtype=np.float64))
+    else:
+        n = nel or wl["nel"]
+        g = MeshGraph((n,) * 3, p)
+        part = g.partition(wl["parts"], "rcb")
+    L = n * p + 1
+    return part, n, L ** 3, 6 * L * L * (L - 1)
+
+
+def build_problem(dev, precision, wl: dict, part):
     import torch
 
     import synthetic as syn
     from paper_2410_01657_gb300 import nn as gnn
-    from paper_2410_01657_gb300.graph import MeshGraph
 
-    part = MeshGraph((nel,) * 3, P).partition(R, "rcb")
+    Hh = wl["H"]
     G = part.to_device(dev)
-    params = syn.gnn_params(SEED, H, NH, M)
-    modes = syn.fourier_modes(SEED, 8)
-    pos = part.array("row_pos")
-    u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=dev)
-    t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=dev)
+    params = syn.gnn_params(SEED, Hh, NH, M)
     net = gnn.ConsistentGNN(params, precision=precision, device=dev)
-    with torch.no_grad():
-        x0, e0 = net.encode(G, u, G.edge_attr())
+    u = t = None
+    if wl["inputs"] == "encoders":
+        modes = syn.fourier_modes(SEED, 8)
+        pos = part.array("row_pos")
+        u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=dev)
+        t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=dev)
+        with torch.no_grad():
+            x0, e0 = net.encode(G, u, G.edge_attr())
+    else:
+        g = torch.Generator(device=dev).manual_seed(SEED)
+        x0 = torch.randn(part.n_rows, Hh, device=dev, generator=g)
+        e0 = torch.randn(part.n_edges, Hh, device=dev, generator=g).to(
+            torch.bfloat16 if precision == "bf16" else torch.float32)
     layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
-    stack = gnn.LayerStack(G, layers, H, precision, x0, e0)
-    dx_top = torch.tensor(syn.normal((part.n_rows, H), SEED + 7, 1e-3), dtype=torch.float32, device=dev)
-    return part, G, net, stack, dx_top, u, t
+    stack = gnn.LayerStack(G, layers, Hh, precision, x0, e0, inference=wl["mode"] == "fwd")
+    dx_top = None
+    if wl["mode"] == "fwdbwd":
+        g = torch.Generator(device=dev).manual_seed(SEED + 7)
+        dx_top = 1e-3 * torch.randn(part.n_rows, Hh, device=dev, generator=g)
+    return G, net, stack, dx_top, u, t
 
 
-def time_stack(stack, dx_top, steps, warmup, profile=True, fwd_only=False):
+def _timed(run, steps, profile):
     import torch
 
     from paper_2410_01657_gb300 import binding as B
 
     stream = torch.cuda.current_stream()
-    run = stack.forward if fwd_only else (lambda: stack.step(dx_top))
-    for _ in range(warmup):
-        run()
-    torch.cuda.synchronize()
     if profile:
         B.call("gnn_profile_start", 1 << 16)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -285,9 +343,30 @@ def time_stack(stack, dx_top, steps, warmup, profile=True, fwd_only=False):
     torch.cuda.synchronize()
     if profile:
         B.call("gnn_profile_stop")
-    ms = ev0.elapsed_time(ev1) / steps
-    report = B.profile_report() if profile else {}
-    return ms, report
+    return ev0.elapsed_time(ev1) / steps, (B.profile_report() if profile else {})
+
+
+def time_stack(stack, dx_top, steps, warmup, profile=True, graph=False):
+    """Mean device time of one step (ms) and the per-kernel CUDA-event report.
+
+    Eager: the profiled steps are the timed steps. Graph: the kernel report
+    comes from the same number of eager profiled steps, then the step is
+    captured once and `steps` replays are timed (the value)."""
+    import torch
+
+    run = lambda: stack.step(dx_top)
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    ms, report = _timed(run, steps, profile)
+    if not graph:
+        return ms, report, None
+    stack.capture(dx_top)
+    for _ in range(warmup):
+        stack.replay()
+    torch.cuda.synchronize()
+    ms_graph, _ = _timed(stack.replay, steps, False)
+    return ms_graph, report, ms
 
 
 def time_e2e(net, G, u, t, steps, warmup, dev):
@@ -350,14 +429,23 @@ def main():
         torch.cuda.synchronize()
 
     precision = args.precision
-    part, G, net, stack, dx_top, u, t = build_problem(dev, precision, args.nel)
-    L_lat = args.nel * P + 1
-    e_unpart = 6 * L_lat * L_lat * (L_lat - 1)
-    n_unpart = L_lat ** 3
+    wl = dict(WORKLOADS[args.workload])
+    Hw = wl["H"]
+    fwd_only = wl["mode"] == "fwd" or args.mode == "fwd"
+    if fwd_only:
+        wl["mode"] = "fwd"
+    use_graph = args.graph or wl["graph"]
+    part, n_el, n_unpart, e_unpart = workload_graph(wl, args.nel)
+    G, net, stack, dx_top, u, t = build_problem(dev, precision, wl, part)
+    tune = None
+    if (args.autotune or wl.get("uneven")) and precision == "bf16":
+        tune = stack.autotune(dx_top)
+        tune = {k: v for k, v in tune.items() if k != "candidates"} | {
+            "candidates": [{k: v for k, v in c.items() if k != "fwd_choices"} for c in tune.get("candidates", [])]}
     peaks = load_peaks()
     barrier()
     with ClockSampler(local) as clk:
-        ms, report = time_stack(stack, dx_top, args.steps, args.warmup, fwd_only=args.mode == "fwd")
+        ms, report, ms_eager = time_stack(stack, dx_top, args.steps, args.warmup, graph=use_graph)
     barrier()
     ms = max_over_ranks(ms, dist, dev)
     value = world * e_unpart * M / (ms * 1e-3)
@@ -367,15 +455,15 @@ def main():
     top_name, (top_n, top_ms) = top
     edge_bytes = 2 if precision == "bf16" else 4
     roof = None
-    abytes = algorithmic_bytes(top_name, G, H, edge_bytes)
+    abytes = algorithmic_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only)
     if abytes is not None:
         ach = abytes / (top_ms / top_n * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": measured_traffic(top_name, G.n_edges),
-                "peak_src": peaks["src"],
-                "share": top_ms / total_ms}
+                "frac": ach / peaks["hbm_gbs"],
+                "traffic": measured_traffic(top_name, G.n_edges) if args.workload == "c2" else None,
+                "peak_src": peaks["src"], "share": top_ms / total_ms}
     elif top_name == "k_sgemm":
-        flops = sgemm_flops_per_step(G, H, NH + 2, M) * args.steps
+        flops = sgemm_flops_per_step(G, Hw, NH + 2, M) * args.steps
         ach = flops / (top_ms * 1e-3) / 1e12
         peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -383,19 +471,18 @@ def main():
                 "share": top_ms / total_ms}
 
     fp32 = None
-    if precision == "bf16" and not args.no_fp32:
+    if precision == "bf16" and not args.no_fp32 and wl["inputs"] == "encoders":
         del stack
         torch.cuda.empty_cache()
-        _, G32, _, stack32, dx32, _, _ = build_problem(dev, "fp32", args.nel)
-        ms32, _ = time_stack(stack32, dx32, max(3, args.steps // 2), 2, profile=False,
-                             fwd_only=args.mode == "fwd")
+        _, _, stack32, dx32, _, _ = build_problem(dev, "fp32", wl, part)
+        ms32, _, _ = time_stack(stack32, dx32, max(3, args.steps // 2), 2, profile=False)
         fp32 = {"value": e_unpart * M / (ms32 * 1e-3), "unit": "edges/s", "ms_per_step": ms32,
                 "speedup_of_bf16": ms32 / ms}
         del stack32
         torch.cuda.empty_cache()
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and wl["inputs"] == "encoders" and not fwd_only:
         ms_e, h2d, d2h = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
         e2e = {"value": world * e_unpart * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -408,19 +495,27 @@ def main():
                "seconds": tsec}
 
     if rank == 0:
-        line = {"metric": "MP-layer edges/s fwd+bwd" if args.mode == "fwdbwd" else "MP-layer edges/s fwd", "value": value, "unit": "edges/s", "n_gpus": world,
+        kind = "fwd+bwd" if not fwd_only else "fwd"
+        edge_state = e_unpart * Hw * edge_bytes
+        line = {"metric": f"MP-layer edges/s {kind}", "value": value, "unit": "edges/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
-                "config": {"workload": f"consistent NMP layers x4 fwd+bwd, {args.nel}^3 elements p=5 GLL brick "
-                                       f"({n_unpart:,} nodes, {e_unpart:,} edges), 8 RCB sub-graphs, H=64, "
-                                       "MLP 2 hidden",
-                           "rows": part.n_rows, "edges_partitioned": part.n_edges,
-                           "l2": "inputs larger than L2 (edge state > 400 MB), no flush",
+                "config": {"workload": f"consistent NMP layers x{M} {kind}, {n_el}^3 elements: {wl['desc']} "
+                                       f"({n_unpart:,} nodes, {e_unpart:,} edges), H={Hw}, MLP {NH} hidden",
+                           "name": args.workload, "inputs": wl["inputs"],
+                           "rows": part.n_rows, "edges_partitioned": part.n_edges, "tile_edges": G.tile_edges,
+                           "l2": f"inputs larger than L2 (edge state {edge_state / 1e6:.0f} MB), no flush",
+                           "timing": "CUDA-graph replays; kernel table from as many eager steps" if use_graph
+                           else "eager steps",
                            "parallelism": f"replicas x{world}"},
                 "nodes_per_s": world * n_unpart * M / (ms * 1e-3),
                 "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu,
                 "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
                 "clocks": clk.summary()}
+        if ms_eager is not None:
+            line["eager_ms_per_step"] = ms_eager
+        if tune is not None:
+            line["autotune"] = tune
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

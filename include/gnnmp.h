@@ -273,6 +273,28 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
                     const float* dx_out, const void* de_out, float* dx_in, void* de_in,
                     const gnn_mp_params* dW, void* ws, size_t ws_bytes, void* stream);
 
+/* One timed launch choice of gnn_mp_autotune. */
+typedef struct gnn_tune_entry {
+    int32_t edge_fwd_kernel;   /* GNN_EDGE_FWD_*                                          */
+    int32_t ctas_per_sm;       /* 0 = occupancy limit                                     */
+    float ms;                  /* mean device time of one gnn_mp_forward call             */
+} gnn_tune_entry;
+
+/* Autotuner of the BF16 layer forward on one graph: times gnn_mp_forward
+ * (same arguments as there) for every launch choice of the edge forward that
+ * is valid for cfg->hidden, `reps` calls each after one untimed call, with
+ * CUDA events on `stream`; writes the fastest choice into cfg->edge_fwd_kernel
+ * and cfg->ctas_per_sm and, if out != NULL, up to max_out timings into out
+ * (*n_out = number written). Tile shapes are chosen one level up, by timing
+ * this call on graphs re-tiled with gnn_partition_set_tile_edges.
+ * Synchronises `stream` (not capturable: tune before capturing a graph) and
+ * overwrites x_out, e_out and a_star_out. Errors: those of gnn_mp_forward;
+ * GNN_EDTYPE for GNN_PREC_FP32, which has no launch choices. */
+int gnn_mp_autotune(const gnn_graph_dev* G, gnn_mp_config* cfg, const gnn_mp_params* W,
+                    const float* x_in, const void* e_in, float* x_out, void* e_out, float* a_star_out,
+                    void* ws, size_t ws_bytes, int32_t reps, gnn_tune_entry* out, int32_t max_out,
+                    int32_t* n_out, void* stream);
+
 /* gnn_mp_forward for callers that cannot allocate device memory when they run
  * the layer: code executing while a CUDA stream is being captured without a
  * graph memory pool, or a host framework that owns the device allocator and

@@ -57,6 +57,10 @@ class gnn_partition_info(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class gnn_tune_entry(C.Structure):
+    _fields_ = [("edge_fwd_kernel", C.c_int32), ("ctas_per_sm", C.c_int32), ("ms", C.c_float)]
+
+
 class gnn_graph_dev(C.Structure):
     _fields_ = [("n_rows", C.c_int64), ("n_edges", C.c_int64),
                 ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("edge_w", C.c_void_p),
@@ -101,6 +105,9 @@ _SIGS = {
     "gnn_mp_workspace_size": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                         C.POINTER(gnn_mp_params), C.POINTER(C.c_size_t),
                                         C.POINTER(C.c_size_t)]),
+    "gnn_mp_autotune": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config), C.POINTER(gnn_mp_params),
+                                  _P, _P, _P, _P, _P, _P, C.c_size_t, C.c_int32, C.POINTER(gnn_tune_entry),
+                                  C.c_int32, C.POINTER(C.c_int32), _P]),
     "gnn_mp_forward": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                  C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "gnn_mp_backward": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),

@@ -193,6 +193,7 @@ class DeviceGraph:
         g.max_in_degree = int(part.info.max_in_degree)
         g.tile_meta = B.ptr(t["tile_meta"])
         self.struct = g
+        self._tile_edges = part.tile_edges
 
     @property
     def n_rows(self) -> int:
@@ -201,6 +202,27 @@ class DeviceGraph:
     @property
     def n_edges(self) -> int:
         return self.part.n_edges
+
+    @property
+    def tile_edges(self) -> int:
+        """Edge cap of the tiles held on the device."""
+        return self._tile_edges
+
+    def retile(self, tile_edges: int) -> "DeviceGraph":
+        """Re-tile the partition (at most `tile_edges` edges per edge tile) and
+        upload only the tile arrays; every other device array is kept."""
+        import torch
+
+        part = self.part
+        if part.tile_edges != tile_edges:
+            part.set_tile_edges(tile_edges)
+        for name in ("edge_tiles", "tile_meta"):
+            self.t[name] = torch.from_numpy(part.array(name)).to(self.device)
+        self.struct.n_edge_tiles = int(part.info.n_edge_tiles)
+        self.struct.edge_tiles = B.ptr(self.t["edge_tiles"])
+        self.struct.tile_meta = B.ptr(self.t["tile_meta"])
+        self._tile_edges = int(tile_edges)
+        return self
 
     def edge_attr(self):
         import torch

@@ -203,38 +203,87 @@ class _MLP(torch.nn.Module):
         return list(self.params)
 
 
-class LayerStack:
-    """M consistent NMP layers, forward then backward, on preallocated buffers.
+def gnn_mp_autotune(G: DeviceGraph, cfg, W, x, e, x_out, e_out, a_star=None, ws=None, reps: int = 5):
+    """Native autotuner of the edge forward's launch choice on this graph (see
+    gnn_mp_autotune in gnnmp.h). Updates ``cfg`` in place; returns the timings
+    as [(edge_fwd_kernel, ctas_per_sm, ms)]."""
+    if ws is None:
+        ws = workspace(mp_workspace_sizes(G, cfg, W)[0], x.device)
+    out = (B.gnn_tune_entry * 8)()
+    n = C.c_int32()
+    B.call("gnn_mp_autotune", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(x_out),
+           B.ptr(e_out), B.ptr(a_star), B.ptr(ws), ws.numel(), int(reps), out, 8, C.byref(n), _stream())
+    return [(int(out[i].edge_fwd_kernel), int(out[i].ctas_per_sm), float(out[i].ms)) for i in range(n.value)]
 
-    Every buffer (node/edge states of each layer, saved a*, gradients,
-    workspace) is allocated once, so ``step`` issues library calls only and
-    can be captured in a CUDA graph. ``layers`` is a list of
+
+_TUNED: dict = {}
+
+
+class LayerStack:
+    """M consistent NMP layers on preallocated buffers: a training step
+    (forward then backward) or, with ``inference=True``, the forward alone.
+
+    Every buffer (node/edge states, saved a*, gradients, workspace) is
+    allocated once, so ``step`` / ``forward`` issue library calls only and can
+    be captured in a CUDA graph (``capture``). ``layers`` is a list of
     (edge tensors, node tensors, edge dims, node dims) per layer; gradients
-    accumulate into ``dparams`` (zeroed by ``zero_grad``)."""
+    accumulate into ``dparams`` (zeroed by ``zero_grad``).
+
+    Inference keeps the inputs and two edge-state and two node-state buffers
+    (ping-pong) and skips the last layer's edge-state write (GNN_FLAG_NO_EDGE_OUT): only the
+    aggregates reach the node update, so no per-edge output of the last layer
+    touches HBM."""
 
     def __init__(self, G: DeviceGraph, layers, hidden: int, precision: str, x0, e0, halo: bool = True,
-                 ln_eps: float = 1e-5):
+                 ln_eps: float = 1e-5, inference: bool = False):
         self.G = G
         self.M = len(layers)
+        self.hidden = hidden
+        self.precision = precision
+        self.inference = inference
         self.cfg = mp_config(hidden, precision, halo, ln_eps)
+        self.cfg_last = mp_config(hidden, precision, halo, ln_eps, B.GNN_FLAG_NO_EDGE_OUT if inference else 0)
         dev = x0.device
         edt = torch.bfloat16 if precision == "bf16" else torch.float32
         self.W, self.dW, self.dparams = [], [], []
         for (te, tn, de, dn) in layers:
             tens = list(te) + list(tn)
             self.W.append(mp_params(de, dn, tens))
-            dp = [torch.zeros_like(t) for t in tens]
-            self.dparams.append(dp)
-            self.dW.append(mp_params(de, dn, dp))
+            if not inference:
+                dp = [torch.zeros_like(t) for t in tens]
+                self.dparams.append(dp)
+                self.dW.append(mp_params(de, dn, dp))
         self._keep = [layers]
         NR, E = G.n_rows, G.n_edges
-        self.x = [x0.contiguous()] + [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
-        self.e = [e0.to(edt).contiguous()] + [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
-        self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
-        self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(self.M + 1)]
-        self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
+        if inference:
+            self.x = [x0.contiguous(), torch.empty(NR, hidden, device=dev), torch.empty(NR, hidden, device=dev)]
+            self.e = [e0.to(edt).contiguous()] + [torch.empty(E, hidden, device=dev, dtype=edt)
+                                                  for _ in range(min(2, self.M - 1))]
+            self.a = []
+        else:
+            self.x = [x0.contiguous()] + [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
+            self.e = [e0.to(edt).contiguous()] + [torch.empty(E, hidden, device=dev, dtype=edt)
+                                                  for _ in range(self.M)]
+            self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
+            self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(self.M + 1)]
+            self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
         f, b = mp_workspace_sizes(G, self.cfg, self.W[0])
-        self.ws = workspace(max(f, b), dev)
+        self.ws = workspace(f if inference else max(f, b), dev)
+        self.graph = None
+
+    # buffers of layer l: inputs, outputs, saved a* (ping-pong in inference)
+    def _io(self, l: int):
+        if not self.inference:
+            return self.x[l], self.e[l], self.x[l + 1], self.e[l + 1], self.a[l]
+        xi = self.x[0] if l == 0 else self.x[1 + (l - 1) % 2]
+        xo = self.x[1 + l % 2]
+        ei = self.e[0] if l == 0 else self.e[1 + (l - 1) % 2]
+        eo = None if l == self.M - 1 else self.e[1 + l % 2]
+        return xi, ei, xo, eo, None
+
+    @property
+    def x_out(self):
+        return self._io(self.M - 1)[2]
 
     def zero_grad(self):
         for dp in self.dparams:
@@ -243,20 +292,107 @@ class LayerStack:
 
     def forward(self):
         for l in range(self.M):
-            gnn_mp_forward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.x[l + 1], self.e[l + 1],
-                           self.a[l], self.ws)
+            xi, ei, xo, eo, a = self._io(l)
+            cfg = self.cfg_last if l == self.M - 1 else self.cfg
+            gnn_mp_forward(self.G, cfg, self.W[l], xi, ei, xo, eo, a, self.ws)
 
     def backward(self, dx_top):
         """dx_top: dL/dx of the last layer's output; dL/de of it is zero."""
+        assert not self.inference, "an inference stack has no backward"
         dx_out, de_out = dx_top, None
         for l in range(self.M - 1, -1, -1):
             gnn_mp_backward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.a[l], dx_out, de_out,
                             self.dx[l], self.de[l], self.dW[l], self.ws)
             dx_out, de_out = self.dx[l], self.de[l]
 
-    def step(self, dx_top):
-        self.forward()
-        self.backward(dx_top)
+    def step(self, dx_top=None):
+        if self.inference:
+            self.forward()
+        else:
+            self.forward()
+            self.backward(dx_top)
+
+    # ------------------------------------------------------------------ CUDA graph
+    def capture(self, dx_top=None, warmup: int = 2) -> torch.cuda.CUDAGraph:
+        """Capture one ``step`` into a CUDA graph (replay with ``replay``). The
+        launch choices and tiles in force now are frozen into the graph."""
+        s = torch.cuda.Stream(device=self.ws.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):   # first calls look up device attributes outside the capture
+                self.step(dx_top)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self.step(dx_top)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    # ------------------------------------------------------------------ autotuning
+    def autotune(self, dx_top=None, tile_caps=(128, 96, 64, 32), reps: int = 3, cache_file: str | None = None):
+        """Choose the edge-tile cap (gnn_partition_set_tile_edges) and the edge
+        forward's launch choice (gnn_mp_autotune) for this graph by timing:
+        for every cap, the native tuner picks the launch choice, then a whole
+        ``step`` is timed; the fastest (cap, choice) is kept. Results are
+        cached per (device, H, layer shapes, precision, graph size, mode), in
+        memory and in ``cache_file`` (JSON) when given. Returns the report."""
+        import json
+        import os
+
+        if self.precision != "bf16":
+            return {"tuned": False, "reason": "the FP32 path has no launch choices"}
+        dev = self.ws.device
+        key = "|".join(str(v) for v in (torch.cuda.get_device_name(dev), self.hidden, self.W[0].edge.n_lin,
+                                          self.W[0].node.n_lin, self.precision, self.G.n_rows, self.G.n_edges,
+                                          "inf" if self.inference else "train"))
+        cache = dict(_TUNED)
+        if cache_file and os.path.exists(cache_file):
+            with open(cache_file) as fh:
+                cache.update(json.load(fh))
+        if key in cache:
+            r = cache[key]
+            self._apply(r["tile_edges"], r["edge_fwd_kernel"], r["ctas_per_sm"])
+            return dict(r, cached=True)
+        xi, ei, xo, eo, a = self._io(0)
+        scratch_e = eo if eo is not None else torch.empty_like(ei)
+        rows = []
+        caps = [c for c in tile_caps if self.G.part.info.max_in_degree <= c <= B.GNN_EDGE_TILE]
+        for cap in caps:
+            self.G.retile(cap)
+            cfg = mp_config(self.hidden, self.precision, self.cfg.halo_mode == B.GNN_HALO_SYNC, self.cfg.ln_eps)
+            timings = gnn_mp_autotune(self.G, cfg, self.W[0], xi, ei, xo, scratch_e, a, self.ws, reps)
+            self._apply(cap, cfg.edge_fwd_kernel, cfg.ctas_per_sm)
+            self.step(dx_top)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                self.step(dx_top)
+            e1.record()
+            torch.cuda.synchronize()
+            rows.append({"tile_edges": cap, "edge_fwd_kernel": cfg.edge_fwd_kernel, "ctas_per_sm": cfg.ctas_per_sm,
+                         "step_ms": e0.elapsed_time(e1) / reps, "fwd_choices": timings})
+        best = min(rows, key=lambda r: r["step_ms"])
+        self._apply(best["tile_edges"], best["edge_fwd_kernel"], best["ctas_per_sm"])
+        self.zero_grad()
+        res = {"tile_edges": best["tile_edges"], "edge_fwd_kernel": best["edge_fwd_kernel"],
+               "ctas_per_sm": best["ctas_per_sm"], "step_ms": best["step_ms"], "candidates": rows}
+        _TUNED[key] = res
+        if cache_file:
+            cache[key] = res
+            with open(cache_file, "w") as fh:
+                json.dump(cache, fh, indent=1)
+        return dict(res, cached=False)
+
+    def _apply(self, tile_edges: int, kernel: int, ctas_per_sm: int):
+        if self.G.tile_edges != tile_edges:
+            self.G.retile(tile_edges)
+        for c in (self.cfg, self.cfg_last):
+            c.edge_fwd_kernel = int(kernel)
+            c.ctas_per_sm = int(ctas_per_sm)
+        self.graph = None
 
 
 class ConsistentGNN(torch.nn.Module):

@@ -142,3 +142,66 @@ def test_inference_h32_last_layer_without_edge_output():
         xt, et = xo, eo
     B.call("gnn_check", None)
     assert rel_l2(xt.cpu().numpy(), np.concatenate(xs)) < 2e-2
+
+
+def _stack_case(H=64, M=3, inference=False, seed=50):
+    brick, subs, part = _uneven_case(seed=seed)
+    G = part.to_device(DEV)
+    params = syn.gnn_params(seed, H, 2, M, randomize_affine=True)
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
+    g = torch.Generator(device=DEV).manual_seed(seed)
+    x0 = torch.randn(part.n_rows, H, device=DEV, generator=g)
+    e0 = torch.randn(part.n_edges, H, device=DEV, generator=g).to(torch.bfloat16)
+    dx = 1e-3 * torch.randn(part.n_rows, H, device=DEV, generator=g)
+    stack = gnn.LayerStack(G, layers, H, "bf16", x0, e0, inference=inference)
+    return part, G, layers, x0, e0, dx, stack
+
+
+def test_inference_stack_equals_training_forward():
+    H, M = 32, 4
+    part, G, layers, x0, e0, dx, tr = _stack_case(H, M)
+    inf = gnn.LayerStack(G, layers, H, "bf16", x0, e0, inference=True)
+    tr.forward()
+    inf.forward()
+    inf.forward()                     # repeated steps read the same inputs
+    torch.cuda.synchronize()
+    assert torch.equal(inf.x_out, tr.x[M])
+    assert len(inf.e) == 3 and len(inf.x) == 3
+
+
+def test_cuda_graph_replay_matches_eager_step():
+    part, G, layers, x0, e0, dx, stack = _stack_case()
+    stack.zero_grad()
+    stack.step(dx)
+    torch.cuda.synchronize()
+    x_ref = stack.x[-1].clone()
+    g_ref = [t.clone() for t in stack.dparams[0]]
+    stack.capture(dx)
+    stack.zero_grad()
+    stack.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(stack.x[-1], x_ref)
+    for t, r in zip(stack.dparams[0], g_ref):
+        assert torch.equal(t, r)
+    B.call("gnn_check", None)
+
+
+def test_autotune_keeps_results_and_caches(tmp_path):
+    part, G, layers, x0, e0, dx, stack = _stack_case(H=32, M=2, inference=True, seed=60)
+    stack.forward()
+    torch.cuda.synchronize()
+    ref = stack.x_out.clone()
+    cache = str(tmp_path / "tune.json")
+    rep = stack.autotune(tile_caps=(128, 64, 32), reps=2, cache_file=cache)
+    assert not rep["cached"] and rep["tile_edges"] in (128, 64, 32)
+    assert len(rep["candidates"]) == 3
+    kinds = {c[0] for c in rep["candidates"][0]["fwd_choices"]}
+    assert kinds == {B.GNN_EDGE_FWD_RT, B.GNN_EDGE_FWD_WS, B.GNN_EDGE_FWD_ONE}
+    assert G.tile_edges == rep["tile_edges"] and part.tile_edges == rep["tile_edges"]
+    stack.forward()
+    torch.cuda.synchronize()
+    assert rel_l2(stack.x_out.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    gnn._TUNED.clear()
+    rep2 = stack.autotune(tile_caps=(128, 64, 32), reps=2, cache_file=cache)
+    assert rep2["cached"] and rep2["tile_edges"] == rep["tile_edges"]

@@ -150,9 +150,14 @@ __device__ __forceinline__ void flush_acc(uint32_t tmem, int N, int m_valid, int
 // ------------------------------------------------------------------ shared memory plans
 
 struct EdgeBwdSmem {
-    uint32_t w, e0, de, g, hb, ones, stage, par, seg, red, bar, tm, total;
+    uint32_t w, e0, de, g, hb, ones, slot, par, seg, red, bar, tm, total;
 };
 
+// Edge-backward shared memory. g holds the tile's dz rows during the adjoint
+// and, during the recompute, the aggregate gradients da of the tile's
+// receivers (when they fit: nr * H * 4 <= TILE). hb holds the recomputed
+// hidden activations and, once the adjoint no longer reads them, the staging
+// of the segmented sum dP. slot: each thread's P|Q rows for the next tile.
 template <int H>
 __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     using C = CfgB<H>;
@@ -163,12 +168,14 @@ __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     s.seg = s.e0 + 4 * C::TILE;                    // 2 tile records (GNN_TILE_META_BYTES each)
     s.g = align_up(s.seg + 2 * GNN_TILE_META_BYTES, 1024);
     s.hb = s.g + C::TILE;
-    s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
-    s.stage = align_up(s.ones + 128 * C::S, 1024);
-    s.par = s.stage + 128 * (H + 4) * 4;
+    const uint32_t hb_min = 128 * H * 4, hb_tiles = (uint32_t)(n_lin - 1) * C::TILE;
+    const uint32_t hb_bytes = hb_tiles > hb_min ? hb_tiles : hb_min;
+    s.ones = align_up(s.hb + hb_bytes, 1024);
+    s.slot = align_up(s.ones + 128 * C::S, 1024);
+    s.par = s.slot + 2 * C::TILE;
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma
-    s.tm = s.bar + 24;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma, ready, da, wgrad
+    s.tm = s.bar + 48;
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
     s.total = end + 1024;
@@ -222,6 +229,9 @@ __host__ __device__ inline ProjBwdSmem proj_bwd_smem() {
 // TMEM column plans
 template <int H>
 __host__ __device__ inline uint32_t edge_bwd_tcols(int n_lin) { return H + n_lin * (H + 16); }
+// ... plus the LayerNorm parameter-gradient accumulators (2H columns) when they fit
+template <int H>
+__host__ __device__ inline bool edge_bwd_ln_in_tmem(int n_lin) { return edge_bwd_tcols<H>(n_lin) + 2 * H <= 512; }
 template <int H>
 __host__ __device__ inline uint32_t node_bwd_tcols(int n_lin) {
     return 2 * H + (2 * H + 16) + (n_lin - 1) * (H + 16);
@@ -467,7 +477,10 @@ struct EdgeBwdArgs {
     float eps;
 };
 
-template <int H>
+// LNT: the per-thread LayerNorm gradient sums live in TMEM columns after the
+// weight-gradient accumulators (read, add, write back once per tile) instead
+// of 2*CW registers.
+template <int H, bool LNT>
 __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_constant__ CUtensorMap tmap_e,
                                                             const __grid_constant__ CUtensorMap tmap_de,
                                                             EdgeBwdArgs A) {
@@ -482,17 +495,23 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     uint8_t* sG = sm + P.g;
     uint8_t* sHB = sm + P.hb;
     uint8_t* sOnes = sm + P.ones;
-    float* sStage = reinterpret_cast<float*>(sm + P.stage);
+    float* sStage = reinterpret_cast<float*>(sHB);               // dP staging at the last adjoint step
     float* sPar = reinterpret_cast<float*>(sm + P.par);
     float* sRed = reinterpret_cast<float*>(sm + P.red);
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.bar);   // full[2]: stage loaded
-    uint64_t* bar = full + 2;
+    uint64_t* bar = full + 2;       // MMA completion
+    uint64_t* ready = full + 3;     // one arrival per warp: operands written, accumulator read
+    uint64_t* da_full = full + 4;   // the tile's da rows have landed in sG
+    uint64_t* bar_w = full + 5;     // weight-gradient MMAs of an adjoint step (complete behind the epilogue)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, CW = C::CW;
-    const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L));
+    const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L) + (LNT ? 2 * H : 0));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    constexpr int NCH = 4 * CW / 16;                               // 16-byte chunks of a P|Q slot
+    uint8_t* sSlot = sm + P.slot + (g * 128 + row) * (4 * CW);
+    auto slot_at = [&](int k) { return sSlot + 16 * (k ^ ((row >> (NCH >= 8 ? 0 : 1)) & (NCH - 1))); };
 
     if (warp == 0) {
         tmem_alloc(tslot, NCOLS);
@@ -502,6 +521,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         mbar_init(full, 1);
         mbar_init(full + 1, 1);
         mbar_init(bar, 1);
+        mbar_init(ready, C::NT / 32);
+        mbar_init(da_full, 1);
+        mbar_init(bar_w, 1);
         fence_mbar_init();
     }
     load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, C::NT);
@@ -520,83 +542,141 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     const uint32_t tWork = tmem;
     auto tDW = [&](int k) -> uint32_t { return tmem + (uint32_t)(H + k * (H + 16)); };
     const uint32_t ones_addr = smem_u32(sOnes);
-    float acc_g[CW], acc_b[CW];
+    // LayerNorm gradient sums of this thread: sum_rows g * xhat and sum_rows g, CW columns each
+    constexpr int ACW = LNT ? 1 : CW;
+    float acc_g[ACW], acc_b[ACW];
 #pragma unroll
-    for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
-    uint32_t ph = 0;
+    for (int i = 0; i < ACW; ++i) acc_g[i] = acc_b[i] = 0.f;
+    const uint32_t tLN = tmem + ((uint32_t)(32 * q) << 16) + edge_bwd_tcols<H>(L) + (uint32_t)(g * 2 * CW);
+    if constexpr (LNT) {
+        float z[16] = {};
+#pragma unroll
+        for (int i = 0; i < 2 * CW; i += 16) tmem_st16(tLN + i, z);
+        tmem_st_wait();
+    }
+    uint32_t ph = 0, ph_rdy = 0, ph_da = 0, ph_w = 0;
     bool ok = true, first = true;
+    // MMA hand-off without block barriers: every warp arrives on `ready` once its
+    // operand writes and its TMEM reads of the accumulator are done; thread 0
+    // waits for all warps, issues and commits to `bar`; every thread waits on
+    // `bar` by itself. After a timeout a thread stops waiting and issuing; the
+    // block leaves the tile loop together at the tile-end barrier.
+    auto handoff = [&](auto&& issue, uint64_t* done) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready);
+        if (tid == 0) {
+            ok = ok && mbar_wait(ready, ph_rdy);
+            ph_rdy ^= 1;
+            tc_fence_after();
+            if (ok) {
+                issue();
+                mma_commit(done);
+            }
+        }
+    };
+    auto mma_wait = [&]() {
+        ok = ok && mbar_wait(bar, ph);
+        ph ^= 1;
+        __syncwarp();
+        tc_fence_after();
+    };
     const uint32_t tx_bytes = C::TILE * (A.has_de_out ? 2 : 1) + GNN_TILE_META_BYTES;
     // stage s <- tile t: its record by bulk copy, its e (and de_out) rows by TMA
-    auto issue_stage = [&](int s, int64_t t) {
+    // (e0: the tile's first edge, read from its global record one tile in advance)
+    auto issue_stage = [&](int s, int64_t t, int32_t e0) {
         uint8_t* rec = sRec0 + s * GNN_TILE_META_BYTES;
         uint8_t* se = sStg0 + s * 2 * C::TILE;
-        const int32_t e0 = reinterpret_cast<const int32_t*>(A.tile_meta + t * GNN_TILE_META_BYTES)[2];
         mbar_arrive_expect_tx(full + s, tx_bytes);
         bulk_load(rec, A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, full + s);
         tma_load_2d(se, &tmap_e, 0, e0, full + s);
         if (A.has_de_out) tma_load_2d(se + C::TILE, &tmap_de, 0, e0, full + s);
     };
-    if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) issue_stage(0, blockIdx.x);
+    // this thread's P|Q slot <- its edge's receiver P row and sender Q row (own columns)
+    // of the tile whose record is in stage s
+    auto gather = [&](int s) {
+        const uint8_t* rec = sRec0 + s * GNN_TILE_META_BYTES;
+        if (row < reinterpret_cast<const int32_t*>(rec)[3]) {
+            const int64_t rcv = reinterpret_cast<const int32_t*>(rec)[0] + reinterpret_cast<const int16_t*>(rec + 544)[row];
+            const int64_t snd = reinterpret_cast<const int32_t*>(rec + 800)[row];
+#pragma unroll
+            for (int k = 0; k < NCH / 2; ++k) {
+                cp_async16(slot_at(k), A.pq + rcv * 2 * H + c0 + 8 * k);
+                cp_async16(slot_at(k + NCH / 2), A.pq + snd * 2 * H + H + c0 + 8 * k);
+            }
+        }
+        cp_async_commit();
+    };
+    auto first_edge = [&](int64_t t) { return ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8); };
+    int32_t e0_next = 0;   // thread 0: first edge of the CTA's next tile
+    if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) {
+        issue_stage(0, blockIdx.x, first_edge(blockIdx.x));
+        if ((int64_t)blockIdx.x + gridDim.x < A.n_tiles) e0_next = first_edge(blockIdx.x + gridDim.x);
+    }
+    if ((int64_t)blockIdx.x < A.n_tiles) {
+        ok = mbar_wait(full, 0);
+        if (ok) gather(0);
+    }
     int j = 0;
 
-    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
+    for (int64_t t = blockIdx.x; t < A.n_tiles; t += gridDim.x, ++j) {
         const int st = j & 1;
-        ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
-        if (!ok) break;
-        // the other stage was released at the end of the previous tile: prefetch the next tile
-        if (tid == 0 && t + gridDim.x < A.n_tiles) issue_stage(st ^ 1, t + gridDim.x);
+        ok = ok && mbar_wait(full + st, (uint32_t)(j >> 1) & 1u);
+        __syncwarp();
         const uint8_t* rec = sRec0 + st * GNN_TILE_META_BYTES;
         const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
         const int32_t* sRp = reinterpret_cast<const int32_t*>(rec + 16);
         const int16_t* sSeg = reinterpret_cast<const int16_t*>(rec + 544);
-        const int32_t* sCol = reinterpret_cast<const int32_t*>(rec + 800);
         const float* sW1d = reinterpret_cast<const float*>(rec + 1312);
         uint8_t* sE0 = sStg0 + st * 2 * C::TILE;
         uint8_t* sDE = sE0 + C::TILE;
         const int32_t r0 = hdr[0], r1 = hdr[1], e0 = hdr[2], ne = hdr[3];
         const bool valid = row < ne;
         const int64_t eg = (int64_t)e0 + row;
-        if (tid == 0) {
+        // the receivers' da rows into sG for the LayerNorm adjoint (sG is free until then)
+        const bool da_bulk = (r1 - r0) * H * 4 <= C::TILE;
+        if (tid == 0 && ok && da_bulk) {
+            mbar_arrive_expect_tx(da_full, (uint32_t)(r1 - r0) * H * 4);
+            bulk_load(sG, A.da + (int64_t)r0 * H, (uint32_t)(r1 - r0) * H * 4, da_full);
+        }
+        if (tid == 0 && ok) {
             tc_fence_after();
             issue_mma(tWork, sE0, sW, H, H);
             mma_commit(bar);
-        }
-        float w = 0.f;
-        float pq[CW], dar[CW];
-        int64_t rcv = 0;
-        if (valid) {
-            rcv = r0 + sSeg[row];
-            const int64_t snd = sCol[row];
-            w = sW1d[row];
-#pragma unroll
-            for (int i = 0; i < CW; i += 8) {
-                float pv[8], qv[8];
-                ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
-                ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) pq[i + jj] = pv[jj] + qv[jj];
+            // the other stage was released at the end of the previous tile: prefetch the next tile
+            if (t + gridDim.x < A.n_tiles) {
+                issue_stage(st ^ 1, t + gridDim.x, e0_next);
+                if (t + 2 * (int64_t)gridDim.x < A.n_tiles) e0_next = first_edge(t + 2 * (int64_t)gridDim.x);
             }
-            const float4* pd = reinterpret_cast<const float4*>(A.da + rcv * H + c0);
-#pragma unroll
-            for (int i = 0; i < CW / 4; ++i) {
-                float4 u = __ldg(pd + i);
-                dar[4 * i] = u.x; dar[4 * i + 1] = u.y; dar[4 * i + 2] = u.z; dar[4 * i + 3] = u.w;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < CW; ++i) pq[i] = dar[i] = 0.f;
         }
+        cp_async_wait_all();   // this thread's P|Q slot for the tile
         // ---- recompute the chain
         float v[CW];
-        for (int k = 0; k < L && ok; ++k) {
-            ok = block_wait(bar, ph, tid);
-            ph ^= 1;
-            tc_fence_after();
-            if (!ok) break;
+        for (int k = 0; k < L; ++k) {
+            mma_wait();
             ld_acc<CW>(tWork, q, c0, v);
             if (k == 0) {
+                if (valid) {
 #pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] += pq[i] + sPar[c0 + i];
+                    for (int kc = 0; kc < NCH / 2; ++kc) {
+                        const uint4 up = *reinterpret_cast<const uint4*>(slot_at(kc));
+                        const uint4 uq = *reinterpret_cast<const uint4*>(slot_at(kc + NCH / 2));
+                        const uint32_t pw[4] = {up.x, up.y, up.z, up.w}, qw[4] = {uq.x, uq.y, uq.z, uq.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            float p0, p1, q0, q1;
+                            unpack_bf16x2(pw[h], p0, p1);
+                            unpack_bf16x2(qw[h], q0, q1);
+                            v[8 * kc + 2 * h] += (p0 + q0) + sPar[c0 + 8 * kc + 2 * h];
+                            v[8 * kc + 2 * h + 1] += (p1 + q1) + sPar[c0 + 8 * kc + 2 * h + 1];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < CW; ++i) v[i] += sPar[c0 + i];
+                }
+
             } else {
 #pragma unroll
                 for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
@@ -605,21 +685,26 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
                 for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
-                fence_proxy_async();
-                tc_fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    tc_fence_after();
-                    issue_mma(tWork, sHB + k * C::TILE, sW + (k + 1) * C::WT, H, H);
-                    mma_commit(bar);
-                }
+                handoff([&] { issue_mma(tWork, sHB + k * C::TILE, sW + (k + 1) * C::WT, H, H); }, bar);
             }
         }
-        if (!ok) break;
         tc_fence_before();
         // ---- gradient of e' (adjoint of Eq. 5b plus the upstream edge gradient)
         float gv[CW];
+        if (da_bulk) {
+            ok = ok && mbar_wait(da_full, ph_da);
+            ph_da ^= 1;
+        }
         if (valid) {
+            float dar[CW];
+            const float* src = da_bulk ? reinterpret_cast<const float*>(sG) + (int64_t)sSeg[row] * H + c0
+                                       : A.da + (int64_t)(r0 + sSeg[row]) * H + c0;
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                const float4 u = *reinterpret_cast<const float4*>(src + 4 * i);
+                dar[4 * i] = u.x; dar[4 * i + 1] = u.y; dar[4 * i + 2] = u.z; dar[4 * i + 3] = u.w;
+            }
+            const float w = sW1d[row];
             float deo[CW];
             if (A.has_de_out) ld_row_tile<CW>(sDE, row, c0, S, deo);
 #pragma unroll
@@ -636,13 +721,34 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
         for (int i = 0; i < CW; ++i) {
             const float xh = (v[i] - mean) * rstd;
-            acc_g[i] += gv[i] * xh;
-            acc_b[i] += gv[i];
             const float d = gv[i] * sPar[L * H + c0 + i];
             dz[i] = d;
             v[i] = xh;
             m1 += d;
             m2 += d * xh;
+        }
+        if constexpr (LNT) {
+#pragma unroll
+            for (int i0 = 0; i0 < CW; i0 += 16) {
+                float ag[16], ab[16];
+                tmem_ld16(tLN + i0, ag);
+                tmem_ld16(tLN + CW + i0, ab);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    ag[i] += gv[i0 + i] * v[i0 + i];
+                    ab[i] += gv[i0 + i];
+                }
+                tmem_st16(tLN + i0, ag);
+                tmem_st16(tLN + CW + i0, ab);
+            }
+            tmem_st_wait();
+        } else {
+#pragma unroll
+            for (int i = 0; i < ACW; ++i) {
+                acc_g[i] += gv[i] * v[i];
+                acc_b[i] += gv[i];
+            }
         }
         float s1, s2;
         row_sum2<C::CG>(m1, m2, sRed + 2 * C::CG * 128, row, g, s1, s2);
@@ -651,17 +757,22 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
         for (int i = 0; i < CW; ++i) dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
         // ---- chain adjoint
-        for (int k = L - 1; k >= 0 && ok; --k) {
+        for (int k = L - 1; k >= 0; --k) {
+            if (k < L - 1) {   // the previous step's wgrad reads sG: wait for it (per thread, no barrier)
+                ok = ok && mbar_wait(bar_w, ph_w);
+                ph_w ^= 1;
+            }
             st_row_tile<CW>(sG, row, c0, S, dz);
-            fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
+            handoff([&] {
                 issue_dgrad(tWork, sG, S, sW + k * C::WT, S, H, (uint32_t)H * S, H, H);
+                mma_commit(bar);
                 uint8_t* hk = (k == 0) ? sE0 : sHB + (k - 1) * C::TILE;
                 issue_wgrad(tDW(k), sG, S, 128u * S, hk, S, ones_addr - smem_u32(hk), H + 16, !first);
-                mma_commit(bar);
+            }, bar_w);
+            if (k == L - 1 && t + gridDim.x < A.n_tiles) {
+                // the slot was consumed by the first recompute step and the next tile's stage
+                // (issued at this tile's start) has landed by now: request its P|Q rows
+                if (mbar_wait(full + (st ^ 1), (uint32_t)((j + 1) >> 1) & 1u)) gather(st ^ 1);
             }
             if (k == 0) {
                 // dz1 per edge (for the sender-side sum) and its receiver-side segmented sum
@@ -671,6 +782,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 }
                 constexpr int NC = H / 4;
                 float4* sS4 = reinterpret_cast<float4*>(sStage);
+                __syncthreads();   // every warp is past its last read of hb, which the staging overwrites
 #pragma unroll
                 for (int i = 0; i < CW / 4; ++i)
                     sS4[row * NC + stage_chunk<NC>(c0 / 4 + i, row)] =
@@ -691,10 +803,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                     *reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + 4 * c) = acc;
                 }
             }
-            ok = block_wait(bar, ph, tid);
-            ph ^= 1;
-            tc_fence_after();
-            if (!ok) break;
+            mma_wait();
             float dh[CW];
             ld_acc<CW>(tWork, q, c0, dh);
             if (k > 0) {
@@ -712,11 +821,14 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             tc_fence_before();
         }
         first = false;
+        ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads this tile's e stage and sG
+        ph_w ^= 1;
         fence_proxy_async();
-        __syncthreads();
+        if (__syncthreads_or(!ok)) break;   // stage release; the block leaves together after a timeout
+        tc_fence_after();
     }
     tc_fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {
@@ -728,8 +840,20 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 for (int i = tid; i < H * N; i += C::NT) part[off + i] = 0.f;
             off += (int64_t)H * N;
         }
-        rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
-        rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
+        if constexpr (LNT) {
+            float ag[CW], ab[CW];
+#pragma unroll
+            for (int i0 = 0; i0 < CW; i0 += 16) {
+                tmem_ld16(tLN + i0, ag + i0);
+                tmem_ld16(tLN + CW + i0, ab + i0);
+            }
+            tmem_ld_wait();
+            rows_reduce_store<CW>(ag, sRed, q, lane, g, c0, part + off);
+            rows_reduce_store<CW>(ab, sRed, q, lane, g, c0, part + off + H);
+        } else {
+            rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
+            rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -805,14 +929,33 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
                 dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
                 xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
             }
-            for (int32_t k = A.t_ptr[r]; k < A.t_ptr[r + 1]; ++k) {      // sender-side sum, edge order
-                const int64_t e = A.t_eid[k];
+            // sender-side sum in edge order; the edge ids and then the dz1 rows of up to
+            // four edges are requested together so their latencies overlap
+            const int32_t k0 = A.t_ptr[r], k1 = A.t_ptr[r + 1];
+            for (int32_t kb = k0; kb < k1; kb += 4) {
+                int64_t e[4];
 #pragma unroll
-                for (int i = 0; i < CW; i += 8) {
-                    float z[8];
-                    ld_bf16x8(A.dz1 + e * H + c0 + i, z);
+                for (int u = 0; u < 4; ++u) e[u] = kb + u < k1 ? (int64_t)__ldg(A.t_eid + kb + u) : -1;
+                uint4 z[4][CW / 8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) dq[i + j] += z[j];
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int i = 0; i < CW / 8; ++i)
+                        z[u][i] = e[u] >= 0 ? __ldg(reinterpret_cast<const uint4*>(A.dz1 + e[u] * H + c0) + i)
+                                            : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (e[u] < 0) break;
+#pragma unroll
+                    for (int i = 0; i < CW / 8; ++i) {
+                        float f[8];
+                        unpack_bf16x2(z[u][i].x, f[0], f[1]);
+                        unpack_bf16x2(z[u][i].y, f[2], f[3]);
+                        unpack_bf16x2(z[u][i].z, f[4], f[5]);
+                        unpack_bf16x2(z[u][i].w, f[6], f[7]);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) dq[8 * i + j] += f[j];
+                    }
                 }
             }
         }
@@ -1052,13 +1195,21 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.eps = cfg.ln_eps;
         const EdgeBwdSmem P = edge_bwd_smem<H>(Le);
         int grid;
-        rc = persistent_grid(k_edge_bwd<H>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le)), G.n_edge_tiles,
-                             &grid);
+        const bool lnt = edge_bwd_ln_in_tmem<H>(Le);
+        if (lnt)
+            rc = persistent_grid(k_edge_bwd<H, true>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le) + 2 * H),
+                                 G.n_edge_tiles, &grid);
+        else
+            rc = persistent_grid(k_edge_bwd<H, false>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le)),
+                                 G.n_edge_tiles, &grid);
         if (rc) return rc;
         grid = std::min(grid, nsm);
         {
             ProfScope _ps(s, "k_edge_bwd");
-            k_edge_bwd<H><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
+            if (lnt)
+                k_edge_bwd<H, true><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
+            else
+                k_edge_bwd<H, false><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
         }
         GNN_LAUNCH_CHECK("k_edge_bwd");
         RedSeg seg[MAX_SEGS];

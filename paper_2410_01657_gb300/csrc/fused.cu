@@ -39,8 +39,11 @@ using namespace tc;
 
 // ------------------------------------------------------------------ k_proj_fwd
 
+// One tile = 128 node rows. The FP32 x rows of the CTA's next tile are loaded
+// by TMA into the other of two stages while the current tile is converted to
+// BF16, multiplied and written.
 template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict__ x, int64_t n_rows,
+__global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__ CUtensorMap tmap_x, int64_t n_rows,
                                                         const float* __restrict__ W1, __nv_bfloat16* __restrict__ pq) {
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
@@ -48,17 +51,22 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict
     const ProjSmem L = proj_smem<H>();
     uint8_t* sW = sm + L.w;
     uint8_t* sA = sm + L.a;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint64_t* bar = full + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * C::CW;
     constexpr uint32_t NCOLS = 2 * H < 32 ? 32 : 2 * H;
+    constexpr uint32_t XBYTES = 128 * H * 4;
+    auto sX = [&](int s) { return sm + L.x + s * XBYTES; };
 
     if (warp == 0) {
         tmem_alloc(tslot, NCOLS);
         tmem_relinquish();
     }
     if (tid == 0) {
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
         mbar_init(bar, 1);
         fence_mbar_init();
     }
@@ -73,20 +81,27 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict
     uint32_t phase = 0;
     bool ok = true;
     const int64_t n_tiles = (n_rows + 127) / 128;
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    if (tid == 0 && (int64_t)blockIdx.x < n_tiles) {
+        mbar_arrive_expect_tx(full, XBYTES);
+        tma_f32_tile<H>(sX(0), &tmap_x, (int64_t)blockIdx.x * 128, full);
+    }
+    int j = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+        const int st = j & 1;
+        ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
+        if (!ok) break;
+        // the other stage was read by the previous tile (ordered by its closing barrier)
+        if (tid == 0 && t + gridDim.x < n_tiles) {
+            mbar_arrive_expect_tx(full + (st ^ 1), XBYTES);
+            tma_f32_tile<H>(sX(st ^ 1), &tmap_x, (t + gridDim.x) * 128, full + (st ^ 1));
+        }
         const int64_t r = t * 128 + row;
         const bool valid = r < n_rows;
         float v[C::CW];
-        if (valid) {
-            const float4* p = reinterpret_cast<const float4*>(x + r * H + c0);
 #pragma unroll
-            for (int i = 0; i < C::CW / 4; ++i) {
-                float4 a = __ldg(p + i);
-                v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < C::CW; ++i) v[i] = 0.f;
+        for (int i = 0; i < C::CW / 4; ++i) {
+            const float4 u = ld_f32x4_tile<H>(sX(st), row, c0 + 4 * i);   // rows past n_rows read as zero
+            v[4 * i] = u.x; v[4 * i + 1] = u.y; v[4 * i + 2] = u.z; v[4 * i + 3] = u.w;
         }
         st_row_tile<C::CW>(sA, row, c0, C::S, v);
         fence_proxy_async();
@@ -112,7 +127,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const float* __restrict
                 st_bf16x8(pq + r * 2 * H + H + c0 + i, qv + i);
             }
         }
-        __syncthreads();   // sA and TMEM are reused by the next tile
+        fence_proxy_async();   // generic reads of the x stage precede its next TMA write
+        __syncthreads();       // sA, the x stage and TMEM are reused
     }
     tc_fence_before();
     __syncthreads();
@@ -903,13 +919,14 @@ struct NodeFwdArgs {
     float eps;
 };
 
-template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
+template <int H, bool PF>
+__global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__ CUtensorMap tmap_a,
+                                                        const __grid_constant__ CUtensorMap tmap_x, NodeFwdArgs A) {
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     const int n_lin = A.mlp.n_lin;
-    const NodeFwdSmem L = node_fwd_smem<H>(n_lin);
+    const NodeFwdSmem L = node_fwd_smem<H, PF>(n_lin);
     uint8_t* sW0 = sm + L.w0;
     uint8_t* sW = sm + L.w;
     uint8_t* sA0 = sm + L.a0;
@@ -917,6 +934,9 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
     float* sPar = reinterpret_cast<float*>(sm + L.par);
     float* sRed = reinterpret_cast<float*>(sm + L.red);
     uint64_t* bar_mma = reinterpret_cast<uint64_t*>(sm + L.bar);
+    uint64_t* full = bar_mma + 1;   // full[2]: FP32 input stage landed (prefetch)
+    constexpr uint32_t XB = 128 * H * 4;
+    auto sXa = [&](int s) { return sm + L.xs + s * 2 * XB; };   // a* rows, then x rows
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
     constexpr int S2 = span_of(2 * H);
 
@@ -929,6 +949,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
     }
     if (tid == 0) {
         mbar_init(bar_mma, 1);
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
         fence_mbar_init();
     }
     load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
@@ -946,12 +968,34 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
     uint32_t ph = 0;
     bool ok = true;
     const int64_t n_tiles = (A.n_rows + 127) / 128;
+    auto issue = [&](int s, int64_t t) {   // thread 0: the FP32 a* and x rows of tile t
+        mbar_arrive_expect_tx(full + s, 2 * XB);
+        tma_f32_tile<H>(sXa(s), &tmap_a, t * 128, full + s);
+        tma_f32_tile<H>(sXa(s) + XB, &tmap_x, t * 128, full + s);
+    };
+    if constexpr (PF) {
+        if (tid == 0 && (int64_t)blockIdx.x < n_tiles) issue(0, blockIdx.x);
+    }
+    int j = 0;
 
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
+        const int st = j & 1;
         float xa[C::CW], xv[C::CW];
-        if (valid) {
+        if constexpr (PF) {
+            ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
+            if (!ok) break;
+            // the other stage was read by the previous tile (ordered by its closing barrier)
+            if (tid == 0 && t + gridDim.x < n_tiles) issue(st ^ 1, t + gridDim.x);
+#pragma unroll
+            for (int i = 0; i < C::CW / 4; ++i) {   // rows past n_rows read as zero
+                const float4 u = ld_f32x4_tile<H>(sXa(st), row, c0 + 4 * i);
+                const float4 w = ld_f32x4_tile<H>(sXa(st) + XB, row, c0 + 4 * i);
+                xa[4 * i] = u.x; xa[4 * i + 1] = u.y; xa[4 * i + 2] = u.z; xa[4 * i + 3] = u.w;
+                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+            }
+        } else if (valid) {
             const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
             const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
 #pragma unroll
@@ -1037,6 +1081,10 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
             float4* po = reinterpret_cast<float4*>(A.x_out + r * H + c0);
 #pragma unroll
             for (int i = 0; i < C::CW / 4; ++i) {
+                if constexpr (PF) {   // the residual x from the stage (not kept in registers)
+                    const float4 w = ld_f32x4_tile<H>(sXa(st) + XB, row, c0 + 4 * i);
+                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                }
                 float4 o;
                 o.x = xv[4 * i] + (v[4 * i] - mean) * rstd * gam[4 * i] + bet[4 * i];
                 o.y = xv[4 * i + 1] + (v[4 * i + 1] - mean) * rstd * gam[4 * i + 1] + bet[4 * i + 1];
@@ -1045,6 +1093,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(NodeFwdArgs A) {
                 po[i] = o;
             }
         }
+        if constexpr (PF) fence_proxy_async();   // generic reads of the stage precede its next TMA write
         __syncthreads();
     }
     tc_fence_before();
@@ -1089,11 +1138,14 @@ int proj_h(const gnn_graph_dev& G, const gnn_mp_params& W, const float* x_in, __
     if (NR == 0) return GNN_OK;
     const ProjSmem L = proj_smem<H>();
     int grid;
-    int rc = persistent_grid(k_proj_fwd<H>, C::NT, L.total, 2 * H < 32 ? 32 : 2 * H, (NR + 127) / 128, &grid);
+    CUtensorMap tmx;
+    int rc = make_f32_tmap(&tmx, x_in, NR, H);
+    if (rc) return rc;
+    rc = persistent_grid(k_proj_fwd<H>, C::NT, L.total, 2 * H < 32 ? 32 : 2 * H, (NR + 127) / 128, &grid);
     if (rc) return rc;
     {
         ProfScope _ps(s, "k_proj_fwd");
-        k_proj_fwd<H><<<grid, C::NT, L.total, s>>>(x_in, NR, W.edge.W[0], pq);
+        k_proj_fwd<H><<<grid, C::NT, L.total, s>>>(tmx, NR, W.edge.W[0], pq);
     }
     GNN_LAUNCH_CHECK("k_proj_fwd");
     return GNN_OK;
@@ -1175,13 +1227,26 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
     A.n_rows = NR;
     A.mlp = mlp_dev(W.node);
     A.eps = cfg.ln_eps;
-    const NodeFwdSmem L = node_fwd_smem<H>(W.node.n_lin);
     int grid;
-    int rc = persistent_grid(k_node_fwd<H>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
+    CUtensorMap tma, tmx;
+    int rc = make_f32_tmap(&tma, a, NR, H);
+    if (rc) return rc;
+    if ((rc = make_f32_tmap(&tmx, x_in, NR, H))) return rc;
+    // prefetching stages when they fit beside the weights (H <= 64), else one tile at a time
+    const NodeFwdSmem Lp = node_fwd_smem<H, true>(W.node.n_lin);
+    const bool pf = H <= 64 && Lp.total <= 227 * 1024;
+    const NodeFwdSmem L = pf ? Lp : node_fwd_smem<H, false>(W.node.n_lin);
+    if (pf)
+        rc = persistent_grid(k_node_fwd<H, true>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
+    else
+        rc = persistent_grid(k_node_fwd<H, false>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
     if (rc) return rc;
     {
         ProfScope _ps(s, "k_node_fwd");
-        k_node_fwd<H><<<grid, C::NT, L.total, s>>>(A);
+        if (pf)
+            k_node_fwd<H, true><<<grid, C::NT, L.total, s>>>(tma, tmx, A);
+        else
+            k_node_fwd<H, false><<<grid, C::NT, L.total, s>>>(tma, tmx, A);
     }
     GNN_LAUNCH_CHECK("k_node_fwd");
     return GNN_OK;

@@ -110,6 +110,24 @@ __device__ __forceinline__ void ld_acc(uint32_t tmem, int q, int c0, float* v) {
     tmem_ld_wait();
 }
 
+// FP32 node-row tile loaded by make_f32_tmap boxes (128 rows x BW columns
+// each, BW = min(H, 32), swizzled over BW*4 bytes): four floats at (r, c..c+3).
+template <int H>
+__device__ __forceinline__ float4 ld_f32x4_tile(const uint8_t* tile, int r, int c) {
+    constexpr int BW = H < 32 ? H : 32, SB = BW * 4;
+    const uint32_t o = (uint32_t)r * SB + (uint32_t)(c % BW) * 4;
+    const uint32_t sw = o ^ (((o >> 7) & (uint32_t)(SB / 16 - 1)) << 4);
+    return *reinterpret_cast<const float4*>(tile + (uint32_t)(c / BW) * 128 * SB + sw);
+}
+
+// Issue the TMA loads of the FP32 node-row tile starting at row r0 (H/BW boxes).
+template <int H>
+__device__ __forceinline__ void tma_f32_tile(uint8_t* dst, const CUtensorMap* map, int64_t r0, uint64_t* bar) {
+    constexpr int BW = H < 32 ? H : 32;
+#pragma unroll
+    for (int b = 0; b < H / BW; ++b) tma_load_2d(dst + b * 128 * BW * 4, map, b * BW, (int32_t)r0, bar);
+}
+
 // Physical 16-byte chunk of staging chunk c of edge row e (NC chunks of four
 // FP32 per row): the rows of one 8-thread shared-memory phase hit distinct banks.
 template <int NC>
@@ -195,8 +213,11 @@ __host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin) {
 }
 
 struct NodeFwdSmem {
-    uint32_t w0, w, a0, a1, par, red, bar, tm, total;
+    uint32_t w0, w, a0, a1, par, red, xs, bar, tm, total;
 };
+
+// Node-forward input staging (PF): two stages of the FP32 [a* | x] rows of a
+// tile ([128 x H] each), loaded by TMA one tile ahead; used when they fit.
 
 // H = 128 streams the [a*, x] input through one [128 x H] buffer in two K
 // halves (the whole 2H-wide tile would not fit next to the weights).
@@ -205,7 +226,7 @@ struct NodeSplit {
     static constexpr bool value = H >= 128;
 };
 
-template <int H>
+template <int H, bool PF = false>
 __host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin) {
     using C = Cfg<H>;
     constexpr bool split = NodeSplit<H>::value;
@@ -216,14 +237,15 @@ __host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin) {
     s.a1 = split ? s.a0 : s.a0 + 2 * C::TILE;          // split: the chain reuses the input buffer
     s.par = align_up(s.a1 + C::TILE, 16);
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 2 * C::CG * 128 * 4, 8);
-    s.tm = s.bar + 16;
+    s.xs = align_up(s.red + 2 * C::CG * 128 * 4, 1024);
+    s.bar = align_up(s.xs + (PF ? 2 * 2 * 128 * H * 4 : 0), 8);   // mma, full[2]
+    s.tm = s.bar + 24;
     s.total = s.tm + 16 + 1024;
     return s;
 }
 
 struct ProjSmem {
-    uint32_t w, a, bar, tm, total;
+    uint32_t w, a, x, bar, tm, total;
 };
 
 template <int H>
@@ -232,8 +254,9 @@ __host__ __device__ inline ProjSmem proj_smem() {
     ProjSmem s;
     s.w = 0;                                          // [2H x H]: W1a rows then W1b rows
     s.a = align_up(s.w + 2 * C::WT, 1024);
-    s.bar = align_up(s.a + C::TILE, 8);
-    s.tm = s.bar + 16;
+    s.x = align_up(s.a + C::TILE, 1024);              // 2 stages of FP32 x rows [128 x H]
+    s.bar = align_up(s.x + 2 * 128 * H * 4, 8);       // full[2], mma
+    s.tm = s.bar + 24;
     s.total = s.tm + 16 + 1024;
     return s;
 }
@@ -280,6 +303,26 @@ inline int make_row_tmap(CUtensorMap* m, const void* base, int64_t rows, int H) 
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GNN_REQUIRE(r == CUDA_SUCCESS, GNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GNN_OK;
+}
+
+// Tensor map over a [rows x H] FP32 row-major matrix for node-row tiles:
+// box = 128 rows x min(H, 32) columns, swizzled over the box width (128 or
+// 64 bytes), so that one thread per row reads its columns without bank
+// conflicts (ld_f32x4_tile).
+inline int make_f32_tmap(CUtensorMap* m, const void* base, int64_t rows, int H) {
+    EncodeTiledFn enc = encode_fn();
+    GNN_REQUIRE(enc, GNN_ECUDA, "cuTensorMapEncodeTiled is not available");
+    GNN_REQUIRE(((uintptr_t)base & 15) == 0, GNN_EINVAL, "node buffer must be 16-byte aligned for TMA");
+    const int bw = H < 32 ? H : 32;
+    cuuint64_t dims[2] = {(cuuint64_t)H, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)H * 4};
+    cuuint32_t box[2] = {(cuuint32_t)bw, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, bw == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     GNN_REQUIRE(r == CUDA_SUCCESS, GNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GNN_OK;
 }

@@ -309,6 +309,13 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     const int64_t n_tiles = (A.n_rows + 127) / 128;
 
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        if (tid == 0 && t + gridDim.x < n_tiles) {   // the next tile's input rows into L2
+            const int64_t rn = (t + gridDim.x) * 128;
+            const uint32_t nb = (uint32_t)(std::min<int64_t>(128, A.n_rows - rn) * H * 4);
+            prefetch_l2(A.a_star + rn * H, nb);
+            prefetch_l2(A.x + rn * H, nb);
+            prefetch_l2(A.dx_out + rn * H, nb);
+        }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
         float xv[CW], av[CW], gv[CW];
@@ -915,6 +922,12 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
     const int64_t n_tiles = (A.n_rows + 127) / 128;
 
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        if (tid == 0 && t + gridDim.x < n_tiles) {   // the next tile's input rows into L2
+            const int64_t rn = (t + gridDim.x) * 128;
+            const int64_t nr = std::min<int64_t>(128, A.n_rows - rn);
+            prefetch_l2(A.dP + rn * H, (uint32_t)(nr * H * 4));
+            prefetch_l2(A.x + rn * H, (uint32_t)(nr * H * 4));
+        }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
         float dp[CW], dq[CW], xv[CW];

@@ -224,8 +224,9 @@ typedef struct gnn_mp_params {
 #define GNN_FLAG_NO_EDGE_OUT 1  /* forward: do not write e_out (last layer in inference)  */
 
 /* Launch choices of the fused BF16 edge forward. Every choice computes the
- * same arithmetic in the same summation order; results agree to FP32
- * rounding (instruction contraction may differ). 0 = library default. */
+ * same arithmetic; FP32 results agree to rounding (instruction pairing and
+ * contraction differ), so a value rounded to BF16 afterwards (edge state, MMA
+ * operands) can differ in its last bit. 0 = library default. */
 #define GNN_EDGE_FWD_AUTO 0   /* RT for H <= 64, ONE for H = 128                                */
 #define GNN_EDGE_FWD_RT   1   /* record-tiled consumer groups, P|Q rows prefetched (H <= 64)   */
 #define GNN_EDGE_FWD_WS   2   /* producer warp + two consumer groups (H <= 64)                 */

@@ -801,7 +801,12 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                         unpack_bf16x2(uq.z, qv[4], qv[5]);
                         unpack_bf16x2(uq.w, qv[6], qv[7]);
 #pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) v[8 * kc + jj] += (pv[jj] + qv[jj]) + bk[8 * kc + jj];
+                        for (int jj = 0; jj < 8; jj += 2) {
+                            const float2 pq2 = __fadd2_rn(make_float2(pv[jj], pv[jj + 1]), make_float2(qv[jj], qv[jj + 1]));
+                            const float2 t2 = __fadd2_rn(pq2, *reinterpret_cast<const float2*>(bk + 8 * kc + jj));
+                            float2* vv = reinterpret_cast<float2*>(v + 8 * kc + jj);
+                            *vv = __fadd2_rn(*vv, t2);
+                        }
                     }
                 }
                 // the slot is consumed: request the group's next tile (its record landed a tile ago)
@@ -809,12 +814,10 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                     if (mbar_wait(full + (s ^ 1), (uint32_t)((u + 1) >> 1) & 1u)) gather(s ^ 1);
                 }
             } else {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] += bk[i];
+                add_bias2<CW>(v, bk);
             }
             if (k < n_lin - 1) {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
+                elu_inplace2<CW>(v);
                 st_row_tile<CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -830,14 +833,15 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
         tc_fence_before();
         float mean, rstd;
         if constexpr (CG == 1) {
-            float su = 0.f, sq = 0.f;
+            float2 su2 = make_float2(0.f, 0.f), sq2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < CW; ++i) {
-                su += v[i];
-                sq += v[i] * v[i];
+            for (int i = 0; i < CW; i += 2) {
+                const float2 x2 = make_float2(v[i], v[i + 1]);
+                su2 = __fadd2_rn(su2, x2);
+                sq2 = __ffma2_rn(x2, x2, sq2);
             }
-            mean = su * (1.f / H);
-            rstd = rsqrtf(fmaxf(sq * (1.f / H) - mean * mean, 0.f) + A.eps);
+            mean = (su2.x + su2.y) * (1.f / H);
+            rstd = rsqrtf(fmaxf((sq2.x + sq2.y) * (1.f / H) - mean * mean, 0.f) + A.eps);
         } else {
             row_stats_named<H, CG, CW>(v, sRed, row, cg, A.eps, bid, GT, mean, rstd);
         }
@@ -846,8 +850,16 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
             ld_row_tile<CW>(sE, row, c0, C::S, eo);
             const float* gam = sPar + n_lin * H + c0;
             const float* bet = sPar + (n_lin + 1) * H + c0;
+            const float2 r2 = make_float2(rstd, rstd), m2 = make_float2(-mean * rstd, -mean * rstd);
 #pragma unroll
-            for (int i = 0; i < CW; ++i) v[i] = eo[i] + (v[i] - mean) * rstd * gam[i] + bet[i];
+            for (int i = 0; i < CW; i += 2) {
+                const float2 xh = __ffma2_rn(make_float2(v[i], v[i + 1]), r2, m2);
+                const float2 y = __ffma2_rn(xh, *reinterpret_cast<const float2*>(gam + i),
+                                            *reinterpret_cast<const float2*>(bet + i));
+                const float2 o = __fadd2_rn(y, make_float2(eo[i], eo[i + 1]));
+                v[i] = o.x;
+                v[i + 1] = o.y;
+            }
         }
         if (valid && A.e_out) {
 #pragma unroll

@@ -883,9 +883,19 @@ struct ProjBwdArgs {
     int64_t n_rows;
 };
 
+// Thread layout: 128 rows x H/32 column groups of 32 columns (two CTAs per SM).
 template <int H>
-__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
-    using C = CfgB<H>;
+struct CfgP {
+    static constexpr int S = span_of(H);
+    static constexpr int S2 = span_of(2 * H);
+    static constexpr int CG = H >= 32 ? H / 32 : 1;
+    static constexpr int CW = H / CG;
+    static constexpr int NT = 128 * CG;
+};
+
+template <int H>
+__global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
+    using C = CfgP<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     const ProjBwdSmem P = proj_bwd_smem<H>();
@@ -930,34 +940,27 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
         }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
-        float dp[CW], dq[CW], xv[CW];
+        float dq[CW];
 #pragma unroll
-        for (int i = 0; i < CW; ++i) dp[i] = dq[i] = xv[i] = 0.f;
+        for (int i = 0; i < CW; ++i) dq[i] = 0.f;
         if (valid) {
-            const float4* pp = reinterpret_cast<const float4*>(A.dP + r * H + c0);
-            const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
-#pragma unroll
-            for (int i = 0; i < CW / 4; ++i) {
-                float4 u = __ldg(pp + i), w = __ldg(px + i);
-                dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
-                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
-            }
-            // sender-side sum in edge order; the edge ids and then the dz1 rows of up to
-            // four edges are requested together so their latencies overlap
+            // sender-side sum in edge order; the edge ids and then the dz1 rows of UB
+            // edges are requested together so their latencies overlap
+            constexpr int UB = CW >= 32 ? 2 : 4;
             const int32_t k0 = A.t_ptr[r], k1 = A.t_ptr[r + 1];
-            for (int32_t kb = k0; kb < k1; kb += 4) {
-                int64_t e[4];
+            for (int32_t kb = k0; kb < k1; kb += UB) {
+                int64_t e[UB];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) e[u] = kb + u < k1 ? (int64_t)__ldg(A.t_eid + kb + u) : -1;
-                uint4 z[4][CW / 8];
+                for (int u = 0; u < UB; ++u) e[u] = kb + u < k1 ? (int64_t)__ldg(A.t_eid + kb + u) : -1;
+                uint4 z[UB][CW / 8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < UB; ++u)
 #pragma unroll
                     for (int i = 0; i < CW / 8; ++i)
                         z[u][i] = e[u] >= 0 ? __ldg(reinterpret_cast<const uint4*>(A.dz1 + e[u] * H + c0) + i)
                                             : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < UB; ++u) {
                     if (e[u] < 0) break;
 #pragma unroll
                     for (int i = 0; i < CW / 8; ++i) {
@@ -973,11 +976,25 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_proj_bwd(ProjBwdArgs A) {
             }
         }
 #pragma unroll
-        for (int i = 0; i < CW; i += 8) {
-            st_tile8(sA, row, c0 + i, 128, S2, dp + i);
-            st_tile8(sA, row, H + c0 + i, 128, S2, dq + i);
+        for (int i = 0; i < CW; i += 8) st_tile8(sA, row, H + c0 + i, 128, S2, dq + i);
+        {
+            float dp[CW], xv[CW];
+#pragma unroll
+            for (int i = 0; i < CW; ++i) dp[i] = xv[i] = 0.f;
+            if (valid) {
+                const float4* pp = reinterpret_cast<const float4*>(A.dP + r * H + c0);
+                const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+#pragma unroll
+                for (int i = 0; i < CW / 4; ++i) {
+                    float4 u = __ldg(pp + i), w = __ldg(px + i);
+                    dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
+                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) st_tile8(sA, row, c0 + i, 128, S2, dp + i);
+            st_row_tile<CW>(sX, row, c0, S, xv);
         }
-        st_row_tile<CW>(sX, row, c0, S, xv);
         fence_proxy_async();
         tc_fence_before();
         __syncthreads();
@@ -1095,8 +1112,10 @@ BwdWs carve_bwd(void* ws, const gnn_graph_dev& G, int H, int Le, int Ln, bool ne
     w.da = (float*)take((size_t)NR * H * 4);
     w.dP = (float*)take((size_t)NR * H * 4);
     w.dz1 = (__nv_bfloat16*)take((size_t)E * H * 2);
-    const int64_t ps = std::max(edge_pstride(H, Le), std::max(node_pstride(H, Ln), proj_pstride(H)));
-    w.part = (float*)take((size_t)ncta * ps * 4);
+    // per-CTA weight-gradient partials: one CTA per SM for the edge and node kernels,
+    // up to two per SM for the projection kernel
+    const int64_t ps = std::max(edge_pstride(H, Le), node_pstride(H, Ln));
+    w.part = (float*)take((size_t)std::max(ncta * ps, 2 * ncta * proj_pstride(H)) * 4);
     w.bytes = off + 256;
     return w;
 }
@@ -1256,12 +1275,12 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.n_rows = NR;
         const ProjBwdSmem P = proj_bwd_smem<H>();
         int grid;
-        rc = persistent_grid(k_proj_bwd<H>, C::NT, P.total, pow2_cols(2 * H), (NR + 127) / 128, &grid);
+        rc = persistent_grid(k_proj_bwd<H>, CfgP<H>::NT, P.total, pow2_cols(2 * H), (NR + 127) / 128, &grid);
         if (rc) return rc;
-        grid = std::min(grid, nsm);
+        grid = std::min(grid, 2 * nsm);
         {
             ProfScope _ps(s, "k_proj_bwd");
-            k_proj_bwd<H><<<grid, C::NT, P.total, s>>>(A);
+            k_proj_bwd<H><<<grid, CfgP<H>::NT, P.total, s>>>(A);
         }
         GNN_LAUNCH_CHECK("k_proj_bwd");
         RedSeg seg[2];

@@ -61,6 +61,31 @@ __device__ __forceinline__ float elu1_fast(float z) {
     return fmaxf(z, ex2_sfu(fminf(z, 0.f) * 1.4426950408889634f) - 1.f);
 }
 
+// Paired forms on the packed FP32 pipe (two lanes per instruction).
+__device__ __forceinline__ float2 elu1_fast2(float2 z) {
+    const float2 m = make_float2(fminf(z.x, 0.f), fminf(z.y, 0.f));
+    const float2 t = __fmul2_rn(m, make_float2(1.4426950408889634f, 1.4426950408889634f));
+    const float2 e = __fadd2_rn(make_float2(ex2_sfu(t.x), ex2_sfu(t.y)), make_float2(-1.f, -1.f));
+    return make_float2(fmaxf(z.x, e.x), fmaxf(z.y, e.y));
+}
+
+// v[i] += b[i] for CW values (CW even, b 8-byte aligned).
+template <int CW>
+__device__ __forceinline__ void add_bias2(float* v, const float* b) {
+    float2* v2 = reinterpret_cast<float2*>(v);
+    const float2* b2 = reinterpret_cast<const float2*>(b);
+#pragma unroll
+    for (int i = 0; i < CW / 2; ++i) v2[i] = __fadd2_rn(v2[i], b2[i]);
+}
+
+// v = ELU(v) for CW values.
+template <int CW>
+__device__ __forceinline__ void elu_inplace2(float* v) {
+    float2* v2 = reinterpret_cast<float2*>(v);
+#pragma unroll
+    for (int i = 0; i < CW / 2; ++i) v2[i] = elu1_fast2(v2[i]);
+}
+
 // dL/dz of h = ELU(z) from the output: dh for h > 0, dh (h + 1) = dh e^z otherwise.
 __device__ __forceinline__ float elu1_bwd_from_out(float dh, float h) { return fmaf(dh, fminf(h, 0.f), dh); }
 

@@ -104,8 +104,11 @@ def test_edge_forward_kernel_choices_agree(H):
         outs[(variant, cps)] = (xo, eo, a)
     ref = outs[(B.GNN_EDGE_FWD_RT, 0)]
     for k, o in outs.items():
-        for u, v in zip(o, ref):
-            assert rel_l2(u, v) < 1e-5, k
+        # the FP32 aggregate to FP32 rounding; the BF16 edge state, and the node state computed
+        # from BF16 operands, may differ where a last-bit FP32 difference flips a BF16 rounding
+        assert rel_l2(o[2], ref[2]) < 1e-5, k
+        assert rel_l2(o[0], ref[0]) < 1e-4, k
+        assert rel_l2(o[1], ref[1]) < 1e-4 and np.mean(o[1] != ref[1]) < 1e-3, k
 
 
 def test_edge_forward_kernel_choice_validation():

@@ -1066,12 +1066,9 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
             tc_fence_after();
             if (!ok) break;
             ld_acc<C::CW>(tmem, q, c0, v);
-            const float* bk = sPar + k * H + c0;
-#pragma unroll
-            for (int i = 0; i < C::CW; ++i) v[i] += bk[i];
+            add_bias2<C::CW>(v, sPar + k * H + c0);
             if (k < n_lin - 1) {
-#pragma unroll
-                for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
+                elu_inplace2<C::CW>(v);
                 st_row_tile<C::CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();

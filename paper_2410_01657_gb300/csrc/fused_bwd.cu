@@ -355,11 +355,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             tc_fence_after();
             if (!ok) break;
             ld_acc<CW>(tWork, q, c0, v);
-#pragma unroll
-            for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
+            add_bias2<CW>(v, sPar + k * H + c0);
             if (k < L - 1) {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
+                elu_inplace2<CW>(v);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
                 fence_proxy_async();
                 tc_fence_before();
@@ -422,8 +420,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                 float dh[CW], hv[CW];
                 ld_acc<CW>(tWork, q, c0, dh);
                 ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
-#pragma unroll
-                for (int i = 0; i < CW; ++i) dz[i] = elu1_bwd_from_out(dh[i], hv[i]);
+                elu_bwd2<CW>(dz, dh, hv);
             } else {
                 float da[CW], dxp[CW];
                 ld_acc<CW>(tWork, q, c0, da);
@@ -675,22 +672,21 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                             float p0, p1, q0, q1;
                             unpack_bf16x2(pw[h], p0, p1);
                             unpack_bf16x2(qw[h], q0, q1);
-                            v[8 * kc + 2 * h] += (p0 + q0) + sPar[c0 + 8 * kc + 2 * h];
-                            v[8 * kc + 2 * h + 1] += (p1 + q1) + sPar[c0 + 8 * kc + 2 * h + 1];
+                            const float2 t2 = __fadd2_rn(__fadd2_rn(make_float2(p0, p1), make_float2(q0, q1)),
+                                                         *reinterpret_cast<const float2*>(sPar + c0 + 8 * kc + 2 * h));
+                            float2* vv = reinterpret_cast<float2*>(v + 8 * kc + 2 * h);
+                            *vv = __fadd2_rn(*vv, t2);
                         }
                     }
                 } else {
-#pragma unroll
-                    for (int i = 0; i < CW; ++i) v[i] += sPar[c0 + i];
+                    add_bias2<CW>(v, sPar + c0);
                 }
 
             } else {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] += sPar[k * H + c0 + i];
+                add_bias2<CW>(v, sPar + k * H + c0);
             }
             if (k < L - 1) {
-#pragma unroll
-                for (int i = 0; i < CW; ++i) v[i] = elu1_fast(v[i]);
+                elu_inplace2<CW>(v);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
                 handoff([&] { issue_mma(tWork, sHB + k * C::TILE, sW + (k + 1) * C::WT, H, H); }, bar);
             }
@@ -816,8 +812,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             if (k > 0) {
                 float hv[CW];
                 ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
-#pragma unroll
-                for (int i = 0; i < CW; ++i) dz[i] = elu1_bwd_from_out(dh[i], hv[i]);
+                elu_bwd2<CW>(dz, dh, hv);
             } else if (valid) {
                 float o[CW];
 #pragma unroll

@@ -86,6 +86,18 @@ __device__ __forceinline__ void elu_inplace2(float* v) {
     for (int i = 0; i < CW / 2; ++i) v2[i] = elu1_fast2(v2[i]);
 }
 
+// dz = dL/dz of h = ELU(z) from dh and the output h, in pairs (see elu1_bwd_from_out).
+template <int CW>
+__device__ __forceinline__ void elu_bwd2(float* dz, const float* dh, const float* h) {
+#pragma unroll
+    for (int i = 0; i < CW; i += 2) {
+        const float2 d = make_float2(dh[i], dh[i + 1]);
+        const float2 r = __ffma2_rn(d, make_float2(fminf(h[i], 0.f), fminf(h[i + 1], 0.f)), d);
+        dz[i] = r.x;
+        dz[i + 1] = r.y;
+    }
+}
+
 // dL/dz of h = ELU(z) from the output: dh for h > 0, dh (h + 1) = dh e^z otherwise.
 __device__ __forceinline__ float elu1_bwd_from_out(float dh, float h) { return fmaf(dh, fminf(h, 0.f), dh); }
 

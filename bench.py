@@ -188,22 +188,23 @@ def load_peaks() -> dict:
 
 # ---------------------------------------------------------------- oracle timing (CPU)
 
-def oracle_sample(n_el: int, steps: int = 1):
-    """Time the FP64 oracle on an n_el^3 p=5 brick (8 RCB parts, H=64, 4 layers fwd+bwd).
-    Returns (edges/s in the metric's unit, seconds per step, sample description, threads)."""
+def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts: int = R, fwd_only: bool = False):
+    """Time the FP64 oracle on an n_el^3 brick of order p (RCB parts, 4 layers of
+    width `hidden`, forward + backward unless fwd_only): a bounded sample of a
+    workload family. Returns (edges/s, seconds per step, description, threads)."""
     import numpy as np
 
     import synthetic as syn
     from oracle import graph as og
     from oracle import model as om
 
-    b = og.build_brick((n_el,) * 3, P)
-    subs = og.build_subgraphs(b, og.partition_rcb(b, R), R)
-    params = syn.gnn_params(SEED, H, NH, M)
+    b = og.build_brick((n_el,) * 3, p)
+    subs = og.build_subgraphs(b, og.partition_rcb(b, parts), parts)
+    params = syn.gnn_params(SEED, hidden, NH, M)
     rng = np.random.default_rng(1)
-    xg = rng.standard_normal((b.n_nodes, H))
+    xg = rng.standard_normal((b.n_nodes, hidden))
     xs = [xg[sg.gid] for sg in subs]
-    es = [rng.standard_normal((sg.n_edges, H)) for sg in subs]
+    es = [rng.standard_normal((sg.n_edges, hidden)) for sg in subs]
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
@@ -211,15 +212,16 @@ def oracle_sample(n_el: int, steps: int = 1):
         for lp in params["layers"]:
             x, e, c = om.layer_forward(lp, subs, x, e)
             caches.append(c)
-        dx = [np.ones_like(a) for a in x]
-        de = [np.zeros_like(a) for a in e]
-        for li in range(M - 1, -1, -1):
-            dx, de, _ = om.layer_backward(params["layers"][li], subs, caches[li], dx, de)
+        if not fwd_only:
+            dx = [np.ones_like(a) for a in x]
+            de = [np.zeros_like(a) for a in e]
+            for li in range(M - 1, -1, -1):
+                dx, de, _ = om.layer_backward(params["layers"][li], subs, caches[li], dx, de)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
     return (b.n_edges * M / t, t,
-            f"{n_el}^3 elements p=5 ({b.n_nodes} nodes, {b.n_edges} edges), 8 RCB parts, H=64, "
-            f"4 layers fwd+bwd, FP64 numpy", _blas_threads())
+            f"{n_el}^3 elements p={p} ({b.n_nodes} nodes, {b.n_edges} edges), {parts} RCB parts, H={hidden}, "
+            f"4 layers {'fwd' if fwd_only else 'fwd+bwd'}, FP64 numpy", _blas_threads())
 
 
 def _blas_threads() -> int:
@@ -470,6 +472,17 @@ def main():
                 "frac": ach / peak, "traffic": None, "peak_src": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock",
                 "share": top_ms / total_ms}
 
+    # the cost of consistency: the same stack with Eq. 5c-5d skipped (the paper's "None" layers)
+    from paper_2410_01657_gb300 import binding as Bd
+    for c in (stack.cfg, stack.cfg_last):
+        c.halo_mode = Bd.GNN_HALO_NONE
+    stack.graph = None
+    ms_none, _, _ = time_stack(stack, dx_top, max(3, args.steps // 2), 2, profile=False)
+    for c in (stack.cfg, stack.cfg_last):
+        c.halo_mode = Bd.GNN_HALO_SYNC
+    inconsistent = {"ms_per_step": ms_none, "cost_of_consistency": (ms_eager or ms) / ms_none,
+                    "note": "same stack without the halo swap + sync (inconsistent layers), eager"}
+
     fp32 = None
     if precision == "bf16" and not args.no_fp32 and wl["inputs"] == "encoders":
         del stack
@@ -490,7 +503,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, tsec, desc, threads = oracle_sample(6)
+        # a bounded sample of the same workload family: a small brick of the same order,
+        # width, partition count and pass (about 5-20 s of host time)
+        n_s = {5: 6, 7: 4}[wl["p"]]
+        v, tsec, desc, threads = oracle_sample(n_s, p=wl["p"], hidden=Hw, parts=wl["parts"] if wl["parts"] <= 16 else 8,
+                                               fwd_only=fwd_only)
         cpu = {"value": v, "unit": "edges/s", "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": tsec}
 
@@ -509,7 +526,7 @@ def main():
                            else "eager steps",
                            "parallelism": f"replicas x{world}"},
                 "nodes_per_s": world * n_unpart * M / (ms * 1e-3),
-                "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu,
+                "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu, "inconsistent": inconsistent,
                 "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
                 "clocks": clk.summary()}
         if ms_eager is not None:

@@ -1,0 +1,55 @@
+"""The paper's consistency property on the GPU path (Sec. II-B, Eq. 2; Fig. 5).
+
+A network of consistent NMP layers gives the same loss for every number of
+sub-graphs R; the same network with the halo swap + sync skipped (the paper's
+"None" layers) does not, and its error grows as the sub-graphs get smaller."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from paper_2410_01657_gb300 import _build
+from paper_2410_01657_gb300 import binding as B
+from paper_2410_01657_gb300 import nn as gnn
+from paper_2410_01657_gb300.graph import MeshGraph
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+RS = (1, 2, 4, 8, 16, 32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.load()
+
+
+def _loss(R, precision, halo, H=16):
+    graph = MeshGraph((8, 8, 8), 1)
+    part = graph.partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(11, H, 2, 4)
+    modes = syn.fourier_modes(11, 8)
+    pos = part.array("row_pos")
+    u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=DEV)
+    t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=DEV)
+    net = gnn.ConsistentGNN(params, precision=precision, halo=halo, device=DEV)
+    with torch.no_grad():
+        y = net(G, u, G.edge_attr())
+        loss = gnn.consistent_loss(y, t, G)
+    B.call("gnn_check", None)
+    return float(loss.item())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 2e-3)])
+def test_consistent_loss_is_independent_of_R(precision, tol):
+    ref = _loss(1, precision, True)
+    for R in RS[1:]:
+        assert abs(_loss(R, precision, True) - ref) <= tol * abs(ref), R
+
+
+def test_inconsistent_layers_drift_with_R():
+    ref = _loss(1, "fp32", False)
+    dev = [abs(_loss(R, "fp32", False) - ref) / abs(ref) for R in RS[1:]]
+    assert min(dev) > 1e-4                 # every partition changes the result
+    assert dev[-1] > 3 * dev[0]             # and more sub-graphs change it more

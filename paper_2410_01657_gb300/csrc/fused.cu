@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__
         if (valid) {
 #pragma unroll
             for (int i = 0; i < C::CW; i += 8) {
-                st_bf16x8(pq + r * 2 * H + c0 + i, pv + i);
-                st_bf16x8(pq + r * 2 * H + H + c0 + i, qv + i);
+                st_bf16x8(pq + r * H + c0 + i, pv + i);
+                st_bf16x8(pq + n_rows * H + r * H + c0 + i, qv + i);
             }
         }
         fence_proxy_async();   // generic reads of the x stage precede its next TMA write
@@ -146,7 +146,8 @@ struct EdgeFwdArgs {
     const uint8_t* tile_meta;   // per-tile records (GNN_TILE_META_BYTES each)
     int64_t n_tiles;
     int64_t n_edges;
-    const __nv_bfloat16* pq;
+    const __nv_bfloat16* pq;    // P rows [n_rows x H]
+    const __nv_bfloat16* q;     // Q rows [n_rows x H] (pq + n_rows*H)
     __nv_bfloat16* e_out;
     float* a;
     MlpDev mlp;
@@ -228,8 +229,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < C::CW; i += 8) {
                 float pv[8], qv[8];
-                ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
-                ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
+                ld_bf16x8(A.pq + rcv * H + c0 + i, pv);
+                ld_bf16x8(A.q + snd * H + c0 + i, qv);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) pq[i + j] = pv[j] + qv[j];
             }
@@ -522,8 +523,8 @@ __global__ void __launch_bounds__(WsCfg<H>::NT, 1)
 #pragma unroll
                 for (int i = 0; i < C::CW; i += 8) {
                     float pv[8], qv[8];
-                    ld_bf16x8(A.pq + rcv * 2 * H + c0 + i, pv);
-                    ld_bf16x8(A.pq + snd * 2 * H + H + c0 + i, qv);
+                    ld_bf16x8(A.pq + rcv * H + c0 + i, pv);
+                    ld_bf16x8(A.q + snd * H + c0 + i, qv);
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) pq[i + jj] = pv[jj] + qv[jj];
                 }
@@ -623,7 +624,7 @@ struct RtCfg {
     static constexpr int GT = Cfg<H>::NT;          // threads per group
     static constexpr int NT = NG * GT;
     static constexpr int SC = H / 2;               // columns per segmented-sum pass
-    static constexpr int SLOT = 4 * Cfg<H>::CW;    // bytes of a thread's P|Q slot
+    static constexpr int SLOT = 2 * Cfg<H>::CW;    // bytes of a thread's Q slot
     static constexpr int NCH = SLOT / 16;          // 16-byte chunks per slot
     static constexpr int SWZ_SHIFT = NCH >= 8 ? 0 : (NCH == 4 ? 1 : 2);
     static constexpr uint32_t NCOLS = NG * Cfg<H>::TCOLS < 32 ? 32 : NG * Cfg<H>::TCOLS;
@@ -634,7 +635,8 @@ struct EdgeFwdRtSmem {
 };
 
 // Per group (gsz bytes at grp + g*gsz): e stages [2 x TILE], activation tile
-// (TILE), P|Q slots (2 x TILE), tile records [2 x GNN_TILE_META_BYTES].
+// (TILE), the tile's P rows [128 x H] (TILE), Q slots (TILE), tile records
+// [2 x GNN_TILE_META_BYTES].
 template <int H>
 __host__ __device__ inline EdgeFwdRtSmem edge_fwd_rt_smem(int n_lin) {
     using C = Cfg<H>;
@@ -646,7 +648,7 @@ __host__ __device__ inline EdgeFwdRtSmem edge_fwd_rt_smem(int n_lin) {
     s.grp = align_up(s.red + R::NG * 2 * C::CG * 128 * 4, 1024);
     s.gsz = 5 * C::TILE + 2 * GNN_TILE_META_BYTES;
     s.bar = s.grp + R::NG * s.gsz;
-    s.tm = s.bar + 8 * 3 * R::NG;
+    s.tm = s.bar + 8 * 4 * R::NG;
     s.total = s.tm + 16 + 1024;
     return s;
 }
@@ -682,11 +684,13 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
     const bool elected = gt == 0;
     uint8_t* G = sm + L.grp + g * L.gsz;
     uint8_t* sA1 = G + 2 * C::TILE;
-    uint8_t* sSlot = G + 3 * C::TILE + (cg * 128 + row) * R::SLOT;
+    uint8_t* sP = G + 3 * C::TILE;                                  // P rows of the tile's receivers
+    uint8_t* sSlot = G + 4 * C::TILE + (cg * 128 + row) * R::SLOT;   // this thread's Q columns
     uint8_t* sRec = G + 5 * C::TILE;
     float* sRed = reinterpret_cast<float*>(sm + L.red) + g * 2 * CG * 128;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar) + 3 * g;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar) + 4 * g;
     uint64_t* mbar = full + 2;
+    uint64_t* p_full = full + 3;   // the tile's P rows have landed
 
     if (warp == 0) {
         tmem_alloc(tslot, R::NCOLS);
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
     }
     if (tid == 0) {
         uint64_t* b = reinterpret_cast<uint64_t*>(sm + L.bar);
-        for (int i = 0; i < 3 * R::NG; ++i) mbar_init(b + i, 1);
+        for (int i = 0; i < 4 * R::NG; ++i) mbar_init(b + i, 1);
         fence_mbar_init();
     }
     load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, R::NT);
@@ -721,20 +725,27 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
         for (int kb = 0; kb < (H + 63) / 64; ++kb) tma_load_2d(G + s * C::TILE + kb * 128 * 128, &tmap_e, kb * 64, e0,
                                                                full + s);
     };
-    // this thread's P|Q slot <- tile whose record is in stage s
+    // the receivers' P rows of the tile whose record is in stage s: one bulk copy of the
+    // tile's consecutive rows (elected thread); each thread's Q slot <- the Q row of its
+    // edge's sender, own columns, by cp.async
+    auto fetch_p = [&](int s) {
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(sRec + s * GNN_TILE_META_BYTES);
+        const int32_t nr = min(max(hdr[1] - hdr[0], 0), 128);   // a tile has 1..128 rows
+        const uint32_t bytes = (uint32_t)nr * H * 2;
+        if (bytes == 0) {
+            mbar_arrive(p_full);
+            return;
+        }
+        mbar_arrive_expect_tx(p_full, bytes);
+        bulk_load(sP, A.pq + (int64_t)hdr[0] * H, bytes, p_full);
+    };
     auto gather = [&](int s) {
         const uint8_t* rec = sRec + s * GNN_TILE_META_BYTES;
-        const int32_t ne = reinterpret_cast<const int32_t*>(rec)[3];
-        if (row < ne) {
-            const int64_t rcv = reinterpret_cast<const int32_t*>(rec)[0] + reinterpret_cast<const int16_t*>(rec + 544)[row];
+        if (row < reinterpret_cast<const int32_t*>(rec)[3]) {
             const int64_t snd = reinterpret_cast<const int32_t*>(rec + 800)[row];
-            const __nv_bfloat16* P = A.pq + rcv * 2 * H + c0;
-            const __nv_bfloat16* Q = A.pq + snd * 2 * H + H + c0;
+            const __nv_bfloat16* Q = A.q + snd * H + c0;
 #pragma unroll
-            for (int k = 0; k < NCH / 2; ++k) {
-                cp_async16(sSlot + 16 * slot_chunk<H>(k, row), P + 8 * k);
-                cp_async16(sSlot + 16 * slot_chunk<H>(k + NCH / 2, row), Q + 8 * k);
-            }
+            for (int k = 0; k < NCH; ++k) cp_async16(sSlot + 16 * slot_chunk<H>(k, row), Q + 8 * k);
         }
         cp_async_commit();
     };
@@ -751,10 +762,14 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
     }
     if (t_first < A.n_tiles) {
         ok = mbar_wait(full, 0);
-        if (ok) gather(0);
+        if (ok) {
+            gather(0);
+            if (elected) fetch_p(0);
+        }
     }
+    bool p_pending = elected && t_first < A.n_tiles && ok;   // elected: a P copy not yet consumed
 
-    uint32_t ph_mma = 0;
+    uint32_t ph_mma = 0, ph_p = 0;
     int u = 0;
     for (int64_t t = t_first; t < A.n_tiles && ok; t += stride, ++u) {
         const int s = u & 1;
@@ -777,6 +792,7 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
         const bool valid = row < ne;
         const float w = valid ? reinterpret_cast<const float*>(rec + 1312)[row] : 0.f;
         cp_async_wait_all();
+        bool next_ready = false;   // the next tile's record is in stage s^1
         float v[CW];
         for (int k = 0; k < n_lin && ok; ++k) {
             ok = group_wait(mbar, ph_mma, elected, bid, GT);
@@ -786,12 +802,16 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
             ld_acc<CW>(tm, q, c0, v);
             const float* bk = sPar + k * H + c0;
             if (k == 0) {
+                ok = ok && mbar_wait(p_full, ph_p);   // the tile's P rows
+                ph_p ^= 1;
+                if (elected) p_pending = false;
                 if (valid) {
+                    const uint8_t* prow = sP + (int)reinterpret_cast<const int16_t*>(rec + 544)[row] * (2 * H) + 2 * c0;
 #pragma unroll
-                    for (int kc = 0; kc < NCH / 2; ++kc) {
+                    for (int kc = 0; kc < NCH; ++kc) {
                         float pv[8], qv[8];
-                        const uint4 up = *reinterpret_cast<const uint4*>(sSlot + 16 * slot_chunk<H>(kc, row));
-                        const uint4 uq = *reinterpret_cast<const uint4*>(sSlot + 16 * slot_chunk<H>(kc + NCH / 2, row));
+                        const uint4 up = *reinterpret_cast<const uint4*>(prow + 16 * kc);
+                        const uint4 uq = *reinterpret_cast<const uint4*>(sSlot + 16 * slot_chunk<H>(kc, row));
                         unpack_bf16x2(up.x, pv[0], pv[1]);
                         unpack_bf16x2(up.y, pv[2], pv[3]);
                         unpack_bf16x2(up.z, pv[4], pv[5]);
@@ -809,11 +829,19 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                         }
                     }
                 }
-                // the slot is consumed: request the group's next tile (its record landed a tile ago)
+                // this thread's Q slot is consumed: request the group's next tile's (its record
+                // landed a tile ago)
                 if (t_next < A.n_tiles) {
-                    if (mbar_wait(full + (s ^ 1), (uint32_t)((u + 1) >> 1) & 1u)) gather(s ^ 1);
+                    next_ready = mbar_wait(full + (s ^ 1), (uint32_t)((u + 1) >> 1) & 1u);
+                    ok = ok && next_ready;
+                    if (next_ready) gather(s ^ 1);
                 }
             } else {
+                if (k == 1 && elected && next_ready && ok) {
+                    // every thread has read the P rows (the barrier before this MMA): the next tile's
+                    fetch_p(s ^ 1);
+                    p_pending = true;
+                }
                 add_bias2<CW>(v, bk);
             }
             if (k < n_lin - 1) {
@@ -914,6 +942,7 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
             if (pending & (1u << s)) mbar_wait(full + s, (pending >> (2 + s)) & 1u);
     }
     cp_async_wait_all();
+    if (p_pending) mbar_wait(p_full, ph_p);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1180,6 +1209,7 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.n_tiles = G.n_edge_tiles;
         A.n_edges = E;
         A.pq = pq;
+        A.q = pq + NR * H;
         A.e_out = e_out;
         A.a = a;
         A.mlp = mlp_dev(W.edge);

@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
 struct EdgeBwdArgs {
     const uint8_t* tile_meta;   // per-tile records (GNN_TILE_META_BYTES each)
     int64_t n_tiles;
-    const __nv_bfloat16* pq;
+    const __nv_bfloat16* pq;    // P rows [n_rows x H]
+    const __nv_bfloat16* q;     // Q rows [n_rows x H]
     const float* da;            // gradient of the aggregate after the halo adjoint
     int has_de_out;
     __nv_bfloat16* de_in;
@@ -606,8 +607,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             const int64_t snd = reinterpret_cast<const int32_t*>(rec + 800)[row];
 #pragma unroll
             for (int k = 0; k < NCH / 2; ++k) {
-                cp_async16(slot_at(k), A.pq + rcv * 2 * H + c0 + 8 * k);
-                cp_async16(slot_at(k + NCH / 2), A.pq + snd * 2 * H + H + c0 + 8 * k);
+                cp_async16(slot_at(k), A.pq + rcv * H + c0 + 8 * k);
+                cp_async16(slot_at(k + NCH / 2), A.q + snd * H + c0 + 8 * k);
             }
         }
         cp_async_commit();
@@ -1211,6 +1212,7 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.tile_meta = (const uint8_t*)G.tile_meta;
         A.n_tiles = G.n_edge_tiles;
         A.pq = w.pq;
+        A.q = w.pq + NR * H;
         A.da = w.da;
         A.has_de_out = de_out != nullptr;
         A.de_in = de_in;

@@ -157,7 +157,8 @@ struct EdgeBwdSmem {
 // and, during the recompute, the aggregate gradients da of the tile's
 // receivers (when they fit: nr * H * 4 <= TILE). hb holds the recomputed
 // hidden activations and, once the adjoint no longer reads them, the staging
-// of the segmented sum dP. slot: each thread's P|Q rows for the next tile.
+// of the segmented sum dP. slot: the next tile's P rows [128 x H], then each
+// thread's Q columns for it.
 template <int H>
 __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     using C = CfgB<H>;
@@ -174,8 +175,8 @@ __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     s.slot = align_up(s.ones + 128 * C::S, 1024);
     s.par = s.slot + 2 * C::TILE;
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma, ready, da, wgrad
-    s.tm = s.bar + 48;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma, ready, da, wgrad, P rows
+    s.tm = s.bar + 56;
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
     s.total = end + 1024;
@@ -508,15 +509,17 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     uint64_t* ready = full + 3;     // one arrival per warp: operands written, accumulator read
     uint64_t* da_full = full + 4;   // the tile's da rows have landed in sG
     uint64_t* bar_w = full + 5;     // weight-gradient MMAs of an adjoint step (complete behind the epilogue)
+    uint64_t* p_full = full + 6;    // the tile's P rows have landed in sP
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L) + (LNT ? 2 * H : 0));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
-    constexpr int NCH = 4 * CW / 16;                               // 16-byte chunks of a P|Q slot
-    uint8_t* sSlot = sm + P.slot + (g * 128 + row) * (4 * CW);
-    auto slot_at = [&](int k) { return sSlot + 16 * (k ^ ((row >> (NCH >= 8 ? 0 : 1)) & (NCH - 1))); };
+    constexpr int NCH = 2 * CW / 16;                               // 16-byte chunks of a Q slot
+    uint8_t* sP = sm + P.slot;                                     // P rows of the tile's receivers
+    uint8_t* sSlot = sm + P.slot + C::TILE + (g * 128 + row) * (2 * CW);
+    auto slot_at = [&](int k) { return sSlot + 16 * (k ^ ((row >> (NCH >= 8 ? 0 : (NCH == 4 ? 1 : 2))) & (NCH - 1))); };
 
     if (warp == 0) {
         tmem_alloc(tslot, NCOLS);
@@ -529,6 +532,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         mbar_init(ready, C::NT / 32);
         mbar_init(da_full, 1);
         mbar_init(bar_w, 1);
+        mbar_init(p_full, 1);
         fence_mbar_init();
     }
     load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, C::NT);
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         for (int i = 0; i < 2 * CW; i += 16) tmem_st16(tLN + i, z);
         tmem_st_wait();
     }
-    uint32_t ph = 0, ph_rdy = 0, ph_da = 0, ph_w = 0;
+    uint32_t ph = 0, ph_rdy = 0, ph_da = 0, ph_w = 0, ph_p = 0;
     bool ok = true, first = true;
     // MMA hand-off without block barriers: every warp arrives on `ready` once its
     // operand writes and its TMEM reads of the accumulator are done; thread 0
@@ -598,20 +602,31 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         tma_load_2d(se, &tmap_e, 0, e0, full + s);
         if (A.has_de_out) tma_load_2d(se + C::TILE, &tmap_de, 0, e0, full + s);
     };
-    // this thread's P|Q slot <- its edge's receiver P row and sender Q row (own columns)
-    // of the tile whose record is in stage s
+    // the receivers' P rows of the tile whose record is in stage s: one bulk copy of the
+    // tile's consecutive rows (thread 0); this thread's Q slot <- the Q row of its edge's
+    // sender, own columns, by cp.async
+    bool p_pending = false;   // thread 0: a P copy not yet consumed (waited for before exit)
+    auto fetch_p = [&](int s) {
+        p_pending = true;
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(sRec0 + s * GNN_TILE_META_BYTES);
+        const int32_t nr = min(max(hdr[1] - hdr[0], 0), 128);   // a tile has 1..128 rows
+        const uint32_t bytes = (uint32_t)nr * H * 2;
+        if (bytes == 0) {
+            mbar_arrive(p_full);
+            return;
+        }
+        mbar_arrive_expect_tx(p_full, bytes);
+        bulk_load(sP, A.pq + (int64_t)hdr[0] * H, bytes, p_full);
+    };
     auto gather = [&](int s) {
         const uint8_t* rec = sRec0 + s * GNN_TILE_META_BYTES;
         if (row < reinterpret_cast<const int32_t*>(rec)[3]) {
-            const int64_t rcv = reinterpret_cast<const int32_t*>(rec)[0] + reinterpret_cast<const int16_t*>(rec + 544)[row];
             const int64_t snd = reinterpret_cast<const int32_t*>(rec + 800)[row];
 #pragma unroll
-            for (int k = 0; k < NCH / 2; ++k) {
-                cp_async16(slot_at(k), A.pq + rcv * H + c0 + 8 * k);
-                cp_async16(slot_at(k + NCH / 2), A.q + snd * H + c0 + 8 * k);
-            }
+            for (int k = 0; k < NCH; ++k) cp_async16(slot_at(k), A.q + snd * H + c0 + 8 * k);
         }
         cp_async_commit();
+        if (tid == 0) fetch_p(s);
     };
     auto first_edge = [&](int64_t t) { return ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8); };
     int32_t e0_next = 0;   // thread 0: first edge of the CTA's next tile
@@ -662,11 +677,15 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             mma_wait();
             ld_acc<CW>(tWork, q, c0, v);
             if (k == 0) {
+                ok = ok && mbar_wait(p_full, ph_p);   // the tile's P rows
+                ph_p ^= 1;
+                p_pending = false;
                 if (valid) {
+                    const uint8_t* prow = sP + (int)sSeg[row] * (2 * H) + 2 * c0;
 #pragma unroll
-                    for (int kc = 0; kc < NCH / 2; ++kc) {
-                        const uint4 up = *reinterpret_cast<const uint4*>(slot_at(kc));
-                        const uint4 uq = *reinterpret_cast<const uint4*>(slot_at(kc + NCH / 2));
+                    for (int kc = 0; kc < NCH; ++kc) {
+                        const uint4 up = *reinterpret_cast<const uint4*>(prow + 16 * kc);
+                        const uint4 uq = *reinterpret_cast<const uint4*>(slot_at(kc));
                         const uint32_t pw[4] = {up.x, up.y, up.z, up.w}, qw[4] = {uq.x, uq.y, uq.z, uq.w};
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
@@ -830,6 +849,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         if (__syncthreads_or(!ok)) break;   // stage release; the block leaves together after a timeout
         tc_fence_after();
     }
+    if (p_pending) mbar_wait(p_full, ph_p);
+    cp_async_wait_all();
     tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();

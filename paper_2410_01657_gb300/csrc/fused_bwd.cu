@@ -109,6 +109,40 @@ __device__ __forceinline__ void row_sum2(float a, float b, float* red, int row, 
     __syncthreads();
 }
 
+// LayerNorm statistics and adjoint sums of a row split over CG threads, in
+// one exchange: with d = g * gamma, the forward's mean and rstd come from
+// sum v and sum v^2, and the adjoint's (1/H) sum d and (1/H) sum d * xhat
+// from sum d and sum d * v, since sum d * xhat = rstd (sum d v - mean sum d).
+template <int H, int CG, int CW>
+__device__ __forceinline__ void row_stats_adj(const float* v, const float* d, float* red, int row, int g, float eps,
+                                              float& mean, float& rstd, float& s1, float& s2) {
+    float sv = 0.f, sq = 0.f, sd = 0.f, sdv = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        sv += v[i];
+        sq += v[i] * v[i];
+        sd += d[i];
+        sdv += d[i] * v[i];
+    }
+    red[(0 * CG + g) * 128 + row] = sv;
+    red[(1 * CG + g) * 128 + row] = sq;
+    red[(2 * CG + g) * 128 + row] = sd;
+    red[(3 * CG + g) * 128 + row] = sdv;
+    __syncthreads();
+    sv = sq = sd = sdv = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) {
+        sv += red[(0 * CG + k) * 128 + row];
+        sq += red[(1 * CG + k) * 128 + row];
+        sd += red[(2 * CG + k) * 128 + row];
+        sdv += red[(3 * CG + k) * 128 + row];
+    }
+    mean = sv * (1.f / H);
+    rstd = rsqrtf(fmaxf(sq * (1.f / H) - mean * mean, 0.f) + eps);
+    s1 = sd * (1.f / H);
+    s2 = rstd * (sdv - mean * sd) * (1.f / H);
+}
+
 // Reduce per-thread column accumulators acc[CW] over the 128 rows of the CTA
 // (lanes by shuffle, then the 4 lane quarters in order) into out[c0..c0+CW).
 template <int CW>
@@ -372,28 +406,19 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
         }
         if (!ok) break;
         tc_fence_before();
-        // ---- LayerNorm adjoint
-        float mean, rstd;
-        row_stats<H, C::CG, CW>(v, sRed, row, g, A.eps, mean, rstd);
+        // ---- LayerNorm adjoint (statistics and adjoint sums in one exchange)
         float dz[CW];
-        float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) dz[i] = gv[i] * sPar[L * H + c0 + i];
+        float mean, rstd, s1, s2;
+        row_stats_adj<H, C::CG, CW>(v, dz, sRed, row, g, A.eps, mean, rstd, s1, s2);
 #pragma unroll
         for (int i = 0; i < CW; ++i) {
-            const float xh = (v[i] - mean) * rstd;
-            acc_g[i] += gv[i] * xh;
+            v[i] = (v[i] - mean) * rstd;   // xhat
+            acc_g[i] += gv[i] * v[i];
             acc_b[i] += gv[i];
-            const float d = gv[i] * sPar[L * H + c0 + i];
-            dz[i] = d;
-            v[i] = xh;
-            m1 += d;
-            m2 += d * xh;
+            dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
         }
-        float s1, s2;
-        row_sum2<C::CG>(m1, m2, sRed + 2 * C::CG * 128, row, g, s1, s2);
-        s1 *= 1.f / H;
-        s2 *= 1.f / H;
-#pragma unroll
-        for (int i = 0; i < CW; ++i) dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
         // ---- chain adjoint, layer L-1 .. 0
         for (int k = L - 1; k >= 0 && ok; --k) {
             st_row_tile<CW>(sG, row, c0, S, dz);
@@ -736,20 +761,14 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
 #pragma unroll
             for (int i = 0; i < CW; ++i) gv[i] = 0.f;
         }
-        // ---- LayerNorm adjoint
-        float mean, rstd;
-        row_stats<H, C::CG, CW>(v, sRed, row, g, A.eps, mean, rstd);
+        // ---- LayerNorm adjoint (statistics and adjoint sums in one exchange)
         float dz[CW];
-        float m1 = 0.f, m2 = 0.f;
 #pragma unroll
-        for (int i = 0; i < CW; ++i) {
-            const float xh = (v[i] - mean) * rstd;
-            const float d = gv[i] * sPar[L * H + c0 + i];
-            dz[i] = d;
-            v[i] = xh;
-            m1 += d;
-            m2 += d * xh;
-        }
+        for (int i = 0; i < CW; ++i) dz[i] = gv[i] * sPar[L * H + c0 + i];
+        float mean, rstd, s1, s2;
+        row_stats_adj<H, C::CG, CW>(v, dz, sRed, row, g, A.eps, mean, rstd, s1, s2);
+#pragma unroll
+        for (int i = 0; i < CW; ++i) v[i] = (v[i] - mean) * rstd;   // xhat
         if constexpr (LNT) {
 #pragma unroll
             for (int i0 = 0; i0 < CW; i0 += 16) {
@@ -773,10 +792,6 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 acc_b[i] += gv[i];
             }
         }
-        float s1, s2;
-        row_sum2<C::CG>(m1, m2, sRed + 2 * C::CG * 128, row, g, s1, s2);
-        s1 *= 1.f / H;
-        s2 *= 1.f / H;
 #pragma unroll
         for (int i = 0; i < CW; ++i) dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
         // ---- chain adjoint

@@ -234,8 +234,8 @@ __host__ __device__ inline NodeBwdSmem node_bwd_smem(int n_lin) {
     s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
     s.par = align_up(s.ones + 128 * C::S, 16);
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);
-    s.tm = s.bar + 16;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // mma, wgrad, ready
+    s.tm = s.bar + 24;
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;
     s.total = end + 1024;
@@ -302,7 +302,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     uint8_t* sOnes = sm + P.ones;
     float* sPar = reinterpret_cast<float*>(sm + P.par);
     float* sRed = reinterpret_cast<float*>(sm + P.red);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);   // MMA completion
+    uint64_t* bar_w = bar + 1;                                  // weight-gradient MMAs of an adjoint step
+    uint64_t* ready = bar + 2;                                  // one arrival per warp before an MMA
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, S2 = C::S2, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(node_bwd_tcols<H>(L));
@@ -316,6 +318,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     }
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(bar_w, 1);
+        mbar_init(ready, C::NT / 32);
         fence_mbar_init();
     }
     load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
@@ -339,11 +343,34 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     float acc_g[CW], acc_b[CW];
 #pragma unroll
     for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
-    uint32_t ph = 0;
+    uint32_t ph = 0, ph_w = 0, ph_rdy = 0;
     bool ok = true, first = true;
     const int64_t n_tiles = (A.n_rows + 127) / 128;
+    // MMA hand-off as in k_edge_bwd: warps arrive on `ready` after their operand writes and
+    // accumulator reads, thread 0 issues, every thread waits on the completion barrier itself
+    auto handoff = [&](auto&& issue, uint64_t* done) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready);
+        if (tid == 0) {
+            ok = ok && mbar_wait(ready, ph_rdy);
+            ph_rdy ^= 1;
+            tc_fence_after();
+            if (ok) {
+                issue();
+                mma_commit(done);
+            }
+        }
+    };
+    auto mma_wait = [&]() {
+        ok = ok && mbar_wait(bar, ph);
+        ph ^= 1;
+        __syncwarp();
+        tc_fence_after();
+    };
 
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         if (tid == 0 && t + gridDim.x < n_tiles) {   // the next tile's input rows into L2
             const int64_t rn = (t + gridDim.x) * 128;
             const uint32_t nb = (uint32_t)(std::min<int64_t>(128, A.n_rows - rn) * H * 4);
@@ -374,37 +401,19 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             st_tile8(sAin, row, c0 + i, 128, S2, av + i);
             st_tile8(sAin, row, H + c0 + i, 128, S2, xv + i);
         }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_mma(tWork, sAin, sW0, H, 2 * H);
-            mma_commit(bar);
-        }
+        handoff([&] { issue_mma(tWork, sAin, sW0, H, 2 * H); }, bar);
         // ---- recompute the chain
         float v[CW];
-        for (int k = 0; k < L && ok; ++k) {
-            ok = block_wait(bar, ph, tid);
-            ph ^= 1;
-            tc_fence_after();
-            if (!ok) break;
+        for (int k = 0; k < L; ++k) {
+            mma_wait();
             ld_acc<CW>(tWork, q, c0, v);
             add_bias2<CW>(v, sPar + k * H + c0);
             if (k < L - 1) {
                 elu_inplace2<CW>(v);
                 st_row_tile<CW>(sHB + k * C::TILE, row, c0, S, v);
-                fence_proxy_async();
-                tc_fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    tc_fence_after();
-                    issue_mma(tWork, sHB + k * C::TILE, sW + k * C::WT, H, H);
-                    mma_commit(bar);
-                }
+                handoff([&] { issue_mma(tWork, sHB + k * C::TILE, sW + k * C::WT, H, H); }, bar);
             }
         }
-        if (!ok) break;
         tc_fence_before();
         // ---- LayerNorm adjoint (statistics and adjoint sums in one exchange)
         float dz[CW];
@@ -420,28 +429,26 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
         }
         // ---- chain adjoint, layer L-1 .. 0
-        for (int k = L - 1; k >= 0 && ok; --k) {
+        for (int k = L - 1; k >= 0; --k) {
+            if (k < L - 1) {   // the previous step's wgrad reads sG
+                ok = ok && mbar_wait(bar_w, ph_w);
+                ph_w ^= 1;
+            }
             st_row_tile<CW>(sG, row, c0, S, dz);
-            fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
+            handoff([&] {
                 if (k == 0) {
                     issue_dgrad(tWork, sG, S, sW0, S2, H, (uint32_t)H * S2, 2 * H, H);
+                    mma_commit(bar);
                     issue_wgrad(tDW(0), sG, S, 128u * S, sAin, S2, 128u * S2, 2 * H + 16, !first);
                 } else {
                     issue_dgrad(tWork, sG, S, sW + (k - 1) * C::WT, S, H, (uint32_t)H * S, H, H);
+                    mma_commit(bar);
                     uint8_t* hk = sHB + (k - 1) * C::TILE;
                     issue_wgrad(tDW(k), sG, S, 128u * S, hk, S, (uint32_t)(smem_u32(sOnes) - smem_u32(hk)), H + 16,
                                 !first);
                 }
-                mma_commit(bar);
-            }
-            ok = block_wait(bar, ph, tid);
-            ph ^= 1;
-            tc_fence_after();
-            if (!ok) break;
+            }, bar_w);
+            mma_wait();
             if (k > 0) {
                 float dh[CW], hv[CW];
                 ld_acc<CW>(tWork, q, c0, dh);
@@ -465,11 +472,14 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             tc_fence_before();
         }
         first = false;
-        __syncthreads();
+        ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads sAin and sG
+        ph_w ^= 1;
+        if (__syncthreads_or(!ok)) break;   // the block leaves together after a timeout
+        tc_fence_after();
     }
     // ---- flush the CTA's partial gradients
     tc_fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {

@@ -1,0 +1,108 @@
+"""Gradient checks of the GPU paths beyond the oracle comparison (needs a GB300).
+
+* Central finite differences of the consistent loss through the plain FP32
+  path (the whole network: encoders, consistent layers, decoder, Eq. 8), on 32
+  seeded weights, h = 1e-3 max(1, |w|): agreement within 1e-2 relative wherever
+  the gradient is above the FP32 noise floor of the difference quotient.
+* The precision form (H = 128, BF16 GEMM operands) on a p = 7 brick: one layer
+  forward against the FP64 oracle and against the plain FP32 path (the BF16
+  backward covers H <= 64)."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import model as om
+from paper_2410_01657_gb300 import _build
+from paper_2410_01657_gb300 import binding as B
+from paper_2410_01657_gb300 import nn as gnn
+from paper_2410_01657_gb300.graph import MeshGraph
+
+from gpu_util import oracle_subgraphs, rel_l2, split_edges, split_rows
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.load()
+
+
+def test_fp32_network_gradient_matches_central_differences():
+    nel, p, H, M, R = (3, 3, 2), 2, 8, 2, 3
+    part = MeshGraph(nel, p).partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(21, H, 2, M, randomize_affine=True)
+    modes = syn.fourier_modes(21, 8)
+    pos = part.array("row_pos")
+    u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=DEV)
+    t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=DEV)
+    net = gnn.ConsistentGNN(params, precision="fp32", device=DEV)
+    attr = G.edge_attr()
+    loss = gnn.consistent_loss(net(G, u, attr), t, G)
+    loss.backward()
+
+    def value():
+        with torch.no_grad():
+            return float(gnn.consistent_loss(net(G, u, attr), t, G).item())
+
+    plist = [p for p in net.parameters()]
+    rng = np.random.default_rng(22)
+    checked = 0
+    for _ in range(32):
+        prm = plist[rng.integers(len(plist))]
+        idx = tuple(int(rng.integers(n)) for n in prm.shape)
+        g = float(prm.grad[idx].item())
+        w0 = float(prm.data[idx].item())
+        h = 1e-3 * max(1.0, abs(w0))
+        with torch.no_grad():
+            prm.data[idx] = w0 + h
+            lp = value()
+            prm.data[idx] = w0 - h
+            lm = value()
+            prm.data[idx] = w0
+        fd = (lp - lm) / (2 * h)
+        noise = 4 * 6e-8 * abs(loss.item()) / h      # a few FP32 ulps of the loss over 2h
+        if abs(g) > 20 * noise:
+            assert abs(fd - g) <= 1e-2 * abs(g) + 2 * noise, (idx, g, fd)
+            checked += 1
+    assert checked >= 16
+    B.call("gnn_check", None)
+
+
+def test_precision_form_h128_layer_forward():
+    nel, p, H, R = (6, 5, 4), 7, 128, 4
+    brick, subs = oracle_subgraphs(nel, p, R)
+    part = MeshGraph(nel, p).partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(31, H, 2, 1, randomize_affine=True)
+    rng = np.random.default_rng(32)
+    gid = part.array("row_gid")
+    x = rng.standard_normal((part.graph.n_nodes, H))[gid]
+    recv = part.receivers()
+    col = part.array("col")
+    key = gid[recv] * part.graph.n_nodes + gid[col]
+    uk, inv = np.unique(key, return_inverse=True)
+    e = rng.standard_normal((uk.size, H))[inv]
+    e = torch.as_tensor(e, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    outs = {}
+    for precision in ("bf16", "fp32"):
+        net = gnn.ConsistentGNN(params, precision=precision, device=DEV)
+        layer = net.layers[0]
+        edt = torch.bfloat16 if precision == "bf16" else torch.float32
+        xt = torch.as_tensor(x, dtype=torch.float32, device=DEV)
+        et = torch.as_tensor(e, dtype=torch.float32, device=DEV).to(edt)
+        W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
+        xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
+        gnn.gnn_mp_forward(G, gnn.mp_config(H, precision), W, xt, et, xo, eo, a)
+        B.call("gnn_check", None)
+        outs[precision] = (xo.cpu().numpy(), eo.float().cpu().numpy(), a.cpu().numpy())
+    ref = (np.concatenate(x1), np.concatenate(e1), np.concatenate(cache["a_star"]))
+    for u, r in zip(outs["fp32"], ref):
+        assert rel_l2(u, r) < 1e-5
+    for u, r, f in zip(outs["bf16"], ref, outs["fp32"]):
+        assert rel_l2(u, r) < 2e-2 and rel_l2(u, f) < 2e-2
+    assert part.n_edges > 100000

@@ -338,6 +338,22 @@ int gnn_mlp_backward(const gnn_mlp* P, int64_t n_rows, const float* X, const voi
                      int32_t dy_bf16, float* dX, const gnn_mlp* dP, float ln_eps,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* The same row MLP on the fused BF16 path (tcgen05 GEMMs with BF16 operands
+ * and FP32 accumulation, FP32 bias / ELU / LayerNorm, activations recomputed
+ * per tile in the backward). Covered shapes, H in {16, 32, 64}:
+ *   encoder: dims[0] <= 16, every other width H, with LayerNorm;
+ *   decoder: dims[0] = H, hidden widths H, dims[n_lin] <= 16, no LayerNorm.
+ * Same arguments and results as gnn_mlp_forward / gnn_mlp_backward (to BF16
+ * tolerance); the forward needs no workspace, the backward the size
+ * reported here (per-CTA gradient partials). GNN_EUNSUPPORTED for other
+ * shapes (use the FP32 calls). */
+int gnn_mlp_workspace_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* fwd_bytes, size_t* bwd_bytes);
+int gnn_mlp_forward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,
+                         float ln_eps, void* ws, size_t ws_bytes, void* stream);
+int gnn_mlp_backward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY,
+                          int32_t dy_bf16, float* dX, const gnn_mlp* dP, float ln_eps,
+                          void* ws, size_t ws_bytes, void* stream);
+
 /* Consistent MSE loss, Eq. 8a-8c: L = sum_rows sum_f (1/d_i)(y - t)^2 /
  * (N_eff * F) with N_eff = sum_rows 1/d_i. y, t: device FP32 [n_rows x F].
  * loss: device FP32 scalar (written). dy: device FP32 [n_rows x F] = dL/dy,

@@ -195,6 +195,47 @@ int gnn_mlp_backward(const gnn_mlp* P, int64_t n_rows, const float* X, const voi
     return gnn::plain::mlp_backward(*P, n_rows, X, dY, dy_bf16, dX, *dP, ln_eps, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+int gnn_mlp_workspace_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* fwd_bytes, size_t* bwd_bytes) {
+    GNN_REQUIRE(P && fwd_bytes && bwd_bytes, GNN_EINVAL, "gnn_mlp_workspace_size_bf16: NULL argument");
+    GNN_REQUIRE(n_rows >= 0, GNN_ESHAPE, "gnn_mlp_workspace_size_bf16: negative rows");
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_workspace_size_bf16", "row");
+    if (rc) return rc;
+    GNN_REQUIRE(gnn::fused::rowmlp_supported(*P), GNN_EUNSUPPORTED,
+                "gnn_mlp_workspace_size_bf16: shape not covered by the fused row MLP");
+    *fwd_bytes = 0;
+    *bwd_bytes = gnn::fused::rowmlp_backward_ws(*P);
+    return GNN_OK;
+}
+
+int gnn_mlp_forward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16, float ln_eps,
+                         void* ws, size_t ws_bytes, void* stream) {
+    GNN_REQUIRE(P, GNN_EINVAL, "gnn_mlp_forward_bf16: NULL parameters");
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_forward_bf16", "row");
+    if (rc) return rc;
+    GNN_REQUIRE(n_rows >= 0, GNN_ESHAPE, "gnn_mlp_forward_bf16: negative rows");
+    if (n_rows) GNN_REQUIRE(X && Y, GNN_EINVAL, "gnn_mlp_forward_bf16: NULL buffer");
+    GNN_REQUIRE(ln_eps > 0.f, GNN_EINVAL, "gnn_mlp_forward_bf16: ln_eps must be positive");
+    GNN_REQUIRE(n_rows < (int64_t)1 << 31, GNN_ESHAPE, "gnn_mlp_forward_bf16: more than 2^31-1 rows");
+    (void)ws;
+    (void)ws_bytes;
+    return gnn::fused::rowmlp_forward(*P, n_rows, X, Y, y_bf16, ln_eps, (cudaStream_t)stream);
+}
+
+int gnn_mlp_backward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY, int32_t dy_bf16,
+                          float* dX, const gnn_mlp* dP, float ln_eps, void* ws, size_t ws_bytes, void* stream) {
+    GNN_REQUIRE(P && dP, GNN_EINVAL, "gnn_mlp_backward_bf16: NULL parameters");
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_backward_bf16", "row");
+    if (rc) return rc;
+    if ((rc = check_mlp(*dP, P->dims[0], 0, P->dims[P->n_lin], P->gamma != nullptr, "gnn_mlp_backward_bf16", "grad")))
+        return rc;
+    GNN_REQUIRE(n_rows >= 0, GNN_ESHAPE, "gnn_mlp_backward_bf16: negative rows");
+    if (n_rows) GNN_REQUIRE(X && dY && ws, GNN_EINVAL, "gnn_mlp_backward_bf16: NULL buffer");
+    GNN_REQUIRE(ln_eps > 0.f, GNN_EINVAL, "gnn_mlp_backward_bf16: ln_eps must be positive");
+    GNN_REQUIRE(n_rows < (int64_t)1 << 31, GNN_ESHAPE, "gnn_mlp_backward_bf16: more than 2^31-1 rows");
+    return gnn::fused::rowmlp_backward(*P, n_rows, X, dY, dy_bf16, dX, *dP, ln_eps, ws, ws_bytes,
+                                       (cudaStream_t)stream);
+}
+
 int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, int32_t F, float* loss, float* dy,
                         void* ws, size_t ws_bytes, void* stream) {
     int rc = check_graph(G, "gnn_consistent_loss");

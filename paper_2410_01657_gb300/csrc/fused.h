@@ -35,5 +35,13 @@ int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
                  const float* x_in, float* x_out, cudaStream_t s);
 
+// Fused BF16 row MLP (encoders / decoder of the network).
+bool rowmlp_supported(const gnn_mlp& P);
+size_t rowmlp_backward_ws(const gnn_mlp& P);
+int rowmlp_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps,
+                   cudaStream_t s);
+int rowmlp_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
+                    const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s);
+
 }  // namespace fused
 }  // namespace gnn

@@ -28,158 +28,12 @@
 #include <cstring>
 
 #include "fused.h"
-#include "fused_common.cuh"
+#include "fused_bwd_common.cuh"
 #include "plain.h"
 #include "profiler.h"
 
 namespace gnn {
 namespace fused {
-
-template <int H>
-struct CfgB {
-    static constexpr int S = span_of(H);
-    static constexpr int S2 = span_of(2 * H);
-    static constexpr int CG = H >= 16 ? H / 16 : 1;
-    static constexpr int CW = H / CG;         // 16
-    static constexpr int NT = 128 * CG;
-    static constexpr int TILE = 128 * H * 2;
-    static constexpr int WT = H * H * 2;
-    static constexpr int NW = H + 16;         // wgrad N: H inputs + the ones block
-};
-
-__host__ __device__ constexpr uint32_t pow2_cols(uint32_t n) {
-    uint32_t c = 32;
-    while (c < n) c <<= 1;
-    return c;
-}
-
-// ------------------------------------------------------------------ device helpers
-
-// D[128 x N] (+)= A[128 x K] (K-major row tile, span Sa) * B where B is a
-// K x N MN-major row tile (rows = K, contiguous = N, span Sb, N-blocks lbo apart).
-__device__ __forceinline__ void issue_dgrad(uint32_t d, const uint8_t* A, int Sa, const uint8_t* Bt, int Sb,
-                                            int b_rows, uint32_t lbo, int N, int K) {
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
-    const uint32_t id = idesc_bf16(128, N, 0, 1);
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo, 8 * Sb, swz_code(Sb));
-        mma_bf16(d, kmajor_desc(a, 128, Sa, k0), bd, id, k0 > 0 ? 1u : 0u);
-        (void)b_rows;
-    }
-}
-
-// D[128 x N] (+)= A^T B over the 128 rows of two MN-major row tiles:
-// A: rows = K (=128), contiguous = M features (span Sa, M-blocks lbo_a apart);
-// B: rows = K, contiguous = N features (span Sb, N-blocks lbo_b apart).
-__device__ __forceinline__ void issue_wgrad(uint32_t d, const uint8_t* A, int Sa, uint32_t lbo_a, const uint8_t* Bt,
-                                            int Sb, uint32_t lbo_b, int N, bool accumulate) {
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
-    const uint32_t id = idesc_bf16(128, N, 1, 1);
-    for (int k0 = 0; k0 < 128; k0 += 16) {
-        const uint64_t ad = sdesc(a + (uint32_t)k0 * Sa, lbo_a, 8 * Sa, swz_code(Sa));
-        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo_b, 8 * Sb, swz_code(Sb));
-        mma_bf16(d, ad, bd, id, (accumulate || k0 > 0) ? 1u : 0u);
-    }
-}
-
-// Ones block: a [128 x S/2] row tile whose column 0 is 1 and the rest 0.
-__device__ __forceinline__ void fill_ones(uint8_t* dst, int S, int tid, int nt) {
-    const int per = S / 2;
-    for (int i = tid; i < 128 * (per / 8); i += nt) {
-        const int r = i / (per / 8), c = (i % (per / 8)) * 8;
-        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (c == 0) v[0] = 1.f;
-        st_tile8(dst, r, c, 128, S, v);
-    }
-}
-
-// Row sums of two per-thread partial vectors over the CG threads of a row.
-template <int CG>
-__device__ __forceinline__ void row_sum2(float a, float b, float* red, int row, int g, float& sa, float& sb) {
-    red[g * 128 + row] = a;
-    red[(CG + g) * 128 + row] = b;
-    __syncthreads();
-    sa = 0.f;
-    sb = 0.f;
-#pragma unroll
-    for (int k = 0; k < CG; ++k) {
-        sa += red[k * 128 + row];
-        sb += red[(CG + k) * 128 + row];
-    }
-    __syncthreads();
-}
-
-// LayerNorm statistics and adjoint sums of a row split over CG threads, in
-// one exchange: with d = g * gamma, the forward's mean and rstd come from
-// sum v and sum v^2, and the adjoint's (1/H) sum d and (1/H) sum d * xhat
-// from sum d and sum d * v, since sum d * xhat = rstd (sum d v - mean sum d).
-template <int H, int CG, int CW>
-__device__ __forceinline__ void row_stats_adj(const float* v, const float* d, float* red, int row, int g, float eps,
-                                              float& mean, float& rstd, float& s1, float& s2) {
-    float sv = 0.f, sq = 0.f, sd = 0.f, sdv = 0.f;
-#pragma unroll
-    for (int i = 0; i < CW; ++i) {
-        sv += v[i];
-        sq += v[i] * v[i];
-        sd += d[i];
-        sdv += d[i] * v[i];
-    }
-    red[(0 * CG + g) * 128 + row] = sv;
-    red[(1 * CG + g) * 128 + row] = sq;
-    red[(2 * CG + g) * 128 + row] = sd;
-    red[(3 * CG + g) * 128 + row] = sdv;
-    __syncthreads();
-    sv = sq = sd = sdv = 0.f;
-#pragma unroll
-    for (int k = 0; k < CG; ++k) {
-        sv += red[(0 * CG + k) * 128 + row];
-        sq += red[(1 * CG + k) * 128 + row];
-        sd += red[(2 * CG + k) * 128 + row];
-        sdv += red[(3 * CG + k) * 128 + row];
-    }
-    mean = sv * (1.f / H);
-    rstd = rsqrtf(fmaxf(sq * (1.f / H) - mean * mean, 0.f) + eps);
-    s1 = sd * (1.f / H);
-    s2 = rstd * (sdv - mean * sd) * (1.f / H);
-}
-
-// Reduce per-thread column accumulators acc[CW] over the 128 rows of the CTA
-// (lanes by shuffle, then the 4 lane quarters in order) into out[c0..c0+CW).
-template <int CW>
-__device__ __forceinline__ void rows_reduce_store(float* acc, float* red, int q, int lane, int g, int c0, float* out) {
-#pragma unroll
-    for (int i = 0; i < CW; ++i) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-    }
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < CW; ++i) red[(g * 4 + q) * CW + i] = acc[i];
-    }
-    __syncthreads();
-    if (q == 0 && lane < CW) {
-        float s = 0.f;
-        for (int k = 0; k < 4; ++k) s += red[(g * 4 + k) * CW + lane];
-        out[c0 + lane] = s;
-    }
-    __syncthreads();
-}
-
-// Flush a TMEM accumulator [128 lanes x N cols] (rows < m_valid) into dst[m*N + n].
-template <int CG>
-__device__ __forceinline__ void flush_acc(uint32_t tmem, int N, int m_valid, int q, int lane, int g, float* dst) {
-    const int m = 32 * q + lane;
-    for (int c = g * 16; c < N; c += CG * 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-        tmem_ld_wait();
-        if (m < m_valid) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) dst[(int64_t)m * N + c + i] = v[i];
-        }
-    }
-}
 
 // ------------------------------------------------------------------ shared memory plans
 
@@ -1087,14 +941,6 @@ __global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
 // ------------------------------------------------------------------ partial reduction
 
 // dst[r*dst_ld + c] += sum over CTAs b (ascending) of part[b*pstride + src_off + r*src_ld + c]
-struct RedSeg {
-    float* dst;
-    int dst_ld, rows, cols;
-    int64_t src_off, src_ld;
-};
-
-constexpr int MAX_SEGS = 2 * GNN_MAX_LIN + 4;
-
 struct RedArgs {
     RedSeg seg[MAX_SEGS];
     int n_seg;
@@ -1119,6 +965,27 @@ __global__ void k_reduce_grads(RedArgs A) {
 }
 
 // =================================================================== host side
+
+int reduce_grads(RedSeg* segs, int n, const float* part, int64_t pstride, int n_cta, cudaStream_t s) {
+    RedArgs A{};
+    A.n_seg = n;
+    A.seg_start[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        A.seg[i] = segs[i];
+        A.seg_start[i + 1] = A.seg_start[i] + (int64_t)segs[i].rows * segs[i].cols;
+    }
+    A.part = part;
+    A.pstride = pstride;
+    A.n_cta = n_cta;
+    const int64_t tot = A.seg_start[n];
+    if (tot == 0) return GNN_OK;
+    {
+        ProfScope _ps(s, "k_reduce_grads");
+        k_reduce_grads<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A);
+    }
+    GNN_LAUNCH_CHECK("k_reduce_grads");
+    return GNN_OK;
+}
 
 namespace {
 
@@ -1160,27 +1027,6 @@ BwdWs carve_bwd(void* ws, const gnn_graph_dev& G, int H, int Le, int Ln, bool ne
     w.part = (float*)take((size_t)std::max(ncta * ps, 2 * ncta * proj_pstride(H)) * 4);
     w.bytes = off + 256;
     return w;
-}
-
-int reduce_grads(RedSeg* segs, int n, const float* part, int64_t pstride, int n_cta, cudaStream_t s) {
-    RedArgs A{};
-    A.n_seg = n;
-    A.seg_start[0] = 0;
-    for (int i = 0; i < n; ++i) {
-        A.seg[i] = segs[i];
-        A.seg_start[i + 1] = A.seg_start[i] + (int64_t)segs[i].rows * segs[i].cols;
-    }
-    A.part = part;
-    A.pstride = pstride;
-    A.n_cta = n_cta;
-    const int64_t tot = A.seg_start[n];
-    if (tot == 0) return GNN_OK;
-    {
-        ProfScope _ps(s, "k_reduce_grads");
-        k_reduce_grads<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A);
-    }
-    GNN_LAUNCH_CHECK("k_reduce_grads");
-    return GNN_OK;
 }
 
 template <int H>

@@ -131,37 +131,52 @@ class ConsistentMPFunction(torch.autograd.Function):
         return (dx, de, None, None, None, None, *dparams)
 
 
+def rowmlp_fused_shape(dims, has_ln: bool) -> bool:
+    """True when the fused BF16 row MLP covers this block (gnn_mlp_forward_bf16):
+    hidden widths H in {16, 32, 64}; an encoder (in <= 16, out H, LayerNorm) or a
+    decoder (in H, out <= 16, no LayerNorm)."""
+    H = dims[1]
+    if len(dims) < 3 or H not in (16, 32, 64) or any(d != H for d in dims[1:-1]):
+        return False
+    if has_ln:
+        return dims[0] <= 16 and dims[-1] == H
+    return dims[0] == H and dims[-1] <= 16
+
+
 class RowMLPFunction(torch.autograd.Function):
-    """Row-wise MLP block (encoders, decoder)."""
+    """Row-wise MLP block (encoders, decoder): the fused BF16 kernels when
+    ``fused`` and the shape is covered, else the plain FP32 kernels."""
 
     @staticmethod
-    def forward(ctx, X, dims, has_ln, out_bf16, ln_eps, need_dx, *params):
+    def forward(ctx, X, dims, has_ln, out_bf16, ln_eps, need_dx, fused, *params):
         P = mlp_struct(dims, params, has_ln)
         f, b = C.c_size_t(), C.c_size_t()
         rows = X.shape[0]
-        B.call("gnn_mlp_workspace_size", C.byref(P), rows, C.byref(f), C.byref(b))
+        fused = bool(fused) and rowmlp_fused_shape(dims, has_ln)
+        sfx = "_bf16" if fused else ""
+        B.call("gnn_mlp_workspace_size" + sfx, C.byref(P), rows, C.byref(f), C.byref(b))
         X = X.contiguous()
         Y = torch.empty((rows, dims[-1]), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=X.device)
         ws = workspace(f.value, X.device)
-        B.call("gnn_mlp_forward", C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps), B.ptr(ws),
-               ws.numel(), _stream())
-        ctx.meta = (dims, has_ln, out_bf16, ln_eps, need_dx, int(b.value))
+        B.call("gnn_mlp_forward" + sfx, C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps),
+               B.ptr(ws), ws.numel(), _stream())
+        ctx.meta = (dims, has_ln, out_bf16, ln_eps, need_dx, int(b.value), sfx)
         ctx.save_for_backward(X, *params)
         return Y
 
     @staticmethod
     def backward(ctx, dY):
         X, *params = ctx.saved_tensors
-        dims, has_ln, out_bf16, ln_eps, need_dx, bwd = ctx.meta
+        dims, has_ln, out_bf16, ln_eps, need_dx, bwd, sfx = ctx.meta
         P = mlp_struct(dims, params, has_ln)
         dparams = [torch.zeros_like(p) for p in params]
         dP = mlp_struct(dims, dparams, has_ln)
         dY = dY.to(torch.bfloat16 if out_bf16 else torch.float32).contiguous()
         dX = torch.empty_like(X) if need_dx else None
         ws = workspace(bwd, X.device)
-        B.call("gnn_mlp_backward", C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16), B.ptr(dX),
+        B.call("gnn_mlp_backward" + sfx, C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16), B.ptr(dX),
                C.byref(dP), float(ln_eps), B.ptr(ws), ws.numel(), _stream())
-        return (dX, None, None, None, None, None, *dparams)
+        return (dX, None, None, None, None, None, None, *dparams)
 
 
 class ConsistentLossFunction(torch.autograd.Function):
@@ -419,7 +434,8 @@ class ConsistentGNN(torch.nn.Module):
         self.hidden = self.enc_node.dims[-1]
 
     def _row_mlp(self, m: _MLP, X, out_bf16: bool, need_dx: bool):
-        return RowMLPFunction.apply(X, m.dims, m.has_ln, out_bf16, self.ln_eps, need_dx, *m.tensors())
+        return RowMLPFunction.apply(X, m.dims, m.has_ln, out_bf16, self.ln_eps, need_dx, self.precision == "bf16",
+                                    *m.tensors())
 
     def encode(self, G: DeviceGraph, u, attr):
         x = self._row_mlp(self.enc_node, u, False, False)

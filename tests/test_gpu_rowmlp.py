@@ -1,0 +1,113 @@
+"""The fused BF16 row MLP (encoders and decoder of the network, Sec. III)
+against the FP64 oracle's MLP and the plain FP32 path (needs a GB300).
+
+Tolerances as for the layer: 2e-2 relative L2 on outputs, 5e-2 on gradients.
+Row counts are ragged (not multiples of the 128-row tile) and span many CTAs."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import model as om
+from paper_2410_01657_gb300 import _build
+from paper_2410_01657_gb300 import binding as B
+from paper_2410_01657_gb300 import nn as gnn
+
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.load()
+
+
+def _mlp_params(dims, has_ln, seed):
+    rng = np.random.default_rng(seed)
+    W = [rng.uniform(-1, 1, (dims[k + 1], dims[k])) * np.sqrt(6.0 / (dims[k] + dims[k + 1]))
+         for k in range(len(dims) - 1)]
+    b = [0.1 * rng.standard_normal(dims[k + 1]) for k in range(len(dims) - 1)]
+    P = {"W": W, "b": b}
+    if has_ln:
+        P["gamma"] = 1.0 + 0.1 * rng.standard_normal(dims[-1])
+        P["beta"] = 0.1 * rng.standard_normal(dims[-1])
+    return P
+
+
+def _run(P, dims, has_ln, X, dY, fused, out_bf16=False, need_dx=False):
+    ts = [torch.nn.Parameter(torch.as_tensor(t, dtype=torch.float32, device=DEV))
+          for t in [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if has_ln else [])]
+    Xt = torch.as_tensor(X, dtype=torch.float32, device=DEV).requires_grad_(need_dx)
+    Y = gnn.RowMLPFunction.apply(Xt, dims, has_ln, out_bf16, 1e-5, need_dx, fused, *ts)
+    Y.backward(torch.as_tensor(dY, dtype=torch.float32, device=DEV).to(Y.dtype))
+    B.call("gnn_check", None)
+    n = len(dims) - 1
+    g = {"W": [t.grad.double().cpu().numpy() for t in ts[:n]], "b": [t.grad.double().cpu().numpy() for t in ts[n:2 * n]]}
+    if has_ln:
+        g["gamma"], g["beta"] = ts[2 * n].grad.double().cpu().numpy(), ts[2 * n + 1].grad.double().cpu().numpy()
+    dx = Xt.grad.double().cpu().numpy() if need_dx else None
+    return Y.detach().float().cpu().numpy(), g, dx
+
+
+def _check(P, dims, has_ln, rows, seed, out_bf16=False, need_dx=False):
+    assert gnn.rowmlp_fused_shape(dims, has_ln)
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((rows, dims[0]))
+    dY = rng.standard_normal((rows, dims[-1]))
+    Yo, cache = om.mlp_forward(P, X)
+    dXo, go = om.mlp_backward(P, cache, dY)
+    Yf, gf, dxf = _run(P, dims, has_ln, X, dY, True, out_bf16, need_dx)
+    Yp, gp, dxp = _run(P, dims, has_ln, X, dY, False, False, need_dx)
+    assert rel_l2(Yp, Yo) < 1e-5                      # the plain FP32 reference itself
+    assert rel_l2(Yf, Yo) < 2e-2 and rel_l2(Yf, Yp) < 2e-2
+    for key in gf:
+        for a, ref in zip(gf[key] if isinstance(gf[key], list) else [gf[key]],
+                          go[key] if isinstance(go[key], list) else [go[key]]):
+            assert rel_l2(a, ref) < 5e-2, (key, rel_l2(a, ref))
+    if need_dx:
+        assert rel_l2(dxf, dXo) < 5e-2
+
+
+@pytest.mark.parametrize("H", [16, 32, 64])
+@pytest.mark.parametrize("n_in,n_hidden", [(3, 2), (4, 2), (4, 0)])
+def test_encoder(H, n_in, n_hidden):
+    dims = [n_in] + [H] * (n_hidden + 2)
+    _check(_mlp_params(dims, True, H + n_in + n_hidden), dims, True, 5003, 7, out_bf16=(n_in == 4))
+
+
+@pytest.mark.parametrize("H", [16, 32, 64])
+@pytest.mark.parametrize("n_hidden", [0, 2])
+def test_decoder(H, n_hidden):
+    dims = [H] * (n_hidden + 2) + [3]
+    _check(_mlp_params(dims, False, H + n_hidden), dims, False, 5003, 8, need_dx=True)
+
+
+def test_encoder_many_tiles_and_deterministic():
+    dims = [4, 64, 64, 64, 64]
+    P = _mlp_params(dims, True, 3)
+    _check(P, dims, True, 200001, 9)
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((70001, 4))
+    dY = rng.standard_normal((70001, 64))
+    a = _run(P, dims, True, X, dY, True)
+    b = _run(P, dims, True, X, dY, True)
+    assert np.array_equal(a[0], b[0])
+    for k in a[1]:
+        for u, v in zip(a[1][k] if isinstance(a[1][k], list) else [a[1][k]],
+                        b[1][k] if isinstance(b[1][k], list) else [b[1][k]]):
+            assert np.array_equal(u, v)
+
+
+def test_uncovered_shape_is_rejected():
+    dims = [8, 24, 24, 5]
+    assert not gnn.rowmlp_fused_shape(dims, False)
+    s = gnn.mlp_struct(dims, [torch.zeros(1, device=DEV)] * 6, False)
+    f, b = ctypes.c_size_t(), ctypes.c_size_t()
+    with pytest.raises(B.GnnError) as ei:
+        B.call("gnn_mlp_workspace_size_bf16", ctypes.byref(s), 10, ctypes.byref(f), ctypes.byref(b))
+    assert ei.value.code == B.GNN_EUNSUPPORTED

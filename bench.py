@@ -57,6 +57,9 @@ WORKLOADS = {
                     "CUDA graph, autotuned tiles"),
     "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=False,
                desc="48^3 elements p=7 GLL brick, 16 RCB sub-graphs, inference: last layer writes no edge state"),
+    "large": dict(nel=16, p=5, parts=8, H=32, nh=5, mode="fwdbwd", inputs="encoders", graph=False,
+                  desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs, the paper's large model (Table 1: "
+                       "H=32, 5 MLP hidden layers)"),
 }
 
 
@@ -71,7 +74,8 @@ def parse():
                     help="fwd: forward only (inference form of the layer stack)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd; c4: 64 uneven jittered "
-                         "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference")
+                         "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference; large: the C2 graph with the "
+                         "paper's large model (H=32, 5 MLP hidden layers)")
     ap.add_argument("--nel", type=int, default=None,
                     help="elements per axis of the brick (default: the workload's; smaller for profiling)")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step")
@@ -188,7 +192,8 @@ def load_peaks() -> dict:
 
 # ---------------------------------------------------------------- oracle timing (CPU)
 
-def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts: int = R, fwd_only: bool = False):
+def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts: int = R, fwd_only: bool = False,
+                  nh: int = NH):
     """Time the FP64 oracle on an n_el^3 brick of order p (RCB parts, 4 layers of
     width `hidden`, forward + backward unless fwd_only): a bounded sample of a
     workload family. Returns (edges/s, seconds per step, description, threads)."""
@@ -200,7 +205,7 @@ def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts:
 
     b = og.build_brick((n_el,) * 3, p)
     subs = og.build_subgraphs(b, og.partition_rcb(b, parts), parts)
-    params = syn.gnn_params(SEED, hidden, NH, M)
+    params = syn.gnn_params(SEED, hidden, nh, M)
     rng = np.random.default_rng(1)
     xg = rng.standard_normal((b.n_nodes, hidden))
     xs = [xg[sg.gid] for sg in subs]
@@ -221,7 +226,7 @@ def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts:
     t = statistics.median(times)
     return (b.n_edges * M / t, t,
             f"{n_el}^3 elements p={p} ({b.n_nodes} nodes, {b.n_edges} edges), {parts} RCB parts, H={hidden}, "
-            f"4 layers {'fwd' if fwd_only else 'fwd+bwd'}, FP64 numpy", _blas_threads())
+            f"MLP {nh} hidden, 4 layers {'fwd' if fwd_only else 'fwd+bwd'}, FP64 numpy", _blas_threads())
 
 
 def _blas_threads() -> int:
@@ -305,7 +310,7 @@ def build_problem(dev, precision, wl: dict, part):
 
     Hh = wl["H"]
     G = part.to_device(dev)
-    params = syn.gnn_params(SEED, Hh, NH, M)
+    params = syn.gnn_params(SEED, Hh, wl.get("nh", NH), M)
     net = gnn.ConsistentGNN(params, precision=precision, device=dev)
     u = t = None
     if wl["inputs"] == "encoders":
@@ -465,7 +470,7 @@ def main():
                 "traffic": measured_traffic(top_name, G.n_edges) if args.workload == "c2" else None,
                 "peak_src": peaks["src"], "share": top_ms / total_ms}
     elif top_name == "k_sgemm":
-        flops = sgemm_flops_per_step(G, Hw, NH + 2, M) * args.steps
+        flops = sgemm_flops_per_step(G, Hw, wl.get("nh", NH) + 2, M) * args.steps
         ach = flops / (top_ms * 1e-3) / 1e12
         peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -507,7 +512,7 @@ def main():
         # width, partition count and pass (about 5-20 s of host time)
         n_s = {5: 6, 7: 4}[wl["p"]]
         v, tsec, desc, threads = oracle_sample(n_s, p=wl["p"], hidden=Hw, parts=wl["parts"] if wl["parts"] <= 16 else 8,
-                                               fwd_only=fwd_only)
+                                               fwd_only=fwd_only, nh=wl.get("nh", NH))
         cpu = {"value": v, "unit": "edges/s", "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": tsec}
 
@@ -518,7 +523,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
                 "config": {"workload": f"consistent NMP layers x{M} {kind}, {n_el}^3 elements: {wl['desc']} "
-                                       f"({n_unpart:,} nodes, {e_unpart:,} edges), H={Hw}, MLP {NH} hidden",
+                                       f"({n_unpart:,} nodes, {e_unpart:,} edges), H={Hw}, MLP {wl.get('nh', NH)} hidden",
                            "name": args.workload, "inputs": wl["inputs"],
                            "rows": part.n_rows, "edges_partitioned": part.n_edges, "tile_edges": G.tile_edges,
                            "l2": f"inputs larger than L2 (edge state {edge_state / 1e6:.0f} MB), no flush",

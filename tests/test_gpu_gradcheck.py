@@ -6,7 +6,9 @@
   the gradient is above the FP32 noise floor of the difference quotient.
 * The precision form (H = 128, BF16 GEMM operands) on a p = 7 brick: one layer
   forward against the FP64 oracle and against the plain FP32 path (the BF16
-  backward covers H <= 64)."""
+  backward covers H <= 64), and the same forward on a standalone 99^3-node
+  brick (14^3 elements, p = 7, 5.8M edges) split into 2 sub-graphs, against
+  the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -106,3 +108,38 @@ def test_precision_form_h128_layer_forward():
     for u, r, f in zip(outs["bf16"], ref, outs["fp32"]):
         assert rel_l2(u, r) < 2e-2 and rel_l2(u, f) < 2e-2
     assert part.n_edges > 100000
+
+
+def test_precision_form_million_node_subbrick():
+    # the C3 precision form on a standalone 14^3-element p=7 brick (99^3 = 970,299 nodes,
+    # 5.8M directed edges), H=128, one consistent layer forward, 2 RCB sub-graphs:
+    # BF16 against the FP64 oracle
+    nel, p, H, R = (14, 14, 14), 7, 128, 2
+    brick, subs = oracle_subgraphs(nel, p, R)
+    assert brick.n_nodes == 99 ** 3
+    part = MeshGraph(nel, p).partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(41, H, 2, 1, randomize_affine=True)
+    rng = np.random.default_rng(42)
+    gid = part.array("row_gid")
+    xg = rng.standard_normal((part.graph.n_nodes, H)).astype(np.float32).astype(np.float64)
+    x = xg[gid]
+    # one state per directed global edge, BF16-rounded
+    recv = part.receivers()
+    col = part.array("col")
+    key = gid[recv] * part.graph.n_nodes + gid[col]
+    uk, inv = np.unique(key, return_inverse=True)
+    eu = torch.as_tensor(rng.standard_normal((uk.size, H)), dtype=torch.float32).to(torch.bfloat16)
+    e = eu.to(torch.float32).numpy().astype(np.float64)[inv]
+    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layer = net.layers[0]
+    xt = torch.as_tensor(x, dtype=torch.float32, device=DEV)
+    et = torch.as_tensor(e, dtype=torch.float32, device=DEV).to(torch.bfloat16)
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
+    xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
+    gnn.gnn_mp_forward(G, gnn.mp_config(H, "bf16"), W, xt, et, xo, eo, a)
+    B.call("gnn_check", None)
+    assert rel_l2(a.cpu().numpy(), np.concatenate(cache["a_star"])) < 2e-2
+    assert rel_l2(eo.float().cpu().numpy(), np.concatenate(e1)) < 2e-2
+    assert rel_l2(xo.cpu().numpy(), np.concatenate(x1)) < 2e-2

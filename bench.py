@@ -18,7 +18,8 @@ roofline  -- the dominant kernel's algorithmic bytes (or FLOPs) per launch over
              its CUDA-event launch time, against MEASURED_PEAKS.json.
 cpu_baseline -- the FP64 numpy oracle on a bounded sample, host cores.
 
-``--workload`` selects the other graph families (c3: 32^3 p=7 H=128 forward;
+``--workload`` selects the other graph families (c3: 32^3 p=7 H=128 fwd+bwd,
+``--mode fwd`` for its inference form;
 c4: 64 uneven sub-graphs of a jittered p=5 brick, H=64 fwd+bwd, autotuned and
 replayed as a CUDA graph; c5: 48^3 p=7 H=32 inference); their layer inputs
 are seeded random states drawn on the device, and they report no fp32/e2e leg.
@@ -50,8 +51,8 @@ SEED = 0
 WORKLOADS = {
     "c2": dict(nel=16, p=5, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False,
                desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs"),
-    "c3": dict(nel=32, p=7, parts=8, H=128, mode="fwd", inputs="random", graph=False,
-               desc="32^3 elements p=7 GLL brick, 8 RCB sub-graphs, forward (inference) only"),
+    "c3": dict(nel=32, p=7, parts=8, H=128, mode="fwdbwd", inputs="random", graph=False,
+               desc="32^3 elements p=7 GLL brick, 8 RCB sub-graphs, the precision form (H=128)"),
     "c4": dict(nel=None, p=5, parts=64, H=64, mode="fwdbwd", inputs="random", graph=True, uneven=True,
                desc="jittered p=5 brick in 64 RCB sub-graphs of log-uniform element counts in [50, 5000], "
                     "CUDA graph, autotuned tiles"),
@@ -73,7 +74,7 @@ def parse():
     ap.add_argument("--mode", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwd: forward only (inference form of the layer stack)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                    help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd; c4: 64 uneven jittered "
+                    help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd+bwd; c4: 64 uneven jittered "
                          "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference; large: the C2 graph with the "
                          "paper's large model (H=32, 5 MLP hidden layers)")
     ap.add_argument("--nel", type=int, default=None,
@@ -135,20 +136,34 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 
-def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False):
-    """Least HBM bytes one launch of a fused kernel must move (one layer; for
-    the edge forward of an inference stack, the mean over its M launches, the
-    last of which writes no edge state).
+def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False,
+                      n_lin: int = NH + 2):
+    """Least HBM bytes all launches of a kernel move in one step of M layers
+    (for the edge forward of an inference stack the last layer writes no edge
+    state).
 
     Per edge: read e (s_e H), write e' (s_e H), col (4), 1/d (4); per row:
-    the row's CSR pointer and node tensors (see the per-kernel notes)."""
+    the row's CSR pointer and node tensors (see the per-kernel notes). The
+    layered H = 128 backward counts its scratch rows (BF16 h, dz, [a*, x]) as
+    the inputs and outputs of the kernels that read and write them."""
     E, N = G.n_edges, G.n_rows
     se = edge_bytes
+    h2 = 2 * hidden                 # one BF16 row
     if kernel == "k_edge_fwd":      # e in/out, col, w, P/Q gathers (bf16 2H per row), a out (fp32 H)
         writes = (M - 1) / M if last_layer_no_edge_out else 1.0
-        return E * ((1 + writes) * se * hidden + 8) + N * (2 * 2 * hidden + 4 * hidden + 4)
+        return M * (E * ((1 + writes) * se * hidden + 8) + N * (2 * 2 * hidden + 4 * hidden + 4))
     if kernel == "k_edge_bwd":      # e in, de_out in, de_in out, dz1 out, col, w; da in, P/Q, dP out per row
-        return E * (4 * se * hidden + 8) + N * (4 * hidden + 2 * 2 * hidden + 4 * hidden + 4)
+        return M * (E * (4 * se * hidden + 8) + N * (4 * hidden + 2 * 2 * hidden + 4 * hidden + 4))
+    if kernel == "k_edge_fwd_save":   # e, de_out in, col, w; h_0..h_{L-2}, dz out; da, P/Q per row
+        return M * (E * (2 * h2 + 8 + (n_lin - 1) * h2 + h2) + N * (4 * hidden + 2 * h2 + 4))
+    if kernel == "k_node_fwd_save":   # a*, x, dx' in (fp32); [a*, x] bf16, h_0..h_{L-2}, dz out
+        return M * N * (3 * 4 * hidden + 2 * h2 + (n_lin - 1) * h2 + h2)
+    if kernel == "k_bwd_chain":       # per Linear k >= 1: dz_k, h_{k-1} in, dz_{k-1} out
+        return M * (n_lin - 1) * (E + N) * 3 * h2
+    if kernel == "k_bwd_edge0":       # dz_0, e, de_out in, de_in, dz_0 out; da in, dP out per row
+        return M * (E * 5 * h2 + N * 2 * 4 * hidden)
+    if kernel == "k_bwd_node0":       # dz_0, [a*, x] bf16, dx' in; da*, dx_in out (fp32)
+        return M * N * (h2 + 2 * h2 + 3 * 4 * hidden)
     return None
 
 
@@ -462,9 +477,10 @@ def main():
     top_name, (top_n, top_ms) = top
     edge_bytes = 2 if precision == "bf16" else 4
     roof = None
-    abytes = algorithmic_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only)
-    if abytes is not None:
-        ach = abytes / (top_ms / top_n * 1e-3) / 1e9
+    abytes = algorithmic_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only,
+                               n_lin=wl.get("nh", NH) + 2)
+    if abytes is not None:   # bytes of one step over the kernel's device time in one step
+        ach = abytes / (top_ms / args.steps * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"],
                 "traffic": measured_traffic(top_name, G.n_edges) if args.workload == "c2" else None,

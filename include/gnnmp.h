@@ -268,7 +268,12 @@ int gnn_mp_forward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_m
  * writes dL/dx_in (FP32) and dL/de_in (edge dtype) and ACCUMULATES (+=) the
  * parameter gradients into dW (same shapes as W, FP32) in a fixed order.
  * a_star: the forward's a_star_out, or NULL to recompute it. The halo adjoint
- * is the same copy-sum as the forward (the map a -> a* is symmetric). */
+ * is the same copy-sum as the forward (the map a -> a* is symmetric).
+ * BF16 at H = 128: the MLP adjoints run one Linear at a time over tiles of
+ * 128 rows with the recomputed activations in workspace scratch, in chunks
+ * of tiles; gnn_mp_workspace_size reports the size for the largest chunk,
+ * and a smaller ws_bytes (at least the size for a one-tile chunk) gives more,
+ * smaller chunks with the same results. GNN_ENOMEM below that. */
 int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
                     const float* x_in, const void* e_in, const float* a_star,
                     const float* dx_out, const void* de_out, float* dx_in, void* de_in,

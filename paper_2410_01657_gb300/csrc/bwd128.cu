@@ -1,0 +1,714 @@
+// Layered BF16 backward of the consistent NMP layer at H = 128 (Eq. 3 with
+// per-layer recomputation of the MLP activations).
+//
+// At H = 128 one SM cannot hold the single-kernel edge adjoint of the smaller
+// widths: every 128 x 128 FP32 weight-gradient accumulator takes a quarter of
+// TMEM and every BF16 activation tile 32 KB of shared memory. The adjoint
+// therefore runs one Linear at a time over tiles of 128 rows, with the
+// recomputed activations in an HBM scratch of tile-padded rows (the rows past
+// a tile's end are zero, so they add nothing to any product or sum):
+//   k_node_fwd<128, false, true> / k_edge_fwd<128, true>   (forward units)
+//       recompute the MLP, save h_0 .. h_{L-2} (and a node tile's BF16
+//       [a*, x] rows), apply the LayerNorm adjoint: dz_{L-1}, dgamma, dbeta,
+//       db_{L-1}
+//   k_bwd_chain, k = L-1 .. 1
+//       dh_{k-1} = dz_k W_k, dz_{k-1} = dh_{k-1} ELU'(h_{k-1}),
+//       dW_k += dz_k^T h_{k-1} (TMEM, over the CTA's tiles), db_{k-1}
+//   k_bwd_node0   [da*, dx] = dz_0 W_0, dW_0 += dz_0^T [a*, x], dx_in = dx' + dx
+//   k_halo        adjoint of Eq. 5c-5d on da*
+//   k_bwd_edge0   de_in = g + dz_0 W1c with g = de' + da_i / d_ij, dW1c += dz_0^T e,
+//                 dz_0 per edge and its sum over each receiver's edges (dP)
+//   k_proj_bwd    dQ, dx_in += dP W1a + dQ W1b, dW1a, dW1b
+// Tiles are processed in chunks of at most kChunkTiles so that the scratch
+// stays bounded; each kernel's per-CTA partials are summed (CTA order) into
+// dW right after it, so every gradient has a fixed summation order.
+
+#include <algorithm>
+
+#include "fused.h"
+#include "fused_bwd_common.cuh"
+#include "plain.h"
+#include "profiler.h"
+
+namespace gnn {
+namespace fused {
+
+namespace {
+
+constexpr int H128 = 128;
+constexpr int kTile = 128 * H128 * 2;        // [128 x 128] BF16 row tile
+constexpr int kS = 128;                       // swizzle span of a 128-wide BF16 tile
+constexpr int64_t kChunkTiles = 32768;        // tiles per scratch chunk
+constexpr int64_t kPstride = 2 * H128 * H128 + H128;   // per-CTA partial floats (largest kernel: dW_0 of nodes)
+
+// ------------------------------------------------------------------ k_bwd_chain
+
+struct ChainArgs {
+    const float* W;              // W_k [H x H] (FP32)
+    __nv_bfloat16* dz_out;       // dz_{k-1} rows (tile-padded)
+    int64_t n_tiles;
+    float* part;                 // per-CTA: dW_k [H x H], then db_{k-1} [H]
+    int64_t pstride;
+};
+
+// 128 rows x 2 column groups of 64 columns; two CTAs per SM, one stage each
+// (the other CTA's work covers a CTA's load latency).
+constexpr int kChainNT = 256;
+
+__global__ void __launch_bounds__(kChainNT, 2) k_bwd_chain(const __grid_constant__ CUtensorMap tm_dz,
+                                                          const __grid_constant__ CUtensorMap tm_h, ChainArgs A) {
+    constexpr int H = H128, S = kS, CG = 2, CW = 64, NT = kChainNT, NCH = CW / 16;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    uint8_t* sW = sm;
+    uint8_t* sDz = sm + kTile;
+    uint8_t* sH = sm + 2 * kTile;
+    float* sRed = reinterpret_cast<float*>(sm + 3 * kTile);            // 4 x H floats
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + 3 * kTile + 4 * H * 4);
+    uint64_t* bar = full + 1;     // dgrad done
+    uint64_t* bar_w = full + 2;   // wgrad done (the stage is free)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 3);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    if (warp == 0) {
+        tmem_alloc(tslot, 2 * H);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(full, 1);
+        mbar_init(bar, 1);
+        mbar_init(bar_w, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.W, H, 0, H, H, tid, NT);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, tWork = tmem, tDW = tmem + H;
+    bool lp = false, mp = false;    // thread 0: a load / MMAs in flight that nobody has waited for
+    auto issue = [&](int64_t t) {   // thread 0: dz_k and h_{k-1} rows of tile t
+        lp = true;
+        mbar_arrive_expect_tx(full, 2 * kTile);
+        for (int kb = 0; kb < 2; ++kb) {
+            tma_load_2d(sDz + kb * 128 * S, &tm_dz, kb * 64, (int32_t)(t * 128), full);
+            tma_load_2d(sH + kb * 128 * S, &tm_h, kb * 64, (int32_t)(t * 128), full);
+        }
+    };
+    if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) issue(blockIdx.x);
+    float acc[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) acc[j] = 0.f;
+    uint32_t ph = 0;
+    bool ok = true, first = true;
+
+    for (int64_t t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+        ok = block_wait(full, ph, tid);
+        if (!ok) break;
+        lp = false;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_dgrad(tWork, sDz, S, sW, S, H, (uint32_t)H * S, H, H);
+            mma_commit(bar);
+            issue_wgrad(tDW, sDz, S, 128u * S, sH, S, 128u * S, H, !first);
+            mma_commit(bar_w);
+            mp = true;
+        }
+        ok = block_wait(bar, ph, tid);
+        tc_fence_after();
+        if (!ok) break;
+        __nv_bfloat16* zrow = A.dz_out + (t * 128 + row) * H + c0;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            float dh[16], hv[16];
+            tmem_ld16(tWork + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * j), dh);
+            ld_tile8(sH, row, c0 + 16 * j, 128, S, hv);
+            ld_tile8(sH, row, c0 + 16 * j + 8, 128, S, hv + 8);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
+            st_bf16x8(zrow + 16 * j, dh);
+            st_bf16x8(zrow + 16 * j + 8, dh + 8);
+            acc[j] += warp_colsum16(dh, lane);
+        }
+        tc_fence_before();
+        fence_proxy_async();
+        ok = block_wait(bar_w, ph, tid);   // every thread is past its reads of the stage
+        if (!ok) break;
+        mp = false;
+        ph ^= 1;
+        tc_fence_after();
+        first = false;
+        if (tid == 0 && t + gridDim.x < A.n_tiles) issue(t + gridDim.x);
+    }
+    if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
+        if (mp) mbar_wait(bar_w, ph);
+        if (lp) mbar_wait(full, mp ? ph ^ 1 : ph);
+    }
+    ok = __syncthreads_and(ok) != 0;
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        if (!first) flush_acc<CG>(tDW, H, H, q, lane, g, part);
+        else
+            for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
+    }
+    colsum_store<H, NCH>(acc, sRed, q, lane, c0, tid, NT, part + H * H);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 2 * H);
+}
+
+constexpr uint32_t chain_smem() { return 3 * kTile + 4 * H128 * 4 + 64 + 1024; }
+
+
+// ------------------------------------------------------------------ k_bwd_edge0
+
+struct Edge0Args {
+    const uint8_t* tile_meta;    // per-tile records (GNN_TILE_META_BYTES each)
+    int64_t t0, t1;              // tile range; the scratch rows of tile t start at (t - t0) * 128
+    const float* W1;             // W1 [H x 3H]; W1c = columns 2H .. 3H
+    const __nv_bfloat16* de_out; // NULL: zero
+    const float* da;             // aggregate gradient after the halo adjoint
+    __nv_bfloat16* de_in;
+    __nv_bfloat16* dz1;          // per-edge dz_0 [E x H]
+    float* dP;                   // [n_rows x H]
+    float* part;                 // per-CTA: dW1c [H x H]
+    int64_t pstride;
+};
+
+// 128 rows x 4 column groups of 32 columns, one CTA per SM, two stages of
+// {tile record, dz_0 rows, e rows}.
+constexpr int kE0NT = 512;
+struct Edge0Smem {
+    static constexpr uint32_t w = 0, st = kTile;          // stage s: dz tile, then e tile, at st + s * 2 * kTile
+    static constexpr uint32_t rec = st + 4 * kTile;       // stage s: record at rec + s * GNN_TILE_META_BYTES
+    static constexpr uint32_t bar = rec + 2 * GNN_TILE_META_BYTES;
+    static constexpr uint32_t total = bar + 64 + 1024;
+};
+
+__global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ CUtensorMap tm_dz,
+                                                       const __grid_constant__ CUtensorMap tm_e, Edge0Args A) {
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kE0NT;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    uint8_t* sW = sm + Edge0Smem::w;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + Edge0Smem::bar);   // full[2]
+    uint64_t* bar = full + 2;     // dgrad done
+    uint64_t* bar_w = full + 3;   // wgrad done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 4);
+    auto sDz = [&](int s) { return sm + Edge0Smem::st + s * 2 * kTile; };
+    auto sRec = [&](int s) { return sm + Edge0Smem::rec + s * GNN_TILE_META_BYTES; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    if (warp == 0) {
+        tmem_alloc(tslot, 2 * H);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(full, 1);
+        mbar_init(full + 1, 1);
+        mbar_init(bar, 1);
+        mbar_init(bar_w, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW, A.W1, 3 * H, 2 * H, H, H, tid, NT);   // W1c as a K-major [H x H] tile
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, tWork = tmem, tDW = tmem + H;
+    int64_t n_issued = 0;   // thread 0: loads issued (stage i & 1, phase (i >> 1) & 1)
+    auto issue = [&](int s, int64_t t) {   // thread 0: record, dz_0 rows and e rows of tile t
+        const int32_t e0 = ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8);
+        ++n_issued;
+        mbar_arrive_expect_tx(full + s, 2 * kTile + GNN_TILE_META_BYTES);
+        bulk_load(sRec(s), A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, full + s);
+        for (int kb = 0; kb < 2; ++kb) {
+            tma_load_2d(sDz(s) + kb * 128 * S, &tm_dz, kb * 64, (int32_t)((t - A.t0) * 128), full + s);
+            tma_load_2d(sDz(s) + kTile + kb * 128 * S, &tm_e, kb * 64, e0, full + s);
+        }
+    };
+    const int64_t tfirst = A.t0 + blockIdx.x;
+    if (tid == 0 && tfirst < A.t1) issue(0, tfirst);
+    uint32_t ph = 0;
+    bool ok = true, first = true, mp = false;
+    int j = 0;
+    int64_t n_consumed = 0;
+
+    for (int64_t t = tfirst; t < A.t1; t += gridDim.x, ++j) {
+        const int st = j & 1;
+        ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
+        if (!ok) break;
+        ++n_consumed;
+        uint8_t* dzt = sDz(st);
+        uint8_t* et = dzt + kTile;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_dgrad(tWork, dzt, S, sW, S, H, (uint32_t)H * S, H, H);
+            mma_commit(bar);
+            issue_wgrad(tDW, dzt, S, 128u * S, et, S, 128u * S, H, !first);
+            mma_commit(bar_w);
+            mp = true;
+            // the other stage was released at the end of the previous tile
+            if (t + gridDim.x < A.t1) issue(st ^ 1, t + gridDim.x);
+        }
+        const uint8_t* rec = sRec(st);
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
+        const int32_t* sRp = reinterpret_cast<const int32_t*>(rec + 16);
+        const int16_t* sSeg = reinterpret_cast<const int16_t*>(rec + 544);
+        const float* sWd = reinterpret_cast<const float*>(rec + 1312);
+        const int32_t r0 = hdr[0], r1 = hdr[1], e0 = hdr[2], ne = hdr[3];
+        const bool valid = row < ne;
+        const int64_t eg = (int64_t)e0 + row;
+        // gradient of e' (Eq. 5b adjoint plus the upstream de'), requested before the MMA wait
+        float gv[CW];
+        if (valid) {
+            const float w = sWd[row];
+            const float* dar = A.da + (int64_t)(r0 + sSeg[row]) * H + c0;
+#pragma unroll
+            for (int i = 0; i < CW; i += 4) {
+                const float4 u = __ldg(reinterpret_cast<const float4*>(dar + i));
+                gv[i] = w * u.x;
+                gv[i + 1] = w * u.y;
+                gv[i + 2] = w * u.z;
+                gv[i + 3] = w * u.w;
+            }
+            if (A.de_out) {
+#pragma unroll
+                for (int i = 0; i < CW; i += 8) {
+                    float d8[8];
+                    ld_bf16x8(A.de_out + eg * H + c0 + i, d8);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) gv[i + k] = d8[k] + gv[i + k];
+                }
+            }
+            // dz_0 per edge, for the sender-side sums of the projection adjoint
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) {
+                float z8[8];
+                ld_tile8(dzt, row, c0 + i, 128, S, z8);
+                st_bf16x8(A.dz1 + eg * H + c0 + i, z8);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) gv[i] = 0.f;
+        }
+        // receiver-side sums of dz_0 over each receiver's edges (dP, fixed edge order)
+        for (int it = tid; it < (r1 - r0) * (H / 8); it += NT) {
+            const int rr = it / (H / 8), c = (it % (H / 8)) * 8;
+            float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) {
+                float z8[8];
+                ld_tile8(dzt, e, c, 128, S, z8);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s8[k] += z8[k];
+            }
+            float4* dp = reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + c);
+            dp[0] = make_float4(s8[0], s8[1], s8[2], s8[3]);
+            dp[1] = make_float4(s8[4], s8[5], s8[6], s8[7]);
+        }
+        ok = block_wait(bar, ph, tid);
+        tc_fence_after();
+        if (!ok) break;
+        float dh[CW];
+        ld_acc<CW>(tWork, q, c0, dh);
+        tc_fence_before();
+        if (valid) {   // residual branch plus W1c^T dz_0
+#pragma unroll
+            for (int i = 0; i < CW; ++i) dh[i] = gv[i] + dh[i];
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) st_bf16x8(A.de_in + eg * H + c0 + i, dh + i);
+        }
+        fence_proxy_async();
+        ok = block_wait(bar_w, ph, tid);   // the stage is free: wgrad done, every thread past its reads
+        if (!ok) break;
+        mp = false;
+        ph ^= 1;
+        tc_fence_after();
+        first = false;
+    }
+    if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
+        if (mp) mbar_wait(bar_w, ph);
+        if (n_issued > n_consumed) {   // at most the last load is outstanding
+            const int64_t i = n_issued - 1;
+            mbar_wait(full + (i & 1), (uint32_t)(i >> 1) & 1u);
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        if (!first) flush_acc<CG>(tDW, H, H, q, lane, g, part);
+        else
+            for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 2 * H);
+}
+
+// ------------------------------------------------------------------ k_bwd_node0
+
+struct Node0Args {
+    int64_t t0, t1;              // tile range; the scratch rows of tile t start at (t - t0) * 128
+    int64_t n_rows;
+    const float* W0;             // W_0 of the node MLP [H x 2H]
+    const float* dx_out;
+    float* da;                   // out: gradient of a*
+    float* dx_in;                // out: dx_out + the x part
+    float* part;                 // per-CTA: dW_0 [H x 2H]
+    int64_t pstride;
+};
+
+// 128 rows x 4 column groups, one CTA per SM (TMEM: a 256-column input
+// gradient and the 256-column dW_0 accumulator). The epilogue reads only TMEM
+// and global memory, so the next tile's rows load while it runs.
+constexpr int kN0NT = 512;
+struct Node0Smem {
+    static constexpr uint32_t w = 0, dz = 2 * kTile, xa = 3 * kTile;
+    static constexpr uint32_t bar = 5 * kTile;
+    static constexpr uint32_t total = bar + 64 + 1024;
+};
+
+__global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ CUtensorMap tm_dz,
+                                                       const __grid_constant__ CUtensorMap tm_xa, Node0Args A) {
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kN0NT;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    uint8_t* sW0 = sm + Node0Smem::w;
+    uint8_t* sDz = sm + Node0Smem::dz;
+    uint8_t* sXa = sm + Node0Smem::xa;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + Node0Smem::bar);
+    uint64_t* bar = full + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    if (warp == 0) {
+        tmem_alloc(tslot, 4 * H);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(full, 1);
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    load_weight(sW0, A.W0, 2 * H, 0, H, 2 * H, tid, NT);   // [H x 2H], K-major over the 2H inputs
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, tWork = tmem, tDW = tmem + 2 * H;
+    bool lp = false, mp = false;
+    auto issue = [&](int64_t t) {   // thread 0: dz_0 rows and [a*, x] rows of tile t
+        lp = true;
+        const int32_t y = (int32_t)((t - A.t0) * 128);
+        mbar_arrive_expect_tx(full, 3 * kTile);
+        for (int kb = 0; kb < 2; ++kb) tma_load_2d(sDz + kb * 128 * S, &tm_dz, kb * 64, y, full);
+        for (int kb = 0; kb < 4; ++kb) tma_load_2d(sXa + kb * 128 * S, &tm_xa, kb * 64, y, full);
+    };
+    const int64_t tfirst = A.t0 + blockIdx.x;
+    if (tid == 0 && tfirst < A.t1) issue(tfirst);
+    uint32_t ph = 0;
+    bool ok = true, first = true;
+
+    for (int64_t t = tfirst; t < A.t1; t += gridDim.x) {
+        ok = block_wait(full, ph, tid);
+        if (!ok) break;
+        lp = false;
+        if (tid == 0) {
+            tc_fence_after();
+            issue_dgrad(tWork, sDz, S, sW0, S, H, (uint32_t)H * S, 2 * H, H);
+            issue_wgrad(tDW, sDz, S, 128u * S, sXa, S, 128u * S, 2 * H, !first);
+            mma_commit(bar);
+            mp = true;
+        }
+        const int64_t r = t * 128 + row;
+        const bool valid = r < A.n_rows;
+        float gx[CW];
+        if (valid) {
+            const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) {
+                const float4 u = __ldg(pg + i);
+                gx[4 * i] = u.x; gx[4 * i + 1] = u.y; gx[4 * i + 2] = u.z; gx[4 * i + 3] = u.w;
+            }
+        }
+        ok = block_wait(bar, ph, tid);
+        if (!ok) break;
+        mp = false;
+        ph ^= 1;
+        tc_fence_after();
+        first = false;
+        // both MMAs are done: the stage takes the next tile while the epilogue runs
+        if (tid == 0 && t + gridDim.x < A.t1) issue(t + gridDim.x);
+        float d[CW];
+        ld_acc<CW>(tWork, q, c0, d);   // gradient of a* (first H inputs)
+        if (valid) {
+            float4* po = reinterpret_cast<float4*>(A.da + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) po[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+        }
+        ld_acc<CW>(tWork + H, q, c0, d);   // gradient of x (last H inputs) plus the residual branch
+        tc_fence_before();
+        if (valid) {
+            float4* po = reinterpret_cast<float4*>(A.dx_in + r * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i)
+                po[i] = make_float4(gx[4 * i] + d[4 * i], gx[4 * i + 1] + d[4 * i + 1], gx[4 * i + 2] + d[4 * i + 2],
+                                    gx[4 * i + 3] + d[4 * i + 3]);
+        }
+    }
+    if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
+        if (mp) mbar_wait(bar, ph);
+        if (lp) mbar_wait(full, mp ? ph ^ 1 : ph);
+    }
+    ok = __syncthreads_and(ok) != 0;
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        if (!first) flush_acc<CG>(tDW, 2 * H, H, q, lane, g, part);
+        else
+            for (int i = tid; i < 2 * H * H; i += NT) part[i] = 0.f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 4 * H);
+}
+
+// =================================================================== host side
+
+using namespace host;
+
+struct B128Ws {
+    __nv_bfloat16* pq;
+    float* a;
+    float* da;
+    float* dP;
+    __nv_bfloat16* dz1;
+    float* part;
+    __nv_bfloat16* hs;       // (L-1) x [chunk rows x H]
+    int64_t hs_stride;
+    __nv_bfloat16* dzs[2];   // [chunk rows x H] each
+    __nv_bfloat16* xa;       // [chunk rows x 2H]
+    int64_t chunk;           // tiles per chunk
+    size_t bytes;
+};
+
+// Tiles per chunk when the workspace is not limiting.
+int64_t default_chunk(const gnn_graph_dev& G) {
+    const int64_t node_tiles = (G.n_rows + 127) / 128;
+    return std::max<int64_t>(1, std::min<int64_t>(kChunkTiles, std::max<int64_t>(node_tiles, G.n_edge_tiles)));
+}
+
+B128Ws carve_b128(void* ws, const gnn_graph_dev& G, int Le, int Ln, bool need_a, int64_t chunk) {
+    constexpr int H = H128;
+    B128Ws w{};
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        void* p = ws ? (char*)ws + off : nullptr;
+        off += n;
+        return p;
+    };
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    w.chunk = chunk;
+    const int64_t rows = w.chunk * 128;
+    const int L = std::max(Le, Ln);
+    w.pq = (__nv_bfloat16*)take((size_t)NR * 2 * H * 2);
+    w.a = need_a ? (float*)take((size_t)NR * H * 4) : nullptr;
+    w.da = (float*)take((size_t)NR * H * 4);
+    w.dP = (float*)take((size_t)NR * H * 4);
+    w.dz1 = (__nv_bfloat16*)take((size_t)E * H * 2);
+    w.part = (float*)take((size_t)2 * num_sms() * kPstride * 4);
+    w.hs_stride = rows * H;
+    w.hs = (__nv_bfloat16*)take((size_t)(L - 1) * rows * H * 2);
+    w.dzs[0] = (__nv_bfloat16*)take((size_t)rows * H * 2);
+    w.dzs[1] = (__nv_bfloat16*)take((size_t)rows * H * 2);
+    w.xa = (__nv_bfloat16*)take((size_t)rows * 2 * H * 2);
+    w.bytes = off + 256;
+    return w;
+}
+
+// dz_{k-1} and the gradients of W_k, b_{k-1} for k = L-1 .. 1 over a chunk of
+// n_tiles tiles; returns the buffer that holds dz_0.
+int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, cudaStream_t s) {
+    constexpr int H = H128;
+    const int L = W.n_lin;
+    const uint32_t smem = chain_smem();
+    int grid;
+    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 2 * H, n_tiles, &grid);
+    if (rc) return rc;
+    const int64_t rows = n_tiles * 128;
+    for (int k = L - 1; k >= 1; --k) {
+        CUtensorMap tm_dz, tm_h;
+        if ((rc = make_row_tmap(&tm_dz, w.dzs[*cur], rows, H))) return rc;
+        if ((rc = make_row_tmap(&tm_h, w.hs + (int64_t)(k - 1) * w.hs_stride, rows, H))) return rc;
+        ChainArgs A;
+        A.W = W.W[k];
+        A.dz_out = w.dzs[*cur ^ 1];
+        A.n_tiles = n_tiles;
+        A.part = w.part;
+        A.pstride = kPstride;
+        {
+            ProfScope _ps(s, "k_bwd_chain");
+            k_bwd_chain<<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
+        }
+        GNN_LAUNCH_CHECK("k_bwd_chain");
+        RedSeg seg[2];
+        seg[0] = RedSeg{dW.W[k], H, H, H, 0, H};
+        seg[1] = RedSeg{dW.b[k - 1], H, 1, H, (int64_t)H * H, 0};
+        if ((rc = reduce_grads(seg, 2, w.part, kPstride, grid, s))) return rc;
+        *cur ^= 1;
+    }
+    return GNN_OK;
+}
+
+// gamma, beta and the last bias of an MLP from the recomputation's partials
+int reduce_ln(const gnn_mlp& dW, const B128Ws& w, int grid, cudaStream_t s) {
+    constexpr int H = H128;
+    RedSeg seg[3];
+    seg[0] = RedSeg{dW.gamma, H, 1, H, 0, 0};
+    seg[1] = RedSeg{dW.beta, H, 1, H, H, 0};
+    seg[2] = RedSeg{dW.b[dW.n_lin - 1], H, 1, H, 2 * H, 0};
+    return reduce_grads(seg, 3, w.part, kPstride, grid, s);
+}
+
+}  // namespace
+
+size_t backward_h128_ws(const gnn_graph_dev& G, const gnn_mp_params& W) {
+    return carve_b128(nullptr, G, W.edge.n_lin, W.node.n_lin, true, default_chunk(G)).bytes;
+}
+
+int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                  const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
+                  float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
+                  cudaStream_t s) {
+    constexpr int H = H128;
+    const int Le = W.edge.n_lin, Ln = W.node.n_lin;
+    GNN_REQUIRE(Le >= 2 && Le <= 4 && Ln >= 2 && Ln <= 4, GNN_EUNSUPPORTED,
+                "gnn_mp_backward: BF16 backward at H=128 supports 2 to 4 Linear layers per MLP");
+    // the largest chunk of tiles whose scratch fits the workspace given
+    const bool need_a = a_star == nullptr;
+    int64_t chunk = default_chunk(G);
+    if (ws_bytes < carve_b128(nullptr, G, Le, Ln, need_a, chunk).bytes) {
+        const size_t fixed = carve_b128(nullptr, G, Le, Ln, need_a, 0).bytes;
+        const size_t per_tile = carve_b128(nullptr, G, Le, Ln, need_a, 2).bytes - carve_b128(nullptr, G, Le, Ln, need_a, 1).bytes;
+        chunk = ws_bytes > fixed ? (int64_t)((ws_bytes - fixed) / per_tile) : 0;
+        while (chunk > 0 && carve_b128(nullptr, G, Le, Ln, need_a, chunk).bytes > ws_bytes) --chunk;
+        GNN_REQUIRE(chunk >= 1, GNN_ENOMEM, "gnn_mp_backward: workspace too small (%zu bytes)", ws_bytes);
+    }
+    B128Ws w = carve_b128(ws, G, Le, Ln, need_a, chunk);
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    if (NR == 0) return GNN_OK;
+    int rc;
+    // 0. recompute P|Q (and a* when it was not saved)
+    if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
+    if (!a_star) {
+        if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, nullptr, w.a, s))) return rc;
+    }
+    const float* astar = a_star ? a_star : w.a;
+    // 1. node MLP adjoint, chunk by chunk
+    const int64_t node_tiles = (NR + 127) / 128;
+    for (int64_t t0 = 0; t0 < node_tiles; t0 += w.chunk) {
+        const int64_t t1 = std::min(node_tiles, t0 + w.chunk);
+        RecomputeSave o{};
+        o.t0 = t0;
+        o.t1 = t1;
+        o.hs = w.hs;
+        o.hs_stride = w.hs_stride;
+        o.xa = w.xa;
+        o.dz = w.dzs[0];
+        o.dx_out = dx_out;
+        o.part = w.part;
+        o.pstride = kPstride;
+        if ((rc = node_recompute_save(G, cfg, W, astar, x_in, o, s))) return rc;
+        if ((rc = reduce_ln(dW.node, w, o.grid, s))) return rc;
+        int cur = 0;
+        if ((rc = chain_backward(W.node, dW.node, w, t1 - t0, &cur, s))) return rc;
+        CUtensorMap tm_dz, tm_xa;
+        const int64_t rows = (t1 - t0) * 128;
+        if ((rc = make_row_tmap(&tm_dz, w.dzs[cur], rows, H))) return rc;
+        if ((rc = make_row_tmap(&tm_xa, w.xa, rows, 2 * H))) return rc;
+        Node0Args A;
+        A.t0 = t0;
+        A.t1 = t1;
+        A.n_rows = NR;
+        A.W0 = W.node.W[0];
+        A.dx_out = dx_out;
+        A.da = w.da;
+        A.dx_in = dx_in;
+        A.part = w.part;
+        A.pstride = kPstride;
+        int grid;
+        if ((rc = persistent_grid(k_bwd_node0, kN0NT, Node0Smem::total, 4 * H, t1 - t0, &grid))) return rc;
+        {
+            ProfScope _ps(s, "k_bwd_node0");
+            k_bwd_node0<<<grid, kN0NT, Node0Smem::total, s>>>(tm_dz, tm_xa, A);
+        }
+        GNN_LAUNCH_CHECK("k_bwd_node0");
+        RedSeg seg[1] = {RedSeg{dW.node.W[0], 2 * H, H, 2 * H, 0, 2 * H}};
+        if ((rc = reduce_grads(seg, 1, w.part, kPstride, grid, s))) return rc;
+    }
+    // 2. adjoint of the halo swap + sync
+    if (cfg.halo_mode == GNN_HALO_SYNC) {
+        if ((rc = plain::halo(G, w.da, H, s))) return rc;
+    }
+    // 3. edge MLP adjoint, chunk by chunk
+    if (E > 0) {
+        GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
+                    "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
+        CUtensorMap tm_e;
+        if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
+        for (int64_t t0 = 0; t0 < G.n_edge_tiles; t0 += w.chunk) {
+            const int64_t t1 = std::min<int64_t>(G.n_edge_tiles, t0 + w.chunk);
+            RecomputeSave o{};
+            o.t0 = t0;
+            o.t1 = t1;
+            o.hs = w.hs;
+            o.hs_stride = w.hs_stride;
+            o.dz = w.dzs[0];
+            o.da = w.da;
+            o.de_out = de_out;
+            o.part = w.part;
+            o.pstride = kPstride;
+            if ((rc = edge_recompute_save(G, cfg, W, e_in, w.pq, o, s))) return rc;
+            if ((rc = reduce_ln(dW.edge, w, o.grid, s))) return rc;
+            int cur = 0;
+            if ((rc = chain_backward(W.edge, dW.edge, w, t1 - t0, &cur, s))) return rc;
+            CUtensorMap tm_dz;
+            if ((rc = make_row_tmap(&tm_dz, w.dzs[cur], (t1 - t0) * 128, H))) return rc;
+            Edge0Args A;
+            A.tile_meta = static_cast<const uint8_t*>(G.tile_meta);
+            A.t0 = t0;
+            A.t1 = t1;
+            A.W1 = W.edge.W[0];
+            A.de_out = de_out;
+            A.da = w.da;
+            A.de_in = de_in;
+            A.dz1 = w.dz1;
+            A.dP = w.dP;
+            A.part = w.part;
+            A.pstride = kPstride;
+            int grid;
+            if ((rc = persistent_grid(k_bwd_edge0, kE0NT, Edge0Smem::total, 2 * H, t1 - t0, &grid))) return rc;
+            {
+                ProfScope _ps(s, "k_bwd_edge0");
+                k_bwd_edge0<<<grid, kE0NT, Edge0Smem::total, s>>>(tm_dz, tm_e, A);
+            }
+            GNN_LAUNCH_CHECK("k_bwd_edge0");
+            RedSeg seg[1] = {RedSeg{dW.edge.W[0] + 2 * H, 3 * H, H, H, 0, H}};   // W1c columns of W1
+            if ((rc = reduce_grads(seg, 1, w.part, kPstride, grid, s))) return rc;
+        }
+    } else {
+        GNN_CUDA_CHECK(cudaMemsetAsync(w.dP, 0, sizeof(float) * NR * H, s), "memset");
+    }
+    // 4. projection adjoint: sender-side sums, dx_in += [dP dQ] [W1a; W1b], dW1a, dW1b
+    return proj_backward(G, H, W, x_in, w.dP, w.dz1, dx_in, dW, w.part, s);
+}
+
+}  // namespace fused
+}  // namespace gnn

@@ -152,15 +152,29 @@ struct EdgeFwdArgs {
     float* a;
     MlpDev mlp;
     float eps;
+    // Backward recomputation (k_edge_fwd<H, true>): tiles [t0, n_tiles); the
+    // scratch row of edge row i of tile t is (t - t0) * 128 + i (zero past ne).
+    int64_t t0;
+    __nv_bfloat16* hs;            // hidden activations h_0 .. h_{L-2}, hs_stride elements apart
+    int64_t hs_stride;
+    __nv_bfloat16* dz;            // gradient of the last pre-activation (LayerNorm adjoint)
+    const float* da;              // gradient of the aggregate after the halo adjoint
+    const __nv_bfloat16* de_out;  // upstream gradient of e' (NULL: zero)
+    float* part;                  // per-CTA partials: gamma, beta, last bias gradients (3H)
+    int64_t pstride;
 };
 
-template <int H>
+// SAVE: the backward's recomputation of the edge MLP (Eq. 5a) over a range of
+// tiles: the hidden activations go to scratch instead of the next Linear only,
+// and the LayerNorm epilogue is replaced by its adjoint, whose input is the
+// gradient of e' (upstream de' plus da_i / d_ij, the adjoint of Eq. 5b).
+template <int H, bool SAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     const int n_lin = A.mlp.n_lin;
-    const EdgeFwdSmem L = edge_fwd_smem<H>(n_lin);
+    const EdgeFwdSmem L = edge_fwd_smem<H>(n_lin, SAVE);
     uint8_t* sW = sm + L.w;
     uint8_t* sA0 = sm + L.a0;
     uint8_t* sA1 = sm + L.a1;
@@ -200,8 +214,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
     const uint32_t tmem = *tslot;
     uint32_t ph_tma = 0, ph_mma = 0;
     bool ok = true;
+    constexpr int NCH = C::CW / 16;
+    float accG[NCH], accB[NCH], accZ[NCH];   // SAVE: column sums of g*xhat, g, dz
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) accG[j] = accB[j] = accZ[j] = 0.f;
+    const int64_t tb = SAVE ? A.t0 : 0;
 
-    for (int64_t t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
+    for (int64_t t = tb + blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
         const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
         const int32_t e0 = A.row_ptr[r0], e1 = A.row_ptr[r1];
         const int ne = e1 - e0;
@@ -265,6 +284,16 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
 #pragma unroll
                 for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
                 st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+                if constexpr (SAVE) {
+                    __nv_bfloat16* hrow = A.hs + k * A.hs_stride + ((t - tb) * 128 + row) * H + c0;
+#pragma unroll
+                    for (int i = 0; i < C::CW; i += 8) {
+                        float z8[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) z8[j] = valid ? v[i + j] : 0.f;
+                        st_bf16x8(hrow + i, z8);
+                    }
+                }
                 fence_proxy_async();
                 tc_fence_before();
                 __syncthreads();
@@ -277,6 +306,43 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
         }
         if (!ok) break;
         tc_fence_before();
+        if constexpr (SAVE) {
+            // gradient of e': upstream de' plus da_i / d_ij, then the LayerNorm adjoint
+            float gv[C::CW];
+            if (valid) {
+                const float* dar = A.da + (int64_t)(r0 + sSeg[row]) * H + c0;
+#pragma unroll
+                for (int i = 0; i < C::CW; i += 4) {
+                    const float4 u = __ldg(reinterpret_cast<const float4*>(dar + i));
+                    gv[i] = w * u.x;
+                    gv[i + 1] = w * u.y;
+                    gv[i + 2] = w * u.z;
+                    gv[i + 3] = w * u.w;
+                }
+                if (A.de_out) {
+#pragma unroll
+                    for (int i = 0; i < C::CW; i += 8) {
+                        float d8[8];
+                        ld_bf16x8(A.de_out + eg * H + c0 + i, d8);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) gv[i + j] = d8[j] + gv[i + j];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) gv[i] = 0.f;
+            }
+            const float* gam = sPar + n_lin * H + c0;
+            float mean, rstd, s1, s2;
+            row_stats_adj_gamma<H, C::CG, C::CW>(v, gv, gam, sRed, row, g, A.eps, mean, rstd, s1, s2);
+            ln_adjoint_row<C::CW>(v, gv, gam, mean, rstd, s1, s2, valid, lane, accG, accB, accZ);
+            __nv_bfloat16* zrow = A.dz + ((t - tb) * 128 + row) * H + c0;
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) st_bf16x8(zrow + i, v + i);
+            fence_proxy_async();
+            __syncthreads();   // the tile's smem (CSR slice, input tile) is rewritten by the next tile
+            continue;
+        }
         // LayerNorm + residual (Eq. 5a)
         float mean, rstd;
         row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
@@ -312,6 +378,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
         }
         fence_proxy_async();
         __syncthreads();
+    }
+    if constexpr (SAVE) {
+        float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+        colsum_store<H, NCH>(accG, sRed, q, lane, c0, tid, C::NT, part);
+        colsum_store<H, NCH>(accB, sRed, q, lane, c0, tid, C::NT, part + H);
+        colsum_store<H, NCH>(accZ, sRed, q, lane, c0, tid, C::NT, part + 2 * H);
     }
     tc_fence_before();
     __syncthreads();
@@ -958,16 +1030,31 @@ struct NodeFwdArgs {
     int64_t n_rows;
     MlpDev mlp;
     float eps;
+    // Backward recomputation (k_node_fwd<H, false, true>): tiles [t0, t1); the
+    // scratch row of node row t*128 + i is (t - t0) * 128 + i (zero past n_rows).
+    int64_t t0, t1;
+    __nv_bfloat16* hs;            // hidden activations h_0 .. h_{L-2}, hs_stride elements apart
+    int64_t hs_stride;
+    __nv_bfloat16* xa;            // the BF16 input rows [a*, x] (2H wide)
+    __nv_bfloat16* dz;            // gradient of the last pre-activation (LayerNorm adjoint)
+    const float* dx_out;          // upstream gradient of x'
+    float* part;                  // per-CTA partials: gamma, beta, last bias gradients (3H)
+    int64_t pstride;
 };
 
-template <int H, bool PF>
+// SAVE: the backward's recomputation of the node MLP (Eq. 5e): the BF16 input
+// rows and hidden activations go to scratch and the LayerNorm epilogue is
+// replaced by its adjoint, whose input is the gradient of x' (the residual
+// branch passes it through unchanged).
+template <int H, bool PF, bool SAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__ CUtensorMap tmap_a,
                                                         const __grid_constant__ CUtensorMap tmap_x, NodeFwdArgs A) {
+    static_assert(!(PF && SAVE), "the recomputation reads its inputs directly");
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     const int n_lin = A.mlp.n_lin;
-    const NodeFwdSmem L = node_fwd_smem<H, PF>(n_lin);
+    const NodeFwdSmem L = node_fwd_smem<H, PF>(n_lin, SAVE);
     uint8_t* sW0 = sm + L.w0;
     uint8_t* sW = sm + L.w;
     uint8_t* sA0 = sm + L.a0;
@@ -1018,10 +1105,17 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         if (tid == 0 && (int64_t)blockIdx.x < n_tiles) issue(0, blockIdx.x);
     }
     int j = 0;
+    constexpr int NCH = C::CW / 16;
+    float accG[NCH], accB[NCH], accZ[NCH];   // SAVE: column sums of g*xhat, g, dz
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) accG[i] = accB[i] = accZ[i] = 0.f;
+    const int64_t tb = SAVE ? A.t0 : 0, te = SAVE ? A.t1 : n_tiles;
 
-    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+    for (int64_t t = tb + blockIdx.x; t < te && ok; t += gridDim.x, ++j) {
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
+        const int64_t srow = (t - tb) * 128 + row;   // SAVE: scratch row
+        (void)srow;
         const int st = j & 1;
         float xa[C::CW], xv[C::CW];
         if constexpr (PF) {
@@ -1048,6 +1142,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         } else {
 #pragma unroll
             for (int i = 0; i < C::CW; ++i) xa[i] = xv[i] = 0.f;
+        }
+        if constexpr (SAVE) {
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) {
+                st_bf16x8(A.xa + srow * 2 * H + c0 + i, xa + i);
+                st_bf16x8(A.xa + srow * 2 * H + H + c0 + i, xv + i);
+            }
         }
         if constexpr (!NodeSplit<H>::value) {
 #pragma unroll
@@ -1099,6 +1200,16 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
             if (k < n_lin - 1) {
                 elu_inplace2<C::CW>(v);
                 st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+                if constexpr (SAVE) {
+                    __nv_bfloat16* hrow = A.hs + k * A.hs_stride + srow * H + c0;
+#pragma unroll
+                    for (int i = 0; i < C::CW; i += 8) {
+                        float z8[8];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) z8[jj] = valid ? v[i + jj] : 0.f;
+                        st_bf16x8(hrow + i, z8);
+                    }
+                }
                 fence_proxy_async();
                 tc_fence_before();
                 __syncthreads();
@@ -1111,6 +1222,28 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         }
         if (!ok) break;
         tc_fence_before();
+        if constexpr (SAVE) {
+            float gv[C::CW];
+            if (valid) {
+                const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
+#pragma unroll
+                for (int i = 0; i < C::CW / 4; ++i) {
+                    const float4 u = __ldg(pg + i);
+                    gv[4 * i] = u.x; gv[4 * i + 1] = u.y; gv[4 * i + 2] = u.z; gv[4 * i + 3] = u.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) gv[i] = 0.f;
+            }
+            const float* gam = sPar + n_lin * H + c0;
+            float mean, rstd, s1, s2;
+            row_stats_adj_gamma<H, C::CG, C::CW>(v, gv, gam, sRed, row, g, A.eps, mean, rstd, s1, s2);
+            ln_adjoint_row<C::CW>(v, gv, gam, mean, rstd, s1, s2, valid, lane, accG, accB, accZ);
+#pragma unroll
+            for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.dz + srow * H + c0 + i, v + i);
+            __syncthreads();
+            continue;
+        }
         float mean, rstd;
         row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
         const float* gam = sPar + n_lin * H + c0;
@@ -1133,6 +1266,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         }
         if constexpr (PF) fence_proxy_async();   // generic reads of the stage precede its next TMA write
         __syncthreads();
+    }
+    if constexpr (SAVE) {
+        float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+        colsum_store<H, NCH>(accG, sRed, q, lane, c0, tid, C::NT, part);
+        colsum_store<H, NCH>(accB, sRed, q, lane, c0, tid, C::NT, part + H);
+        colsum_store<H, NCH>(accZ, sRed, q, lane, c0, tid, C::NT, part + 2 * H);
     }
     tc_fence_before();
     __syncthreads();
@@ -1390,6 +1529,82 @@ int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
     if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
     if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s))) return rc;
     return node_forward(G, cfg, W, a, x_in, x_out, s);
+}
+
+// ------------------------------------------------------------------ backward recomputation (H = 128)
+
+int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                        const __nv_bfloat16* e_in, const __nv_bfloat16* pq, RecomputeSave& o, cudaStream_t s) {
+    constexpr int H = 128;
+    using C = Cfg<H>;
+    const int64_t NR = G.n_rows, E = G.n_edges;
+    GNN_REQUIRE(cfg.hidden == H, GNN_EUNSUPPORTED, "edge_recompute_save: H=%d", cfg.hidden);
+    CUtensorMap tm;
+    int rc = make_row_tmap(&tm, e_in, E, H);
+    if (rc) return rc;
+    EdgeFwdArgs A{};
+    A.row_ptr = G.row_ptr;
+    A.col = G.col;
+    A.edge_w = G.edge_w;
+    A.tiles = G.edge_tiles;
+    A.tile_meta = static_cast<const uint8_t*>(G.tile_meta);
+    A.n_tiles = o.t1;
+    A.n_edges = E;
+    A.pq = pq;
+    A.q = pq + NR * H;
+    A.mlp = mlp_dev(W.edge);
+    A.eps = cfg.ln_eps;
+    A.t0 = o.t0;
+    A.hs = o.hs;
+    A.hs_stride = o.hs_stride;
+    A.dz = o.dz;
+    A.da = o.da;
+    A.de_out = o.de_out;
+    A.part = o.part;
+    A.pstride = o.pstride;
+    const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin, true);
+    if ((rc = persistent_grid(k_edge_fwd<H, true>, C::NT, L.total, C::TCOLS, o.t1 - o.t0, &o.grid))) return rc;
+    {
+        ProfScope _ps(s, "k_edge_fwd_save");
+        k_edge_fwd<H, true><<<o.grid, C::NT, L.total, s>>>(tm, A);
+    }
+    GNN_LAUNCH_CHECK("k_edge_fwd_save");
+    return GNN_OK;
+}
+
+int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                        const float* a_star, const float* x_in, RecomputeSave& o, cudaStream_t s) {
+    constexpr int H = 128;
+    using C = Cfg<H>;
+    GNN_REQUIRE(cfg.hidden == H, GNN_EUNSUPPORTED, "node_recompute_save: H=%d", cfg.hidden);
+    NodeFwdArgs A{};
+    A.a_star = a_star;
+    A.x = x_in;
+    A.n_rows = G.n_rows;
+    A.mlp = mlp_dev(W.node);
+    A.eps = cfg.ln_eps;
+    A.t0 = o.t0;
+    A.t1 = o.t1;
+    A.hs = o.hs;
+    A.hs_stride = o.hs_stride;
+    A.xa = o.xa;
+    A.dz = o.dz;
+    A.dx_out = o.dx_out;
+    A.part = o.part;
+    A.pstride = o.pstride;
+    CUtensorMap tma, tmx;   // unused by the recomputation (it reads its rows directly)
+    int rc = make_f32_tmap(&tma, a_star, G.n_rows, H);
+    if (rc) return rc;
+    if ((rc = make_f32_tmap(&tmx, x_in, G.n_rows, H))) return rc;
+    const NodeFwdSmem L = node_fwd_smem<H, false>(W.node.n_lin, true);
+    if ((rc = persistent_grid(k_node_fwd<H, false, true>, C::NT, L.total, C::TCOLS, o.t1 - o.t0, &o.grid)))
+        return rc;
+    {
+        ProfScope _ps(s, "k_node_fwd_save");
+        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, A);
+    }
+    GNN_LAUNCH_CHECK("k_node_fwd_save");
+    return GNN_OK;
 }
 
 }  // namespace fused

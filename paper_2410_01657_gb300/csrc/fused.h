@@ -35,6 +35,41 @@ int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
                  const float* x_in, float* x_out, cudaStream_t s);
 
+// Backward recomputation of the edge or node MLP at H = 128 over the tiles
+// [t0, t1): saves the hidden activations (and, for nodes, the BF16 [a*, x]
+// input rows) to tile-padded scratch rows (t - t0) * 128 + i, and applies the
+// LayerNorm adjoint to the gradient of the layer output. Writes per-CTA
+// partials [dgamma | dbeta | db_last] (3H floats, pstride apart) for `grid` CTAs.
+struct RecomputeSave {
+    int64_t t0, t1;
+    __nv_bfloat16* hs;            // h_0 .. h_{L-2}, hs_stride elements apart
+    int64_t hs_stride;
+    __nv_bfloat16* xa;            // nodes: [rows x 2H]
+    __nv_bfloat16* dz;            // gradient of the last pre-activation [rows x H]
+    const float* da;              // edges: aggregate gradient after the halo adjoint
+    const __nv_bfloat16* de_out;  // edges: upstream gradient of e' (NULL: zero)
+    const float* dx_out;          // nodes: upstream gradient of x'
+    float* part;
+    int64_t pstride;
+    int grid;                     // out
+};
+int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                        const __nv_bfloat16* e_in, const __nv_bfloat16* pq, RecomputeSave& o, cudaStream_t s);
+int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
+                        const float* a_star, const float* x_in, RecomputeSave& o, cudaStream_t s);
+
+// Projection adjoint of the BF16 backward: dQ from dz1 over each row's sent
+// edges, dx_in += dP W1a + dQ W1b, dW1a and dW1b added into dW.edge.W[0].
+int proj_backward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const float* x_in, const float* dP,
+                  const __nv_bfloat16* dz1, float* dx_in, const gnn_mp_params& dW, float* part, cudaStream_t s);
+
+// Layered BF16 backward at H = 128 (recomputation, per-Linear adjoint kernels).
+size_t backward_h128_ws(const gnn_graph_dev& G, const gnn_mp_params& W);
+int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
+                  const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
+                  float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
+                  cudaStream_t s);
+
 // Fused BF16 row MLP (encoders / decoder of the network).
 bool rowmlp_supported(const gnn_mlp& P);
 size_t rowmlp_backward_ws(const gnn_mlp& P);

@@ -789,8 +789,11 @@ struct CfgP {
     static constexpr int NT = 128 * CG;
 };
 
+// Two CTAs per SM up to H = 64; at H = 128 one (registers and shared memory).
+// The weight gradient [dW1a; dW1b] = [dP dQ]^T x is one M = 2H MMA up to
+// H = 64 and two M = 128 halves at H = 128.
 template <int H>
-__global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
+__global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(ProjBwdArgs A) {
     using C = CfgP<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -801,7 +804,8 @@ __global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, S2 = C::S2, CW = C::CW;
-    constexpr uint32_t NCOLS = pow2_cols(2 * H);
+    constexpr bool MSPLIT = 2 * H > 128;
+    constexpr uint32_t NCOLS = pow2_cols(MSPLIT ? 3 * H : 2 * H);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
@@ -897,7 +901,12 @@ __global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
         if (tid == 0) {
             tc_fence_after();
             issue_dgrad(tWork, sA, S2, sW, S, 2 * H, (uint32_t)(2 * H) * S, H, 2 * H);
-            issue_wgrad(tDW, sA, S2, 128u * S2, sX, S, 128u * S, H, !first);
+            if constexpr (MSPLIT) {   // dW1a from the dP columns, dW1b from the dQ columns
+                issue_wgrad(tDW, sA, S2, 128u * S2, sX, S, 128u * S, H, !first);
+                issue_wgrad(tDW + H, sA + (H / (S2 / 2)) * 128 * S2, S2, 128u * S2, sX, S, 128u * S, H, !first);
+            } else {
+                issue_wgrad(tDW, sA, S2, 128u * S2, sX, S, 128u * S, H, !first);
+            }
             mma_commit(bar);
         }
         ok = block_wait(bar, ph, tid);
@@ -927,10 +936,14 @@ __global__ void __launch_bounds__(CfgP<H>::NT, 2) k_proj_bwd(ProjBwdArgs A) {
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {
-        const int M = 2 * H < 128 ? 2 * H : 128;
-        if (!first) flush_acc<C::CG>(tDW, H, M, q, lane, g, part);
-        else
+        if (first) {
             for (int i = tid; i < 2 * H * H; i += C::NT) part[i] = 0.f;
+        } else if constexpr (MSPLIT) {
+            flush_acc<C::CG>(tDW, H, H, q, lane, g, part);
+            flush_acc<C::CG>(tDW + H, H, H, q, lane, g, part + H * H);
+        } else {
+            flush_acc<C::CG>(tDW, H, 2 * H, q, lane, g, part);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -1027,6 +1040,39 @@ BwdWs carve_bwd(void* ws, const gnn_graph_dev& G, int H, int Le, int Ln, bool ne
     w.part = (float*)take((size_t)std::max(ncta * ps, 2 * ncta * proj_pstride(H)) * 4);
     w.bytes = off + 256;
     return w;
+}
+
+template <int H>
+int proj_backward_h(const gnn_graph_dev& G, const gnn_mp_params& W, const float* x_in, const float* dP,
+                    const __nv_bfloat16* dz1, float* dx_in, const gnn_mp_params& dW, float* part, cudaStream_t s) {
+    const int64_t NR = G.n_rows;
+    if (NR == 0) return GNN_OK;
+    ProjBwdArgs A;
+    A.x = x_in;
+    A.dP = dP;
+    A.dz1 = dz1;
+    A.t_ptr = G.t_ptr;
+    A.t_eid = G.t_eid;
+    A.W1 = W.edge.W[0];
+    A.dx_in = dx_in;
+    A.part = part;
+    A.pstride = proj_pstride(H);
+    A.n_rows = NR;
+    const ProjBwdSmem P = proj_bwd_smem<H>();
+    int grid;
+    int rc = persistent_grid(k_proj_bwd<H>, CfgP<H>::NT, P.total, pow2_cols(2 * H > 128 ? 3 * H : 2 * H),
+                             (NR + 127) / 128, &grid);
+    if (rc) return rc;
+    grid = std::min(grid, 2 * num_sms());
+    {
+        ProfScope _ps(s, "k_proj_bwd");
+        k_proj_bwd<H><<<grid, CfgP<H>::NT, P.total, s>>>(A);
+    }
+    GNN_LAUNCH_CHECK("k_proj_bwd");
+    RedSeg seg[2];
+    seg[0] = RedSeg{dW.edge.W[0], 3 * H, H, H, 0, H};                     // dW1a -> W1[:, 0:H]
+    seg[1] = RedSeg{dW.edge.W[0] + H, 3 * H, H, H, (int64_t)H * H, H};    // dW1b -> W1[:, H:2H]
+    return reduce_grads(seg, 2, part, A.pstride, grid, s);
 }
 
 template <int H>
@@ -1150,40 +1196,25 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         GNN_CUDA_CHECK(cudaMemsetAsync(w.dP, 0, sizeof(float) * NR * H, s), "memset");
     }
     // 4. projection adjoint: sender-side sums, dx_in += [dP dQ] [W1a; W1b], dW1a, dW1b
-    {
-        ProjBwdArgs A;
-        A.x = x_in;
-        A.dP = w.dP;
-        A.dz1 = w.dz1;
-        A.t_ptr = G.t_ptr;
-        A.t_eid = G.t_eid;
-        A.W1 = W.edge.W[0];
-        A.dx_in = dx_in;
-        A.part = w.part;
-        A.pstride = proj_pstride(H);
-        A.n_rows = NR;
-        const ProjBwdSmem P = proj_bwd_smem<H>();
-        int grid;
-        rc = persistent_grid(k_proj_bwd<H>, CfgP<H>::NT, P.total, pow2_cols(2 * H), (NR + 127) / 128, &grid);
-        if (rc) return rc;
-        grid = std::min(grid, 2 * nsm);
-        {
-            ProfScope _ps(s, "k_proj_bwd");
-            k_proj_bwd<H><<<grid, CfgP<H>::NT, P.total, s>>>(A);
-        }
-        GNN_LAUNCH_CHECK("k_proj_bwd");
-        RedSeg seg[2];
-        seg[0] = RedSeg{dW.edge.W[0], 3 * H, H, H, 0, H};                     // dW1a -> W1[:, 0:H]
-        seg[1] = RedSeg{dW.edge.W[0] + H, 3 * H, H, H, (int64_t)H * H, H};    // dW1b -> W1[:, H:2H]
-        if ((rc = reduce_grads(seg, 2, w.part, A.pstride, grid, s))) return rc;
-    }
-    return GNN_OK;
+    return proj_backward_h<H>(G, W, x_in, w.dP, w.dz1, dx_in, dW, w.part, s);
 }
 
 }  // namespace
 
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
+    if (cfg.hidden == 128) return backward_h128_ws(G, W);
     return carve_bwd(nullptr, G, cfg.hidden, W.edge.n_lin, W.node.n_lin, true).bytes;
+}
+
+int proj_backward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const float* x_in, const float* dP,
+                  const __nv_bfloat16* dz1, float* dx_in, const gnn_mp_params& dW, float* part, cudaStream_t s) {
+    switch (H) {
+        case 16: return proj_backward_h<16>(G, W, x_in, dP, dz1, dx_in, dW, part, s);
+        case 32: return proj_backward_h<32>(G, W, x_in, dP, dz1, dx_in, dW, part, s);
+        case 64: return proj_backward_h<64>(G, W, x_in, dP, dz1, dx_in, dW, part, s);
+        case 128: return proj_backward_h<128>(G, W, x_in, dP, dz1, dx_in, dW, part, s);
+        default: return set_error(GNN_EUNSUPPORTED, "proj_backward: H=%d", H);
+    }
 }
 
 int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
@@ -1194,8 +1225,9 @@ int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_p
         case 16: return backward_h<16>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
         case 32: return backward_h<32>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
         case 64: return backward_h<64>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
+        case 128: return backward_h128(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
         default:
-            return set_error(GNN_EUNSUPPORTED, "gnn_mp_backward: the BF16 backward covers H in {16, 32, 64}");
+            return set_error(GNN_EUNSUPPORTED, "gnn_mp_backward: the BF16 backward covers H in {16, 32, 64, 128}");
     }
 }
 

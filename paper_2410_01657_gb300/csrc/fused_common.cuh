@@ -210,6 +210,102 @@ __device__ __forceinline__ void row_stats(const float* v, float* red, int row, i
     rstd = rsqrtf(fmaxf(tq * (1.f / H) - mean * mean, 0.f) + eps);
 }
 
+// LayerNorm statistics of v and the adjoint sums of d = g * gamma over a row
+// split over CG threads, in one exchange through red[4][CG][128]: mean, rstd,
+// s1 = (1/H) sum d and s2 = (1/H) sum d * xhat = rstd (sum d v - mean sum d) / H.
+template <int H, int CG, int CW>
+__device__ __forceinline__ void row_stats_adj_gamma(const float* v, const float* gv, const float* gam, float* red,
+                                                    int row, int g, float eps, float& mean, float& rstd, float& s1,
+                                                    float& s2) {
+    float sv = 0.f, sq = 0.f, sd = 0.f, sdv = 0.f;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        const float d = gv[i] * gam[i];
+        sv += v[i];
+        sq += v[i] * v[i];
+        sd += d;
+        sdv += d * v[i];
+    }
+    red[(0 * CG + g) * 128 + row] = sv;
+    red[(1 * CG + g) * 128 + row] = sq;
+    red[(2 * CG + g) * 128 + row] = sd;
+    red[(3 * CG + g) * 128 + row] = sdv;
+    __syncthreads();
+    sv = sq = sd = sdv = 0.f;
+#pragma unroll
+    for (int k = 0; k < CG; ++k) {
+        sv += red[(0 * CG + k) * 128 + row];
+        sq += red[(1 * CG + k) * 128 + row];
+        sd += red[(2 * CG + k) * 128 + row];
+        sdv += red[(3 * CG + k) * 128 + row];
+    }
+    __syncthreads();   // red is reused by the caller
+    mean = sv * (1.f / H);
+    rstd = rsqrtf(fmaxf(sq * (1.f / H) - mean * mean, 0.f) + eps);
+    s1 = sd * (1.f / H);
+    s2 = rstd * (sdv - mean * sd) * (1.f / H);
+}
+
+// Sum of v[0..15] over the 32 lanes of a warp by recursive halving: at each
+// step a lane keeps half of its values and adds its partner's copy of that
+// half. Lane l returns the total of value (l >> 1); lanes l and l^1 agree.
+__device__ __forceinline__ float warp_colsum16(const float* v, int lane) {
+    float a[8], b[4], c[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        a[i] = (b4 ? v[i + 8] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 8], 16);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        b[i] = (b3 ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, b3 ? a[i] : a[i + 4], 8);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        c[i] = (b2 ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, b2 ? b[i] : b[i + 2], 4);
+    float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
+// Column sums accumulated per warp by warp_colsum16 (acc[j]: column
+// c0 + 16 j + (lane >> 1) over the warp's 32 rows) summed over the four row
+// quarters in ascending order into out[0..H); red holds 4*H floats.
+template <int H, int NCH>
+__device__ __forceinline__ void colsum_store(const float* acc, float* red, int q, int lane, int c0, int tid, int nt,
+                                             float* out) {
+    __syncthreads();
+    if ((lane & 1) == 0) {
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) red[q * H + c0 + 16 * j + (lane >> 1)] = acc[j];
+    }
+    __syncthreads();
+    for (int c = tid; c < H; c += nt) out[c] = ((red[c] + red[H + c]) + red[2 * H + c]) + red[3 * H + c];
+    __syncthreads();
+}
+
+// LayerNorm adjoint of one row's CW columns (the thread's share), given the
+// statistics of row_stats_adj_gamma: v (the pre-LayerNorm values) is replaced
+// by dz = rstd (g gamma - s1 - xhat s2); the column sums of g * xhat, g and
+// dz over the warp's rows are added to accG, accB, accZ (one per 16 columns).
+// Rows that are not valid contribute zeros.
+template <int CW>
+__device__ __forceinline__ void ln_adjoint_row(float* v, const float* gv, const float* gam, float mean, float rstd,
+                                               float s1, float s2, bool valid, int lane, float* accG, float* accB,
+                                               float* accZ) {
+#pragma unroll
+    for (int j = 0; j < CW / 16; ++j) {
+        float t[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = 16 * j + i;
+            const float xh = valid ? (v[c] - mean) * rstd : 0.f;
+            t[i] = gv[c] * xh;
+            v[c] = valid ? rstd * (gv[c] * gam[c] - s1 - xh * s2) : 0.f;
+        }
+        accG[j] += warp_colsum16(t, lane);
+        accB[j] += warp_colsum16(gv + 16 * j, lane);
+        accZ[j] += warp_colsum16(v + 16 * j, lane);
+    }
+}
+
 __device__ __forceinline__ void ld_bf16x8(const __nv_bfloat16* p, float* v) {
     uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
     unpack_bf16x2(u.x, v[0], v[1]);
@@ -233,8 +329,10 @@ struct EdgeFwdSmem {
     uint32_t w, a0, a1, par, seg, red, bar, tm, total;
 };
 
+// adj: the backward's recomputation (SAVE mode), whose LayerNorm adjoint
+// exchanges four row sums instead of two.
 template <int H>
-__host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin) {
+__host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin, bool adj = false) {
     using C = Cfg<H>;
     EdgeFwdSmem s;
     s.w = 0;
@@ -243,7 +341,7 @@ __host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin) {
     s.par = align_up(s.a1 + C::TILE, 16);
     s.seg = s.par + (n_lin + 2) * H * 4;               // seg[128] then the tile's CSR slice rp[132]
     s.red = s.seg + (128 + 132) * 4;
-    s.bar = align_up(s.red + 2 * C::CG * 128 * 4, 8);
+    s.bar = align_up(s.red + (adj ? 4 : 2) * C::CG * 128 * 4, 8);
     s.tm = s.bar + 16;
     s.total = s.tm + 16 + 1024;      // + slack for 1024-byte alignment of the base
     return s;
@@ -264,7 +362,7 @@ struct NodeSplit {
 };
 
 template <int H, bool PF = false>
-__host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin) {
+__host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin, bool adj = false) {
     using C = Cfg<H>;
     constexpr bool split = NodeSplit<H>::value;
     NodeFwdSmem s;
@@ -274,7 +372,7 @@ __host__ __device__ inline NodeFwdSmem node_fwd_smem(int n_lin) {
     s.a1 = split ? s.a0 : s.a0 + 2 * C::TILE;          // split: the chain reuses the input buffer
     s.par = align_up(s.a1 + C::TILE, 16);
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.xs = align_up(s.red + 2 * C::CG * 128 * 4, 1024);
+    s.xs = align_up(s.red + (adj ? 4 : 2) * C::CG * 128 * 4, 1024);
     s.bar = align_up(s.xs + (PF ? 2 * 2 * 128 * H * 4 : 0), 8);   // mma, full[2]
     s.tm = s.bar + 24;
     s.total = s.tm + 16 + 1024;

@@ -247,7 +247,9 @@ class LayerStack:
     Inference keeps the inputs and two edge-state and two node-state buffers
     (ping-pong) and skips the last layer's edge-state write (GNN_FLAG_NO_EDGE_OUT): only the
     aggregates reach the node update, so no per-edge output of the last layer
-    touches HBM."""
+    touches HBM. Training keeps every layer's input states and a* (the
+    backward recomputes from them) and two node- and two edge-gradient buffers
+    (ping-pong: layer l writes dx[l % 2], de[l % 2]; dx[0] ends as dL/dx0)."""
 
     def __init__(self, G: DeviceGraph, layers, hidden: int, precision: str, x0, e0, halo: bool = True,
                  ln_eps: float = 1e-5, inference: bool = False):
@@ -280,8 +282,8 @@ class LayerStack:
             self.e = [e0.to(edt).contiguous()] + [torch.empty(E, hidden, device=dev, dtype=edt)
                                                   for _ in range(self.M)]
             self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
-            self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(self.M + 1)]
-            self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(self.M)]
+            self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(2)]
+            self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(min(2, self.M))]
         f, b = mp_workspace_sizes(G, self.cfg, self.W[0])
         self.ws = workspace(f if inference else max(f, b), dev)
         self.graph = None
@@ -316,9 +318,10 @@ class LayerStack:
         assert not self.inference, "an inference stack has no backward"
         dx_out, de_out = dx_top, None
         for l in range(self.M - 1, -1, -1):
+            dx_in, de_in = self.dx[l % 2], self.de[l % 2]
             gnn_mp_backward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.a[l], dx_out, de_out,
-                            self.dx[l], self.de[l], self.dW[l], self.ws)
-            dx_out, de_out = self.dx[l], self.de[l]
+                            dx_in, de_in, self.dW[l], self.ws)
+            dx_out, de_out = dx_in, de_in
 
     def step(self, dx_top=None):
         if self.inference:

@@ -165,7 +165,7 @@ def test_fused_partitioned_vs_unpartitioned():
     assert rel_l2(out[8], out[1]) < 1e-2
 
 
-def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=True):
+def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=True, ws_bytes=None):
     brick, subs, part, G, params, x, e = _layer_case(nel, p, R, H, n_hidden, seed=seed)
     lp = params["layers"][0]
     rng = np.random.default_rng(seed + 5)
@@ -186,8 +186,9 @@ def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=Tr
     xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
     gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
     dxi, dei = torch.empty_like(xt), torch.empty_like(et)
+    ws = None if ws_bytes is None else gnn.workspace(ws_bytes(G, cfg, W), DEV)
     gnn.gnn_mp_backward(G, cfg, W, xt, et, a, _to(dx1), _to(de1, torch.bfloat16) if with_de else None,
-                        dxi, dei, dW)
+                        dxi, dei, dW, ws)
     B.call("gnn_check", None)
     refs = list(g["edge"]["W"]) + list(g["edge"]["b"]) + [g["edge"]["gamma"], g["edge"]["beta"]] \
         + list(g["node"]["W"]) + list(g["node"]["b"]) + [g["node"]["gamma"], g["node"]["beta"]]
@@ -195,7 +196,7 @@ def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=Tr
             np.concatenate(dx0), np.concatenate(de0), refs)
 
 
-@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 2), (64, 2), (64, 0), (32, 5)])
+@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 2), (64, 2), (64, 0), (32, 5), (128, 2), (128, 1), (128, 0)])
 @pytest.mark.parametrize("R", [1, 3])
 def test_fused_layer_backward_vs_oracle(H, n_hidden, R):
     dx, de, dws, dx_ref, de_ref, refs = _layer_backward_case(H, n_hidden, R)
@@ -210,6 +211,45 @@ def test_fused_layer_backward_without_edge_grad():
     assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
     for got, ref in zip(dws, refs):
         assert rel_l2(got, ref) < TOL_GRAD
+
+
+def test_fused_backward_h128_without_edge_grad():
+    dx, de, dws, dx_ref, de_ref, refs = _layer_backward_case(128, 2, 2, with_de=False)
+    assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
+    for got, ref in zip(dws, refs):
+        assert rel_l2(got, ref) < TOL_GRAD
+
+
+def _ws_chunks(tiles, n_lin=4):
+    # a workspace that holds the scratch of `tiles` tiles per chunk: the H = 128
+    # backward then runs several chunks. Scratch per tile of 128 rows: the
+    # hidden activations h_0..h_{L-2}, two dz buffers and the [a*, x] rows.
+    def size(G, cfg, W):
+        full = gnn.mp_workspace_sizes(G, cfg, W)[1]
+        t_all = max(G.part.info.n_edge_tiles, (G.n_rows + 127) // 128)
+        per_tile = 128 * 128 * 2 * ((n_lin - 1) + 2 + 2)
+        return full - (t_all - tiles) * per_tile
+    return size
+
+
+def test_fused_backward_h128_chunks_match_one_chunk():
+    one = _layer_backward_case(128, 2, 3, nel=(4, 4, 3), p=3, seed=17)
+    many = _layer_backward_case(128, 2, 3, nel=(4, 4, 3), p=3, seed=17, ws_bytes=_ws_chunks(3))
+    dx, de, dws, dx_ref, de_ref, refs = many
+    assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
+    for got, ref in zip(dws, refs):
+        assert rel_l2(got, ref) < TOL_GRAD
+    # activations and per-edge/per-node outputs do not depend on the chunking;
+    # the weight gradients are summed chunk by chunk, so only up to rounding
+    assert np.array_equal(one[0], many[0]) and np.array_equal(one[1], many[1])
+    for a, b in zip(one[2], many[2]):
+        assert rel_l2(a, b) < 1e-5
+
+
+def test_fused_backward_h128_workspace_too_small():
+    with pytest.raises(B.GnnError) as ei:
+        _layer_backward_case(128, 2, 1, ws_bytes=lambda G, cfg, W: 1024)
+    assert ei.value.code == B.GNN_ENOMEM
 
 
 def test_fused_backward_many_tiles_and_deterministic():

@@ -51,34 +51,45 @@ struct ChainArgs {
     int64_t pstride;
 };
 
-// 128 rows x 2 column groups of 64 columns; two CTAs per SM, one stage each
-// (the other CTA's work covers a CTA's load latency).
-constexpr int kChainNT = 256;
+// One CTA per SM, 128 rows x 4 column groups of 32 columns. Three stages of
+// {dz_k rows, h_{k-1} rows} keep two tiles' loads in flight, and two TMEM
+// accumulators let thread 0 issue tile j+1's MMAs while the block runs tile
+// j's epilogue (the weight gradient accumulates in a third region).
+constexpr int kChainNT = 512;
+constexpr int kChainNS = 3;
+struct ChainSmem {
+    static constexpr uint32_t w = 0, st = kTile;                      // stage s: dz, then h, at st + s * 2 * kTile
+    static constexpr uint32_t red = st;                               // 4 x H floats, after the tile loop
+    static constexpr uint32_t bar = st + kChainNS * 2 * kTile;        // full[NS], done_d[2], done_w[2], TMEM slot
+    static constexpr uint32_t total = bar + 64 + 1024;
+};
+static_assert(ChainSmem::total <= 227 * 1024, "k_bwd_chain shared memory");
 
-__global__ void __launch_bounds__(kChainNT, 2) k_bwd_chain(const __grid_constant__ CUtensorMap tm_dz,
+__global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant__ CUtensorMap tm_dz,
                                                           const __grid_constant__ CUtensorMap tm_h, ChainArgs A) {
-    constexpr int H = H128, S = kS, CG = 2, CW = 64, NT = kChainNT, NCH = CW / 16;
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kChainNT, NCH = CW / 16, NS = kChainNS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
-    uint8_t* sW = sm;
-    uint8_t* sDz = sm + kTile;
-    uint8_t* sH = sm + 2 * kTile;
-    float* sRed = reinterpret_cast<float*>(sm + 3 * kTile);            // 4 x H floats
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + 3 * kTile + 4 * H * 4);
-    uint64_t* bar = full + 1;     // dgrad done
-    uint64_t* bar_w = full + 2;   // wgrad done (the stage is free)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 3);
+    uint8_t* sW = sm + ChainSmem::w;
+    float* sRed = reinterpret_cast<float*>(sm + ChainSmem::red);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + ChainSmem::bar);   // full[NS]: stage loaded
+    uint64_t* done_d = full + NS;     // done_d[b]: dgrad into accumulator b complete
+    uint64_t* done_w = done_d + 2;    // done_w[b]: that tile's wgrad complete (its stage is free)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done_w + 2);
+    auto sDz = [&](int s) { return sm + ChainSmem::st + s * 2 * kTile; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
     if (warp == 0) {
-        tmem_alloc(tslot, 2 * H);
+        tmem_alloc(tslot, 4 * H);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(full, 1);
-        mbar_init(bar, 1);
-        mbar_init(bar_w, 1);
+        for (int i = 0; i < NS; ++i) mbar_init(full + i, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(done_d + i, 1);
+            mbar_init(done_w + i, 1);
+        }
         fence_mbar_init();
     }
     load_weight(sW, A.W, H, 0, H, H, tid, NT);
@@ -86,70 +97,86 @@ __global__ void __launch_bounds__(kChainNT, 2) k_bwd_chain(const __grid_constant
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot, tWork = tmem, tDW = tmem + H;
-    bool lp = false, mp = false;    // thread 0: a load / MMAs in flight that nobody has waited for
-    auto issue = [&](int64_t t) {   // thread 0: dz_k and h_{k-1} rows of tile t
-        lp = true;
-        mbar_arrive_expect_tx(full, 2 * kTile);
+    const uint32_t tmem = *tslot, tDW = tmem + 2 * H;
+    auto tWork = [&](int b) { return tmem + (uint32_t)(b * H); };
+    const int64_t n_mine = A.n_tiles > (int64_t)blockIdx.x
+                               ? (A.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };
+    // thread 0 only: loads issued / MMAs issued so far, and whether it is still well
+    int64_t n_ld = 0, n_mma = 0;
+    bool ok0 = true;
+    auto issue_load = [&]() {   // next tile of this CTA into stage n_ld % NS
+        const int s = (int)(n_ld % NS);
+        const int32_t y = (int32_t)(tile_of(n_ld) * 128);
+        mbar_arrive_expect_tx(full + s, 2 * kTile);
         for (int kb = 0; kb < 2; ++kb) {
-            tma_load_2d(sDz + kb * 128 * S, &tm_dz, kb * 64, (int32_t)(t * 128), full);
-            tma_load_2d(sH + kb * 128 * S, &tm_h, kb * 64, (int32_t)(t * 128), full);
+            tma_load_2d(sDz(s) + kb * 128 * S, &tm_dz, kb * 64, y, full + s);
+            tma_load_2d(sDz(s) + kTile + kb * 128 * S, &tm_h, kb * 64, y, full + s);
         }
+        ++n_ld;
     };
-    if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) issue(blockIdx.x);
+    auto issue_mma = [&]() {    // MMAs of tile n_mma once its stage has landed
+        const int s = (int)(n_mma % NS), b = (int)(n_mma & 1);
+        ok0 = ok0 && mbar_wait(full + s, (uint32_t)(n_mma / NS) & 1u);
+        if (!ok0) return;
+        tc_fence_after();
+        issue_dgrad(tWork(b), sDz(s), S, sW, S, H, (uint32_t)H * S, H, H);
+        mma_commit(done_d + b);
+        issue_wgrad(tDW, sDz(s), S, 128u * S, sDz(s) + kTile, S, 128u * S, H, n_mma > 0);
+        mma_commit(done_w + b);
+        ++n_mma;
+    };
+    if (tid == 0) {
+        while (n_ld < n_mine && n_ld < NS) issue_load();
+        if (n_mine > 0) issue_mma();
+    }
     float acc[NCH];
 #pragma unroll
     for (int j = 0; j < NCH; ++j) acc[j] = 0.f;
-    uint32_t ph = 0;
-    bool ok = true, first = true;
+    bool ok = true;
 
-    for (int64_t t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
-        ok = block_wait(full, ph, tid);
-        if (!ok) break;
-        lp = false;
-        if (tid == 0) {
-            tc_fence_after();
-            issue_dgrad(tWork, sDz, S, sW, S, H, (uint32_t)H * S, H, H);
-            mma_commit(bar);
-            issue_wgrad(tDW, sDz, S, 128u * S, sH, S, 128u * S, H, !first);
-            mma_commit(bar_w);
-            mp = true;
-        }
-        ok = block_wait(bar, ph, tid);
+    for (int64_t j = 0; j < n_mine; ++j) {
+        const int s = (int)(j % NS), b = (int)(j & 1);
+        const uint32_t par = (uint32_t)(j >> 1) & 1u;
+        // tile j+1's MMAs run during this epilogue (its accumulator was read in iteration j-1)
+        if (tid == 0 && j + 1 < n_mine) issue_mma();
+        ok = ok && mbar_wait(done_d + b, par);
+        __syncwarp();
         tc_fence_after();
-        if (!ok) break;
+        const int64_t t = tile_of(j);
         __nv_bfloat16* zrow = A.dz_out + (t * 128 + row) * H + c0;
+        const uint8_t* hT = sDz(s) + kTile;
 #pragma unroll
-        for (int j = 0; j < NCH; ++j) {
+        for (int jj = 0; jj < NCH; ++jj) {
             float dh[16], hv[16];
-            tmem_ld16(tWork + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * j), dh);
-            ld_tile8(sH, row, c0 + 16 * j, 128, S, hv);
-            ld_tile8(sH, row, c0 + 16 * j + 8, 128, S, hv + 8);
+            tmem_ld16(tWork(b) + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * jj), dh);
+            ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
+            ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
             tmem_ld_wait();
 #pragma unroll
             for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
-            st_bf16x8(zrow + 16 * j, dh);
-            st_bf16x8(zrow + 16 * j + 8, dh + 8);
-            acc[j] += warp_colsum16(dh, lane);
+            st_bf16x8(zrow + 16 * jj, dh);
+            st_bf16x8(zrow + 16 * jj + 8, dh + 8);
+            acc[jj] += warp_colsum16(dh, lane);
         }
         tc_fence_before();
         fence_proxy_async();
-        ok = block_wait(bar_w, ph, tid);   // every thread is past its reads of the stage
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // every thread is past its reads of stage s
         if (!ok) break;
-        mp = false;
-        ph ^= 1;
-        tc_fence_after();
-        first = false;
-        if (tid == 0 && t + gridDim.x < A.n_tiles) issue(t + gridDim.x);
+        if (tid == 0) {   // stage s is free once tile j's wgrad is done: the CTA's tile j+NS goes there
+            ok0 = mbar_wait(done_w + b, par);
+            if (ok0 && n_ld < n_mine) issue_load();
+        }
     }
-    if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
-        if (mp) mbar_wait(bar_w, ph);
-        if (lp) mbar_wait(full, mp ? ph ^ 1 : ph);
+    if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
+        if (n_mma > 0) mbar_wait(done_w + ((n_mma - 1) & 1), (uint32_t)((n_mma - 1) >> 1) & 1u);
+        for (int64_t i = n_mma; i < n_ld; ++i) mbar_wait(full + (i % NS), (uint32_t)(i / NS) & 1u);
     }
-    ok = __syncthreads_and(ok) != 0;
+    ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+    tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {
-        if (!first) flush_acc<CG>(tDW, H, H, q, lane, g, part);
+        if (n_mine > 0) flush_acc<CG>(tDW, H, H, q, lane, g, part);
         else
             for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
     }
@@ -157,11 +184,8 @@ __global__ void __launch_bounds__(kChainNT, 2) k_bwd_chain(const __grid_constant
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 2 * H);
+    if (warp == 0) tmem_dealloc(tmem, 4 * H);
 }
-
-constexpr uint32_t chain_smem() { return 3 * kTile + 4 * H128 * 4 + 64 + 1024; }
-
 
 // ------------------------------------------------------------------ k_bwd_edge0
 
@@ -538,9 +562,9 @@ B128Ws carve_b128(void* ws, const gnn_graph_dev& G, int Le, int Ln, bool need_a,
 int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, cudaStream_t s) {
     constexpr int H = H128;
     const int L = W.n_lin;
-    const uint32_t smem = chain_smem();
+    const uint32_t smem = ChainSmem::total;
     int grid;
-    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 2 * H, n_tiles, &grid);
+    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 4 * H, n_tiles, &grid);
     if (rc) return rc;
     const int64_t rows = n_tiles * 128;
     for (int k = L - 1; k >= 1; --k) {

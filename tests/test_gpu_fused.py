@@ -263,10 +263,11 @@ def test_fused_backward_many_tiles_and_deterministic():
         assert np.array_equal(a, b)
 
 
-def test_fused_network_training_step_vs_oracle():
+@pytest.mark.parametrize("H", [32, 128])
+def test_fused_network_training_step_vs_oracle(H):
     # encoders + 2 consistent layers + decoder + Eq. 8 loss, BF16 layers, R=3
     from gpu_util import flat_grads, node_field, oracle_network
-    nel, p, H, M, R = (3, 3, 2), 2, 32, 2, 3
+    nel, p, M, R = (3, 3, 2), 2, 2, 3
     brick, subs = oracle_subgraphs(nel, p, R, "rcb")
     part = MeshGraph(nel, p).partition(R, "rcb")
     G = part.to_device(DEV)

@@ -5,10 +5,10 @@
   seeded weights, h = 1e-3 max(1, |w|): agreement within 1e-2 relative wherever
   the gradient is above the FP32 noise floor of the difference quotient.
 * The precision form (H = 128, BF16 GEMM operands) on a p = 7 brick: one layer
-  forward against the FP64 oracle and against the plain FP32 path (the BF16
-  backward covers H <= 64), and the same forward on a standalone 99^3-node
-  brick (14^3 elements, p = 7, 5.8M edges) split into 2 sub-graphs, against
-  the FP64 oracle."""
+  forward and backward (input and parameter gradients) against the FP64
+  oracle and against the plain FP32 path, and the forward on a standalone
+  99^3-node brick (14^3 elements, p = 7, 5.8M edges) split into 2
+  sub-graphs, against the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -74,7 +74,7 @@ def test_fp32_network_gradient_matches_central_differences():
     B.call("gnn_check", None)
 
 
-def test_precision_form_h128_layer_forward():
+def test_precision_form_h128_layer_forward_backward():
     nel, p, H, R = (6, 5, 4), 7, 128, 4
     brick, subs = oracle_subgraphs(nel, p, R)
     part = MeshGraph(nel, p).partition(R, "rcb")
@@ -89,24 +89,47 @@ def test_precision_form_h128_layer_forward():
     uk, inv = np.unique(key, return_inverse=True)
     e = rng.standard_normal((uk.size, H))[inv]
     e = torch.as_tensor(e, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
-    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
-    outs = {}
+    lp = params["layers"][0]
+    x1, e1, cache = om.layer_forward(lp, subs, split_rows(x, subs), split_edges(e, subs))
+    # a consistent upstream gradient of x' and a BF16 one of e'
+    dx1 = rng.standard_normal((part.graph.n_nodes, H))[gid] / np.maximum(part.array("node_deg")[:, None], 1)
+    de1 = rng.standard_normal((uk.size, H))[inv] * 0.5
+    de1 = torch.as_tensor(de1, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    dx0, de0, g = om.layer_backward(lp, subs, cache, split_rows(dx1, subs), split_edges(de1, subs))
+    gref = list(g["edge"]["W"]) + list(g["edge"]["b"]) + [g["edge"]["gamma"], g["edge"]["beta"]] \
+        + list(g["node"]["W"]) + list(g["node"]["b"]) + [g["node"]["gamma"], g["node"]["beta"]]
+    outs, grads = {}, {}
     for precision in ("bf16", "fp32"):
         net = gnn.ConsistentGNN(params, precision=precision, device=DEV)
         layer = net.layers[0]
         edt = torch.bfloat16 if precision == "bf16" else torch.float32
         xt = torch.as_tensor(x, dtype=torch.float32, device=DEV)
         et = torch.as_tensor(e, dtype=torch.float32, device=DEV).to(edt)
-        W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
+        tens = layer.edge.tensors() + layer.node.tensors()
+        W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+        cfg = gnn.mp_config(H, precision)
         xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
-        gnn.gnn_mp_forward(G, gnn.mp_config(H, precision), W, xt, et, xo, eo, a)
+        gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
+        dparams = [torch.zeros_like(t) for t in tens]
+        dxi, dei = torch.empty_like(xt), torch.empty_like(et)
+        gnn.gnn_mp_backward(G, cfg, W, xt, et, a, torch.as_tensor(dx1, dtype=torch.float32, device=DEV),
+                            torch.as_tensor(de1, dtype=torch.float32, device=DEV).to(edt), dxi, dei,
+                            gnn.mp_params(layer.edge.dims, layer.node.dims, dparams))
         B.call("gnn_check", None)
-        outs[precision] = (xo.cpu().numpy(), eo.float().cpu().numpy(), a.cpu().numpy())
-    ref = (np.concatenate(x1), np.concatenate(e1), np.concatenate(cache["a_star"]))
+        outs[precision] = (xo.cpu().numpy(), eo.float().cpu().numpy(), a.cpu().numpy(),
+                           dxi.cpu().numpy(), dei.float().cpu().numpy())
+        grads[precision] = [d.cpu().numpy() for d in dparams]
+    ref = (np.concatenate(x1), np.concatenate(e1), np.concatenate(cache["a_star"]),
+           np.concatenate(dx0), np.concatenate(de0))
     for u, r in zip(outs["fp32"], ref):
         assert rel_l2(u, r) < 1e-5
-    for u, r, f in zip(outs["bf16"], ref, outs["fp32"]):
-        assert rel_l2(u, r) < 2e-2 and rel_l2(u, f) < 2e-2
+    for u, r in zip(grads["fp32"], gref):
+        assert rel_l2(u, r) < 1e-5
+    for k, (u, r, f) in enumerate(zip(outs["bf16"], ref, outs["fp32"])):
+        tol = 2e-2 if k < 3 else 5e-2    # outputs, then input gradients
+        assert rel_l2(u, r) < tol and rel_l2(u, f) < tol, (k, rel_l2(u, r))
+    for k, (u, r) in enumerate(zip(grads["bf16"], gref)):
+        assert rel_l2(u, r) < 5e-2, (k, rel_l2(u, r))
     assert part.n_edges > 100000
 
 

@@ -148,6 +148,7 @@ struct EdgeFwdArgs {
     int64_t n_edges;
     const __nv_bfloat16* pq;    // P rows [n_rows x H]
     const __nv_bfloat16* q;     // Q rows [n_rows x H] (pq + n_rows*H)
+    const __nv_bfloat16* e_in;  // edge states [n_edges x H] (the residual of Eq. 5a)
     __nv_bfloat16* e_out;
     float* a;
     MlpDev mlp;
@@ -168,6 +169,13 @@ struct EdgeFwdArgs {
 // tiles: the hidden activations go to scratch instead of the next Linear only,
 // and the LayerNorm epilogue is replaced by its adjoint, whose input is the
 // gradient of e' (upstream de' plus da_i / d_ij, the adjoint of Eq. 5b).
+//
+// One tile at a time per CTA. The tile's record (CSR slice, receivers,
+// senders, 1/d) and edge-state rows arrive by bulk copy / TMA; as soon as the
+// first Linear has read the edge-state rows, the next tile's record and rows
+// are requested into the same buffers, so their latency hides behind this
+// tile's chain. The residual of Eq. 5a re-reads e from global memory (L2), and
+// the 1/d-weighted sums of Eq. 5b are staged in the activation buffer.
 template <int H, bool SAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
     using C = Cfg<H>;
@@ -179,14 +187,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
     uint8_t* sA0 = sm + L.a0;
     uint8_t* sA1 = sm + L.a1;
     float* sPar = reinterpret_cast<float*>(sm + L.par);   // bias[n_lin][H], gamma[H], beta[H]
-    int32_t* sSeg = reinterpret_cast<int32_t*>(sm + L.seg);
     float* sRed = reinterpret_cast<float*>(sm + L.red);
-    uint64_t* bar_tma = reinterpret_cast<uint64_t*>(sm + L.bar);
-    uint64_t* bar_mma = bar_tma + 1;
+    uint64_t* bar_ld = reinterpret_cast<uint64_t*>(sm + L.bar);   // a tile's record and edge rows landed
+    uint64_t* bar_mma = bar_ld + 1;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.tm);
-    float* sStage = reinterpret_cast<float*>(sA0);         // aliases A0+A1 after the chain
-    constexpr int SC = H / 2;                               // staged columns per pass
-    constexpr int SLD = SC + 4;
+    auto sRec = [&](int s) { return sm + L.seg + s * GNN_TILE_META_BYTES; };
+    constexpr int SC = H / 2;                               // staged columns per pass (fills sA1 in FP32)
+    constexpr int NC = SC / 4;                              // 16-byte chunks per staged row
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * C::CW;
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar_tma, 1);
+        mbar_init(bar_ld, 1);
         mbar_init(bar_mma, 1);
         fence_mbar_init();
     }
@@ -212,65 +219,79 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t ph_tma = 0, ph_mma = 0;
+    uint32_t ph_mma = 0;
     bool ok = true;
     constexpr int NCH = C::CW / 16;
     float accG[NCH], accB[NCH], accZ[NCH];   // SAVE: column sums of g*xhat, g, dz
 #pragma unroll
     for (int j = 0; j < NCH; ++j) accG[j] = accB[j] = accZ[j] = 0.f;
     const int64_t tb = SAVE ? A.t0 : 0;
-
-    for (int64_t t = tb + blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
-        const int32_t r0 = A.tiles[t], r1 = A.tiles[t + 1];
-        const int32_t e0 = A.row_ptr[r0], e1 = A.row_ptr[r1];
-        const int ne = e1 - e0;
-        if (tid == 0) {
-            mbar_arrive_expect_tx(bar_tma, C::TILE);
+    bool ld_pending = false;   // thread 0: a record + edge-row load nobody has waited for
+    auto issue_ld = [&](int s, int64_t t) {
+        const int32_t e0 = ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8);
+        mbar_arrive_expect_tx(bar_ld, C::TILE + GNN_TILE_META_BYTES);
+        bulk_load(sRec(s), A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, bar_ld);
 #pragma unroll
-            for (int kb = 0; kb < (H + 63) / 64; ++kb)
-                tma_load_2d(sA0 + kb * 128 * 128, &tmap_e, kb * 64, e0, bar_tma);
+        for (int kb = 0; kb < (H + 63) / 64; ++kb) tma_load_2d(sA0 + kb * 128 * 128, &tmap_e, kb * 64, e0, bar_ld);
+        ld_pending = true;
+    };
+    if (tid == 0 && tb + (int64_t)blockIdx.x < A.n_tiles) issue_ld(0, tb + blockIdx.x);
+    int j = 0;
+
+    for (int64_t t = tb + blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
+        ok = block_wait(bar_ld, (uint32_t)j & 1u, tid);
+        if (!ok) break;
+        ld_pending = false;
+        const uint8_t* rec = sRec(j & 1);
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
+        const int32_t* sRp = reinterpret_cast<const int32_t*>(rec + 16);
+        const int16_t* sSeg = reinterpret_cast<const int16_t*>(rec + 544);
+        const int32_t* sCol = reinterpret_cast<const int32_t*>(rec + 800);
+        const float* sWd = reinterpret_cast<const float*>(rec + 1312);
+        const int32_t r0 = hdr[0], r1 = hdr[1], e0 = hdr[2], ne = hdr[3];
+        if (tid == 0) {
+            tc_fence_after();
+            issue_mma(tmem, sA0, sW, H, H);
+            mma_commit(bar_mma);
         }
-        // the tile's CSR slice (local edge offsets) and the receiver of each edge
-        int32_t* sRp = sSeg + 128;
-        for (int rr = tid; rr <= r1 - r0; rr += C::NT) sRp[rr] = A.row_ptr[r0 + rr] - e0;
-        __syncthreads();
-        for (int rr = tid; rr < r1 - r0; rr += C::NT)
-            for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) sSeg[e] = rr;
-        __syncthreads();
         const bool valid = row < ne;
         const int64_t eg = (int64_t)e0 + row;
         float w = 0.f;
         float pq[C::CW];
         if (valid) {
             const int64_t rcv = r0 + sSeg[row];
-            const int64_t snd = A.col[eg];
-            w = A.edge_w[eg];
+            const int64_t snd = sCol[row];
+            w = sWd[row];
 #pragma unroll
             for (int i = 0; i < C::CW; i += 8) {
                 float pv[8], qv[8];
                 ld_bf16x8(A.pq + rcv * H + c0 + i, pv);
                 ld_bf16x8(A.q + snd * H + c0 + i, qv);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) pq[i + j] = pv[j] + qv[j];
+                for (int k = 0; k < 8; ++k) pq[i + k] = pv[k] + qv[k];
             }
         } else {
 #pragma unroll
             for (int i = 0; i < C::CW; ++i) pq[i] = 0.f;
         }
-        ok = block_wait(bar_tma, ph_tma, tid);
-        ph_tma ^= 1;
-        if (!ok) break;
-        if (tid == 0) {
-            tc_fence_after();
-            issue_mma(tmem, sA0, sW, H, H);
-            mma_commit(bar_mma);
-        }
         float v[C::CW];
+        uint4 eres[C::CW / 8];   // forward: the residual e row (BF16), requested before the last MMA wait
         for (int k = 0; k < n_lin && ok; ++k) {
+            if constexpr (!SAVE) {
+                if (k == n_lin - 1 && valid) {
+#pragma unroll
+                    for (int i = 0; i < C::CW / 8; ++i)
+                        eres[i] = __ldg(reinterpret_cast<const uint4*>(A.e_in + eg * H + c0) + i);
+                }
+            }
             ok = block_wait(bar_mma, ph_mma, tid);
             ph_mma ^= 1;
             tc_fence_after();
             if (!ok) break;
+            if (k == 0 && tid == 0 && t + gridDim.x < A.n_tiles) {
+                // the first Linear has read the edge rows: the next tile's record and rows
+                issue_ld((j + 1) & 1, t + gridDim.x);
+            }
             ld_acc<C::CW>(tmem, q, c0, v);
             const float* bk = sPar + k * H + c0;
             if (k == 0) {
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
                     for (int i = 0; i < C::CW; i += 8) {
                         float z8[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) z8[j] = valid ? v[i + j] : 0.f;
+                        for (int jj = 0; jj < 8; ++jj) z8[jj] = valid ? v[i + jj] : 0.f;
                         st_bf16x8(hrow + i, z8);
                     }
                 }
@@ -325,7 +346,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
                         float d8[8];
                         ld_bf16x8(A.de_out + eg * H + c0 + i, d8);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) gv[i + j] = d8[j] + gv[i + j];
+                        for (int jj = 0; jj < 8; ++jj) gv[i + jj] = d8[jj] + gv[i + jj];
                     }
                 }
             } else {
@@ -339,46 +360,64 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             __nv_bfloat16* zrow = A.dz + ((t - tb) * 128 + row) * H + c0;
 #pragma unroll
             for (int i = 0; i < C::CW; i += 8) st_bf16x8(zrow + i, v + i);
-            fence_proxy_async();
-            __syncthreads();   // the tile's smem (CSR slice, input tile) is rewritten by the next tile
+            __syncthreads();   // the record of this tile is rewritten two tiles later, sRed next tile
             continue;
         }
         // LayerNorm + residual (Eq. 5a)
         float mean, rstd;
         row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
-        float eo[C::CW];
-        ld_row_tile<C::CW>(sA0, row, c0, C::S, eo);
         const float* gam = sPar + n_lin * H + c0;
         const float* bet = sPar + (n_lin + 1) * H + c0;
+        if (valid) {
 #pragma unroll
-        for (int i = 0; i < C::CW; ++i) v[i] = eo[i] + (v[i] - mean) * rstd * gam[i] + bet[i];
-        if (valid && A.e_out) {
+            for (int i = 0; i < C::CW / 8; ++i) {
+                float eo[8];
+                unpack_bf16x2(eres[i].x, eo[0], eo[1]);
+                unpack_bf16x2(eres[i].y, eo[2], eo[3]);
+                unpack_bf16x2(eres[i].z, eo[4], eo[5]);
+                unpack_bf16x2(eres[i].w, eo[6], eo[7]);
 #pragma unroll
-            for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.e_out + eg * H + c0 + i, v + i);
+                for (int k = 0; k < 8; ++k) v[8 * i + k] = eo[k] + (v[8 * i + k] - mean) * rstd * gam[8 * i + k] + bet[8 * i + k];
+            }
+            if (A.e_out) {
+#pragma unroll
+                for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.e_out + eg * H + c0 + i, v + i);
+            }
         }
-        // 1/d-weighted segmented sum over each receiver's edges (Eq. 5b), two column passes
+        // 1/d-weighted segmented sum over each receiver's edges (Eq. 5b), two column
+        // passes staged in FP32 in the activation buffer (its last reader, the final
+        // Linear, has completed)
+        float4* sS4 = reinterpret_cast<float4*>(sA1);
         __syncthreads();
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-            for (int i = 0; i < C::CW; ++i) {
-                const int c = c0 + i;
-                if (c >= pass * SC && c < (pass + 1) * SC) sStage[row * SLD + (c - pass * SC)] = w * v[i];
+            for (int i = 0; i < C::CW; i += 4) {
+                const int c = c0 + i - pass * SC;
+                if (c >= 0 && c < SC)
+                    sS4[row * NC + stage_chunk<NC>(c / 4, row)] =
+                        valid ? make_float4(w * v[i], w * v[i + 1], w * v[i + 2], w * v[i + 3])
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
             const int nr = r1 - r0;
-            for (int it = tid; it < nr * SC; it += C::NT) {
-                const int rr = it / SC, cc = it % SC;
-                const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];
-                float s = 0.f;
-                for (int32_t e = b0; e < b1; ++e) s += sStage[e * SLD + cc];
-                A.a[(int64_t)(r0 + rr) * H + pass * SC + cc] = s;
+            for (int it = tid; it < nr * NC; it += C::NT) {
+                const int rr = it / NC, cc = it % NC;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int32_t e = sRp[rr]; e < sRp[rr + 1]; ++e) {
+                    const float4 u = sS4[e * NC + stage_chunk<NC>(cc, e)];
+                    acc.x += u.x;
+                    acc.y += u.y;
+                    acc.z += u.z;
+                    acc.w += u.w;
+                }
+                *reinterpret_cast<float4*>(A.a + (int64_t)(r0 + rr) * H + pass * SC + 4 * cc) = acc;
             }
             __syncthreads();
         }
-        fence_proxy_async();
-        __syncthreads();
+        fence_proxy_async();   // generic writes of sA1 precede the next tile's MMA reads
     }
+    if (tid == 0 && ld_pending) mbar_wait(bar_ld, (uint32_t)j & 1u);   // after a timeout: bounded
     if constexpr (SAVE) {
         float* part = A.part + (int64_t)blockIdx.x * A.pstride;
         colsum_store<H, NCH>(accG, sRed, q, lane, c0, tid, C::NT, part);
@@ -1349,6 +1388,7 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.n_edges = E;
         A.pq = pq;
         A.q = pq + NR * H;
+        A.e_in = e_in;
         A.e_out = e_out;
         A.a = a;
         A.mlp = mlp_dev(W.edge);
@@ -1378,6 +1418,8 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
             }
         }
         if (variant == GNN_EDGE_FWD_ONE) {
+            GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
+                        "gnn_mp_forward: tile_meta must be a 16-byte aligned device array");
             const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin);
             rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid, cfg.ctas_per_sm);
             if (rc) return rc;
@@ -1539,6 +1581,8 @@ int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
     using C = Cfg<H>;
     const int64_t NR = G.n_rows, E = G.n_edges;
     GNN_REQUIRE(cfg.hidden == H, GNN_EUNSUPPORTED, "edge_recompute_save: H=%d", cfg.hidden);
+    GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
+                "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
     CUtensorMap tm;
     int rc = make_row_tmap(&tm, e_in, E, H);
     if (rc) return rc;
@@ -1552,6 +1596,7 @@ int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
     A.n_edges = E;
     A.pq = pq;
     A.q = pq + NR * H;
+    A.e_in = e_in;
     A.mlp = mlp_dev(W.edge);
     A.eps = cfg.ln_eps;
     A.t0 = o.t0;

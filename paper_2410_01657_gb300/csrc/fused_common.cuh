@@ -339,9 +339,9 @@ __host__ __device__ inline EdgeFwdSmem edge_fwd_smem(int n_lin, bool adj = false
     s.a0 = align_up(s.w + n_lin * C::WT, 1024);
     s.a1 = s.a0 + C::TILE;
     s.par = align_up(s.a1 + C::TILE, 16);
-    s.seg = s.par + (n_lin + 2) * H * 4;               // seg[128] then the tile's CSR slice rp[132]
-    s.red = s.seg + (128 + 132) * 4;
-    s.bar = align_up(s.red + (adj ? 4 : 2) * C::CG * 128 * 4, 8);
+    s.seg = align_up(s.par + (n_lin + 2) * H * 4, 128);   // two tile records (GNN_TILE_META_BYTES each)
+    s.red = s.seg + 2 * GNN_TILE_META_BYTES;
+    s.bar = align_up(s.red + (adj ? 4 : 2) * C::CG * 128 * 4, 8);   // record/rows landed, MMA done
     s.tm = s.bar + 16;
     s.total = s.tm + 16 + 1024;      // + slack for 1024-byte alignment of the base
     return s;

@@ -33,13 +33,13 @@ __host__ __device__ constexpr uint32_t pow2_cols(uint32_t n) {
 // K x N MN-major row tile (rows = K, contiguous = N, span Sb, N-blocks lbo apart).
 __device__ __forceinline__ void issue_dgrad(uint32_t d, const uint8_t* A, int Sa, const uint8_t* Bt, int Sb,
                                             int b_rows, uint32_t lbo, int N, int K) {
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint64_t a0 = kmajor_desc(smem_u32(A), 128, Sa, 0);
+    const uint64_t b0 = sdesc(smem_u32(Bt), lbo, 8 * Sb, swz_code(Sb));
     const uint32_t id = idesc_bf16(128, N, 0, 1);
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo, 8 * Sb, swz_code(Sb));
-        mma_bf16(d, kmajor_desc(a, 128, Sa, k0), bd, id, k0 > 0 ? 1u : 0u);
-        (void)b_rows;
-    }
+    (void)b_rows;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16)
+        mma_bf16(d, desc_step(a0, kmajor_off(128, Sa, k0)), desc_step(b0, (uint32_t)k0 * Sb), id, k0 > 0 ? 1u : 0u);
 }
 
 // D[128 x N] (+)= A^T B over the 128 rows of two MN-major row tiles:
@@ -47,13 +47,13 @@ __device__ __forceinline__ void issue_dgrad(uint32_t d, const uint8_t* A, int Sa
 // B: rows = K, contiguous = N features (span Sb, N-blocks lbo_b apart).
 __device__ __forceinline__ void issue_wgrad(uint32_t d, const uint8_t* A, int Sa, uint32_t lbo_a, const uint8_t* Bt,
                                             int Sb, uint32_t lbo_b, int N, bool accumulate) {
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint64_t a0 = sdesc(smem_u32(A), lbo_a, 8 * Sa, swz_code(Sa));
+    const uint64_t b0 = sdesc(smem_u32(Bt), lbo_b, 8 * Sb, swz_code(Sb));
     const uint32_t id = idesc_bf16(128, N, 1, 1);
-    for (int k0 = 0; k0 < 128; k0 += 16) {
-        const uint64_t ad = sdesc(a + (uint32_t)k0 * Sa, lbo_a, 8 * Sa, swz_code(Sa));
-        const uint64_t bd = sdesc(b + (uint32_t)k0 * Sb, lbo_b, 8 * Sb, swz_code(Sb));
-        mma_bf16(d, ad, bd, id, (accumulate || k0 > 0) ? 1u : 0u);
-    }
+#pragma unroll
+    for (int k0 = 0; k0 < 128; k0 += 16)
+        mma_bf16(d, desc_step(a0, (uint32_t)k0 * Sa), desc_step(b0, (uint32_t)k0 * Sb), id,
+                 (accumulate || k0 > 0) ? 1u : 0u);
 }
 
 // Ones block: a [128 x S/2] row tile whose column 0 is 1 and the rest 0.

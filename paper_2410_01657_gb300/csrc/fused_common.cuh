@@ -118,13 +118,27 @@ __device__ __forceinline__ void load_weight(uint8_t* dst, const float* __restric
     }
 }
 
+// The MMA issue loops below build each operand's descriptor once and step
+// its start-address field (16-byte units, bits 0..13) by the K-step's byte
+// offset: the issuing thread's work per MMA is two adds, which keeps the
+// block's wait for the issue short. Shared-memory offsets stay below 256 KB,
+// so the field never carries into the next one.
+__device__ __forceinline__ uint64_t desc_step(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
+// Byte offset of the K-step at column k0 of a K-major row tile (rows, span S).
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int rows, int S, int k0) {
+    return (uint32_t)(k0 / (S / 2)) * rows * S + (uint32_t)(k0 % (S / 2)) * 2;
+}
+
 // Issue D = A[128 x K] * B[N x K]^T (both K-major row tiles) from one thread.
 __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const uint8_t* A, const uint8_t* Bt, int N, int K) {
     const int S = span_of(K);
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint64_t a0 = kmajor_desc(smem_u32(A), 128, S, 0), b0 = kmajor_desc(smem_u32(Bt), N, S, 0);
     const uint32_t id = idesc_bf16(128, N);
+#pragma unroll
     for (int k0 = 0; k0 < K; k0 += 16)
-        mma_bf16(d_tmem, kmajor_desc(a, 128, S, k0), kmajor_desc(b, N, S, k0), id, k0 > 0 ? 1u : 0u);
+        mma_bf16(d_tmem, desc_step(a0, kmajor_off(128, S, k0)), desc_step(b0, kmajor_off(N, S, k0)), id,
+                 k0 > 0 ? 1u : 0u);
 }
 
 // D (+)= A[128 x K] * B[N x (b_k0 .. b_k0+K)]^T where B is a K-major row tile
@@ -132,10 +146,11 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const uint8_t* A, con
 __device__ __forceinline__ void issue_mma_koff(uint32_t d_tmem, const uint8_t* A, const uint8_t* Bt, int N, int K,
                                                int b_k0, int b_ktot, bool accumulate) {
     const int Sa = span_of(K), Sb = span_of(b_ktot);
-    const uint32_t a = smem_u32(A), b = smem_u32(Bt);
+    const uint64_t a0 = kmajor_desc(smem_u32(A), 128, Sa, 0), b0 = kmajor_desc(smem_u32(Bt), N, Sb, 0);
     const uint32_t id = idesc_bf16(128, N);
+#pragma unroll
     for (int k0 = 0; k0 < K; k0 += 16)
-        mma_bf16(d_tmem, kmajor_desc(a, 128, Sa, k0), kmajor_desc(b, N, Sb, b_k0 + k0), id,
+        mma_bf16(d_tmem, desc_step(a0, kmajor_off(128, Sa, k0)), desc_step(b0, kmajor_off(N, Sb, b_k0 + k0)), id,
                  (accumulate || k0 > 0) ? 1u : 0u);
 }
 

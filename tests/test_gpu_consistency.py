@@ -2,7 +2,9 @@
 
 A network of consistent NMP layers gives the same loss for every number of
 sub-graphs R; the same network with the halo swap + sync skipped (the paper's
-"None" layers) does not, and its error grows as the sub-graphs get smaller."""
+"None" layers) does not, and its error grows as the sub-graphs get smaller.
+Training (Adam, target = input) with consistent layers follows the same loss
+curve for R = 1 and R = 8; with "None" layers the curves part."""
 import numpy as np
 import pytest
 import torch
@@ -53,3 +55,39 @@ def test_inconsistent_layers_drift_with_R():
     dev = [abs(_loss(R, "fp32", False) - ref) / abs(ref) for R in RS[1:]]
     assert min(dev) > 1e-4                 # every partition changes the result
     assert dev[-1] > 3 * dev[0]             # and more sub-graphs change it more
+
+
+def _train(R, precision, halo, steps=25, H=16, lr=2e-3):
+    # the paper's training comparison (target = input): Adam on the consistent loss
+    graph = MeshGraph((8, 8, 8), 1)
+    part = graph.partition(R, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(13, H, 2, 2)
+    modes = syn.fourier_modes(13, 8)
+    u = torch.tensor(syn.fourier_field(part.array("row_pos"), modes), dtype=torch.float32, device=DEV)
+    net = gnn.ConsistentGNN(params, precision=precision, halo=halo, device=DEV)
+    opt = torch.optim.Adam(net.parameters(), lr=lr)
+    attr = G.edge_attr()
+    curve = []
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        loss = gnn.consistent_loss(net(G, u, attr), u, G)
+        loss.backward()
+        opt.step()
+        curve.append(float(loss.item()))
+    B.call("gnn_check", None)
+    return np.array(curve)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 2e-2)])
+def test_training_curve_is_independent_of_R(precision, tol):
+    # consistent layers: the R = 8 run follows the R = 1 run step by step (the
+    # partitioned loss and its gradient equal the single-graph ones)
+    c1, c8 = _train(1, precision, True), _train(8, precision, True)
+    assert c1[-1] < 0.5 * c1[0]                       # it trains
+    assert np.max(np.abs(c8 - c1) / np.abs(c1)) < tol
+
+
+def test_inconsistent_training_curve_departs():
+    c1, c8 = _train(1, "fp32", False), _train(8, "fp32", False)
+    assert np.max(np.abs(c8 - c1) / np.abs(c1)) > 1e-3

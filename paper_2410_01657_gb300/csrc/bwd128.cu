@@ -19,9 +19,10 @@
 //   k_bwd_edge0   de_in = g + dz_0 W1c with g = de' + da_i / d_ij, dW1c += dz_0^T e,
 //                 dz_0 per edge and its sum over each receiver's edges (dP)
 //   k_proj_bwd    dQ, dx_in += dP W1a + dQ W1b, dW1a, dW1b
-// Tiles are processed in chunks of at most kChunkTiles so that the scratch
-// stays bounded; each kernel's per-CTA partials are summed (CTA order) into
-// dW right after it, so every gradient has a fixed summation order.
+// Tiles are processed in chunks of at most kChunkTiles (fewer when the
+// caller's workspace is smaller) so that the scratch stays bounded; each
+// kernel's per-CTA partials are summed (CTA order) into dW right after it, so
+// every gradient has a fixed summation order.
 
 #include <algorithm>
 

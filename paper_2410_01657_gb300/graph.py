@@ -225,5 +225,9 @@ class DeviceGraph:
         return self
 
     def edge_attr(self):
+        """Edge attributes [dx, dy, dz, |d|] (graph geometry, FP32 [n_edges x 4]),
+        uploaded on first use and kept on the device with the graph."""
         import torch
-        return torch.from_numpy(self.part.array("edge_attr")).to(self.device)
+        if "edge_attr" not in self.t:
+            self.t["edge_attr"] = torch.from_numpy(self.part.array("edge_attr")).to(self.device)
+        return self.t["edge_attr"]

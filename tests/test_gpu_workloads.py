@@ -201,7 +201,11 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     assert G.tile_edges == rep["tile_edges"] and part.tile_edges == rep["tile_edges"]
     stack.forward()
     torch.cuda.synchronize()
-    assert rel_l2(stack.x_out.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    # the tuned launch choice may differ from the default one: launch choices agree to FP32
+    # rounding except where a last-bit difference flips a BF16 rounding of an activation or of
+    # the edge state (about 1e-4 per layer, see test_edge_forward_kernel_choices_agree), and
+    # such flips carry into the next layer
+    assert rel_l2(stack.x_out.cpu().numpy(), ref.cpu().numpy()) < 1e-3
     gnn._TUNED.clear()
     rep2 = stack.autotune(tile_caps=(128, 64, 32), reps=2, cache_file=cache)
     assert rep2["cached"] and rep2["tile_edges"] == rep["tile_edges"]

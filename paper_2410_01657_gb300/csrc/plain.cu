@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_sgemm(GemmArgs a) {
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    const int64_t m0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 64;   // rows in x: up to 2^31-1 blocks
     int64_t kbeg = 0, kend = a.K;
     float* C = a.C;
     if (a.k_chunk > 0) {
@@ -448,7 +448,9 @@ static inline unsigned grid1(int64_t n, int threads = 256) { return (unsigned)((
 
 static int gemm(const GemmArgs& a, int64_t nsplit, cudaStream_t s) {
     if (a.M == 0 || a.N == 0) return GNN_OK;
-    dim3 grid((unsigned)((a.N + 63) / 64), (unsigned)((a.M + 63) / 64), (unsigned)std::max<int64_t>(1, nsplit));
+    const int64_t mb = (a.M + 63) / 64;
+    GNN_REQUIRE(mb <= 0x7fffffff, GNN_ESHAPE, "sgemm: too many rows");
+    dim3 grid((unsigned)mb, (unsigned)((a.N + 63) / 64), (unsigned)std::max<int64_t>(1, nsplit));
     GNN_REQUIRE(grid.y <= 65535u && grid.z <= 65535u, GNN_ESHAPE, "sgemm: grid too large");
     {
         ProfScope _ps(s, "k_sgemm");

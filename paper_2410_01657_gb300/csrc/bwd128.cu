@@ -246,8 +246,9 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *tslot, tWork = tmem, tDW = tmem + H;
     int64_t n_issued = 0;   // thread 0: loads issued (stage i & 1, phase (i >> 1) & 1)
-    auto issue = [&](int s, int64_t t) {   // thread 0: record, dz_0 rows and e rows of tile t
-        const int32_t e0 = ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8);
+    auto tile_hdr = [&](int64_t t) { return ld_nc_v4s32(A.tile_meta + t * GNN_TILE_META_BYTES); };
+    int4 hdr_next = make_int4(0, 0, 0, 0);   // thread 0: the next tile's header, read one tile ahead
+    auto issue = [&](int s, int64_t t, int32_t e0) {   // thread 0: record, dz_0 rows and e rows of tile t
         ++n_issued;
         mbar_arrive_expect_tx(full + s, 2 * kTile + GNN_TILE_META_BYTES);
         bulk_load(sRec(s), A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, full + s);
@@ -257,7 +258,10 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         }
     };
     const int64_t tfirst = A.t0 + blockIdx.x;
-    if (tid == 0 && tfirst < A.t1) issue(0, tfirst);
+    if (tid == 0 && tfirst < A.t1) {
+        issue(0, tfirst, tile_hdr(tfirst).z);
+        if (tfirst + gridDim.x < A.t1) hdr_next = tile_hdr(tfirst + gridDim.x);
+    }
     uint32_t ph = 0;
     bool ok = true, first = true, mp = false;
     int j = 0;
@@ -278,7 +282,12 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
             mma_commit(bar_w);
             mp = true;
             // the other stage was released at the end of the previous tile
-            if (t + gridDim.x < A.t1) issue(st ^ 1, t + gridDim.x);
+            if (t + gridDim.x < A.t1) {
+                issue(st ^ 1, t + gridDim.x, hdr_next.z);
+                if (hdr_next.y > hdr_next.x)   // its receivers' da rows into L2
+                    prefetch_l2(A.da + (int64_t)hdr_next.x * H, (uint32_t)(hdr_next.y - hdr_next.x) * H * 4);
+                if (t + 2 * (int64_t)gridDim.x < A.t1) hdr_next = tile_hdr(t + 2 * (int64_t)gridDim.x);
+            }
         }
         const uint8_t* rec = sRec(st);
         const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);

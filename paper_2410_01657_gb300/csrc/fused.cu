@@ -227,15 +227,19 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
     for (int j = 0; j < NCH; ++j) accG[j] = accB[j] = accZ[j] = 0.f;
     const int64_t tb = SAVE ? A.t0 : 0;
     bool ld_pending = false;   // thread 0: a record + edge-row load nobody has waited for
-    auto issue_ld = [&](int s, int64_t t) {
-        const int32_t e0 = ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8);
+    auto tile_hdr = [&](int64_t t) { return ld_nc_v4s32(A.tile_meta + t * GNN_TILE_META_BYTES); };
+    int4 hdr_next = make_int4(0, 0, 0, 0);   // thread 0: the next tile's header, read one tile ahead
+    auto issue_ld = [&](int s, int64_t t, int32_t e0) {
         mbar_arrive_expect_tx(bar_ld, C::TILE + GNN_TILE_META_BYTES);
         bulk_load(sRec(s), A.tile_meta + t * GNN_TILE_META_BYTES, GNN_TILE_META_BYTES, bar_ld);
 #pragma unroll
         for (int kb = 0; kb < (H + 63) / 64; ++kb) tma_load_2d(sA0 + kb * 128 * 128, &tmap_e, kb * 64, e0, bar_ld);
         ld_pending = true;
     };
-    if (tid == 0 && tb + (int64_t)blockIdx.x < A.n_tiles) issue_ld(0, tb + blockIdx.x);
+    if (tid == 0 && tb + (int64_t)blockIdx.x < A.n_tiles) {
+        issue_ld(0, tb + blockIdx.x, tile_hdr(tb + blockIdx.x).z);
+        if (tb + (int64_t)blockIdx.x + gridDim.x < A.n_tiles) hdr_next = tile_hdr(tb + blockIdx.x + gridDim.x);
+    }
     int j = 0;
 
     for (int64_t t = tb + blockIdx.x; t < A.n_tiles && ok; t += gridDim.x, ++j) {
@@ -290,7 +294,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             if (!ok) break;
             if (k == 0 && tid == 0 && t + gridDim.x < A.n_tiles) {
                 // the first Linear has read the edge rows: the next tile's record and rows
-                issue_ld((j + 1) & 1, t + gridDim.x);
+                issue_ld((j + 1) & 1, t + gridDim.x, hdr_next.z);
+                if constexpr (SAVE) {   // and its receivers' da rows into L2 for the LayerNorm adjoint
+                    if (hdr_next.y > hdr_next.x)
+                        prefetch_l2(A.da + (int64_t)hdr_next.x * H, (uint32_t)(hdr_next.y - hdr_next.x) * H * 4);
+                }
+                if (t + 2 * (int64_t)gridDim.x < A.n_tiles) hdr_next = tile_hdr(t + 2 * (int64_t)gridDim.x);
             }
             ld_acc<C::CW>(tmem, q, c0, v);
             const float* bk = sPar + k * H + c0;

@@ -132,6 +132,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Non-coherent 32-bit global load (read-only data).
 __device__ __forceinline__ int32_t ld_nc_s32(const void* p) { return __ldg(reinterpret_cast<const int32_t*>(p)); }
+// Non-coherent 16-byte global load (read-only, 16-byte aligned): e.g. a tile record's
+// header {first row, end row, first edge, edge count}.
+__device__ __forceinline__ int4 ld_nc_v4s32(const void* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
 
 // ------------------------------------------------------------------ tcgen05
 

@@ -121,6 +121,12 @@ __host__ __device__ inline uint32_t edge_bwd_tcols(int n_lin) { return H + n_lin
 // ... plus the LayerNorm parameter-gradient accumulators (2H columns) when they fit
 template <int H>
 __host__ __device__ inline bool edge_bwd_ln_in_tmem(int n_lin) { return edge_bwd_tcols<H>(n_lin) + 2 * H <= 512; }
+// Offset of the LayerNorm parameter gradients in a node-adjoint CTA's partials
+// (after the weight-gradient blocks [H x (2H+16)] and (n_lin-1) x [H x (H+16)]).
+template <int H>
+__host__ __device__ inline int64_t node_ln_off(int n_lin) {
+    return (int64_t)H * (2 * H + 16) + (int64_t)(n_lin - 1) * H * (H + 16);
+}
 template <int H>
 __host__ __device__ inline uint32_t node_bwd_tcols(int n_lin) {
     return 2 * H + (2 * H + 16) + (n_lin - 1) * (H + 16);
@@ -194,9 +200,11 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     auto tDW = [&](int k) -> uint32_t {
         return tmem + (uint32_t)(2 * H + (k == 0 ? 0 : (2 * H + 16) + (k - 1) * (H + 16)));
     };
-    float acc_g[CW], acc_b[CW];
+    // LayerNorm parameter-gradient column sums, per warp (warp_colsum16): one register each
+    constexpr int NCH = CW / 16;
+    float acc_g[NCH], acc_b[NCH];
 #pragma unroll
-    for (int i = 0; i < CW; ++i) acc_g[i] = acc_b[i] = 0.f;
+    for (int i = 0; i < NCH; ++i) acc_g[i] = acc_b[i] = 0.f;
     uint32_t ph = 0, ph_w = 0, ph_rdy = 0;
     bool ok = true, first = true;
     const int64_t n_tiles = (A.n_rows + 127) / 128;
@@ -278,9 +286,15 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
 #pragma unroll
         for (int i = 0; i < CW; ++i) {
             v[i] = (v[i] - mean) * rstd;   // xhat
-            acc_g[i] += gv[i] * v[i];
-            acc_b[i] += gv[i];
             dz[i] = rstd * (dz[i] - s1 - v[i] * s2);
+        }
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            float t16[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) t16[i] = gv[16 * j + i] * v[16 * j + i];
+            acc_g[j] += warp_colsum16(t16, lane);
+            acc_b[j] += warp_colsum16(gv + 16 * j, lane);
         }
         // ---- chain adjoint, layer L-1 .. 0
         for (int k = L - 1; k >= 0; --k) {
@@ -345,9 +359,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                 for (int i = tid; i < H * N; i += C::NT) part[off + i] = 0.f;
             off += (int64_t)H * N;
         }
-        rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
-        rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
     }
+    colsum_store<H, NCH>(acc_g, sRed, q, lane, c0, tid, C::NT, part + node_ln_off<H>(L));
+    colsum_store<H, NCH>(acc_b, sRed, q, lane, c0, tid, C::NT, part + node_ln_off<H>(L) + H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -440,8 +454,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     const uint32_t tWork = tmem;
     auto tDW = [&](int k) -> uint32_t { return tmem + (uint32_t)(H + k * (H + 16)); };
     const uint32_t ones_addr = smem_u32(sOnes);
-    // LayerNorm gradient sums of this thread: sum_rows g * xhat and sum_rows g, CW columns each
-    constexpr int ACW = LNT ? 1 : CW;
+    // LayerNorm gradient sums sum_rows g * xhat and sum_rows g: in TMEM (LNT, one lane per
+    // row), else as per-warp column sums (warp_colsum16, one register per 16 columns)
+    constexpr int ACW = LNT ? 1 : CW / 16;
     float acc_g[ACW], acc_b[ACW];
 #pragma unroll
     for (int i = 0; i < ACW; ++i) acc_g[i] = acc_b[i] = 0.f;
@@ -651,9 +666,12 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             tmem_st_wait();
         } else {
 #pragma unroll
-            for (int i = 0; i < ACW; ++i) {
-                acc_g[i] += gv[i] * v[i];
-                acc_b[i] += gv[i];
+            for (int j = 0; j < ACW; ++j) {
+                float t16[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) t16[i] = gv[16 * j + i] * v[16 * j + i];
+                acc_g[j] += warp_colsum16(t16, lane);
+                acc_b[j] += warp_colsum16(gv + 16 * j, lane);
             }
         }
 #pragma unroll
@@ -753,10 +771,12 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             tmem_ld_wait();
             rows_reduce_store<CW>(ag, sRed, q, lane, g, c0, part + off);
             rows_reduce_store<CW>(ab, sRed, q, lane, g, c0, part + off + H);
-        } else {
-            rows_reduce_store<CW>(acc_g, sRed, q, lane, g, c0, part + off);
-            rows_reduce_store<CW>(acc_b, sRed, q, lane, g, c0, part + off + H);
         }
+    }
+    if constexpr (!LNT) {   // after the L weight-gradient blocks [H x (H+16)]
+        const int64_t ln_off = (int64_t)L * H * (H + 16);
+        colsum_store<H, ACW>(acc_g, sRed, q, lane, c0, tid, C::NT, part + ln_off);
+        colsum_store<H, ACW>(acc_b, sRed, q, lane, c0, tid, C::NT, part + ln_off + H);
     }
     tc_fence_before();
     __syncthreads();

@@ -170,8 +170,10 @@ def test_inference_stack_equals_training_forward():
     assert len(inf.e) == 3 and len(inf.x) == 3
 
 
-def test_cuda_graph_replay_matches_eager_step():
-    part, G, layers, x0, e0, dx, stack = _stack_case()
+@pytest.mark.parametrize("H,M", [(64, 3), (128, 2)])
+def test_cuda_graph_replay_matches_eager_step(H, M):
+    # H = 128 captures the layered adjoint (recomputation, per-Linear kernels, reductions)
+    part, G, layers, x0, e0, dx, stack = _stack_case(H, M)
     stack.zero_grad()
     stack.step(dx)
     torch.cuda.synchronize()

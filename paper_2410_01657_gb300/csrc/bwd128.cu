@@ -450,6 +450,11 @@ __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ 
     bool ok = true, first = true;
 
     for (int64_t t = tfirst; t < A.t1; t += gridDim.x) {
+        if (tid == 0 && t + gridDim.x < A.t1) {   // the next tile's dx' rows into L2
+            const int64_t rn = (t + gridDim.x) * 128;
+            if (rn < A.n_rows)
+                prefetch_l2(A.dx_out + rn * H, (uint32_t)(min((int64_t)128, A.n_rows - rn) * H * 4));
+        }
         ok = block_wait(full, ph, tid);
         if (!ok) break;
         lp = false;

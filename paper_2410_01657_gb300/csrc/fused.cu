@@ -1165,6 +1165,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         const int64_t srow = (t - tb) * 128 + row;   // SAVE: scratch row
         (void)srow;
         const int st = j & 1;
+        if constexpr (!PF) {   // the next tile's input rows into L2 (they are read per thread)
+            if (tid == 0 && t + gridDim.x < te) {
+                const int64_t rn = (t + gridDim.x) * 128;
+                const uint32_t nb = (uint32_t)(min((int64_t)128, A.n_rows - rn) * H * 4);
+                prefetch_l2(A.a_star + rn * H, nb);
+                prefetch_l2(A.x + rn * H, nb);
+                if constexpr (SAVE) prefetch_l2(A.dx_out + rn * H, nb);
+            }
+        }
         float xa[C::CW], xv[C::CW];
         if constexpr (PF) {
             ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);

@@ -66,12 +66,18 @@ typedef struct gnn_mesh_desc {
 
 typedef struct gnn_graph gnn_graph;   /* opaque, library-owned host object */
 
+#define GNN_GRAPH_BRICK    0   /* built by gnn_graph_build                                  */
+#define GNN_GRAPH_ELEMENTS 1   /* built by gnn_graph_build_elements                         */
+
 typedef struct gnn_graph_info {
-    int64_t n_nodes;         /* lattice points: prod(L)                                   */
+    int64_t n_nodes;         /* brick: lattice points, prod(L)                            */
     int64_t n_edges;         /* directed edges of the R=1 graph                           */
     int64_t n_elem;
-    int32_t L[3];            /* lattice points per axis: nel*p (+1 if not periodic)      */
-    int32_t p;
+    int32_t L[3];            /* brick: lattice points per axis, nel*p (+1 if not periodic); 0 otherwise */
+    int32_t p;               /* brick: polynomial order; 0 otherwise                      */
+    int64_t n_elem_nodes;    /* entries of the element node lists (brick: n_elem*(p+1)^3) */
+    int32_t kind;            /* GNN_GRAPH_*                                               */
+    int32_t max_degree;      /* largest in-degree of the R=1 graph                        */
 } gnn_graph_info;
 
 /* Build the R=1 GLL-brick graph. Global id of lattice point (ix,iy,iz) is
@@ -80,13 +86,45 @@ typedef struct gnn_graph_info {
  * spacing on axis a), except the normal coordinate on non-periodic faces.
  * *out is freed with gnn_graph_destroy. Errors: GNN_EINVAL, GNN_ENOMEM. */
 int gnn_graph_build(const gnn_mesh_desc* desc, gnn_graph** out);
+
+/* General element meshes. Sec. II-A notes that the graph construction and its
+ * distribution apply to any mesh made of finite elements; here elements of any
+ * type and size may be mixed. Element e holds the global node ids
+ * elem_nodes[elem_ptr[e] .. elem_ptr[e+1]) and the undirected edges joining
+ * its local nodes u and v for every pair (u, v) = (edge_pairs[2k],
+ * edge_pairs[2k+1]), k in [edge_ptr[e], edge_ptr[e+1]) -- a hex of order p
+ * lists its (p+1)^3 GLL nodes and stencil pairs, a tetrahedron its 4 vertices
+ * and 6 edges, a polyhedral cell with a centre node the spokes from it. The
+ * R=1 graph is the union of the element edges in both directions (receiver-
+ * sorted, senders ascending; a node's in-degree is not bounded). An element's
+ * centre, which GNN_PART_RCB and GNN_PART_SLAB_Z split, is the mean position
+ * of its nodes. The arrays are read during the call only.
+ * Errors: GNN_EINVAL (NULL arrays, offsets not starting at 0 or descending, a
+ * node id or local index out of range, a pair joining a node to itself, a node
+ * in no element or on no edge -- every row of a partition then receives at
+ * least one edge, as the edge kernels expect), GNN_ESHAPE (more than 2^31-1
+ * nodes), GNN_ENOMEM. */
+typedef struct gnn_elem_mesh_desc {
+    int64_t n_nodes;
+    const double* pos;          /* host [n_nodes x 3] node positions                         */
+    int64_t n_elem;
+    const int64_t* elem_ptr;    /* host [n_elem+1] offsets into elem_nodes                   */
+    const int64_t* elem_nodes;  /* host [elem_ptr[n_elem]] global node ids, 0 <= id < n_nodes */
+    const int64_t* edge_ptr;    /* host [n_elem+1] offsets into edge_pairs, in pairs         */
+    const int32_t* edge_pairs;  /* host [2 x edge_ptr[n_elem]] element-local node indices    */
+} gnn_elem_mesh_desc;
+int gnn_graph_build_elements(const gnn_elem_mesh_desc* desc, gnn_graph** out);
+
 void gnn_graph_destroy(gnn_graph* g);
 int gnn_graph_get_info(const gnn_graph* g, gnn_graph_info* info);
 /* Copy-out accessors into caller-owned host buffers of the stated length. */
 int gnn_graph_copy_pos(const gnn_graph* g, double* pos /* [n_nodes*3] */);
 int gnn_graph_copy_csr(const gnn_graph* g, int64_t* row_ptr /* [n_nodes+1] */,
                        int64_t* col /* [n_edges] */);
-int gnn_graph_copy_elements(const gnn_graph* g, int64_t* elem_nodes /* [n_elem*(p+1)^3] */);
+/* Element node lists, concatenated ([n_elem_nodes]; a brick element's (p+1)^3
+ * nodes in local order i + (p+1)*(j + (p+1)*k)), and their offsets. */
+int gnn_graph_copy_elements(const gnn_graph* g, int64_t* elem_nodes /* [n_elem_nodes] */);
+int gnn_graph_copy_element_ptr(const gnn_graph* g, int64_t* elem_ptr /* [n_elem+1] */);
 
 /* ================================================ partitioning + halo (host)
  * Sec. II-A, Figs. 3-4: elements are split over R sub-graphs; each keeps the
@@ -97,14 +135,16 @@ int gnn_graph_copy_elements(const gnn_graph* g, int64_t* elem_nodes /* [n_elem*(
  * halo rows of Fig. 4 become a copy list: for every global id held by >= 2
  * sub-graphs, the rows holding it in increasing sub-graph order.
  */
-#define GNN_PART_SLAB_Z 0    /* R contiguous z-layers of elements                        */
+#define GNN_PART_SLAB_Z 0    /* R contiguous z-layers of elements (element meshes: R
+                                 runs of the elements sorted by (centre z, id), run r
+                                 holding sorted positions [floor(r*n/R), floor((r+1)*n/R))) */
 #define GNN_PART_RCB    1    /* recursive coordinate bisection of element centres        */
 
 typedef struct gnn_partition gnn_partition;   /* opaque, library-owned host object */
 
 typedef struct gnn_partition_info {
     int32_t n_parts;         /* R                                                          */
-    int32_t max_in_degree;   /* largest receiver in-degree over all rows                  */
+    int32_t max_in_degree;   /* largest receiver in-degree over all rows (<= GNN_EDGE_TILE) */
     int64_t n_rows;          /* sum of local rows over sub-graphs                          */
     int64_t n_edges;         /* sum of local directed edges                                */
     int64_t n_shared;        /* global ids held by >= 2 sub-graphs                        */
@@ -124,10 +164,32 @@ typedef struct gnn_partition_info {
  * rest along the axis of largest element-centre extent (lowest axis on ties),
  * after a stable sort by (centre, element id), giving the left side
  * floor(count*W_left/W + 0.5) elements (at least one per part).
+ * Brick elements have their lattice centres; element-mesh elements the mean
+ * of their node positions.
  * Errors: GNN_EINVAL (R out of range, bad weights), GNN_ESHAPE (more than
- * 2^31-1 rows or edges), GNN_ENOMEM. */
+ * 2^31-1 rows or edges), GNN_EUNSUPPORTED (a node or edge held by more than
+ * 255 rows or sub-graphs), GNN_ENOMEM. */
 int gnn_partition_halo(const gnn_graph* g, int32_t R, int32_t method,
                        const double* target_weights, gnn_partition** out);
+/* Partition g with a caller-given element -> sub-graph map (host [n_elem]
+ * values in [0, R), every sub-graph non-empty), e.g. a solver's own domain
+ * decomposition. Everything else as gnn_partition_halo.
+ * Errors: GNN_EINVAL (R out of range, a value out of range, an empty part),
+ * GNN_ESHAPE, GNN_EUNSUPPORTED, GNN_ENOMEM. */
+int gnn_partition_elements(const gnn_graph* g, int32_t R, const int32_t* elem_part,
+                           gnn_partition** out);
+
+/* Nodes of high in-degree. The edge kernels take tiles of whole receivers
+ * (GNN_EDGE_TILE edges at most), so a node whose in-degree within one
+ * sub-graph exceeds GNN_EDGE_TILE is held there by k = ceil(degree /
+ * GNN_EDGE_TILE) consecutive rows (copies), copy c receiving the c-th of k
+ * near-equal consecutive runs of its in-edges (senders ascending) and sending
+ * to the nodes of that run. The copies enter the copy list like the copies in
+ * other sub-graphs, so Eq. 5c-5d sums their partial aggregates (the carry of
+ * the split receiver) and every copy continues with the same a*; d_i (Eq. 8b)
+ * counts all rows holding node i. Rows within a sub-graph stay ordered by
+ * global id. GNN_EUNSUPPORTED when a node would need more than 255 rows in
+ * total (d_i and d_ij are 8-bit). */
 void gnn_partition_destroy(gnn_partition* p);
 int gnn_partition_get_info(const gnn_partition* p, gnn_partition_info* info);
 
@@ -141,7 +203,8 @@ int gnn_partition_set_tile_edges(gnn_partition* p, int32_t tile_edges);
 
 /* Arrays of a partition, copied into a caller-owned host buffer of exactly
  * `bytes` bytes (GNN_ESHAPE otherwise). Row r of sub-graph s is global row
- * row_offsets[s] + r; local rows are ordered by global id. */
+ * row_offsets[s] + r; local rows are ordered by global id (the copies of a
+ * split high in-degree node are consecutive). */
 #define GNN_P_ROW_OFFSETS  0   /* int64 [R+1]                                               */
 #define GNN_P_EDGE_OFFSETS 1   /* int64 [R+1]                                               */
 #define GNN_P_ROW_GID      2   /* int64 [n_rows] global id of each row                      */

@@ -183,14 +183,20 @@ def partition_rcb(brick: Brick, R: int, target_weights=None) -> np.ndarray:
     after a stable sort by (coordinate, element id); the left share is
     floor(n * W_left / W + 0.5) elements, clamped so every part keeps at
     least one element. W sums the target weights of the parts on each side."""
-    n_elem = brick.n_elem
+    h = [brick.extent[a] / brick.nel[a] for a in range(3)]
+    centre = np.stack([(brick.elem_ijk[:, a] + 0.5) * h[a] for a in range(3)], axis=1)
+    return rcb_of_centres(centre, R, target_weights)
+
+
+def rcb_of_centres(centre: np.ndarray, R: int, target_weights=None) -> np.ndarray:
+    """Element -> part by recursive coordinate bisection of the given element
+    centres ([n_elem, 3]), by the rule of ``partition_rcb``."""
+    n_elem = centre.shape[0]
     if not (1 <= R <= n_elem):
         raise ValueError("RCB needs 1 <= R <= number of elements")
     w = np.ones(R) if target_weights is None else np.asarray(target_weights, dtype=np.float64)
     if w.shape != (R,) or np.any(w <= 0):
         raise ValueError("target weights must be R positive numbers")
-    h = [brick.extent[a] / brick.nel[a] for a in range(3)]
-    centre = np.stack([(brick.elem_ijk[:, a] + 0.5) * h[a] for a in range(3)], axis=1)
     part = np.empty(n_elem, dtype=np.int64)
 
     def split(elems: np.ndarray, r0: int, nr: int):
@@ -274,6 +280,14 @@ def build_subgraphs(brick: Brick, part: np.ndarray, R: int, with_halo: bool = Tr
         u = en[:, pairs[:, 0]].ravel()
         v = en[:, pairs[:, 1]].ravel()
         edge_sets.append(np.unique(np.concatenate([u * N + v, v * N + u])))
+    return subgraphs_of_sets(N, node_sets, edge_sets, with_halo)
+
+
+def subgraphs_of_sets(N: int, node_sets: list, edge_sets: list, with_halo: bool = True) -> list:
+    """Reduced sub-graphs from each rank's global node ids (ascending) and
+    directed edge keys recv*N + send (ascending): d_ij and d_i count the ranks
+    holding each edge and node; halo rows as in ``build_subgraphs``."""
+    R = len(node_sets)
     node_count = np.zeros(N, dtype=np.int64)
     for s in node_sets:
         node_count[s] += 1
@@ -325,3 +339,104 @@ def unpartitioned(brick: Brick) -> list:
     return [SubGraph(gid=np.arange(N, dtype=np.int64), recv=brick.recv.copy(),
                      send=brick.send.copy(), edge_deg=np.ones(brick.n_edges, dtype=np.int64),
                      node_deg=np.ones(N, dtype=np.int64))]
+
+
+# --------------------------------------------------------------------------- general element meshes
+
+@dataclass
+class ElementMesh:
+    """A mesh of elements of any types (Sec. II-A: the graph construction and
+    its distribution apply to any mesh made of finite elements). Element e
+    holds the global nodes elem_nodes[elem_ptr[e]:elem_ptr[e+1]] and the
+    undirected edges between its local nodes edge_pairs[k] = (u, v),
+    k in [edge_ptr[e], edge_ptr[e+1])."""
+    pos: np.ndarray
+    elem_ptr: np.ndarray
+    elem_nodes: np.ndarray
+    edge_ptr: np.ndarray
+    edge_pairs: np.ndarray
+    recv: np.ndarray         # [E] receiver global id of each directed edge (sorted)
+    send: np.ndarray         # [E] sender global id
+
+    @property
+    def n_nodes(self) -> int:
+        return self.pos.shape[0]
+
+    @property
+    def n_edges(self) -> int:
+        return self.recv.shape[0]
+
+    @property
+    def n_elem(self) -> int:
+        return self.elem_ptr.shape[0] - 1
+
+    def element(self, e: int):
+        """Global node ids and global (u, v) edge pairs of element e."""
+        nodes = self.elem_nodes[self.elem_ptr[e]:self.elem_ptr[e + 1]]
+        pr = self.edge_pairs[self.edge_ptr[e]:self.edge_ptr[e + 1]]
+        return nodes, nodes[pr[:, 0]], nodes[pr[:, 1]]
+
+
+def element_mesh(pos, elem_ptr, elem_nodes, edge_ptr, edge_pairs) -> ElementMesh:
+    """The R=1 graph of an element mesh: every element edge in both directions,
+    unique, sorted by receiver and then sender."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    mesh = ElementMesh(pos=pos, elem_ptr=np.asarray(elem_ptr, dtype=np.int64),
+                       elem_nodes=np.asarray(elem_nodes, dtype=np.int64),
+                       edge_ptr=np.asarray(edge_ptr, dtype=np.int64),
+                       edge_pairs=np.asarray(edge_pairs, dtype=np.int64).reshape(-1, 2),
+                       recv=np.zeros(0, np.int64), send=np.zeros(0, np.int64))
+    N = mesh.n_nodes
+    keys = _element_edge_keys(mesh, range(mesh.n_elem))
+    mesh.recv, mesh.send = keys // N, keys % N
+    return mesh
+
+
+def _element_edge_keys(mesh: ElementMesh, elems) -> np.ndarray:
+    N = mesh.n_nodes
+    ks = [np.zeros(0, np.int64)]
+    for e in elems:
+        _, u, v = mesh.element(e)
+        ks.append(u * N + v)
+        ks.append(v * N + u)
+    return np.unique(np.concatenate(ks))
+
+
+def element_centres(mesh: ElementMesh) -> np.ndarray:
+    """Mean position of each element's nodes."""
+    return np.stack([mesh.pos[mesh.element(e)[0]].mean(axis=0) for e in range(mesh.n_elem)])
+
+
+def partition_rcb_elements(mesh: ElementMesh, R: int, target_weights=None) -> np.ndarray:
+    return rcb_of_centres(element_centres(mesh), R, target_weights)
+
+
+def partition_slab_elements(mesh: ElementMesh, R: int) -> np.ndarray:
+    """R runs of the elements sorted by (centre z, element id); run r holds
+    sorted positions [floor(r*n/R), floor((r+1)*n/R))."""
+    n = mesh.n_elem
+    if not (1 <= R <= n):
+        raise ValueError("slab partition needs 1 <= R <= number of elements")
+    order = np.lexsort((np.arange(n), element_centres(mesh)[:, 2]))
+    part = np.empty(n, dtype=np.int64)
+    for r in range(R):
+        part[order[(r * n) // R:((r + 1) * n) // R]] = r
+    return part
+
+
+def build_element_subgraphs(mesh: ElementMesh, part: np.ndarray, R: int, with_halo: bool = True) -> list:
+    """Reduced distributed graph of an element mesh: rank r keeps the nodes and
+    edges of its elements (Fig. 3(c)), with halo rows (Fig. 4)."""
+    node_sets, edge_sets = [], []
+    for r in range(R):
+        elems = np.nonzero(np.asarray(part) == r)[0]
+        node_sets.append(np.unique(np.concatenate([mesh.element(e)[0] for e in elems])))
+        edge_sets.append(_element_edge_keys(mesh, elems))
+    return subgraphs_of_sets(mesh.n_nodes, node_sets, edge_sets, with_halo)
+
+
+def element_mesh_unpartitioned(mesh: ElementMesh) -> list:
+    """The R=1 graph of an element mesh as a one-rank sub-graph list."""
+    N = mesh.n_nodes
+    return [SubGraph(gid=np.arange(N, dtype=np.int64), recv=mesh.recv.copy(), send=mesh.send.copy(),
+                     edge_deg=np.ones(mesh.n_edges, dtype=np.int64), node_deg=np.ones(N, dtype=np.int64))]

@@ -18,6 +18,7 @@ GNN_EINVAL, GNN_ESHAPE, GNN_EDTYPE, GNN_ECUDA = -1, -2, -3, -4
 GNN_EHALO, GNN_ETIMEOUT, GNN_ENOMEM, GNN_EUNSUPPORTED = -5, -6, -7, -8
 
 GNN_PART_SLAB_Z, GNN_PART_RCB = 0, 1
+GNN_GRAPH_BRICK, GNN_GRAPH_ELEMENTS = 0, 1
 GNN_PREC_FP32, GNN_PREC_BF16 = 0, 1
 GNN_HALO_SYNC, GNN_HALO_NONE = 0, 1
 GNN_FLAG_NO_EDGE_OUT = 1
@@ -45,9 +46,16 @@ class gnn_mesh_desc(C.Structure):
                 ("jitter", C.POINTER(C.c_double))]
 
 
+class gnn_elem_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("pos", C.c_void_p), ("n_elem", C.c_int64),
+                ("elem_ptr", C.c_void_p), ("elem_nodes", C.c_void_p), ("edge_ptr", C.c_void_p),
+                ("edge_pairs", C.c_void_p)]
+
+
 class gnn_graph_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_edges", C.c_int64), ("n_elem", C.c_int64),
-                ("L", C.c_int32 * 3), ("p", C.c_int32)]
+                ("L", C.c_int32 * 3), ("p", C.c_int32), ("n_elem_nodes", C.c_int64),
+                ("kind", C.c_int32), ("max_degree", C.c_int32)]
 
 
 class gnn_partition_info(C.Structure):
@@ -97,7 +105,10 @@ _SIGS = {
     "gnn_graph_copy_pos": (C.c_int, [_P, _P]),
     "gnn_graph_copy_csr": (C.c_int, [_P, _P, _P]),
     "gnn_graph_copy_elements": (C.c_int, [_P, _P]),
+    "gnn_graph_build_elements": (C.c_int, [C.POINTER(gnn_elem_mesh_desc), C.POINTER(_P)]),
+    "gnn_graph_copy_element_ptr": (C.c_int, [_P, _P]),
     "gnn_partition_halo": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
+    "gnn_partition_elements": (C.c_int, [_P, C.c_int32, _P, C.POINTER(_P)]),
     "gnn_partition_destroy": (None, [_P]),
     "gnn_partition_get_info": (C.c_int, [_P, C.POINTER(gnn_partition_info)]),
     "gnn_partition_copy": (C.c_int, [_P, C.c_int32, _P, C.c_size_t]),

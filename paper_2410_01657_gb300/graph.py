@@ -1,8 +1,10 @@
 """Mesh graphs and partitions of libgnnmp as Python objects.
 
-``MeshGraph`` wraps ``gnn_graph_build`` (the R=1 GLL-brick graph, Sec. II-A),
-``Partition`` wraps ``gnn_partition_halo`` (reduced sub-graphs, multiplicities
-and the halo copy list, Figs. 3-4), and ``DeviceGraph`` holds the partition's
+``MeshGraph`` wraps ``gnn_graph_build`` (the R=1 GLL-brick graph, Sec. II-A)
+and ``gnn_graph_build_elements`` (a mesh of elements of any types),
+``Partition`` wraps ``gnn_partition_halo`` / ``gnn_partition_elements``
+(reduced sub-graphs, multiplicities and the halo copy list, Figs. 3-4), and
+``DeviceGraph`` holds the partition's
 arrays in device memory (allocated by torch) together with the
 ``gnn_graph_dev`` struct that the compute entry points take.
 """
@@ -16,7 +18,8 @@ from . import binding as B
 
 
 class MeshGraph:
-    """R=1 graph of a brick of nel[0] x nel[1] x nel[2] hex elements of order p."""
+    """R=1 graph of a brick of nel[0] x nel[1] x nel[2] hex elements of order p
+    (or, built by ``from_elements``, of a general element mesh)."""
 
     def __init__(self, nel, p, extent=(1.0, 1.0, 1.0), periodic=(False, False, False),
                  jitter=None, jitter_frac=0.0):
@@ -38,6 +41,35 @@ class MeshGraph:
         self.info = B.gnn_graph_info()
         B.call("gnn_graph_get_info", self._h, C.byref(self.info))
         self.nel, self.p = tuple(int(v) for v in nel), int(p)
+
+    @classmethod
+    def from_elements(cls, pos, elem_ptr, elem_nodes, edge_ptr, edge_pairs) -> "MeshGraph":
+        """Graph of a general element mesh: element e holds the global nodes
+        elem_nodes[elem_ptr[e]:elem_ptr[e+1]] and the undirected edges between
+        its local nodes edge_pairs[k] = (u, v), k in [edge_ptr[e], edge_ptr[e+1])."""
+        B.load()
+        arrs = [np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3),
+                np.ascontiguousarray(elem_ptr, dtype=np.int64),
+                np.ascontiguousarray(elem_nodes, dtype=np.int64),
+                np.ascontiguousarray(edge_ptr, dtype=np.int64),
+                np.ascontiguousarray(edge_pairs, dtype=np.int32).reshape(-1, 2)]
+        d = B.gnn_elem_mesh_desc()
+        d.n_nodes = arrs[0].shape[0]
+        d.n_elem = arrs[1].shape[0] - 1
+        d.pos, d.elem_ptr, d.elem_nodes, d.edge_ptr, d.edge_pairs = (B.ptr(a) for a in arrs)
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        B.call("gnn_graph_build_elements", C.byref(d), C.byref(h))
+        self._h = h
+        self._jitter = None
+        self.info = B.gnn_graph_info()
+        B.call("gnn_graph_get_info", self._h, C.byref(self.info))
+        self.nel, self.p = None, 0
+        return self
+
+    @property
+    def is_brick(self) -> bool:
+        return int(self.info.kind) == B.GNN_GRAPH_BRICK
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -69,13 +101,21 @@ class MeshGraph:
         return rp, col
 
     def elements(self) -> np.ndarray:
-        q = self.p + 1
-        out = np.empty((int(self.info.n_elem), q ** 3), dtype=np.int64)
+        """Brick: [n_elem, (p+1)^3] node ids; element mesh: the flat node lists
+        (offsets from ``element_ptr``)."""
+        out = np.empty(int(self.info.n_elem_nodes), dtype=np.int64)
         B.call("gnn_graph_copy_elements", self._h, B.ptr(out))
+        return out.reshape(int(self.info.n_elem), -1) if self.is_brick else out
+
+    def element_ptr(self) -> np.ndarray:
+        out = np.empty(int(self.info.n_elem) + 1, dtype=np.int64)
+        B.call("gnn_graph_copy_element_ptr", self._h, B.ptr(out))
         return out
 
-    def partition(self, R: int, method: str = "rcb", target_weights=None) -> "Partition":
-        return Partition(self, R, method, target_weights)
+    def partition(self, R: int, method: str = "rcb", target_weights=None, elem_part=None) -> "Partition":
+        """R sub-graphs by ``method`` ("rcb" or "slab"), or by the given
+        element -> sub-graph map ``elem_part``."""
+        return Partition(self, R, method, target_weights, elem_part)
 
 
 _ARRAYS = {
@@ -103,13 +143,19 @@ _ARRAYS = {
 class Partition:
     """R reduced sub-graphs of a MeshGraph, concatenated (host arrays)."""
 
-    def __init__(self, graph: MeshGraph, R: int, method: str = "rcb", target_weights=None):
-        m = {"slab": B.GNN_PART_SLAB_Z, "slab_z": B.GNN_PART_SLAB_Z, "rcb": B.GNN_PART_RCB}[method]
-        w = None
-        if target_weights is not None:
-            w = np.ascontiguousarray(target_weights, dtype=np.float64)
+    def __init__(self, graph: MeshGraph, R: int, method: str = "rcb", target_weights=None, elem_part=None):
         h = C.c_void_p()
-        B.call("gnn_partition_halo", graph._h, int(R), m, B.ptr(w), C.byref(h))
+        if elem_part is not None:
+            ep = np.ascontiguousarray(elem_part, dtype=np.int32)
+            if ep.shape != (int(graph.info.n_elem),):
+                raise ValueError("elem_part must hold one sub-graph index per element")
+            B.call("gnn_partition_elements", graph._h, int(R), B.ptr(ep), C.byref(h))
+        else:
+            m = {"slab": B.GNN_PART_SLAB_Z, "slab_z": B.GNN_PART_SLAB_Z, "rcb": B.GNN_PART_RCB}[method]
+            w = None
+            if target_weights is not None:
+                w = np.ascontiguousarray(target_weights, dtype=np.float64)
+            B.call("gnn_partition_halo", graph._h, int(R), m, B.ptr(w), C.byref(h))
         self._h = h
         self.graph = graph
         self.info = B.gnn_partition_info()

@@ -17,6 +17,10 @@ Recipes (all numpy PCG64 via ``numpy.random.default_rng(seed)``):
   smooth low-wavenumber Taylor-Green velocity the paper trains on (Sec. III-B).
 * Mesh jitter: U[-1,1] per global node and axis; the graph builder scales it.
 * Partition sizes: element counts drawn log-uniform on [lo, hi].
+* Mixed element mesh (``mixed_element_mesh``): a unit cube of n^3 lattice
+  cells, each drawn (U[0,1) < tet_fraction) as one 8-node hexahedron or as
+  its 6 Kuhn tetrahedra, plus fan cells joining one apex above the top face to
+  bands of top-face nodes; interior nodes jittered U[-1/2,1/2]*jitter/n.
 """
 from __future__ import annotations
 
@@ -168,3 +172,75 @@ def uneven_brick(n_parts: int, lo: float, hi: float, seed: int):
     while n ** 3 < counts.sum():
         n += 1
     return n, rescale_counts(counts, n ** 3)
+
+
+# local node index of a p=1 hexahedron: i + 2*(j + 2*k)
+HEX_EDGES = np.array([(0, 1), (2, 3), (4, 5), (6, 7),        # along x
+                      (0, 2), (1, 3), (4, 6), (5, 7),        # along y
+                      (0, 4), (1, 5), (2, 6), (3, 7)],       # along z
+                     dtype=np.int32)
+TET_EDGES = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)], dtype=np.int32)
+
+
+def kuhn_tets() -> list:
+    """The 6 Kuhn tetrahedra of the unit cube as hex-local vertex indices: for
+    each order (a, b, c) of the axes, the path 0 -> +e_a -> +e_b -> +e_c = 7."""
+    out = []
+    for a, b, c in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        v1 = 1 << a
+        v2 = v1 | (1 << b)
+        out.append((0, v1, v2, 7))
+    return out
+
+
+def mixed_element_mesh(n: int, seed: int, tet_fraction: float = 0.5, n_fans: int = 2,
+                       jitter: float = 0.2) -> dict:
+    """Element lists of a mixed mesh on the unit cube (input structure only).
+
+    Lattice node (i, j, k), 0 <= i, j, k <= n, has id i + (n+1)*(j + (n+1)*k)
+    and sits at (i, j, k)/n, interior nodes moved by jitter*U[-1/2,1/2]/n per
+    axis; the apex (id (n+1)^3, present when n_fans > 0) sits at
+    (1/2, 1/2, 1 + 1/n). Cells in order
+    i + n*(j + n*k) become one hexahedron (8 nodes, ``HEX_EDGES``) or, when
+    U[0,1) < tet_fraction, 6 tetrahedra (``kuhn_tets``, ``TET_EDGES``). Then
+    fan f < n_fans holds the apex (local 0) and the top-face nodes of the
+    columns floor(f*n/n_fans) .. floor((f+1)*n/n_fans) (neighbouring fans share
+    a column) with a spoke from the apex to each. Returns pos, elem_ptr,
+    elem_nodes, edge_ptr, edge_pairs and the element kind (0 hex, 1 tet, 2 fan)."""
+    rng = np.random.default_rng(seed)
+    m = n + 1
+    N = m ** 3 + (1 if n_fans > 0 else 0)
+    k, j, i = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    pos = np.zeros((N, 3))
+    interior = np.all((ijk > 0) & (ijk < n), axis=1)
+    off = rng.uniform(-0.5, 0.5, size=(m ** 3, 3)) * jitter / n
+    pos[:m ** 3] = ijk / n + np.where(interior[:, None], off, 0.0)
+    if n_fans > 0:
+        pos[m ** 3] = (0.5, 0.5, 1.0 + 1.0 / n)
+    draw = rng.uniform(size=n ** 3)
+    nodes, pairs, kind = [], [], []
+    for c in range(n ** 3):
+        ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+        hexn = [(ci + (v & 1)) + m * ((cj + ((v >> 1) & 1)) + m * (ck + ((v >> 2) & 1))) for v in range(8)]
+        if draw[c] < tet_fraction:
+            for t in kuhn_tets():
+                nodes.append([hexn[v] for v in t])
+                pairs.append(TET_EDGES)
+                kind.append(1)
+        else:
+            nodes.append(hexn)
+            pairs.append(HEX_EDGES)
+            kind.append(0)
+    for f in range(n_fans):
+        lo, hi = (f * n) // n_fans, ((f + 1) * n) // n_fans
+        top = [ii + m * (jj + m * n) for ii in range(lo, hi + 1) for jj in range(m)]
+        nodes.append([m ** 3] + top)
+        pairs.append(np.array([(0, t + 1) for t in range(len(top))], dtype=np.int32))
+        kind.append(2)
+    elem_ptr = np.concatenate([[0], np.cumsum([len(x) for x in nodes])]).astype(np.int64)
+    edge_ptr = np.concatenate([[0], np.cumsum([len(x) for x in pairs])]).astype(np.int64)
+    return {"pos": pos, "elem_ptr": elem_ptr,
+            "elem_nodes": np.concatenate([np.asarray(x, dtype=np.int64) for x in nodes]),
+            "edge_ptr": edge_ptr, "edge_pairs": np.concatenate(pairs).astype(np.int32),
+            "kind": np.asarray(kind, dtype=np.int8)}

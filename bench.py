@@ -58,6 +58,11 @@ WORKLOADS = {
                     "CUDA graph, autotuned tiles"),
     "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=False,
                desc="48^3 elements p=7 GLL brick, 16 RCB sub-graphs, inference: last layer writes no edge state"),
+    "mixed": dict(nel=64, p=1, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False, mesh="mixed",
+                  cells="cells", sample=24, ref_sample=16,
+                  desc="mixed element mesh of the unit cube (each cell one hexahedron or its 6 Kuhn tetrahedra, "
+                       "drawn 50/50) with 8 fan cells on one apex of in-degree 4,225, held as co-resident copies "
+                       "of <= 128 in-edges, 8 RCB sub-graphs"),
     "large": dict(nel=16, p=5, parts=8, H=32, nh=5, mode="fwdbwd", inputs="encoders", graph=False,
                   desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs, the paper's large model (Table 1: "
                        "H=32, 5 MLP hidden layers)"),
@@ -76,7 +81,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd+bwd; c4: 64 uneven jittered "
                          "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference; large: the C2 graph with the "
-                         "paper's large model (H=32, 5 MLP hidden layers)")
+                         "paper's large model (H=32, 5 MLP hidden layers); mixed: a 64^3-cell mesh of mixed "
+                         "element types with a node of in-degree 4,225, H=64 fwd+bwd")
     ap.add_argument("--nel", type=int, default=None,
                     help="elements per axis of the brick (default: the workload's; smaller for profiling)")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step")
@@ -208,18 +214,26 @@ def load_peaks() -> dict:
 # ---------------------------------------------------------------- oracle timing (CPU)
 
 def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts: int = R, fwd_only: bool = False,
-                  nh: int = NH):
-    """Time the FP64 oracle on an n_el^3 brick of order p (RCB parts, 4 layers of
-    width `hidden`, forward + backward unless fwd_only): a bounded sample of a
-    workload family. Returns (edges/s, seconds per step, description, threads)."""
+                  nh: int = NH, mesh: str = "brick"):
+    """Time the FP64 oracle on an n_el^3 brick of order p (or, mesh="mixed", the
+    n_el^3-cell mixed element mesh; RCB parts, 4 layers of width `hidden`,
+    forward + backward unless fwd_only): a bounded sample of a workload family.
+    Returns (edges/s, seconds per step, description, threads)."""
     import numpy as np
 
     import synthetic as syn
     from oracle import graph as og
     from oracle import model as om
 
-    b = og.build_brick((n_el,) * 3, p)
-    subs = og.build_subgraphs(b, og.partition_rcb(b, parts), parts)
+    if mesh == "mixed":
+        m = syn.mixed_element_mesh(n_el, SEED, n_fans=8)
+        b = og.element_mesh(m["pos"], m["elem_ptr"], m["elem_nodes"], m["edge_ptr"], m["edge_pairs"])
+        subs = og.build_element_subgraphs(b, og.partition_rcb_elements(b, parts), parts)
+        what = f"{n_el}^3-cell mixed element mesh"
+    else:
+        b = og.build_brick((n_el,) * 3, p)
+        subs = og.build_subgraphs(b, og.partition_rcb(b, parts), parts)
+        what = f"{n_el}^3 elements p={p}"
     params = syn.gnn_params(SEED, hidden, nh, M)
     rng = np.random.default_rng(1)
     xg = rng.standard_normal((b.n_nodes, hidden))
@@ -240,7 +254,7 @@ def oracle_sample(n_el: int, steps: int = 1, p: int = P, hidden: int = H, parts:
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
     return (b.n_edges * M / t, t,
-            f"{n_el}^3 elements p={p} ({b.n_nodes} nodes, {b.n_edges} edges), {parts} RCB parts, H={hidden}, "
+            f"{what} ({b.n_nodes} nodes, {b.n_edges} edges), {parts} RCB parts, H={hidden}, "
             f"MLP {nh} hidden, 4 layers {'fwd' if fwd_only else 'fwd+bwd'}, FP64 numpy", _blas_threads())
 
 
@@ -257,7 +271,7 @@ def _blas_threads() -> int:
 
 def workload_config_text(wl: dict, n_el, n_unpart, e_unpart, kind: str) -> str:
     """The `config.workload` text of a workload (shared by both arms)."""
-    return (f"consistent NMP layers x{M} {kind}, {n_el}^3 elements: {wl['desc']} "
+    return (f"consistent NMP layers x{M} {kind}, {n_el}^3 {wl.get('cells', 'elements')}: {wl['desc']} "
             f"({n_unpart:,} nodes, {e_unpart:,} edges), H={wl['H']}, MLP {wl.get('nh', NH)} hidden")
 
 
@@ -272,8 +286,9 @@ def run_reference(args):
     wl = dict(WORKLOADS[args.workload])
     fwd_only = wl["mode"] == "fwd" or args.mode == "fwd"
     kind = "fwd" if fwd_only else "fwd+bwd"
-    sample = dict(n_el={5: 4, 7: 3}[wl["p"]], p=wl["p"], hidden=wl["H"],
-                  parts=wl["parts"] if wl["parts"] <= 16 else 8, fwd_only=fwd_only, nh=wl.get("nh", NH))
+    sample = dict(n_el=wl.get("ref_sample") or {5: 4, 7: 3}[wl["p"]], p=wl["p"], hidden=wl["H"],
+                  parts=wl["parts"] if wl["parts"] <= 16 else 8, fwd_only=fwd_only, nh=wl.get("nh", NH),
+                  mesh=wl.get("mesh", "brick"))
     for _ in range(args.warmup):
         oracle_sample(**sample)
     vals, secs = [], []
@@ -285,6 +300,9 @@ def run_reference(args):
     value = statistics.median(vals)
     if wl.get("uneven") or args.nel:
         workload = f"{wl['desc']}, H={wl['H']}, MLP {wl.get('nh', NH)} hidden, {kind}"
+    elif wl.get("mesh") == "mixed":
+        n_nodes, n_edges = mixed_mesh_counts(wl["nel"])
+        workload = workload_config_text(wl, wl["nel"], n_nodes, n_edges, kind)
     else:
         L = wl["nel"] * wl["p"] + 1
         workload = workload_config_text(wl, wl["nel"], L ** 3, 6 * L * L * (L - 1), kind)
@@ -312,6 +330,21 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def mixed_mesh_counts(n: int):
+    """Nodes and directed edges of the n^3-cell mixed mesh (its element lists, counted with numpy)."""
+    import numpy as np
+
+    import synthetic as syn
+
+    m = syn.mixed_element_mesh(n, SEED, n_fans=8)
+    N = m["pos"].shape[0]
+    el = np.repeat(np.arange(m["elem_ptr"].size - 1), np.diff(m["edge_ptr"]))
+    base = m["elem_ptr"][el]
+    u = m["elem_nodes"][base + m["edge_pairs"][:, 0]]
+    v = m["elem_nodes"][base + m["edge_pairs"][:, 1]]
+    return N, int(np.unique(np.concatenate([u * N + v, v * N + u])).size)
+
+
 def workload_graph(wl: dict, nel):
     """(Partition, unpartitioned nodes, unpartitioned directed edges) of a workload."""
     import numpy as np
@@ -320,6 +353,11 @@ def workload_graph(wl: dict, nel):
     from paper_2410_01657_gb300.graph import MeshGraph
 
     p = wl["p"]
+    if wl.get("mesh") == "mixed":
+        n = nel or wl["nel"]
+        m = syn.mixed_element_mesh(n, SEED, n_fans=8)
+        g = MeshGraph.from_elements(m["pos"], m["elem_ptr"], m["elem_nodes"], m["edge_ptr"], m["edge_pairs"])
+        return g.partition(wl["parts"], "rcb"), n, g.n_nodes, g.n_edges
     if wl.get("uneven"):
         n, weights = syn.uneven_brick(wl["parts"], 50, 5000, SEED)
         if nel:
@@ -547,9 +585,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         # a bounded sample of the same workload family: a small brick of the same order,
         # width, partition count and pass (about 5-20 s of host time)
-        n_s = {5: 6, 7: 4}[wl["p"]]
+        n_s = wl.get("sample") or {5: 6, 7: 4}[wl["p"]]
         v, tsec, desc, threads = oracle_sample(n_s, p=wl["p"], hidden=Hw, parts=wl["parts"] if wl["parts"] <= 16 else 8,
-                                               fwd_only=fwd_only, nh=wl.get("nh", NH))
+                                               fwd_only=fwd_only, nh=wl.get("nh", NH), mesh=wl.get("mesh", "brick"))
         cpu = {"value": v, "unit": "edges/s", "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": tsec}
 

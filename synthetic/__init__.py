@@ -219,28 +219,42 @@ def mixed_element_mesh(n: int, seed: int, tet_fraction: float = 0.5, n_fans: int
     if n_fans > 0:
         pos[m ** 3] = (0.5, 0.5, 1.0 + 1.0 / n)
     draw = rng.uniform(size=n ** 3)
-    nodes, pairs, kind = [], [], []
-    for c in range(n ** 3):
-        ci, cj, ck = c % n, (c // n) % n, c // (n * n)
-        hexn = [(ci + (v & 1)) + m * ((cj + ((v >> 1) & 1)) + m * (ck + ((v >> 2) & 1))) for v in range(8)]
-        if draw[c] < tet_fraction:
-            for t in kuhn_tets():
-                nodes.append([hexn[v] for v in t])
-                pairs.append(TET_EDGES)
-                kind.append(1)
-        else:
-            nodes.append(hexn)
-            pairs.append(HEX_EDGES)
-            kind.append(0)
+    c = np.arange(n ** 3)
+    ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+    v = np.arange(8)
+    hexn = ((ci[:, None] + (v & 1)) + m * ((cj[:, None] + ((v >> 1) & 1)) + m * (ck[:, None] + ((v >> 2) & 1))))
+    tet = draw < tet_fraction
+    kuhn = np.array(kuhn_tets())
+    # elements in cell order: a hexahedron, or the cell's 6 tetrahedra
+    n_el = np.where(tet, 6, 1)
+    first = np.concatenate([[0], np.cumsum(n_el)])
+    kind = np.zeros(first[-1], dtype=np.int8)
+    size = np.full(first[-1], 8, dtype=np.int64)
+    npair = np.full(first[-1], len(HEX_EDGES), dtype=np.int64)
+    tet_el = (first[:-1][tet][:, None] + np.arange(6)).ravel()
+    kind[tet_el], size[tet_el], npair[tet_el] = 1, 4, len(TET_EDGES)
+    cell_ptr = np.concatenate([[0], np.cumsum(np.where(tet, 24, 8))])
+    cell_nodes = np.empty(cell_ptr[-1], dtype=np.int64)
+    hex_cells = np.nonzero(~tet)[0]
+    cell_nodes[(cell_ptr[hex_cells][:, None] + v).ravel()] = hexn[hex_cells].ravel()
+    tet_cells = np.nonzero(tet)[0]
+    cell_nodes[(cell_ptr[tet_cells][:, None] + np.arange(24)).ravel()] = hexn[tet_cells][:, kuhn].ravel()
+    pair_ptr = np.concatenate([[0], np.cumsum(npair)])
+    k = np.arange(pair_ptr[-1]) - np.repeat(pair_ptr[:-1], npair)
+    kk = np.repeat(kind, npair)
+    edge_pairs = np.where((kk == 0)[:, None], HEX_EDGES[np.minimum(k, len(HEX_EDGES) - 1)],
+                          TET_EDGES[np.minimum(k, len(TET_EDGES) - 1)])
+    fan_nodes, fan_pairs = [], []
     for f in range(n_fans):
         lo, hi = (f * n) // n_fans, ((f + 1) * n) // n_fans
-        top = [ii + m * (jj + m * n) for ii in range(lo, hi + 1) for jj in range(m)]
-        nodes.append([m ** 3] + top)
-        pairs.append(np.array([(0, t + 1) for t in range(len(top))], dtype=np.int32))
-        kind.append(2)
-    elem_ptr = np.concatenate([[0], np.cumsum([len(x) for x in nodes])]).astype(np.int64)
-    edge_ptr = np.concatenate([[0], np.cumsum([len(x) for x in pairs])]).astype(np.int64)
-    return {"pos": pos, "elem_ptr": elem_ptr,
-            "elem_nodes": np.concatenate([np.asarray(x, dtype=np.int64) for x in nodes]),
-            "edge_ptr": edge_ptr, "edge_pairs": np.concatenate(pairs).astype(np.int32),
-            "kind": np.asarray(kind, dtype=np.int8)}
+        ii, jj = np.meshgrid(np.arange(lo, hi + 1), np.arange(m), indexing="ij")
+        top = (ii + m * (jj + m * n)).ravel()
+        fan_nodes.append(np.concatenate([[m ** 3], top]))
+        fan_pairs.append(np.stack([np.zeros(top.size), np.arange(1, top.size + 1)], axis=1).astype(np.int32))
+    sizes = np.concatenate([size, [x.size for x in fan_nodes]]).astype(np.int64)
+    npairs = np.concatenate([npair, [x.shape[0] for x in fan_pairs]]).astype(np.int64)
+    return {"pos": pos, "elem_ptr": np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64),
+            "elem_nodes": np.concatenate([cell_nodes] + fan_nodes).astype(np.int64),
+            "edge_ptr": np.concatenate([[0], np.cumsum(npairs)]).astype(np.int64),
+            "edge_pairs": np.concatenate([edge_pairs] + fan_pairs).astype(np.int32),
+            "kind": np.concatenate([kind, np.full(n_fans, 2, dtype=np.int8)])}

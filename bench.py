@@ -143,10 +143,24 @@ class ClockSampler:
 # ---------------------------------------------------------------- roofline bookkeeping
 
 def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False,
-                      n_lin: int = NH + 2):
+                      n_lin: int = NH + 2, saved_act: bool = False):
     """Least HBM bytes all launches of a kernel move in one step of M layers
     (for the edge forward of an inference stack the last layer writes no edge
-    state).
+    state; with saved activations the edge forward also writes, and the edge
+    adjoint reads, h_0 .. h_{L-2} of every edge, and the adjoint gathers no P|Q)."""
+    E, N = G.n_edges, G.n_rows
+    h2 = 2 * hidden
+    if saved_act and kernel == "k_edge_fwd":
+        return (algorithmic_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
+                + M * E * (n_lin - 1) * h2)
+    if saved_act and kernel == "k_edge_bwd":   # e, de_out in, de_in, dz1 out, col, w, h_0..h_{L-2}; da in, dP out
+        return M * (E * (4 * edge_bytes * hidden + 8 + (n_lin - 1) * h2) + N * (2 * 4 * hidden + 4))
+    return _algorithmic_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
+
+
+def _algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool,
+                       n_lin: int):
+    """Recompute form of ``algorithmic_bytes``.
 
     Per edge: read e (s_e H), write e' (s_e H), col (4), 1/d (4); per row:
     the row's CSR pointer and node tensors (see the per-kernel notes). The
@@ -536,7 +550,7 @@ def main():
     edge_bytes = 2 if precision == "bf16" else 4
     roof = None
     abytes = algorithmic_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only,
-                               n_lin=wl.get("nh", NH) + 2)
+                               n_lin=wl.get("nh", NH) + 2, saved_act=any(a is not None for a in stack.act))
     if abytes is not None:   # bytes of one step over the kernel's device time in one step
         ach = abytes / (top_ms / args.steps * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",

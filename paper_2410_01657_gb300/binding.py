@@ -124,6 +124,13 @@ _SIGS = {
     "gnn_mp_backward": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                   C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P, _P,
                                   C.POINTER(gnn_mp_params), _P, C.c_size_t, _P]),
+    "gnn_mp_act_size": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config), C.POINTER(gnn_mp_params),
+                                  C.POINTER(C.c_size_t)]),
+    "gnn_mp_forward_act": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
+                                     C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "gnn_mp_backward_act": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
+                                      C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P, _P, _P,
+                                      C.POINTER(gnn_mp_params), _P, C.c_size_t, _P]),
     "gnn_mp_forward_static": (C.c_int, [C.POINTER(gnn_graph_dev), C.POINTER(gnn_mp_config),
                                         C.POINTER(gnn_mp_params), _P, _P, _P, _P, _P, _P]),
     "gnn_halo_exchange": (C.c_int, [C.POINTER(gnn_graph_dev), _P, C.c_int32, _P]),

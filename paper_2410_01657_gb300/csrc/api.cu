@@ -97,6 +97,63 @@ int gnn_mp_workspace_size(const gnn_graph_dev* G, const gnn_mp_config* cfg, cons
     return GNN_OK;
 }
 
+int gnn_mp_act_size(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W, size_t* bytes) {
+    int rc = check_graph(G, "gnn_mp_act_size");
+    if (rc) return rc;
+    if ((rc = check_cfg(cfg, W, "gnn_mp_act_size"))) return rc;
+    GNN_REQUIRE(bytes, GNN_EINVAL, "gnn_mp_act_size: NULL output");
+    *bytes = gnn::fused::mp_act_bytes(*G, *cfg, *W);
+    return GNN_OK;
+}
+
+static int check_act(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W, const void* act,
+                     const char* fn) {
+    if (gnn::fused::mp_act_bytes(*G, *cfg, *W) == 0 || G->n_edges == 0) return GNN_OK;
+    GNN_REQUIRE(act && ((uintptr_t)act & 15) == 0, GNN_EINVAL, "%s: act must be a 16-byte aligned device buffer",
+                fn);
+    return GNN_OK;
+}
+
+int gnn_mp_forward_act(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                       const float* x_in, const void* e_in, float* x_out, void* e_out, float* a_star_out, void* act,
+                       void* ws, size_t ws_bytes, void* stream) {
+    int rc = check_graph(G, "gnn_mp_forward_act");
+    if (rc) return rc;
+    if ((rc = check_cfg(cfg, W, "gnn_mp_forward_act"))) return rc;
+    if ((rc = check_act(G, cfg, W, act, "gnn_mp_forward_act"))) return rc;
+    if (cfg->precision == GNN_PREC_FP32 || gnn::fused::mp_act_bytes(*G, *cfg, *W) == 0)
+        return gnn_mp_forward(G, cfg, W, x_in, e_in, x_out, e_out, a_star_out, ws, ws_bytes, stream);
+    if (G->n_rows) GNN_REQUIRE(x_in && x_out, GNN_EINVAL, "gnn_mp_forward_act: NULL node buffer");
+    if (G->n_edges) GNN_REQUIRE(e_in, GNN_EINVAL, "gnn_mp_forward_act: NULL e_in");
+    GNN_REQUIRE(e_out || (cfg->flags & GNN_FLAG_NO_EDGE_OUT) || G->n_edges == 0, GNN_EINVAL,
+                "gnn_mp_forward_act: NULL e_out without GNN_FLAG_NO_EDGE_OUT");
+    GNN_REQUIRE(x_out != x_in || G->n_rows == 0, GNN_EINVAL, "gnn_mp_forward_act: x_out aliases x_in");
+    GNN_REQUIRE(ws || ws_bytes == 0, GNN_EINVAL, "gnn_mp_forward_act: NULL workspace");
+    return gnn::fused::mp_forward(*G, *cfg, *W, x_in, (const __nv_bfloat16*)e_in, x_out, (__nv_bfloat16*)e_out,
+                                  a_star_out, ws, ws_bytes, (cudaStream_t)stream, (__nv_bfloat16*)act);
+}
+
+int gnn_mp_backward_act(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W,
+                        const float* x_in, const void* e_in, const float* a_star, const void* act,
+                        const float* dx_out, const void* de_out, float* dx_in, void* de_in, const gnn_mp_params* dW,
+                        void* ws, size_t ws_bytes, void* stream) {
+    int rc = check_graph(G, "gnn_mp_backward_act");
+    if (rc) return rc;
+    if ((rc = check_cfg(cfg, W, "gnn_mp_backward_act"))) return rc;
+    if ((rc = check_act(G, cfg, W, act, "gnn_mp_backward_act"))) return rc;
+    if (cfg->precision == GNN_PREC_FP32 || gnn::fused::mp_act_bytes(*G, *cfg, *W) == 0)
+        return gnn_mp_backward(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes,
+                               stream);
+    GNN_REQUIRE(dW, GNN_EINVAL, "gnn_mp_backward_act: NULL gradient struct");
+    if ((rc = check_cfg(cfg, dW, "gnn_mp_backward_act(dW)"))) return rc;
+    if (G->n_rows) GNN_REQUIRE(x_in && dx_out && dx_in, GNN_EINVAL, "gnn_mp_backward_act: NULL node buffer");
+    if (G->n_edges) GNN_REQUIRE(e_in && de_in, GNN_EINVAL, "gnn_mp_backward_act: NULL edge buffer");
+    GNN_REQUIRE(ws || ws_bytes == 0, GNN_EINVAL, "gnn_mp_backward_act: NULL workspace");
+    return gnn::fused::mp_backward(*G, *cfg, *W, x_in, (const __nv_bfloat16*)e_in, a_star, dx_out,
+                                   (const __nv_bfloat16*)de_out, dx_in, (__nv_bfloat16*)de_in, *dW, ws, ws_bytes,
+                                   (cudaStream_t)stream, (const __nv_bfloat16*)act);
+}
+
 int gnn_mp_forward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_mp_params* W, const float* x_in,
                    const void* e_in, float* x_out, void* e_out, float* a_star_out, void* ws, size_t ws_bytes,
                    void* stream) {

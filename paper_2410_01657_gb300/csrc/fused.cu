@@ -163,6 +163,9 @@ struct EdgeFwdArgs {
     const __nv_bfloat16* de_out;  // upstream gradient of e' (NULL: zero)
     float* part;                  // per-CTA partials: gamma, beta, last bias gradients (3H)
     int64_t pstride;
+    // Training forward (k_edge_fwd_rt<H, true>): the hidden activations h_0 .. h_{L-2}
+    // of every edge, BF16 rows act[(k * n_edges + e) * H], for the backward.
+    __nv_bfloat16* act;
 };
 
 // SAVE: the backward's recomputation of the edge MLP (Eq. 5a) over a range of
@@ -783,7 +786,9 @@ __device__ __forceinline__ int slot_chunk(int k, int row) {
 
 
 
-template <int H>
+// ASAVE: also store each edge's hidden activations (the BF16 operands of the
+// next Linear) to A.act, so that the backward need not recompute them.
+template <int H, bool ASAVE = false>
 __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
     k_edge_fwd_rt(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
     using C = Cfg<H>;
@@ -974,6 +979,18 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                     tc_fence_after();
                     issue_mma(tm, sA1, sW + (k + 1) * C::WT, H, H);
                     mma_commit(mbar);
+                }
+                if constexpr (ASAVE) {
+                    // the saved copy of the group's finished BF16 tile leaves while the next MMA
+                    // reads it: whole rows per warp (coalesced); the next writes of sA1 come after
+                    // the group barrier of the next MMA wait
+                    constexpr int CPR = H / 8;   // 16-byte chunks per row
+                    __nv_bfloat16* dst = A.act + ((int64_t)k * A.n_edges + e0) * H;
+                    for (int i = gt; i < ne * CPR; i += GT) {
+                        const int r = i / CPR, j = i - r * CPR;
+                        *reinterpret_cast<uint4*>(dst + (int64_t)r * H + 8 * j) =
+                            *reinterpret_cast<const uint4*>(sA1 + tile_off(r, 8 * j, 128, C::S));
+                    }
                 }
             }
         }
@@ -1388,7 +1405,7 @@ int proj_h(const gnn_graph_dev& G, const gnn_mp_params& W, const float* x_in, __
 // Edge MLP + residual + weighted segmented sum (Eq. 5a-5b), then Eq. 5c-5d.
 template <int H>
 int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const __nv_bfloat16* e_in,
-           const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a, cudaStream_t s) {
+           const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a, __nv_bfloat16* act, cudaStream_t s) {
     using C = Cfg<H>;
     const int64_t NR = G.n_rows, E = G.n_edges;
     if (NR == 0) return GNN_OK;
@@ -1411,20 +1428,29 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.a = a;
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
+        A.act = act;
         int grid;
         int variant = cfg.edge_fwd_kernel;
-        if (variant == GNN_EDGE_FWD_AUTO) variant = H <= 64 ? GNN_EDGE_FWD_RT : GNN_EDGE_FWD_ONE;
+        if (variant == GNN_EDGE_FWD_AUTO || act) variant = H <= 64 ? GNN_EDGE_FWD_RT : GNN_EDGE_FWD_ONE;
         if constexpr (H <= 64) {
             if (variant == GNN_EDGE_FWD_RT) {
                 using R = RtCfg<H>;
                 GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
                             "gnn_mp_forward: tile_meta must be a 16-byte aligned device array");
                 const EdgeFwdRtSmem L = edge_fwd_rt_smem<H>(W.edge.n_lin);
-                rc = persistent_grid(k_edge_fwd_rt<H>, R::NT, L.total, R::NCOLS, (G.n_edge_tiles + R::NG - 1) / R::NG,
-                                     &grid, cfg.ctas_per_sm);
-                if (rc) return rc;
-                ProfScope _ps(s, "k_edge_fwd");
-                k_edge_fwd_rt<H><<<grid, R::NT, L.total, s>>>(tm, A);
+                const int64_t ntile = (G.n_edge_tiles + R::NG - 1) / R::NG;
+                if (act) {
+                    rc = persistent_grid(k_edge_fwd_rt<H, true>, R::NT, L.total, R::NCOLS, ntile, &grid,
+                                         cfg.ctas_per_sm);
+                    if (rc) return rc;
+                    ProfScope _ps(s, "k_edge_fwd");
+                    k_edge_fwd_rt<H, true><<<grid, R::NT, L.total, s>>>(tm, A);
+                } else {
+                    rc = persistent_grid(k_edge_fwd_rt<H>, R::NT, L.total, R::NCOLS, ntile, &grid, cfg.ctas_per_sm);
+                    if (rc) return rc;
+                    ProfScope _ps(s, "k_edge_fwd");
+                    k_edge_fwd_rt<H><<<grid, R::NT, L.total, s>>>(tm, A);
+                }
             } else if (variant == GNN_EDGE_FWD_WS) {
                 const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(W.edge.n_lin);
                 const uint32_t ncols = C::TCOLS * WS_NG < 32 ? 32 : C::TCOLS * WS_NG;
@@ -1512,8 +1538,15 @@ int proj_forward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const fl
 
 int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
                       const __nv_bfloat16* e_in, const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a,
-                      cudaStream_t s) {
-    GNN_H_DISPATCH(cfg.hidden, edge_h<HH>(G, cfg, W, e_in, pq, e_out, a, s));
+                      cudaStream_t s, __nv_bfloat16* act) {
+    GNN_H_DISPATCH(cfg.hidden, edge_h<HH>(G, cfg, W, e_in, pq, e_out, a, act, s));
+}
+
+size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
+    if (cfg.precision != GNN_PREC_BF16 || cfg.hidden > 64 || W.edge.n_lin < 2) return 0;
+    // the backward addresses activation row k * n_edges + e with a 32-bit TMA coordinate
+    if ((int64_t)(W.edge.n_lin - 1) * G.n_edges >= ((int64_t)1 << 31)) return 0;
+    return (size_t)(W.edge.n_lin - 1) * (size_t)G.n_edges * (size_t)cfg.hidden * 2;
 }
 
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
@@ -1577,7 +1610,7 @@ int mp_forward_static(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
 
 int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
-               size_t ws_bytes, cudaStream_t s) {
+               size_t ws_bytes, cudaStream_t s, __nv_bfloat16* act) {
     const int H = cfg.hidden;
     GNN_REQUIRE(H == 16 || H == 32 || H == 64 || H == 128, GNN_ESHAPE, "gnn_mp_forward: BF16 path needs H in {16,32,64,128}");
     GNN_REQUIRE(W.edge.n_lin >= 2 && W.node.n_lin >= 2, GNN_ESHAPE, "MLPs need >= 2 Linear layers");
@@ -1587,7 +1620,8 @@ int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
     float* a = a_star_out ? a_star_out : w.a;
     int rc;
     if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
-    if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s))) return rc;
+    if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s, mp_act_bytes(G, cfg, W) ? act : nullptr)))
+        return rc;
     return node_forward(G, cfg, W, a, x_in, x_out, s);
 }
 

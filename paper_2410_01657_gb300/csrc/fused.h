@@ -12,13 +12,17 @@ namespace fused {
 cudaError_t take_device_error(unsigned int* out);
 size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
+// Bytes of the saved edge-MLP activations (BF16 h_0 .. h_{L-2} of every edge)
+// that mp_forward writes and mp_backward reads when given `act`; 0 where the
+// backward recomputes them instead (H = 128 has its own layered adjoint).
+size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
-               size_t ws_bytes, cudaStream_t s);
+               size_t ws_bytes, cudaStream_t s, __nv_bfloat16* act = nullptr);
 int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                 const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
                 float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
-                cudaStream_t s);
+                cudaStream_t s, const __nv_bfloat16* act = nullptr);
 
 // gnn_mp_forward without a caller workspace (built-in scratch area).
 size_t static_scratch_bytes();
@@ -31,7 +35,7 @@ int proj_forward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const fl
                  cudaStream_t s);
 int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
                       const __nv_bfloat16* e_in, const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a,
-                      cudaStream_t s);
+                      cudaStream_t s, __nv_bfloat16* act = nullptr);
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
                  const float* x_in, float* x_out, cudaStream_t s);
 

@@ -63,8 +63,8 @@ __host__ __device__ inline EdgeBwdSmem edge_bwd_smem(int n_lin) {
     s.slot = align_up(s.ones + 128 * C::S, 1024);
     s.par = s.slot + 2 * C::TILE;
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma, ready, da, wgrad, P rows
-    s.tm = s.bar + 56;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // full[2], mma, ready, da, wgrad, P rows, h[GNN_MAX_LIN]
+    s.tm = s.bar + 8 * (7 + GNN_MAX_LIN);
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
     s.total = end + 1024;
@@ -384,14 +384,22 @@ struct EdgeBwdArgs {
     int64_t pstride;
     MlpDev mlp;
     float eps;
+    int64_t n_edges;            // SAVED: rows of one activation block of tmap_h
 };
 
 // LNT: the per-thread LayerNorm gradient sums live in TMEM columns after the
 // weight-gradient accumulators (read, add, write back once per tile) instead
 // of 2*CW registers.
-template <int H, bool LNT>
+// SAVED: the forward stored the hidden activations h_0 .. h_{L-2} of every edge
+// (rows k * n_edges + e of tmap_h); the tile's rows arrive by TMA into the
+// activation buffers and only the last Linear is recomputed (no P|Q gather, no
+// ELU chain). Buffer k is refilled with the next tile's rows as soon as the
+// adjoint step that reads it last has passed its hand-off, so the loads have
+// most of a tile's time to land; the dP staging moves to the P|Q slot area.
+template <int H, bool LNT, bool SAVED>
 __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_constant__ CUtensorMap tmap_e,
                                                             const __grid_constant__ CUtensorMap tmap_de,
+                                                            const __grid_constant__ CUtensorMap tmap_h,
                                                             EdgeBwdArgs A) {
     using C = CfgB<H>;
     extern __shared__ uint8_t smem_raw[];
@@ -404,7 +412,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     uint8_t* sG = sm + P.g;
     uint8_t* sHB = sm + P.hb;
     uint8_t* sOnes = sm + P.ones;
-    float* sStage = reinterpret_cast<float*>(sHB);               // dP staging at the last adjoint step
+    float* sStage = reinterpret_cast<float*>(SAVED ? sm + P.slot : sHB);   // dP staging at the last adjoint step
     float* sPar = reinterpret_cast<float*>(sm + P.par);
     float* sRed = reinterpret_cast<float*>(sm + P.red);
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.bar);   // full[2]: stage loaded
@@ -413,6 +421,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     uint64_t* da_full = full + 4;   // the tile's da rows have landed in sG
     uint64_t* bar_w = full + 5;     // weight-gradient MMAs of an adjoint step (complete behind the epilogue)
     uint64_t* p_full = full + 6;    // the tile's P rows have landed in sP
+    uint64_t* h_full = full + 7;    // SAVED: h_k of the tile has landed in sHB + k * TILE
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(edge_bwd_tcols<H>(L) + (LNT ? 2 * H : 0));
@@ -436,6 +445,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         mbar_init(da_full, 1);
         mbar_init(bar_w, 1);
         mbar_init(p_full, 1);
+        if (SAVED)
+            for (int k = 0; k < L - 1; ++k) mbar_init(h_full + k, 1);
         fence_mbar_init();
     }
     load_weight(sW, A.mlp.W[0], 3 * H, 2 * H, H, H, tid, C::NT);
@@ -533,14 +544,31 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         if (tid == 0) fetch_p(s);
     };
     auto first_edge = [&](int64_t t) { return ld_nc_s32(A.tile_meta + t * GNN_TILE_META_BYTES + 8); };
+    // SAVED: h_k rows of the tile starting at edge eh into buffer k (thread 0); per-thread
+    // parity bit k of h_full[k] (one phase per tile); thread 0's loads not yet waited for
+    const uint32_t hmask = SAVED ? ((1u << (L - 1)) - 1u) : 0u;
+    uint32_t ph_h = 0, h_pend = 0;
+    auto load_h = [&](int k, int32_t eh) {
+        mbar_arrive_expect_tx(h_full + k, C::TILE);
+        tma_load_2d(sHB + k * C::TILE, &tmap_h, 0, (int32_t)((int64_t)k * A.n_edges + eh), h_full + k);
+        h_pend |= 1u << k;
+    };
+    auto wait_h = [&](int k) {
+        ok = ok && mbar_wait(h_full + k, (ph_h >> k) & 1u);
+        h_pend &= ~(1u << k);
+    };
     int32_t e0_next = 0;   // thread 0: first edge of the CTA's next tile
+    int32_t e0_h = 0;      // thread 0: first edge of the tile after the current one (its h loads)
     if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) {
-        issue_stage(0, blockIdx.x, first_edge(blockIdx.x));
+        const int32_t e0_first = first_edge(blockIdx.x);
+        issue_stage(0, blockIdx.x, e0_first);
+        if (SAVED)
+            for (int k = 0; k < L - 1; ++k) load_h(k, e0_first);
         if ((int64_t)blockIdx.x + gridDim.x < A.n_tiles) e0_next = first_edge(blockIdx.x + gridDim.x);
     }
     if ((int64_t)blockIdx.x < A.n_tiles) {
         ok = mbar_wait(full, 0);
-        if (ok) gather(0);
+        if (ok && !SAVED) gather(0);
     }
     int j = 0;
 
@@ -565,19 +593,29 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             bulk_load(sG, A.da + (int64_t)r0 * H, (uint32_t)(r1 - r0) * H * 4, da_full);
         }
         if (tid == 0 && ok) {
+            e0_h = e0_next;
+            if (SAVED) wait_h(L - 2);
             tc_fence_after();
-            issue_mma(tWork, sE0, sW, H, H);
-            mma_commit(bar);
+            if (ok) {
+                if (SAVED) issue_mma(tWork, sHB + (L - 2) * C::TILE, sW + (L - 1) * C::WT, H, H);
+                else issue_mma(tWork, sE0, sW, H, H);
+                mma_commit(bar);
+            }
             // the other stage was released at the end of the previous tile: prefetch the next tile
             if (t + gridDim.x < A.n_tiles) {
                 issue_stage(st ^ 1, t + gridDim.x, e0_next);
                 if (t + 2 * (int64_t)gridDim.x < A.n_tiles) e0_next = first_edge(t + 2 * (int64_t)gridDim.x);
             }
         }
-        cp_async_wait_all();   // this thread's P|Q slot for the tile
-        // ---- recompute the chain
+        // ---- recompute the chain (SAVED: only the last Linear, from the saved h_{L-2})
         float v[CW];
-        for (int k = 0; k < L; ++k) {
+        if constexpr (SAVED) {
+            mma_wait();
+            ld_acc<CW>(tWork, q, c0, v);
+            add_bias2<CW>(v, sPar + (L - 1) * H + c0);
+        }
+        if constexpr (!SAVED) cp_async_wait_all();   // this thread's P|Q slot for the tile
+        for (int k = 0; k < (SAVED ? 0 : L); ++k) {
             mma_wait();
             ld_acc<CW>(tWork, q, c0, v);
             if (k == 0) {
@@ -682,6 +720,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 ok = ok && mbar_wait(bar_w, ph_w);
                 ph_w ^= 1;
             }
+            if (SAVED && k > 0) wait_h(k - 1);   // this step's wgrad operand and ELU derivative input
             st_row_tile<CW>(sG, row, c0, S, dz);
             handoff([&] {
                 issue_dgrad(tWork, sG, S, sW + k * C::WT, S, H, (uint32_t)H * S, H, H);
@@ -689,7 +728,10 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 uint8_t* hk = (k == 0) ? sE0 : sHB + (k - 1) * C::TILE;
                 issue_wgrad(tDW(k), sG, S, 128u * S, hk, S, ones_addr - smem_u32(hk), H + 16, !first);
             }, bar_w);
-            if (k == L - 1 && t + gridDim.x < A.n_tiles) {
+            // SAVED: every thread has passed its last read of h_k (step k + 1) and its wgrad has
+            // completed (bar_w, waited at the top of this step): the next tile's h_k goes there
+            if (SAVED && tid == 0 && ok && k <= L - 2 && t + gridDim.x < A.n_tiles) load_h(k, e0_h);
+            if (!SAVED && k == L - 1 && t + gridDim.x < A.n_tiles) {
                 // the slot was consumed by the first recompute step and the next tile's stage
                 // (issued at this tile's start) has landed by now: request its P|Q rows
                 if (mbar_wait(full + (st ^ 1), (uint32_t)((j + 1) >> 1) & 1u)) gather(st ^ 1);
@@ -702,7 +744,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 }
                 constexpr int NC = H / 4;
                 float4* sS4 = reinterpret_cast<float4*>(sStage);
-                __syncthreads();   // every warp is past its last read of hb, which the staging overwrites
+                if (!SAVED) __syncthreads();   // every warp is past its last read of hb, which the staging overwrites
 #pragma unroll
                 for (int i = 0; i < CW / 4; ++i)
                     sS4[row * NC + stage_chunk<NC>(c0 / 4 + i, row)] =
@@ -742,11 +784,15 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         first = false;
         ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads this tile's e stage and sG
         ph_w ^= 1;
+        ph_h ^= hmask;
         fence_proxy_async();
         if (__syncthreads_or(!ok)) break;   // stage release; the block leaves together after a timeout
         tc_fence_after();
     }
     if (p_pending) mbar_wait(p_full, ph_p);
+    if (SAVED && tid == 0)   // loads issued before a timeout ended the tile loop
+        for (int k = 0; k < L - 1; ++k)
+            if ((h_pend >> k) & 1u) mbar_wait(h_full + k, (ph_h >> k) & 1u);
     cp_async_wait_all();
     tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
@@ -1099,7 +1145,7 @@ template <int H>
 int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
                float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
-               cudaStream_t s) {
+               cudaStream_t s, const __nv_bfloat16* act) {
     using C = CfgB<H>;
     const int Le = W.edge.n_lin, Ln = W.node.n_lin;
     GNN_REQUIRE(edge_bwd_tcols<H>(Le) <= 512 && node_bwd_tcols<H>(Ln) <= 512, GNN_EUNSUPPORTED,
@@ -1110,8 +1156,10 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
     const int64_t NR = G.n_rows, E = G.n_edges;
     if (NR == 0) return GNN_OK;
     int rc;
-    // 0. recompute P|Q (and a* when it was not saved)
-    if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
+    // 0. recompute P|Q (and a* when it was not saved); saved activations need no P|Q
+    if (!act || !a_star) {
+        if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
+    }
     if (!a_star) {
         if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, nullptr, w.a, s))) return rc;
     }
@@ -1161,9 +1209,11 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
     }
     // 3. edge MLP adjoint
     if (E > 0) {
-        CUtensorMap tm_e, tm_de;
+        CUtensorMap tm_e, tm_de, tm_h;
         if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
         if ((rc = make_row_tmap(&tm_de, de_out ? (const void*)de_out : (const void*)e_in, E, H))) return rc;
+        tm_h = tm_e;
+        if (act && (rc = make_row_tmap(&tm_h, act, (int64_t)(Le - 1) * E, H))) return rc;
         EdgeBwdArgs A;
         GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
                     "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
@@ -1180,25 +1230,25 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.pstride = edge_pstride(H, Le);
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
+        A.n_edges = E;
         const EdgeBwdSmem P = edge_bwd_smem<H>(Le);
-        int grid;
+        int grid = 0;
         const bool lnt = edge_bwd_ln_in_tmem<H>(Le);
-        if (lnt)
-            rc = persistent_grid(k_edge_bwd<H, true>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le) + 2 * H),
-                                 G.n_edge_tiles, &grid);
-        else
-            rc = persistent_grid(k_edge_bwd<H, false>, C::NT, P.total, pow2_cols(edge_bwd_tcols<H>(Le)),
-                                 G.n_edge_tiles, &grid);
+        auto run = [&](auto kern, uint32_t cols) -> int {
+            int r = persistent_grid(kern, C::NT, P.total, cols, G.n_edge_tiles, &grid);
+            if (r) return r;
+            grid = std::min(grid, nsm);
+            {
+                ProfScope _ps(s, "k_edge_bwd");
+                kern<<<grid, C::NT, P.total, s>>>(tm_e, tm_de, tm_h, A);
+            }
+            GNN_LAUNCH_CHECK("k_edge_bwd");
+            return GNN_OK;
+        };
+        const uint32_t cols_l = pow2_cols(edge_bwd_tcols<H>(Le) + 2 * H), cols = pow2_cols(edge_bwd_tcols<H>(Le));
+        if (act) rc = lnt ? run(k_edge_bwd<H, true, true>, cols_l) : run(k_edge_bwd<H, false, true>, cols);
+        else rc = lnt ? run(k_edge_bwd<H, true, false>, cols_l) : run(k_edge_bwd<H, false, false>, cols);
         if (rc) return rc;
-        grid = std::min(grid, nsm);
-        {
-            ProfScope _ps(s, "k_edge_bwd");
-            if (lnt)
-                k_edge_bwd<H, true><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
-            else
-                k_edge_bwd<H, false><<<grid, C::NT, P.total, s>>>(tm_e, tm_de, A);
-        }
-        GNN_LAUNCH_CHECK("k_edge_bwd");
         RedSeg seg[MAX_SEGS];
         int n = 0;
         int64_t off = 0;
@@ -1240,11 +1290,12 @@ int proj_backward(const gnn_graph_dev& G, int H, const gnn_mp_params& W, const f
 int mp_backward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                 const __nv_bfloat16* e_in, const float* a_star, const float* dx_out, const __nv_bfloat16* de_out,
                 float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
-                cudaStream_t s) {
+                cudaStream_t s, const __nv_bfloat16* act) {
+    if (!mp_act_bytes(G, cfg, W)) act = nullptr;
     switch (cfg.hidden) {
-        case 16: return backward_h<16>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
-        case 32: return backward_h<32>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
-        case 64: return backward_h<64>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
+        case 16: return backward_h<16>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s, act);
+        case 32: return backward_h<32>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s, act);
+        case 64: return backward_h<64>(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s, act);
         case 128: return backward_h128(G, cfg, W, x_in, e_in, a_star, dx_out, de_out, dx_in, de_in, dW, ws, ws_bytes, s);
         default:
             return set_error(GNN_EUNSUPPORTED, "gnn_mp_backward: the BF16 backward covers H in {16, 32, 64, 128}");

@@ -75,18 +75,42 @@ def mp_workspace_sizes(G: DeviceGraph, cfg, W) -> tuple:
     return int(f.value), int(b.value)
 
 
-def gnn_mp_forward(G: DeviceGraph, cfg, W, x, e, x_out, e_out, a_star=None, ws=None):
-    """Direct call of gnn_mp_forward on preallocated tensors (no autograd)."""
+def mp_act_bytes(G: DeviceGraph, cfg, W) -> int:
+    """Bytes of the saved edge activations of gnn_mp_forward_act (0: the backward recomputes)."""
+    n = C.c_size_t()
+    B.call("gnn_mp_act_size", C.byref(G.struct), C.byref(cfg), C.byref(W), C.byref(n))
+    return int(n.value)
+
+
+def act_buffer(G: DeviceGraph, cfg, W, device):
+    """A buffer for the saved edge activations of one layer, or None where none are kept."""
+    n = mp_act_bytes(G, cfg, W)
+    return torch.empty(n // 2, dtype=torch.bfloat16, device=device) if n else None
+
+
+def gnn_mp_forward(G: DeviceGraph, cfg, W, x, e, x_out, e_out, a_star=None, ws=None, act=None):
+    """Direct call of gnn_mp_forward (gnn_mp_forward_act when ``act`` is given,
+    which also stores the edge activations) on preallocated tensors (no autograd)."""
     if ws is None:
         ws = workspace(mp_workspace_sizes(G, cfg, W)[0], x.device)
+    if act is not None:
+        B.call("gnn_mp_forward_act", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(x_out),
+               B.ptr(e_out), B.ptr(a_star), B.ptr(act), B.ptr(ws), ws.numel(), _stream())
+        return
     B.call("gnn_mp_forward", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(x_out),
            B.ptr(e_out), B.ptr(a_star), B.ptr(ws), ws.numel(), _stream())
 
 
-def gnn_mp_backward(G: DeviceGraph, cfg, W, x, e, a_star, dx_out, de_out, dx_in, de_in, dW, ws=None):
-    """Direct call of gnn_mp_backward on preallocated tensors; dW accumulates."""
+def gnn_mp_backward(G: DeviceGraph, cfg, W, x, e, a_star, dx_out, de_out, dx_in, de_in, dW, ws=None, act=None):
+    """Direct call of gnn_mp_backward (gnn_mp_backward_act with the forward's
+    saved ``act``) on preallocated tensors; dW accumulates."""
     if ws is None:
         ws = workspace(mp_workspace_sizes(G, cfg, W)[1], x.device)
+    if act is not None:
+        B.call("gnn_mp_backward_act", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e),
+               B.ptr(a_star), B.ptr(act), B.ptr(dx_out), B.ptr(de_out), B.ptr(dx_in), B.ptr(de_in), C.byref(dW),
+               B.ptr(ws), ws.numel(), _stream())
+        return
     B.call("gnn_mp_backward", C.byref(G.struct), C.byref(cfg), C.byref(W), B.ptr(x), B.ptr(e), B.ptr(a_star),
            B.ptr(dx_out), B.ptr(de_out), B.ptr(dx_in), B.ptr(de_in), C.byref(dW), B.ptr(ws), ws.numel(),
            _stream())
@@ -97,7 +121,9 @@ def gnn_halo_exchange(G: DeviceGraph, rows: torch.Tensor) -> None:
 
 
 class ConsistentMPFunction(torch.autograd.Function):
-    """One consistent NMP layer, Eq. 5a-5e, with the hand-written adjoint (Eq. 3)."""
+    """One consistent NMP layer, Eq. 5a-5e, with the hand-written adjoint (Eq. 3).
+    The edge activations are kept from the forward to the backward where the
+    library supports it (gnn_mp_forward_act / gnn_mp_backward_act)."""
 
     @staticmethod
     def forward(ctx, x, e, G, cfg_args, edge_dims, node_dims, *params):
@@ -109,7 +135,9 @@ class ConsistentMPFunction(torch.autograd.Function):
         x_out = torch.empty_like(x)
         e_out = torch.empty_like(e)
         a_star = torch.empty_like(x)
-        gnn_mp_forward(G, cfg, W, x, e, x_out, e_out, a_star, workspace(fwd, x.device))
+        act = act_buffer(G, cfg, W, x.device)
+        gnn_mp_forward(G, cfg, W, x, e, x_out, e_out, a_star, workspace(fwd, x.device), act)
+        ctx.act = act
         ctx.G, ctx.cfg_args, ctx.dims = G, cfg_args, (edge_dims, node_dims)
         ctx.save_for_backward(x, e, a_star, *params)
         return x_out, e_out
@@ -127,7 +155,8 @@ class ConsistentMPFunction(torch.autograd.Function):
         de = torch.empty_like(e)
         dx_out = torch.zeros_like(x) if dx_out is None else dx_out.contiguous()
         de_out = None if de_out is None else de_out.to(e.dtype).contiguous()
-        gnn_mp_backward(G, cfg, W, x, e, a_star, dx_out, de_out, dx, de, dW, workspace(bwd, x.device))
+        gnn_mp_backward(G, cfg, W, x, e, a_star, dx_out, de_out, dx, de, dW, workspace(bwd, x.device), ctx.act)
+        ctx.act = None
         return (dx, de, None, None, None, None, *dparams)
 
 
@@ -247,12 +276,16 @@ class LayerStack:
     Inference keeps the inputs and two edge-state and two node-state buffers
     (ping-pong) and skips the last layer's edge-state write (GNN_FLAG_NO_EDGE_OUT): only the
     aggregates reach the node update, so no per-edge output of the last layer
-    touches HBM. Training keeps every layer's input states and a* (the
-    backward recomputes from them) and two node- and two edge-gradient buffers
-    (ping-pong: layer l writes dx[l % 2], de[l % 2]; dx[0] ends as dL/dx0)."""
+    touches HBM. Training keeps every layer's input states and a*, the edge
+    MLP's activations where the library supports it (``save_act``; the
+    backward then recomputes only the last edge Linear, else the whole chain)
+    and two node- and two edge-gradient buffers (ping-pong: layer l writes
+    dx[l % 2], de[l % 2]; dx[0] ends as dL/dx0). With saved activations the
+    forward always uses the record-tiled edge kernel (the autotuner's choice of
+    forward kernel then only affects ``forward`` of an inference stack)."""
 
     def __init__(self, G: DeviceGraph, layers, hidden: int, precision: str, x0, e0, halo: bool = True,
-                 ln_eps: float = 1e-5, inference: bool = False):
+                 ln_eps: float = 1e-5, inference: bool = False, save_act: bool = True):
         self.G = G
         self.M = len(layers)
         self.hidden = hidden
@@ -284,6 +317,9 @@ class LayerStack:
             self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
             self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(2)]
             self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(min(2, self.M))]
+        self.act = [None] * self.M
+        if not inference and save_act:
+            self.act = [act_buffer(G, self.cfg, self.W[l], dev) for l in range(self.M)]
         f, b = mp_workspace_sizes(G, self.cfg, self.W[0])
         self.ws = workspace(f if inference else max(f, b), dev)
         self.graph = None
@@ -311,7 +347,7 @@ class LayerStack:
         for l in range(self.M):
             xi, ei, xo, eo, a = self._io(l)
             cfg = self.cfg_last if l == self.M - 1 else self.cfg
-            gnn_mp_forward(self.G, cfg, self.W[l], xi, ei, xo, eo, a, self.ws)
+            gnn_mp_forward(self.G, cfg, self.W[l], xi, ei, xo, eo, a, self.ws, self.act[l])
 
     def backward(self, dx_top):
         """dx_top: dL/dx of the last layer's output; dL/de of it is zero."""
@@ -320,7 +356,7 @@ class LayerStack:
         for l in range(self.M - 1, -1, -1):
             dx_in, de_in = self.dx[l % 2], self.de[l % 2]
             gnn_mp_backward(self.G, self.cfg, self.W[l], self.x[l], self.e[l], self.a[l], dx_out, de_out,
-                            dx_in, de_in, self.dW[l], self.ws)
+                            dx_in, de_in, self.dW[l], self.ws, self.act[l])
             dx_out, de_out = dx_in, de_in
 
     def step(self, dx_top=None):

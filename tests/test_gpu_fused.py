@@ -283,3 +283,53 @@ def test_fused_network_training_step_vs_oracle(H):
     gg = dict(flat_grads(net.grads_numpy()))
     for name, ref in flat_grads(g):
         assert rel_l2(gg[name], ref) < TOL_GRAD, (name, rel_l2(gg[name], ref))
+
+
+@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 5), (64, 2), (64, 0)])
+def test_saved_edge_activations(H, n_hidden):
+    # gnn_mp_forward_act stores h_0 .. h_{L-2} of every edge (the oracle's hidden activations
+    # in BF16) and leaves the layer outputs bitwise unchanged; gnn_mp_backward_act, which
+    # recomputes only the last edge Linear from them, agrees with the recomputing adjoint
+    # and with the oracle, on a ragged multi-tile graph
+    brick, subs, part, G, params, x, e = _layer_case((6, 5, 4), 3, 5, H, n_hidden, seed=23)
+    lp = params["layers"][0]
+    x1, e1, cache = om.layer_forward(lp, subs, split_rows(x, subs), split_edges(e, subs))
+    rng = np.random.default_rng(24)
+    dx1 = rng.standard_normal(x.shape)
+    de1 = _bf16_round(rng.standard_normal(e.shape) * 0.5)
+    dx0, de0, g = om.layer_backward(lp, subs, cache, split_rows(dx1, subs), split_edges(de1, subs))
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layer = net.layers[0]
+    tens = layer.edge.tensors() + layer.node.tensors()
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+    cfg = gnn.mp_config(H, "bf16")
+    cfg.edge_fwd_kernel = B.GNN_EDGE_FWD_RT
+    xt, et = _to(x), _to(e, torch.bfloat16)
+    L = n_hidden + 2
+    act = gnn.act_buffer(G, cfg, W, DEV)
+    assert act is not None and act.numel() == (L - 1) * part.n_edges * H
+    outs = {}
+    for name, buf in (("recompute", None), ("saved", act)):
+        xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
+        gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a, act=buf)
+        dparams = [torch.zeros_like(p) for p in tens]
+        dxi, dei = torch.empty_like(xt), torch.empty_like(et)
+        gnn.gnn_mp_backward(G, cfg, W, xt, et, a, _to(dx1), _to(de1, torch.bfloat16), dxi, dei,
+                            gnn.mp_params(layer.edge.dims, layer.node.dims, dparams), act=buf)
+        B.call("gnn_check", None)
+        outs[name] = [t.float().cpu().numpy() for t in [xo, eo, a, dxi, dei] + dparams]
+    rec, sav = outs["recompute"], outs["saved"]
+    for u, v in zip(rec[:3], sav[:3]):
+        assert np.array_equal(u, v)
+    for u, v in zip(rec[3:], sav[3:]):
+        assert rel_l2(v, u) < 1e-6
+    A = act.float().cpu().numpy().reshape(L - 1, part.n_edges, H)
+    for k in range(L - 1):
+        assert rel_l2(A[k], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
+    assert rel_l2(sav[3], np.concatenate(dx0)) < TOL_GRAD
+    assert rel_l2(sav[4], np.concatenate(de0)) < TOL_GRAD
+    gref = []
+    for m in ("edge", "node"):
+        gref += list(g[m]["W"]) + list(g[m]["b"]) + [g[m]["gamma"], g[m]["beta"]]
+    for got, ref in zip(sav[5:], gref):
+        assert rel_l2(got, ref) < TOL_GRAD

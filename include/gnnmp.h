@@ -342,20 +342,23 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
                     const float* dx_out, const void* de_out, float* dx_in, void* de_in,
                     const gnn_mp_params* dW, void* ws, size_t ws_bytes, void* stream);
 
-/* Training with saved edge activations. The backward above recomputes each
- * edge's MLP chain, which makes its per-tile work a serial run of 2L tensor-core
- * steps; keeping the activations instead -- as the paper's autograd training
- * does -- leaves one recomputed Linear. gnn_mp_forward_act is gnn_mp_forward
- * that also writes, for every edge, the edge MLP's hidden activations h_0 ..
- * h_{L-2} (the ELU outputs, rounded to the BF16 operands of Linears 2..L) to
- * act; gnn_mp_backward_act, given that act, reads them by TMA, recomputes only
- * the last Linear and needs no P|Q rows. Same results as gnn_mp_forward with
- * GNN_EDGE_FWD_RT (the edge forward it always uses) and gnn_mp_backward.
- * act: device BF16 [(L_e - 1) x n_edges x H], row k * n_edges + e, of
- * gnn_mp_act_size bytes (16-byte aligned), caller-owned and unchanged from the
- * forward to the backward (L_e = W->edge.n_lin). gnn_mp_act_size reports 0
+/* Training with saved activations. The backward above recomputes each MLP
+ * chain, which makes its per-tile work a serial run of 2L tensor-core steps;
+ * keeping the activations instead -- as the paper's autograd training does --
+ * leaves one recomputed Linear per MLP. gnn_mp_forward_act is gnn_mp_forward
+ * that also writes the hidden activations h_0 .. h_{L-2} (the ELU outputs,
+ * rounded to the BF16 operands of Linears 2..L) of every edge and every node
+ * row to act; gnn_mp_backward_act, given that act, reads them by TMA,
+ * recomputes only the last Linear of each MLP and needs no P|Q rows. Same
+ * results as gnn_mp_forward with GNN_EDGE_FWD_RT (the edge forward it always
+ * uses) and gnn_mp_backward. act: device BF16, 16-byte aligned, of
+ * gnn_mp_act_size bytes, caller-owned and unchanged from the forward to the
+ * backward: edge block k (k < L_e - 1, L_e = W->edge.n_lin) holds rows
+ * k * n_edges + e, then node block k (k < L_n - 1) rows k * R + r with
+ * R = ceil(n_rows / 128) * 128 (the rows past n_rows are padding). gnn_mp_act_size reports 0
  * where the backward recomputes instead (the FP32 path, BF16 at H = 128,
- * whose adjoint is layered, and graphs with (L_e - 1) * n_edges >= 2^31);
+ * whose adjoint is layered, and graphs with (L_e - 1) * n_edges or
+ * (L_n - 1) * R >= 2^31);
  * there act may be NULL and the two calls are
  * gnn_mp_forward / gnn_mp_backward. Errors: those of gnn_mp_forward /
  * gnn_mp_backward; GNN_EINVAL for a NULL or misaligned act that is needed. */

@@ -1105,16 +1105,21 @@ struct NodeFwdArgs {
     const float* dx_out;          // upstream gradient of x'
     float* part;                  // per-CTA partials: gamma, beta, last bias gradients (3H)
     int64_t pstride;
+    int64_t act_rows;             // ASAVE: rows of one activation block of tmap_h (tiles * 128)
 };
 
 // SAVE: the backward's recomputation of the node MLP (Eq. 5e): the BF16 input
 // rows and hidden activations go to scratch and the LayerNorm epilogue is
 // replaced by its adjoint, whose input is the gradient of x' (the residual
 // branch passes it through unchanged).
-template <int H, bool PF, bool SAVE = false>
+// ASAVE (training forward): each finished BF16 hidden tile also goes to block k
+// of tmap_h (row k * act_rows + t * 128 + i) by a TMA store, for the backward.
+template <int H, bool PF, bool SAVE = false, bool ASAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__ CUtensorMap tmap_a,
-                                                        const __grid_constant__ CUtensorMap tmap_x, NodeFwdArgs A) {
+                                                        const __grid_constant__ CUtensorMap tmap_x,
+                                                        const __grid_constant__ CUtensorMap tmap_h, NodeFwdArgs A) {
     static_assert(!(PF && SAVE), "the recomputation reads its inputs directly");
+    static_assert(!(ASAVE && (SAVE || NodeSplit<H>::value)), "saved activations: the H <= 64 layer forward");
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -1265,6 +1270,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         }
         float v[C::CW];
         for (int k = 0; k < n_lin && ok; ++k) {
+            if (ASAVE && tid == 0) bulk_wait_read_all();   // sA1 may be rewritten after the barrier
             ok = block_wait(bar_mma, ph, tid);
             ph ^= 1;
             tc_fence_after();
@@ -1291,6 +1297,10 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                     tc_fence_after();
                     issue_mma(tmem, sA1, sW + k * C::WT, H, H);
                     mma_commit(bar_mma);
+                    if constexpr (ASAVE) {
+                        tma_store_2d(&tmap_h, 0, (int32_t)(k * A.act_rows + t * 128), sA1);
+                        bulk_commit();
+                    }
                 }
             }
         }
@@ -1347,6 +1357,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         colsum_store<H, NCH>(accB, sRed, q, lane, c0, tid, C::NT, part + H);
         colsum_store<H, NCH>(accZ, sRed, q, lane, c0, tid, C::NT, part + 2 * H);
     }
+    if (ASAVE && tid == 0) bulk_wait_all();   // the saved tiles are written before the CTA exits
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1480,7 +1491,7 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
 
 template <int H>
 int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
-           const float* x_in, float* x_out, cudaStream_t s) {
+           const float* x_in, float* x_out, __nv_bfloat16* act, cudaStream_t s) {
     using C = Cfg<H>;
     const int64_t NR = G.n_rows;
     if (NR == 0) return GNN_OK;
@@ -1500,20 +1511,24 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
     const NodeFwdSmem Lp = node_fwd_smem<H, true>(W.node.n_lin);
     const bool pf = H <= 64 && Lp.total <= 227 * 1024;
     const NodeFwdSmem L = pf ? Lp : node_fwd_smem<H, false>(W.node.n_lin);
-    if (pf)
-        rc = persistent_grid(k_node_fwd<H, true>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
-    else
-        rc = persistent_grid(k_node_fwd<H, false>, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
-    if (rc) return rc;
-    {
-        ProfScope _ps(s, "k_node_fwd");
-        if (pf)
-            k_node_fwd<H, true><<<grid, C::NT, L.total, s>>>(tma, tmx, A);
-        else
-            k_node_fwd<H, false><<<grid, C::NT, L.total, s>>>(tma, tmx, A);
+    // saved activations: block k of act holds h_k of tile t at rows k * act_rows + t * 128
+    A.act_rows = (NR + 127) / 128 * 128;
+    CUtensorMap tmh = tma;
+    if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(W.node.n_lin - 1) * A.act_rows, H))) return rc;
+    auto run = [&](auto kern) -> int {
+        int r = persistent_grid(kern, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
+        if (r) return r;
+        {
+            ProfScope _ps(s, "k_node_fwd");
+            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, A);
+        }
+        GNN_LAUNCH_CHECK("k_node_fwd");
+        return GNN_OK;
+    };
+    if constexpr (H <= 64) {
+        if (act) return pf ? run(k_node_fwd<H, true, false, true>) : run(k_node_fwd<H, false, false, true>);
     }
-    GNN_LAUNCH_CHECK("k_node_fwd");
-    return GNN_OK;
+    return pf ? run(k_node_fwd<H, true>) : run(k_node_fwd<H, false>);
 }
 
 }  // namespace
@@ -1542,16 +1557,23 @@ int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
     GNN_H_DISPATCH(cfg.hidden, edge_h<HH>(G, cfg, W, e_in, pq, e_out, a, act, s));
 }
 
+size_t mp_act_elems_edge(const gnn_graph_dev& G, const gnn_mp_params& W, int H) {
+    return (size_t)(W.edge.n_lin - 1) * (size_t)G.n_edges * (size_t)H;
+}
+
 size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
-    if (cfg.precision != GNN_PREC_BF16 || cfg.hidden > 64 || W.edge.n_lin < 2) return 0;
-    // the backward addresses activation row k * n_edges + e with a 32-bit TMA coordinate
-    if ((int64_t)(W.edge.n_lin - 1) * G.n_edges >= ((int64_t)1 << 31)) return 0;
-    return (size_t)(W.edge.n_lin - 1) * (size_t)G.n_edges * (size_t)cfg.hidden * 2;
+    if (cfg.precision != GNN_PREC_BF16 || cfg.hidden > 64 || W.edge.n_lin < 2 || W.node.n_lin < 2) return 0;
+    // activation rows are 32-bit TMA coordinates: edge row k * n_edges + e, node row k * rows + r
+    const int64_t rows = (G.n_rows + 127) / 128 * 128;
+    if ((int64_t)(W.edge.n_lin - 1) * G.n_edges >= ((int64_t)1 << 31) ||
+        (int64_t)(W.node.n_lin - 1) * rows >= ((int64_t)1 << 31))
+        return 0;
+    return (mp_act_elems_edge(G, W, cfg.hidden) + (size_t)(W.node.n_lin - 1) * (size_t)rows * cfg.hidden) * 2;
 }
 
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
-                 const float* x_in, float* x_out, cudaStream_t s) {
-    GNN_H_DISPATCH(cfg.hidden, node_h<HH>(G, cfg, W, a, x_in, x_out, s));
+                 const float* x_in, float* x_out, cudaStream_t s, __nv_bfloat16* act) {
+    GNN_H_DISPATCH(cfg.hidden, node_h<HH>(G, cfg, W, a, x_in, x_out, act, s));
 }
 
 // ------------------------------------------------------------------ forward with a built-in scratch area
@@ -1620,9 +1642,9 @@ int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
     float* a = a_star_out ? a_star_out : w.a;
     int rc;
     if ((rc = proj_forward(G, H, W, x_in, w.pq, s))) return rc;
-    if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s, mp_act_bytes(G, cfg, W) ? act : nullptr)))
-        return rc;
-    return node_forward(G, cfg, W, a, x_in, x_out, s);
+    if (!mp_act_bytes(G, cfg, W)) act = nullptr;
+    if ((rc = aggregate_forward(G, cfg, W, e_in, w.pq, eo, a, s, act))) return rc;
+    return node_forward(G, cfg, W, a, x_in, x_out, s, act ? act + mp_act_elems_edge(G, W, H) : nullptr);
 }
 
 // ------------------------------------------------------------------ backward recomputation (H = 128)
@@ -1698,7 +1720,7 @@ int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
         return rc;
     {
         ProfScope _ps(s, "k_node_fwd_save");
-        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, A);
+        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tma, A);
     }
     GNN_LAUNCH_CHECK("k_node_fwd_save");
     return GNN_OK;

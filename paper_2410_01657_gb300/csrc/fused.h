@@ -12,10 +12,14 @@ namespace fused {
 cudaError_t take_device_error(unsigned int* out);
 size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
-// Bytes of the saved edge-MLP activations (BF16 h_0 .. h_{L-2} of every edge)
-// that mp_forward writes and mp_backward reads when given `act`; 0 where the
-// backward recomputes them instead (H = 128 has its own layered adjoint).
+// Bytes of the saved MLP activations (BF16 h_0 .. h_{L-2} of every edge, then
+// of every node row) that mp_forward writes and mp_backward reads when given
+// `act`; 0 where the backward recomputes them instead (H = 128 has its own
+// layered adjoint).
 size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
+// Elements of the edge part of those activations; the node MLP's h_0 .. h_{L-2}
+// follow, block k of ceil(n_rows / 128) * 128 rows each.
+size_t mp_act_elems_edge(const gnn_graph_dev& G, const gnn_mp_params& W, int H);
 int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,
                size_t ws_bytes, cudaStream_t s, __nv_bfloat16* act = nullptr);
@@ -37,7 +41,7 @@ int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
                       const __nv_bfloat16* e_in, const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a,
                       cudaStream_t s, __nv_bfloat16* act = nullptr);
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
-                 const float* x_in, float* x_out, cudaStream_t s);
+                 const float* x_in, float* x_out, cudaStream_t s, __nv_bfloat16* act = nullptr);
 
 // Backward recomputation of the edge or node MLP at H = 128 over the tiles
 // [t0, t1): saves the hidden activations (and, for nodes, the BF16 [a*, x]

@@ -88,8 +88,8 @@ __host__ __device__ inline NodeBwdSmem node_bwd_smem(int n_lin) {
     s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
     s.par = align_up(s.ones + 128 * C::S, 16);
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // mma, wgrad, ready
-    s.tm = s.bar + 24;
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // mma, wgrad, ready, h[GNN_MAX_LIN]
+    s.tm = s.bar + 8 * (3 + GNN_MAX_LIN);
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;
     s.total = end + 1024;
@@ -145,10 +145,16 @@ struct NodeBwdArgs {
     int64_t n_rows;
     MlpDev mlp;
     float eps;
+    int64_t act_rows;   // SAVED: rows of one activation block of tmap_h (tiles * 128)
 };
 
-template <int H>
-__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
+// SAVED: the forward stored the node MLP's hidden activations (block k, row
+// k * act_rows + r, of tmap_h); they arrive by TMA into the activation buffers,
+// each refilled with the next tile's rows once its last reader has passed (as
+// in k_edge_bwd), and only the last Linear is recomputed.
+template <int H, bool SAVED>
+__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_constant__ CUtensorMap tmap_h,
+                                                            NodeBwdArgs A) {
     using C = CfgB<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -165,6 +171,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.bar);   // MMA completion
     uint64_t* bar_w = bar + 1;                                  // weight-gradient MMAs of an adjoint step
     uint64_t* ready = bar + 2;                                  // one arrival per warp before an MMA
+    uint64_t* h_full = bar + 3;                                 // SAVED: h_k of the tile has landed
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, S2 = C::S2, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(node_bwd_tcols<H>(L));
@@ -180,6 +187,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
         mbar_init(bar, 1);
         mbar_init(bar_w, 1);
         mbar_init(ready, C::NT / 32);
+        if (SAVED)
+            for (int k = 0; k < L - 1; ++k) mbar_init(h_full + k, 1);
         fence_mbar_init();
     }
     load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
@@ -231,6 +240,19 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
         __syncwarp();
         tc_fence_after();
     };
+    const uint32_t hmask = SAVED ? ((1u << (L - 1)) - 1u) : 0u;
+    uint32_t ph_h = 0, h_pend = 0;   // per-thread parity of h_full[k]; thread 0's loads not yet waited for
+    auto load_h = [&](int k, int64_t tt) {
+        mbar_arrive_expect_tx(h_full + k, C::TILE);
+        tma_load_2d(sHB + k * C::TILE, &tmap_h, 0, (int32_t)(k * A.act_rows + tt * 128), h_full + k);
+        h_pend |= 1u << k;
+    };
+    auto wait_h = [&](int k) {
+        ok = ok && mbar_wait(h_full + k, (ph_h >> k) & 1u);
+        h_pend &= ~(1u << k);
+    };
+    if (SAVED && tid == 0 && (int64_t)blockIdx.x < n_tiles)
+        for (int k = 0; k < L - 1; ++k) load_h(k, blockIdx.x);
 
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         if (tid == 0 && t + gridDim.x < n_tiles) {   // the next tile's input rows into L2
@@ -263,10 +285,24 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
             st_tile8(sAin, row, c0 + i, 128, S2, av + i);
             st_tile8(sAin, row, H + c0 + i, 128, S2, xv + i);
         }
-        handoff([&] { issue_mma(tWork, sAin, sW0, H, 2 * H); }, bar);
-        // ---- recompute the chain
+        // ---- recompute the chain (SAVED: only the last Linear, from the saved h_{L-2})
         float v[CW];
-        for (int k = 0; k < L; ++k) {
+        if constexpr (SAVED) {
+            if (tid == 0) {
+                wait_h(L - 2);
+                tc_fence_after();
+                if (ok) {
+                    issue_mma(tWork, sHB + (L - 2) * C::TILE, sW + (L - 2) * C::WT, H, H);
+                    mma_commit(bar);
+                }
+            }
+            mma_wait();
+            ld_acc<CW>(tWork, q, c0, v);
+            add_bias2<CW>(v, sPar + (L - 1) * H + c0);
+        } else {
+            handoff([&] { issue_mma(tWork, sAin, sW0, H, 2 * H); }, bar);
+        }
+        for (int k = 0; k < (SAVED ? 0 : L); ++k) {
             mma_wait();
             ld_acc<CW>(tWork, q, c0, v);
             add_bias2<CW>(v, sPar + k * H + c0);
@@ -302,6 +338,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                 ok = ok && mbar_wait(bar_w, ph_w);
                 ph_w ^= 1;
             }
+            if (SAVED && k > 0) wait_h(k - 1);   // this step's wgrad operand and ELU derivative input
             st_row_tile<CW>(sG, row, c0, S, dz);
             handoff([&] {
                 if (k == 0) {
@@ -316,6 +353,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
                                 !first);
                 }
             }, bar_w);
+            // SAVED: h_k's last reader (step k + 1) is done: the next tile's h_k goes there
+            if (SAVED && tid == 0 && ok && k <= L - 2 && t + gridDim.x < n_tiles) load_h(k, t + gridDim.x);
             mma_wait();
             if (k > 0) {
                 float dh[CW], hv[CW];
@@ -342,9 +381,13 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(NodeBwdArgs A) {
         first = false;
         ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads sAin and sG
         ph_w ^= 1;
+        ph_h ^= hmask;
         if (__syncthreads_or(!ok)) break;   // the block leaves together after a timeout
         tc_fence_after();
     }
+    if (SAVED && tid == 0)   // loads issued before a timeout ended the tile loop
+        for (int k = 0; k < L - 1; ++k)
+            if ((h_pend >> k) & 1u) mbar_wait(h_full + k, (ph_h >> k) & 1u);
     // ---- flush the CTA's partial gradients
     tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
@@ -1178,17 +1221,25 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.n_rows = NR;
         A.mlp = mlp_dev(W.node);
         A.eps = cfg.ln_eps;
+        A.act_rows = (NR + 127) / 128 * 128;
         const NodeBwdSmem P = node_bwd_smem<H>(Ln);
-        int grid;
-        rc = persistent_grid(k_node_bwd<H>, C::NT, P.total, pow2_cols(node_bwd_tcols<H>(Ln)), (NR + 127) / 128,
-                             &grid);
-        if (rc) return rc;
-        grid = std::min(grid, nsm);
-        {
-            ProfScope _ps(s, "k_node_bwd");
-            k_node_bwd<H><<<grid, C::NT, P.total, s>>>(A);
-        }
-        GNN_LAUNCH_CHECK("k_node_bwd");
+        CUtensorMap tm_hn;
+        std::memset(&tm_hn, 0, sizeof(tm_hn));
+        if (act && (rc = make_row_tmap(&tm_hn, act + mp_act_elems_edge(G, W, H), (int64_t)(Ln - 1) * A.act_rows, H)))
+            return rc;
+        int grid = 0;
+        auto run = [&](auto kern) -> int {
+            int r = persistent_grid(kern, C::NT, P.total, pow2_cols(node_bwd_tcols<H>(Ln)), (NR + 127) / 128, &grid);
+            if (r) return r;
+            grid = std::min(grid, nsm);
+            {
+                ProfScope _ps(s, "k_node_bwd");
+                kern<<<grid, C::NT, P.total, s>>>(tm_hn, A);
+            }
+            GNN_LAUNCH_CHECK("k_node_bwd");
+            return GNN_OK;
+        };
+        if ((rc = act ? run(k_node_bwd<H, true>) : run(k_node_bwd<H, false>))) return rc;
         RedSeg seg[MAX_SEGS];
         int n = 0;
         int64_t off = 0;

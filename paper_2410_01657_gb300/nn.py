@@ -76,21 +76,21 @@ def mp_workspace_sizes(G: DeviceGraph, cfg, W) -> tuple:
 
 
 def mp_act_bytes(G: DeviceGraph, cfg, W) -> int:
-    """Bytes of the saved edge activations of gnn_mp_forward_act (0: the backward recomputes)."""
+    """Bytes of the saved MLP activations of gnn_mp_forward_act (0: the backward recomputes)."""
     n = C.c_size_t()
     B.call("gnn_mp_act_size", C.byref(G.struct), C.byref(cfg), C.byref(W), C.byref(n))
     return int(n.value)
 
 
 def act_buffer(G: DeviceGraph, cfg, W, device):
-    """A buffer for the saved edge activations of one layer, or None where none are kept."""
+    """A buffer for the saved MLP activations of one layer, or None where none are kept."""
     n = mp_act_bytes(G, cfg, W)
     return torch.empty(n // 2, dtype=torch.bfloat16, device=device) if n else None
 
 
 def gnn_mp_forward(G: DeviceGraph, cfg, W, x, e, x_out, e_out, a_star=None, ws=None, act=None):
     """Direct call of gnn_mp_forward (gnn_mp_forward_act when ``act`` is given,
-    which also stores the edge activations) on preallocated tensors (no autograd)."""
+    which also stores the MLP activations) on preallocated tensors (no autograd)."""
     if ws is None:
         ws = workspace(mp_workspace_sizes(G, cfg, W)[0], x.device)
     if act is not None:
@@ -122,7 +122,7 @@ def gnn_halo_exchange(G: DeviceGraph, rows: torch.Tensor) -> None:
 
 class ConsistentMPFunction(torch.autograd.Function):
     """One consistent NMP layer, Eq. 5a-5e, with the hand-written adjoint (Eq. 3).
-    The edge activations are kept from the forward to the backward where the
+    The MLP activations are kept from the forward to the backward where the
     library supports it (gnn_mp_forward_act / gnn_mp_backward_act)."""
 
     @staticmethod
@@ -276,9 +276,9 @@ class LayerStack:
     Inference keeps the inputs and two edge-state and two node-state buffers
     (ping-pong) and skips the last layer's edge-state write (GNN_FLAG_NO_EDGE_OUT): only the
     aggregates reach the node update, so no per-edge output of the last layer
-    touches HBM. Training keeps every layer's input states and a*, the edge
-    MLP's activations where the library supports it (``save_act``; the
-    backward then recomputes only the last edge Linear, else the whole chain)
+    touches HBM. Training keeps every layer's input states and a*, the MLPs'
+    activations where the library supports it (``save_act``; the backward
+    then recomputes only the last Linear of each MLP, else the whole chains)
     and two node- and two edge-gradient buffers (ping-pong: layer l writes
     dx[l % 2], de[l % 2]; dx[0] ends as dL/dx0). With saved activations the
     forward always uses the record-tiled edge kernel (the autotuner's choice of

@@ -287,10 +287,10 @@ def test_fused_network_training_step_vs_oracle(H):
 
 @pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 5), (64, 2), (64, 0)])
 def test_saved_edge_activations(H, n_hidden):
-    # gnn_mp_forward_act stores h_0 .. h_{L-2} of every edge (the oracle's hidden activations
-    # in BF16) and leaves the layer outputs bitwise unchanged; gnn_mp_backward_act, which
-    # recomputes only the last edge Linear from them, agrees with the recomputing adjoint
-    # and with the oracle, on a ragged multi-tile graph
+    # gnn_mp_forward_act stores h_0 .. h_{L-2} of every edge and node row (the oracle's hidden
+    # activations in BF16) and leaves the layer outputs bitwise unchanged; gnn_mp_backward_act,
+    # which recomputes only the last Linear of each MLP from them, agrees with the recomputing
+    # adjoint and with the oracle, on a ragged multi-tile graph
     brick, subs, part, G, params, x, e = _layer_case((6, 5, 4), 3, 5, H, n_hidden, seed=23)
     lp = params["layers"][0]
     x1, e1, cache = om.layer_forward(lp, subs, split_rows(x, subs), split_edges(e, subs))
@@ -307,7 +307,8 @@ def test_saved_edge_activations(H, n_hidden):
     xt, et = _to(x), _to(e, torch.bfloat16)
     L = n_hidden + 2
     act = gnn.act_buffer(G, cfg, W, DEV)
-    assert act is not None and act.numel() == (L - 1) * part.n_edges * H
+    rows = (part.n_rows + 127) // 128 * 128
+    assert act is not None and act.numel() == (L - 1) * (part.n_edges + rows) * H
     outs = {}
     for name, buf in (("recompute", None), ("saved", act)):
         xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
@@ -323,9 +324,11 @@ def test_saved_edge_activations(H, n_hidden):
         assert np.array_equal(u, v)
     for u, v in zip(rec[3:], sav[3:]):
         assert rel_l2(v, u) < 1e-6
-    A = act.float().cpu().numpy().reshape(L - 1, part.n_edges, H)
+    Ae = act[:(L - 1) * part.n_edges * H].float().cpu().numpy().reshape(L - 1, part.n_edges, H)
+    An = act[(L - 1) * part.n_edges * H:].float().cpu().numpy().reshape(L - 1, rows, H)
     for k in range(L - 1):
-        assert rel_l2(A[k], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
+        assert rel_l2(Ae[k], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
+        assert rel_l2(An[k, :part.n_rows], np.concatenate([c["inputs"][k + 1] for c in cache["c_node"]])) < TOL_OUT
     assert rel_l2(sav[3], np.concatenate(dx0)) < TOL_GRAD
     assert rel_l2(sav[4], np.concatenate(de0)) < TOL_GRAD
     gref = []

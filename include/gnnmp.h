@@ -353,12 +353,15 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
  * results as gnn_mp_forward with GNN_EDGE_FWD_RT (the edge forward it always
  * uses) and gnn_mp_backward. act: device BF16, 16-byte aligned, of
  * gnn_mp_act_size bytes, caller-owned and unchanged from the forward to the
- * backward: edge block k (k < L_e - 1, L_e = W->edge.n_lin) holds rows
- * k * n_edges + e, then node block k (k < L_n - 1) rows k * R + r with
- * R = ceil(n_rows / 128) * 128 (the rows past n_rows are padding). gnn_mp_act_size reports 0
- * where the backward recomputes instead (the FP32 path, BF16 at H = 128,
- * whose adjoint is layered, and graphs with (L_e - 1) * n_edges or
- * (L_n - 1) * R >= 2^31);
+ * backward, in whole 128-row tiles (each tile's rows are stored with one
+ * TMA store): edge block k (k < L_e - 1, L_e = W->edge.n_lin) holds row
+ * k * T + t * 128 + i for edge row i of edge tile t (T = n_edge_tiles * 128;
+ * a tile's rows past its edge count are padding), then node block k
+ * (k < L_n - 1) rows k * R + r with R = ceil(n_rows / 128) * 128. The size
+ * depends on the tiling: after gnn_partition_set_tile_edges ask again.
+ * gnn_mp_act_size reports 0 where the backward recomputes instead (the FP32
+ * path, BF16 at H = 128, whose adjoint is layered, and graphs with
+ * (L_e - 1) * T or (L_n - 1) * R >= 2^31);
  * there act may be NULL and the two calls are
  * gnn_mp_forward / gnn_mp_backward. Errors: those of gnn_mp_forward /
  * gnn_mp_backward; GNN_EINVAL for a NULL or misaligned act that is needed. */

@@ -164,8 +164,10 @@ struct EdgeFwdArgs {
     float* part;                  // per-CTA partials: gamma, beta, last bias gradients (3H)
     int64_t pstride;
     // Training forward (k_edge_fwd_rt<H, true>): the hidden activations h_0 .. h_{L-2}
-    // of every edge, BF16 rows act[(k * n_edges + e) * H], for the backward.
+    // of edge row i of tile t go to row k * act_rows + t * 128 + i of tmap_h (whole
+    // 128-row tiles, so one TMA store per tile never touches another tile's rows).
     __nv_bfloat16* act;
+    int64_t act_rows;
 };
 
 // SAVE: the backward's recomputation of the edge MLP (Eq. 5a) over a range of
@@ -790,7 +792,8 @@ __device__ __forceinline__ int slot_chunk(int k, int row) {
 // next Linear) to A.act, so that the backward need not recompute them.
 template <int H, bool ASAVE = false>
 __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
-    k_edge_fwd_rt(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
+    k_edge_fwd_rt(const __grid_constant__ CUtensorMap tmap_e, const __grid_constant__ CUtensorMap tmap_h,
+                  EdgeFwdArgs A) {
     using C = Cfg<H>;
     using R = RtCfg<H>;
     constexpr int GT = R::GT, SC = R::SC, CW = C::CW, CG = C::CG, NCH = R::NCH;
@@ -920,6 +923,7 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
         bool next_ready = false;   // the next tile's record is in stage s^1
         float v[CW];
         for (int k = 0; k < n_lin && ok; ++k) {
+            if (ASAVE && elected) bulk_wait_read_all();   // sA1 may be rewritten after the group barrier
             ok = group_wait(mbar, ph_mma, elected, bid, GT);
             ph_mma ^= 1;
             tc_fence_after();
@@ -979,17 +983,9 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                     tc_fence_after();
                     issue_mma(tm, sA1, sW + (k + 1) * C::WT, H, H);
                     mma_commit(mbar);
-                }
-                if constexpr (ASAVE) {
-                    // the saved copy of the group's finished BF16 tile leaves while the next MMA
-                    // reads it: whole rows per warp (coalesced); the next writes of sA1 come after
-                    // the group barrier of the next MMA wait
-                    constexpr int CPR = H / 8;   // 16-byte chunks per row
-                    __nv_bfloat16* dst = A.act + ((int64_t)k * A.n_edges + e0) * H;
-                    for (int i = gt; i < ne * CPR; i += GT) {
-                        const int r = i / CPR, j = i - r * CPR;
-                        *reinterpret_cast<uint4*>(dst + (int64_t)r * H + 8 * j) =
-                            *reinterpret_cast<const uint4*>(sA1 + tile_off(r, 8 * j, 128, C::S));
+                    if constexpr (ASAVE) {   // the saved copy leaves while the MMA reads the same tile
+                        tma_store_2d(&tmap_h, 0, (int32_t)(k * A.act_rows + t * 128), sA1);
+                        bulk_commit();
                     }
                 }
             }
@@ -1080,6 +1076,7 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
     }
     cp_async_wait_all();
     if (p_pending) mbar_wait(p_full, ph_p);
+    if (ASAVE && elected) bulk_wait_all();   // the saved tiles are written before the CTA exits
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1440,6 +1437,9 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
         A.act = act;
+        A.act_rows = G.n_edge_tiles * 128;
+        CUtensorMap tmh = tm;
+        if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(W.edge.n_lin - 1) * A.act_rows, H))) return rc;
         int grid;
         int variant = cfg.edge_fwd_kernel;
         if (variant == GNN_EDGE_FWD_AUTO || act) variant = H <= 64 ? GNN_EDGE_FWD_RT : GNN_EDGE_FWD_ONE;
@@ -1455,12 +1455,12 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
                                          cfg.ctas_per_sm);
                     if (rc) return rc;
                     ProfScope _ps(s, "k_edge_fwd");
-                    k_edge_fwd_rt<H, true><<<grid, R::NT, L.total, s>>>(tm, A);
+                    k_edge_fwd_rt<H, true><<<grid, R::NT, L.total, s>>>(tm, tmh, A);
                 } else {
                     rc = persistent_grid(k_edge_fwd_rt<H>, R::NT, L.total, R::NCOLS, ntile, &grid, cfg.ctas_per_sm);
                     if (rc) return rc;
                     ProfScope _ps(s, "k_edge_fwd");
-                    k_edge_fwd_rt<H><<<grid, R::NT, L.total, s>>>(tm, A);
+                    k_edge_fwd_rt<H><<<grid, R::NT, L.total, s>>>(tm, tmh, A);
                 }
             } else if (variant == GNN_EDGE_FWD_WS) {
                 const EdgeFwdWsSmem L = edge_fwd_ws_smem<H>(W.edge.n_lin);
@@ -1558,14 +1558,15 @@ int aggregate_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
 }
 
 size_t mp_act_elems_edge(const gnn_graph_dev& G, const gnn_mp_params& W, int H) {
-    return (size_t)(W.edge.n_lin - 1) * (size_t)G.n_edges * (size_t)H;
+    return (size_t)(W.edge.n_lin - 1) * (size_t)G.n_edge_tiles * 128 * (size_t)H;
 }
 
 size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
     if (cfg.precision != GNN_PREC_BF16 || cfg.hidden > 64 || W.edge.n_lin < 2 || W.node.n_lin < 2) return 0;
-    // activation rows are 32-bit TMA coordinates: edge row k * n_edges + e, node row k * rows + r
+    // activation rows are 32-bit TMA coordinates: edge row k * tiles * 128 + t * 128 + i,
+    // node row k * rows + r
     const int64_t rows = (G.n_rows + 127) / 128 * 128;
-    if ((int64_t)(W.edge.n_lin - 1) * G.n_edges >= ((int64_t)1 << 31) ||
+    if ((int64_t)(W.edge.n_lin - 1) * G.n_edge_tiles * 128 >= ((int64_t)1 << 31) ||
         (int64_t)(W.node.n_lin - 1) * rows >= ((int64_t)1 << 31))
         return 0;
     return (mp_act_elems_edge(G, W, cfg.hidden) + (size_t)(W.node.n_lin - 1) * (size_t)rows * cfg.hidden) * 2;

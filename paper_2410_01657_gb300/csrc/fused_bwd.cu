@@ -427,14 +427,14 @@ struct EdgeBwdArgs {
     int64_t pstride;
     MlpDev mlp;
     float eps;
-    int64_t n_edges;            // SAVED: rows of one activation block of tmap_h
+    int64_t act_rows;           // SAVED: rows of one activation block of tmap_h (tiles * 128)
 };
 
 // LNT: the per-thread LayerNorm gradient sums live in TMEM columns after the
 // weight-gradient accumulators (read, add, write back once per tile) instead
 // of 2*CW registers.
 // SAVED: the forward stored the hidden activations h_0 .. h_{L-2} of every edge
-// (rows k * n_edges + e of tmap_h); the tile's rows arrive by TMA into the
+// (row k * act_rows + t * 128 + i of tmap_h for edge row i of tile t); the tile's rows arrive by TMA into the
 // activation buffers and only the last Linear is recomputed (no P|Q gather, no
 // ELU chain). Buffer k is refilled with the next tile's rows as soon as the
 // adjoint step that reads it last has passed its hand-off, so the loads have
@@ -591,9 +591,9 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
     // parity bit k of h_full[k] (one phase per tile); thread 0's loads not yet waited for
     const uint32_t hmask = SAVED ? ((1u << (L - 1)) - 1u) : 0u;
     uint32_t ph_h = 0, h_pend = 0;
-    auto load_h = [&](int k, int32_t eh) {
+    auto load_h = [&](int k, int64_t tt) {
         mbar_arrive_expect_tx(h_full + k, C::TILE);
-        tma_load_2d(sHB + k * C::TILE, &tmap_h, 0, (int32_t)((int64_t)k * A.n_edges + eh), h_full + k);
+        tma_load_2d(sHB + k * C::TILE, &tmap_h, 0, (int32_t)(k * A.act_rows + tt * 128), h_full + k);
         h_pend |= 1u << k;
     };
     auto wait_h = [&](int k) {
@@ -601,12 +601,10 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         h_pend &= ~(1u << k);
     };
     int32_t e0_next = 0;   // thread 0: first edge of the CTA's next tile
-    int32_t e0_h = 0;      // thread 0: first edge of the tile after the current one (its h loads)
     if (tid == 0 && (int64_t)blockIdx.x < A.n_tiles) {
-        const int32_t e0_first = first_edge(blockIdx.x);
-        issue_stage(0, blockIdx.x, e0_first);
+        issue_stage(0, blockIdx.x, first_edge(blockIdx.x));
         if (SAVED)
-            for (int k = 0; k < L - 1; ++k) load_h(k, e0_first);
+            for (int k = 0; k < L - 1; ++k) load_h(k, blockIdx.x);
         if ((int64_t)blockIdx.x + gridDim.x < A.n_tiles) e0_next = first_edge(blockIdx.x + gridDim.x);
     }
     if ((int64_t)blockIdx.x < A.n_tiles) {
@@ -636,7 +634,6 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             bulk_load(sG, A.da + (int64_t)r0 * H, (uint32_t)(r1 - r0) * H * 4, da_full);
         }
         if (tid == 0 && ok) {
-            e0_h = e0_next;
             if (SAVED) wait_h(L - 2);
             tc_fence_after();
             if (ok) {
@@ -773,7 +770,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
             }, bar_w);
             // SAVED: every thread has passed its last read of h_k (step k + 1) and its wgrad has
             // completed (bar_w, waited at the top of this step): the next tile's h_k goes there
-            if (SAVED && tid == 0 && ok && k <= L - 2 && t + gridDim.x < A.n_tiles) load_h(k, e0_h);
+            if (SAVED && tid == 0 && ok && k <= L - 2 && t + gridDim.x < A.n_tiles) load_h(k, t + gridDim.x);
             if (!SAVED && k == L - 1 && t + gridDim.x < A.n_tiles) {
                 // the slot was consumed by the first recompute step and the next tile's stage
                 // (issued at this tile's start) has landed by now: request its P|Q rows
@@ -1264,7 +1261,7 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
         if ((rc = make_row_tmap(&tm_de, de_out ? (const void*)de_out : (const void*)e_in, E, H))) return rc;
         tm_h = tm_e;
-        if (act && (rc = make_row_tmap(&tm_h, act, (int64_t)(Le - 1) * E, H))) return rc;
+        if (act && (rc = make_row_tmap(&tm_h, act, (int64_t)(Le - 1) * G.n_edge_tiles * 128, H))) return rc;
         EdgeBwdArgs A;
         GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
                     "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
@@ -1281,7 +1278,7 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.pstride = edge_pstride(H, Le);
         A.mlp = mlp_dev(W.edge);
         A.eps = cfg.ln_eps;
-        A.n_edges = E;
+        A.act_rows = G.n_edge_tiles * 128;
         const EdgeBwdSmem P = edge_bwd_smem<H>(Le);
         int grid = 0;
         const bool lnt = edge_bwd_ln_in_tmem<H>(Le);

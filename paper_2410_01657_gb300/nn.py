@@ -317,12 +317,18 @@ class LayerStack:
             self.a = [torch.empty(NR, hidden, device=dev) for _ in range(self.M)]
             self.dx = [torch.empty(NR, hidden, device=dev) for _ in range(2)]
             self.de = [torch.empty(E, hidden, device=dev, dtype=edt) for _ in range(min(2, self.M))]
-        self.act = [None] * self.M
-        if not inference and save_act:
-            self.act = [act_buffer(G, self.cfg, self.W[l], dev) for l in range(self.M)]
+        self.save_act = not inference and save_act
+        self._alloc_act()
         f, b = mp_workspace_sizes(G, self.cfg, self.W[0])
         self.ws = workspace(f if inference else max(f, b), dev)
         self.graph = None
+
+    def _alloc_act(self):
+        # the saved activations come in whole edge tiles: their size follows the tiling
+        self.act = [None] * self.M   # (frees the old buffers first)
+        if self.save_act:
+            self.act = [act_buffer(self.G, self.cfg, self.W[l], self.x[0].device) for l in range(self.M)]
+        self._act_tiles = int(self.G.struct.n_edge_tiles)
 
     # buffers of layer l: inputs, outputs, saved a* (ping-pong in inference)
     def _io(self, l: int):
@@ -344,6 +350,8 @@ class LayerStack:
                 t.zero_()
 
     def forward(self):
+        if self._act_tiles != int(self.G.struct.n_edge_tiles):
+            self._alloc_act()
         for l in range(self.M):
             xi, ei, xo, eo, a = self._io(l)
             cfg = self.cfg_last if l == self.M - 1 else self.cfg

@@ -308,7 +308,13 @@ def test_saved_edge_activations(H, n_hidden):
     L = n_hidden + 2
     act = gnn.act_buffer(G, cfg, W, DEV)
     rows = (part.n_rows + 127) // 128 * 128
-    assert act is not None and act.numel() == (L - 1) * (part.n_edges + rows) * H
+    tiles, rp = part.array("edge_tiles").astype(np.int64), part.array("row_ptr").astype(np.int64)
+    nt = len(tiles) - 1
+    assert act is not None and act.numel() == (L - 1) * (nt * 128 + rows) * H
+    # edge e of tile t (first edge e0_t) is activation row t * 128 + e - e0_t
+    e0 = rp[tiles[:-1]]
+    erow = np.concatenate([t * 128 + np.arange(rp[tiles[t + 1]] - e0[t]) for t in range(nt)])
+    assert erow.size == part.n_edges
     outs = {}
     for name, buf in (("recompute", None), ("saved", act)):
         xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
@@ -324,10 +330,10 @@ def test_saved_edge_activations(H, n_hidden):
         assert np.array_equal(u, v)
     for u, v in zip(rec[3:], sav[3:]):
         assert rel_l2(v, u) < 1e-6
-    Ae = act[:(L - 1) * part.n_edges * H].float().cpu().numpy().reshape(L - 1, part.n_edges, H)
-    An = act[(L - 1) * part.n_edges * H:].float().cpu().numpy().reshape(L - 1, rows, H)
+    Ae = act[:(L - 1) * nt * 128 * H].float().cpu().numpy().reshape(L - 1, nt * 128, H)
+    An = act[(L - 1) * nt * 128 * H:].float().cpu().numpy().reshape(L - 1, rows, H)
     for k in range(L - 1):
-        assert rel_l2(Ae[k], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
+        assert rel_l2(Ae[k][erow], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
         assert rel_l2(An[k, :part.n_rows], np.concatenate([c["inputs"][k + 1] for c in cache["c_node"]])) < TOL_OUT
     assert rel_l2(sav[3], np.concatenate(dx0)) < TOL_GRAD
     assert rel_l2(sav[4], np.concatenate(de0)) < TOL_GRAD

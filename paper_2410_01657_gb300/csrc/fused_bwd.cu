@@ -777,11 +777,8 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 if (mbar_wait(full + (st ^ 1), (uint32_t)((j + 1) >> 1) & 1u)) gather(st ^ 1);
             }
             if (k == 0) {
-                // dz1 per edge (for the sender-side sum) and its receiver-side segmented sum
-                if (valid) {
-#pragma unroll
-                    for (int i = 0; i < CW; i += 8) st_bf16x8(A.dz1 + eg * H + c0 + i, dz + i);
-                }
+                // dz1 per edge (for the sender-side sum; from sG, after the barrier below) and its
+                // receiver-side segmented sum
                 constexpr int NC = H / 4;
                 float4* sS4 = reinterpret_cast<float4*>(sStage);
                 if (!SAVED) __syncthreads();   // every warp is past its last read of hb, which the staging overwrites
@@ -790,6 +787,14 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                     sS4[row * NC + stage_chunk<NC>(c0 / 4 + i, row)] =
                         make_float4(dz[4 * i], dz[4 * i + 1], dz[4 * i + 2], dz[4 * i + 3]);
                 __syncthreads();
+                {   // whole rows per warp: the tile's dz1 rows, as the MMAs read them from sG
+                    constexpr int CPR = H / 8;   // 16-byte chunks per row
+                    for (int i = tid; i < ne * CPR; i += C::NT) {
+                        const int r = i / CPR, jj = i - r * CPR;
+                        *reinterpret_cast<uint4*>(A.dz1 + ((int64_t)e0 + r) * H + 8 * jj) =
+                            *reinterpret_cast<const uint4*>(sG + tile_off(r, 8 * jj, 128, S));
+                    }
+                }
                 const int nr = r1 - r0;
                 for (int it = tid; it < nr * NC; it += C::NT) {
                     const int rr = it / NC, c = it % NC;
@@ -812,12 +817,11 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
                 float hv[CW];
                 ld_row_tile<CW>(sHB + (k - 1) * C::TILE, row, c0, S, hv);
                 elu_bwd2<CW>(dz, dh, hv);
-            } else if (valid) {
+            } else {
                 float o[CW];
 #pragma unroll
                 for (int i = 0; i < CW; ++i) o[i] = gv[i] + dh[i];      // residual + W1c^T dz1
-#pragma unroll
-                for (int i = 0; i < CW; i += 8) st_bf16x8(A.de_in + eg * H + c0 + i, o + i);
+                st_row_tile<CW>(sDE, row, c0, S, o);   // copied out by whole rows after the next barrier
             }
             tc_fence_before();
         }
@@ -825,6 +829,15 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_edge_bwd(const __grid_consta
         ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads this tile's e stage and sG
         ph_w ^= 1;
         ph_h ^= hmask;
+        __syncthreads();   // every row of de_in is in the stage's de tile
+        {
+            constexpr int CPR = H / 8;
+            for (int i = tid; i < ne * CPR; i += C::NT) {
+                const int r = i / CPR, jj = i - r * CPR;
+                *reinterpret_cast<uint4*>(A.de_in + ((int64_t)e0 + r) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(sDE + tile_off(r, 8 * jj, 128, S));
+            }
+        }
         fence_proxy_async();
         if (__syncthreads_or(!ok)) break;   // stage release; the block leaves together after a timeout
         tc_fence_after();

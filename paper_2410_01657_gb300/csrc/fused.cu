@@ -1022,10 +1022,9 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                 v[i + 1] = o.y;
             }
         }
-        if (valid && A.e_out) {
-#pragma unroll
-            for (int i = 0; i < CW; i += 8) st_bf16x8(A.e_out + (e0 + row) * H + c0 + i, v + i);
-        }
+        // e' goes to this tile's e stage (its last reader was the residual above) and leaves
+        // by whole rows per warp after the first barrier of the sums below
+        if (A.e_out) st_row_tile<CW>(sE, row, c0, C::S, v);
         // Eq. 5b: a_r = sum over the row's edges of w * e' (edge order), in two passes of SC
         // columns staged in sA1 as 16-byte chunks; one thread per (row, chunk) sums a segment
         float4* sS = reinterpret_cast<float4*>(sA1);
@@ -1048,6 +1047,14 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
                 }
             }
             named_sync(bid, GT);
+            if (pass == 0 && A.e_out) {
+                constexpr int CPR = H / 8;   // 16-byte chunks per row
+                for (int i = gt; i < ne * CPR; i += GT) {
+                    const int r = i / CPR, jj = i - r * CPR;
+                    *reinterpret_cast<uint4*>(A.e_out + (e0 + r) * H + 8 * jj) =
+                        *reinterpret_cast<const uint4*>(sE + tile_off(r, 8 * jj, 128, C::S));
+                }
+            }
             for (int it = gt; it < nr * NC; it += GT) {
                 const int rr = it / NC, c = it % NC;
                 const int32_t b0 = sRp[rr], b1 = sRp[rr + 1];

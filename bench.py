@@ -493,7 +493,15 @@ def time_e2e(net, G, u, t, steps, warmup, dev):
         one()
     ev1.record()
     torch.cuda.synchronize()
-    return ev0.elapsed_time(ev1) / steps, h2d, 4
+    ms = ev0.elapsed_time(ev1) / steps
+    # the library kernels of one more step, event-timed (torch's own kernels are not listed)
+    from paper_2410_01657_gb300 import binding as B
+    B.call("gnn_profile_start", 1 << 12)
+    one()
+    torch.cuda.synchronize()
+    B.call("gnn_profile_stop")
+    kernels = {k: {"launches": n, "ms": round(v, 4)} for k, (n, v) in B.profile_report().items()}
+    return ms, h2d, 4, kernels
 
 
 def main():
@@ -589,9 +597,9 @@ def main():
 
     e2e = None
     if not args.no_e2e and wl["inputs"] == "encoders" and not fwd_only:
-        ms_e, h2d, d2h = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
+        ms_e, h2d, d2h, e2e_k = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
         e2e = {"value": world * e_unpart * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "library_kernels_one_step": e2e_k,
                "step": "encoders + 4 layers + decoder + consistent loss, fwd+bwd; node field and target "
                        "copied from pinned host memory each step, loss read back"}
 

@@ -357,7 +357,8 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
  * TMA store): edge block k (k < L_e - 1, L_e = W->edge.n_lin) holds row
  * k * T + t * 128 + i for edge row i of edge tile t (T = n_edge_tiles * 128;
  * a tile's rows past its edge count are padding), then node block k
- * (k < L_n - 1) rows k * R + r with R = ceil(n_rows / 128) * 128. The size
+ * (k < L_n - 1) rows k * R + r with R = ceil(n_rows / 128) * 128, then the
+ * node MLP's BF16 input rows [a*, x] (R rows, 2H wide). The size
  * depends on the tiling: after gnn_partition_set_tile_edges ask again.
  * gnn_mp_act_size reports 0 where the backward recomputes instead (the FP32
  * path, BF16 at H = 128, whose adjoint is layered, and graphs with

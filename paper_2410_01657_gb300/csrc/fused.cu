@@ -1117,11 +1117,13 @@ struct NodeFwdArgs {
 // replaced by its adjoint, whose input is the gradient of x' (the residual
 // branch passes it through unchanged).
 // ASAVE (training forward): each finished BF16 hidden tile also goes to block k
-// of tmap_h (row k * act_rows + t * 128 + i) by a TMA store, for the backward.
+// of tmap_h (row k * act_rows + t * 128 + i), and the BF16 input tile [a*, x]
+// to tmap_xa (row t * 128 + i), by TMA stores, for the backward.
 template <int H, bool PF, bool SAVE = false, bool ASAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__ CUtensorMap tmap_a,
                                                         const __grid_constant__ CUtensorMap tmap_x,
-                                                        const __grid_constant__ CUtensorMap tmap_h, NodeFwdArgs A) {
+                                                        const __grid_constant__ CUtensorMap tmap_h,
+                                                        const __grid_constant__ CUtensorMap tmap_xa, NodeFwdArgs A) {
     static_assert(!(PF && SAVE), "the recomputation reads its inputs directly");
     static_assert(!(ASAVE && (SAVE || NodeSplit<H>::value)), "saved activations: the H <= 64 layer forward");
     using C = Cfg<H>;
@@ -1246,6 +1248,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                 tc_fence_after();
                 issue_mma(tmem, sA0, sW0, H, 2 * H);
                 mma_commit(bar_mma);
+                if constexpr (ASAVE) {   // one box per S2 / 2 columns, as the tile is laid out
+#pragma unroll
+                    for (int kb = 0; kb < 2 * H / (S2 / 2); ++kb)
+                        tma_store_2d(&tmap_xa, kb * (S2 / 2), (int32_t)(t * 128), sA0 + kb * 128 * S2);
+                    bulk_commit();
+                }
             }
         } else {
             // K half 0 (a*) then K half 1 (x) through the same [128 x H] buffer
@@ -1519,15 +1527,18 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
     const bool pf = H <= 64 && Lp.total <= 227 * 1024;
     const NodeFwdSmem L = pf ? Lp : node_fwd_smem<H, false>(W.node.n_lin);
     // saved activations: block k of act holds h_k of tile t at rows k * act_rows + t * 128
+    // and the BF16 [a*, x] input tiles after them (row t * 128 + i, 2H wide)
     A.act_rows = (NR + 127) / 128 * 128;
-    CUtensorMap tmh = tma;
+    CUtensorMap tmh = tma, tmxa = tma;
     if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(W.node.n_lin - 1) * A.act_rows, H))) return rc;
+    if (act && (rc = make_row_tmap(&tmxa, act + (int64_t)(W.node.n_lin - 1) * A.act_rows * H, A.act_rows, 2 * H)))
+        return rc;
     auto run = [&](auto kern) -> int {
         int r = persistent_grid(kern, C::NT, L.total, C::TCOLS, (NR + 127) / 128, &grid);
         if (r) return r;
         {
             ProfScope _ps(s, "k_node_fwd");
-            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, A);
+            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, tmxa, A);
         }
         GNN_LAUNCH_CHECK("k_node_fwd");
         return GNN_OK;
@@ -1576,7 +1587,8 @@ size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_
     if ((int64_t)(W.edge.n_lin - 1) * G.n_edge_tiles * 128 >= ((int64_t)1 << 31) ||
         (int64_t)(W.node.n_lin - 1) * rows >= ((int64_t)1 << 31))
         return 0;
-    return (mp_act_elems_edge(G, W, cfg.hidden) + (size_t)(W.node.n_lin - 1) * (size_t)rows * cfg.hidden) * 2;
+    // node part: (L_n - 1) hidden blocks [rows x H] and the input block [rows x 2H]
+    return (mp_act_elems_edge(G, W, cfg.hidden) + (size_t)(W.node.n_lin + 1) * (size_t)rows * cfg.hidden) * 2;
 }
 
 int node_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
@@ -1728,7 +1740,7 @@ int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
         return rc;
     {
         ProfScope _ps(s, "k_node_fwd_save");
-        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tma, A);
+        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tma, tma, A);
     }
     GNN_LAUNCH_CHECK("k_node_fwd_save");
     return GNN_OK;

@@ -18,7 +18,8 @@ size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
 // layered adjoint).
 size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 // Elements of the edge part of those activations; the node MLP's h_0 .. h_{L-2}
-// follow, block k of ceil(n_rows / 128) * 128 rows each.
+// follow, block k of R = ceil(n_rows / 128) * 128 rows each, then the node
+// MLP's BF16 input rows [a*, x] (R rows, 2H wide).
 size_t mp_act_elems_edge(const gnn_graph_dev& G, const gnn_mp_params& W, int H);
 int mp_forward(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* x_in,
                const __nv_bfloat16* e_in, float* x_out, __nv_bfloat16* e_out, float* a_star_out, void* ws,

@@ -88,8 +88,8 @@ __host__ __device__ inline NodeBwdSmem node_bwd_smem(int n_lin) {
     s.ones = align_up(s.hb + (n_lin - 1) * C::TILE, 1024);
     s.par = align_up(s.ones + 128 * C::S, 16);
     s.red = s.par + (n_lin + 2) * H * 4;
-    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // mma, wgrad, ready, h[GNN_MAX_LIN]
-    s.tm = s.bar + 8 * (3 + GNN_MAX_LIN);
+    s.bar = align_up(s.red + 4 * C::CG * 128 * 4, 8);   // mma, wgrad, ready, h[GNN_MAX_LIN], xa
+    s.tm = s.bar + 8 * (4 + GNN_MAX_LIN);
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;
     s.total = end + 1024;
@@ -149,11 +149,13 @@ struct NodeBwdArgs {
 };
 
 // SAVED: the forward stored the node MLP's hidden activations (block k, row
-// k * act_rows + r, of tmap_h); they arrive by TMA into the activation buffers,
-// each refilled with the next tile's rows once its last reader has passed (as
-// in k_edge_bwd), and only the last Linear is recomputed.
+// k * act_rows + r, of tmap_h) and its BF16 input rows [a*, x] (tmap_xa); they
+// arrive by TMA into the activation buffers and the input tile, each refilled
+// with the next tile's rows once its last reader has passed (as in k_edge_bwd),
+// and only the last Linear is recomputed; a* and x are not read.
 template <int H, bool SAVED>
 __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_constant__ CUtensorMap tmap_h,
+                                                            const __grid_constant__ CUtensorMap tmap_xa,
                                                             NodeBwdArgs A) {
     using C = CfgB<H>;
     extern __shared__ uint8_t smem_raw[];
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_consta
     uint64_t* bar_w = bar + 1;                                  // weight-gradient MMAs of an adjoint step
     uint64_t* ready = bar + 2;                                  // one arrival per warp before an MMA
     uint64_t* h_full = bar + 3;                                 // SAVED: h_k of the tile has landed
+    uint64_t* xa_full = bar + 3 + GNN_MAX_LIN;                  // SAVED: the tile's [a*, x] rows have landed
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.tm);
     constexpr int S = C::S, S2 = C::S2, CW = C::CW;
     const uint32_t NCOLS = pow2_cols(node_bwd_tcols<H>(L));
@@ -187,8 +190,10 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_consta
         mbar_init(bar, 1);
         mbar_init(bar_w, 1);
         mbar_init(ready, C::NT / 32);
-        if (SAVED)
+        if (SAVED) {
             for (int k = 0; k < L - 1; ++k) mbar_init(h_full + k, 1);
+            mbar_init(xa_full, 1);
+        }
         fence_mbar_init();
     }
     load_weight(sW0, A.mlp.W[0], 2 * H, 0, H, 2 * H, tid, C::NT);
@@ -251,8 +256,19 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_consta
         ok = ok && mbar_wait(h_full + k, (ph_h >> k) & 1u);
         h_pend &= ~(1u << k);
     };
-    if (SAVED && tid == 0 && (int64_t)blockIdx.x < n_tiles)
+    uint32_t ph_xa = 0;
+    bool xa_pend = false;   // thread 0
+    auto load_xa = [&](int64_t tt) {
+        mbar_arrive_expect_tx(xa_full, 2 * C::TILE);
+#pragma unroll
+        for (int kb = 0; kb < 2 * H / (S2 / 2); ++kb)
+            tma_load_2d(sAin + kb * 128 * S2, &tmap_xa, kb * (S2 / 2), (int32_t)(tt * 128), xa_full);
+        xa_pend = true;
+    };
+    if (SAVED && tid == 0 && (int64_t)blockIdx.x < n_tiles) {
         for (int k = 0; k < L - 1; ++k) load_h(k, blockIdx.x);
+        load_xa(blockIdx.x);
+    }
 
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         if (tid == 0 && t + gridDim.x < n_tiles) {   // the next tile's input rows into L2
@@ -264,32 +280,50 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_consta
         }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
-        float xv[CW], av[CW], gv[CW];
-        if (valid) {
-            const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
-            const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
-            const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
+        float gv[CW];
+        if constexpr (SAVED) {
+            if (valid) {
+                const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
 #pragma unroll
-            for (int i = 0; i < CW / 4; ++i) {
-                float4 u = __ldg(pa + i), w = __ldg(px + i), z = __ldg(pg + i);
-                av[4 * i] = u.x; av[4 * i + 1] = u.y; av[4 * i + 2] = u.z; av[4 * i + 3] = u.w;
-                xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
-                gv[4 * i] = z.x; gv[4 * i + 1] = z.y; gv[4 * i + 2] = z.z; gv[4 * i + 3] = z.w;
+                for (int i = 0; i < CW / 4; ++i) {
+                    const float4 z = __ldg(pg + i);
+                    gv[4 * i] = z.x; gv[4 * i + 1] = z.y; gv[4 * i + 2] = z.z; gv[4 * i + 3] = z.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) gv[i] = 0.f;
             }
         } else {
+            float xv[CW], av[CW];
+            if (valid) {
+                const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
+                const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+                const float4* pg = reinterpret_cast<const float4*>(A.dx_out + r * H + c0);
 #pragma unroll
-            for (int i = 0; i < CW; ++i) av[i] = xv[i] = gv[i] = 0.f;
-        }
+                for (int i = 0; i < CW / 4; ++i) {
+                    float4 u = __ldg(pa + i), w = __ldg(px + i), z = __ldg(pg + i);
+                    av[4 * i] = u.x; av[4 * i + 1] = u.y; av[4 * i + 2] = u.z; av[4 * i + 3] = u.w;
+                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                    gv[4 * i] = z.x; gv[4 * i + 1] = z.y; gv[4 * i + 2] = z.z; gv[4 * i + 3] = z.w;
+                }
+            } else {
 #pragma unroll
-        for (int i = 0; i < CW; i += 8) {
-            st_tile8(sAin, row, c0 + i, 128, S2, av + i);
-            st_tile8(sAin, row, H + c0 + i, 128, S2, xv + i);
+                for (int i = 0; i < CW; ++i) av[i] = xv[i] = gv[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < CW; i += 8) {
+                st_tile8(sAin, row, c0 + i, 128, S2, av + i);
+                st_tile8(sAin, row, H + c0 + i, 128, S2, xv + i);
+            }
         }
         // ---- recompute the chain (SAVED: only the last Linear, from the saved h_{L-2})
         float v[CW];
         if constexpr (SAVED) {
             if (tid == 0) {
                 wait_h(L - 2);
+                ok = ok && mbar_wait(xa_full, ph_xa);   // the input tile of the step-0 weight gradient
+                ph_xa ^= 1;
+                xa_pend = false;
                 tc_fence_after();
                 if (ok) {
                     issue_mma(tWork, sHB + (L - 2) * C::TILE, sW + (L - 2) * C::WT, H, H);
@@ -382,12 +416,15 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_node_bwd(const __grid_consta
         ok = ok && mbar_wait(bar_w, ph_w);   // the last wgrad reads sAin and sG
         ph_w ^= 1;
         ph_h ^= hmask;
+        if (SAVED && tid == 0 && ok && t + gridDim.x < n_tiles) load_xa(t + gridDim.x);   // sAin is free
         if (__syncthreads_or(!ok)) break;   // the block leaves together after a timeout
         tc_fence_after();
     }
-    if (SAVED && tid == 0)   // loads issued before a timeout ended the tile loop
+    if (SAVED && tid == 0) {   // loads issued before a timeout ended the tile loop
         for (int k = 0; k < L - 1; ++k)
             if ((h_pend >> k) & 1u) mbar_wait(h_full + k, (ph_h >> k) & 1u);
+        if (xa_pend) mbar_wait(xa_full, ph_xa);
+    }
     // ---- flush the CTA's partial gradients
     tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
@@ -1233,10 +1270,14 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
         A.eps = cfg.ln_eps;
         A.act_rows = (NR + 127) / 128 * 128;
         const NodeBwdSmem P = node_bwd_smem<H>(Ln);
-        CUtensorMap tm_hn;
+        CUtensorMap tm_hn, tm_xa;
         std::memset(&tm_hn, 0, sizeof(tm_hn));
-        if (act && (rc = make_row_tmap(&tm_hn, act + mp_act_elems_edge(G, W, H), (int64_t)(Ln - 1) * A.act_rows, H)))
-            return rc;
+        std::memset(&tm_xa, 0, sizeof(tm_xa));
+        if (act) {
+            const __nv_bfloat16* an = act + mp_act_elems_edge(G, W, H);
+            if ((rc = make_row_tmap(&tm_hn, an, (int64_t)(Ln - 1) * A.act_rows, H))) return rc;
+            if ((rc = make_row_tmap(&tm_xa, an + (int64_t)(Ln - 1) * A.act_rows * H, A.act_rows, 2 * H))) return rc;
+        }
         int grid = 0;
         auto run = [&](auto kern) -> int {
             int r = persistent_grid(kern, C::NT, P.total, pow2_cols(node_bwd_tcols<H>(Ln)), (NR + 127) / 128, &grid);
@@ -1244,7 +1285,7 @@ int backward_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_pa
             grid = std::min(grid, nsm);
             {
                 ProfScope _ps(s, "k_node_bwd");
-                kern<<<grid, C::NT, P.total, s>>>(tm_hn, A);
+                kern<<<grid, C::NT, P.total, s>>>(tm_hn, tm_xa, A);
             }
             GNN_LAUNCH_CHECK("k_node_bwd");
             return GNN_OK;

@@ -310,7 +310,7 @@ def test_saved_edge_activations(H, n_hidden):
     rows = (part.n_rows + 127) // 128 * 128
     tiles, rp = part.array("edge_tiles").astype(np.int64), part.array("row_ptr").astype(np.int64)
     nt = len(tiles) - 1
-    assert act is not None and act.numel() == (L - 1) * (nt * 128 + rows) * H
+    assert act is not None and act.numel() == (L - 1) * (nt * 128 + rows) * H + rows * 2 * H
     # edge e of tile t (first edge e0_t) is activation row t * 128 + e - e0_t
     e0 = rp[tiles[:-1]]
     erow = np.concatenate([t * 128 + np.arange(rp[tiles[t + 1]] - e0[t]) for t in range(nt)])
@@ -331,7 +331,11 @@ def test_saved_edge_activations(H, n_hidden):
     for u, v in zip(rec[3:], sav[3:]):
         assert rel_l2(v, u) < 1e-6
     Ae = act[:(L - 1) * nt * 128 * H].float().cpu().numpy().reshape(L - 1, nt * 128, H)
-    An = act[(L - 1) * nt * 128 * H:].float().cpu().numpy().reshape(L - 1, rows, H)
+    ne_act, nn_act = (L - 1) * nt * 128 * H, (L - 1) * rows * H
+    An = act[ne_act:ne_act + nn_act].float().cpu().numpy().reshape(L - 1, rows, H)
+    Axa = act[ne_act + nn_act:].float().cpu().numpy().reshape(rows, 2 * H)
+    ref_xa = np.concatenate([np.concatenate(cache["a_star"]), x], axis=1)
+    assert rel_l2(Axa[:part.n_rows], ref_xa) < TOL_OUT
     for k in range(L - 1):
         assert rel_l2(Ae[k][erow], np.concatenate([c["inputs"][k + 1] for c in cache["c_edge"]])) < TOL_OUT
         assert rel_l2(An[k, :part.n_rows], np.concatenate([c["inputs"][k + 1] for c in cache["c_node"]])) < TOL_OUT

@@ -455,6 +455,20 @@ int gnn_mlp_forward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, void*
 int gnn_mlp_backward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY,
                           int32_t dy_bf16, float* dX, const gnn_mlp* dP, float ln_eps,
                           void* ws, size_t ws_bytes, void* stream);
+/* Training with saved activations, as gnn_mp_forward_act: the forward also
+ * writes the hidden activations h_0 .. h_{L-2} (BF16, block k of R =
+ * ceil(n_rows / 128) * 128 rows of H, row k * R + r) to act, and the backward
+ * given that act recomputes only the last Linear. act: device, 16-byte
+ * aligned, of gnn_mlp_act_size_bf16 bytes, caller-owned and unchanged from the
+ * forward to the backward; 0 bytes (act may be NULL: the plain calls) for
+ * shapes outside the fused row MLP or (L - 1) * R >= 2^31. Same results as
+ * gnn_mlp_forward_bf16 / gnn_mlp_backward_bf16. */
+int gnn_mlp_act_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* bytes);
+int gnn_mlp_forward_bf16_act(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,
+                             float ln_eps, void* act, void* stream);
+int gnn_mlp_backward_bf16_act(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY,
+                              int32_t dy_bf16, float* dX, const gnn_mlp* dP, float ln_eps,
+                              const void* act, void* ws, size_t ws_bytes, void* stream);
 
 /* Consistent MSE loss, Eq. 8a-8c: L = sum_rows sum_f (1/d_i)(y - t)^2 /
  * (N_eff * F) with N_eff = sum_rows 1/d_i. y, t: device FP32 [n_rows x F].

@@ -146,6 +146,10 @@ _SIGS = {
                                        C.c_size_t, _P]),
     "gnn_mlp_backward_bf16": (C.c_int, [C.POINTER(gnn_mlp), C.c_int64, _P, _P, C.c_int32, _P,
                                         C.POINTER(gnn_mlp), C.c_float, _P, C.c_size_t, _P]),
+    "gnn_mlp_act_size_bf16": (C.c_int, [C.POINTER(gnn_mlp), C.c_int64, C.POINTER(C.c_size_t)]),
+    "gnn_mlp_forward_bf16_act": (C.c_int, [C.POINTER(gnn_mlp), C.c_int64, _P, _P, C.c_int32, C.c_float, _P, _P]),
+    "gnn_mlp_backward_bf16_act": (C.c_int, [C.POINTER(gnn_mlp), C.c_int64, _P, _P, C.c_int32, _P,
+                                            C.POINTER(gnn_mlp), C.c_float, _P, _P, C.c_size_t, _P]),
     "gnn_consistent_loss": (C.c_int, [C.POINTER(gnn_graph_dev), _P, _P, C.c_int32, _P, _P, _P,
                                       C.c_size_t, _P]),
     "gnn_profile_start": (C.c_int, [C.c_int32]),

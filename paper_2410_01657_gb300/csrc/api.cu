@@ -293,6 +293,52 @@ int gnn_mlp_backward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, cons
                                        (cudaStream_t)stream);
 }
 
+int gnn_mlp_act_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* bytes) {
+    GNN_REQUIRE(P && bytes, GNN_EINVAL, "gnn_mlp_act_size_bf16: NULL argument");
+    GNN_REQUIRE(n_rows >= 0, GNN_ESHAPE, "gnn_mlp_act_size_bf16: negative rows");
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_act_size_bf16", "row");
+    if (rc) return rc;
+    *bytes = gnn::fused::rowmlp_act_bytes(*P, n_rows);
+    return GNN_OK;
+}
+
+int gnn_mlp_forward_bf16_act(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16, float ln_eps,
+                             void* act, void* stream) {
+    GNN_REQUIRE(P, GNN_EINVAL, "gnn_mlp_forward_bf16_act: NULL parameters");
+    if (gnn::fused::rowmlp_act_bytes(*P, n_rows))
+        GNN_REQUIRE(act && ((uintptr_t)act & 15) == 0, GNN_EINVAL,
+                    "gnn_mlp_forward_bf16_act: act must be a 16-byte aligned device buffer");
+    else
+        act = nullptr;
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_forward_bf16_act", "row");
+    if (rc) return rc;
+    GNN_REQUIRE(n_rows >= 0 && n_rows < (int64_t)1 << 31, GNN_ESHAPE, "gnn_mlp_forward_bf16_act: rows out of range");
+    if (n_rows) GNN_REQUIRE(X && Y, GNN_EINVAL, "gnn_mlp_forward_bf16_act: NULL buffer");
+    GNN_REQUIRE(ln_eps > 0.f, GNN_EINVAL, "gnn_mlp_forward_bf16_act: ln_eps must be positive");
+    return gnn::fused::rowmlp_forward(*P, n_rows, X, Y, y_bf16, ln_eps, (cudaStream_t)stream, (__nv_bfloat16*)act);
+}
+
+int gnn_mlp_backward_bf16_act(const gnn_mlp* P, int64_t n_rows, const float* X, const void* dY, int32_t dy_bf16,
+                              float* dX, const gnn_mlp* dP, float ln_eps, const void* act, void* ws, size_t ws_bytes,
+                              void* stream) {
+    GNN_REQUIRE(P && dP, GNN_EINVAL, "gnn_mlp_backward_bf16_act: NULL parameters");
+    if (gnn::fused::rowmlp_act_bytes(*P, n_rows))
+        GNN_REQUIRE(act && ((uintptr_t)act & 15) == 0, GNN_EINVAL,
+                    "gnn_mlp_backward_bf16_act: act must be a 16-byte aligned device buffer");
+    else
+        act = nullptr;
+    int rc = check_mlp(*P, P->dims[0], 0, P->dims[P->n_lin], false, "gnn_mlp_backward_bf16_act", "row");
+    if (rc) return rc;
+    if ((rc = check_mlp(*dP, P->dims[0], 0, P->dims[P->n_lin], P->gamma != nullptr, "gnn_mlp_backward_bf16_act",
+                        "grad")))
+        return rc;
+    GNN_REQUIRE(n_rows >= 0 && n_rows < (int64_t)1 << 31, GNN_ESHAPE, "gnn_mlp_backward_bf16_act: rows out of range");
+    if (n_rows) GNN_REQUIRE(X && dY && ws, GNN_EINVAL, "gnn_mlp_backward_bf16_act: NULL buffer");
+    GNN_REQUIRE(ln_eps > 0.f, GNN_EINVAL, "gnn_mlp_backward_bf16_act: ln_eps must be positive");
+    return gnn::fused::rowmlp_backward(*P, n_rows, X, dY, dy_bf16, dX, *dP, ln_eps, ws, ws_bytes,
+                                       (cudaStream_t)stream, (const __nv_bfloat16*)act);
+}
+
 int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, int32_t F, float* loss, float* dy,
                         void* ws, size_t ws_bytes, void* stream) {
     int rc = check_graph(G, "gnn_consistent_loss");

@@ -82,10 +82,14 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
 // Fused BF16 row MLP (encoders / decoder of the network).
 bool rowmlp_supported(const gnn_mlp& P);
 size_t rowmlp_backward_ws(const gnn_mlp& P);
+// Bytes of a row MLP's saved activations (n_lin - 1 blocks of ceil(n_rows / 128)
+// * 128 BF16 rows of H), 0 where none are kept.
+size_t rowmlp_act_bytes(const gnn_mlp& P, int64_t n_rows);
 int rowmlp_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps,
-                   cudaStream_t s);
+                   cudaStream_t s, __nv_bfloat16* act = nullptr);
 int rowmlp_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
-                    const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s);
+                    const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s,
+                    const __nv_bfloat16* act = nullptr);
 
 }  // namespace fused
 }  // namespace gnn

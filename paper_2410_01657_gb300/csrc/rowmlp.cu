@@ -10,6 +10,7 @@
 // Other shapes stay on the plain FP32 path (gnn_mlp_* with GNN_PREC_FP32).
 
 #include <algorithm>
+#include <cstring>
 
 #include "fused.h"
 #include "fused_bwd_common.cuh"
@@ -34,6 +35,7 @@ struct RowMlpArgs {
     int64_t pstride;
     MlpDev mlp;
     float eps;
+    int64_t act_rows;           // saved activations: rows of one block of tmap_h (tiles * 128)
 };
 
 // ------------------------------------------------------------------ forward
@@ -90,8 +92,10 @@ __device__ __forceinline__ void load_input_row(uint8_t* sA0, const float* X, int
     }
 }
 
-template <int H, int KP, int NP, bool LN>
-__global__ void __launch_bounds__(Cfg<H>::NT) k_rowmlp_fwd(RowMlpArgs A) {
+// ASAVE (training forward): each finished BF16 hidden tile also goes to block k
+// of tmap_h (row k * act_rows + t * 128 + i) by a TMA store, for the backward.
+template <int H, int KP, int NP, bool LN, bool ASAVE = false>
+__global__ void __launch_bounds__(Cfg<H>::NT) k_rowmlp_fwd(const __grid_constant__ CUtensorMap tmap_h, RowMlpArgs A) {
     using C = Cfg<H>;
     constexpr int CW = C::CW, CG = C::CG, S = C::S, SKP = span_of(KP);
     extern __shared__ uint8_t smem_raw[];
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_rowmlp_fwd(RowMlpArgs A) {
         }
         float v[CW];
         for (int k = 0; k < n_lin - 1 && ok; ++k) {   // hidden layers: Linear -> ELU
+            if (ASAVE && tid == 0) bulk_wait_read_all();   // sA1 may be rewritten after the barrier
             ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
@@ -181,9 +186,14 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_rowmlp_fwd(RowMlpArgs A) {
                 else
                     issue_mma(tmem, sA1, sWl, NP, H);
                 mma_commit(bar);
+                if constexpr (ASAVE) {
+                    tma_store_2d(&tmap_h, 0, (int32_t)(k * A.act_rows + t * 128), sA1);
+                    bulk_commit();
+                }
             }
         }
         if (!ok) break;
+        if (ASAVE && tid == 0) bulk_wait_read_all();
         ok = block_wait(bar, ph, tid);   // the last Linear
         ph ^= 1;
         tc_fence_after();
@@ -263,16 +273,21 @@ __host__ __device__ inline RowBwdSmem rowmlp_bwd_smem(int n_lin) {
     s.ones = align_up(s.hb + (n_lin - 1) * 128 * H * 2, 1024);
     s.par = s.ones + 128 * S;
     s.red = s.par + ((n_lin - 1) * H + 3 * NP) * 4;
-    s.bar = align_up(s.red + 4 * (H / 16) * 128 * 4, 8);
-    s.tm = s.bar + 8;
+    s.bar = align_up(s.red + 4 * (H / 16) * 128 * 4, 8);   // mma, h[GNN_MAX_LIN]
+    s.tm = s.bar + 8 * (1 + GNN_MAX_LIN);
     uint32_t end = s.tm + 16;
     end = end > s.g + 32768 ? end : s.g + 32768;   // M-padded wgrad views read 32 KB from g
     s.total = end + 1024;
     return s;
 }
 
-template <int H, int KP, int NP, bool LN, bool DX>
-__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
+// SAVED: the forward stored the hidden activations (block k, row k * act_rows +
+// r, of tmap_h); they arrive by TMA into the activation buffers, each refilled
+// with the next tile's rows once its last reader has passed, and only the last
+// Linear is recomputed.
+template <int H, int KP, int NP, bool LN, bool DX, bool SAVED = false>
+__global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(const __grid_constant__ CUtensorMap tmap_h,
+                                                              RowMlpArgs A) {
     using C = CfgB<H>;
     constexpr int S = C::S, SKP = span_of(KP), SNP = span_of(NP), CW = C::CW, CG = C::CG;
     extern __shared__ uint8_t smem_raw[];
@@ -299,8 +314,11 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
         tmem_alloc(tslot, NCOLS);
         tmem_relinquish();
     }
+    uint64_t* h_full = bar + 1;   // SAVED: h_k of the tile has landed
     if (tid == 0) {
         mbar_init(bar, 1);
+        if (SAVED)
+            for (int k = 0; k < n_lin - 1; ++k) mbar_init(h_full + k, 1);
         fence_mbar_init();
     }
     for (int i = tid; i < H * (KP / 8); i += C::NT) {
@@ -358,15 +376,39 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
             mma_commit(bar);
         }
     };
+    constexpr int HT = 128 * H * 2;   // one activation tile
+    const uint32_t hmask = SAVED ? ((1u << (n_lin - 1)) - 1u) : 0u;
+    // per-thread parity of h_full[k]; thread 0: loads not yet waited for, the phase parity
+    // of each (a timeout can end the tile loop between a load and its tile's end)
+    uint32_t ph_h = 0, h_pend = 0, ld_par = 0, pend_par = 0;
+    auto load_h = [&](int k, int64_t tt) {
+        mbar_arrive_expect_tx(h_full + k, HT);
+        tma_load_2d(sHB + k * HT, &tmap_h, 0, (int32_t)(k * A.act_rows + tt * 128), h_full + k);
+        h_pend |= 1u << k;
+        pend_par = (pend_par & ~(1u << k)) | (ld_par & (1u << k));
+        ld_par ^= 1u << k;
+    };
+    auto wait_h = [&](int k) {
+        ok = ok && mbar_wait(h_full + k, (ph_h >> k) & 1u);
+        h_pend &= ~(1u << k);
+    };
+    if (SAVED && tid == 0 && (int64_t)blockIdx.x < n_tiles)
+        for (int k = 0; k < n_lin - 1; ++k) load_h(k, blockIdx.x);
 
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
+        const bool more = t + gridDim.x < n_tiles;
         load_input_row<KP, CW, CG>(sA0, A.X, r, valid, K0, row, g, c0);
-        mma_sync_issue([&] { issue_mma(tWork, sA0, sW0, H, KP); });
+        if constexpr (SAVED) {   // the last Linear from the saved h_{L-2}
+            wait_h(n_lin - 2);
+            mma_sync_issue([&] { issue_mma(tWork, sHB + (n_lin - 2) * HT, sWl, NP, H); });
+        } else {
+            mma_sync_issue([&] { issue_mma(tWork, sA0, sW0, H, KP); });
+        }
         // ---- recompute: hidden activations into hb, the last pre-activation in registers
         float v[CW];
-        for (int k = 0; k < n_lin - 1 && ok; ++k) {
+        for (int k = 0; k < (SAVED ? 0 : n_lin - 1) && ok; ++k) {
             ok = block_wait(bar, ph, tid);
             ph ^= 1;
             tc_fence_after();
@@ -448,6 +490,12 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
         }
         // ---- adjoint of the chain, layer n_lin-1 .. 0
         for (int l = n_lin - 1; l >= 0 && ok; --l) {
+            if (SAVED && l > 0) wait_h(l - 1);   // this step's wgrad operand and ELU derivative input
+            // SAVED: h_l's last reader (step l + 1) is done once every thread passes the barrier
+            // in this step's issue: the next tile's h_l goes there
+            auto refill = [&] {
+                if (SAVED && l <= n_lin - 2 && more) load_h(l, t + gridDim.x);
+            };
             if (l == n_lin - 1) {
                 // dh = dz W_last (K = NP), dW_last += dz^T [h ; 1]
                 uint8_t* hk = sHB + (l - 1) * 128 * H * 2;
@@ -455,6 +503,7 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
                     issue_dgrad(tWork, sG, SNP, sWl, S, NP, (uint32_t)NP * S, H, NP);
                     issue_wgrad(tDW(l), sG, SNP, 128u * SNP, hk, S, (uint32_t)(smem_u32(sOnes) - smem_u32(hk)), H + 16,
                                 !first);
+                    refill();
                 });
             } else if (l > 0) {
                 uint8_t* hk = sHB + (l - 1) * 128 * H * 2;
@@ -462,12 +511,14 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
                     issue_dgrad(tWork, sG, S, sWm + (l - 1) * H * H * 2, S, H, (uint32_t)H * S, H, H);
                     issue_wgrad(tDW(l), sG, S, 128u * S, hk, S, (uint32_t)(smem_u32(sOnes) - smem_u32(hk)), H + 16,
                                 !first);
+                    refill();
                 });
             } else {
                 // dX = dz W0 (N = KP), dW0 += dz^T [x ; 1]
                 mma_sync_issue([&] {
                     if (DX) issue_dgrad(tWork, sG, S, sW0, SKP, H, (uint32_t)H * SKP, KP, H);
                     issue_wgrad(tDW(0), sG, S, 128u * S, sA0, SKP, 128u * SKP, KP + 16, !first);
+                    refill();
                 });
             }
             ok = block_wait(bar, ph, tid);
@@ -503,8 +554,12 @@ __global__ void __launch_bounds__(CfgB<H>::NT, 1) k_rowmlp_bwd(RowMlpArgs A) {
             }
         }
         first = false;
+        ph_h ^= hmask;
         __syncthreads();
     }
+    if (SAVED && tid == 0)   // loads issued before a timeout ended the tile loop
+        for (int k = 0; k < n_lin - 1; ++k)
+            if ((h_pend >> k) & 1u) mbar_wait(h_full + k, (pend_par >> k) & 1u);
     // ---- flush the CTA's partial gradients
     tc_fence_before();
     __syncthreads();
@@ -549,8 +604,12 @@ int64_t rowmlp_pstride(int H, int KP, int NP, int n_lin, bool ln) {
     return p + (ln ? 2 * H : 0);
 }
 
+// Saved activations of a row MLP: (n_lin - 1) blocks of whole 128-row tiles [R x H].
+int64_t rowmlp_act_rows(int64_t n_rows) { return (n_rows + 127) / 128 * 128; }
+
 template <int H, int KP, int NP, bool LN>
-int rowmlp_fwd_h(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps, cudaStream_t s) {
+int rowmlp_fwd_h(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps, cudaStream_t s,
+                 __nv_bfloat16* act) {
     using C = Cfg<H>;
     RowMlpArgs A{};
     A.X = X;
@@ -562,20 +621,28 @@ int rowmlp_fwd_h(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int 
     A.mlp = mlp_dev(P);
     A.eps = eps;
     const RowFwdSmem L = rowmlp_fwd_smem<H, KP, NP>(P.n_lin);
-    int grid;
-    int rc = persistent_grid(k_rowmlp_fwd<H, KP, NP, LN>, C::NT, L.total, C::TCOLS, (n_rows + 127) / 128, &grid);
-    if (rc) return rc;
-    {
-        ProfScope _ps(s, "k_rowmlp_fwd");
-        k_rowmlp_fwd<H, KP, NP, LN><<<grid, C::NT, L.total, s>>>(A);
-    }
-    GNN_LAUNCH_CHECK("k_rowmlp_fwd");
-    return GNN_OK;
+    A.act_rows = rowmlp_act_rows(n_rows);
+    CUtensorMap tmh;
+    std::memset(&tmh, 0, sizeof(tmh));
+    int rc;
+    if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(P.n_lin - 1) * A.act_rows, H))) return rc;
+    int grid = 0;
+    auto run = [&](auto kern) -> int {
+        int r = persistent_grid(kern, C::NT, L.total, C::TCOLS, (n_rows + 127) / 128, &grid);
+        if (r) return r;
+        {
+            ProfScope _ps(s, "k_rowmlp_fwd");
+            kern<<<grid, C::NT, L.total, s>>>(tmh, A);
+        }
+        GNN_LAUNCH_CHECK("k_rowmlp_fwd");
+        return GNN_OK;
+    };
+    return act ? run(k_rowmlp_fwd<H, KP, NP, LN, true>) : run(k_rowmlp_fwd<H, KP, NP, LN, false>);
 }
 
 template <int H, int KP, int NP, bool LN, bool DX>
 int rowmlp_bwd_h(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
-                 const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s) {
+                 const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s, const __nv_bfloat16* act) {
     using C = CfgB<H>;
     const int L = P.n_lin, K0 = P.dims[0], NO = P.dims[L];
     const uint32_t tcols = rowmlp_bwd_tcols<H, KP>(L, LN);
@@ -597,16 +664,25 @@ int rowmlp_bwd_h(const gnn_mlp& P, int64_t n_rows, const float* X, const void* d
     A.mlp = mlp_dev(P);
     A.eps = eps;
     const RowBwdSmem Pl = rowmlp_bwd_smem<H, KP, NP>(L);
-    int grid;
-    int rc = persistent_grid(k_rowmlp_bwd<H, KP, NP, LN, DX>, C::NT, Pl.total, pow2_cols(tcols),
-                             (n_rows + 127) / 128, &grid);
+    A.act_rows = rowmlp_act_rows(n_rows);
+    CUtensorMap tmh;
+    std::memset(&tmh, 0, sizeof(tmh));
+    int rc;
+    if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(L - 1) * A.act_rows, H))) return rc;
+    int grid = 0;
+    auto run = [&](auto kern) -> int {
+        int r = persistent_grid(kern, C::NT, Pl.total, pow2_cols(tcols), (n_rows + 127) / 128, &grid);
+        if (r) return r;
+        grid = std::min(grid, nsm);
+        {
+            ProfScope _ps(s, "k_rowmlp_bwd");
+            kern<<<grid, C::NT, Pl.total, s>>>(tmh, A);
+        }
+        GNN_LAUNCH_CHECK("k_rowmlp_bwd");
+        return GNN_OK;
+    };
+    rc = act ? run(k_rowmlp_bwd<H, KP, NP, LN, DX, true>) : run(k_rowmlp_bwd<H, KP, NP, LN, DX, false>);
     if (rc) return rc;
-    grid = std::min(grid, nsm);
-    {
-        ProfScope _ps(s, "k_rowmlp_bwd");
-        k_rowmlp_bwd<H, KP, NP, LN, DX><<<grid, C::NT, Pl.total, s>>>(A);
-    }
-    GNN_LAUNCH_CHECK("k_rowmlp_bwd");
     // partial layout: per layer [M x (in + 16)] (bias in column `in`), then gamma, beta
     RedSeg seg[MAX_SEGS];
     int n = 0;
@@ -656,35 +732,45 @@ size_t rowmlp_backward_ws(const gnn_mlp& P) {
     return (size_t)num_sms() * rowmlp_pstride(H, enc ? 16 : H, enc ? H : 16, P.n_lin, enc) * 4 + 256;
 }
 
+size_t rowmlp_act_bytes(const gnn_mlp& P, int64_t n_rows) {
+    int H;
+    if (!rowmlp_shape(P, &H) || n_rows <= 0) return 0;
+    // activation rows are 32-bit TMA coordinates
+    if ((int64_t)(P.n_lin - 1) * rowmlp_act_rows(n_rows) >= ((int64_t)1 << 31)) return 0;
+    return (size_t)(P.n_lin - 1) * (size_t)rowmlp_act_rows(n_rows) * (size_t)H * 2;
+}
+
 int rowmlp_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps,
-                   cudaStream_t s) {
+                   cudaStream_t s, __nv_bfloat16* act) {
     int H;
     const int k = rowmlp_shape(P, &H);
     GNN_REQUIRE(k, GNN_EUNSUPPORTED, "gnn_mlp_forward_bf16: shape not covered by the fused row MLP");
     if (n_rows == 0) return GNN_OK;
+    if (!rowmlp_act_bytes(P, n_rows)) act = nullptr;
     if (k == ROW_ENC) {
         switch (H) {
-            case 16: return rowmlp_fwd_h<16, 16, 16, true>(P, n_rows, X, Y, y_bf16, eps, s);
-            case 32: return rowmlp_fwd_h<32, 16, 32, true>(P, n_rows, X, Y, y_bf16, eps, s);
-            default: return rowmlp_fwd_h<64, 16, 64, true>(P, n_rows, X, Y, y_bf16, eps, s);
+            case 16: return rowmlp_fwd_h<16, 16, 16, true>(P, n_rows, X, Y, y_bf16, eps, s, act);
+            case 32: return rowmlp_fwd_h<32, 16, 32, true>(P, n_rows, X, Y, y_bf16, eps, s, act);
+            default: return rowmlp_fwd_h<64, 16, 64, true>(P, n_rows, X, Y, y_bf16, eps, s, act);
         }
     }
     switch (H) {
-        case 16: return rowmlp_fwd_h<16, 16, 16, false>(P, n_rows, X, Y, y_bf16, eps, s);
-        case 32: return rowmlp_fwd_h<32, 32, 16, false>(P, n_rows, X, Y, y_bf16, eps, s);
-        default: return rowmlp_fwd_h<64, 64, 16, false>(P, n_rows, X, Y, y_bf16, eps, s);
+        case 16: return rowmlp_fwd_h<16, 16, 16, false>(P, n_rows, X, Y, y_bf16, eps, s, act);
+        case 32: return rowmlp_fwd_h<32, 32, 16, false>(P, n_rows, X, Y, y_bf16, eps, s, act);
+        default: return rowmlp_fwd_h<64, 64, 16, false>(P, n_rows, X, Y, y_bf16, eps, s, act);
     }
 }
 
 int rowmlp_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
-                    const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s) {
+                    const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s, const __nv_bfloat16* act) {
     int H;
     const int k = rowmlp_shape(P, &H);
     GNN_REQUIRE(k, GNN_EUNSUPPORTED, "gnn_mlp_backward_bf16: shape not covered by the fused row MLP");
     if (n_rows == 0) return GNN_OK;
-#define GNN_ROW_BWD(HH, KP, NP, LN)                                                                     \
-    return dX ? rowmlp_bwd_h<HH, KP, NP, LN, true>(P, n_rows, X, dY, dy_bf16, dX, dP, eps, ws, ws_bytes, s) \
-              : rowmlp_bwd_h<HH, KP, NP, LN, false>(P, n_rows, X, dY, dy_bf16, dX, dP, eps, ws, ws_bytes, s)
+    if (!rowmlp_act_bytes(P, n_rows)) act = nullptr;
+#define GNN_ROW_BWD(HH, KP, NP, LN)                                                                          \
+    return dX ? rowmlp_bwd_h<HH, KP, NP, LN, true>(P, n_rows, X, dY, dy_bf16, dX, dP, eps, ws, ws_bytes, s, act) \
+              : rowmlp_bwd_h<HH, KP, NP, LN, false>(P, n_rows, X, dY, dy_bf16, dX, dP, eps, ws, ws_bytes, s, act)
     if (k == ROW_ENC) {
         switch (H) {
             case 16: GNN_ROW_BWD(16, 16, 16, true);

@@ -126,7 +126,7 @@ class ConsistentMPFunction(torch.autograd.Function):
     library supports it (gnn_mp_forward_act / gnn_mp_backward_act)."""
 
     @staticmethod
-    def forward(ctx, x, e, G, cfg_args, edge_dims, node_dims, *params):
+    def forward(ctx, x, e, G, cfg_args, edge_dims, node_dims, save, *params):
         cfg = mp_config(*cfg_args)
         W = mp_params(edge_dims, node_dims, params)
         fwd, _ = mp_workspace_sizes(G, cfg, W)
@@ -135,7 +135,7 @@ class ConsistentMPFunction(torch.autograd.Function):
         x_out = torch.empty_like(x)
         e_out = torch.empty_like(e)
         a_star = torch.empty_like(x)
-        act = act_buffer(G, cfg, W, x.device)
+        act = act_buffer(G, cfg, W, x.device) if save else None
         gnn_mp_forward(G, cfg, W, x, e, x_out, e_out, a_star, workspace(fwd, x.device), act)
         ctx.act = act
         ctx.G, ctx.cfg_args, ctx.dims = G, cfg_args, (edge_dims, node_dims)
@@ -157,7 +157,7 @@ class ConsistentMPFunction(torch.autograd.Function):
         de_out = None if de_out is None else de_out.to(e.dtype).contiguous()
         gnn_mp_backward(G, cfg, W, x, e, a_star, dx_out, de_out, dx, de, dW, workspace(bwd, x.device), ctx.act)
         ctx.act = None
-        return (dx, de, None, None, None, None, *dparams)
+        return (dx, de, None, None, None, None, None, *dparams)
 
 
 def rowmlp_fused_shape(dims, has_ln: bool) -> bool:
@@ -177,7 +177,7 @@ class RowMLPFunction(torch.autograd.Function):
     ``fused`` and the shape is covered, else the plain FP32 kernels."""
 
     @staticmethod
-    def forward(ctx, X, dims, has_ln, out_bf16, ln_eps, need_dx, fused, *params):
+    def forward(ctx, X, dims, has_ln, out_bf16, ln_eps, need_dx, fused, save, *params):
         P = mlp_struct(dims, params, has_ln)
         f, b = C.c_size_t(), C.c_size_t()
         rows = X.shape[0]
@@ -186,9 +186,19 @@ class RowMLPFunction(torch.autograd.Function):
         B.call("gnn_mlp_workspace_size" + sfx, C.byref(P), rows, C.byref(f), C.byref(b))
         X = X.contiguous()
         Y = torch.empty((rows, dims[-1]), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=X.device)
-        ws = workspace(f.value, X.device)
-        B.call("gnn_mlp_forward" + sfx, C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps),
-               B.ptr(ws), ws.numel(), _stream())
+        act = None
+        if fused and save:   # keep the activations for the backward (training)
+            n = C.c_size_t()
+            B.call("gnn_mlp_act_size_bf16", C.byref(P), rows, C.byref(n))
+            act = torch.empty(int(n.value) // 2, dtype=torch.bfloat16, device=X.device) if n.value else None
+        if act is not None:
+            B.call("gnn_mlp_forward_bf16_act", C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps),
+                   B.ptr(act), _stream())
+        else:
+            ws = workspace(f.value, X.device)
+            B.call("gnn_mlp_forward" + sfx, C.byref(P), rows, B.ptr(X), B.ptr(Y), int(out_bf16), float(ln_eps),
+                   B.ptr(ws), ws.numel(), _stream())
+        ctx.act = act
         ctx.meta = (dims, has_ln, out_bf16, ln_eps, need_dx, int(b.value), sfx)
         ctx.save_for_backward(X, *params)
         return Y
@@ -203,9 +213,14 @@ class RowMLPFunction(torch.autograd.Function):
         dY = dY.to(torch.bfloat16 if out_bf16 else torch.float32).contiguous()
         dX = torch.empty_like(X) if need_dx else None
         ws = workspace(bwd, X.device)
-        B.call("gnn_mlp_backward" + sfx, C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16), B.ptr(dX),
-               C.byref(dP), float(ln_eps), B.ptr(ws), ws.numel(), _stream())
-        return (dX, None, None, None, None, None, None, *dparams)
+        if ctx.act is not None:
+            B.call("gnn_mlp_backward_bf16_act", C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16),
+                   B.ptr(dX), C.byref(dP), float(ln_eps), B.ptr(ctx.act), B.ptr(ws), ws.numel(), _stream())
+            ctx.act = None
+        else:
+            B.call("gnn_mlp_backward" + sfx, C.byref(P), X.shape[0], B.ptr(X), B.ptr(dY), int(out_bf16), B.ptr(dX),
+                   C.byref(dP), float(ln_eps), B.ptr(ws), ws.numel(), _stream())
+        return (dX, None, None, None, None, None, None, None, *dparams)
 
 
 class ConsistentLossFunction(torch.autograd.Function):
@@ -482,7 +497,7 @@ class ConsistentGNN(torch.nn.Module):
 
     def _row_mlp(self, m: _MLP, X, out_bf16: bool, need_dx: bool):
         return RowMLPFunction.apply(X, m.dims, m.has_ln, out_bf16, self.ln_eps, need_dx, self.precision == "bf16",
-                                    *m.tensors())
+                                    torch.is_grad_enabled(), *m.tensors())
 
     def encode(self, G: DeviceGraph, u, attr):
         x = self._row_mlp(self.enc_node, u, False, False)
@@ -493,7 +508,7 @@ class ConsistentGNN(torch.nn.Module):
         cfg_args = (self.hidden, self.precision, self.halo, self.ln_eps, 0)
         for layer in self.layers:
             x, e = ConsistentMPFunction.apply(x, e, G, cfg_args, layer.edge.dims, layer.node.dims,
-                                              *layer.edge.tensors(), *layer.node.tensors())
+                                              torch.is_grad_enabled(), *layer.edge.tensors(), *layer.node.tensors())
         return x, e
 
     def forward(self, G: DeviceGraph, u, attr):

@@ -144,7 +144,7 @@ def test_layer_backward_fp32_vs_oracle_with_edge_grad():
     tens = layer.edge.tensors() + layer.node.tensors()
     xt, et = _to(x).requires_grad_(True), _to(e).requires_grad_(True)
     xo, eo = gnn.ConsistentMPFunction.apply(xt, et, G, (H, "fp32", True, 1e-5, 0), layer.edge.dims,
-                                            layer.node.dims, *tens)
+                                            layer.node.dims, True, *tens)
     assert rel_l2(xo.detach().cpu().numpy(), np.concatenate(x1)) < 1e-5
     assert rel_l2(eo.detach().cpu().numpy(), np.concatenate(e1)) < 1e-5
     torch.autograd.backward([xo, eo], [_to(np.concatenate(dx1)), _to(np.concatenate(de1))])

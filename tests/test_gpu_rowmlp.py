@@ -39,11 +39,11 @@ def _mlp_params(dims, has_ln, seed):
     return P
 
 
-def _run(P, dims, has_ln, X, dY, fused, out_bf16=False, need_dx=False):
+def _run(P, dims, has_ln, X, dY, fused, out_bf16=False, need_dx=False, save=False):
     ts = [torch.nn.Parameter(torch.as_tensor(t, dtype=torch.float32, device=DEV))
           for t in [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if has_ln else [])]
     Xt = torch.as_tensor(X, dtype=torch.float32, device=DEV).requires_grad_(need_dx)
-    Y = gnn.RowMLPFunction.apply(Xt, dims, has_ln, out_bf16, 1e-5, need_dx, fused, *ts)
+    Y = gnn.RowMLPFunction.apply(Xt, dims, has_ln, out_bf16, 1e-5, need_dx, fused, save, *ts)
     Y.backward(torch.as_tensor(dY, dtype=torch.float32, device=DEV).to(Y.dtype))
     B.call("gnn_check", None)
     n = len(dims) - 1
@@ -65,6 +65,16 @@ def _check(P, dims, has_ln, rows, seed, out_bf16=False, need_dx=False):
     Yp, gp, dxp = _run(P, dims, has_ln, X, dY, False, False, need_dx)
     assert rel_l2(Yp, Yo) < 1e-5                      # the plain FP32 reference itself
     assert rel_l2(Yf, Yo) < 2e-2 and rel_l2(Yf, Yp) < 2e-2
+    # with saved activations (gnn_mlp_*_bf16_act): the same forward, and the adjoint of the
+    # recomputing kernels to FP32 rounding
+    Ys, gs, dxs = _run(P, dims, has_ln, X, dY, True, out_bf16, need_dx, save=True)
+    assert np.array_equal(Ys, Yf)
+    for key in gf:
+        for a, ref in zip(gs[key] if isinstance(gs[key], list) else [gs[key]],
+                          gf[key] if isinstance(gf[key], list) else [gf[key]]):
+            assert rel_l2(a, ref) < 1e-6, (key, rel_l2(a, ref))
+    if need_dx:
+        assert rel_l2(dxs, dxf) < 1e-6
     for key in gf:
         for a, ref in zip(gf[key] if isinstance(gf[key], list) else [gf[key]],
                           go[key] if isinstance(go[key], list) else [go[key]]):

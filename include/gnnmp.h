@@ -361,8 +361,9 @@ int gnn_mp_backward(const gnn_graph_dev* G, const gnn_mp_config* cfg, const gnn_
  * node MLP's BF16 input rows [a*, x] (R rows, 2H wide). The size
  * depends on the tiling: after gnn_partition_set_tile_edges ask again.
  * gnn_mp_act_size reports 0 where the backward recomputes instead (the FP32
- * path, BF16 at H = 128, whose adjoint is layered, and graphs with
- * (L_e - 1) * T or (L_n - 1) * R >= 2^31);
+ * path, BF16 at H = 128, whose adjoint is layered, tilings with T above
+ * 1.25 n_edges -- edge caps below 128, whose tiles would hold mostly padding
+ * -- and graphs with (L_e - 1) * T or (L_n - 1) * R >= 2^31);
  * there act may be NULL and the two calls are
  * gnn_mp_forward / gnn_mp_backward. Errors: those of gnn_mp_forward /
  * gnn_mp_backward; GNN_EINVAL for a NULL or misaligned act that is needed. */

@@ -1581,6 +1581,9 @@ size_t mp_act_elems_edge(const gnn_graph_dev& G, const gnn_mp_params& W, int H) 
 
 size_t mp_act_bytes(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W) {
     if (cfg.precision != GNN_PREC_BF16 || cfg.hidden > 64 || W.edge.n_lin < 2 || W.node.n_lin < 2) return 0;
+    // whole 128-row tiles pay only when the tiles are nearly full (the default edge cap); a
+    // graph re-tiled to smaller caps would store mostly padding, so it recomputes instead
+    if (G.n_edge_tiles * 128 > G.n_edges + G.n_edges / 4 + 128) return 0;
     // activation rows are 32-bit TMA coordinates: edge row k * tiles * 128 + t * 128 + i,
     // node row k * rows + r
     const int64_t rows = (G.n_rows + 127) / 128 * 128;

@@ -181,8 +181,13 @@ struct EdgeFwdArgs {
 // are requested into the same buffers, so their latency hides behind this
 // tile's chain. The residual of Eq. 5a re-reads e from global memory (L2), and
 // the 1/d-weighted sums of Eq. 5b are staged in the activation buffer.
+// SAVE writes each hidden tile and the tile's dz with TMA stores (tmap_hs: block k at
+// row k * hs_stride / H + (t - t0) * 128; tmap_dz: row (t - t0) * 128), rows past
+// the tile's edges zero.
 template <int H, bool SAVE = false>
-__global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__ CUtensorMap tmap_e, EdgeFwdArgs A) {
+__global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__ CUtensorMap tmap_e,
+                                                        const __grid_constant__ CUtensorMap tmap_hs,
+                                                        const __grid_constant__ CUtensorMap tmap_dz, EdgeFwdArgs A) {
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -293,6 +298,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
                         eres[i] = __ldg(reinterpret_cast<const uint4*>(A.e_in + eg * H + c0) + i);
                 }
             }
+            if (SAVE && tid == 0) bulk_wait_read_all();   // sA1 may be rewritten after the barrier
             ok = block_wait(bar_mma, ph_mma, tid);
             ph_mma ^= 1;
             tc_fence_after();
@@ -318,17 +324,11 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             if (k < n_lin - 1) {
 #pragma unroll
                 for (int i = 0; i < C::CW; ++i) v[i] = elu1_fast(v[i]);
-                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
-                if constexpr (SAVE) {
-                    __nv_bfloat16* hrow = A.hs + k * A.hs_stride + ((t - tb) * 128 + row) * H + c0;
+                if constexpr (SAVE) {   // the saved rows past the tile's edges are zero
 #pragma unroll
-                    for (int i = 0; i < C::CW; i += 8) {
-                        float z8[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) z8[jj] = valid ? v[i + jj] : 0.f;
-                        st_bf16x8(hrow + i, z8);
-                    }
+                    for (int i = 0; i < C::CW; ++i) v[i] = valid ? v[i] : 0.f;
                 }
+                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();
                 __syncthreads();
@@ -336,6 +336,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
                     tc_fence_after();
                     issue_mma(tmem, sA1, sW + (k + 1) * C::WT, H, H);
                     mma_commit(bar_mma);
+                    if constexpr (SAVE) {   // the hidden tile to scratch while the MMA reads it
+#pragma unroll
+                        for (int kb = 0; kb < (H + 63) / 64; ++kb)
+                            tma_store_2d(&tmap_hs, kb * 64, (int32_t)(k * (A.hs_stride / H) + (t - tb) * 128),
+                                         sA1 + kb * 128 * 128);
+                        bulk_commit();
+                    }
                 }
             }
         }
@@ -371,10 +378,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
             float mean, rstd, s1, s2;
             row_stats_adj_gamma<H, C::CG, C::CW>(v, gv, gam, sRed, row, g, A.eps, mean, rstd, s1, s2);
             ln_adjoint_row<C::CW>(v, gv, gam, mean, rstd, s1, s2, valid, lane, accG, accB, accZ);
-            __nv_bfloat16* zrow = A.dz + ((t - tb) * 128 + row) * H + c0;
-#pragma unroll
-            for (int i = 0; i < C::CW; i += 8) st_bf16x8(zrow + i, v + i);
+            st_row_tile<C::CW>(sA1, row, c0, C::S, v);   // dz to scratch by TMA (the last MMA has read sA1)
+            fence_proxy_async();
             __syncthreads();   // the record of this tile is rewritten two tiles later, sRed next tile
+            if (tid == 0) {
+#pragma unroll
+                for (int kb = 0; kb < (H + 63) / 64; ++kb)
+                    tma_store_2d(&tmap_dz, kb * 64, (int32_t)((t - tb) * 128), sA1 + kb * 128 * 128);
+                bulk_commit();
+            }
             continue;
         }
         // LayerNorm + residual (Eq. 5a)
@@ -393,14 +405,21 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
 #pragma unroll
                 for (int k = 0; k < 8; ++k) v[8 * i + k] = eo[k] + (v[8 * i + k] - mean) * rstd * gam[8 * i + k] + bet[8 * i + k];
             }
-            if (A.e_out) {
-#pragma unroll
-                for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.e_out + eg * H + c0 + i, v + i);
+        }
+        // e' leaves by whole rows per warp, staged in the activation buffer (its last
+        // reader, the final Linear, has completed), before the sums below reuse it
+        if (A.e_out) {
+            st_row_tile<C::CW>(sA1, row, c0, C::S, v);
+            __syncthreads();
+            constexpr int CPR = H / 8;   // 16-byte chunks per row
+            for (int i = tid; i < ne * CPR; i += C::NT) {
+                const int rr = i / CPR, jj = i - rr * CPR;
+                *reinterpret_cast<uint4*>(A.e_out + ((int64_t)e0 + rr) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(sA1 + tile_off(rr, 8 * jj, 128, C::S));
             }
         }
         // 1/d-weighted segmented sum over each receiver's edges (Eq. 5b), two column
-        // passes staged in FP32 in the activation buffer (its last reader, the final
-        // Linear, has completed)
+        // passes staged in FP32 in the activation buffer
         float4* sS4 = reinterpret_cast<float4*>(sA1);
         __syncthreads();
 #pragma unroll
@@ -432,6 +451,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_edge_fwd(const __grid_constant__
         fence_proxy_async();   // generic writes of sA1 precede the next tile's MMA reads
     }
     if (tid == 0 && ld_pending) mbar_wait(bar_ld, (uint32_t)j & 1u);   // after a timeout: bounded
+    if (SAVE && tid == 0) bulk_wait_all();   // the scratch tiles are written before the CTA exits
     if constexpr (SAVE) {
         float* part = A.part + (int64_t)blockIdx.x * A.pstride;
         colsum_store<H, NCH>(accG, sRed, q, lane, c0, tid, C::NT, part);
@@ -1494,7 +1514,7 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
             rc = persistent_grid(k_edge_fwd<H>, C::NT, L.total, C::TCOLS, G.n_edge_tiles, &grid, cfg.ctas_per_sm);
             if (rc) return rc;
             ProfScope _ps(s, "k_edge_fwd");
-            k_edge_fwd<H><<<grid, C::NT, L.total, s>>>(tm, A);
+            k_edge_fwd<H><<<grid, C::NT, L.total, s>>>(tm, tm, tm, A);
         }
         GNN_LAUNCH_CHECK("k_edge_fwd");
     } else {
@@ -1705,10 +1725,13 @@ int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
     A.part = o.part;
     A.pstride = o.pstride;
     const EdgeFwdSmem L = edge_fwd_smem<H>(W.edge.n_lin, true);
+    CUtensorMap tmhs, tmdz;
+    if ((rc = make_row_tmap(&tmhs, o.hs, (int64_t)(W.edge.n_lin - 1) * (o.hs_stride / H), H))) return rc;
+    if ((rc = make_row_tmap(&tmdz, o.dz, o.hs_stride / H, H))) return rc;
     if ((rc = persistent_grid(k_edge_fwd<H, true>, C::NT, L.total, C::TCOLS, o.t1 - o.t0, &o.grid))) return rc;
     {
         ProfScope _ps(s, "k_edge_fwd_save");
-        k_edge_fwd<H, true><<<o.grid, C::NT, L.total, s>>>(tm, A);
+        k_edge_fwd<H, true><<<o.grid, C::NT, L.total, s>>>(tm, tmhs, tmdz, A);
     }
     GNN_LAUNCH_CHECK("k_edge_fwd_save");
     return GNN_OK;

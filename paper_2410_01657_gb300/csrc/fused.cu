@@ -1139,12 +1139,17 @@ struct NodeFwdArgs {
 // ASAVE (training forward): each finished BF16 hidden tile also goes to block k
 // of tmap_h (row k * act_rows + t * 128 + i), and the BF16 input tile [a*, x]
 // to tmap_xa (row t * 128 + i), by TMA stores, for the backward.
+// SAVE (H = 128) stores the BF16 [a*, x] halves, the hidden tiles and dz with TMA
+// stores too: tmap_xa row (t - t0) * 128 (2H wide), tmap_h block k at row
+// k * hs_stride / H + (t - t0) * 128, tmap_dz row (t - t0) * 128.
 template <int H, bool PF, bool SAVE = false, bool ASAVE = false>
 __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__ CUtensorMap tmap_a,
                                                         const __grid_constant__ CUtensorMap tmap_x,
                                                         const __grid_constant__ CUtensorMap tmap_h,
-                                                        const __grid_constant__ CUtensorMap tmap_xa, NodeFwdArgs A) {
+                                                        const __grid_constant__ CUtensorMap tmap_xa,
+                                                        const __grid_constant__ CUtensorMap tmap_dz, NodeFwdArgs A) {
     static_assert(!(PF && SAVE), "the recomputation reads its inputs directly");
+    static_assert(!SAVE || NodeSplit<H>::value, "the recomputation form is the H = 128 one");
     static_assert(!(ASAVE && (SAVE || NodeSplit<H>::value)), "saved activations: the H <= 64 layer forward");
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
@@ -1248,13 +1253,6 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < C::CW; ++i) xa[i] = xv[i] = 0.f;
         }
-        if constexpr (SAVE) {
-#pragma unroll
-            for (int i = 0; i < C::CW; i += 8) {
-                st_bf16x8(A.xa + srow * 2 * H + c0 + i, xa + i);
-                st_bf16x8(A.xa + srow * 2 * H + H + c0 + i, xv + i);
-            }
-        }
         if constexpr (!NodeSplit<H>::value) {
 #pragma unroll
             for (int i = 0; i < C::CW; i += 8) {
@@ -1285,7 +1283,14 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                 tc_fence_after();
                 issue_mma_koff(tmem, sA0, sW0, H, H, 0, 2 * H, false);
                 mma_commit(bar_mma);
+                if constexpr (SAVE) {   // the a* half of the saved input rows
+#pragma unroll
+                    for (int kb = 0; kb < H / 64; ++kb)
+                        tma_store_2d(&tmap_xa, kb * 64, (int32_t)((t - tb) * 128), sA0 + kb * 128 * 128);
+                    bulk_commit();
+                }
             }
+            if (SAVE && tid == 0) bulk_wait_read_all();   // sA0 is rewritten after the barrier
             ok = block_wait(bar_mma, ph, tid);
             ph ^= 1;
             tc_fence_after();
@@ -1298,11 +1303,17 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                 tc_fence_after();
                 issue_mma_koff(tmem, sA0, sW0, H, H, H, 2 * H, true);
                 mma_commit(bar_mma);
+                if constexpr (SAVE) {   // and the x half
+#pragma unroll
+                    for (int kb = 0; kb < H / 64; ++kb)
+                        tma_store_2d(&tmap_xa, H + kb * 64, (int32_t)((t - tb) * 128), sA0 + kb * 128 * 128);
+                    bulk_commit();
+                }
             }
         }
         float v[C::CW];
         for (int k = 0; k < n_lin && ok; ++k) {
-            if (ASAVE && tid == 0) bulk_wait_read_all();   // sA1 may be rewritten after the barrier
+            if ((ASAVE || SAVE) && tid == 0) bulk_wait_read_all();   // sA0 / sA1 may be rewritten after the barrier
             ok = block_wait(bar_mma, ph, tid);
             ph ^= 1;
             tc_fence_after();
@@ -1311,17 +1322,11 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
             add_bias2<C::CW>(v, sPar + k * H + c0);
             if (k < n_lin - 1) {
                 elu_inplace2<C::CW>(v);
-                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
-                if constexpr (SAVE) {
-                    __nv_bfloat16* hrow = A.hs + k * A.hs_stride + srow * H + c0;
+                if constexpr (SAVE) {   // the saved rows past the graph's rows are zero
 #pragma unroll
-                    for (int i = 0; i < C::CW; i += 8) {
-                        float z8[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) z8[jj] = valid ? v[i + jj] : 0.f;
-                        st_bf16x8(hrow + i, z8);
-                    }
+                    for (int i = 0; i < C::CW; ++i) v[i] = valid ? v[i] : 0.f;
                 }
+                st_row_tile<C::CW>(sA1, row, c0, C::S, v);
                 fence_proxy_async();
                 tc_fence_before();
                 __syncthreads();
@@ -1331,6 +1336,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                     mma_commit(bar_mma);
                     if constexpr (ASAVE) {
                         tma_store_2d(&tmap_h, 0, (int32_t)(k * A.act_rows + t * 128), sA1);
+                        bulk_commit();
+                    }
+                    if constexpr (SAVE) {
+#pragma unroll
+                        for (int kb = 0; kb < H / 64; ++kb)
+                            tma_store_2d(&tmap_h, kb * 64, (int32_t)(k * (A.hs_stride / H) + (t - tb) * 128),
+                                         sA1 + kb * 128 * 128);
                         bulk_commit();
                     }
                 }
@@ -1355,9 +1367,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
             float mean, rstd, s1, s2;
             row_stats_adj_gamma<H, C::CG, C::CW>(v, gv, gam, sRed, row, g, A.eps, mean, rstd, s1, s2);
             ln_adjoint_row<C::CW>(v, gv, gam, mean, rstd, s1, s2, valid, lane, accG, accB, accZ);
-#pragma unroll
-            for (int i = 0; i < C::CW; i += 8) st_bf16x8(A.dz + srow * H + c0 + i, v + i);
+            st_row_tile<C::CW>(sA1, row, c0, C::S, v);   // dz to scratch by TMA (the last MMA has read sA1)
+            fence_proxy_async();
             __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int kb = 0; kb < H / 64; ++kb)
+                    tma_store_2d(&tmap_dz, kb * 64, (int32_t)((t - tb) * 128), sA1 + kb * 128 * 128);
+                bulk_commit();
+            }
             continue;
         }
         float mean, rstd;
@@ -1389,7 +1407,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         colsum_store<H, NCH>(accB, sRed, q, lane, c0, tid, C::NT, part + H);
         colsum_store<H, NCH>(accZ, sRed, q, lane, c0, tid, C::NT, part + 2 * H);
     }
-    if (ASAVE && tid == 0) bulk_wait_all();   // the saved tiles are written before the CTA exits
+    if ((ASAVE || SAVE) && tid == 0) bulk_wait_all();   // the saved tiles are written before the CTA exits
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1558,7 +1576,7 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         if (r) return r;
         {
             ProfScope _ps(s, "k_node_fwd");
-            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, tmxa, A);
+            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, tmxa, tma, A);
         }
         GNN_LAUNCH_CHECK("k_node_fwd");
         return GNN_OK;
@@ -1761,12 +1779,17 @@ int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
     int rc = make_f32_tmap(&tma, a_star, G.n_rows, H);
     if (rc) return rc;
     if ((rc = make_f32_tmap(&tmx, x_in, G.n_rows, H))) return rc;
+    CUtensorMap tmhs, tmxa, tmdz;   // the scratch tiles, written by TMA stores
+    const int64_t cap = o.hs_stride / H;   // scratch rows per block
+    if ((rc = make_row_tmap(&tmhs, o.hs, (int64_t)(W.node.n_lin - 1) * cap, H))) return rc;
+    if ((rc = make_row_tmap(&tmxa, o.xa, cap, 2 * H))) return rc;
+    if ((rc = make_row_tmap(&tmdz, o.dz, cap, H))) return rc;
     const NodeFwdSmem L = node_fwd_smem<H, false>(W.node.n_lin, true);
     if ((rc = persistent_grid(k_node_fwd<H, false, true>, C::NT, L.total, C::TCOLS, o.t1 - o.t0, &o.grid)))
         return rc;
     {
         ProfScope _ps(s, "k_node_fwd_save");
-        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tma, tma, A);
+        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tmhs, tmxa, tmdz, A);
     }
     GNN_LAUNCH_CHECK("k_node_fwd_save");
     return GNN_OK;

@@ -319,16 +319,18 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
                     for (int k = 0; k < 8; ++k) gv[i + k] = d8[k] + gv[i + k];
                 }
             }
-            // dz_0 per edge, for the sender-side sums of the projection adjoint
-#pragma unroll
-            for (int i = 0; i < CW; i += 8) {
-                float z8[8];
-                ld_tile8(dzt, row, c0 + i, 128, S, z8);
-                st_bf16x8(A.dz1 + eg * H + c0 + i, z8);
-            }
         } else {
 #pragma unroll
             for (int i = 0; i < CW; ++i) gv[i] = 0.f;
+        }
+        {   // dz_0 per edge, for the sender-side sums of the projection adjoint: whole rows per
+            // warp from the stage's dz tile (TMA-loaded, complete since the stage barrier)
+            constexpr int CPR = H / 8;
+            for (int i = tid; i < ne * CPR; i += NT) {
+                const int rr = i / CPR, jj = i - rr * CPR;
+                *reinterpret_cast<uint4*>(A.dz1 + ((int64_t)e0 + rr) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(dzt + tile_off(rr, 8 * jj, 128, S));
+            }
         }
         // receiver-side sums of dz_0 over each receiver's edges (dP, fixed edge order)
         for (int it = tid; it < (r1 - r0) * (H / 8); it += NT) {
@@ -350,12 +352,8 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         float dh[CW];
         ld_acc<CW>(tWork, q, c0, dh);
         tc_fence_before();
-        if (valid) {   // residual branch plus W1c^T dz_0
 #pragma unroll
-            for (int i = 0; i < CW; ++i) dh[i] = gv[i] + dh[i];
-#pragma unroll
-            for (int i = 0; i < CW; i += 8) st_bf16x8(A.de_in + eg * H + c0 + i, dh + i);
-        }
+        for (int i = 0; i < CW; ++i) dh[i] = gv[i] + dh[i];   // residual branch plus W1c^T dz_0
         fence_proxy_async();
         ok = block_wait(bar_w, ph, tid);   // the stage is free: wgrad done, every thread past its reads
         if (!ok) break;
@@ -363,6 +361,19 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         ph ^= 1;
         tc_fence_after();
         first = false;
+        // de_in by whole rows per warp, staged in the stage's e tile (the wgrad has read it); the
+        // stage is refilled only after the next tile's stage barrier
+        st_row_tile<CW>(et, row, c0, S, dh);
+        __syncthreads();
+        {
+            constexpr int CPR = H / 8;
+            for (int i = tid; i < ne * CPR; i += NT) {
+                const int rr = i / CPR, jj = i - rr * CPR;
+                *reinterpret_cast<uint4*>(A.de_in + ((int64_t)e0 + rr) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(et + tile_off(rr, 8 * jj, 128, S));
+            }
+        }
+        fence_proxy_async();   // generic accesses of the stage precede its TMA refill
     }
     if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
         if (mp) mbar_wait(bar_w, ph);

@@ -207,16 +207,21 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_rowmlp_fwd(const __grid_constant
             row_stats<H, CG, CW>(v, sRed, row, g, A.eps, mean, rstd);
 #pragma unroll
             for (int i = 0; i < CW; ++i) v[i] = (v[i] - mean) * rstd * bl[NP + c0 + i] + bl[2 * NP + c0 + i];
-            if (valid) {
-                if (A.y_bf16) {
-                    __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(A.Y) + r * NO + c0;
-#pragma unroll
-                    for (int i = 0; i < CW; i += 8) st_bf16x8(y + i, v + i);
-                } else {
-                    float4* y = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.Y) + r * NO + c0);
-#pragma unroll
-                    for (int i = 0; i < CW / 4; ++i) y[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            if (A.y_bf16) {   // whole rows per warp, staged in the activation tile (the last MMA has read it)
+                st_row_tile<CW>(sA1, row, c0, S, v);
+                __syncthreads();
+                constexpr int CPR = H / 8;   // 16-byte chunks per row (NO == H)
+                const int nrow = (int)(A.n_rows - t * 128 < 128 ? A.n_rows - t * 128 : 128);
+                __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(A.Y) + t * 128 * NO;
+                for (int i = tid; i < nrow * CPR; i += C::NT) {
+                    const int rr = i / CPR, jj = i - rr * CPR;
+                    *reinterpret_cast<uint4*>(y + (int64_t)rr * NO + 8 * jj) =
+                        *reinterpret_cast<const uint4*>(sA1 + tile_off(rr, 8 * jj, 128, S));
                 }
+            } else if (valid) {
+                float4* y = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.Y) + r * NO + c0);
+#pragma unroll
+                for (int i = 0; i < CW / 4; ++i) y[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
         } else {              // NP = 16 output columns, held by column group 0
             if (g == 0) {

@@ -8,7 +8,9 @@ layers. Inputs (x0, e0 from the encoders, a seeded upstream gradient) are
 resident in HBM; the edge state (>400 MB) is larger than L2, so no flush is
 needed between steps. Metric: MP-layer edges/s = 3,149,280 * 4 / step time.
 
-value     -- fused BF16 path (FP32 accumulation and sums), device-timed.
+value     -- fused BF16 path (FP32 accumulation and sums), device-timed; the
+             training step keeps the MLP activations from the forward to the
+             backward (gnn_mp_forward_act / gnn_mp_backward_act).
 fp32      -- the plain FP32 SIMT path on the same graph and step.
 e2e       -- the full network training step through the public API
              (encoders, 4 layers, decoder, consistent loss, backward) with

@@ -92,3 +92,26 @@ def test_row_mlp_activation_size(lib, dims, ln, H):
     # a shape outside the fused row MLP keeps no activations
     wide = _mlp([4, 48, 48, 48], True)
     assert lib.gnn_mlp_act_size_bf16(C.byref(wide), 1000, C.byref(n)) == B.GNN_OK and n.value == 0
+
+
+def test_act_calls_reject_missing_or_misaligned_buffers(lib):
+    # checked before any device work: a NULL or misaligned act where one is needed is GNN_EINVAL
+    part = MeshGraph((5, 4, 3), 3).partition(4, "rcb")
+    H = 64
+    cfg = B.gnn_mp_config()
+    cfg.hidden, cfg.precision, cfg.ln_eps = H, B.GNN_PREC_BF16, 1e-5
+    W = B.gnn_mp_params()
+    W.edge = _mlp([3 * H] + [H] * 4, True)
+    W.node = _mlp([2 * H] + [H] * 4, True)
+    G = _graph_dev(part)
+    for act in (None, FAKE + 8):
+        rc = lib.gnn_mp_forward_act(C.byref(G), C.byref(cfg), C.byref(W), FAKE, FAKE, FAKE + 64, FAKE, FAKE, act,
+                                    FAKE, 1 << 30, None)
+        assert rc == B.GNN_EINVAL
+        rc = lib.gnn_mp_backward_act(C.byref(G), C.byref(cfg), C.byref(W), FAKE, FAKE, FAKE, act, FAKE, None, FAKE,
+                                     FAKE, C.byref(W), FAKE, 1 << 30, None)
+        assert rc == B.GNN_EINVAL
+        m = _mlp([4, H, H, H, H], True)
+        assert lib.gnn_mlp_forward_bf16_act(C.byref(m), 1000, FAKE, FAKE, 1, 1e-5, act, None) == B.GNN_EINVAL
+        assert lib.gnn_mlp_backward_bf16_act(C.byref(m), 1000, FAKE, FAKE, 1, None, C.byref(m), 1e-5, act, FAKE,
+                                             1 << 20, None) == B.GNN_EINVAL

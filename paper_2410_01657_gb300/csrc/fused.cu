@@ -1112,6 +1112,16 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
 
 // ------------------------------------------------------------------ k_node_fwd
 
+// Four floats at (r, c..c+3) of an FP32 node-row tile in the layout of
+// make_f32_tmap boxes (the store counterpart of ld_f32x4_tile).
+template <int H>
+__device__ __forceinline__ void st_f32x4_tile(uint8_t* tile, int r, int c, float4 v) {
+    constexpr int BW = H < 32 ? H : 32, SB = BW * 4;
+    const uint32_t o = (uint32_t)r * SB + (uint32_t)(c % BW) * 4;
+    const uint32_t sw = o ^ (((o >> 7) & (uint32_t)(SB / 16 - 1)) << 4);
+    *reinterpret_cast<float4*>(tile + (uint32_t)(c / BW) * 128 * SB + sw) = v;
+}
+
 struct NodeFwdArgs {
     const float* a_star;
     const float* x;
@@ -1147,7 +1157,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                                                         const __grid_constant__ CUtensorMap tmap_x,
                                                         const __grid_constant__ CUtensorMap tmap_h,
                                                         const __grid_constant__ CUtensorMap tmap_xa,
-                                                        const __grid_constant__ CUtensorMap tmap_dz, NodeFwdArgs A) {
+                                                        const __grid_constant__ CUtensorMap tmap_dz,
+                                                        const __grid_constant__ CUtensorMap tmap_xo, NodeFwdArgs A) {
     static_assert(!(PF && SAVE), "the recomputation reads its inputs directly");
     static_assert(!SAVE || NodeSplit<H>::value, "the recomputation form is the H = 128 one");
     static_assert(!(ASAVE && (SAVE || NodeSplit<H>::value)), "saved activations: the H <= 64 layer forward");
@@ -1231,8 +1242,12 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         if constexpr (PF) {
             ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
             if (!ok) break;
-            // the other stage was read by the previous tile (ordered by its closing barrier)
-            if (tid == 0 && t + gridDim.x < n_tiles) issue(st ^ 1, t + gridDim.x);
+            // the other stage was read by the previous tile (ordered by its closing barrier) and
+            // its x' tile stored (waited for here)
+            if (tid == 0 && t + gridDim.x < n_tiles) {
+                bulk_wait_read_all();
+                issue(st ^ 1, t + gridDim.x);
+            }
 #pragma unroll
             for (int i = 0; i < C::CW / 4; ++i) {   // rows past n_rows read as zero
                 const float4 u = ld_f32x4_tile<H>(sXa(st), row, c0 + 4 * i);
@@ -1382,24 +1397,43 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         row_stats<H, C::CG, C::CW>(v, sRed, row, g, A.eps, mean, rstd);
         const float* gam = sPar + n_lin * H + c0;
         const float* bet = sPar + (n_lin + 1) * H + c0;
-        if (valid) {
-            float4* po = reinterpret_cast<float4*>(A.x_out + r * H + c0);
+        if constexpr (PF) {
+            // x' overwrites the residual x in the stage (each thread its own chunks) and leaves by
+            // TMA stores of the tile's boxes (rows past n_rows are not written)
 #pragma unroll
             for (int i = 0; i < C::CW / 4; ++i) {
-                if constexpr (PF) {   // the residual x from the stage (not kept in registers)
-                    const float4 w = ld_f32x4_tile<H>(sXa(st) + XB, row, c0 + 4 * i);
-                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
-                }
+                const float4 w = ld_f32x4_tile<H>(sXa(st) + XB, row, c0 + 4 * i);
                 float4 o;
-                o.x = xv[4 * i] + (v[4 * i] - mean) * rstd * gam[4 * i] + bet[4 * i];
-                o.y = xv[4 * i + 1] + (v[4 * i + 1] - mean) * rstd * gam[4 * i + 1] + bet[4 * i + 1];
-                o.z = xv[4 * i + 2] + (v[4 * i + 2] - mean) * rstd * gam[4 * i + 2] + bet[4 * i + 2];
-                o.w = xv[4 * i + 3] + (v[4 * i + 3] - mean) * rstd * gam[4 * i + 3] + bet[4 * i + 3];
-                po[i] = o;
+                o.x = w.x + (v[4 * i] - mean) * rstd * gam[4 * i] + bet[4 * i];
+                o.y = w.y + (v[4 * i + 1] - mean) * rstd * gam[4 * i + 1] + bet[4 * i + 1];
+                o.z = w.z + (v[4 * i + 2] - mean) * rstd * gam[4 * i + 2] + bet[4 * i + 2];
+                o.w = w.w + (v[4 * i + 3] - mean) * rstd * gam[4 * i + 3] + bet[4 * i + 3];
+                st_f32x4_tile<H>(sXa(st) + XB, row, c0 + 4 * i, o);
             }
+            fence_proxy_async();   // generic accesses of the stage precede the TMA store and its next load
+            __syncthreads();
+            if (tid == 0) {
+                constexpr int BW = H < 32 ? H : 32;
+#pragma unroll
+                for (int b = 0; b < H / BW; ++b)
+                    tma_store_2d(&tmap_xo, b * BW, (int32_t)(t * 128), sXa(st) + XB + b * 128 * BW * 4);
+                bulk_commit();
+            }
+        } else {
+            if (valid) {
+                float4* po = reinterpret_cast<float4*>(A.x_out + r * H + c0);
+#pragma unroll
+                for (int i = 0; i < C::CW / 4; ++i) {
+                    float4 o;
+                    o.x = xv[4 * i] + (v[4 * i] - mean) * rstd * gam[4 * i] + bet[4 * i];
+                    o.y = xv[4 * i + 1] + (v[4 * i + 1] - mean) * rstd * gam[4 * i + 1] + bet[4 * i + 1];
+                    o.z = xv[4 * i + 2] + (v[4 * i + 2] - mean) * rstd * gam[4 * i + 2] + bet[4 * i + 2];
+                    o.w = xv[4 * i + 3] + (v[4 * i + 3] - mean) * rstd * gam[4 * i + 3] + bet[4 * i + 3];
+                    po[i] = o;
+                }
+            }
+            __syncthreads();
         }
-        if constexpr (PF) fence_proxy_async();   // generic reads of the stage precede its next TMA write
-        __syncthreads();
     }
     if constexpr (SAVE) {
         float* part = A.part + (int64_t)blockIdx.x * A.pstride;
@@ -1407,7 +1441,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
         colsum_store<H, NCH>(accB, sRed, q, lane, c0, tid, C::NT, part + H);
         colsum_store<H, NCH>(accZ, sRed, q, lane, c0, tid, C::NT, part + 2 * H);
     }
-    if ((ASAVE || SAVE) && tid == 0) bulk_wait_all();   // the saved tiles are written before the CTA exits
+    if ((ASAVE || SAVE || PF) && tid == 0) bulk_wait_all();   // the stored tiles are written before the CTA exits
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1567,7 +1601,8 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
     // saved activations: block k of act holds h_k of tile t at rows k * act_rows + t * 128
     // and the BF16 [a*, x] input tiles after them (row t * 128 + i, 2H wide)
     A.act_rows = (NR + 127) / 128 * 128;
-    CUtensorMap tmh = tma, tmxa = tma;
+    CUtensorMap tmh = tma, tmxa = tma, tmxo = tma;
+    if (pf && (rc = make_f32_tmap(&tmxo, x_out, NR, H))) return rc;   // x' leaves by TMA stores
     if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(W.node.n_lin - 1) * A.act_rows, H))) return rc;
     if (act && (rc = make_row_tmap(&tmxa, act + (int64_t)(W.node.n_lin - 1) * A.act_rows * H, A.act_rows, 2 * H)))
         return rc;
@@ -1576,7 +1611,7 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         if (r) return r;
         {
             ProfScope _ps(s, "k_node_fwd");
-            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, tmxa, tma, A);
+            kern<<<grid, C::NT, L.total, s>>>(tma, tmx, tmh, tmxa, tma, tmxo, A);
         }
         GNN_LAUNCH_CHECK("k_node_fwd");
         return GNN_OK;
@@ -1789,7 +1824,7 @@ int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
         return rc;
     {
         ProfScope _ps(s, "k_node_fwd_save");
-        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tmhs, tmxa, tmdz, A);
+        k_node_fwd<H, false, true><<<o.grid, C::NT, L.total, s>>>(tma, tmx, tmhs, tmxa, tmdz, tma, A);
     }
     GNN_LAUNCH_CHECK("k_node_fwd_save");
     return GNN_OK;

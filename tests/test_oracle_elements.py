@@ -152,3 +152,33 @@ def test_consistency_eq2_eq3_mixed_elements(R, how):
     assert abs(LR - L1) <= 1e-13 * abs(L1)
     f1, fR = _flat(g1), _flat(gR)
     assert np.abs(fR - f1).max() <= 1e-11 * np.abs(f1).max()
+
+
+def test_mixed_mesh_recipe_by_loops():
+    # the generator's element lists, rebuilt cell by cell from its documented recipe
+    n, seed, tf, nf = 3, 11, 0.4, 2
+    m = syn.mixed_element_mesh(n, seed, tet_fraction=tf, n_fans=nf)
+    rng = np.random.default_rng(seed)
+    q = n + 1
+    rng.uniform(-0.5, 0.5, size=(q ** 3, 3))          # the jitter draw comes first
+    draw = rng.uniform(size=n ** 3)
+    nodes, pairs, kind = [], [], []
+    for c in range(n ** 3):
+        ci, cj, ck = c % n, (c // n) % n, c // (n * n)
+        hexn = [(ci + (v & 1)) + q * ((cj + ((v >> 1) & 1)) + q * (ck + ((v >> 2) & 1))) for v in range(8)]
+        if draw[c] < tf:
+            for t in syn.kuhn_tets():
+                nodes.append([hexn[v] for v in t]); pairs.append(syn.TET_EDGES); kind.append(1)
+        else:
+            nodes.append(hexn); pairs.append(syn.HEX_EDGES); kind.append(0)
+    for f in range(nf):
+        lo, hi = (f * n) // nf, ((f + 1) * n) // nf
+        top = [i + q * (j + q * n) for i in range(lo, hi + 1) for j in range(q)]
+        nodes.append([q ** 3] + top)
+        pairs.append(np.array([(0, k + 1) for k in range(len(top))], dtype=np.int32)); kind.append(2)
+    assert np.array_equal(m["elem_ptr"], np.concatenate([[0], np.cumsum([len(x) for x in nodes])]))
+    assert np.array_equal(m["elem_nodes"], np.concatenate([np.asarray(x) for x in nodes]))
+    assert np.array_equal(m["edge_ptr"], np.concatenate([[0], np.cumsum([len(x) for x in pairs])]))
+    assert np.array_equal(m["edge_pairs"], np.concatenate(pairs))
+    assert np.array_equal(m["kind"], kind)
+    assert m["pos"].shape == (q ** 3 + 1, 3) and np.allclose(m["pos"][-1], (0.5, 0.5, 1 + 1 / n))

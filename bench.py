@@ -217,14 +217,33 @@ def sgemm_flops_per_step(G, hidden: int, n_lin: int, layers: int) -> float:
     return layers * per_layer_fwd * 4.0     # forward + recompute + dgrad + wgrad
 
 
+def algorithmic_flops_per_step(G, hidden: int, n_lin: int, layers: int, fwd_only: bool = False,
+                               split: bool = True) -> float:
+    """Tensor FLOPs one step of the layer stack must compute (Eq. 5a, 5e).
+
+    Forward, per edge: with the first Linear split (its x_i and x_j blocks
+    applied once per row) the edge MLP costs 2H^2 * n_lin (the e block and the
+    n_lin - 1 hidden Linears); unsplit, 2H^2 * (n_lin + 2). Per row: the node
+    MLP 2H^2 * (n_lin + 1) (its 2H-wide first Linear and the rest), plus the
+    split's two per-row projections, 4H^2. A training step is 3x the forward
+    (forward, input gradients, weight gradients); recomputation is not counted."""
+    E, N, Hh = G.n_edges, G.n_rows, hidden
+    h2 = 2.0 * Hh * Hh
+    edge = h2 * (n_lin if split else n_lin + 2)
+    row = h2 * (n_lin + 1) + (2.0 * h2 if split else 0.0)
+    return (1.0 if fwd_only else 3.0) * layers * (E * edge + N * row)
+
+
 def load_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             d = json.load(fh)
         return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured",
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
                 "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "sm_max_mhz": 2070.0}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback",
+                "sm_max_mhz": 2070.0}
 
 
 # ---------------------------------------------------------------- oracle timing (CPU)
@@ -574,6 +593,17 @@ def main():
         roof = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "peak_src": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock",
                 "share": top_ms / total_ms}
+    tensor = None
+    if precision == "bf16":   # the whole step against the tensor bound (the other side of the roofline max)
+        n_lin = wl.get("nh", NH) + 2
+        fl = algorithmic_flops_per_step(G, Hw, n_lin, M, fwd_only)
+        fl_model = algorithmic_flops_per_step(G, Hw, n_lin, M, fwd_only, split=False)
+        ach_t = fl / (ms * 1e-3) / 1e12
+        tensor = {"bound": "tensor", "achieved": ach_t, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                  "frac": ach_t / peaks["bf16_tflops_sustained"], "flops_per_step": fl,
+                  "model_flops_per_step": fl_model, "peak_src": peaks["src"] + ", bf16 sustained",
+                  "note": "algorithmic FLOPs of the whole step (first Linear split, recompute not counted) "
+                          "over the step time"}
 
     # the cost of consistency: the same stack with Eq. 5c-5d skipped (the paper's "None" layers)
     from paper_2410_01657_gb300 import binding as Bd
@@ -629,7 +659,7 @@ def main():
                            else "eager steps",
                            "parallelism": f"replicas x{world}"},
                 "nodes_per_s": world * n_unpart * M / (ms * 1e-3),
-                "roofline": roof, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu, "inconsistent": inconsistent,
+                "roofline": roof, "tensor": tensor, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu, "inconsistent": inconsistent,
                 "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
                 "clocks": clk.summary()}
         if ms_eager is not None:

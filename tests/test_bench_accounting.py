@@ -1,0 +1,67 @@
+"""The numerators of the bench's roofline figures (CPU only).
+
+FLOPs: counted here Linear by Linear over the MLP shapes of Eq. 5a and 5e
+(2 * in * out per row of each Linear), then checked against the closed forms
+per layer: edge 2H^2 (n_h + 2) with the first Linear split into per-row x_i / x_j
+projections (4H^2 per row), 2H^2 (n_h + 4) unsplit, node 2H^2 (n_h + 3).
+Bytes: the edge forward's least traffic counted field by field."""
+import types
+
+import pytest
+
+import bench
+
+
+def _graph(E, N):
+    return types.SimpleNamespace(n_edges=E, n_rows=N)
+
+
+def _linear_chain(d_in, H, n_lin):
+    dims = [d_in] + [H] * n_lin
+    return sum(2 * dims[k] * dims[k + 1] for k in range(n_lin))
+
+
+@pytest.mark.parametrize("H,n_h", [(16, 2), (32, 5), (64, 2), (128, 2), (64, 0)])
+@pytest.mark.parametrize("fwd_only", [False, True])
+def test_step_flops_by_linear_layers(H, n_h, fwd_only):
+    E, N, layers = 3_149_280 + 12_345, 531_441 + 678, 4
+    n_lin = n_h + 2
+    G = _graph(E, N)
+    edge_unsplit = _linear_chain(3 * H, H, n_lin)
+    edge_split = edge_unsplit - 2 * (2 * H * H)       # the x_i, x_j blocks of the first Linear ...
+    row = _linear_chain(2 * H, H, n_lin) + 2 * (2 * H * H)   # ... move to the rows, once each
+    passes = 1 if fwd_only else 3
+    assert edge_split == 2 * H * H * (n_h + 2) and edge_unsplit == 2 * H * H * (n_h + 4)
+    assert row == 2 * H * H * (n_h + 3) + 4 * H * H
+    got = bench.algorithmic_flops_per_step(G, H, n_lin, layers, fwd_only)
+    assert got == passes * layers * (E * edge_split + N * row)
+    got_model = bench.algorithmic_flops_per_step(G, H, n_lin, layers, fwd_only, split=False)
+    assert got_model == passes * layers * (E * edge_unsplit + N * _linear_chain(2 * H, H, n_lin))
+
+
+def test_c2_edge_forward_sits_below_the_tensor_ridge():
+    # per edge at H = 64, n_h = 2, BF16 edge state: 2H^2 * 4 = 32,768 FLOPs over
+    # 2 * 2H + 8 = 264 bytes, about 124 FLOP/B, under the ridge of the measured
+    # peaks (about 286 FLOP/B): the HBM side of the roofline binds
+    G = _graph(3_149_280, 0)
+    fl = bench.algorithmic_flops_per_step(G, 64, 4, 4, fwd_only=True)
+    by = bench.algorithmic_bytes("k_edge_fwd", G, 64, 2, n_lin=4)
+    assert fl / by == pytest.approx(32768 / 264, rel=1e-12)
+    pk = bench.load_peaks()
+    assert fl / by < pk["bf16_tflops"] * 1e12 / (pk["hbm_gbs"] * 1e9)
+
+
+@pytest.mark.parametrize("se", [2, 4])
+def test_edge_forward_bytes_field_by_field(se):
+    E, N, H, M = 1000, 300, 64, bench.M
+    G = _graph(E, N)
+    per_edge = se * H + se * H + 4 + 4            # e in, e' out, sender index, 1/d_ij
+    per_row = 2 * H * 2 + 4 * H + 4               # P and Q rows (BF16), a (FP32), CSR pointer
+    assert bench.algorithmic_bytes("k_edge_fwd", G, H, se) == M * (E * per_edge + N * per_row)
+    # an inference stack's last layer writes no edge state
+    no_last = bench.algorithmic_bytes("k_edge_fwd", G, H, se, last_layer_no_edge_out=True)
+    assert no_last == pytest.approx(M * (E * per_edge + N * per_row) - E * se * H)
+    # saved activations: the forward also writes h_0 .. h_{L-2} (BF16) of every edge
+    n_lin = 4
+    saved = bench.algorithmic_bytes("k_edge_fwd", G, H, se, n_lin=n_lin, saved_act=True)
+    assert saved == M * (E * per_edge + N * per_row) + M * E * (n_lin - 1) * 2 * H

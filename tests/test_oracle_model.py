@@ -5,13 +5,19 @@ its gradient; closed-form special cases (zero weights, H=1, constant messages
 whose aggregate is the lattice in-degree); a brute-force per-node loop over the
 unpartitioned definition on a tiny graph; permutation equivariance; the
 consistency property Eq. 2 / Eq. 3 (R-way == R=1); and central finite
-differences of the whole network loss."""
+differences of the whole network loss; Table 1's parameter counts pin the
+MLP layout (tests/golden/table1_param_counts.json)."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
 
 import synthetic as syn
 from oracle import graph, model
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _torch_mlp(P):
@@ -74,6 +80,30 @@ def test_mlp_special_cases():
     # ELU: identity above 0, e^z - 1 below
     z = np.array([-3.0, -1e-3, 0.0, 2.5])
     np.testing.assert_allclose(model.elu(z), [np.exp(-3) - 1, np.exp(-1e-3) - 1, 0.0, 2.5], rtol=1e-12)
+
+
+def _array_sizes(tree):
+    if isinstance(tree, np.ndarray):
+        return tree.size
+    if isinstance(tree, dict):
+        return sum(_array_sizes(v) for v in tree.values())
+    return sum(_array_sizes(v) for v in tree)
+
+
+def test_table1_parameter_counts():
+    # Table 1: 3 node inputs, 3 outputs; (H, layers, MLP hidden layers) -> trainable parameters
+    g = json.load(open(os.path.join(GOLD, "table1_param_counts.json")))
+    for key in ("small", "large"):
+        c = g[key]
+        p = syn.gnn_params(0, c["hidden"], c["mlp_hidden_layers"], c["n_layers"])
+        assert _array_sizes(p) == c["params"], key
+        assert model.network_param_count(p) == c["params"], key
+        # the counts single out this layout among the plausible readings
+        for kw in ({"f_e": 7}, {"f_e": 3}):   # the text's 7 edge inputs; positions alone
+            assert model.network_param_count(
+                syn.gnn_params(0, c["hidden"], c["mlp_hidden_layers"], c["n_layers"], **kw)) != c["params"]
+        for n_h in (c["mlp_hidden_layers"] - 1, c["mlp_hidden_layers"] + 1):   # Linears counted differently
+            assert model.network_param_count(syn.gnn_params(0, c["hidden"], n_h, c["n_layers"])) != c["params"]
 
 
 def _constant_message_layer(rng, H, c):

@@ -18,6 +18,8 @@ e2e       -- the full network training step through the public API
              back, in the same metric.
 roofline  -- the dominant kernel's algorithmic bytes (or FLOPs) per launch over
              its CUDA-event launch time, against MEASURED_PEAKS.json.
+tensor    -- the whole step's algorithmic FLOPs over the step time, against
+             the sustained BF16 peak of MEASURED_PEAKS.json.
 cpu_baseline -- the FP64 numpy oracle on a bounded sample, host cores.
 
 ``--workload`` selects the other graph families (c3: 32^3 p=7 H=128 fwd+bwd,
@@ -61,7 +63,7 @@ WORKLOADS = {
     "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=False,
                desc="48^3 elements p=7 GLL brick, 16 RCB sub-graphs, inference: last layer writes no edge state"),
     "mixed": dict(nel=64, p=1, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False, mesh="mixed",
-                  cells="cells", sample=24, ref_sample=16,
+                  cells="cells", sample=32, ref_sample=16,
                   desc="mixed element mesh of the unit cube (each cell one hexahedron or its 6 Kuhn tetrahedra, "
                        "drawn 50/50) with 8 fan cells on one apex of in-degree 4,225, held as co-resident copies "
                        "of <= 128 in-edges, 8 RCB sub-graphs"),
@@ -638,8 +640,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         # a bounded sample of the same workload family: a small brick of the same order,
-        # width, partition count and pass (about 5-20 s of host time)
-        n_s = wl.get("sample") or {5: 6, 7: 4}[wl["p"]]
+        # width, partition count and pass (about 10-20 s of host time on 16 cores)
+        n_s = wl.get("sample") or {5: 8, 7: 5}[wl["p"]]
         v, tsec, desc, threads = oracle_sample(n_s, p=wl["p"], hidden=Hw, parts=wl["parts"] if wl["parts"] <= 16 else 8,
                                                fwd_only=fwd_only, nh=wl.get("nh", NH), mesh=wl.get("mesh", "brick"))
         cpu = {"value": v, "unit": "edges/s", "cores": threads, "kind": "oracle", "sample": desc,

@@ -1,0 +1,133 @@
+"""The benchmarked training step at full size against the FP64 oracle on
+sampled nodes (needs a GB300).
+
+The graph, partition, model and launch configuration are the benchmark's: the
+16^3-element p=5 GLL brick (531,441 nodes, 3,149,280 directed edges) in 8 RCB
+sub-graphs, four consistent layers of width 64 with 2 MLP hidden layers, BF16
+fused path with the MLP activations kept from the forward to the backward. The
+inputs are seeded: a state per global node and per directed global edge (so the
+copies of a node or edge agree) and an upstream gradient per row. One step runs
+on the GPU; the oracle evaluates the same four layers on the ball of 2M + 1 = 9
+hops around each sampled node, which gives that node's values exactly (the
+sampling is checked on the CPU in test_oracle_ball.py). Compared: x_4 on every
+copy of a sampled node, e_4 on every copy of its in-edges, and dL/dx_0, dL/de_0
+summed over the copies; relative L2 over the sample, BF16 tolerances (outputs
+2e-2, gradients 5e-2). The sample holds nodes with 1, 2, 4 and 8 copies."""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import synthetic as syn
+from oracle import graph as og
+from paper_2410_01657_gb300 import _build
+from paper_2410_01657_gb300 import binding as B
+from paper_2410_01657_gb300 import nn as gnn
+
+from ball_util import check_sample, neighbour_csr
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    B.load()
+
+
+class _Rows:
+    """Rows of a host tensor as float64 numpy, indexed on demand."""
+
+    def __init__(self, t):
+        self.t = t
+
+    def __getitem__(self, idx):
+        return self.t[torch.as_tensor(np.asarray(idx, dtype=np.int64))].double().numpy()
+
+
+def _sample_ids(L: int, rng) -> list:
+    m = L // 2
+    lid = lambda i, j, k: i + L * (j + L * k)
+    fixed = [lid(m, m, m), lid(m, m, 10), lid(m, 10, 10), lid(0, 0, 0), lid(L - 1, m, 20), lid(3, L - 1, m)]
+    return fixed + [int(v) for v in rng.choice(L ** 3, 6, replace=False)]
+
+
+def _compare(params, b, samples, ed_rows, gid, ekey, node_deg, x0g, e0g, dx_glob, xM, eM, dx0, de0):
+    """(got, ref) of x_M, e_M, dL/dx_0, dL/de_0 over the sampled nodes; eM and
+    de0 hold the rows of ed_rows (concatenated), xM and dx0 every row."""
+    N = b.n_nodes
+    ptr, nbr = neighbour_csr(N, b.recv, b.send)
+    got = {k: [] for k in ("x", "e", "dx", "de")}
+    ref = {k: [] for k in ("x", "e", "dx", "de")}
+    o = 0
+    for k, rows_e in zip(samples, ed_rows):
+        s = check_sample(params["layers"], N, b.recv, b.send, ptr, nbr, k, x0g, e0g, dx_glob)
+        rows = np.nonzero(gid == k)[0]
+        assert rows.size == node_deg[rows[0]]
+        for r in rows:
+            got["x"].append(xM[r])
+            ref["x"].append(s["x"])
+        got["dx"].append(dx0[rows].sum(axis=0))
+        ref["dx"].append(s["dx"])
+        pos = np.searchsorted(s["eid"], ekey[rows_e])
+        assert np.array_equal(s["eid"][pos], ekey[rows_e]) and np.unique(pos).size == s["eid"].size
+        n = rows_e.size
+        got["e"].append(eM[o:o + n])
+        ref["e"].append(s["e"][pos])
+        de_sum = np.zeros_like(s["de"])
+        np.add.at(de_sum, pos, de0[o:o + n])
+        got["de"].append(de_sum)
+        ref["de"].append(s["de"])
+        o += n
+    assert o == eM.shape[0]
+    return {k: (np.vstack(got[k]), np.vstack(ref[k])) for k in got}
+
+
+def test_c2_training_step_sampled_vs_oracle():
+    wl = bench.WORKLOADS["c2"]
+    H, M, NH = wl["H"], bench.M, bench.NH
+    part, nel, N, E = bench.workload_graph(wl, None)
+    b = og.build_brick((nel,) * 3, wl["p"])
+    assert (b.n_nodes, b.n_edges) == (N, E) == (531_441, 3_149_280)
+    gid = part.array("row_gid")
+    recv_gid = gid[part.receivers()]
+    ekey = np.searchsorted(b.recv * N + b.send, recv_gid * N + gid[part.array("col")])
+    node_deg = part.array("node_deg")
+
+    rng = np.random.default_rng(11)
+    x0g = rng.standard_normal((N, H)).astype(np.float32)
+    e0g = torch.from_numpy(rng.standard_normal((E, H), dtype=np.float32)).to(torch.bfloat16)
+    dx_rows = rng.standard_normal((part.n_rows, H), dtype=np.float32)
+    dx_glob = torch.zeros(N, H, dtype=torch.float64).index_add_(
+        0, torch.from_numpy(gid), torch.from_numpy(dx_rows).double()).numpy()
+
+    # the GPU step, as the benchmark runs it
+    G = part.to_device(DEV)
+    params = syn.gnn_params(bench.SEED, H, NH, M)
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
+    x0 = torch.from_numpy(x0g[gid]).to(DEV)
+    e0 = e0g.to(DEV)[torch.from_numpy(ekey).to(DEV)]
+    stack = gnn.LayerStack(G, layers, H, "bf16", x0, e0)
+    assert all(a is not None for a in stack.act)
+    stack.step(torch.from_numpy(dx_rows).to(DEV))
+    torch.cuda.synchronize()
+    B.call("gnn_check", None)
+
+    samples = _sample_ids(nel * wl["p"] + 1, np.random.default_rng(12))
+    assert {1, 2, 4, 8} <= {int(node_deg[gid == k][0]) for k in samples}
+    ed_rows = [np.nonzero(recv_gid == k)[0] for k in samples]
+    idx = torch.from_numpy(np.concatenate(ed_rows)).to(DEV)
+    eM = stack.e[M][idx].float().cpu().numpy().astype(np.float64)
+    de0 = stack.de[0][idx].float().cpu().numpy().astype(np.float64)
+    xM = stack.x[M].cpu().numpy().astype(np.float64)
+    dx0 = stack.dx[0].cpu().numpy().astype(np.float64)
+
+    pairs = _compare(params, b, samples, ed_rows, gid, ekey, node_deg, x0g.astype(np.float64), _Rows(e0g),
+                     dx_glob, xM, eM, dx0, de0)
+    err = {k: rel_l2(g, r) for k, (g, r) in pairs.items()}
+    print("\nC2 full size, sampled rel-L2:", {k: f"{v:.2e}" for k, v in err.items()})
+    assert err["x"] < 2e-2 and err["e"] < 2e-2, err
+    assert err["dx"] < 5e-2 and err["de"] < 5e-2, err

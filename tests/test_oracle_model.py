@@ -233,6 +233,27 @@ def _flat(g):
     return np.concatenate([x.ravel() for x in parts])
 
 
+@pytest.mark.parametrize("R", [1, 3, 8])
+def test_consistent_loss_is_the_global_mse(R):
+    # Eq. 8: with every copy holding its node's value, the 1/d_i weights and
+    # N_eff = sum 1/d_i turn the per-rank sums into the plain mean squared
+    # error over the unique nodes; the loss gradient summed over a node's
+    # copies is 2 (y - t) / (N F)
+    b = graph.build_brick((4, 3, 5), 2)
+    subs = graph.build_subgraphs(b, graph.partition_rcb(b, R), R) if R > 1 else graph.unpartitioned(b)
+    rng = np.random.default_rng(9)
+    y, t = rng.standard_normal((b.n_nodes, 3)), rng.standard_normal((b.n_nodes, 3))
+    ys, ts = [y[sg.gid] for sg in subs], [t[sg.gid] for sg in subs]
+    assert abs(model.consistent_loss(subs, ys, ts) - np.mean((y - t) ** 2)) < 1e-14
+    g = np.zeros_like(y)
+    for sg, gr in zip(subs, model.consistent_loss_grad(subs, ys, ts)):
+        np.add.at(g, sg.gid, gr)
+    np.testing.assert_allclose(g, 2 * (y - t) / y.size, rtol=1e-12, atol=1e-15)
+    if R > 1:   # the weights matter: without them, shared nodes count several times
+        plain = sum(float(((a - c) ** 2).sum()) for a, c in zip(ys, ts)) / (sum(sg.n_local for sg in subs) * 3)
+        assert abs(plain - np.mean((y - t) ** 2)) > 1e-6
+
+
 @pytest.mark.parametrize("R,method,weights", [(2, "slab", None), (8, "rcb", None),
                                               (5, "rcb", [2, 1, 1, 3, 1])])
 def test_consistency_eq2_eq3(R, method, weights):

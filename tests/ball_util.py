@@ -44,7 +44,7 @@ def ball(ptr: np.ndarray, nbr: np.ndarray, centre: int, radius: int) -> np.ndarr
 
 
 def stack_on_nodes(layers: list, N: int, recv: np.ndarray, send: np.ndarray, nodes: np.ndarray,
-                   x0: np.ndarray, e0: np.ndarray, dx_top: np.ndarray):
+                   x0: np.ndarray, e0: np.ndarray, dx_top: np.ndarray, backward: bool = True):
     """Forward and adjoint of the layers on the sub-graph induced by `nodes`.
 
     recv/send: the global directed edges, sorted by recv * N + send (the edge
@@ -60,18 +60,23 @@ def stack_on_nodes(layers: list, N: int, recv: np.ndarray, send: np.ndarray, nod
     for lp in layers:
         xs, es, c = om.layer_forward(lp, [sub], xs, es)
         caches.append(c)
+    if not backward:
+        return eid, xs[0], es[0], None, None
     dx, de = [dx_top[nodes]], [np.zeros_like(es[0])]
     for lp, c in zip(reversed(layers), reversed(caches)):
         dx, de, _ = om.layer_backward(lp, [sub], c, dx, de)
     return eid, xs[0], es[0], dx[0], de[0]
 
 
-def check_sample(layers, N, recv, send, ptr, nbr, centre, x0, e0, dx_top):
+def check_sample(layers, N, recv, send, ptr, nbr, centre, x0, e0, dx_top, grads: bool = True):
     """Exact (up to rounding) oracle values at one centre node: x_M and dL/dx_0
-    of the node, and e_M and dL/de_0 of its in-edges (global edge ids)."""
+    of the node, and e_M and dL/de_0 of its in-edges (global edge ids). With
+    grads=False the ball has M hops, enough for x_M and e_M only."""
     M = len(layers)
-    nodes = ball(ptr, nbr, centre, 2 * M + 1)
-    eid, xM, eM, dx0, de0 = stack_on_nodes(layers, N, recv, send, nodes, x0, e0, dx_top)
+    nodes = ball(ptr, nbr, centre, 2 * M + 1 if grads else M)
+    eid, xM, eM, dx0, de0 = stack_on_nodes(layers, N, recv, send, nodes, x0, e0, dx_top, backward=grads)
     k = int(np.searchsorted(nodes, centre))
     mine = recv[eid] == centre
+    if not grads:
+        return {"x": xM[k], "eid": eid[mine], "e": eM[mine]}
     return {"x": xM[k], "dx": dx0[k], "eid": eid[mine], "e": eM[mine], "de": de0[mine]}

@@ -131,3 +131,68 @@ def test_c2_training_step_sampled_vs_oracle():
     print("\nC2 full size, sampled rel-L2:", {k: f"{v:.2e}" for k, v in err.items()})
     assert err["x"] < 2e-2 and err["e"] < 2e-2, err
     assert err["dx"] < 5e-2 and err["de"] < 5e-2, err
+
+
+def test_mixed_mesh_training_step_sampled_vs_oracle():
+    # the benchmark's mixed-element mesh (64^3 cells, hexahedra and Kuhn
+    # tetrahedra, 8 fan cells on one apex of in-degree 4,225 held as co-resident
+    # copy rows), 8 RCB parts, the same stack; the apex is checked forward (its
+    # M-hop ball), three nodes at least 2M + 2 hops below the fans forward and
+    # backward
+    wl = bench.WORKLOADS["mixed"]
+    H, M, NH = wl["H"], bench.M, bench.NH
+    part, n, N, E = bench.workload_graph(wl, None)
+    m = syn.mixed_element_mesh(n, bench.SEED, n_fans=8)
+    mesh = og.element_mesh(m["pos"], m["elem_ptr"], m["elem_nodes"], m["edge_ptr"], m["edge_pairs"])
+    assert (mesh.n_nodes, mesh.n_edges) == (N, E)
+    gid = part.array("row_gid")
+    recv_gid = gid[part.receivers()]
+    ekey = np.searchsorted(mesh.recv * N + mesh.send, recv_gid * N + gid[part.array("col")])
+    node_deg = part.array("node_deg")
+    hub = N - 1
+    assert int((recv_gid == hub).sum()) >= 4225 and int((gid == hub).sum()) > 1
+
+    rng = np.random.default_rng(13)
+    x0g = rng.standard_normal((N, H)).astype(np.float32)
+    e0g = torch.from_numpy(rng.standard_normal((E, H), dtype=np.float32)).to(torch.bfloat16)
+    dx_rows = rng.standard_normal((part.n_rows, H), dtype=np.float32)
+    dx_glob = torch.zeros(N, H, dtype=torch.float64).index_add_(
+        0, torch.from_numpy(gid), torch.from_numpy(dx_rows).double()).numpy()
+
+    G = part.to_device(DEV)
+    params = syn.gnn_params(bench.SEED, H, NH, M)
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
+    stack = gnn.LayerStack(G, layers, H, "bf16", torch.from_numpy(x0g[gid]).to(DEV),
+                           e0g.to(DEV)[torch.from_numpy(ekey).to(DEV)])
+    assert all(a is not None for a in stack.act)
+    stack.step(torch.from_numpy(dx_rows).to(DEV))
+    torch.cuda.synchronize()
+    B.call("gnn_check", None)
+
+    q = n + 1
+    low = np.random.default_rng(14).choice(q * q * (n - 2 * M - 1), 2, replace=False)
+    samples = [q // 2 + q * (q // 2 + q * (q // 2))] + [int(v) for v in low]
+    ed_rows = [np.nonzero(recv_gid == k)[0] for k in samples]
+    idx = torch.from_numpy(np.concatenate(ed_rows)).to(DEV)
+    x0d = x0g.astype(np.float64)
+    pairs = _compare(params, mesh, samples, ed_rows, gid, ekey, node_deg, x0d, _Rows(e0g), dx_glob,
+                     stack.x[M].cpu().numpy().astype(np.float64),
+                     stack.e[M][idx].float().cpu().numpy().astype(np.float64),
+                     stack.dx[0].cpu().numpy().astype(np.float64),
+                     stack.de[0][idx].float().cpu().numpy().astype(np.float64))
+    err = {k: rel_l2(g, r) for k, (g, r) in pairs.items()}
+
+    # the apex: every copy row's x_M, every in-edge's e_M
+    s = check_sample(params["layers"], N, mesh.recv, mesh.send, *neighbour_csr(N, mesh.recv, mesh.send), hub,
+                     x0d, _Rows(e0g), dx_glob, grads=False)
+    rows, rows_e = np.nonzero(gid == hub)[0], np.nonzero(recv_gid == hub)[0]
+    assert rows.size == node_deg[rows[0]]
+    pos = np.searchsorted(s["eid"], ekey[rows_e])
+    assert np.array_equal(s["eid"][pos], ekey[rows_e]) and np.unique(pos).size == s["eid"].size == 4225
+    eh = stack.e[M][torch.from_numpy(rows_e).to(DEV)].float().cpu().numpy().astype(np.float64)
+    err["x_apex"] = rel_l2(stack.x[M][torch.from_numpy(rows).to(DEV)].cpu().numpy(), np.tile(s["x"], (rows.size, 1)))
+    err["e_apex"] = rel_l2(eh, s["e"][pos])
+    print("\nmixed mesh full size, sampled rel-L2:", {k: f"{v:.2e}" for k, v in err.items()})
+    assert max(err["x"], err["e"], err["x_apex"], err["e_apex"]) < 2e-2, err
+    assert err["dx"] < 5e-2 and err["de"] < 5e-2, err

@@ -66,3 +66,6 @@ def test_smaller_ball_misses_gradient_terms(case):
     k = int(np.searchsorted(nodes, c))
     np.testing.assert_allclose(xs[k], xM[c], rtol=1e-12, atol=1e-12)   # M hops: the forward is exact
     assert np.abs(dxs[k] - dx0[c]).max() > 1e-6 * np.abs(dx0[c]).max()
+    s = check_sample(layers, b.n_nodes, b.recv, b.send, ptr, nbr, c, x0, e0, dx_top, grads=False)
+    np.testing.assert_allclose(s["x"], xM[c], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(s["e"], eM[s["eid"]], rtol=1e-12, atol=1e-12)

@@ -65,3 +65,25 @@ def test_edge_forward_bytes_field_by_field(se):
     n_lin = 4
     saved = bench.algorithmic_bytes("k_edge_fwd", G, H, se, n_lin=n_lin, saved_act=True)
     assert saved == M * (E * per_edge + N * per_row) + M * E * (n_lin - 1) * 2 * H
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm is the oracle on the host cores: it runs here, without a GPU
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "edges/s" and d["higher_is_better"] is True
+    assert d["metric"] == "MP-layer edges/s fwd+bwd" and d["value"] > 0 and d["steps"] == 1
+    assert "3,149,280 edges" in d["config"]["workload"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -1,32 +1,40 @@
 #!/usr/bin/env python
 """Throughput of the consistent NMP layer (forward + backward) on one GB300.
 
-One step = M=4 consistent NMP layers forward (Eq. 5a-5e) then their adjoint,
-on the 16^3-element p=5 GLL brick (531,441 nodes, 3,149,280 directed edges)
-split into 8 RCB sub-graphs resident on the GPU, H=64, MLPs with 2 hidden
-layers. Inputs (x0, e0 from the encoders, a seeded upstream gradient) are
-resident in HBM; the edge state (>400 MB) is larger than L2, so no flush is
-needed between steps. Metric: MP-layer edges/s = 3,149,280 * 4 / step time.
+One step = M=4 consistent NMP layers forward (Eq. 5a-5e) then their adjoint
+(Eq. 3), recomputing each layer's MLP activations in the backward. The
+default workload is the precision form: the 32^3-element p=7 GLL brick
+(11,390,625 nodes, 68,040,000 directed edges) split into 8 RCB sub-graphs
+resident on the GPU, H=128, MLPs with 2 hidden layers, BF16 GEMM operands with
+FP32 accumulation and FP32 sums. The layer inputs x0, e0 come from the node
+and edge encoders on a 32-mode Fourier field; they and a seeded upstream
+gradient are resident in HBM, and the edge state (17 GB) is far larger than
+L2, so no flush is needed between steps. Metric: MP-layer edges/s =
+68,040,000 * 4 / step time, the step time being the median of K CUDA-graph
+replays, each timed by its own CUDA events with no profiler running.
 
-value     -- fused BF16 path (FP32 accumulation and sums), device-timed; the
-             training step keeps the MLP activations from the forward to the
-             backward (gnn_mp_forward_act / gnn_mp_backward_act).
-fp32      -- the plain FP32 SIMT path on the same graph and step.
+value     -- fused BF16 path, device-timed (median replay).
+roofline  -- the whole step's algorithmic HBM bytes per unit of work (the
+             per-edge and per-node figures of the method's forward and
+             adjoint, no scratch or saved activations) over the step time,
+             against the measured HBM peak, beside the tensor-FLOP side; the
+             slower side is the bound. roofline_kernel: the dominant kernel's
+             event-timed launches against the bytes it moves as designed.
+fp32      -- the plain FP32 SIMT path against the fused BF16 path on the same
+             graph (for the H=128 brick, on a 16^3-element p=7 sub-brick:
+             the plain path's FP32 per-edge workspace does not fit the
+             full graph).
 e2e       -- the full network training step through the public API
-             (encoders, 4 layers, decoder, consistent loss, backward) with
-             inputs copied from pinned host memory each step and the loss read
-             back, in the same metric.
-roofline  -- the dominant kernel's algorithmic bytes (or FLOPs) per launch over
-             its CUDA-event launch time, against MEASURED_PEAKS.json.
-tensor    -- the whole step's algorithmic FLOPs over the step time, against
-             the sustained BF16 peak of MEASURED_PEAKS.json.
+             (encoders, 4 layers, decoder, consistent loss, backward) with the
+             node field and target copied from pinned host memory each step
+             and the loss read back, in the same metric.
 cpu_baseline -- the FP64 numpy oracle on a bounded sample, host cores.
 
-``--workload`` selects the other graph families (c3: 32^3 p=7 H=128 fwd+bwd,
-``--mode fwd`` for its inference form;
-c4: 64 uneven sub-graphs of a jittered p=5 brick, H=64 fwd+bwd, autotuned and
-replayed as a CUDA graph; c5: 48^3 p=7 H=32 inference); their layer inputs
-are seeded random states drawn on the device, and they report no fp32/e2e leg.
+``--workload`` selects the other graph families (c2: 16^3 p=5 H=64; c4: 64
+uneven sub-graphs of a jittered p=5 brick, H=64, autotuned; c5: 48^3 p=7 H=32
+inference; large; mixed). ``--save-act`` runs the H <= 64 training step with
+the MLP activations kept from the forward (an option; the default
+recomputes).
 
 ``--impl reference`` times the oracle alone (the reference arm).
 """
@@ -53,21 +61,21 @@ SEED = 0
 #   inputs "random":   seeded N(0,1) layer states drawn on the device (the
 #                      encoders' FP32 workspace would not fit beside them)
 WORKLOADS = {
-    "c2": dict(nel=16, p=5, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False,
+    "c2": dict(nel=16, p=5, parts=8, H=64, mode="fwdbwd", inputs="encoders", modes=8, graph=True,
                desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs"),
-    "c3": dict(nel=32, p=7, parts=8, H=128, mode="fwdbwd", inputs="random", graph=False,
+    "c3": dict(nel=32, p=7, parts=8, H=128, mode="fwdbwd", inputs="encoders", modes=32, graph=True, fp32_nel=16,
                desc="32^3 elements p=7 GLL brick, 8 RCB sub-graphs, the precision form (H=128)"),
     "c4": dict(nel=None, p=5, parts=64, H=64, mode="fwdbwd", inputs="random", graph=True, uneven=True,
                desc="jittered p=5 brick in 64 RCB sub-graphs of log-uniform element counts in [50, 5000], "
                     "CUDA graph, autotuned tiles"),
-    "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=False,
+    "c5": dict(nel=48, p=7, parts=16, H=32, mode="fwd", inputs="random", graph=True,
                desc="48^3 elements p=7 GLL brick, 16 RCB sub-graphs, inference: last layer writes no edge state"),
-    "mixed": dict(nel=64, p=1, parts=8, H=64, mode="fwdbwd", inputs="encoders", graph=False, mesh="mixed",
+    "mixed": dict(nel=64, p=1, parts=8, H=64, mode="fwdbwd", inputs="encoders", modes=8, graph=True, mesh="mixed",
                   cells="cells", sample=32, ref_sample=16,
                   desc="mixed element mesh of the unit cube (each cell one hexahedron or its 6 Kuhn tetrahedra, "
                        "drawn 50/50) with 8 fan cells on one apex of in-degree 4,225, held as co-resident copies "
                        "of <= 128 in-edges, 8 RCB sub-graphs"),
-    "large": dict(nel=16, p=5, parts=8, H=32, nh=5, mode="fwdbwd", inputs="encoders", graph=False,
+    "large": dict(nel=16, p=5, parts=8, H=32, nh=5, mode="fwdbwd", inputs="encoders", modes=8, graph=True,
                   desc="16^3 elements p=5 GLL brick, 8 RCB sub-graphs, the paper's large model (Table 1: "
                        "H=32, 5 MLP hidden layers)"),
 }
@@ -82,14 +90,16 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwdbwd", "fwd"],
                     help="fwd: forward only (inference form of the layer stack)")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                    help="c2 (default): 16^3 p=5 H=64 fwd+bwd; c3: 32^3 p=7 H=128 fwd+bwd; c4: 64 uneven jittered "
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
+                    help="c3 (default): 32^3 p=7 H=128 fwd+bwd; c2: 16^3 p=5 H=64 fwd+bwd; c4: 64 uneven jittered "
                          "sub-graphs H=64 fwd+bwd; c5: 48^3 p=7 H=32 inference; large: the C2 graph with the "
                          "paper's large model (H=32, 5 MLP hidden layers); mixed: a 64^3-cell mesh of mixed "
                          "element types with a node of in-degree 4,225, H=64 fwd+bwd")
     ap.add_argument("--nel", type=int, default=None,
                     help="elements per axis of the brick (default: the workload's; smaller for profiling)")
-    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step")
+    ap.add_argument("--eager", action="store_true", help="time eager steps instead of CUDA-graph replays")
+    ap.add_argument("--save-act", action="store_true",
+                    help="H <= 64 training: keep the MLP activations from the forward (default: recompute)")
     ap.add_argument("--autotune", action="store_true", help="autotune tiles and the edge forward first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -146,25 +156,78 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 
-def algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False,
-                      n_lin: int = NH + 2, saved_act: bool = False):
-    """Least HBM bytes all launches of a kernel move in one step of M layers
-    (for the edge forward of an inference stack the last layer writes no edge
-    state; with saved activations the edge forward also writes, and the edge
-    adjoint reads, h_0 .. h_{L-2} of every edge, and the adjoint gathers no P|Q)."""
+def method_bytes_per_step(n_edges: int, n_rows: int, hidden: int, edge_bytes: int, layers: int = M,
+                          fwd_only: bool = False, last_layer_no_edge_out: bool = False) -> float:
+    """Least HBM bytes one step of the layer stack must move: the method's
+    per-unit figures, not this implementation's traffic.
+
+    Forward, per layer: per edge read e and write e' (2 s_e H), its sender
+    index (4) and multiplicity (1); per node read and write x (FP32), write and
+    read a* (FP32) and the CSR pointer (16H + 4). The adjoint adds per edge read
+    e_in and read/write FP32 edge gradients (s_e H + 8H + 5) and per node about
+    28H (x, a* and their gradients in and out). No scratch, saved activation or
+    recomputed row is counted. Units are the partitioned rows and edges the
+    sub-graphs hold (halo copies are rows the method processes)."""
+    E, N, Hh, se = n_edges, n_rows, hidden, edge_bytes
+    fwd = E * (2 * se * Hh + 5) + N * (16 * Hh + 4)
+    if fwd_only:
+        return layers * fwd - (E * se * Hh if last_layer_no_edge_out else 0)
+    bwd = E * (se * Hh + 8 * Hh + 5) + N * 28 * Hh
+    return layers * (fwd + bwd)
+
+
+def step_roofline(step_ms: float, n_edges: int, n_rows: int, hidden: int, edge_bytes: int, n_lin: int,
+                  fwd_only: bool, peaks: dict, last_layer_no_edge_out: bool = False) -> dict:
+    """The whole step against both sides of the roofline: HBM (method bytes over
+    the measured copy bandwidth) and tensor (algorithmic FLOPs over the measured
+    sustained BF16 GEMM rate); the slower side is the bound."""
+    by = method_bytes_per_step(n_edges, n_rows, hidden, edge_bytes, M, fwd_only, last_layer_no_edge_out)
+    G = _Units(n_edges, n_rows)
+    fl = algorithmic_flops_per_step(G, hidden, n_lin, M, fwd_only)
+    t_hbm = by / (peaks["hbm_gbs"] * 1e9)
+    t_ten = fl / (peaks["bf16_tflops_sustained"] * 1e12)
+    t = step_ms * 1e-3
+    if t_hbm >= t_ten:
+        out = {"bound": "hbm", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        out = {"bound": "tensor", "achieved": fl / t / 1e12, "peak": peaks["bf16_tflops_sustained"],
+               "unit": "TFLOP/s"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out.update({"scope": "whole step (all launches of the 4-layer fwd+bwd step)" if not fwd_only
+                else "whole step (all launches of the 4-layer forward)",
+                "bytes_per_step": by, "flops_per_step": fl, "bound_ms": max(t_hbm, t_ten) * 1e3,
+                "hbm_ms": t_hbm * 1e3, "tensor_ms": t_ten * 1e3,
+                "tensor_frac": fl / t / 1e12 / peaks["bf16_tflops_sustained"],
+                "hbm_frac": by / t / 1e9 / peaks["hbm_gbs"],
+                "peak_src": peaks["src"] + " (HBM copy; BF16 GEMM sustained)"})
+    return out
+
+
+class _Units:
+    def __init__(self, n_edges, n_rows):
+        self.n_edges, self.n_rows = n_edges, n_rows
+
+
+def design_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool = False,
+                 n_lin: int = NH + 2, saved_act: bool = False):
+    """HBM bytes all launches of a kernel move in one step of M layers as this
+    implementation is designed (its inputs, outputs and scratch each once): the
+    yardstick of how close a kernel runs to its own streaming time. Unlike
+    ``method_bytes_per_step`` this counts the P|Q rows of the split first
+    Linear, the H = 128 adjoint's scratch rows and, with saved activations, the
+    stored h_0 .. h_{L-2}."""
     E, N = G.n_edges, G.n_rows
     h2 = 2 * hidden
     if saved_act and kernel == "k_edge_fwd":
-        return (algorithmic_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
+        return (design_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
                 + M * E * (n_lin - 1) * h2)
     if saved_act and kernel == "k_edge_bwd":   # e, de_out in, de_in, dz1 out, col, w, h_0..h_{L-2}; da in, dP out
         return M * (E * (4 * edge_bytes * hidden + 8 + (n_lin - 1) * h2) + N * (2 * 4 * hidden + 4))
-    return _algorithmic_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
+    return _design_bytes(kernel, G, hidden, edge_bytes, last_layer_no_edge_out, n_lin)
 
 
-def _algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool,
-                       n_lin: int):
-    """Recompute form of ``algorithmic_bytes``.
+def _design_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_no_edge_out: bool, n_lin: int):
+    """Recompute form of ``design_bytes``.
 
     Per edge: read e (s_e H), write e' (s_e H), col (4), 1/d (4); per row:
     the row's CSR pointer and node tensors (see the per-kernel notes). The
@@ -191,20 +254,25 @@ def _algorithmic_bytes(kernel: str, G, hidden: int, edge_bytes: int, last_layer_
     return None
 
 
-def measured_traffic(kernel: str, n_edges: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, scaled by
-    the edge count; None when the kernel sources changed since the capture."""
+def measured_traffic(workload: str, kernels: list, n_edges: int):
+    """DRAM bytes of one step of the listed kernels (sum over their launches)
+    from the committed ncu capture of the workload's family, scaled by the
+    partitioned edge count; None when the kernel sources changed since the
+    capture or a kernel is missing from it."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "edge_kernel_traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", f"step_traffic_{workload}.json")) as fh:
             d = json.load(fh)
         h = hashlib.sha256()
         for f in d["sources_hashed"]:
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
-        if h.hexdigest() != d["source_hash"] or kernel not in d["bytes_per_edge"]:
+        if h.hexdigest() != d["source_hash"]:
             return None
-        return d["bytes_per_edge"][kernel] * n_edges
+        per = d["bytes_per_edge_per_step"]
+        if any(k not in per for k in kernels):
+            return None
+        return {k: per[k] * n_edges for k in kernels}
     except (OSError, KeyError, ValueError):
         return None
 
@@ -411,7 +479,7 @@ def workload_graph(wl: dict, nel):
     return part, n, L ** 3, 6 * L * L * (L - 1)
 
 
-def build_problem(dev, precision, wl: dict, part):
+def build_problem(dev, precision, wl: dict, part, save_act: bool = False):
     import torch
 
     import synthetic as syn
@@ -423,7 +491,7 @@ def build_problem(dev, precision, wl: dict, part):
     net = gnn.ConsistentGNN(params, precision=precision, device=dev)
     u = t = None
     if wl["inputs"] == "encoders":
-        modes = syn.fourier_modes(SEED, 8)
+        modes = syn.fourier_modes(SEED, wl.get("modes", 8))
         pos = part.array("row_pos")
         u = torch.tensor(syn.fourier_field(pos, modes), dtype=torch.float32, device=dev)
         t = torch.tensor(syn.fourier_field(pos, modes, phase_advance=0.1), dtype=torch.float32, device=dev)
@@ -435,7 +503,7 @@ def build_problem(dev, precision, wl: dict, part):
         e0 = torch.randn(part.n_edges, Hh, device=dev, generator=g).to(
             torch.bfloat16 if precision == "bf16" else torch.float32)
     layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
-    stack = gnn.LayerStack(G, layers, Hh, precision, x0, e0, inference=wl["mode"] == "fwd")
+    stack = gnn.LayerStack(G, layers, Hh, precision, x0, e0, inference=wl["mode"] == "fwd", save_act=save_act)
     dx_top = None
     if wl["mode"] == "fwdbwd":
         g = torch.Generator(device=dev).manual_seed(SEED + 7)
@@ -443,52 +511,59 @@ def build_problem(dev, precision, wl: dict, part):
     return G, net, stack, dx_top, u, t
 
 
-def _timed(run, steps, profile):
+def _profiled(run, steps):
+    """Per-kernel CUDA-event report (launches, ms) of `steps` eager calls of `run`."""
     import torch
 
     from paper_2410_01657_gb300 import binding as B
 
-    stream = torch.cuda.current_stream()
-    if profile:
-        B.call("gnn_profile_start", 1 << 16)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    torch.cuda.synchronize()
+    B.call("gnn_profile_start", 1 << 16)
     for _ in range(steps):
         run()
-    ev1.record(stream)
     torch.cuda.synchronize()
-    if profile:
-        B.call("gnn_profile_stop")
-    return ev0.elapsed_time(ev1) / steps, (B.profile_report() if profile else {})
+    B.call("gnn_profile_stop")
+    return B.profile_report()
 
 
-def time_stack(stack, dx_top, steps, warmup, profile=True, graph=False):
-    """Mean device time of one step (ms) and the per-kernel CUDA-event report.
+def time_steps(run, steps: int, stream) -> list:
+    """Device time (ms) of each of `steps` calls of `run`, each bracketed by its
+    own CUDA events on the launching stream; synchronized on both sides."""
+    import torch
 
-    Eager: the profiled steps are the timed steps. Graph: the kernel report
-    comes from the same number of eager profiled steps, then the step is
-    captured once and `steps` replays are timed (the value)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        ev[i].record(stream)
+        run()
+    ev[steps].record(stream)
+    torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+
+
+def prepare_timing(stack, dx_top, warmup: int, graph: bool):
+    """Warm the step up (eager), capture it as a CUDA graph when asked, and return
+    the callable one timed step runs (a graph replay, or an eager step)."""
     import torch
 
     run = lambda: stack.step(dx_top)
     for _ in range(warmup):
         run()
     torch.cuda.synchronize()
-    ms, report = _timed(run, steps, profile)
     if not graph:
-        return ms, report, None
+        return run
     stack.capture(dx_top)
-    for _ in range(warmup):
+    for _ in range(2):
         stack.replay()
     torch.cuda.synchronize()
-    ms_graph, _ = _timed(stack.replay, steps, False)
-    return ms_graph, report, ms
+    return stack.replay
 
 
 def time_e2e(net, G, u, t, steps, warmup, dev):
     """Full training step through the public API with host-resident inputs: the
     step's node field and target are copied from pinned host memory every step;
-    the edge attributes are graph geometry and stay on the device with the graph."""
+    the edge attributes are graph geometry and stay on the device with the graph.
+    Returns (median ms, mean ms, H2D bytes, D2H bytes, library kernels of one step)."""
     import torch
 
     from paper_2410_01657_gb300 import nn as gnn
@@ -509,22 +584,48 @@ def time_e2e(net, G, u, t, steps, warmup, dev):
 
     for _ in range(warmup):
         one()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(steps):
-        one()
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
-    # the library kernels of one more step, event-timed (torch's own kernels are not listed)
+    stream = torch.cuda.current_stream()
+    times = time_steps(one, steps, stream)
+    report = _profiled(one, 1)
+    kernels = {k: {"launches": n, "ms": round(v, 4)} for k, (n, v) in report.items()}
+    return statistics.median(times), statistics.mean(times), h2d, 4, kernels
+
+
+def measure_fp32_peak():
+    """FP32 SIMT FMA throughput of this GPU, measured by the library's FMA kernel
+    (TFLOP/s, 2 FLOPs per FMA) and its SM count."""
+    import ctypes as C
+
     from paper_2410_01657_gb300 import binding as B
-    B.call("gnn_profile_start", 1 << 12)
-    one()
-    torch.cuda.synchronize()
-    B.call("gnn_profile_stop")
-    kernels = {k: {"launches": n, "ms": round(v, 4)} for k, (n, v) in B.profile_report().items()}
-    return ms, h2d, 4, kernels
+    tf, sms = C.c_double(), C.c_int32()
+    B.call("gnn_measure_fp32_fma", C.byref(tf), C.byref(sms), None)
+    return float(tf.value), int(sms.value)
+
+
+def fp32_comparison(dev, wl: dict, part_full, steps: int, warmup: int, ms_bf16_full: float):
+    """The plain FP32 SIMT path against the fused BF16 path, same graph and step
+    (eager steps, median). For the H=128 brick the comparison graph is the
+    16^3-element sub-brick of the same order and partition count."""
+    import torch
+
+    sub_nel = wl.get("fp32_nel")
+    part = part_full if sub_nel is None else workload_graph(dict(wl, nel=sub_nel), sub_nel)[0]
+    res = {}
+    for prec in ("bf16", "fp32"):
+        G, _, stack, dx, _, _ = build_problem(dev, prec, wl, part)
+        run = prepare_timing(stack, dx, 2, graph=False)
+        res[prec] = statistics.median(time_steps(run, steps, torch.cuda.current_stream()))
+        del stack, G
+        torch.cuda.empty_cache()
+    L = (sub_nel or wl["nel"]) * wl["p"] + 1 if wl.get("mesh") != "mixed" else None
+    e_unpart = 6 * L * L * (L - 1) if L else part.graph.n_edges
+    out = {"value": e_unpart * M / (res["fp32"] * 1e-3), "unit": "edges/s", "ms_per_step": res["fp32"],
+           "bf16_ms_per_step_same_graph": res["bf16"], "speedup_of_bf16": res["fp32"] / res["bf16"],
+           "graph": "the benchmark graph" if sub_nel is None else
+           f"{sub_nel}^3 elements p={wl['p']}, {wl['parts']} RCB sub-graphs ({L ** 3:,} nodes, {e_unpart:,} edges): "
+           "the plain path keeps FP32 per-edge activations ([E x 3H] input alone 105 GB at 32^3), which do not "
+           "fit the full graph", "timing": "eager steps, median"}
+    return out
 
 
 def main():
@@ -556,86 +657,110 @@ def main():
     precision = args.precision
     wl = dict(WORKLOADS[args.workload])
     Hw = wl["H"]
+    n_lin = wl.get("nh", NH) + 2
     fwd_only = wl["mode"] == "fwd" or args.mode == "fwd"
     if fwd_only:
         wl["mode"] = "fwd"
-    use_graph = args.graph or wl["graph"]
+    use_graph = wl["graph"] and not args.eager
     part, n_el, n_unpart, e_unpart = workload_graph(wl, args.nel)
-    G, net, stack, dx_top, u, t = build_problem(dev, precision, wl, part)
+    G, net, stack, dx_top, u, t = build_problem(dev, precision, wl, part, save_act=args.save_act)
+    saved_act = any(a is not None for a in stack.act)
     tune = None
     if (args.autotune or wl.get("uneven")) and precision == "bf16":
         tune = stack.autotune(dx_top)
         tune = {k: v for k, v in tune.items() if k != "candidates"} | {
             "candidates": [{k: v for k, v in c.items() if k != "fwd_choices"} for c in tune.get("candidates", [])]}
     peaks = load_peaks()
+    stream = torch.cuda.current_stream()
+    run = prepare_timing(stack, dx_top, args.warmup, use_graph)
     barrier()
     with ClockSampler(local) as clk:
-        ms, report, ms_eager = time_stack(stack, dx_top, args.steps, args.warmup, graph=use_graph)
+        times = time_steps(run, args.steps, stream)
     barrier()
-    ms = max_over_ranks(ms, dist, dev)
+    ms = max_over_ranks(statistics.median(times), dist, dev)
+    ms_mean = max_over_ranks(statistics.mean(times), dist, dev)
     value = world * e_unpart * M / (ms * 1e-3)
-    launches = sum(n for n, _ in report.values())
+
+    # the per-kernel table: separate eager steps with the event profiler on (not timed above)
+    n_prof = 2
+    report = _profiled(lambda: stack.step(dx_top), n_prof)
+    launches_per_step = sum(n for n, _ in report.values()) / n_prof
     total_ms = sum(v for _, v in report.values()) or 1.0
-    top = max(report.items(), key=lambda kv: kv[1][1]) if report else ("none", (1, 0.0))
-    top_name, (top_n, top_ms) = top
     edge_bytes = 2 if precision == "bf16" else 4
-    roof = None
-    abytes = algorithmic_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only,
-                               n_lin=wl.get("nh", NH) + 2, saved_act=any(a is not None for a in stack.act))
-    if abytes is not None:   # bytes of one step over the kernel's device time in one step
-        ach = abytes / (top_ms / args.steps * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": top_name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"],
-                "traffic": measured_traffic(top_name, G.n_edges) if args.workload == "c2" else None,
-                "peak_src": peaks["src"], "share": top_ms / total_ms}
-    elif top_name == "k_sgemm":
-        flops = sgemm_flops_per_step(G, Hw, wl.get("nh", NH) + 2, M) * args.steps
-        ach = flops / (top_ms * 1e-3) / 1e12
-        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "peak_src": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock",
-                "share": top_ms / total_ms}
-    tensor = None
-    if precision == "bf16":   # the whole step against the tensor bound (the other side of the roofline max)
-        n_lin = wl.get("nh", NH) + 2
-        fl = algorithmic_flops_per_step(G, Hw, n_lin, M, fwd_only)
-        fl_model = algorithmic_flops_per_step(G, Hw, n_lin, M, fwd_only, split=False)
-        ach_t = fl / (ms * 1e-3) / 1e12
-        tensor = {"bound": "tensor", "achieved": ach_t, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                  "frac": ach_t / peaks["bf16_tflops_sustained"], "flops_per_step": fl,
-                  "model_flops_per_step": fl_model, "peak_src": peaks["src"] + ", bf16 sustained",
-                  "note": "algorithmic FLOPs of the whole step (first Linear split, recompute not counted) "
-                          "over the step time"}
+    roof = step_roofline(ms, G.n_edges, G.n_rows, Hw, edge_bytes, n_lin, fwd_only, peaks,
+                         last_layer_no_edge_out=fwd_only)
+    traffic = measured_traffic(args.workload, list(report), G.n_edges) if not args.nel and not args.save_act else None
+    roof["traffic"] = sum(traffic.values()) if traffic else None
+    roof_kernel = None
+    if report:
+        top_name, (top_n, top_ms) = max(report.items(), key=lambda kv: kv[1][1])
+        db = design_bytes(top_name, G, Hw, edge_bytes, last_layer_no_edge_out=fwd_only, n_lin=n_lin,
+                          saved_act=saved_act)
+        roof_kernel = {"kernel": top_name, "share": top_ms / total_ms, "launches_per_step": top_n / n_prof,
+                       "ms_per_step": top_ms / n_prof}
+        if db is not None:
+            ach = db / (top_ms / n_prof * 1e-3) / 1e9
+            roof_kernel.update({"bound": "hbm", "design_bytes_per_step": db, "achieved": ach,
+                                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                                "traffic": traffic.get(top_name) if traffic else None,
+                                "note": "bytes the kernel moves as designed (scratch and stored activations "
+                                        "included), over its event-timed launches in profiled eager steps"})
+        elif top_name == "k_sgemm":
+            tf, sms = measure_fp32_peak()
+            flops = sgemm_flops_per_step(G, Hw, n_lin, M)
+            ach = flops / (top_ms / n_prof * 1e-3) / 1e12
+            roof_kernel.update({"bound": "alu", "achieved": ach, "peak": tf, "unit": "TFLOP/s", "frac": ach / tf,
+                                "peak_src": f"measured: FP32 FMA kernel on {sms} SMs"})
 
     # the cost of consistency: the same stack with Eq. 5c-5d skipped (the paper's "None" layers)
-    from paper_2410_01657_gb300 import binding as Bd
     for c in (stack.cfg, stack.cfg_last):
-        c.halo_mode = Bd.GNN_HALO_NONE
+        c.halo_mode = B.GNN_HALO_NONE
     stack.graph = None
-    ms_none, _, _ = time_stack(stack, dx_top, max(3, args.steps // 2), 2, profile=False)
+    run_eager = prepare_timing(stack, dx_top, 1, graph=False)
+    ms_none = statistics.median(time_steps(run_eager, max(3, args.steps // 4), stream))
     for c in (stack.cfg, stack.cfg_last):
-        c.halo_mode = Bd.GNN_HALO_SYNC
-    inconsistent = {"ms_per_step": ms_none, "cost_of_consistency": (ms_eager or ms) / ms_none,
-                    "note": "same stack without the halo swap + sync (inconsistent layers), eager"}
+        c.halo_mode = B.GNN_HALO_SYNC
+    ms_sync = statistics.median(time_steps(run_eager, max(3, args.steps // 4), stream))
+    inconsistent = {"ms_per_step": ms_none, "consistent_ms_per_step": ms_sync, "cost_of_consistency": ms_sync / ms_none,
+                    "note": "same stack without the halo swap + sync (inconsistent layers) against the consistent "
+                            "stack, eager steps, median"}
 
-    fp32 = None
-    if precision == "bf16" and not args.no_fp32 and wl["inputs"] == "encoders":
-        del stack
-        torch.cuda.empty_cache()
-        _, _, stack32, dx32, _, _ = build_problem(dev, "fp32", wl, part)
-        ms32, _, _ = time_stack(stack32, dx32, max(3, args.steps // 2), 2, profile=False)
-        fp32 = {"value": e_unpart * M / (ms32 * 1e-3), "unit": "edges/s", "ms_per_step": ms32,
-                "speedup_of_bf16": ms32 / ms}
-        del stack32
-        torch.cuda.empty_cache()
+    saved = None
+    if not saved_act and not fwd_only and precision == "bf16" and Hw <= 64 and args.workload in ("c2", "mixed", "large"):
+        # the option: H <= 64 training with the MLP activations kept from the forward
+        stack.save_act = True
+        stack._alloc_act()
+        if any(a is not None for a in stack.act):
+            run_s = prepare_timing(stack, dx_top, 2, graph=False)
+            ms_s = statistics.median(time_steps(run_s, max(3, args.steps // 4), stream))
+            saved = {"value": e_unpart * M / (ms_s * 1e-3), "unit": "edges/s", "ms_per_step": ms_s,
+                     "act_bytes_per_step": sum(a.numel() * 2 for a in stack.act),
+                     "note": "option: MLP activations stored by the forward, only the last Linear recomputed "
+                             "(eager steps, median)"}
+        stack.save_act = False
+        stack._alloc_act()
+
+    del stack, run, run_eager
+    torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e and wl["inputs"] == "encoders" and not fwd_only:
-        ms_e, h2d, d2h, e2e_k = time_e2e(net, G, u, t, max(3, args.steps // 2), 2, dev)
+        torch.cuda.synchronize()
+        ms_e, ms_e_mean, h2d, d2h, e2e_k = time_e2e(net, G, u, t, max(3, args.steps // 4), 2, dev)
+        enc_path = "fused BF16 row MLPs" if Hw <= 64 else "plain FP32 row MLPs (the fused row MLP covers H <= 64)"
         e2e = {"value": world * e_unpart * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "library_kernels_one_step": e2e_k,
-               "step": "encoders + 4 layers + decoder + consistent loss, fwd+bwd; node field and target "
-                       "copied from pinned host memory each step, loss read back"}
+               "mean_ms_per_step": ms_e_mean, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "library_kernels_one_step": e2e_k,
+               "step": f"encoders and decoder ({enc_path}) + 4 layers + consistent loss, fwd+bwd; node field and "
+                       "target copied from pinned host memory each step, loss read back; eager steps, median"}
+        net.zero_grad(set_to_none=True)
+        torch.cuda.empty_cache()
+
+    fp32 = None
+    if precision == "bf16" and not args.no_fp32 and wl["inputs"] == "encoders" and not fwd_only:
+        del G
+        torch.cuda.empty_cache()
+        fp32 = fp32_comparison(dev, wl, part, max(3, args.steps // 4), 2, ms)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -649,23 +774,28 @@ def main():
 
     if rank == 0:
         kind = "fwd+bwd" if not fwd_only else "fwd"
-        edge_state = e_unpart * Hw * edge_bytes
+        edge_state = part.n_edges * Hw * edge_bytes
         line = {"metric": f"MP-layer edges/s {kind}", "value": value, "unit": "edges/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": precision, "data": "synthetic",
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "mean_ms_per_step": ms_mean,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
+                "data": "synthetic",
                 "config": {"workload": workload_config_text(wl, n_el, n_unpart, e_unpart, kind),
                            "name": args.workload, "inputs": wl["inputs"],
-                           "rows": part.n_rows, "edges_partitioned": part.n_edges, "tile_edges": G.tile_edges,
+                           "rows": part.n_rows, "edges_partitioned": part.n_edges, "tile_edges": part.tile_edges,
+                           "training_form": ("saved activations (option)" if saved_act else
+                                             "per-layer recomputation of the MLP activations") if not fwd_only
+                           else "inference",
                            "l2": f"inputs larger than L2 (edge state {edge_state / 1e6:.0f} MB), no flush",
-                           "timing": "CUDA-graph replays; kernel table from as many eager steps" if use_graph
-                           else "eager steps",
+                           "timing": ("median of K CUDA-graph replays" if use_graph else "median of K eager steps")
+                           + ", each timed by CUDA events on the launching stream, profiler off",
                            "parallelism": f"replicas x{world}"},
                 "nodes_per_s": world * n_unpart * M / (ms * 1e-3),
-                "roofline": roof, "tensor": tensor, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu, "inconsistent": inconsistent,
-                "gpu_launches": launches, "kernels": {k: {"launches": n, "ms": v} for k, (n, v) in report.items()},
+                "roofline": roof, "roofline_kernel": roof_kernel, "fp32": fp32, "e2e": e2e, "cpu_baseline": cpu,
+                "inconsistent": inconsistent, "saved_activations": saved,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "kernels": {k: {"launches_per_step": n / n_prof, "ms_per_step": v / n_prof, "share": v / total_ms}
+                            for k, (n, v) in report.items()},
                 "clocks": clk.summary()}
-        if ms_eager is not None:
-            line["eager_ms_per_step"] = ms_eager
         if tune is not None:
             line["autotune"] = tune
         print(json.dumps(line))

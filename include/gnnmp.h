@@ -412,9 +412,11 @@ int gnn_mp_autotune(const gnn_graph_dev* G, gnn_mp_config* cfg, const gnn_mp_par
  * about n_rows * 4H bytes of scratch (n_rows * 8H when a_star_out is NULL);
  * larger graphs get GNN_ESHAPE with the required size in gnn_last_error(),
  * before any work is queued. GNN_EDTYPE for GNN_PREC_FP32.
- * The first call on each device looks up the area's device address (with
- * that device current); make that first call before any stream capture. No
- * call allocates or frees device memory. All calls share the one area and
+ * Every call outside stream capture looks up the area's device address on
+ * the current device; a call made while `stream` is being captured uses the
+ * address found by that device's last call outside capture, so make a first
+ * call on each device before any capture (GNN_EINVAL otherwise). No call
+ * allocates or frees device memory. All calls share the one area and
  * every byte of scratch is written before it is read, so nothing carries over
  * between calls, but calls whose executions overlap on the GPU (two streams,
  * or two host threads) race on it: serialise them. */
@@ -431,7 +433,9 @@ int gnn_halo_exchange(const gnn_graph_dev* G, float* rows, int32_t width, void* 
 /* ====================================================== encoder / decoder / loss
  * Row-wise MLP block (node/edge encoders, node decoder; Sec. III): Y = MLP(X)
  * over n_rows rows. X: device FP32 [n_rows x dims[0]]; Y: device
- * [n_rows x dims[n_lin]], FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1). */
+ * [n_rows x dims[n_lin]], FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1).
+ * These FP32 calls run over blocks of at most 2^22 rows; the workspace holds
+ * one block's activations, so it stays bounded for any n_rows. */
 int gnn_mlp_workspace_size(const gnn_mlp* P, int64_t n_rows, size_t* fwd_bytes, size_t* bwd_bytes);
 int gnn_mlp_forward(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,
                     float ln_eps, void* ws, size_t ws_bytes, void* stream);
@@ -488,6 +492,26 @@ int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, 
 int gnn_profile_start(int32_t capacity);
 int gnn_profile_stop(void);
 int gnn_profile_report(char* out, size_t bytes);
+
+/* ====================================================== diagnostics
+ * The paper has no counterpart to these calls.
+ *
+ * gnn_measure_fp32_fma: the current device's FP32 FMA throughput, measured
+ * with the library's own FMA kernel (independent chains of fused multiply-adds
+ * per thread, two blocks of 1024 threads per SM, best of three CUDA-event timed
+ * launches after one warm-up), in TFLOP/s at 2 FLOPs per FMA, and its SM count.
+ * It is the peak the plain FP32 SIMT path is measured against. Synchronous on
+ * `stream`; allocates nothing.
+ *
+ * gnn_selftest_bounded_wait: launches one warp that waits on an mbarrier no
+ * thread ever arrives at, with the same bounded wait every libgnnmp kernel
+ * uses but a limit of limit_ns (1 us .. 1 s) instead of the kernels' 1 s. The
+ * wait gives up, latches the timeout in the device error word and the kernel
+ * returns; *status (device int32) is then 1 (2 would mean the wait completed).
+ * The next gnn_check returns GNN_ETIMEOUT and clears the word; the context stays
+ * usable. Asynchronous on `stream`. */
+int gnn_measure_fp32_fma(double* tflops, int32_t* sm_count, void* stream);
+int gnn_selftest_bounded_wait(uint64_t limit_ns, int32_t* status, void* stream);
 
 #ifdef __cplusplus
 }

@@ -155,6 +155,8 @@ _SIGS = {
     "gnn_profile_start": (C.c_int, [C.c_int32]),
     "gnn_profile_stop": (C.c_int, []),
     "gnn_profile_report": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "gnn_measure_fp32_fma": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_int32), _P]),
+    "gnn_selftest_bounded_wait": (C.c_int, [C.c_uint64, _P, _P]),
 }
 
 

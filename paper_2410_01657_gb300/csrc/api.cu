@@ -6,6 +6,7 @@
 #include "device_common.cuh"
 #include "fused.h"
 #include "plain.h"
+#include "diag.h"
 
 namespace {
 
@@ -72,12 +73,17 @@ extern "C" {
 
 int gnn_check(void* stream) {
     GNN_CUDA_CHECK(cudaStreamSynchronize((cudaStream_t)stream), "gnn_check: stream synchronize");
-    unsigned int w0 = 0, w1 = 0;
-    GNN_CUDA_CHECK(gnn::plain::take_device_error(&w0), "gnn_check: read error word");
-    GNN_CUDA_CHECK(gnn::fused::take_device_error(&w1), "gnn_check: read error word");
-    const unsigned int word = w0 | w1;
+    // every translation unit with waiting kernels has its own error word
+    cudaError_t (*const take[])(unsigned int*) = {
+        gnn::plain::take_device_error, gnn::fused::take_device_error, gnn::fused::take_device_error_bwd,
+        gnn::fused::take_device_error_bwd128, gnn::fused::take_device_error_rowmlp, gnn::diag::take_device_error};
+    unsigned int word = 0;
+    for (auto f : take) {
+        unsigned int w = 0;
+        GNN_CUDA_CHECK(f(&w), "gnn_check: read error word");
+        word |= w;
+    }
     if (word & GNN_DEVERR_TIMEOUT) return set_error(GNN_ETIMEOUT, "gnn_check: a device-side wait timed out");
-    if (word & GNN_DEVERR_BOUNDS) return set_error(GNN_EINVAL, "gnn_check: a device-side bounds check failed");
     return GNN_OK;
 }
 
@@ -347,6 +353,18 @@ int gnn_consistent_loss(const gnn_graph_dev* G, const float* y, const float* t, 
     GNN_REQUIRE(loss && ws, GNN_EINVAL, "gnn_consistent_loss: NULL loss or workspace");
     if (G->n_rows) GNN_REQUIRE(y && t, GNN_EINVAL, "gnn_consistent_loss: NULL y or t");
     return gnn::plain::consistent_loss(*G, y, t, F, loss, dy, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int gnn_measure_fp32_fma(double* tflops, int32_t* sm_count, void* stream) {
+    GNN_REQUIRE(tflops && sm_count, GNN_EINVAL, "gnn_measure_fp32_fma: NULL output");
+    return gnn::diag::measure_fp32_fma(tflops, sm_count, (cudaStream_t)stream);
+}
+
+int gnn_selftest_bounded_wait(uint64_t limit_ns, int32_t* status, void* stream) {
+    GNN_REQUIRE(status, GNN_EINVAL, "gnn_selftest_bounded_wait: NULL status");
+    GNN_REQUIRE(limit_ns >= 1000 && limit_ns <= 1000000000ull, GNN_EINVAL,
+                "gnn_selftest_bounded_wait: limit %llu ns outside [1 us, 1 s]", (unsigned long long)limit_ns);
+    return gnn::diag::selftest_bounded_wait(limit_ns, status, (cudaStream_t)stream);
 }
 
 }  // extern "C"

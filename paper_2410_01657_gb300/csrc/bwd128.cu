@@ -34,6 +34,8 @@
 namespace gnn {
 namespace fused {
 
+cudaError_t take_device_error_bwd128(unsigned int* out) { return take_device_error_word(out); }
+
 namespace {
 
 constexpr int H128 = 128;

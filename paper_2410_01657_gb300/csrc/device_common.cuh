@@ -9,11 +9,11 @@
 
 namespace gnn {
 
-// Latched device error word (0 = ok), one per translation unit. Kernels set
-// it with atomicOr when a bounded wait gives up or a bounds check fails;
-// gnn_check reads and clears every unit's word through take_device_error().
+// Latched device error word (0 = ok), one per translation unit (the units are
+// compiled separately, so each has its own copy). Kernels set it with atomicOr
+// when a bounded wait gives up; gnn_check reads and clears the word of every
+// unit that launches waiting kernels, through its take_device_error().
 #define GNN_DEVERR_TIMEOUT 1u
-#define GNN_DEVERR_BOUNDS 2u
 static __device__ unsigned int g_device_error = 0;
 
 // Host side: read and clear this translation unit's error word.

@@ -1693,18 +1693,26 @@ void* g_static_addr[128] = {};   // device address of g_static_scratch per devic
 
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
 
-// Looks up (once per device, with that device current) the device address of
-// the scratch array; host code must not use the array's name as a pointer.
-static int static_scratch_address(void** out) {
+// The device address of the scratch array on the current device; host code
+// must not use the array's name as a pointer. Outside stream capture the
+// address is looked up on every call (cheap once the module is loaded), so a
+// reset device's reloaded module is seen; while `s` is being captured the
+// address recorded by the device's last call outside capture is used.
+static int static_scratch_address(cudaStream_t s, void** out) {
     int dev = 0;
     GNN_CUDA_CHECK(cudaGetDevice(&dev), "gnn_mp_forward_static: cudaGetDevice");
     GNN_REQUIRE(dev >= 0 && dev < 128, GNN_EUNSUPPORTED, "gnn_mp_forward_static: device ordinal %d", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GNN_CUDA_CHECK(cudaStreamIsCapturing(s, &cs), "gnn_mp_forward_static: cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         GNN_CUDA_CHECK(cudaGetSymbolAddress(&p, g_static_scratch), "gnn_mp_forward_static: cudaGetSymbolAddress");
         g_static_addr[dev] = p;
     }
+    GNN_REQUIRE(g_static_addr[dev], GNN_EINVAL,
+                "gnn_mp_forward_static: first call on device %d made during stream capture; make one call "
+                "outside capture first", dev);
     *out = g_static_addr[dev];
     return GNN_OK;
 }
@@ -1721,7 +1729,7 @@ int mp_forward_static(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gn
                 "use gnn_mp_forward with a workspace",
                 need, kStaticScratchBytes);
     void* scratch = nullptr;
-    int rc = static_scratch_address(&scratch);
+    int rc = static_scratch_address(s, &scratch);
     if (rc) return rc;
     return mp_forward(G, cfg, W, x_in, e_in, x_out, e_out, a_star_out, scratch, kStaticScratchBytes, s);
 }

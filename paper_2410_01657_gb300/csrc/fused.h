@@ -9,7 +9,11 @@
 namespace gnn {
 namespace fused {
 
+// Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu.
 cudaError_t take_device_error(unsigned int* out);
+cudaError_t take_device_error_bwd(unsigned int* out);
+cudaError_t take_device_error_bwd128(unsigned int* out);
+cudaError_t take_device_error_rowmlp(unsigned int* out);
 size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 // Bytes of the saved MLP activations (BF16 h_0 .. h_{L-2} of every edge, then

@@ -35,6 +35,8 @@
 namespace gnn {
 namespace fused {
 
+cudaError_t take_device_error_bwd(unsigned int* out) { return take_device_error_word(out); }
+
 // ------------------------------------------------------------------ shared memory plans
 
 struct EdgeBwdSmem {

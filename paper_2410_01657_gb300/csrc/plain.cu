@@ -880,45 +880,61 @@ static void carve_mlp(Carve& c, const gnn_mlp& P, int64_t rows, bool bwd, float*
     }
 }
 
+// The row MLP runs over blocks of at most kMlpRowBlock rows: its workspace
+// (every activation of a block, FP32) is sized for one block, so an encoder
+// over tens of millions of edge rows needs a bounded workspace. The weight
+// gradients accumulate block after block, in row order.
+constexpr int64_t kMlpRowBlock = (int64_t)1 << 22;
+
 size_t mlp_ws(const gnn_mlp& P, int64_t rows, bool bwd) {
     Carve c(nullptr);
     float *h[GNN_MAX_LIN], *z, *g0, *g1, *part, *dy;
-    carve_mlp(c, P, rows, bwd, h, &z, &g0, &g1, &part, &dy);
+    carve_mlp(c, P, std::min(rows, kMlpRowBlock), bwd, h, &z, &g0, &g1, &part, &dy);
     return c.off + 256;
 }
 
 int mlp_forward(const gnn_mlp& P, int64_t rows, const float* X, void* Y, int y_bf16, float eps, void* ws,
                 size_t ws_bytes, cudaStream_t s) {
     GNN_REQUIRE(ws_bytes >= mlp_ws(P, rows, false), GNN_ENOMEM, "gnn_mlp_forward: workspace too small");
-    Carve c(ws);
-    float *h[GNN_MAX_LIN], *z, *g0, *g1, *part, *dy;
-    carve_mlp(c, P, rows, false, h, &z, &g0, &g1, &part, &dy);
-    int rc = chain_fwd(P, rows, X, P.dims[0], h, z, s);
-    if (rc) return rc;
-    return mlp_output(P, rows, z, eps, nullptr, nullptr, Y, y_bf16, s);
+    const int K0 = P.dims[0], NO = P.dims[P.n_lin];
+    for (int64_t r0 = 0; r0 < rows; r0 += kMlpRowBlock) {
+        const int64_t n = std::min(kMlpRowBlock, rows - r0);
+        Carve c(ws);
+        float *h[GNN_MAX_LIN], *z, *g0, *g1, *part, *dy;
+        carve_mlp(c, P, n, false, h, &z, &g0, &g1, &part, &dy);
+        int rc = chain_fwd(P, n, X + r0 * K0, K0, h, z, s);
+        if (rc) return rc;
+        void* Yb = (char*)Y + (size_t)(r0 * NO) * (y_bf16 ? 2 : 4);
+        if ((rc = mlp_output(P, n, z, eps, nullptr, nullptr, Yb, y_bf16, s))) return rc;
+    }
+    return GNN_OK;
 }
 
 int mlp_backward(const gnn_mlp& P, int64_t rows, const float* X, const void* dY, int dy_bf16, float* dX,
                  const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s) {
     GNN_REQUIRE(ws_bytes >= mlp_ws(P, rows, true), GNN_ENOMEM, "gnn_mlp_backward: workspace too small");
-    Carve c(ws);
-    float *h[GNN_MAX_LIN], *z, *g0, *g1, *part, *dyf;
-    carve_mlp(c, P, rows, true, h, &z, &g0, &g1, &part, &dyf);
-    int rc = chain_fwd(P, rows, X, P.dims[0], h, z, s);
-    if (rc) return rc;
-    const float* dy = (const float*)dY;
-    const int64_t n_out = rows * P.dims[P.n_lin];
-    if (dy_bf16) {
-        if (n_out) {
+    const int K0 = P.dims[0], NO = P.dims[P.n_lin];
+    for (int64_t r0 = 0; r0 < rows; r0 += kMlpRowBlock) {
+        const int64_t n = std::min(kMlpRowBlock, rows - r0);
+        Carve c(ws);
+        float *h[GNN_MAX_LIN], *z, *g0, *g1, *part, *dyf;
+        carve_mlp(c, P, n, true, h, &z, &g0, &g1, &part, &dyf);
+        const float* Xb = X + r0 * K0;
+        int rc = chain_fwd(P, n, Xb, K0, h, z, s);
+        if (rc) return rc;
+        const float* dy = (const float*)dY + r0 * NO;
+        if (dy_bf16) {
             {
                 ProfScope _ps(s, "k_bf16_to_f32");
-                k_bf16_to_f32<<<grid1(n_out), 256, 0, s>>>((const __nv_bfloat16*)dY, dyf, n_out);
+                k_bf16_to_f32<<<grid1(n * NO), 256, 0, s>>>((const __nv_bfloat16*)dY + r0 * NO, dyf, n * NO);
             }
             GNN_LAUNCH_CHECK("k_bf16_to_f32");
+            dy = dyf;
         }
-        dy = dyf;
+        if ((rc = mlp_bwd(P, dP, n, Xb, K0, h, z, dy, dX ? dX + r0 * K0 : nullptr, g0, g1, part, eps, s)))
+            return rc;
     }
-    return mlp_bwd(P, dP, rows, X, P.dims[0], h, z, dy, dX, g0, g1, part, eps, s);
+    return GNN_OK;
 }
 
 int consistent_loss(const gnn_graph_dev& G, const float* y, const float* t, int F, float* loss, float* dy,

@@ -19,6 +19,8 @@
 namespace gnn {
 namespace fused {
 
+cudaError_t take_device_error_rowmlp(unsigned int* out) { return take_device_error_word(out); }
+
 using namespace tc;
 
 struct RowMlpArgs {

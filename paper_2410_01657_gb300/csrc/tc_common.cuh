@@ -49,17 +49,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete, for at most ~1 s;
-// on timeout latches GNN_DEVERR_TIMEOUT and returns false (the caller skips
-// its remaining work instead of hanging the GPU).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Default limit of every device-side wait: 1 s of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+// Waits for the phase with the given parity to complete, for at most
+// limit_ns; on timeout latches GNN_DEVERR_TIMEOUT and returns false (the caller
+// skips its remaining work instead of hanging the GPU).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
     const uint32_t b = smem_u32(bar);
     if (mbar_try_wait(b, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
         if (mbar_try_wait(b, parity)) return true;
         __nanosleep(64);   // yield issue slots to the warps doing work
-        if (globaltimer_ns() - t0 > 1000000000ull) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             raise_device_error(GNN_DEVERR_TIMEOUT);
             return false;
         }

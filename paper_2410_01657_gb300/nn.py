@@ -5,7 +5,8 @@ step of the network runs in libgnnmp's kernels through ``binding``:
 
 * ``ConsistentMPFunction`` -- one consistent NMP layer (Eq. 5a-5e) with its
   hand-written adjoint (``gnn_mp_forward`` / ``gnn_mp_backward``), recomputing
-  the layer's MLP activations in the backward pass instead of storing them;
+  the layer's MLP activations in the backward pass instead of storing them
+  (or, as an option, keeping them: ``gnn_mp_forward_act`` / ``_backward_act``);
 * ``RowMLPFunction`` -- node/edge encoders and the node decoder (Sec. III);
 * ``ConsistentLossFunction`` -- the consistent MSE loss, Eq. 8a-8c;
 * ``ConsistentGNN`` -- encoders, M consistent layers, decoder (Sec. III).
@@ -122,8 +123,9 @@ def gnn_halo_exchange(G: DeviceGraph, rows: torch.Tensor) -> None:
 
 class ConsistentMPFunction(torch.autograd.Function):
     """One consistent NMP layer, Eq. 5a-5e, with the hand-written adjoint (Eq. 3).
-    The MLP activations are kept from the forward to the backward where the
-    library supports it (gnn_mp_forward_act / gnn_mp_backward_act)."""
+    The backward recomputes the MLP activations; with ``save`` they are kept
+    from the forward instead where the library supports it
+    (gnn_mp_forward_act / gnn_mp_backward_act, H <= 64)."""
 
     @staticmethod
     def forward(ctx, x, e, G, cfg_args, edge_dims, node_dims, save, *params):
@@ -291,16 +293,18 @@ class LayerStack:
     Inference keeps the inputs and two edge-state and two node-state buffers
     (ping-pong) and skips the last layer's edge-state write (GNN_FLAG_NO_EDGE_OUT): only the
     aggregates reach the node update, so no per-edge output of the last layer
-    touches HBM. Training keeps every layer's input states and a*, the MLPs'
-    activations where the library supports it (``save_act``; the backward
-    then recomputes only the last Linear of each MLP, else the whole chains)
-    and two node- and two edge-gradient buffers (ping-pong: layer l writes
-    dx[l % 2], de[l % 2]; dx[0] ends as dL/dx0). With saved activations the
-    forward always uses the record-tiled edge kernel (the autotuner's choice of
-    forward kernel then only affects ``forward`` of an inference stack)."""
+    touches HBM. Training keeps every layer's input states and a* and two
+    node- and two edge-gradient buffers (ping-pong: layer l writes dx[l % 2],
+    de[l % 2]; dx[0] ends as dL/dx0); the backward recomputes each layer's MLP
+    activations from them. ``save_act=True`` (an option at H <= 64) keeps the
+    MLPs' activations from the forward instead, so the backward recomputes only
+    the last Linear of each MLP, at the price of 2H(L-1) bytes per edge and
+    per row for every layer; the forward then always uses the record-tiled
+    edge kernel (the autotuner's choice of forward kernel then only affects
+    ``forward`` of an inference stack)."""
 
     def __init__(self, G: DeviceGraph, layers, hidden: int, precision: str, x0, e0, halo: bool = True,
-                 ln_eps: float = 1e-5, inference: bool = False, save_act: bool = True):
+                 ln_eps: float = 1e-5, inference: bool = False, save_act: bool = False):
         self.G = G
         self.M = len(layers)
         self.hidden = hidden
@@ -476,12 +480,15 @@ class ConsistentGNN(torch.nn.Module):
     """Encode-process-decode GNN with consistent NMP layers (Sec. III).
 
     ``params`` is the nested dict of arrays made by ``synthetic.gnn_params``
-    (float64 arrays are cast to FP32 master weights)."""
+    (float64 arrays are cast to FP32 master weights). Training recomputes each
+    layer's MLP activations in the backward; ``save_act=True`` keeps them from
+    the forward where the library supports it (H <= 64)."""
 
     def __init__(self, params: dict, precision: str = "bf16", halo: bool = True, ln_eps: float = 1e-5,
-                 device="cuda"):
+                 device="cuda", save_act: bool = False):
         super().__init__()
         self.precision = precision
+        self.save_act = save_act
         self.halo = halo
         self.ln_eps = ln_eps
         self.enc_node = _MLP(params["enc_node"], device)
@@ -497,7 +504,7 @@ class ConsistentGNN(torch.nn.Module):
 
     def _row_mlp(self, m: _MLP, X, out_bf16: bool, need_dx: bool):
         return RowMLPFunction.apply(X, m.dims, m.has_ln, out_bf16, self.ln_eps, need_dx, self.precision == "bf16",
-                                    torch.is_grad_enabled(), *m.tensors())
+                                    torch.is_grad_enabled() and self.save_act, *m.tensors())
 
     def encode(self, G: DeviceGraph, u, attr):
         x = self._row_mlp(self.enc_node, u, False, False)
@@ -508,7 +515,8 @@ class ConsistentGNN(torch.nn.Module):
         cfg_args = (self.hidden, self.precision, self.halo, self.ln_eps, 0)
         for layer in self.layers:
             x, e = ConsistentMPFunction.apply(x, e, G, cfg_args, layer.edge.dims, layer.node.dims,
-                                              torch.is_grad_enabled(), *layer.edge.tensors(), *layer.node.tensors())
+                                              torch.is_grad_enabled() and self.save_act,
+                                              *layer.edge.tensors(), *layer.node.tensors())
         return x, e
 
     def forward(self, G: DeviceGraph, u, attr):

@@ -21,6 +21,15 @@ Recipes (all numpy PCG64 via ``numpy.random.default_rng(seed)``):
   cells, each drawn (U[0,1) < tet_fraction) as one 8-node hexahedron or as
   its 6 Kuhn tetrahedra, plus fan cells joining one apex above the top face to
   bands of top-face nodes; interior nodes jittered U[-1/2,1/2]*jitter/n.
+* Counter-hashed states (``hashed_values``): for inputs of graphs too large to
+  draw on the host, each value is a fixed function of an integer counter (a
+  global node id or a directed edge key times the width, plus the column), so
+  any subset of rows can be regenerated on either side without the rest. The
+  counter's two 32-bit halves pass through the "lowbias32" integer hash
+  (x ^= x >> 16; x *= 0x7feb352d; x ^= x >> 15; x *= 0x846ca68b; x ^= x >> 16,
+  mod 2^32), seeded by xor; the top bits give uniform values on a grid that
+  BF16 (8 bits) or FP32 (16 bits) holds exactly. The same integer steps run on
+  numpy arrays and on torch tensors (any device), so the values agree bit for bit.
 """
 from __future__ import annotations
 
@@ -34,6 +43,7 @@ __all__ = [
     "jitter_unit",
     "log_uniform_counts",
     "normal",
+    "hashed_values",
 ]
 
 
@@ -258,3 +268,32 @@ def mixed_element_mesh(n: int, seed: int, tet_fraction: float = 0.5, n_fans: int
             "edge_ptr": np.concatenate([[0], np.cumsum(npairs)]).astype(np.int64),
             "edge_pairs": np.concatenate([edge_pairs] + fan_pairs).astype(np.int32),
             "kind": np.concatenate([kind, np.full(n_fans, 2, dtype=np.int8)])}
+
+
+_M32 = 0xFFFFFFFF
+
+
+def _lowbias32(x):
+    """The lowbias32 integer hash on values in [0, 2^32) held in int64 (numpy or
+    torch): only the low 32 bits of each product are kept."""
+    x = x ^ (x >> 16)
+    x = (x * 0x7FEB352D) & _M32
+    x = x ^ (x >> 15)
+    x = (x * 0x846CA68B) & _M32
+    return x ^ (x >> 16)
+
+
+def hashed_values(counter, seed: int, bits: int):
+    """Uniform values on [-2, 2) on a grid of 2^bits points, one per non-negative
+    int64 counter (numpy array or torch tensor; the result has its type and
+    device, float64 for numpy, float32 for torch). bits = 8 gives values BF16
+    holds exactly, bits = 16 values FP32 holds exactly."""
+    assert 1 <= bits <= 16
+    lo = counter & _M32
+    hi = (counter >> 32) & _M32
+    h = _lowbias32(lo ^ _lowbias32(hi ^ (seed & _M32)))
+    q = (h >> (32 - bits)) - (1 << (bits - 1))      # integer in [-2^(bits-1), 2^(bits-1))
+    scale = 2.0 / (1 << (bits - 1))
+    if isinstance(q, np.ndarray):
+        return q.astype(np.float64) * scale
+    return q.float() * scale

@@ -73,3 +73,17 @@ def oracle_network(params, brick, subs, u, target, attr=None, halo=True):
     L = om.consistent_loss(subs, ys, ts)
     g = om.network_backward(params, subs, cache, om.consistent_loss_grad(subs, ys, ts), halo)
     return ys, L, g, cache
+
+
+def max_row_rel(got, ref, rows=None) -> float:
+    """Largest per-row relative L2 error over ``rows`` (all rows when None); a
+    row's norm is floored at 1e-3 of the mean row norm of ``ref``."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if rows is not None:
+        got, ref = got[rows], ref[rows]
+    if ref.shape[0] == 0:
+        return 0.0
+    rn = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * max(float(rn.mean()), 1e-300)
+    return float((np.linalg.norm(got - ref, axis=1) / np.maximum(rn, floor)).max())

@@ -6,9 +6,9 @@
   the gradient is above the FP32 noise floor of the difference quotient.
 * The precision form (H = 128, BF16 GEMM operands) on a p = 7 brick: one layer
   forward and backward (input and parameter gradients) against the FP64
-  oracle and against the plain FP32 path, and the forward on a standalone
-  99^3-node brick (14^3 elements, p = 7, 5.8M edges) split into 2
-  sub-graphs, against the FP64 oracle."""
+  oracle and against the plain FP32 path, and the same forward and backward
+  on a standalone 99^3-node brick (14^3 elements, p = 7, 5.8M edges) split
+  into 2 sub-graphs, against the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -135,8 +135,9 @@ def test_precision_form_h128_layer_forward_backward():
 
 def test_precision_form_million_node_subbrick():
     # the C3 precision form on a standalone 14^3-element p=7 brick (99^3 = 970,299 nodes,
-    # 5.8M directed edges), H=128, one consistent layer forward, 2 RCB sub-graphs:
-    # BF16 against the FP64 oracle
+    # 5.8M directed edges), H=128, one consistent layer forward and backward, 2 RCB
+    # sub-graphs: BF16 outputs within 2e-2 and input and parameter gradients within
+    # 5e-2 of the FP64 oracle (relative L2 over each tensor)
     nel, p, H, R = (14, 14, 14), 7, 128, 2
     brick, subs = oracle_subgraphs(nel, p, R)
     assert brick.n_nodes == 99 ** 3
@@ -154,15 +155,45 @@ def test_precision_form_million_node_subbrick():
     uk, inv = np.unique(key, return_inverse=True)
     eu = torch.as_tensor(rng.standard_normal((uk.size, H)), dtype=torch.float32).to(torch.bfloat16)
     e = eu.to(torch.float32).numpy().astype(np.float64)[inv]
-    x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
+    del eu
+    # a consistent upstream gradient of x' (split over the copies) and a BF16 one of e'
+    dxg = rng.standard_normal((part.graph.n_nodes, H)).astype(np.float32).astype(np.float64)
+    dx1 = dxg[gid] / part.array("node_deg")[:, None]
+    du = torch.as_tensor(0.5 * rng.standard_normal((uk.size, H)), dtype=torch.float32).to(torch.bfloat16)
+    de1 = du.to(torch.float32).numpy().astype(np.float64)[inv]
+    del du, key, uk
+    lp = params["layers"][0]
     net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
     layer = net.layers[0]
+    tens = layer.edge.tensors() + layer.node.tensors()
     xt = torch.as_tensor(x, dtype=torch.float32, device=DEV)
     et = torch.as_tensor(e, dtype=torch.float32, device=DEV).to(torch.bfloat16)
-    W = gnn.mp_params(layer.edge.dims, layer.node.dims, layer.edge.tensors() + layer.node.tensors())
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+    cfg = gnn.mp_config(H, "bf16")
     xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
-    gnn.gnn_mp_forward(G, gnn.mp_config(H, "bf16"), W, xt, et, xo, eo, a)
+    gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
+    dparams = [torch.zeros_like(t) for t in tens]
+    dxi, dei = torch.empty_like(xt), torch.empty_like(et)
+    gnn.gnn_mp_backward(G, cfg, W, xt, et, a, torch.as_tensor(dx1, dtype=torch.float32, device=DEV),
+                        torch.as_tensor(de1, dtype=torch.float32, device=DEV).to(torch.bfloat16), dxi, dei,
+                        gnn.mp_params(layer.edge.dims, layer.node.dims, dparams))
     B.call("gnn_check", None)
-    assert rel_l2(a.cpu().numpy(), np.concatenate(cache["a_star"])) < 2e-2
-    assert rel_l2(eo.float().cpu().numpy(), np.concatenate(e1)) < 2e-2
-    assert rel_l2(xo.cpu().numpy(), np.concatenate(x1)) < 2e-2
+    gpu = {"x'": xo.cpu().numpy(), "e'": eo.float().cpu().numpy(), "a*": a.cpu().numpy(),
+           "dx": dxi.cpu().numpy(), "de": dei.float().cpu().numpy()}
+    gpu_grads = [d.cpu().numpy() for d in dparams]
+    del xt, et, xo, eo, a, dxi, dei, dparams
+    torch.cuda.empty_cache()
+
+    x1, e1, cache = om.layer_forward(lp, subs, split_rows(x, subs), split_edges(e, subs))
+    assert rel_l2(gpu["a*"], np.concatenate(cache["a_star"])) < 2e-2
+    assert rel_l2(gpu["e'"], np.concatenate(e1)) < 2e-2
+    assert rel_l2(gpu["x'"], np.concatenate(x1)) < 2e-2
+    del x1, e1
+    dx0, de0, g = om.layer_backward(lp, subs, cache, split_rows(dx1, subs), split_edges(de1, subs))
+    del cache
+    assert rel_l2(gpu["dx"], np.concatenate(dx0)) < 5e-2
+    assert rel_l2(gpu["de"], np.concatenate(de0)) < 5e-2
+    gref = list(g["edge"]["W"]) + list(g["edge"]["b"]) + [g["edge"]["gamma"], g["edge"]["beta"]] \
+        + list(g["node"]["W"]) + list(g["node"]["b"]) + [g["node"]["gamma"], g["node"]["beta"]]
+    for k, (u, r) in enumerate(zip(gpu_grads, gref)):
+        assert rel_l2(u, r) < 5e-2, (k, rel_l2(u, r))

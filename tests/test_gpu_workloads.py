@@ -46,7 +46,8 @@ def _uneven_case(p=2, seed=3):
     return brick, subs, part
 
 
-def test_uneven_64_subgraphs_layers_fwd_bwd():
+@pytest.mark.parametrize("save_act", [False, True])
+def test_uneven_64_subgraphs_layers_fwd_bwd(save_act):
     H, M = 64, 2
     brick, subs, part = _uneven_case()
     sizes = part.array("part_stats")[:, 0]
@@ -66,7 +67,7 @@ def test_uneven_64_subgraphs_layers_fwd_bwd():
     net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
     layers = [(l.edge.tensors(), l.node.tensors(), l.edge.dims, l.node.dims) for l in net.layers]
     stack = gnn.LayerStack(G, layers, H, "bf16", torch.tensor(x, dtype=torch.float32, device=DEV),
-                           torch.tensor(e, dtype=torch.float32, device=DEV))
+                           torch.tensor(e, dtype=torch.float32, device=DEV), save_act=save_act)
     stack.forward()
     B.call("gnn_check", None)
     assert rel_l2(stack.x[M].cpu().numpy(), np.concatenate(xs)) < 2e-2
@@ -144,7 +145,7 @@ def test_inference_h32_last_layer_without_edge_output():
     assert rel_l2(xt.cpu().numpy(), np.concatenate(xs)) < 2e-2
 
 
-def _stack_case(H=64, M=3, inference=False, seed=50):
+def _stack_case(H=64, M=3, inference=False, seed=50, save_act=False):
     brick, subs, part = _uneven_case(seed=seed)
     G = part.to_device(DEV)
     params = syn.gnn_params(seed, H, 2, M, randomize_affine=True)
@@ -154,7 +155,7 @@ def _stack_case(H=64, M=3, inference=False, seed=50):
     x0 = torch.randn(part.n_rows, H, device=DEV, generator=g)
     e0 = torch.randn(part.n_edges, H, device=DEV, generator=g).to(torch.bfloat16)
     dx = 1e-3 * torch.randn(part.n_rows, H, device=DEV, generator=g)
-    stack = gnn.LayerStack(G, layers, H, "bf16", x0, e0, inference=inference)
+    stack = gnn.LayerStack(G, layers, H, "bf16", x0, e0, inference=inference, save_act=save_act)
     return part, G, layers, x0, e0, dx, stack
 
 
@@ -170,10 +171,10 @@ def test_inference_stack_equals_training_forward():
     assert len(inf.e) == 3 and len(inf.x) == 3
 
 
-@pytest.mark.parametrize("H,M", [(64, 3), (128, 2)])
-def test_cuda_graph_replay_matches_eager_step(H, M):
+@pytest.mark.parametrize("H,M,save_act", [(64, 3, False), (64, 3, True), (128, 2, False)])
+def test_cuda_graph_replay_matches_eager_step(H, M, save_act):
     # H = 128 captures the layered adjoint (recomputation, per-Linear kernels, reductions)
-    part, G, layers, x0, e0, dx, stack = _stack_case(H, M)
+    part, G, layers, x0, e0, dx, stack = _stack_case(H, M, save_act=save_act)
     stack.zero_grad()
     stack.step(dx)
     torch.cuda.synchronize()

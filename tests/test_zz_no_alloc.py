@@ -4,8 +4,9 @@ Code that runs while a CUDA stream is being captured without a graph memory
 pool, or inside a framework that owns the device allocator, cannot hand the
 library a freshly allocated workspace. gnn_mp_forward_static uses a fixed
 scratch area built into the library instead. This file checks, through the C
-ABI, that it computes what gnn_mp_forward computes (two calls in a row, so the
-shared area is reused) and that a graph too large for the area is refused.
+ABI, that it computes bit for bit what gnn_mp_forward computes (two calls in a
+row with a call on another graph between them, so the shared area is reused
+and holds other data) and that a graph too large for the area is refused.
 It is collected last so a failure here never hides the other GPU tests."""
 import ctypes as C
 
@@ -55,18 +56,32 @@ def built():
     B.load()
 
 
-@pytest.mark.parametrize("H,with_a", [(64, True), (32, False)])
+@pytest.mark.parametrize("H,with_a", [(64, True), (64, False), (32, False), (128, True)])
 def test_static_scratch_matches_workspace_forward(H, with_a):
+    # The static entry point runs the same deterministic kernels on the same
+    # tiles as gnn_mp_forward, so the results must agree bit for bit. Between
+    # the two static calls on this graph a call on another graph (another size,
+    # other inputs) leaves different data in the shared area; the second call
+    # must not see any of it.
     part, G, W, tens, x, e = _layer(H)
     cfg = gnn.mp_config(H, "bf16")
     xr, er, ar = torch.empty_like(x), torch.empty_like(e), torch.empty_like(x)
-    gnn.gnn_mp_forward(G, cfg, W, x, e, xr, er, ar)
-    for _ in range(2):   # the second call reuses the area the first one left behind
+    gnn.gnn_mp_forward(G, cfg, W, x, e, xr, er, ar if with_a else None)
+    _, G2, W2, _, x2, e2 = _layer(H, R=2, nel=(3, 5, 4), p=2)
+    for call in range(2):
+        if call == 1:
+            _static_call(G2, cfg, W2, 3.0 * x2, e2, with_a)
         xo, eo, a = _static_call(G, cfg, W, x, e, with_a)
         B.call("gnn_check", None)
-        assert _rel(xo, xr) < TOL and _rel(eo.float(), er.float()) < TOL
+        assert torch.equal(xo, xr), (call, _rel(xo, xr))
+        assert torch.equal(eo, er), (call, _rel(eo.float(), er.float()))
         if with_a:
-            assert _rel(a, ar) < TOL
+            assert torch.equal(a, ar), (call, _rel(a, ar))
+        # and within the fused path's BF16 tolerance of the plain FP32 path
+        cfg32 = gnn.mp_config(H, "fp32")
+        x32, e32 = torch.empty_like(x), torch.empty(e.shape, device=DEV)
+        gnn.gnn_mp_forward(G, cfg32, W, x, e.float(), x32, e32, torch.empty_like(x))
+        assert _rel(xo, x32) < TOL and _rel(eo.float(), e32) < TOL
 
 
 def test_static_scratch_refuses_graphs_beyond_its_size():

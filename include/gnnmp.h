@@ -290,10 +290,12 @@ typedef struct gnn_mp_params {
  * same arithmetic; FP32 results agree to rounding (instruction pairing and
  * contraction differ), so a value rounded to BF16 afterwards (edge state, MMA
  * operands) can differ in its last bit. 0 = library default. */
-#define GNN_EDGE_FWD_AUTO 0   /* RT for H <= 64, ONE for H = 128                                */
+#define GNN_EDGE_FWD_AUTO 0   /* RT for H <= 64, TM for H = 128 (ONE beyond 2 MLP hidden layers) */
 #define GNN_EDGE_FWD_RT   1   /* record-tiled consumer groups, P|Q rows prefetched (H <= 64)   */
 #define GNN_EDGE_FWD_WS   2   /* producer warp + two consumer groups (H <= 64)                 */
 #define GNN_EDGE_FWD_ONE  3   /* one tile at a time per CTA, CTAs per SM by occupancy          */
+#define GNN_EDGE_FWD_TM   4   /* two tile groups per SM, hidden activations kept in tensor
+                                 memory as the next Linear's operand (H = 128, <= 4 Linears) */
 
 typedef struct gnn_mp_config {
     int32_t hidden;          /* H: 16, 32, 64 or 128 (BF16); 1..256 (FP32)                 */

@@ -50,11 +50,13 @@ int check_cfg(const gnn_mp_config* cfg, const gnn_mp_params* W, const char* fn) 
                 "%s: unknown halo mode %d", fn, cfg->halo_mode);
     GNN_REQUIRE(cfg->ln_eps > 0.f, GNN_EINVAL, "%s: ln_eps must be positive", fn);
     const int H = cfg->hidden;
-    GNN_REQUIRE(cfg->edge_fwd_kernel >= GNN_EDGE_FWD_AUTO && cfg->edge_fwd_kernel <= GNN_EDGE_FWD_ONE, GNN_EINVAL,
+    GNN_REQUIRE(cfg->edge_fwd_kernel >= GNN_EDGE_FWD_AUTO && cfg->edge_fwd_kernel <= GNN_EDGE_FWD_TM, GNN_EINVAL,
                 "%s: unknown edge forward kernel %d", fn, cfg->edge_fwd_kernel);
     GNN_REQUIRE(cfg->precision != GNN_PREC_BF16 || H <= 64 ||
                     (cfg->edge_fwd_kernel != GNN_EDGE_FWD_RT && cfg->edge_fwd_kernel != GNN_EDGE_FWD_WS),
                 GNN_EUNSUPPORTED, "%s: edge forward kernel %d needs H <= 64", fn, cfg->edge_fwd_kernel);
+    GNN_REQUIRE(cfg->precision != GNN_PREC_BF16 || H == 128 || cfg->edge_fwd_kernel != GNN_EDGE_FWD_TM,
+                GNN_EUNSUPPORTED, "%s: edge forward kernel %d needs H = 128", fn, cfg->edge_fwd_kernel);
     GNN_REQUIRE(cfg->ctas_per_sm >= 0 && cfg->ctas_per_sm <= 32, GNN_EINVAL, "%s: ctas_per_sm %d out of range",
                 fn, cfg->ctas_per_sm);
     if (cfg->precision == GNN_PREC_FP32)
@@ -76,7 +78,8 @@ int gnn_check(void* stream) {
     // every translation unit with waiting kernels has its own error word
     cudaError_t (*const take[])(unsigned int*) = {
         gnn::plain::take_device_error, gnn::fused::take_device_error, gnn::fused::take_device_error_bwd,
-        gnn::fused::take_device_error_bwd128, gnn::fused::take_device_error_rowmlp, gnn::diag::take_device_error};
+        gnn::fused::take_device_error_bwd128, gnn::fused::take_device_error_rowmlp,
+        gnn::fused::take_device_error_edge128, gnn::diag::take_device_error};
     unsigned int word = 0;
     for (auto f : take) {
         unsigned int w = 0;

@@ -1529,7 +1529,14 @@ int edge_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
         if (act && (rc = make_row_tmap(&tmh, act, (int64_t)(W.edge.n_lin - 1) * A.act_rows, H))) return rc;
         int grid;
         int variant = cfg.edge_fwd_kernel;
-        if (variant == GNN_EDGE_FWD_AUTO || act) variant = H <= 64 ? GNN_EDGE_FWD_RT : GNN_EDGE_FWD_ONE;
+        if (variant == GNN_EDGE_FWD_AUTO || act)
+            variant = H <= 64 ? GNN_EDGE_FWD_RT : (edge_fwd_tm_supported(W) ? GNN_EDGE_FWD_TM : GNN_EDGE_FWD_ONE);
+        if constexpr (H == 128) {
+            if (variant == GNN_EDGE_FWD_TM) {
+                if ((rc = edge_fwd_tm(G, cfg, W, e_in, pq, e_out, a, s))) return rc;
+                return cfg.halo_mode == GNN_HALO_SYNC ? plain::halo(G, a, H, s) : GNN_OK;
+            }
+        }
         if constexpr (H <= 64) {
             if (variant == GNN_EDGE_FWD_RT) {
                 using R = RtCfg<H>;
@@ -1759,6 +1766,8 @@ int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const 
     using C = Cfg<H>;
     const int64_t NR = G.n_rows, E = G.n_edges;
     GNN_REQUIRE(cfg.hidden == H, GNN_EUNSUPPORTED, "edge_recompute_save: H=%d", cfg.hidden);
+    if (edge_fwd_tm_supported(W) && cfg.edge_fwd_kernel != GNN_EDGE_FWD_ONE)
+        return edge_save_tm(G, cfg, W, e_in, pq, o, s);
     GNN_REQUIRE(G.tile_meta && ((uintptr_t)G.tile_meta & 15) == 0, GNN_EINVAL,
                 "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
     CUtensorMap tm;

@@ -9,11 +9,17 @@
 namespace gnn {
 namespace fused {
 
-// Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu.
+// Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu, edge128.cu.
 cudaError_t take_device_error(unsigned int* out);
 cudaError_t take_device_error_bwd(unsigned int* out);
 cudaError_t take_device_error_bwd128(unsigned int* out);
 cudaError_t take_device_error_rowmlp(unsigned int* out);
+cudaError_t take_device_error_edge128(unsigned int* out);
+// The H = 128 edge forward with two tile groups per SM and the hidden
+// activations in tensor memory (edge128.cu); supported for 2..4 Linears.
+bool edge_fwd_tm_supported(const gnn_mp_params& W);
+int edge_fwd_tm(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const __nv_bfloat16* e_in,
+                const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a, cudaStream_t s);
 size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 // Bytes of the saved MLP activations (BF16 h_0 .. h_{L-2} of every edge, then
@@ -68,6 +74,9 @@ struct RecomputeSave {
 };
 int edge_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
                         const __nv_bfloat16* e_in, const __nv_bfloat16* pq, RecomputeSave& o, cudaStream_t s);
+// The same recomputation in the two-group tensor-memory form (edge128.cu; 2..4 Linears).
+int edge_save_tm(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const __nv_bfloat16* e_in,
+                 const __nv_bfloat16* pq, RecomputeSave& o, cudaStream_t s);
 int node_recompute_save(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W,
                         const float* a_star, const float* x_in, RecomputeSave& o, cudaStream_t s);
 

@@ -21,6 +21,7 @@ std::vector<Choice> choices_for(int H) {
         c.push_back({GNN_EDGE_FWD_RT, 0});
         c.push_back({GNN_EDGE_FWD_WS, 0});
     }
+    if (H == 128) c.push_back({GNN_EDGE_FWD_TM, 0});
     c.push_back({GNN_EDGE_FWD_ONE, 0});
     c.push_back({GNN_EDGE_FWD_ONE, 1});
     return c;

@@ -88,27 +88,33 @@ def test_fused_layer_forward_vs_oracle(H, n_hidden, R):
     assert np.array_equal(xo[order][1:][same], xo[order][:-1][same])
 
 
-@pytest.mark.parametrize("H", [16, 32, 64])
-def test_edge_forward_kernel_choices_agree(H):
+@pytest.mark.parametrize("H,n_hidden", [(16, 2), (32, 2), (64, 2), (128, 2), (128, 0)])
+def test_edge_forward_kernel_choices_agree(H, n_hidden):
     # every launch choice of the edge forward on a ragged multi-tile graph: oracle parity, and the
     # choices agree with each other to FP32 rounding
-    brick, subs, part, G, params, x, e = _layer_case((6, 5, 4), 3, 5, H, 2, seed=21)
+    brick, subs, part, G, params, x, e = _layer_case((6, 5, 4), 3, 5, H, n_hidden, seed=21)
     x1, e1, cache = om.layer_forward(params["layers"][0], subs, split_rows(x, subs), split_edges(e, subs))
     outs = {}
-    for variant, cps in ((B.GNN_EDGE_FWD_RT, 0), (B.GNN_EDGE_FWD_WS, 0), (B.GNN_EDGE_FWD_ONE, 0),
-                         (B.GNN_EDGE_FWD_ONE, 1)):
+    choices = ((B.GNN_EDGE_FWD_RT, 0), (B.GNN_EDGE_FWD_WS, 0), (B.GNN_EDGE_FWD_ONE, 0), (B.GNN_EDGE_FWD_ONE, 1)) \
+        if H <= 64 else ((B.GNN_EDGE_FWD_TM, 0), (B.GNN_EDGE_FWD_ONE, 0), (B.GNN_EDGE_FWD_ONE, 1))
+    for variant, cps in choices:
         xo, eo, a = _run_fused_layer(G, params, H, x, e, variant=variant, ctas_per_sm=cps)
         assert rel_l2(a, np.concatenate(cache["a_star"])) < TOL_OUT
         assert rel_l2(eo, np.concatenate(e1)) < TOL_OUT
         assert rel_l2(xo, np.concatenate(x1)) < TOL_OUT
         outs[(variant, cps)] = (xo, eo, a)
-    ref = outs[(B.GNN_EDGE_FWD_RT, 0)]
+    ref = outs[choices[0]]
+    # the H <= 64 choices share one epilogue, so their FP32 aggregates agree to FP32 rounding; at
+    # H = 128 the tensor-memory kernel sums each row's LayerNorm statistics in one thread (the
+    # one-tile kernel combines four partial sums), so a last-bit difference can flip the BF16
+    # rounding of a hidden activation, which carries into the aggregate at the 1e-5 level
+    tol_a, tol_o, flips = (1e-5, 1e-4, 1e-3) if H <= 64 else (1e-4, 1e-3, 1e-2)
     for k, o in outs.items():
-        # the FP32 aggregate to FP32 rounding; the BF16 edge state, and the node state computed
-        # from BF16 operands, may differ where a last-bit FP32 difference flips a BF16 rounding
-        assert rel_l2(o[2], ref[2]) < 1e-5, k
-        assert rel_l2(o[0], ref[0]) < 1e-4, k
-        assert rel_l2(o[1], ref[1]) < 1e-4 and np.mean(o[1] != ref[1]) < 1e-3, k
+        # the BF16 edge state, and the node state computed from BF16 operands, may differ where a
+        # last-bit FP32 difference flips a BF16 rounding
+        assert rel_l2(o[2], ref[2]) < tol_a, k
+        assert rel_l2(o[0], ref[0]) < tol_o, k
+        assert rel_l2(o[1], ref[1]) < tol_o and np.mean(o[1] != ref[1]) < flips, k
 
 
 def test_edge_forward_kernel_choice_validation():
@@ -118,6 +124,10 @@ def test_edge_forward_kernel_choice_validation():
     assert ei.value.code == B.GNN_EUNSUPPORTED
     with pytest.raises(B.GnnError):
         _run_fused_layer(G, params, 128, x, e, variant=7)
+    brick, subs, part, G, params, x, e = _layer_case((2, 2, 2), 2, 1, 64, 2)
+    with pytest.raises(B.GnnError) as ei:
+        _run_fused_layer(G, params, 64, x, e, variant=B.GNN_EDGE_FWD_TM)
+    assert ei.value.code == B.GNN_EUNSUPPORTED
 
 
 def test_fused_forward_tiles_span_many_ctas():

@@ -1255,6 +1255,20 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                 xa[4 * i] = u.x; xa[4 * i + 1] = u.y; xa[4 * i + 2] = u.z; xa[4 * i + 3] = u.w;
                 xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
             }
+        } else if (NodeSplit<H>::value) {
+            // the operand rows are read whole by warps below; the residual x (FP32) is read
+            // per thread for the epilogue, requested here so it lands during the MMA chain
+            if (!SAVE && valid) {
+                const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+#pragma unroll
+                for (int i = 0; i < C::CW / 4; ++i) {
+                    const float4 w = __ldg(px + i);
+                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < C::CW; ++i) xv[i] = 0.f;
+            }
         } else if (valid) {
             const float4* pa = reinterpret_cast<const float4*>(A.a_star + r * H + c0);
             const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
@@ -1289,8 +1303,24 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
                 }
             }
         } else {
-            // K half 0 (a*) then K half 1 (x) through the same [128 x H] buffer
-            st_row_tile<C::CW>(sA0, row, c0, C::S, xa);
+            // K half 0 (a*) then K half 1 (x) through the same [128 x H] buffer, each row read
+            // whole by one warp (lane l: columns 4l .. 4l+3; warp w: rows 8w .. 8w+7); the x
+            // rows wait in registers until the a* half has been multiplied
+            static_assert(C::NT == 512 && H == 128, "row-per-warp fill: 16 warps x 8 rows, 32 lanes x 4 columns");
+            float4 xr[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int rr = 8 * warp + i;
+                const int64_t rg = t * 128 + rr;
+                float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+                xr[i] = av;
+                if (rg < A.n_rows) {
+                    av = __ldg(reinterpret_cast<const float4*>(A.a_star + rg * H) + lane);
+                    xr[i] = __ldg(reinterpret_cast<const float4*>(A.x + rg * H) + lane);
+                }
+                *reinterpret_cast<uint2*>(sA0 + tile_off(rr, 4 * lane, 128, C::S)) =
+                    make_uint2(pack_bf16x2(av.x, av.y), pack_bf16x2(av.z, av.w));
+            }
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();
@@ -1310,7 +1340,10 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_node_fwd(const __grid_constant__
             ph ^= 1;
             tc_fence_after();
             if (!ok) break;
-            st_row_tile<C::CW>(sA0, row, c0, C::S, xv);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                *reinterpret_cast<uint2*>(sA0 + tile_off(8 * warp + i, 4 * lane, 128, C::S)) =
+                    make_uint2(pack_bf16x2(xr[i].x, xr[i].y), pack_bf16x2(xr[i].z, xr[i].w));
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();

@@ -998,60 +998,120 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
         }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
-        float dq[CW];
+        if constexpr (H == 128) {
+            // warp-cooperative rows: warp w fills rows 8w .. 8w+7 of the operand tiles, lane l
+            // columns 4l .. 4l+3, so every dz1, dP and x row is one coalesced 256/512-byte read
+            // (the sender-side sum of each column still runs over the edges in order)
+            constexpr int UE = 4;   // edges per row requested together, for all eight rows at once
+            int32_t k0[8], deg[8];
+            int maxdeg = 0;
 #pragma unroll
-        for (int i = 0; i < CW; ++i) dq[i] = 0.f;
-        if (valid) {
-            // sender-side sum in edge order; the edge ids and then the dz1 rows of UB
-            // edges are requested together so their latencies overlap
-            constexpr int UB = CW >= 32 ? 2 : 4;
-            const int32_t k0 = A.t_ptr[r], k1 = A.t_ptr[r + 1];
-            for (int32_t kb = k0; kb < k1; kb += UB) {
-                int64_t e[UB];
+            for (int i = 0; i < 8; ++i) {
+                const int64_t rg = t * 128 + 8 * warp + i;
+                k0[i] = rg < A.n_rows ? __ldg(A.t_ptr + rg) : 0;
+                deg[i] = rg < A.n_rows ? __ldg(A.t_ptr + rg + 1) - k0[i] : 0;
+                maxdeg = max(maxdeg, deg[i]);
+            }
+            float4 dq[8];
 #pragma unroll
-                for (int u = 0; u < UB; ++u) e[u] = kb + u < k1 ? (int64_t)__ldg(A.t_eid + kb + u) : -1;
-                uint4 z[UB][CW / 8];
+            for (int i = 0; i < 8; ++i) dq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int kb = 0; kb < maxdeg; kb += UE) {
+                uint2 z[8][UE];
 #pragma unroll
-                for (int u = 0; u < UB; ++u)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int i = 0; i < CW / 8; ++i)
-                        z[u][i] = e[u] >= 0 ? __ldg(reinterpret_cast<const uint4*>(A.dz1 + e[u] * H + c0) + i)
-                                            : make_uint4(0u, 0u, 0u, 0u);
+                    for (int u = 0; u < UE; ++u) {
+                        const int64_t e = kb + u < deg[i] ? (int64_t)__ldg(A.t_eid + k0[i] + kb + u) : -1;
+                        z[i][u] = e >= 0 ? __ldg(reinterpret_cast<const uint2*>(A.dz1 + e * H) + lane)
+                                         : make_uint2(0u, 0u);
+                    }
 #pragma unroll
-                for (int u = 0; u < UB; ++u) {
-                    if (e[u] < 0) break;
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int i = 0; i < CW / 8; ++i) {
-                        float f[8];
-                        unpack_bf16x2(z[u][i].x, f[0], f[1]);
-                        unpack_bf16x2(z[u][i].y, f[2], f[3]);
-                        unpack_bf16x2(z[u][i].z, f[4], f[5]);
-                        unpack_bf16x2(z[u][i].w, f[6], f[7]);
+                    for (int u = 0; u < UE; ++u) {
+                        if (kb + u < deg[i]) {
+                            float f0, f1, f2, f3;
+                            unpack_bf16x2(z[i][u].x, f0, f1);
+                            unpack_bf16x2(z[i][u].y, f2, f3);
+                            dq[i].x += f0;
+                            dq[i].y += f1;
+                            dq[i].z += f2;
+                            dq[i].w += f3;
+                        }
+                    }
+            }
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) dq[8 * i + j] += f[j];
+            for (int i = 0; i < 8; ++i) {
+                const int rr = 8 * warp + i;
+                const int64_t rg = t * 128 + rr;
+                float4 dp = make_float4(0.f, 0.f, 0.f, 0.f), xv = dp;
+                if (rg < A.n_rows) {
+                    dp = __ldg(reinterpret_cast<const float4*>(A.dP + rg * H) + lane);
+                    xv = __ldg(reinterpret_cast<const float4*>(A.x + rg * H) + lane);
+                }
+                *reinterpret_cast<uint2*>(sA + tile_off(rr, H + 4 * lane, 128, S2)) =
+                    make_uint2(pack_bf16x2(dq[i].x, dq[i].y), pack_bf16x2(dq[i].z, dq[i].w));
+                *reinterpret_cast<uint2*>(sA + tile_off(rr, 4 * lane, 128, S2)) =
+                    make_uint2(pack_bf16x2(dp.x, dp.y), pack_bf16x2(dp.z, dp.w));
+                *reinterpret_cast<uint2*>(sX + tile_off(rr, 4 * lane, 128, S)) =
+                    make_uint2(pack_bf16x2(xv.x, xv.y), pack_bf16x2(xv.z, xv.w));
+            }
+        } else {
+            float dq[CW];
+#pragma unroll
+            for (int i = 0; i < CW; ++i) dq[i] = 0.f;
+            if (valid) {
+                // sender-side sum in edge order; the edge ids and then the dz1 rows of UB
+                // edges are requested together so their latencies overlap
+                constexpr int UB = CW >= 32 ? 2 : 4;
+                const int32_t k0 = A.t_ptr[r], k1 = A.t_ptr[r + 1];
+                for (int32_t kb = k0; kb < k1; kb += UB) {
+                    int64_t e[UB];
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) e[u] = kb + u < k1 ? (int64_t)__ldg(A.t_eid + kb + u) : -1;
+                    uint4 z[UB][CW / 8];
+#pragma unroll
+                    for (int u = 0; u < UB; ++u)
+#pragma unroll
+                        for (int i = 0; i < CW / 8; ++i)
+                            z[u][i] = e[u] >= 0 ? __ldg(reinterpret_cast<const uint4*>(A.dz1 + e[u] * H + c0) + i)
+                                                : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) {
+                        if (e[u] < 0) break;
+#pragma unroll
+                        for (int i = 0; i < CW / 8; ++i) {
+                            float f[8];
+                            unpack_bf16x2(z[u][i].x, f[0], f[1]);
+                            unpack_bf16x2(z[u][i].y, f[2], f[3]);
+                            unpack_bf16x2(z[u][i].z, f[4], f[5]);
+                            unpack_bf16x2(z[u][i].w, f[6], f[7]);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) dq[8 * i + j] += f[j];
+                        }
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int i = 0; i < CW; i += 8) st_tile8(sA, row, H + c0 + i, 128, S2, dq + i);
-        {
-            float dp[CW], xv[CW];
+            for (int i = 0; i < CW; i += 8) st_tile8(sA, row, H + c0 + i, 128, S2, dq + i);
+            {
+                float dp[CW], xv[CW];
 #pragma unroll
-            for (int i = 0; i < CW; ++i) dp[i] = xv[i] = 0.f;
-            if (valid) {
-                const float4* pp = reinterpret_cast<const float4*>(A.dP + r * H + c0);
-                const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
+                for (int i = 0; i < CW; ++i) dp[i] = xv[i] = 0.f;
+                if (valid) {
+                    const float4* pp = reinterpret_cast<const float4*>(A.dP + r * H + c0);
+                    const float4* px = reinterpret_cast<const float4*>(A.x + r * H + c0);
 #pragma unroll
-                for (int i = 0; i < CW / 4; ++i) {
-                    float4 u = __ldg(pp + i), w = __ldg(px + i);
-                    dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
-                    xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                    for (int i = 0; i < CW / 4; ++i) {
+                        float4 u = __ldg(pp + i), w = __ldg(px + i);
+                        dp[4 * i] = u.x; dp[4 * i + 1] = u.y; dp[4 * i + 2] = u.z; dp[4 * i + 3] = u.w;
+                        xv[4 * i] = w.x; xv[4 * i + 1] = w.y; xv[4 * i + 2] = w.z; xv[4 * i + 3] = w.w;
+                    }
                 }
-            }
 #pragma unroll
-            for (int i = 0; i < CW; i += 8) st_tile8(sA, row, c0 + i, 128, S2, dp + i);
-            st_row_tile<CW>(sX, row, c0, S, xv);
+                for (int i = 0; i < CW; i += 8) st_tile8(sA, row, c0 + i, 128, S2, dp + i);
+                st_row_tile<CW>(sX, row, c0, S, xv);
+            }
         }
         fence_proxy_async();
         tc_fence_before();

@@ -175,7 +175,7 @@ def test_fused_partitioned_vs_unpartitioned():
     assert rel_l2(out[8], out[1]) < 1e-2
 
 
-def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=True, ws_bytes=None):
+def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=True, ws_bytes=None, variant=0):
     brick, subs, part, G, params, x, e = _layer_case(nel, p, R, H, n_hidden, seed=seed)
     lp = params["layers"][0]
     rng = np.random.default_rng(seed + 5)
@@ -192,6 +192,7 @@ def _layer_backward_case(H, n_hidden, R, nel=(4, 3, 3), p=3, seed=11, with_de=Tr
     dparams = [torch.zeros_like(t) for t in tens]
     dW = gnn.mp_params(layer.edge.dims, layer.node.dims, dparams)
     cfg = gnn.mp_config(H, "bf16")
+    cfg.edge_fwd_kernel = variant
     xt, et = _to(x), _to(e, torch.bfloat16)
     xo, eo, a = torch.empty_like(xt), torch.empty_like(et), torch.empty_like(xt)
     gnn.gnn_mp_forward(G, cfg, W, xt, et, xo, eo, a)
@@ -356,3 +357,21 @@ def test_saved_edge_activations(H, n_hidden):
         gref += list(g[m]["W"]) + list(g[m]["b"]) + [g[m]["gamma"], g[m]["beta"]]
     for got, ref in zip(sav[5:], gref):
         assert rel_l2(got, ref) < TOL_GRAD
+
+
+@pytest.mark.parametrize("n_hidden", [2, 0])
+def test_h128_tensor_memory_kernels_match_one_tile_kernels(n_hidden):
+    # the layered H = 128 adjoint with the two-group tensor-memory forward and
+    # recomputation (the default) against the one-tile kernels (GNN_EDGE_FWD_ONE):
+    # both within the oracle's tolerance, and close to each other (their LayerNorm
+    # sums run in different orders, so BF16 roundings of activations can differ)
+    tm = _layer_backward_case(128, n_hidden, 3, nel=(5, 4, 3), seed=23)
+    one = _layer_backward_case(128, n_hidden, 3, nel=(5, 4, 3), seed=23, variant=B.GNN_EDGE_FWD_ONE)
+    for out in (tm, one):
+        dx, de, dws, dx_ref, de_ref, refs = out
+        assert rel_l2(dx, dx_ref) < TOL_GRAD and rel_l2(de, de_ref) < TOL_GRAD
+        for got, ref in zip(dws, refs):
+            assert rel_l2(got, ref) < TOL_GRAD
+    assert rel_l2(tm[0], one[0]) < 5e-3 and rel_l2(tm[1], one[1]) < 5e-3
+    for a, b in zip(tm[2], one[2]):
+        assert rel_l2(a, b) < 1e-2

@@ -107,15 +107,54 @@ __device__ __forceinline__ void tmem_st16u(uint32_t taddr, const uint32_t* r) {
         : "memory");
 }
 
-// 32 accumulator columns [c, c + 32) of this thread's lane, plus bias.
+// 32 accumulator columns [c, c + 32) of this thread's lane, plus bias (16-byte
+// aligned, read as float4).
 __device__ __forceinline__ void ld_acc32(uint32_t taddr, const float* bias, float* v) {
     tmem_ld16(taddr, v);
     tmem_ld16(taddr + 16, v + 16);
     tmem_ld_wait();
-    float2* v2 = reinterpret_cast<float2*>(v);
-    const float2* b2 = reinterpret_cast<const float2*>(bias);
+    const float4* b4 = reinterpret_cast<const float4*>(bias);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v2[i] = __fadd2_rn(v2[i], b2[i]);
+    for (int i = 0; i < 8; ++i) {
+        const float4 b = b4[i];
+        float2* v2 = reinterpret_cast<float2*>(v + 4 * i);
+        v2[0] = __fadd2_rn(v2[0], make_float2(b.x, b.y));
+        v2[1] = __fadd2_rn(v2[1], make_float2(b.z, b.w));
+    }
+}
+
+// 32 FP32 columns of this thread's lane from registers into TMEM.
+__device__ __forceinline__ void st_tmem32(uint32_t taddr, const float* v) {
+    tmem_st16(taddr, v);
+    tmem_st16(taddr + 16, v + 16);
+}
+
+// Sum of 32 values in four independent chains (latency), then combined.
+__device__ __forceinline__ float sum32(const float* v) {
+    float2 a = make_float2(v[0], v[1]), b = make_float2(v[2], v[3]);
+    float2 c = make_float2(v[4], v[5]), d = make_float2(v[6], v[7]);
+#pragma unroll
+    for (int i = 8; i < 32; i += 8) {
+        a = __fadd2_rn(a, make_float2(v[i], v[i + 1]));
+        b = __fadd2_rn(b, make_float2(v[i + 2], v[i + 3]));
+        c = __fadd2_rn(c, make_float2(v[i + 4], v[i + 5]));
+        d = __fadd2_rn(d, make_float2(v[i + 6], v[i + 7]));
+    }
+    a = __fadd2_rn(__fadd2_rn(a, b), __fadd2_rn(c, d));
+    return a.x + a.y;
+}
+
+// Sum of (v - m)^2 over 32 values, four independent chains.
+__device__ __forceinline__ float sqdev32(const float* v, float m) {
+    const float2 nm = make_float2(-m, -m);
+    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+        const float2 d = __fadd2_rn(make_float2(v[i], v[i + 1]), nm);
+        acc[(i / 2) & 3] = __ffma2_rn(d, d, acc[(i / 2) & 3]);
+    }
+    const float2 a = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
+    return a.x + a.y;
 }
 
 // ELU of 32 pre-activations, BF16-packed into 16 TMEM columns (the next Linear's A operand).
@@ -296,47 +335,50 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
         if (!ok) break;
         ph_mma ^= 1;
         tc_fence_after();
-        float ev[kH];   // the pre-LayerNorm row, then e' (FP32)
+        // mean, then the variance about it (FP32, this thread's row, four independent
+        // chains); e' = e + LN(z) stays in registers and, as BF16, goes into the e tile
+        const float* bk = sPar + (n_lin - 1) * kH;
+        const float* gam = sPar + n_lin * kH;
+        const float* bet = sPar + (n_lin + 1) * kH;
+        float ev[kH];
+        float mean, rstd;
         {
-            const float* bk = sPar + (n_lin - 1) * kH;
-            float2 s2 = make_float2(0.f, 0.f);
+            float sp[4];
 #pragma unroll
             for (int c = 0; c < kH; c += 32) {
                 ld_acc32(tAcc + lane_base + c, bk + c, ev + c);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) s2 = __fadd2_rn(s2, make_float2(ev[c + 2 * i], ev[c + 2 * i + 1]));
+                sp[c / 32] = sum32(ev + c);
             }
-            const float mean = (s2.x + s2.y) * (1.f / kH);
-            float2 d2 = make_float2(0.f, 0.f);
+            mean = ((sp[0] + sp[1]) + (sp[2] + sp[3])) * (1.f / kH);
 #pragma unroll
-            for (int i = 0; i < kH; i += 2) {
-                const float2 d = __fadd2_rn(make_float2(ev[i], ev[i + 1]), make_float2(-mean, -mean));
-                d2 = __ffma2_rn(d, d, d2);
+            for (int c = 0; c < kH; c += 32) sp[c / 32] = sqdev32(ev + c, mean);
+            rstd = rsqrtf(((sp[0] + sp[1]) + (sp[2] + sp[3])) * (1.f / kH) + A.eps);
+        }
+#pragma unroll
+        for (int c = 0; c < kH; c += 8) {
+            float er[8];
+            ld_tile8(sE, row, c, 128, kS, er);   // the residual e
+#pragma unroll
+            for (int i = 0; i < 8; i += 4) {
+                const float4 gm = *reinterpret_cast<const float4*>(gam + c + i);
+                const float4 bt = *reinterpret_cast<const float4*>(bet + c + i);
+                const float2 xa = __fmul2_rn(__fadd2_rn(make_float2(ev[c + i], ev[c + i + 1]), make_float2(-mean, -mean)),
+                                             make_float2(rstd, rstd));
+                const float2 xb = __fmul2_rn(__fadd2_rn(make_float2(ev[c + i + 2], ev[c + i + 3]),
+                                                        make_float2(-mean, -mean)),
+                                             make_float2(rstd, rstd));
+                const float2 ya = __fadd2_rn(__ffma2_rn(xa, make_float2(gm.x, gm.y), make_float2(bt.x, bt.y)),
+                                             make_float2(er[i], er[i + 1]));
+                const float2 yb = __fadd2_rn(__ffma2_rn(xb, make_float2(gm.z, gm.w), make_float2(bt.z, bt.w)),
+                                             make_float2(er[i + 2], er[i + 3]));
+                ev[c + i] = valid ? ya.x : 0.f;
+                ev[c + i + 1] = valid ? ya.y : 0.f;
+                ev[c + i + 2] = valid ? yb.x : 0.f;
+                ev[c + i + 3] = valid ? yb.y : 0.f;
             }
-            const float rstd = rsqrtf((d2.x + d2.y) * (1.f / kH) + A.eps);
-            const float* gam = sPar + n_lin * kH;
-            const float* bet = sPar + (n_lin + 1) * kH;
-#pragma unroll
-            for (int c = 0; c < kH; c += 8) {
-                float er[8];
-                ld_tile8(sE, row, c, 128, kS, er);     // the residual: this tile's e row
-#pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    const float2 xh = __fmul2_rn(__fadd2_rn(make_float2(ev[c + i], ev[c + i + 1]),
-                                                            make_float2(-mean, -mean)),
-                                                 make_float2(rstd, rstd));
-                    const float2 y = __ffma2_rn(xh, make_float2(gam[c + i], gam[c + i + 1]),
-                                                make_float2(bet[c + i], bet[c + i + 1]));
-                    const float2 o = __fadd2_rn(y, make_float2(er[i], er[i + 1]));
-                    ev[c + i] = valid ? o.x : 0.f;
-                    ev[c + i + 1] = valid ? o.y : 0.f;
-                }
-            }
+            st_tile8(sE, row, c, 128, kS, ev + c);
         }
         tc_fence_before();
-        // e' leaves as whole rows, staged as BF16 in the e tile (every thread has read its own e row above)
-#pragma unroll
-        for (int c = 0; c < kH; c += 8) st_tile8(sE, row, c, 128, kS, ev + c);
         group_sync(gi);
         if (A.e_out) {
             constexpr int CPR = kH / 8;   // 16-byte chunks per row
@@ -375,6 +417,7 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
         }
         // the e tile and the record are free: the group's next tile
         fence_proxy_async();
+        tc_fence_before();
         group_sync(gi);
         if (leader && t + step < A.n_tiles) issue_ld(t + step, tile_hdr(t + step).z);
     }
@@ -597,84 +640,109 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
                           sE, (int32_t)(k * A.hs_rows) + y);
         }
         if (!ok) break;
-        // the gradient of e': g = de' + w da_i (requested before the last Linear completes)
-        float gv[kH];
-        if (valid) {
-            const float4* dp = reinterpret_cast<const float4*>(A.da + rcv * kH);
+        // the gradient of e': g = de' + w da_i, its first half requested before the last
+        // Linear completes; g is kept in TMEM columns [128, 256) of the group (the activation
+        // operand is not read again in this tile)
+        const uint32_t tG = tAcc + 128;
+        uint4 ga[16], gd[8];
+        auto load_g = [&](int h) {   // columns [64 h, 64 h + 64) of da (FP32) and de' (BF16)
 #pragma unroll
-            for (int i = 0; i < kH / 4; ++i) {
-                const float4 u = __ldg(dp + i);
-                gv[4 * i] = u.x;
-                gv[4 * i + 1] = u.y;
-                gv[4 * i + 2] = u.z;
-                gv[4 * i + 3] = u.w;
+            for (int i = 0; i < 16; ++i)
+                ga[i] = valid ? __ldg(reinterpret_cast<const uint4*>(A.da + rcv * kH + 64 * h) + i)
+                              : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                gd[i] = (valid && A.de_out)
+                            ? __ldg(reinterpret_cast<const uint4*>(A.de_out + ((int64_t)e0 + row) * kH + 64 * h) + i)
+                            : make_uint4(0u, 0u, 0u, 0u);
+        };
+        auto store_g = [&](int h) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {   // 16 columns at a time
+                float g[16];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint4 a = ga[4 * b + i];
+                    g[4 * i] = __uint_as_float(a.x);
+                    g[4 * i + 1] = __uint_as_float(a.y);
+                    g[4 * i + 2] = __uint_as_float(a.z);
+                    g[4 * i + 3] = __uint_as_float(a.w);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const uint4 d = gd[2 * b + i];
+                    const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float d0, d1;
+                        unpack_bf16x2(dw[j], d0, d1);
+                        float2* g2 = reinterpret_cast<float2*>(g + 8 * i + 2 * j);
+                        *g2 = __ffma2_rn(*g2, make_float2(w, w), make_float2(d0, d1));
+                    }
+                }
+                tmem_st16(tG + lane_base + 64 * h + 16 * b, g);
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kH; ++i) gv[i] = 0.f;
-        }
+        };
+        load_g(0);
         if (leader) bulk_wait_read_all();
         w_ok = leader ? mbar_wait(bar_mma + gi, ph_mma) : true;
         ok = group_and(w_ok, gi);
         if (!ok) break;
         ph_mma ^= 1;
         tc_fence_after();
+        store_g(0);
+        load_g(1);
+        store_g(1);
+        tmem_st_wait();
         {
-#pragma unroll
-            for (int i = 0; i < kH; i += 2) {
-                const float2 g2 = __fmul2_rn(make_float2(gv[i], gv[i + 1]), make_float2(w, w));
-                gv[i] = g2.x;
-                gv[i + 1] = g2.y;
-            }
-            if (A.de_out && valid) {
-                const uint4* dp = reinterpret_cast<const uint4*>(A.de_out + ((int64_t)e0 + row) * kH);
-#pragma unroll
-                for (int i = 0; i < kH / 8; ++i) {
-                    const uint4 u = __ldg(dp + i);
-                    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float d0, d1;
-                        unpack_bf16x2(uw[j], d0, d1);
-                        gv[8 * i + 2 * j] += d0;
-                        gv[8 * i + 2 * j + 1] += d1;
-                    }
-                }
-            }
             // LayerNorm statistics and the adjoint sums of d = g gamma over the row
             const float* bl = sPar + (n_lin - 1) * kH;
             const float* gam = sPar + n_lin * kH;
-            float sv = 0.f, sq = 0.f, sd = 0.f, sdv = 0.f;
+            float sv[4], sq[4], sd[4], sdv[4];
 #pragma unroll
             for (int c = 0; c < kH; c += 32) {
-                float z[32];
+                float z[32], g[32];
                 ld_acc32(tAcc + lane_base + c, bl + c, z);
+                tmem_ld16(tG + lane_base + c, g);
+                tmem_ld16(tG + lane_base + c + 16, g + 16);
+                tmem_ld_wait();
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const float d = gv[c + i] * gam[c + i];
-                    sv += z[i];
-                    sq = fmaf(z[i], z[i], sq);
-                    sd += d;
-                    sdv = fmaf(d, z[i], sdv);
+                for (int i = 0; i < 32; i += 4) {
+                    const float4 gm = *reinterpret_cast<const float4*>(gam + c + i);
+                    const float2 za = make_float2(z[i], z[i + 1]), zb = make_float2(z[i + 2], z[i + 3]);
+                    const float2 da_ = __fmul2_rn(make_float2(g[i], g[i + 1]), make_float2(gm.x, gm.y));
+                    const float2 db_ = __fmul2_rn(make_float2(g[i + 2], g[i + 3]), make_float2(gm.z, gm.w));
+                    a0 = __fadd2_rn(a0, __fadd2_rn(za, zb));
+                    a1 = __ffma2_rn(za, za, __ffma2_rn(zb, zb, a1));
+                    a2 = __fadd2_rn(a2, __fadd2_rn(da_, db_));
+                    a3 = __ffma2_rn(da_, za, __ffma2_rn(db_, zb, a3));
                 }
+                sv[c / 32] = a0.x + a0.y;
+                sq[c / 32] = a1.x + a1.y;
+                sd[c / 32] = a2.x + a2.y;
+                sdv[c / 32] = a3.x + a3.y;
             }
-            const float mean = sv * (1.f / kH);
-            const float rstd = rsqrtf(fmaxf(sq * (1.f / kH) - mean * mean, 0.f) + A.eps);
-            const float s1 = sd * (1.f / kH);
-            const float s2 = rstd * (sdv - mean * sd) * (1.f / kH);
+            const float tv = (sv[0] + sv[1]) + (sv[2] + sv[3]), tq = (sq[0] + sq[1]) + (sq[2] + sq[3]);
+            const float td = (sd[0] + sd[1]) + (sd[2] + sd[3]), tdv = (sdv[0] + sdv[1]) + (sdv[2] + sdv[3]);
+            const float mean = tv * (1.f / kH);
+            const float rstd = rsqrtf(fmaxf(tq * (1.f / kH) - mean * mean, 0.f) + A.eps);
+            const float s1 = td * (1.f / kH);
+            const float s2 = rstd * (tdv - mean * td) * (1.f / kH);
 #pragma unroll
             for (int c = 0; c < kH; c += 16) {
-                float z[16], tg[16], dz[16];
+                float z[16], g[16], tg[16], dz[16];
                 tmem_ld16(tAcc + lane_base + c, z);
+                tmem_ld16(tG + lane_base + c, g);
                 tmem_ld_wait();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const float xh = valid ? (z[i] + bl[c + i] - mean) * rstd : 0.f;
-                    tg[i] = gv[c + i] * xh;
-                    dz[i] = valid ? rstd * (gv[c + i] * gam[c + i] - s1 - xh * s2) : 0.f;
+                    tg[i] = g[i] * xh;
+                    dz[i] = valid ? rstd * (g[i] * gam[c + i] - s1 - xh * s2) : 0.f;
                 }
                 accG[c / 16] += warp_colsum16(tg, lane);
-                accB[c / 16] += warp_colsum16(gv + c, lane);
+                accB[c / 16] += warp_colsum16(g, lane);
                 accZ[c / 16] += warp_colsum16(dz, lane);
                 st_tile8(sE, row, c, 128, kS, dz);
                 st_tile8(sE, row, c + 8, 128, kS, dz + 8);

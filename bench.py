@@ -611,10 +611,16 @@ def fp32_comparison(dev, wl: dict, part_full, steps: int, warmup: int, ms_bf16_f
     sub_nel = wl.get("fp32_nel")
     part = part_full if sub_nel is None else workload_graph(dict(wl, nel=sub_nel), sub_nel)[0]
     res = {}
+    sgemm = None
     for prec in ("bf16", "fp32"):
         G, _, stack, dx, _, _ = build_problem(dev, prec, wl, part)
         run = prepare_timing(stack, dx, 2, graph=False)
         res[prec] = statistics.median(time_steps(run, steps, torch.cuda.current_stream()))
+        if prec == "fp32":   # the plain path's SIMT GEMMs against the measured FP32 FMA peak
+            rep = _profiled(run, 1)
+            n_lin = wl.get("nh", NH) + 2
+            if "k_sgemm" in rep:
+                sgemm = (sgemm_flops_per_step(G, wl["H"], n_lin, M), rep["k_sgemm"][1])
         del stack, G
         torch.cuda.empty_cache()
     L = (sub_nel or wl["nel"]) * wl["p"] + 1 if wl.get("mesh") != "mixed" else None
@@ -625,6 +631,14 @@ def fp32_comparison(dev, wl: dict, part_full, steps: int, warmup: int, ms_bf16_f
            f"{sub_nel}^3 elements p={wl['p']}, {wl['parts']} RCB sub-graphs ({L ** 3:,} nodes, {e_unpart:,} edges): "
            "the plain path keeps FP32 per-edge activations ([E x 3H] input alone 105 GB at 32^3), which do not "
            "fit the full graph", "timing": "eager steps, median"}
+    tf, sms = measure_fp32_peak()
+    out["simt_peak"] = {"tflops": tf, "sm_count": sms,
+                        "src": "measured: the library's FP32 FMA kernel (gnn_measure_fp32_fma)"}
+    if sgemm is not None:
+        fl, ms_k = sgemm
+        out["sgemm"] = {"tflops": fl / (ms_k * 1e-3) / 1e12, "frac": fl / (ms_k * 1e-3) / 1e12 / tf,
+                        "ms_per_step": ms_k, "note": "the plain path's k_sgemm launches of one step (forward, "
+                                                     "recompute, input and weight gradients) over the SIMT peak"}
     return out
 
 
@@ -705,7 +719,7 @@ def main():
                                 "traffic": traffic.get(top_name) if traffic else None,
                                 "note": "bytes the kernel moves as designed (scratch and stored activations "
                                         "included), over its event-timed launches in profiled eager steps"})
-        elif top_name == "k_sgemm":
+        elif top_name == "k_sgemm":   # the FP32 bench: the SIMT GEMMs against the measured FP32 FMA peak
             tf, sms = measure_fp32_peak()
             flops = sgemm_flops_per_step(G, Hw, n_lin, M)
             ach = flops / (top_ms / n_prof * 1e-3) / 1e12

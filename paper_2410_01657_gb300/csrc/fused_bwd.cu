@@ -102,6 +102,9 @@ struct ProjBwdSmem {
     uint32_t w, a, x, bar, tm, total;
 };
 
+// H = 128 also stages each tile's sender-edge ids (up to kProjEids of them).
+constexpr int kProjEids = 4096;
+
 template <int H>
 __host__ __device__ inline ProjBwdSmem proj_bwd_smem() {
     using C = CfgB<H>;
@@ -109,7 +112,7 @@ __host__ __device__ inline ProjBwdSmem proj_bwd_smem() {
     s.w = 0;
     s.a = align_up(2 * C::WT, 1024);
     s.x = s.a + 2 * C::TILE;
-    s.bar = align_up(s.x + C::TILE, 8);
+    s.bar = align_up(s.x + C::TILE + (H == 128 ? kProjEids * 4 : 0), 8);
     s.tm = s.bar + 16;
     uint32_t end = s.tm + 16;
     end = end > s.a + 32768 ? end : s.a + 32768;
@@ -1003,6 +1006,15 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
             // columns 4l .. 4l+3, so every dz1, dP and x row is one coalesced 256/512-byte read
             // (the sender-side sum of each column still runs over the edges in order)
             constexpr int UE = 4;   // edges per row requested together, for all eight rows at once
+            // the tile's sender-edge ids are one contiguous range of t_eid: staged in shared
+            // memory by one coalesced read when it fits, so each gather is a single round trip
+            int32_t* sTe = reinterpret_cast<int32_t*>(sX + 128 * H * 2);
+            const int64_t rt0 = t * 128, rt1 = min(A.n_rows, rt0 + 128);
+            const int32_t kt0 = __ldg(A.t_ptr + rt0), kt1 = __ldg(A.t_ptr + rt1);
+            const bool staged = kt1 - kt0 <= kProjEids;
+            if (staged)
+                for (int i = tid; i < kt1 - kt0; i += C::NT) sTe[i] = __ldg(A.t_eid + kt0 + i);
+            __syncthreads();
             int32_t k0[8], deg[8];
             int maxdeg = 0;
 #pragma unroll
@@ -1021,7 +1033,8 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
                     for (int u = 0; u < UE; ++u) {
-                        const int64_t e = kb + u < deg[i] ? (int64_t)__ldg(A.t_eid + k0[i] + kb + u) : -1;
+                        const int32_t k = k0[i] + kb + u;
+                        const int64_t e = kb + u < deg[i] ? (int64_t)(staged ? sTe[k - kt0] : __ldg(A.t_eid + k)) : -1;
                         z[i][u] = e >= 0 ? __ldg(reinterpret_cast<const uint2*>(A.dz1 + e * H) + lane)
                                          : make_uint2(0u, 0u);
                     }
@@ -1134,7 +1147,30 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
         float d[CW];
         ld_acc<CW>(tWork, q, c0, d);
         tc_fence_before();
-        if (valid) {
+        if constexpr (H == 128) {
+            // dx_in += d as whole rows per warp: the MMAs have read the operand tile, which now
+            // stages the FP32 rows [128 x 128] (row r at 512 r bytes, 16-byte chunks swizzled by r)
+            float4* sD = reinterpret_cast<float4*>(sA);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i)
+                sD[row * 32 + (((c0 / 4) + i) ^ (row & 7))] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+            __syncthreads();
+#pragma unroll 2
+            for (int i = 0; i < 8; ++i) {
+                const int rr = 8 * warp + i;
+                const int64_t rg = t * 128 + rr;
+                if (rg < A.n_rows) {
+                    float4* po = reinterpret_cast<float4*>(A.dx_in + rg * H) + lane;
+                    const float4 v = sD[rr * 32 + (lane ^ (rr & 7))];
+                    float4 o = *po;
+                    o.x += v.x;
+                    o.y += v.y;
+                    o.z += v.z;
+                    o.w += v.w;
+                    *po = o;
+                }
+            }
+        } else if (valid) {
             float4* po = reinterpret_cast<float4*>(A.dx_in + r * H + c0);
 #pragma unroll
             for (int i = 0; i < CW / 4; ++i) {

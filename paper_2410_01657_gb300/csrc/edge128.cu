@@ -123,6 +123,23 @@ __device__ __forceinline__ void ld_acc32(uint32_t taddr, const float* bias, floa
     }
 }
 
+// N accumulator columns [0, N) of this thread's lane with a single wait (the loads
+// overlap each other), plus bias.
+template <int N>
+__device__ __forceinline__ void ld_acc_n(uint32_t taddr, const float* bias, float* v) {
+#pragma unroll
+    for (int i = 0; i < N; i += 16) tmem_ld16(taddr + i, v + i);
+    tmem_ld_wait();
+    const float4* b4 = reinterpret_cast<const float4*>(bias);
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 b = b4[i];
+        float2* v2 = reinterpret_cast<float2*>(v + 4 * i);
+        v2[0] = __fadd2_rn(v2[0], make_float2(b.x, b.y));
+        v2[1] = __fadd2_rn(v2[1], make_float2(b.z, b.w));
+    }
+}
+
 // 32 FP32 columns of this thread's lane from registers into TMEM.
 __device__ __forceinline__ void st_tmem32(uint32_t taddr, const float* v) {
     tmem_st16(taddr, v);
@@ -294,12 +311,12 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
         ph_mma ^= 1;
         tc_fence_after();
 #pragma unroll
-        for (int c = 0; c < kH; c += 32) {
-            float v[32];
-            ld_acc32(tAcc + lane_base + c, sPar + c, v);
+        for (int h = 0; h < kH; h += 64) {   // two halves, one TMEM wait each
+            float v[64];
+            ld_acc_n<64>(tAcc + lane_base + h, sPar + h, v);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint4 up = pq[0][c / 8 + i], uq = pq[1][c / 8 + i];
+            for (int i = 0; i < 8; ++i) {
+                const uint4 up = pq[0][h / 8 + i], uq = pq[1][h / 8 + i];
                 const uint32_t pw[4] = {up.x, up.y, up.z, up.w}, qw[4] = {uq.x, uq.y, uq.z, uq.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -310,7 +327,8 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
                     *v2 = __fadd2_rn(*v2, __fadd2_rn(make_float2(p0, p1), make_float2(q0, q1)));
                 }
             }
-            elu_to_tmem(tA + lane_base + (uint32_t)(c / 2), v);
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) elu_to_tmem(tA + lane_base + (uint32_t)((h + c) / 2), v + c);
         }
         hand_off(tAcc, tA, sW + kWT, gi, leader, bar_mma);
         // hidden Linears 1 .. L-2
@@ -320,11 +338,11 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
             if (!ok) break;
             ph_mma ^= 1;
             tc_fence_after();
+            {
+                float v[kH];
+                ld_acc_n<kH>(tAcc + lane_base, sPar + k * kH, v);
 #pragma unroll
-            for (int c = 0; c < kH; c += 32) {
-                float v[32];
-                ld_acc32(tAcc + lane_base + c, sPar + k * kH + c, v);
-                elu_to_tmem(tA + lane_base + (uint32_t)(c / 2), v);
+                for (int c = 0; c < kH; c += 32) elu_to_tmem(tA + lane_base + (uint32_t)(c / 2), v + c);
             }
             hand_off(tAcc, tA, sW + (k + 1) * kWT, gi, leader, bar_mma);
         }
@@ -344,11 +362,9 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
         float mean, rstd;
         {
             float sp[4];
+            ld_acc_n<kH>(tAcc + lane_base, bk, ev);
 #pragma unroll
-            for (int c = 0; c < kH; c += 32) {
-                ld_acc32(tAcc + lane_base + c, bk + c, ev + c);
-                sp[c / 32] = sum32(ev + c);
-            }
+            for (int c = 0; c < kH; c += 32) sp[c / 32] = sum32(ev + c);
             mean = ((sp[0] + sp[1]) + (sp[2] + sp[3])) * (1.f / kH);
 #pragma unroll
             for (int c = 0; c < kH; c += 32) sp[c / 32] = sqdev32(ev + c, mean);
@@ -603,12 +619,12 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
         ph_mma ^= 1;
         tc_fence_after();
 #pragma unroll
-        for (int c = 0; c < kH; c += 32) {
-            float v[32];
-            ld_acc32(tAcc + lane_base + c, sPar + c, v);
+        for (int h = 0; h < kH; h += 64) {   // two halves, one TMEM wait each
+            float v[64];
+            ld_acc_n<64>(tAcc + lane_base + h, sPar + h, v);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint4 up = pq[0][c / 8 + i], uq = pq[1][c / 8 + i];
+            for (int i = 0; i < 8; ++i) {
+                const uint4 up = pq[0][h / 8 + i], uq = pq[1][h / 8 + i];
                 const uint32_t pw[4] = {up.x, up.y, up.z, up.w}, qw[4] = {uq.x, uq.y, uq.z, uq.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -619,7 +635,9 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
                     *v2 = __fadd2_rn(*v2, __fadd2_rn(make_float2(p0, p1), make_float2(q0, q1)));
                 }
             }
-            elu_to_tmem_and_tile(tA + lane_base + (uint32_t)(c / 2), v, sE, row, c, valid);
+#pragma unroll
+            for (int c = 0; c < 64; c += 32)
+                elu_to_tmem_and_tile(tA + lane_base + (uint32_t)((h + c) / 2), v + c, sE, row, h + c, valid);
         }
         save_hand_off(tAcc, tA, sW + kWT, gi, leader, bar_mma, &tmap_hs, sE, y);
         // hidden Linears 1 .. L-2
@@ -630,11 +648,12 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
             if (!ok) break;
             ph_mma ^= 1;
             tc_fence_after();
+            {
+                float v[kH];
+                ld_acc_n<kH>(tAcc + lane_base, sPar + k * kH, v);
 #pragma unroll
-            for (int c = 0; c < kH; c += 32) {
-                float v[32];
-                ld_acc32(tAcc + lane_base + c, sPar + k * kH + c, v);
-                elu_to_tmem_and_tile(tA + lane_base + (uint32_t)(c / 2), v, sE, row, c, valid);
+                for (int c = 0; c < kH; c += 32)
+                    elu_to_tmem_and_tile(tA + lane_base + (uint32_t)(c / 2), v + c, sE, row, c, valid);
             }
             save_hand_off(tAcc, tA, sW + (k + 1) * kWT, gi, leader, bar_mma, &tmap_hs,
                           sE, (int32_t)(k * A.hs_rows) + y);

@@ -197,3 +197,50 @@ def test_precision_form_million_node_subbrick():
         + list(g["node"]["W"]) + list(g["node"]["b"]) + [g["node"]["gamma"], g["node"]["beta"]]
     for k, (u, r) in enumerate(zip(gpu_grads, gref)):
         assert rel_l2(u, r) < 5e-2, (k, rel_l2(u, r))
+
+
+def test_precision_form_bf16_against_fp32_path_on_a_16cube_brick():
+    # the C3 precision form against the plain FP32 GPU path, layer by layer, on the
+    # largest brick the FP32 path holds beside it: 16^3 elements at p=7 (1,442,897
+    # nodes, 8.6M directed edges) in 8 RCB sub-graphs, H = 128, one layer forward and
+    # backward with counter-hashed inputs; every output and gradient within the BF16
+    # tolerances of the FP32 results (outputs 2e-2, gradients 5e-2)
+    import fullsize_util as fu
+
+    nel, p, H, R = (16, 16, 16), 7, 128, 8
+    part = MeshGraph(nel, p).partition(R, "rcb")
+    G = part.to_device(DEV)
+    N = part.graph.n_nodes
+    assert N == 113 ** 3
+    params = syn.gnn_params(51, H, 2, 1, randomize_affine=True)
+    x0, e0, dx = fu.device_inputs(part, H, N, DEV)
+    de1 = (0.5 * e0.float()).to(torch.bfloat16)
+    out = {}
+    for precision in ("bf16", "fp32"):
+        net = gnn.ConsistentGNN(params, precision=precision, device=DEV)
+        layer = net.layers[0]
+        tens = layer.edge.tensors() + layer.node.tensors()
+        W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+        cfg = gnn.mp_config(H, precision)
+        edt = torch.bfloat16 if precision == "bf16" else torch.float32
+        et = e0.to(edt)
+        xo, eo, a = torch.empty_like(x0), torch.empty_like(et), torch.empty_like(x0)
+        gnn.gnn_mp_forward(G, cfg, W, x0, et, xo, eo, a)
+        dparams = [torch.zeros_like(t) for t in tens]
+        dxi, dei = torch.empty_like(x0), torch.empty_like(et)
+        gnn.gnn_mp_backward(G, cfg, W, x0, et, a, dx, de1.to(edt), dxi, dei,
+                            gnn.mp_params(layer.edge.dims, layer.node.dims, dparams))
+        B.call("gnn_check", None)
+        out[precision] = ([xo.cpu(), eo.float().cpu(), a.cpu(), dxi.cpu(), dei.float().cpu()],
+                          [d.cpu() for d in dparams])
+        del xo, eo, a, dxi, dei, et
+        torch.cuda.empty_cache()
+    names = ["x'", "e'", "a*", "dL/dx", "dL/de"]
+    errs = {}
+    for k, (u, r) in enumerate(zip(out["bf16"][0], out["fp32"][0])):
+        errs[names[k]] = rel_l2(u.numpy(), r.numpy())
+        assert errs[names[k]] < (2e-2 if k < 3 else 5e-2), (names[k], errs[names[k]])
+    gerr = [rel_l2(u.numpy(), r.numpy()) for u, r in zip(out["bf16"][1], out["fp32"][1])]
+    assert max(gerr) < 5e-2, gerr
+    print("\nC3 form, 16^3 p=7, BF16 vs the FP32 GPU path:", {k: f"{v:.2e}" for k, v in errs.items()},
+          f"parameter gradients max {max(gerr):.2e} median {float(np.median(gerr)):.2e}")

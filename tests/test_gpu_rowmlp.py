@@ -121,3 +121,47 @@ def test_uncovered_shape_is_rejected():
     with pytest.raises(B.GnnError) as ei:
         B.call("gnn_mlp_workspace_size_bf16", ctypes.byref(s), 10, ctypes.byref(f), ctypes.byref(b))
     assert ei.value.code == B.GNN_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("dims,has_ln", [([4, 128, 128, 128, 128], True), ([128, 128, 128, 128, 3], False)])
+def test_plain_row_mlp_runs_in_row_blocks(dims, has_ln):
+    # The plain FP32 row MLP (the H = 128 encoders and decoder) runs over blocks of 2^22
+    # rows with a workspace sized for one block. On 2^22 + 1,000,003 rows its outputs
+    # must equal, bit for bit, two calls on the two row ranges, and its weight and input
+    # gradients the sum of the two calls' (the blocks accumulate in row order).
+    import ctypes as C
+
+    n0, n1 = 1 << 22, 1_000_003
+    rows = n0 + n1
+    P = _mlp_params(dims, has_ln, 17)
+    ts = [torch.as_tensor(t, dtype=torch.float32, device=DEV)
+          for t in [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if has_ln else [])]
+    S = gnn.mlp_struct(dims, ts, has_ln)
+    g = torch.Generator(device=DEV).manual_seed(5)
+    X = torch.randn(rows, dims[0], device=DEV, generator=g)
+    dY = torch.randn(rows, dims[-1], device=DEV, generator=g)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def fwd_bwd(lo, hi):
+        n = hi - lo
+        f, b = C.c_size_t(), C.c_size_t()
+        B.call("gnn_mlp_workspace_size", C.byref(S), n, C.byref(f), C.byref(b))
+        ws = gnn.workspace(max(f.value, b.value), DEV)
+        Y = torch.empty(n, dims[-1], device=DEV)
+        B.call("gnn_mlp_forward", C.byref(S), n, B.ptr(X[lo:hi]), B.ptr(Y), 0, 1e-5, B.ptr(ws), ws.numel(), stream)
+        dts = [torch.zeros_like(t) for t in ts]
+        dS = gnn.mlp_struct(dims, dts, has_ln)
+        dX = torch.empty(n, dims[0], device=DEV)
+        B.call("gnn_mlp_backward", C.byref(S), n, B.ptr(X[lo:hi]), B.ptr(dY[lo:hi]), 0, B.ptr(dX), C.byref(dS), 1e-5,
+               B.ptr(ws), ws.numel(), stream)
+        B.call("gnn_check", None)
+        return Y, dX, dts, f.value
+
+    Y, dX, dts, ws_all = fwd_bwd(0, rows)
+    Ya, dXa, da, ws_a = fwd_bwd(0, n0)
+    Yb, dXb, db, _ = fwd_bwd(n0, rows)
+    assert ws_all == ws_a                      # the workspace covers one block
+    assert torch.equal(Y[:n0], Ya) and torch.equal(Y[n0:], Yb)
+    assert torch.equal(dX[:n0], dXa) and torch.equal(dX[n0:], dXb)
+    for t, a, b in zip(dts, da, db):
+        assert torch.equal(t, a + b)

@@ -449,13 +449,18 @@ int gnn_mlp_backward(const gnn_mlp* P, int64_t n_rows, const float* X, const voi
 
 /* The same row MLP on the fused BF16 path (tcgen05 GEMMs with BF16 operands
  * and FP32 accumulation, FP32 bias / ELU / LayerNorm, activations recomputed
- * per tile in the backward). Covered shapes, H in {16, 32, 64}:
+ * in the backward). Covered shapes, H in {16, 32, 64}:
  *   encoder: dims[0] <= 16, every other width H, with LayerNorm;
- *   decoder: dims[0] = H, hidden widths H, dims[n_lin] <= 16, no LayerNorm.
+ *   decoder: dims[0] = H, hidden widths H, dims[n_lin] <= 16, no LayerNorm;
+ * and at H = 128 the encoder with 2 to 4 Linear layers, whose backward runs
+ * one Linear at a time over chunks of 128-row tiles with the recomputed
+ * activations in the workspace (Y and dY then 16-byte aligned, else GNN_EINVAL).
  * Same arguments and results as gnn_mlp_forward / gnn_mlp_backward (to BF16
- * tolerance); the forward needs no workspace, the backward the size
- * reported here (per-CTA gradient partials). GNN_EUNSUPPORTED for other
- * shapes (use the FP32 calls). */
+ * tolerance); the forward needs no workspace, the backward the size reported
+ * here for n_rows (per-CTA gradient partials; at H = 128 also the scratch of
+ * up to 2^22 rows, and a smaller workspace down to one tile's scratch is
+ * accepted and runs in more chunks, GNN_ENOMEM below that). GNN_EUNSUPPORTED
+ * for other shapes (use the FP32 calls). */
 int gnn_mlp_workspace_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* fwd_bytes, size_t* bwd_bytes);
 int gnn_mlp_forward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,
                          float ln_eps, void* ws, size_t ws_bytes, void* stream);
@@ -468,7 +473,8 @@ int gnn_mlp_backward_bf16(const gnn_mlp* P, int64_t n_rows, const float* X, cons
  * given that act recomputes only the last Linear. act: device, 16-byte
  * aligned, of gnn_mlp_act_size_bf16 bytes, caller-owned and unchanged from the
  * forward to the backward; 0 bytes (act may be NULL: the plain calls) for
- * shapes outside the fused row MLP or (L - 1) * R >= 2^31. Same results as
+ * shapes outside the fused row MLP, the H = 128 encoder (which recomputes)
+ * or (L - 1) * R >= 2^31. Same results as
  * gnn_mlp_forward_bf16 / gnn_mlp_backward_bf16. */
 int gnn_mlp_act_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* bytes);
 int gnn_mlp_forward_bf16_act(const gnn_mlp* P, int64_t n_rows, const float* X, void* Y, int32_t y_bf16,

@@ -79,7 +79,8 @@ int gnn_check(void* stream) {
     cudaError_t (*const take[])(unsigned int*) = {
         gnn::plain::take_device_error, gnn::fused::take_device_error, gnn::fused::take_device_error_bwd,
         gnn::fused::take_device_error_bwd128, gnn::fused::take_device_error_rowmlp,
-        gnn::fused::take_device_error_edge128, gnn::diag::take_device_error};
+        gnn::fused::take_device_error_edge128, gnn::fused::take_device_error_rowenc128,
+        gnn::diag::take_device_error};
     unsigned int word = 0;
     for (auto f : take) {
         unsigned int w = 0;
@@ -269,7 +270,7 @@ int gnn_mlp_workspace_size_bf16(const gnn_mlp* P, int64_t n_rows, size_t* fwd_by
     GNN_REQUIRE(gnn::fused::rowmlp_supported(*P), GNN_EUNSUPPORTED,
                 "gnn_mlp_workspace_size_bf16: shape not covered by the fused row MLP");
     *fwd_bytes = 0;
-    *bwd_bytes = gnn::fused::rowmlp_backward_ws(*P);
+    *bwd_bytes = gnn::fused::rowmlp_backward_ws(*P, n_rows);
     return GNN_OK;
 }
 

@@ -588,35 +588,7 @@ B128Ws carve_b128(void* ws, const gnn_graph_dev& G, int Le, int Ln, bool need_a,
 // dz_{k-1} and the gradients of W_k, b_{k-1} for k = L-1 .. 1 over a chunk of
 // n_tiles tiles; returns the buffer that holds dz_0.
 int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, cudaStream_t s) {
-    constexpr int H = H128;
-    const int L = W.n_lin;
-    const uint32_t smem = ChainSmem::total;
-    int grid;
-    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 4 * H, n_tiles, &grid);
-    if (rc) return rc;
-    const int64_t rows = n_tiles * 128;
-    for (int k = L - 1; k >= 1; --k) {
-        CUtensorMap tm_dz, tm_h;
-        if ((rc = make_row_tmap(&tm_dz, w.dzs[*cur], rows, H))) return rc;
-        if ((rc = make_row_tmap(&tm_h, w.hs + (int64_t)(k - 1) * w.hs_stride, rows, H))) return rc;
-        ChainArgs A;
-        A.W = W.W[k];
-        A.dz_out = w.dzs[*cur ^ 1];
-        A.n_tiles = n_tiles;
-        A.part = w.part;
-        A.pstride = kPstride;
-        {
-            ProfScope _ps(s, "k_bwd_chain");
-            k_bwd_chain<<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
-        }
-        GNN_LAUNCH_CHECK("k_bwd_chain");
-        RedSeg seg[2];
-        seg[0] = RedSeg{dW.W[k], H, H, H, 0, H};
-        seg[1] = RedSeg{dW.b[k - 1], H, 1, H, (int64_t)H * H, 0};
-        if ((rc = reduce_grads(seg, 2, w.part, kPstride, grid, s))) return rc;
-        *cur ^= 1;
-    }
-    return GNN_OK;
+    return chain_backward_h128(W, dW, w.hs, w.hs_stride, w.dzs, w.part, kPstride, n_tiles, cur, s);
 }
 
 // gamma, beta and the last bias of an MLP from the recomputation's partials
@@ -630,6 +602,40 @@ int reduce_ln(const gnn_mlp& dW, const B128Ws& w, int grid, cudaStream_t s) {
 }
 
 }  // namespace
+
+int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
+                        __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
+                        cudaStream_t s) {
+    constexpr int H = H128;
+    const int L = W.n_lin;
+    const uint32_t smem = ChainSmem::total;
+    int grid;
+    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 4 * H, n_tiles, &grid);
+    if (rc) return rc;
+    const int64_t rows = n_tiles * 128;
+    for (int k = L - 1; k >= 1; --k) {
+        CUtensorMap tm_dz, tm_h;
+        if ((rc = make_row_tmap(&tm_dz, dzs[*cur], rows, H))) return rc;
+        if ((rc = make_row_tmap(&tm_h, hs + (int64_t)(k - 1) * hs_stride, rows, H))) return rc;
+        ChainArgs A;
+        A.W = W.W[k];
+        A.dz_out = dzs[*cur ^ 1];
+        A.n_tiles = n_tiles;
+        A.part = part;
+        A.pstride = pstride;
+        {
+            ProfScope _ps(s, "k_bwd_chain");
+            k_bwd_chain<<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
+        }
+        GNN_LAUNCH_CHECK("k_bwd_chain");
+        RedSeg seg[2];
+        seg[0] = RedSeg{dW.W[k], H, H, H, 0, H};
+        seg[1] = RedSeg{dW.b[k - 1], H, 1, H, (int64_t)H * H, 0};
+        if ((rc = reduce_grads(seg, 2, part, pstride, grid, s))) return rc;
+        *cur ^= 1;
+    }
+    return GNN_OK;
+}
 
 size_t backward_h128_ws(const gnn_graph_dev& G, const gnn_mp_params& W) {
     return carve_b128(nullptr, G, W.edge.n_lin, W.node.n_lin, true, default_chunk(G)).bytes;

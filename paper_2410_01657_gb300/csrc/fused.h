@@ -9,12 +9,14 @@
 namespace gnn {
 namespace fused {
 
-// Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu, edge128.cu.
+// Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu, edge128.cu,
+// rowenc128.cu.
 cudaError_t take_device_error(unsigned int* out);
 cudaError_t take_device_error_bwd(unsigned int* out);
 cudaError_t take_device_error_bwd128(unsigned int* out);
 cudaError_t take_device_error_rowmlp(unsigned int* out);
 cudaError_t take_device_error_edge128(unsigned int* out);
+cudaError_t take_device_error_rowenc128(unsigned int* out);
 // The H = 128 edge forward with two tile groups per SM and the hidden
 // activations in tensor memory (edge128.cu); supported for 2..4 Linears.
 bool edge_fwd_tm_supported(const gnn_mp_params& W);
@@ -92,9 +94,29 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
                   float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
                   cudaStream_t s);
 
+// The per-Linear adjoint k = L-1 .. 1 of an H = 128 MLP (k_bwd_chain, bwd128.cu)
+// over n_tiles tiles of tile-padded BF16 scratch rows: reads dz_{L-1} from
+// dzs[*cur] and h_{k-1} from hs + (k - 1) hs_stride, writes each dz_{k-1} into
+// the other buffer (flipping *cur, so that dzs[*cur] ends holding dz_0) and adds
+// dW_k, db_{k-1} into dW. part holds pstride >= H (H + 1) floats for each CTA of
+// a persistent grid (one CTA per SM).
+int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
+                        __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
+                        cudaStream_t s);
+
+// Fused BF16 encoder row MLP at H = 128 (rowenc128.cu): in <= 16, 2..4 Linears
+// of width 128, LayerNorm; the adjoint recomputes the activations layer by layer
+// in a workspace of rowenc128_backward_ws bytes (smaller ones run in more chunks).
+bool rowenc128_shape(const gnn_mlp& P);
+size_t rowenc128_backward_ws(const gnn_mlp& P, int64_t n_rows);
+int rowenc128_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps,
+                      cudaStream_t s);
+int rowenc128_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
+                       const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s);
+
 // Fused BF16 row MLP (encoders / decoder of the network).
 bool rowmlp_supported(const gnn_mlp& P);
-size_t rowmlp_backward_ws(const gnn_mlp& P);
+size_t rowmlp_backward_ws(const gnn_mlp& P, int64_t n_rows);
 // Bytes of a row MLP's saved activations (n_lin - 1 blocks of ceil(n_rows / 128)
 // * 128 BF16 rows of H), 0 where none are kept.
 size_t rowmlp_act_bytes(const gnn_mlp& P, int64_t n_rows);

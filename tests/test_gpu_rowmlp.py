@@ -113,6 +113,60 @@ def test_encoder_many_tiles_and_deterministic():
             assert np.array_equal(u, v)
 
 
+@pytest.mark.parametrize("n_in,n_hidden,rows,out_bf16,need_dx", [
+    (3, 2, 5003, False, False), (4, 2, 70001, True, True), (16, 0, 1000, False, True),
+    (1, 1, 127, True, False), (5, 2, 1, False, True)])
+def test_encoder_h128(n_in, n_hidden, rows, out_bf16, need_dx):
+    # the H = 128 encoder (tensor-memory forward; layered adjoint with the
+    # recomputed activations in the workspace): ragged row counts, one row, one tile
+    dims = [n_in] + [128] * (n_hidden + 2)
+    _check(_mlp_params(dims, True, 128 + n_in + n_hidden), dims, True, rows, 11, out_bf16=out_bf16,
+           need_dx=need_dx)
+
+
+def test_encoder_h128_chunks_and_determinism():
+    # A workspace smaller than the one reported runs the adjoint in several chunks
+    # of tiles: the same gradients up to the order of the per-chunk sums; two runs
+    # with the same workspace agree bit for bit; a workspace below one tile's scratch
+    # is refused with GNN_ENOMEM; zero rows is a no-op.
+    import ctypes as C
+
+    dims = [4, 128, 128, 128, 128]
+    rows = 200001
+    P = _mlp_params(dims, True, 21)
+    ts = [torch.as_tensor(t, dtype=torch.float32, device=DEV) for t in [*P["W"], *P["b"], P["gamma"], P["beta"]]]
+    S = gnn.mlp_struct(dims, ts, True)
+    g = torch.Generator(device=DEV).manual_seed(3)
+    X = torch.randn(rows, 4, device=DEV, generator=g)
+    dY = torch.randn(rows, 128, device=DEV, generator=g).to(torch.bfloat16)
+    stream = torch.cuda.current_stream().cuda_stream
+    f, b = C.c_size_t(), C.c_size_t()
+    B.call("gnn_mlp_workspace_size_bf16", C.byref(S), rows, C.byref(f), C.byref(b))
+
+    def bwd(ws_bytes, n=rows):
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
+        dts = [torch.zeros_like(t) for t in ts]
+        dS = gnn.mlp_struct(dims, dts, True)
+        dX = torch.empty(n, 4, device=DEV)
+        B.call("gnn_mlp_backward_bf16", C.byref(S), n, B.ptr(X), B.ptr(dY), 1, B.ptr(dX), C.byref(dS), 1e-5,
+               B.ptr(ws), ws_bytes, stream)
+        B.call("gnn_check", None)
+        return dX, dts
+
+    dX, d1 = bwd(b.value)
+    dXa, da = bwd(int(b.value * 0.3))
+    dXb, db = bwd(int(b.value * 0.3))
+    assert torch.equal(dXa, dX)                 # dX is per row: independent of the chunking
+    for u, v, w in zip(d1, da, db):
+        assert torch.equal(v, w)
+        assert (v - u).norm() <= 1e-5 * u.norm()
+    with pytest.raises(B.GnnError) as ei:
+        bwd(1 << 20)
+    assert ei.value.code == B.GNN_ENOMEM
+    _, dz = bwd(b.value, 0)
+    assert all(int(torch.count_nonzero(t)) == 0 for t in dz)
+
+
 def test_uncovered_shape_is_rejected():
     dims = [8, 24, 24, 5]
     assert not gnn.rowmlp_fused_shape(dims, False)

@@ -52,12 +52,17 @@ struct ChainArgs {
     int64_t n_tiles;
     float* part;                 // per-CTA: dW_k [H x H], then db_{k-1} [H]
     int64_t pstride;
+    float* dx;                   // INPUT: dX rows [n_rows x H] (FP32); scratch row i is row row0 + i
+    int64_t row0, n_rows;
 };
 
 // One CTA per SM, 128 rows x 4 column groups of 32 columns. Three stages of
 // {dz_k rows, h_{k-1} rows} keep two tiles' loads in flight, and two TMEM
 // accumulators let thread 0 issue tile j+1's MMAs while the block runs tile
 // j's epilogue (the weight gradient accumulates in a third region).
+// INPUT: the first Linear of a row MLP whose input X is no activation: h_{k-1}
+// is the BF16 copy of X, and the epilogue writes dX = dz_0 W_0 in FP32 instead
+// of an ELU adjoint (no bias gradient).
 constexpr int kChainNT = 512;
 constexpr int kChainNS = 3;
 struct ChainSmem {
@@ -68,6 +73,7 @@ struct ChainSmem {
 };
 static_assert(ChainSmem::total <= 227 * 1024, "k_bwd_chain shared memory");
 
+template <bool INPUT>
 __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant__ CUtensorMap tm_dz,
                                                           const __grid_constant__ CUtensorMap tm_h, ChainArgs A) {
     constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kChainNT, NCH = CW / 16, NS = kChainNS;
@@ -147,20 +153,35 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
         __syncwarp();
         tc_fence_after();
         const int64_t t = tile_of(j);
-        __nv_bfloat16* zrow = A.dz_out + (t * 128 + row) * H + c0;
-        const uint8_t* hT = sDz(s) + kTile;
+        if constexpr (INPUT) {
+            const int64_t gr = A.row0 + t * 128 + row;
 #pragma unroll
-        for (int jj = 0; jj < NCH; ++jj) {
-            float dh[16], hv[16];
-            tmem_ld16(tWork(b) + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * jj), dh);
-            ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
-            ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
-            tmem_ld_wait();
+            for (int jj = 0; jj < NCH; ++jj) {
+                float dh[16];
+                tmem_ld16(tWork(b) + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * jj), dh);
+                tmem_ld_wait();
+                if (A.dx && gr < A.n_rows) {
+                    float4* d4 = reinterpret_cast<float4*>(A.dx + gr * H + c0 + 16 * jj);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
-            st_bf16x8(zrow + 16 * jj, dh);
-            st_bf16x8(zrow + 16 * jj + 8, dh + 8);
-            acc[jj] += warp_colsum16(dh, lane);
+                    for (int i = 0; i < 4; ++i) d4[i] = make_float4(dh[4 * i], dh[4 * i + 1], dh[4 * i + 2], dh[4 * i + 3]);
+                }
+            }
+        } else {
+            __nv_bfloat16* zrow = A.dz_out + (t * 128 + row) * H + c0;
+            const uint8_t* hT = sDz(s) + kTile;
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj) {
+                float dh[16], hv[16];
+                tmem_ld16(tWork(b) + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 + 16 * jj), dh);
+                ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
+                ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
+                st_bf16x8(zrow + 16 * jj, dh);
+                st_bf16x8(zrow + 16 * jj + 8, dh + 8);
+                acc[jj] += warp_colsum16(dh, lane);
+            }
         }
         tc_fence_before();
         fence_proxy_async();
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
         else
             for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
     }
-    colsum_store<H, NCH>(acc, sRed, q, lane, c0, tid, NT, part + H * H);
+    if constexpr (!INPUT) colsum_store<H, NCH>(acc, sRed, q, lane, c0, tid, NT, part + H * H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -610,14 +631,14 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
     const int L = W.n_lin;
     const uint32_t smem = ChainSmem::total;
     int grid;
-    int rc = persistent_grid(k_bwd_chain, kChainNT, smem, 4 * H, n_tiles, &grid);
+    int rc = persistent_grid(k_bwd_chain<false>, kChainNT, smem, 4 * H, n_tiles, &grid);
     if (rc) return rc;
     const int64_t rows = n_tiles * 128;
     for (int k = L - 1; k >= 1; --k) {
         CUtensorMap tm_dz, tm_h;
         if ((rc = make_row_tmap(&tm_dz, dzs[*cur], rows, H))) return rc;
         if ((rc = make_row_tmap(&tm_h, hs + (int64_t)(k - 1) * hs_stride, rows, H))) return rc;
-        ChainArgs A;
+        ChainArgs A{};
         A.W = W.W[k];
         A.dz_out = dzs[*cur ^ 1];
         A.n_tiles = n_tiles;
@@ -625,7 +646,7 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
         A.pstride = pstride;
         {
             ProfScope _ps(s, "k_bwd_chain");
-            k_bwd_chain<<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
+            k_bwd_chain<false><<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
         }
         GNN_LAUNCH_CHECK("k_bwd_chain");
         RedSeg seg[2];
@@ -635,6 +656,33 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
         *cur ^= 1;
     }
     return GNN_OK;
+}
+
+int chain_input_h128(const float* W0, float* dW0, const __nv_bfloat16* dz, const __nv_bfloat16* xb, float* dx,
+                     int64_t row0, int64_t n_rows, float* part, int64_t pstride, int64_t n_tiles, cudaStream_t s) {
+    constexpr int H = H128;
+    const uint32_t smem = ChainSmem::total;
+    int grid;
+    int rc = persistent_grid(k_bwd_chain<true>, kChainNT, smem, 4 * H, n_tiles, &grid);
+    if (rc) return rc;
+    CUtensorMap tm_dz, tm_h;
+    if ((rc = make_row_tmap(&tm_dz, dz, n_tiles * 128, H))) return rc;
+    if ((rc = make_row_tmap(&tm_h, xb, n_tiles * 128, H))) return rc;
+    ChainArgs A{};
+    A.W = W0;
+    A.n_tiles = n_tiles;
+    A.part = part;
+    A.pstride = pstride;
+    A.dx = dx;
+    A.row0 = row0;
+    A.n_rows = n_rows;
+    {
+        ProfScope _ps(s, "k_bwd_chain");
+        k_bwd_chain<true><<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
+    }
+    GNN_LAUNCH_CHECK("k_bwd_chain");
+    RedSeg seg[1] = {RedSeg{dW0, H, H, H, 0, H}};
+    return reduce_grads(seg, 1, part, pstride, grid, s);
 }
 
 size_t backward_h128_ws(const gnn_graph_dev& G, const gnn_mp_params& W) {

@@ -10,13 +10,14 @@ namespace gnn {
 namespace fused {
 
 // Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu, edge128.cu,
-// rowenc128.cu.
+// rowenc128.cu, rowdec128.cu.
 cudaError_t take_device_error(unsigned int* out);
 cudaError_t take_device_error_bwd(unsigned int* out);
 cudaError_t take_device_error_bwd128(unsigned int* out);
 cudaError_t take_device_error_rowmlp(unsigned int* out);
 cudaError_t take_device_error_edge128(unsigned int* out);
 cudaError_t take_device_error_rowenc128(unsigned int* out);
+cudaError_t take_device_error_rowdec128(unsigned int* out);
 // The H = 128 edge forward with two tile groups per SM and the hidden
 // activations in tensor memory (edge128.cu); supported for 2..4 Linears.
 bool edge_fwd_tm_supported(const gnn_mp_params& W);
@@ -103,6 +104,12 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
 int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
                         __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
                         cudaStream_t s);
+// The same kernel on the first Linear of a row MLP whose input X is data: with
+// dz_0 and the BF16 copy of X in tile-padded scratch rows (row i of the scratch
+// is row row0 + i of X), writes dX = dz_0 W_0 (FP32 [n_rows x H], rows below
+// n_rows only) and adds dW_0 = dz_0^T X into dW0 ([H x H]).
+int chain_input_h128(const float* W0, float* dW0, const __nv_bfloat16* dz, const __nv_bfloat16* xb, float* dx,
+                     int64_t row0, int64_t n_rows, float* part, int64_t pstride, int64_t n_tiles, cudaStream_t s);
 
 // Fused BF16 encoder row MLP at H = 128 (rowenc128.cu): in <= 16, 2..4 Linears
 // of width 128, LayerNorm; the adjoint recomputes the activations layer by layer
@@ -113,6 +120,14 @@ int rowenc128_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y,
                       cudaStream_t s);
 int rowenc128_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
                        const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s);
+
+// Fused BF16 decoder row MLP at H = 128 (rowdec128.cu): in = hidden = 128, out <= 16,
+// 2..4 Linears, no LayerNorm; workspace and chunking as the encoder's.
+bool rowdec128_shape(const gnn_mlp& P);
+size_t rowdec128_backward_ws(const gnn_mlp& P, int64_t n_rows);
+int rowdec128_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, cudaStream_t s);
+int rowdec128_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
+                       const gnn_mlp& dP, void* ws, size_t ws_bytes, cudaStream_t s);
 
 // Fused BF16 row MLP (encoders / decoder of the network).
 bool rowmlp_supported(const gnn_mlp& P);

@@ -7,8 +7,9 @@
 // Two shapes are covered, fixed at compile time, for H in {16, 32, 64}:
 //   encoder  in_dim <= 16 (padded to 16), hidden H, out H, LayerNorm;
 //   decoder  in_dim = H, hidden H, out_dim <= 16 (padded to 16), no LayerNorm.
-// The encoder at H = 128 (2..4 Linears) runs in rowenc128.cu. Other shapes stay
-// on the plain FP32 path (gnn_mlp_* with GNN_PREC_FP32).
+// At H = 128 (2..4 Linears) the encoder runs in rowenc128.cu and the decoder in
+// rowdec128.cu. Other shapes stay on the plain FP32 path (gnn_mlp_* with
+// GNN_PREC_FP32).
 
 #include <algorithm>
 #include <cstring>
@@ -729,11 +730,12 @@ int rowmlp_shape(const gnn_mlp& P, int* H) {
 
 bool rowmlp_supported(const gnn_mlp& P) {
     int H;
-    return rowmlp_shape(P, &H) != 0 || rowenc128_shape(P);
+    return rowmlp_shape(P, &H) != 0 || rowenc128_shape(P) || rowdec128_shape(P);
 }
 
 size_t rowmlp_backward_ws(const gnn_mlp& P, int64_t n_rows) {
     if (rowenc128_shape(P)) return rowenc128_backward_ws(P, n_rows);
+    if (rowdec128_shape(P)) return rowdec128_backward_ws(P, n_rows);
     int H;
     const int k = rowmlp_shape(P, &H);
     if (!k) return 0;
@@ -751,7 +753,9 @@ size_t rowmlp_act_bytes(const gnn_mlp& P, int64_t n_rows) {
 
 int rowmlp_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, int y_bf16, float eps,
                    cudaStream_t s, __nv_bfloat16* act) {
-    if (rowenc128_shape(P)) return rowenc128_forward(P, n_rows, X, Y, y_bf16, eps, s);   // keeps no activations
+    // H = 128: no activations kept (the adjoint recomputes them)
+    if (rowenc128_shape(P)) return rowenc128_forward(P, n_rows, X, Y, y_bf16, eps, s);
+    if (rowdec128_shape(P)) return rowdec128_forward(P, n_rows, X, Y, y_bf16, s);
     int H;
     const int k = rowmlp_shape(P, &H);
     GNN_REQUIRE(k, GNN_EUNSUPPORTED, "gnn_mlp_forward_bf16: shape not covered by the fused row MLP");
@@ -774,6 +778,7 @@ int rowmlp_forward(const gnn_mlp& P, int64_t n_rows, const float* X, void* Y, in
 int rowmlp_backward(const gnn_mlp& P, int64_t n_rows, const float* X, const void* dY, int dy_bf16, float* dX,
                     const gnn_mlp& dP, float eps, void* ws, size_t ws_bytes, cudaStream_t s, const __nv_bfloat16* act) {
     if (rowenc128_shape(P)) return rowenc128_backward(P, n_rows, X, dY, dy_bf16, dX, dP, eps, ws, ws_bytes, s);
+    if (rowdec128_shape(P)) return rowdec128_backward(P, n_rows, X, dY, dy_bf16, dX, dP, ws, ws_bytes, s);
     int H;
     const int k = rowmlp_shape(P, &H);
     GNN_REQUIRE(k, GNN_EUNSUPPORTED, "gnn_mlp_backward_bf16: shape not covered by the fused row MLP");

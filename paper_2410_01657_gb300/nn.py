@@ -165,13 +165,13 @@ class ConsistentMPFunction(torch.autograd.Function):
 def rowmlp_fused_shape(dims, has_ln: bool) -> bool:
     """True when the fused BF16 row MLP covers this block (gnn_mlp_forward_bf16):
     hidden widths H in {16, 32, 64}, an encoder (in <= 16, out H, LayerNorm) or a
-    decoder (in H, out <= 16, no LayerNorm); and at H = 128 an encoder of 2 to 4
+    decoder (in H, out <= 16, no LayerNorm); at H = 128 either with 2 to 4
     Linear layers."""
     H = dims[1]
     if len(dims) < 3 or H not in (16, 32, 64, 128) or any(d != H for d in dims[1:-1]):
         return False
-    if H == 128:
-        return has_ln and dims[0] <= 16 and dims[-1] == H and len(dims) <= 5
+    if H == 128 and len(dims) > 5:
+        return False
     if has_ln:
         return dims[0] <= 16 and dims[-1] == H
     return dims[0] == H and dims[-1] <= 16

@@ -124,21 +124,32 @@ def test_encoder_h128(n_in, n_hidden, rows, out_bf16, need_dx):
            need_dx=need_dx)
 
 
-def test_encoder_h128_chunks_and_determinism():
+@pytest.mark.parametrize("n_hidden,n_out,rows,need_dx", [
+    (2, 3, 5003, True), (1, 16, 70001, True), (0, 1, 1000, False), (2, 5, 1, True)])
+def test_decoder_h128(n_hidden, n_out, rows, need_dx):
+    # the H = 128 decoder: N = 16 last Linear, its adjoint inside the recomputation,
+    # the chain kernel's input pass for dX and dW_0
+    dims = [128] * (n_hidden + 2) + [n_out]
+    _check(_mlp_params(dims, False, 300 + n_hidden + n_out), dims, False, rows, 12, need_dx=need_dx)
+
+
+@pytest.mark.parametrize("dims,has_ln", [([4, 128, 128, 128, 128], True), ([128, 128, 128, 128, 3], False)])
+def test_row_mlp_h128_chunks_and_determinism(dims, has_ln):
     # A workspace smaller than the one reported runs the adjoint in several chunks
     # of tiles: the same gradients up to the order of the per-chunk sums; two runs
     # with the same workspace agree bit for bit; a workspace below one tile's scratch
     # is refused with GNN_ENOMEM; zero rows is a no-op.
     import ctypes as C
 
-    dims = [4, 128, 128, 128, 128]
     rows = 200001
-    P = _mlp_params(dims, True, 21)
-    ts = [torch.as_tensor(t, dtype=torch.float32, device=DEV) for t in [*P["W"], *P["b"], P["gamma"], P["beta"]]]
-    S = gnn.mlp_struct(dims, ts, True)
+    n_in, n_out = dims[0], dims[-1]
+    P = _mlp_params(dims, has_ln, 21)
+    ts = [torch.as_tensor(t, dtype=torch.float32, device=DEV)
+          for t in [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if has_ln else [])]
+    S = gnn.mlp_struct(dims, ts, has_ln)
     g = torch.Generator(device=DEV).manual_seed(3)
-    X = torch.randn(rows, 4, device=DEV, generator=g)
-    dY = torch.randn(rows, 128, device=DEV, generator=g).to(torch.bfloat16)
+    X = torch.randn(rows, n_in, device=DEV, generator=g)
+    dY = torch.randn(rows, n_out, device=DEV, generator=g).to(torch.bfloat16)
     stream = torch.cuda.current_stream().cuda_stream
     f, b = C.c_size_t(), C.c_size_t()
     B.call("gnn_mlp_workspace_size_bf16", C.byref(S), rows, C.byref(f), C.byref(b))
@@ -146,8 +157,8 @@ def test_encoder_h128_chunks_and_determinism():
     def bwd(ws_bytes, n=rows):
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
         dts = [torch.zeros_like(t) for t in ts]
-        dS = gnn.mlp_struct(dims, dts, True)
-        dX = torch.empty(n, 4, device=DEV)
+        dS = gnn.mlp_struct(dims, dts, has_ln)
+        dX = torch.empty(n, n_in, device=DEV)
         B.call("gnn_mlp_backward_bf16", C.byref(S), n, B.ptr(X), B.ptr(dY), 1, B.ptr(dX), C.byref(dS), 1e-5,
                B.ptr(ws), ws_bytes, stream)
         B.call("gnn_check", None)

@@ -22,6 +22,7 @@ GNN_GRAPH_BRICK, GNN_GRAPH_ELEMENTS = 0, 1
 GNN_PREC_FP32, GNN_PREC_BF16 = 0, 1
 GNN_HALO_SYNC, GNN_HALO_NONE = 0, 1
 GNN_FLAG_NO_EDGE_OUT = 1
+GNN_FLAG_ADJ_ONE_LINEAR = 2
 GNN_EDGE_FWD_AUTO, GNN_EDGE_FWD_RT, GNN_EDGE_FWD_WS, GNN_EDGE_FWD_ONE, GNN_EDGE_FWD_TM = 0, 1, 2, 3, 4
 GNN_MAX_LIN = 8
 GNN_EDGE_TILE = 128

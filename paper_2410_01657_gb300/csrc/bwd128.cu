@@ -11,7 +11,7 @@
 //       recompute the MLP, save h_0 .. h_{L-2} (and a node tile's BF16
 //       [a*, x] rows), apply the LayerNorm adjoint: dz_{L-1}, dgamma, dbeta,
 //       db_{L-1}
-//   k_bwd_chain, k = L-1 .. 1
+//   k_bwd_chain2 / k_bwd_chain, k = L-1 .. 1, two Linears per pass while two remain
 //       dh_{k-1} = dz_k W_k, dz_{k-1} = dh_{k-1} ELU'(h_{k-1}),
 //       dW_k += dz_k^T h_{k-1} (TMEM, over the CTA's tiles), db_{k-1}
 //   k_bwd_node0   [da*, dx] = dz_0 W_0, dW_0 += dz_0^T [a*, x], dx_in = dx' + dx
@@ -42,7 +42,7 @@ constexpr int H128 = 128;
 constexpr int kTile = 128 * H128 * 2;        // [128 x 128] BF16 row tile
 constexpr int kS = 128;                       // swizzle span of a 128-wide BF16 tile
 constexpr int64_t kChunkTiles = 32768;        // tiles per scratch chunk
-constexpr int64_t kPstride = 2 * H128 * H128 + H128;   // per-CTA partial floats (largest kernel: dW_0 of nodes)
+constexpr int64_t kPstride = 2 * H128 * H128 + 2 * H128;   // per-CTA partial floats (largest: k_bwd_chain2)
 
 // ------------------------------------------------------------------ k_bwd_chain
 
@@ -205,6 +205,209 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
             for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
     }
     if constexpr (!INPUT) colsum_store<H, NCH>(acc, sRed, q, lane, c0, tid, NT, part + H * H);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 4 * H);
+}
+
+// ------------------------------------------------------------------ k_bwd_chain2
+//
+// Two consecutive Linears k and k-1 of the per-Linear adjoint in one pass, so
+// that dz_{k-1} never travels through HBM: per tile, MMA pair 1 (D1 = dz_k W_k,
+// dW_k += dz_k^T h_{k-1}), epilogue 1 (dz_{k-1} = D1 ELU'(h_{k-1}) as BF16 into
+// the shared-memory slot dz_k came in, which pair 1 has finished reading, and
+// its column sums), MMA pair 2 (D2 = dz_{k-1} W_{k-1}, dW_{k-1} += dz_{k-1}^T
+// h_{k-2}), epilogue 2 (dz_{k-2} = D2 ELU'(h_{k-2}) to HBM, its column sums).
+// The operands and roundings are those of two k_bwd_chain passes, so the
+// results are the same bit for bit. TMEM: D1, D2, dW_k, dW_{k-1} (128 columns
+// each). Two stages of {dz_k, h_{k-1}} rows keep the next tile's load in flight;
+// h_{k-2} has one stage, reloaded as soon as epilogue 2 has read it into
+// registers; thread 0 issues tile j+1's pair 1 right after tile j's pair 2.
+
+struct Chain2Args {
+    const float* Wa;             // W_k [H x H] (FP32)
+    const float* Wb;             // W_{k-1}
+    __nv_bfloat16* dz_out;       // dz_{k-2} rows (tile-padded)
+    int64_t n_tiles;
+    float* part;                 // per-CTA: dW_k, dW_{k-1} [H x H], then db_{k-1}, db_{k-2} [H]
+    int64_t pstride;
+};
+
+constexpr int kC2NT = 512;
+struct Chain2Smem {
+    static constexpr uint32_t wa = 0, wb = kTile;
+    static constexpr uint32_t a = 2 * kTile;          // stage s: dz_k (then dz_{k-1}), h_{k-1}, at a + s * 2 * kTile
+    static constexpr uint32_t b = a + 4 * kTile;      // h_{k-2}
+    static constexpr uint32_t red = a;                // 4 x H floats, after the tile loop
+    static constexpr uint32_t bar = b + kTile;        // fullA[2], fullB, c1, c2, TMEM slot
+    static constexpr uint32_t total = bar + 64 + 1024;
+};
+static_assert(Chain2Smem::total <= 227 * 1024, "k_bwd_chain2 shared memory");
+
+__global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__ CUtensorMap tm_dz,
+                                                         const __grid_constant__ CUtensorMap tm_ha,
+                                                         const __grid_constant__ CUtensorMap tm_hb, Chain2Args A) {
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kC2NT, NCH = CW / 16;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    uint8_t* sWa = sm + Chain2Smem::wa;
+    uint8_t* sWb = sm + Chain2Smem::wb;
+    uint8_t* sHb = sm + Chain2Smem::b;
+    float* sRed = reinterpret_cast<float*>(sm + Chain2Smem::red);
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(sm + Chain2Smem::bar);   // fullA[2]: stage landed
+    uint64_t* fullB = fullA + 2;   // h_{k-2} landed
+    uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
+    uint64_t* c2 = fullA + 4;      // MMA pair 2 complete
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 5);
+    auto sDz = [&](int st) { return sm + Chain2Smem::a + st * 2 * kTile; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    if (warp == 0) {
+        tmem_alloc(tslot, 4 * H);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(fullA + i, 1);
+        fence_mbar_init();
+    }
+    load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
+    load_weight(sWb, A.Wb, H, 0, H, H, tid, NT);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, tD1 = tmem, tD2 = tmem + H, tWa = tmem + 2 * H, tWb = tmem + 3 * H;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int64_t n_mine = A.n_tiles > (int64_t)blockIdx.x
+                               ? (A.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };
+    // thread 0 only: loads and MMA pairs issued so far, and whether it is still well
+    int64_t nA = 0, nB = 0, n1 = 0, n2 = 0;
+    bool ok0 = true;
+    auto issue_A = [&]() {   // dz_k and h_{k-1} rows of tile nA into stage nA % 2
+        const int st = (int)(nA & 1);
+        const int32_t y = (int32_t)(tile_of(nA) * 128);
+        mbar_arrive_expect_tx(fullA + st, 2 * kTile);
+        for (int kb = 0; kb < 2; ++kb) {
+            tma_load_2d(sDz(st) + kb * 128 * S, &tm_dz, kb * 64, y, fullA + st);
+            tma_load_2d(sDz(st) + kTile + kb * 128 * S, &tm_ha, kb * 64, y, fullA + st);
+        }
+        ++nA;
+    };
+    auto issue_B = [&]() {   // h_{k-2} rows of tile nB
+        const int32_t y = (int32_t)(tile_of(nB) * 128);
+        mbar_arrive_expect_tx(fullB, kTile);
+        for (int kb = 0; kb < 2; ++kb) tma_load_2d(sHb + kb * 128 * S, &tm_hb, kb * 64, y, fullB);
+        ++nB;
+    };
+    auto issue_pair1 = [&]() {   // tile n1's first MMA pair once its stage has landed
+        const int st = (int)(n1 & 1);
+        ok0 = ok0 && mbar_wait(fullA + st, (uint32_t)(n1 >> 1) & 1u);
+        if (!ok0) return;
+        tc_fence_after();
+        issue_dgrad(tD1, sDz(st), S, sWa, S, H, (uint32_t)H * S, H, H);
+        issue_wgrad(tWa, sDz(st), S, 128u * S, sDz(st) + kTile, S, 128u * S, H, n1 > 0);
+        mma_commit(c1);
+        ++n1;
+    };
+    if (tid == 0 && n_mine > 0) {
+        while (nA < n_mine && nA < 2) issue_A();
+        issue_B();
+        issue_pair1();
+    }
+    float acc1[NCH], acc2[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) acc1[j] = acc2[j] = 0.f;
+    bool ok = true;
+    for (int64_t j = 0; j < n_mine; ++j) {
+        const int st = (int)(j & 1);
+        const uint32_t par = (uint32_t)j & 1u;   // c1, c2 and fullB complete once per tile
+        // epilogue 1: dz_{k-1} into the dz_k slot of the stage, column sums for db_{k-1}
+        ok = ok && mbar_wait(c1, par);
+        __syncwarp();
+        tc_fence_after();
+        {
+            uint8_t* z = sDz(st);
+            const uint8_t* hT = sDz(st) + kTile;
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj) {
+                float dh[16], hv[16];
+                tmem_ld16(tD1 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+                ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
+                ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
+                st_tile8(z, row, c0 + 16 * jj, 128, S, dh);
+                st_tile8(z, row, c0 + 16 * jj + 8, 128, S, dh + 8);
+                acc1[jj] += warp_colsum16(dh, lane);
+            }
+        }
+        tc_fence_before();
+        fence_proxy_async();
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+        if (!ok) break;
+        if (tid == 0) {   // pair 2 on dz_{k-1}; then the next tile's pair 1 (D1 has been read)
+            ok0 = mbar_wait(fullB, par);
+            if (ok0) {
+                tc_fence_after();
+                issue_dgrad(tD2, sDz(st), S, sWb, S, H, (uint32_t)H * S, H, H);
+                issue_wgrad(tWb, sDz(st), S, 128u * S, sHb, S, 128u * S, H, n2 > 0);
+                mma_commit(c2);
+                ++n2;
+                if (j + 1 < n_mine) issue_pair1();
+            }
+        }
+        // epilogue 2: dz_{k-2} to HBM, column sums for db_{k-2}
+        ok = ok && mbar_wait(c2, par);
+        __syncwarp();
+        tc_fence_after();
+        float hb[CW];   // this thread's h_{k-2}, read before the stage is reloaded
+#pragma unroll
+        for (int i = 0; i < CW; i += 8) ld_tile8(sHb, row, c0 + i, 128, S, hb + i);
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+        if (!ok) break;
+        if (tid == 0 && nB < n_mine) issue_B();   // pair 2 has read h_{k-2} (c2), so has every thread
+        {
+            __nv_bfloat16* zrow = A.dz_out + (tile_of(j) * 128 + row) * H + c0;
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj) {
+                float dh[16];
+                tmem_ld16(tD2 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hb[16 * jj + i]);
+                st_bf16x8(zrow + 16 * jj, dh);
+                st_bf16x8(zrow + 16 * jj + 8, dh + 8);
+                acc2[jj] += warp_colsum16(dh, lane);
+            }
+        }
+        tc_fence_before();
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 is read; stage st is free (c2)
+        if (!ok) break;
+        if (tid == 0 && nA < n_mine) issue_A();   // tile j + 2 into stage st
+    }
+    if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
+        if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
+        if (n2 > 0) mbar_wait(c2, (uint32_t)(n2 - 1) & 1u);
+        for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
+        for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
+    }
+    ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+    tc_fence_after();
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        if (n_mine > 0) {
+            flush_acc<CG>(tWa, H, H, q, lane, g, part);
+            flush_acc<CG>(tWb, H, H, q, lane, g, part + H * H);
+        } else {
+            for (int i = tid; i < 2 * H * H; i += NT) part[i] = 0.f;
+        }
+    }
+    colsum_store<H, NCH>(acc1, sRed, q, lane, c0, tid, NT, part + 2 * H * H);
+    colsum_store<H, NCH>(acc2, sRed, q, lane, c0, tid, NT, part + 2 * H * H + H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -608,8 +811,9 @@ B128Ws carve_b128(void* ws, const gnn_graph_dev& G, int Le, int Ln, bool need_a,
 
 // dz_{k-1} and the gradients of W_k, b_{k-1} for k = L-1 .. 1 over a chunk of
 // n_tiles tiles; returns the buffer that holds dz_0.
-int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, cudaStream_t s) {
-    return chain_backward_h128(W, dW, w.hs, w.hs_stride, w.dzs, w.part, kPstride, n_tiles, cur, s);
+int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, bool pairs,
+                   cudaStream_t s) {
+    return chain_backward_h128(W, dW, w.hs, w.hs_stride, w.dzs, w.part, kPstride, n_tiles, cur, s, pairs);
 }
 
 // gamma, beta and the last bias of an MLP from the recomputation's partials
@@ -626,18 +830,44 @@ int reduce_ln(const gnn_mlp& dW, const B128Ws& w, int grid, cudaStream_t s) {
 
 int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
                         __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool pairs) {
     constexpr int H = H128;
+    GNN_REQUIRE(pstride >= 2 * H * H + 2 * H, GNN_EINVAL, "chain adjoint: partial stride too small");
     const int L = W.n_lin;
-    const uint32_t smem = ChainSmem::total;
-    int grid;
-    int rc = persistent_grid(k_bwd_chain<false>, kChainNT, smem, 4 * H, n_tiles, &grid);
+    int grid, grid2;
+    int rc = persistent_grid(k_bwd_chain<false>, kChainNT, ChainSmem::total, 4 * H, n_tiles, &grid);
     if (rc) return rc;
+    if ((rc = persistent_grid(k_bwd_chain2, kC2NT, Chain2Smem::total, 4 * H, n_tiles, &grid2))) return rc;
     const int64_t rows = n_tiles * 128;
-    for (int k = L - 1; k >= 1; --k) {
+    for (int k = L - 1; k >= 1;) {
         CUtensorMap tm_dz, tm_h;
         if ((rc = make_row_tmap(&tm_dz, dzs[*cur], rows, H))) return rc;
         if ((rc = make_row_tmap(&tm_h, hs + (int64_t)(k - 1) * hs_stride, rows, H))) return rc;
+        if (pairs && k >= 2) {   // Linears k and k-1 in one pass
+            CUtensorMap tm_hb;
+            if ((rc = make_row_tmap(&tm_hb, hs + (int64_t)(k - 2) * hs_stride, rows, H))) return rc;
+            Chain2Args A{};
+            A.Wa = W.W[k];
+            A.Wb = W.W[k - 1];
+            A.dz_out = dzs[*cur ^ 1];
+            A.n_tiles = n_tiles;
+            A.part = part;
+            A.pstride = pstride;
+            {
+                ProfScope _ps(s, "k_bwd_chain2");
+                k_bwd_chain2<<<grid2, kC2NT, Chain2Smem::total, s>>>(tm_dz, tm_h, tm_hb, A);
+            }
+            GNN_LAUNCH_CHECK("k_bwd_chain2");
+            RedSeg seg[4];
+            seg[0] = RedSeg{dW.W[k], H, H, H, 0, H};
+            seg[1] = RedSeg{dW.W[k - 1], H, H, H, (int64_t)H * H, H};
+            seg[2] = RedSeg{dW.b[k - 1], H, 1, H, 2 * (int64_t)H * H, 0};
+            seg[3] = RedSeg{dW.b[k - 2], H, 1, H, 2 * (int64_t)H * H + H, 0};
+            if ((rc = reduce_grads(seg, 4, part, pstride, grid2, s))) return rc;
+            *cur ^= 1;
+            k -= 2;
+            continue;
+        }
         ChainArgs A{};
         A.W = W.W[k];
         A.dz_out = dzs[*cur ^ 1];
@@ -646,7 +876,7 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
         A.pstride = pstride;
         {
             ProfScope _ps(s, "k_bwd_chain");
-            k_bwd_chain<false><<<grid, kChainNT, smem, s>>>(tm_dz, tm_h, A);
+            k_bwd_chain<false><<<grid, kChainNT, ChainSmem::total, s>>>(tm_dz, tm_h, A);
         }
         GNN_LAUNCH_CHECK("k_bwd_chain");
         RedSeg seg[2];
@@ -654,6 +884,7 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
         seg[1] = RedSeg{dW.b[k - 1], H, 1, H, (int64_t)H * H, 0};
         if ((rc = reduce_grads(seg, 2, part, pstride, grid, s))) return rc;
         *cur ^= 1;
+        --k;
     }
     return GNN_OK;
 }
@@ -708,6 +939,7 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
         GNN_REQUIRE(chunk >= 1, GNN_ENOMEM, "gnn_mp_backward: workspace too small (%zu bytes)", ws_bytes);
     }
     B128Ws w = carve_b128(ws, G, Le, Ln, need_a, chunk);
+    const bool pairs = !(cfg.flags & GNN_FLAG_ADJ_ONE_LINEAR);
     const int64_t NR = G.n_rows, E = G.n_edges;
     if (NR == 0) return GNN_OK;
     int rc;
@@ -734,7 +966,7 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
         if ((rc = node_recompute_save(G, cfg, W, astar, x_in, o, s))) return rc;
         if ((rc = reduce_ln(dW.node, w, o.grid, s))) return rc;
         int cur = 0;
-        if ((rc = chain_backward(W.node, dW.node, w, t1 - t0, &cur, s))) return rc;
+        if ((rc = chain_backward(W.node, dW.node, w, t1 - t0, &cur, pairs, s))) return rc;
         CUtensorMap tm_dz, tm_xa;
         const int64_t rows = (t1 - t0) * 128;
         if ((rc = make_row_tmap(&tm_dz, w.dzs[cur], rows, H))) return rc;
@@ -784,7 +1016,7 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
             if ((rc = edge_recompute_save(G, cfg, W, e_in, w.pq, o, s))) return rc;
             if ((rc = reduce_ln(dW.edge, w, o.grid, s))) return rc;
             int cur = 0;
-            if ((rc = chain_backward(W.edge, dW.edge, w, t1 - t0, &cur, s))) return rc;
+            if ((rc = chain_backward(W.edge, dW.edge, w, t1 - t0, &cur, pairs, s))) return rc;
             CUtensorMap tm_dz;
             if ((rc = make_row_tmap(&tm_dz, w.dzs[cur], (t1 - t0) * 128, H))) return rc;
             Edge0Args A;

@@ -95,15 +95,17 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
                   float* dx_in, __nv_bfloat16* de_in, const gnn_mp_params& dW, void* ws, size_t ws_bytes,
                   cudaStream_t s);
 
-// The per-Linear adjoint k = L-1 .. 1 of an H = 128 MLP (k_bwd_chain, bwd128.cu)
-// over n_tiles tiles of tile-padded BF16 scratch rows: reads dz_{L-1} from
-// dzs[*cur] and h_{k-1} from hs + (k - 1) hs_stride, writes each dz_{k-1} into
-// the other buffer (flipping *cur, so that dzs[*cur] ends holding dz_0) and adds
-// dW_k, db_{k-1} into dW. part holds pstride >= H (H + 1) floats for each CTA of
-// a persistent grid (one CTA per SM).
+// The per-Linear adjoint k = L-1 .. 1 of an H = 128 MLP (bwd128.cu) over n_tiles
+// tiles of tile-padded BF16 scratch rows: reads dz_{L-1} from dzs[*cur] and
+// h_{k-1} from hs + (k - 1) hs_stride, adds dW_k, db_{k-1} into dW and leaves
+// dz_0 in dzs[*cur] (each pass writes the other buffer and flips *cur). With
+// `pairs`, Linears k and k-1 share a pass (k_bwd_chain2, dz_{k-1} kept on chip)
+// while two remain, else one pass per Linear (k_bwd_chain); the results are the
+// same bit for bit. part holds pstride >= 2 H (H + 1) floats for each CTA of a
+// persistent grid (one CTA per SM).
 int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
                         __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
-                        cudaStream_t s);
+                        cudaStream_t s, bool pairs = true);
 // The same kernel on the first Linear of a row MLP whose input X is data: with
 // dz_0 and the BF16 copy of X in tile-padded scratch rows (row i of the scratch
 // is row row0 + i of X), writes dX = dz_0 W_0 (FP32 [n_rows x H], rows below

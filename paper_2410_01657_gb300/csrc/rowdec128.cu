@@ -17,7 +17,7 @@
 //                     M = 128, N = 16 MMA accumulates dW_{L-1}^T = h_{L-2}^T dY
 //                     over the group's tiles; dz_{L-2} = dh_{L-2} ELU'(h_{L-2})
 //                     to scratch, and the column sums for db_{L-1}, db_{L-2}
-//   k_bwd_chain       k = L-2 .. 1 (the layer adjoint's per-Linear kernel)
+//   k_bwd_chain2 / k_bwd_chain  k = L-2 .. 1 (the layer adjoint's per-Linear kernels)
 //   k_bwd_chain<INPUT> dX = dz_0 W_0 and dW_0 = dz_0^T X
 // Every gradient is a fixed-order sum (per thread in row order, per CTA in
 // warp and group order, then over the CTAs in CTA order).
@@ -45,7 +45,7 @@ constexpr uint32_t kYT = 128 * kNO * 2;         // [128 x 16] BF16 tile
 constexpr uint32_t kWL = kNO * kH * 2;          // [16 x 128] BF16 last weight tile
 constexpr int kMaxLin = 4;                      // W_0 .. W_2 resident in shared memory
 constexpr int64_t kChunkTiles = 32768;          // tiles per scratch chunk
-constexpr int64_t kPstride = (int64_t)kH * kH + kH;   // per-CTA partial floats (k_bwd_chain)
+constexpr int64_t kPstride = 2 * (int64_t)kH * kH + 2 * kH;   // per-CTA partial floats (k_bwd_chain2)
 // the recomputation's partials: dW_{L-1} [16 x 128], db_{L-1} [16], db_{L-2} [128]
 constexpr int64_t kPdW = 0, kPdbL = kNO * kH, kPdbH = kPdbL + kNO;
 

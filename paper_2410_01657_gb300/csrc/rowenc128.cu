@@ -17,8 +17,8 @@
 //   k_rowenc_save_tm  recompute the MLP, save h_0 .. h_{L-2} (BF16), apply the
 //                     LayerNorm adjoint to dY: dz_{L-1}, and the column sums
 //                     for dgamma, dbeta, db_{L-1}
-//   k_bwd_chain       k = L-1 .. 1: dz_{k-1} = (dz_k W_k) ELU'(h_{k-1}), dW_k,
-//                     db_{k-1} (the layer adjoint's per-Linear kernel)
+//   k_bwd_chain2 / k_bwd_chain  k = L-1 .. 1: dz_{k-1} = (dz_k W_k) ELU'(h_{k-1}),
+//                     dW_k, db_{k-1} (the layer adjoint's per-Linear kernels)
 //   k_rowenc_w0       dW_0 = dz_0^T X, and dX = dz_0 W_0 when asked (db_0 comes
 //                     from the chain's last pass)
 // Every gradient is a fixed-order sum: per thread in row order, per CTA in
@@ -46,7 +46,7 @@ constexpr int kSX = 32;                         // swizzle span of a [128 x 16] 
 constexpr uint32_t kXT = 128 * kKP * 2;         // [128 x 16] BF16 tile
 constexpr int kMaxLin = 4;                      // W_1 .. W_3 resident in shared memory
 constexpr int64_t kChunkTiles = 32768;          // tiles per scratch chunk
-constexpr int64_t kPstride = (int64_t)kH * kH + kH;   // per-CTA partial floats (k_bwd_chain: dW_k, db_{k-1})
+constexpr int64_t kPstride = 2 * (int64_t)kH * kH + 2 * kH;   // per-CTA partial floats (k_bwd_chain2)
 constexpr int kW0PerSm = 4;                     // k_rowenc_w0 CTAs per SM
 
 struct EncArgs {

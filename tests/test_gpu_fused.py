@@ -375,3 +375,46 @@ def test_h128_tensor_memory_kernels_match_one_tile_kernels(n_hidden):
     assert rel_l2(tm[0], one[0]) < 5e-3 and rel_l2(tm[1], one[1]) < 5e-3
     for a, b in zip(tm[2], one[2]):
         assert rel_l2(a, b) < 1e-2
+
+
+@pytest.mark.parametrize("n_hidden", [1, 2])
+def test_h128_adjoint_two_linears_per_pass_match_one(n_hidden):
+    # The layered H = 128 adjoint runs two Linears per pass (k_bwd_chain2, dz_{k-1}
+    # kept in shared memory) by default and one per pass with GNN_FLAG_ADJ_ONE_LINEAR
+    # (k_bwd_chain alone). Both use the same operands and roundings, so every output
+    # and gradient agrees bit for bit. The 12^3 p=3 brick gives each CTA tens of tiles,
+    # so the kernels' stage rings wrap many times; a workspace of 200 tiles per chunk adds
+    # chunk boundaries.
+    H = 128
+    part = MeshGraph((12, 12, 12), 3).partition(3, "rcb")
+    G = part.to_device(DEV)
+    params = syn.gnn_params(9, H, n_hidden, 1, randomize_affine=True)
+    net = gnn.ConsistentGNN(params, precision="bf16", device=DEV)
+    layer = net.layers[0]
+    tens = layer.edge.tensors() + layer.node.tensors()
+    W = gnn.mp_params(layer.edge.dims, layer.node.dims, tens)
+    g = torch.Generator(device=DEV).manual_seed(4)
+    x = torch.randn(G.n_rows, H, device=DEV, generator=g)
+    e = torch.randn(G.n_edges, H, device=DEV, generator=g).to(torch.bfloat16)
+    dx1 = torch.randn(G.n_rows, H, device=DEV, generator=g)
+    de1 = (0.5 * torch.randn(G.n_edges, H, device=DEV, generator=g)).to(torch.bfloat16)
+    cfg = gnn.mp_config(H, "bf16")
+    xo, eo, a = torch.empty_like(x), torch.empty_like(e), torch.empty_like(x)
+    gnn.gnn_mp_forward(G, cfg, W, x, e, xo, eo, a)
+
+    def backward(flags, ws=None):
+        c = gnn.mp_config(H, "bf16", flags=flags)
+        dparams = [torch.zeros_like(t) for t in tens]
+        dW = gnn.mp_params(layer.edge.dims, layer.node.dims, dparams)
+        dxi, dei = torch.empty_like(x), torch.empty_like(e)
+        gnn.gnn_mp_backward(G, c, W, x, e, a, dx1, de1, dxi, dei, dW, ws)
+        B.call("gnn_check", None)
+        return [dxi, dei] + dparams
+
+    two, one = backward(0), backward(B.GNN_FLAG_ADJ_ONE_LINEAR)
+    for u, v in zip(two, one):
+        assert torch.equal(u, v)
+    ws = gnn.workspace(_ws_chunks(200, n_hidden + 2)(G, cfg, W), DEV)
+    two_c, one_c = backward(0, ws), backward(B.GNN_FLAG_ADJ_ONE_LINEAR, ws)
+    for u, v in zip(two_c, one_c):
+        assert torch.equal(u, v)

@@ -178,6 +178,68 @@ def test_row_mlp_h128_chunks_and_determinism(dims, has_ln):
     assert all(int(torch.count_nonzero(t)) == 0 for t in dz)
 
 
+@pytest.mark.parametrize("dims,has_ln,rows", [
+    ([4, 128, 128, 128, 128], True, 68_646_144),     # the C3 edge encoder's rows (partitioned edges)
+    ([128, 128, 128, 128, 3], False, 11_543_176)])   # the C3 decoder's rows (partitioned node rows)
+def test_row_mlp_h128_full_size_sampled(dims, has_ln, rows):
+    # The fused H = 128 row MLP over the rows of the full C3 graph (the adjoint in
+    # many chunks of the default workspace), checked on sampled rows: the outputs row
+    # by row against the FP64 oracle, and the gradients by linearity in dY: with dY
+    # zero except on the sampled rows, dW, db (and dgamma, dbeta) over all rows are
+    # the oracle's gradients over the sampled rows alone, and dX is zero elsewhere.
+    import ctypes as C
+
+    n_in, n_out = dims[0], dims[-1]
+    P = _mlp_params(dims, has_ln, 31)
+    ts = [torch.as_tensor(t, dtype=torch.float32, device=DEV)
+          for t in [*P["W"], *P["b"]] + ([P["gamma"], P["beta"]] if has_ln else [])]
+    S = gnn.mlp_struct(dims, ts, has_ln)
+    g = torch.Generator(device=DEV).manual_seed(7)
+    X = torch.randn(rows, n_in, device=DEV, generator=g)
+    stream = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(8)
+    sample = np.unique(np.concatenate([rng.integers(0, rows, 1500), [0, rows - 1, 4_194_303, 4_194_304]]))
+    sample = sample[sample < rows]
+    bf = int(has_ln)   # the edge encoder's rows in BF16, as the network keeps them
+    dt = torch.bfloat16 if bf else torch.float32
+    Y = torch.empty(rows, n_out, device=DEV, dtype=dt)
+    B.call("gnn_mlp_forward_bf16", C.byref(S), rows, B.ptr(X), B.ptr(Y), bf, 1e-5, None, 0, stream)
+    Xs = X[torch.as_tensor(sample, device=DEV)].double().cpu().numpy()
+    Yo, cache = om.mlp_forward(P, Xs)
+    Ys = Y[torch.as_tensor(sample, device=DEV)].double().cpu().numpy()
+    del Y
+    # each row's error against the rows' RMS norm (a 3-wide decoder row can be near zero)
+    err = np.linalg.norm(Ys - Yo, axis=1) / np.sqrt(np.mean(np.sum(Yo ** 2, axis=1)))
+    assert err.max() < 3e-2 and np.sqrt(np.mean(err ** 2)) < 1e-2, (err.max(), np.sqrt(np.mean(err ** 2)))
+    # gradients by linearity in dY
+    dYs = rng.standard_normal((len(sample), n_out))
+    dYs = torch.as_tensor(dYs, dtype=torch.float32).to(dt).double().numpy()   # as the kernel reads them
+    dY = torch.zeros(rows, n_out, device=DEV, dtype=dt)
+    dY[torch.as_tensor(sample, device=DEV)] = torch.as_tensor(dYs, device=DEV).to(dt)
+    f, b = C.c_size_t(), C.c_size_t()
+    B.call("gnn_mlp_workspace_size_bf16", C.byref(S), rows, C.byref(f), C.byref(b))
+    ws = torch.empty(b.value, dtype=torch.uint8, device=DEV)
+    dts = [torch.zeros_like(t) for t in ts]
+    dS = gnn.mlp_struct(dims, dts, has_ln)
+    dX = torch.empty(rows, n_in, device=DEV)
+    B.call("gnn_mlp_backward_bf16", C.byref(S), rows, B.ptr(X), B.ptr(dY), bf, B.ptr(dX), C.byref(dS), 1e-5,
+           B.ptr(ws), ws.numel(), stream)
+    B.call("gnn_check", None)
+    dXo, go = om.mlp_backward(P, cache, dYs)
+    n = len(dims) - 1
+    got = {"W": [t.double().cpu().numpy() for t in dts[:n]], "b": [t.double().cpu().numpy() for t in dts[n:2 * n]]}
+    if has_ln:
+        got["gamma"], got["beta"] = dts[2 * n].double().cpu().numpy(), dts[2 * n + 1].double().cpu().numpy()
+    for key in got:
+        for a, ref in zip(got[key] if isinstance(got[key], list) else [got[key]],
+                          go[key] if isinstance(go[key], list) else [go[key]]):
+            assert rel_l2(a, ref) < 5e-2, (key, rel_l2(a, ref))
+    mask = torch.ones(rows, dtype=torch.bool, device=DEV)
+    mask[torch.as_tensor(sample, device=DEV)] = False
+    assert int(torch.count_nonzero(dX[mask])) == 0
+    assert rel_l2(dX[torch.as_tensor(sample, device=DEV)].double().cpu().numpy(), dXo) < 5e-2
+
+
 def test_uncovered_shape_is_rejected():
     dims = [8, 24, 24, 5]
     assert not gnn.rowmlp_fused_shape(dims, False)

@@ -223,11 +223,14 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
 // results are the same bit for bit. TMEM: D1, D2, dW_k, dW_{k-1} (128 columns
 // each). Two stages of {dz_k, h_{k-1}} rows keep the next tile's load in flight;
 // h_{k-2} has one stage, reloaded as soon as epilogue 2 has read it into
-// registers; thread 0 issues tile j+1's pair 1 right after tile j's pair 2.
+// registers and pair 2's weight-gradient MMA has read it; thread 0 issues tile
+// j+1's pair 1 right after tile j's pair 2. Pair 2 commits twice, so that
+// epilogue 2 starts once its dgrad is done, while the wgrad still runs.
 
 struct Chain2Args {
     const float* Wa;             // W_k [H x H] (FP32)
     const float* Wb;             // W_{k-1}
+    const __nv_bfloat16* hb;     // h_{k-2} rows (prefetched into L2 two tiles ahead)
     __nv_bfloat16* dz_out;       // dz_{k-2} rows (tile-padded)
     int64_t n_tiles;
     float* part;                 // per-CTA: dW_k, dW_{k-1} [H x H], then db_{k-1}, db_{k-2} [H]
@@ -240,7 +243,7 @@ struct Chain2Smem {
     static constexpr uint32_t a = 2 * kTile;          // stage s: dz_k (then dz_{k-1}), h_{k-1}, at a + s * 2 * kTile
     static constexpr uint32_t b = a + 4 * kTile;      // h_{k-2}
     static constexpr uint32_t red = a;                // 4 x H floats, after the tile loop
-    static constexpr uint32_t bar = b + kTile;        // fullA[2], fullB, c1, c2, TMEM slot
+    static constexpr uint32_t bar = b + kTile;        // fullA[2], fullB, c1, c2d, c2w, TMEM slot
     static constexpr uint32_t total = bar + 64 + 1024;
 };
 static_assert(Chain2Smem::total <= 227 * 1024, "k_bwd_chain2 shared memory");
@@ -258,8 +261,9 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
     uint64_t* fullA = reinterpret_cast<uint64_t*>(sm + Chain2Smem::bar);   // fullA[2]: stage landed
     uint64_t* fullB = fullA + 2;   // h_{k-2} landed
     uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
-    uint64_t* c2 = fullA + 4;      // MMA pair 2 complete
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 5);
+    uint64_t* c2d = fullA + 4;     // pair 2's dgrad complete
+    uint64_t* c2w = fullA + 5;     // pair 2's wgrad complete
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 6);
     auto sDz = [&](int st) { return sm + Chain2Smem::a + st * 2 * kTile; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(fullA + i, 1);
+        for (int i = 0; i < 6; ++i) mbar_init(fullA + i, 1);
         fence_mbar_init();
     }
     load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
     // thread 0 only: loads and MMA pairs issued so far, and whether it is still well
     int64_t nA = 0, nB = 0, n1 = 0, n2 = 0;
     bool ok0 = true;
-    auto issue_A = [&]() {   // dz_k and h_{k-1} rows of tile nA into stage nA % 2
+    auto issue_A = [&]() {   // dz_k and h_{k-1} rows of tile nA into stage nA % 2 (and its h_{k-2} into L2)
         const int st = (int)(nA & 1);
         const int32_t y = (int32_t)(tile_of(nA) * 128);
         mbar_arrive_expect_tx(fullA + st, 2 * kTile);
@@ -294,6 +298,7 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
             tma_load_2d(sDz(st) + kb * 128 * S, &tm_dz, kb * 64, y, fullA + st);
             tma_load_2d(sDz(st) + kTile + kb * 128 * S, &tm_ha, kb * 64, y, fullA + st);
         }
+        prefetch_l2(A.hb + (int64_t)y * H, kTile);
         ++nA;
     };
     auto issue_B = [&]() {   // h_{k-2} rows of tile nB
@@ -354,14 +359,15 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
             if (ok0) {
                 tc_fence_after();
                 issue_dgrad(tD2, sDz(st), S, sWb, S, H, (uint32_t)H * S, H, H);
+                mma_commit(c2d);
                 issue_wgrad(tWb, sDz(st), S, 128u * S, sHb, S, 128u * S, H, n2 > 0);
-                mma_commit(c2);
+                mma_commit(c2w);
                 ++n2;
                 if (j + 1 < n_mine) issue_pair1();
             }
         }
         // epilogue 2: dz_{k-2} to HBM, column sums for db_{k-2}
-        ok = ok && mbar_wait(c2, par);
+        ok = ok && mbar_wait(c2d, par);
         __syncwarp();
         tc_fence_after();
         float hb[CW];   // this thread's h_{k-2}, read before the stage is reloaded
@@ -369,7 +375,10 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         for (int i = 0; i < CW; i += 8) ld_tile8(sHb, row, c0 + i, 128, S, hb + i);
         ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
         if (!ok) break;
-        if (tid == 0 && nB < n_mine) issue_B();   // pair 2 has read h_{k-2} (c2), so has every thread
+        if (tid == 0) {   // the wgrad of pair 2 has read h_{k-2} and dz_{k-1}, so has every thread
+            ok0 = mbar_wait(c2w, par);
+            if (ok0 && nB < n_mine) issue_B();
+        }
         {
             __nv_bfloat16* zrow = A.dz_out + (tile_of(j) * 128 + row) * H + c0;
 #pragma unroll
@@ -385,13 +394,16 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
             }
         }
         tc_fence_before();
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 is read; stage st is free (c2)
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 is read; stage st is free (c2w)
         if (!ok) break;
         if (tid == 0 && nA < n_mine) issue_A();   // tile j + 2 into stage st
     }
     if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
         if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
-        if (n2 > 0) mbar_wait(c2, (uint32_t)(n2 - 1) & 1u);
+        if (n2 > 0) {
+            mbar_wait(c2d, (uint32_t)(n2 - 1) & 1u);
+            mbar_wait(c2w, (uint32_t)(n2 - 1) & 1u);
+        }
         for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
         for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
     }
@@ -849,6 +861,7 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
             Chain2Args A{};
             A.Wa = W.W[k];
             A.Wb = W.W[k - 1];
+            A.hb = hs + (int64_t)(k - 2) * hs_stride;
             A.dz_out = dzs[*cur ^ 1];
             A.n_tiles = n_tiles;
             A.part = part;

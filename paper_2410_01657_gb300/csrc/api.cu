@@ -80,7 +80,7 @@ int gnn_check(void* stream) {
         gnn::plain::take_device_error, gnn::fused::take_device_error, gnn::fused::take_device_error_bwd,
         gnn::fused::take_device_error_bwd128, gnn::fused::take_device_error_rowmlp,
         gnn::fused::take_device_error_edge128, gnn::fused::take_device_error_rowenc128,
-        gnn::fused::take_device_error_rowdec128,
+        gnn::fused::take_device_error_rowdec128, gnn::fused::take_device_error_node128,
         gnn::diag::take_device_error};
     unsigned int word = 0;
     for (auto f : take) {

@@ -1622,6 +1622,9 @@ int node_h(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params
     using C = Cfg<H>;
     const int64_t NR = G.n_rows;
     if (NR == 0) return GNN_OK;
+    if constexpr (H == 128) {   // two tile groups per SM, the operands in tensor memory
+        if (!act && node_fwd_tm_supported(W)) return node_fwd_tm(G, cfg, W, a, x_in, x_out, s);
+    }
     NodeFwdArgs A;
     A.a_star = a;
     A.x = x_in;

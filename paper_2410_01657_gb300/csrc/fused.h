@@ -10,7 +10,7 @@ namespace gnn {
 namespace fused {
 
 // Read and clear the device error word of fused.cu, fused_bwd.cu, bwd128.cu, rowmlp.cu, edge128.cu,
-// rowenc128.cu, rowdec128.cu.
+// rowenc128.cu, rowdec128.cu, node128.cu.
 cudaError_t take_device_error(unsigned int* out);
 cudaError_t take_device_error_bwd(unsigned int* out);
 cudaError_t take_device_error_bwd128(unsigned int* out);
@@ -18,11 +18,17 @@ cudaError_t take_device_error_rowmlp(unsigned int* out);
 cudaError_t take_device_error_edge128(unsigned int* out);
 cudaError_t take_device_error_rowenc128(unsigned int* out);
 cudaError_t take_device_error_rowdec128(unsigned int* out);
+cudaError_t take_device_error_node128(unsigned int* out);
 // The H = 128 edge forward with two tile groups per SM and the hidden
 // activations in tensor memory (edge128.cu); supported for 2..4 Linears.
 bool edge_fwd_tm_supported(const gnn_mp_params& W);
 int edge_fwd_tm(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const __nv_bfloat16* e_in,
                 const __nv_bfloat16* pq, __nv_bfloat16* e_out, float* a, cudaStream_t s);
+// The H = 128 node forward in the same two-group tensor-memory form (node128.cu;
+// 2..4 Linears); 16-byte aligned a*, x and x' rows.
+bool node_fwd_tm_supported(const gnn_mp_params& W);
+int node_fwd_tm(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W, const float* a,
+                const float* x_in, float* x_out, cudaStream_t s);
 size_t mp_forward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 size_t mp_backward_ws(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp_params& W);
 // Bytes of the saved MLP activations (BF16 h_0 .. h_{L-2} of every edge, then

@@ -1,6 +1,7 @@
 // C-ABI compute entry points of libgnnmp: argument validation and dispatch to
 // the plain FP32 path (plain.cu) or the fused BF16 tcgen05 path (fused.cu).
 
+#include <cstdio>
 #include <cstring>
 
 #include "device_common.cuh"
@@ -82,13 +83,21 @@ int gnn_check(void* stream) {
         gnn::fused::take_device_error_edge128, gnn::fused::take_device_error_rowenc128,
         gnn::fused::take_device_error_rowdec128, gnn::fused::take_device_error_node128,
         gnn::diag::take_device_error};
+    const char* const unit[] = {"plain", "fused", "fused_bwd", "bwd128", "rowmlp", "edge128", "rowenc128",
+                                "rowdec128", "node128", "diag"};
+    static_assert(sizeof(unit) / sizeof(unit[0]) == sizeof(take) / sizeof(take[0]), "one name per unit");
     unsigned int word = 0;
-    for (auto f : take) {
+    char where[160] = "";
+    size_t n = 0;
+    for (size_t i = 0; i < sizeof(take) / sizeof(take[0]); ++i) {
         unsigned int w = 0;
-        GNN_CUDA_CHECK(f(&w), "gnn_check: read error word");
+        GNN_CUDA_CHECK(take[i](&w), "gnn_check: read error word");
         word |= w;
+        if ((w & GNN_DEVERR_TIMEOUT) && n + 16 < sizeof(where))
+            n += (size_t)snprintf(where + n, sizeof(where) - n, "%s%s", n ? ", " : "", unit[i]);
     }
-    if (word & GNN_DEVERR_TIMEOUT) return set_error(GNN_ETIMEOUT, "gnn_check: a device-side wait timed out");
+    if (word & GNN_DEVERR_TIMEOUT)
+        return set_error(GNN_ETIMEOUT, "gnn_check: a device-side wait timed out (in the kernels of %s)", where);
     return GNN_OK;
 }
 

@@ -41,10 +41,14 @@ using namespace tc;
 
 // One tile = 128 node rows. The FP32 x rows of the CTA's next tile are loaded
 // by TMA into the other of two stages while the current tile is converted to
-// BF16, multiplied and written.
+// BF16 and multiplied; the tile's P and Q rows are staged as BF16 in its own
+// x stage and leave as whole rows by TMA stores (tmap_p, tmap_q: rows past
+// n_rows are clipped).
 template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__ CUtensorMap tmap_x, int64_t n_rows,
-                                                        const float* __restrict__ W1, __nv_bfloat16* __restrict__ pq) {
+__global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__ CUtensorMap tmap_x,
+                                                        const __grid_constant__ CUtensorMap tmap_p,
+                                                        const __grid_constant__ CUtensorMap tmap_q, int64_t n_rows,
+                                                        const float* __restrict__ W1) {
     using C = Cfg<H>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -90,13 +94,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__
         const int st = j & 1;
         ok = block_wait(full + st, (uint32_t)(j >> 1) & 1u, tid);
         if (!ok) break;
-        // the other stage was read by the previous tile (ordered by its closing barrier)
+        // the other stage was read by the previous tile (ordered by its closing barrier) and
+        // its P|Q stores have read it
         if (tid == 0 && t + gridDim.x < n_tiles) {
+            bulk_wait_read_all();
             mbar_arrive_expect_tx(full + (st ^ 1), XBYTES);
             tma_f32_tile<H>(sX(st ^ 1), &tmap_x, (t + gridDim.x) * 128, full + (st ^ 1));
         }
-        const int64_t r = t * 128 + row;
-        const bool valid = r < n_rows;
         float v[C::CW];
 #pragma unroll
         for (int i = 0; i < C::CW / 4; ++i) {
@@ -120,16 +124,23 @@ __global__ void __launch_bounds__(Cfg<H>::NT) k_proj_fwd(const __grid_constant__
         ld_acc<C::CW>(tmem, q, c0, pv);
         ld_acc<C::CW>(tmem, q, H + c0, qv);
         tc_fence_before();
-        if (valid) {
-#pragma unroll
-            for (int i = 0; i < C::CW; i += 8) {
-                st_bf16x8(pq + r * H + c0 + i, pv + i);
-                st_bf16x8(pq + n_rows * H + r * H + c0 + i, qv + i);
-            }
-        }
-        fence_proxy_async();   // generic reads of the x stage precede its next TMA write
+        // every thread read its x rows before the MMA barrier: the stage takes P and Q
+        uint8_t* sP = sX(st);
+        uint8_t* sQ = sX(st) + 128 * H * 2;
+        st_row_tile<C::CW>(sP, row, c0, C::S, pv);
+        st_row_tile<C::CW>(sQ, row, c0, C::S, qv);
+        fence_proxy_async();   // generic accesses of the stage precede the TMA stores and its next TMA write
         __syncthreads();       // sA, the x stage and TMEM are reused
+        if (tid == 0) {
+#pragma unroll
+            for (int kb = 0; kb < H / (C::S / 2); ++kb) {
+                tma_store_2d(&tmap_p, kb * (C::S / 2), (int32_t)(t * 128), sP + kb * 128 * C::S);
+                tma_store_2d(&tmap_q, kb * (C::S / 2), (int32_t)(t * 128), sQ + kb * 128 * C::S);
+            }
+            bulk_commit();
+        }
     }
+    if (tid == 0) bulk_wait_all();   // the P|Q rows are written before the CTA exits
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1517,14 +1528,16 @@ int proj_h(const gnn_graph_dev& G, const gnn_mp_params& W, const float* x_in, __
     if (NR == 0) return GNN_OK;
     const ProjSmem L = proj_smem<H>();
     int grid;
-    CUtensorMap tmx;
+    CUtensorMap tmx, tmp, tmq;
     int rc = make_f32_tmap(&tmx, x_in, NR, H);
     if (rc) return rc;
+    if ((rc = make_row_tmap(&tmp, pq, NR, H))) return rc;
+    if ((rc = make_row_tmap(&tmq, pq + NR * H, NR, H))) return rc;
     rc = persistent_grid(k_proj_fwd<H>, C::NT, L.total, 2 * H < 32 ? 32 : 2 * H, (NR + 127) / 128, &grid);
     if (rc) return rc;
     {
         ProfScope _ps(s, "k_proj_fwd");
-        k_proj_fwd<H><<<grid, C::NT, L.total, s>>>(tmx, NR, W.edge.W[0], pq);
+        k_proj_fwd<H><<<grid, C::NT, L.total, s>>>(tmx, tmp, tmq, NR, W.edge.W[0]);
     }
     GNN_LAUNCH_CHECK("k_proj_fwd");
     return GNN_OK;

@@ -45,8 +45,10 @@ extern "C" {
 const char* gnn_last_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int gnn_version(void);
-/* Synchronise `stream`, then read and clear the device error word.
- * Returns GNN_OK, GNN_ETIMEOUT (a device wait gave up) or GNN_ECUDA. */
+/* Synchronise `stream`, then read and clear the device error words (one per
+ * source file of kernels that wait). Returns GNN_OK, GNN_ETIMEOUT (a device
+ * wait gave up; gnn_last_error() names the source files whose kernels timed
+ * out) or GNN_ECUDA. */
 int gnn_check(void* stream);
 
 /* ====================================================== graph generation (host)

@@ -7,17 +7,20 @@
 // therefore runs one Linear at a time over tiles of 128 rows, with the
 // recomputed activations in an HBM scratch of tile-padded rows (the rows past
 // a tile's end are zero, so they add nothing to any product or sum):
-//   k_node_fwd<128, false, true> / k_edge_fwd<128, true>   (forward units)
+//   k_node_fwd<128, false, true> / k_edge_save_tm   (forward units)
 //       recompute the MLP, save h_0 .. h_{L-2} (and a node tile's BF16
-//       [a*, x] rows), apply the LayerNorm adjoint: dz_{L-1}, dgamma, dbeta,
-//       db_{L-1}
+//       [a*, x] rows), apply the LayerNorm adjoint: dz_{L-1}, dgamma,
+//       db_{L-1}, and (nodes) dbeta
 //   k_bwd_chain2 / k_bwd_chain, k = L-1 .. 1, two Linears per pass while two remain
 //       dh_{k-1} = dz_k W_k, dz_{k-1} = dh_{k-1} ELU'(h_{k-1}),
 //       dW_k += dz_k^T h_{k-1} (TMEM, over the CTA's tiles), db_{k-1}
 //   k_bwd_node0   [da*, dx] = dz_0 W_0, dW_0 += dz_0^T [a*, x], dx_in = dx' + dx
 //   k_halo        adjoint of Eq. 5c-5d on da*
 //   k_bwd_edge0   de_in = g + dz_0 W1c with g = de' + da_i / d_ij, dW1c += dz_0^T e,
-//                 dz_0 per edge and its sum over each receiver's edges (dP)
+//                 dbeta (the column sums of g), dz_0 per edge and its sum over each
+//                 receiver's edges (dP)
+//   k_bwd_chain_edge0   the edge MLP's Linear 1 and k_bwd_edge0 in one pass, when
+//                 the pairs leave Linear 1 alone (dz_0 stays in shared memory)
 //   k_proj_bwd    dQ, dx_in += dP W1a + dQ W1b, dW1a, dW1b
 // Tiles are processed in chunks of at most kChunkTiles (fewer when the
 // caller's workspace is smaller) so that the scratch stays bounded; each
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
         }
         tc_fence_before();
         fence_proxy_async();
+        __syncwarp();   // reconverged before the aligned block barrier
         ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // every thread is past its reads of stage s
         if (!ok) break;
         if (tid == 0) {   // stage s is free once tile j's wgrad is done: the CTA's tile j+NS goes there
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
         if (n_mma > 0) mbar_wait(done_w + ((n_mma - 1) & 1), (uint32_t)((n_mma - 1) >> 1) & 1u);
         for (int64_t i = n_mma; i < n_ld; ++i) mbar_wait(full + (i % NS), (uint32_t)(i / NS) & 1u);
     }
+    __syncwarp();   // reconverged before the aligned block barrier
     ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
@@ -250,7 +255,8 @@ static_assert(Chain2Smem::total <= 227 * 1024, "k_bwd_chain2 shared memory");
 
 __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__ CUtensorMap tm_dz,
                                                          const __grid_constant__ CUtensorMap tm_ha,
-                                                         const __grid_constant__ CUtensorMap tm_hb, Chain2Args A) {
+                                                         const __grid_constant__ CUtensorMap tm_hb,
+                                                         const __grid_constant__ CUtensorMap tm_out, Chain2Args A) {
     constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kC2NT, NCH = CW / 16;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
@@ -352,6 +358,7 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         }
         tc_fence_before();
         fence_proxy_async();
+        __syncwarp();   // reconverged before the aligned block barrier
         ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
         if (!ok) break;
         if (tid == 0) {   // pair 2 on dz_{k-1}; then the next tile's pair 1 (D1 has been read)
@@ -373,14 +380,16 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         float hb[CW];   // this thread's h_{k-2}, read before the stage is reloaded
 #pragma unroll
         for (int i = 0; i < CW; i += 8) ld_tile8(sHb, row, c0 + i, 128, S, hb + i);
+        __syncwarp();   // reconverged before the aligned block barrier
         ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
         if (!ok) break;
         if (tid == 0) {   // the wgrad of pair 2 has read h_{k-2} and dz_{k-1}, so has every thread
             ok0 = mbar_wait(c2w, par);
             if (ok0 && nB < n_mine) issue_B();
         }
-        {
-            __nv_bfloat16* zrow = A.dz_out + (tile_of(j) * 128 + row) * H + c0;
+        __syncwarp();   // warp 0 reconverged before the aligned TMEM loads
+        {   // dz_{k-2} staged in the stage's h_{k-1} slot (pair 1 and epilogue 1 have read it)
+            uint8_t* zt = sDz(st) + kTile;
 #pragma unroll
             for (int jj = 0; jj < NCH; ++jj) {
                 float dh[16];
@@ -388,15 +397,26 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
                 tmem_ld_wait();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hb[16 * jj + i]);
-                st_bf16x8(zrow + 16 * jj, dh);
-                st_bf16x8(zrow + 16 * jj + 8, dh + 8);
+                st_tile8(zt, row, c0 + 16 * jj, 128, S, dh);
+                st_tile8(zt, row, c0 + 16 * jj + 8, 128, S, dh + 8);
                 acc2[jj] += warp_colsum16(dh, lane);
             }
         }
         tc_fence_before();
+        fence_proxy_async();   // the staged rows precede their TMA store and the stage's refill
+        __syncwarp();   // reconverged before the aligned block barrier
         ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 is read; stage st is free (c2w)
         if (!ok) break;
-        if (tid == 0 && nA < n_mine) issue_A();   // tile j + 2 into stage st
+        if (tid == 0) {   // dz_{k-2} leaves as whole rows; tile j + 2 into stage st once the store has read it
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb)
+                tma_store_2d(&tm_out, kb * 64, (int32_t)(tile_of(j) * 128), sDz(st) + kTile + kb * 128 * S);
+            bulk_commit();
+            if (nA < n_mine) {
+                bulk_wait_read_all();
+                issue_A();
+            }
+        }
     }
     if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
         if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
@@ -407,6 +427,8 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
         for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
     }
+    if (tid == 0) bulk_wait_all();   // the stored dz rows are written, the stages free
+    __syncwarp();   // reconverged before the aligned block barrier
     ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
@@ -427,6 +449,10 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
 }
 
 // ------------------------------------------------------------------ k_bwd_edge0
+
+// The gradient of e' from the edge's side of Eq. 5b and the upstream gradient:
+// g = de' + w da_i (w = 1/d_ij), one rounding.
+__device__ __forceinline__ float edge_g(float w, float da, float de) { return __fmaf_rn(w, da, de); }
 
 struct Edge0Args {
     const uint8_t* tile_meta;    // per-tile records (GNN_TILE_META_BYTES each)
@@ -453,10 +479,11 @@ struct Edge0Smem {
 
 __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ CUtensorMap tm_dz,
                                                        const __grid_constant__ CUtensorMap tm_e, Edge0Args A) {
-    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kE0NT;
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kE0NT, NCH = CW / 16;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     uint8_t* sW = sm + Edge0Smem::w;
+    float* sRed = reinterpret_cast<float*>(sm + Edge0Smem::st);   // 4 x H floats, after the tile loop
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + Edge0Smem::bar);   // full[2]
     uint64_t* bar = full + 2;     // dgrad done
     uint64_t* bar_w = full + 3;   // wgrad done
@@ -504,6 +531,9 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
     bool ok = true, first = true, mp = false;
     int j = 0;
     int64_t n_consumed = 0;
+    float accb[NCH];   // column sums of g: the LayerNorm beta gradient
+#pragma unroll
+    for (int jj = 0; jj < NCH; ++jj) accb[jj] = 0.f;
 
     for (int64_t t = tfirst; t < A.t1; t += gridDim.x, ++j) {
         const int st = j & 1;
@@ -540,27 +570,28 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         if (valid) {
             const float w = sWd[row];
             const float* dar = A.da + (int64_t)(r0 + sSeg[row]) * H + c0;
+            float dv[CW];
+            if (A.de_out) {
+#pragma unroll
+                for (int i = 0; i < CW; i += 8) ld_bf16x8(A.de_out + eg * H + c0 + i, dv + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < CW; ++i) dv[i] = 0.f;
+            }
 #pragma unroll
             for (int i = 0; i < CW; i += 4) {
                 const float4 u = __ldg(reinterpret_cast<const float4*>(dar + i));
-                gv[i] = w * u.x;
-                gv[i + 1] = w * u.y;
-                gv[i + 2] = w * u.z;
-                gv[i + 3] = w * u.w;
-            }
-            if (A.de_out) {
-#pragma unroll
-                for (int i = 0; i < CW; i += 8) {
-                    float d8[8];
-                    ld_bf16x8(A.de_out + eg * H + c0 + i, d8);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) gv[i + k] = d8[k] + gv[i + k];
-                }
+                gv[i] = edge_g(w, u.x, dv[i]);
+                gv[i + 1] = edge_g(w, u.y, dv[i + 1]);
+                gv[i + 2] = edge_g(w, u.z, dv[i + 2]);
+                gv[i + 3] = edge_g(w, u.w, dv[i + 3]);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < CW; ++i) gv[i] = 0.f;
         }
+#pragma unroll
+        for (int jj = 0; jj < NCH; ++jj) accb[jj] += warp_colsum16(gv + 16 * jj, lane);
         {   // dz_0 per edge, for the sender-side sums of the projection adjoint: whole rows per
             // warp from the stage's dz tile (TMA-loaded, complete since the stage barrier)
             constexpr int CPR = H / 8;
@@ -591,7 +622,7 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         ld_acc<CW>(tWork, q, c0, dh);
         tc_fence_before();
 #pragma unroll
-        for (int i = 0; i < CW; ++i) dh[i] = gv[i] + dh[i];   // residual branch plus W1c^T dz_0
+        for (int i = 0; i < CW; ++i) dh[i] = __fadd_rn(gv[i], dh[i]);   // residual branch plus W1c^T dz_0
         fence_proxy_async();
         ok = block_wait(bar_w, ph, tid);   // the stage is free: wgrad done, every thread past its reads
         if (!ok) break;
@@ -620,6 +651,7 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
             mbar_wait(full + (i & 1), (uint32_t)(i >> 1) & 1u);
         }
     }
+    __syncwarp();   // reconverged before the aligned block barrier
     ok = __syncthreads_and(ok) != 0;
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {
@@ -627,10 +659,316 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
         else
             for (int i = tid; i < H * H; i += NT) part[i] = 0.f;
     }
+    colsum_store<H, NCH>(accb, sRed, q, lane, c0, tid, NT, part + H * H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 2 * H);
+}
+
+// ------------------------------------------------------------------ k_bwd_chain_edge0
+//
+// The edge MLP's last two adjoint steps in one pass when Linear 1 is the one
+// left for the chain: the work of k_bwd_chain (k = 1) and of k_bwd_edge0, so
+// that dz_0 never travels through the scratch. Per tile: MMA pair 1 (D1 =
+// dz_1 W_1, dW_1 += dz_1^T h_0), epilogue 1 (dz_0 = D1 ELU'(h_0) as BF16 into
+// the shared-memory slot dz_1 came in, its column sums for db_0), MMA pair 2
+// (D2 = dz_0 W1c, dW1c += dz_0^T e) while the block writes dz_0 per edge
+// (whole rows) and sums it over each receiver's edges (dP), epilogue 2 (de_in =
+// g + D2 with g = de' + da_i / d_ij, staged in the stage's h_0 slot and written
+// as whole rows). Operands, roundings and summation orders are those of the two
+// kernels, so the results are the same bit for bit. TMEM: D1, D2, dW_1, dW1c
+// (128 columns each). Two stages of {dz_1, h_0} rows; the e rows have one
+// stage, reloaded once pair 2's weight gradient has read them. The tile records
+// stay in global memory (brought into L2 two tiles ahead); each thread reads
+// its row's fields of the next record while the current tile runs.
+
+struct ChainE0Args {
+    const float* Wa;             // W_1 [H x H] (FP32)
+    const float* W1;             // W_0 = W1 [H x 3H]; W1c = columns 2H .. 3H
+    const uint8_t* tile_meta;    // per-tile records (GNN_TILE_META_BYTES each)
+    int64_t t0, n_tiles;         // the chunk: tiles t0 .. t0 + n_tiles; scratch row of tile t0 + i is 128 i
+    const __nv_bfloat16* de_out; // NULL: zero
+    const float* da;             // aggregate gradient after the halo adjoint
+    __nv_bfloat16* de_in;
+    __nv_bfloat16* dz1;          // per-edge dz_0 [E x H]
+    float* dP;                   // [n_rows x H]
+    float* part;                 // per-CTA: dW_1, dW1c [H x H], then db_0 [H]
+    int64_t pstride;
+};
+
+constexpr int kCE0NT = 512;
+struct ChainE0Smem {
+    static constexpr uint32_t wa = 0, wb = kTile;
+    static constexpr uint32_t a = 2 * kTile;          // stage s: dz_1 (then dz_0), h_0 (then de_in), at a + s * 2 * kTile
+    static constexpr uint32_t e = a + 4 * kTile;      // e rows
+    static constexpr uint32_t red = a;                // 4 x H floats, after the tile loop
+    static constexpr uint32_t bar = e + kTile;        // fullA[2], fullB, c1, c2d, c2w, TMEM slot
+    static constexpr uint32_t total = bar + 64 + 1024;
+};
+static_assert(ChainE0Smem::total <= 227 * 1024, "k_bwd_chain_edge0 shared memory");
+
+__global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_constant__ CUtensorMap tm_dz,
+                                                              const __grid_constant__ CUtensorMap tm_h,
+                                                              const __grid_constant__ CUtensorMap tm_e,
+                                                              ChainE0Args A) {
+    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kCE0NT, NCH = CW / 16, CPR = H / 8;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = aligned_smem(smem_raw);
+    uint8_t* sWa = sm + ChainE0Smem::wa;
+    uint8_t* sWb = sm + ChainE0Smem::wb;
+    uint8_t* sE = sm + ChainE0Smem::e;
+    float* sRed = reinterpret_cast<float*>(sm + ChainE0Smem::red);
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(sm + ChainE0Smem::bar);   // fullA[2]: stage landed
+    uint64_t* fullB = fullA + 2;   // e rows landed
+    uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
+    uint64_t* c2d = fullA + 4;     // pair 2's dgrad complete
+    uint64_t* c2w = fullA + 5;     // pair 2's wgrad complete
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 6);
+    auto sDz = [&](int st) { return sm + ChainE0Smem::a + st * 2 * kTile; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    if (warp == 0) {
+        tmem_alloc(tslot, 4 * H);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 6; ++i) mbar_init(fullA + i, 1);
+        fence_mbar_init();
+    }
+    load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
+    load_weight(sWb, A.W1, 3 * H, 2 * H, H, H, tid, NT);   // W1c as a K-major [H x H] tile
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, tD1 = tmem, tD2 = tmem + H, tWa = tmem + 2 * H, tWb = tmem + 3 * H;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int64_t n_mine = A.n_tiles > (int64_t)blockIdx.x
+                               ? (A.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };   // chunk-relative
+    auto rec_of = [&](int64_t j) { return A.tile_meta + (A.t0 + tile_of(j)) * GNN_TILE_META_BYTES; };
+    // thread 0 only: loads and MMA pairs issued so far, whether it is still well, and
+    // the header of the tile whose e rows load next (read one e load ahead)
+    int64_t nA = 0, nB = 0, n1 = 0, n2 = 0;
+    bool ok0 = true;
+    int4 hB = make_int4(0, 0, 0, 0);
+    auto issue_A = [&]() {   // dz_1 and h_0 rows of tile nA into stage nA % 2, its record into L2
+        const int st = (int)(nA & 1);
+        const int32_t y = (int32_t)(tile_of(nA) * 128);
+        mbar_arrive_expect_tx(fullA + st, 2 * kTile);
+        for (int kb = 0; kb < 2; ++kb) {
+            tma_load_2d(sDz(st) + kb * 128 * S, &tm_dz, kb * 64, y, fullA + st);
+            tma_load_2d(sDz(st) + kTile + kb * 128 * S, &tm_h, kb * 64, y, fullA + st);
+        }
+        prefetch_l2(rec_of(nA), GNN_TILE_META_BYTES);
+        ++nA;
+    };
+    auto issue_B = [&]() {   // e rows of tile nB; its receivers' da rows and its de' rows into L2
+        mbar_arrive_expect_tx(fullB, kTile);
+        for (int kb = 0; kb < 2; ++kb) tma_load_2d(sE + kb * 128 * S, &tm_e, kb * 64, hB.z, fullB);
+        if (hB.y > hB.x) prefetch_l2(A.da + (int64_t)hB.x * H, (uint32_t)(hB.y - hB.x) * H * 4);
+        if (A.de_out && hB.w > 0) prefetch_l2(A.de_out + (int64_t)hB.z * H, (uint32_t)hB.w * H * 2);
+        ++nB;
+        if (nB < n_mine) hB = ld_nc_v4s32(rec_of(nB));
+    };
+    auto issue_pair1 = [&]() {   // tile n1's first MMA pair once its stage has landed
+        const int st = (int)(n1 & 1);
+        ok0 = ok0 && mbar_wait(fullA + st, (uint32_t)(n1 >> 1) & 1u);
+        if (!ok0) return;
+        tc_fence_after();
+        issue_dgrad(tD1, sDz(st), S, sWa, S, H, (uint32_t)H * S, H, H);
+        issue_wgrad(tWa, sDz(st), S, 128u * S, sDz(st) + kTile, S, 128u * S, H, n1 > 0);
+        mma_commit(c1);
+        ++n1;
+    };
+    if (tid == 0 && n_mine > 0) {
+        hB = ld_nc_v4s32(rec_of(0));
+        while (nA < n_mine && nA < 2) issue_A();
+        issue_B();
+        issue_pair1();
+    }
+    // every thread: its row's fields of the next tile's record, read a tile ahead
+    int4 hn = make_int4(0, 0, 0, 0);
+    int segn = 0, rpa = 0, rpb = 0;
+    float wn = 0.f;
+    auto read_rec = [&](int64_t j) {
+        const uint8_t* r = rec_of(j);
+        hn = ld_nc_v4s32(r);
+        segn = __ldg(reinterpret_cast<const int16_t*>(r + 544) + row);
+        wn = __ldg(reinterpret_cast<const float*>(r + 1312) + row);
+        rpa = __ldg(reinterpret_cast<const int32_t*>(r + 16) + (tid >> 4));       // this thread's first
+        rpb = __ldg(reinterpret_cast<const int32_t*>(r + 16) + (tid >> 4) + 1);   // receiver of the dP sums
+    };
+    if (n_mine > 0) read_rec(0);
+    float acc1[NCH], accb[NCH];   // column sums of dz_0 (db_0) and of g (the LayerNorm beta gradient)
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) acc1[j] = accb[j] = 0.f;
+    bool ok = true;
+    for (int64_t j = 0; j < n_mine; ++j) {
+        const int st = (int)(j & 1);
+        const uint32_t par = (uint32_t)j & 1u;   // c1, c2d, c2w and fullB complete once per tile
+        const int32_t r0 = hn.x, r1 = hn.y, e0 = hn.z, ne = hn.w;
+        const int seg = segn, ra0 = rpa, rb0 = rpb;
+        const float w = wn;
+        const int32_t* rp = reinterpret_cast<const int32_t*>(rec_of(j) + 16);
+        const bool valid = row < ne;
+        // the inputs of g (epilogue 2), requested now
+        float4 ga[CW / 4];
+        uint4 gd[CW / 8];
+        if (valid) {
+            const float4* dar = reinterpret_cast<const float4*>(A.da + (int64_t)(r0 + seg) * H + c0);
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) ga[i] = __ldg(dar + i);
+            if (A.de_out) {
+                const uint4* dp = reinterpret_cast<const uint4*>(A.de_out + ((int64_t)e0 + row) * H + c0);
+#pragma unroll
+                for (int i = 0; i < CW / 8; ++i) gd[i] = __ldg(dp + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < CW / 8; ++i) gd[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW / 4; ++i) ga[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < CW / 8; ++i) gd[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        // epilogue 1: dz_0 into the dz_1 slot of the stage, column sums for db_0 (thread 0
+        // waits for pair 1, the block for thread 0)
+        ok = block_wait(c1, par, tid);
+        if (!ok) break;
+        tc_fence_after();
+        uint8_t* z = sDz(st);
+        uint8_t* hT = sDz(st) + kTile;
+#pragma unroll
+        for (int jj = 0; jj < NCH; ++jj) {
+            float dh[16], hv[16];
+            tmem_ld16(tD1 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+            ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
+            ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
+            st_tile8(z, row, c0 + 16 * jj, 128, S, dh);
+            st_tile8(z, row, c0 + 16 * jj + 8, 128, S, dh + 8);
+            acc1[jj] += warp_colsum16(dh, lane);
+        }
+        tc_fence_before();
+        fence_proxy_async();
+        __syncwarp();   // reconverged before the aligned block barrier
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+        if (!ok) break;
+        if (tid == 0) {   // pair 2 on dz_0; then the next tile's pair 1 (D1 has been read)
+            ok0 = mbar_wait(fullB, par);
+            if (ok0) {
+                tc_fence_after();
+                issue_dgrad(tD2, z, S, sWb, S, H, (uint32_t)H * S, H, H);
+                mma_commit(c2d);
+                issue_wgrad(tWb, z, S, 128u * S, sE, S, 128u * S, H, n2 > 0);
+                mma_commit(c2w);
+                ++n2;
+                if (j + 1 < n_mine) issue_pair1();
+            }
+        }
+        if (j + 1 < n_mine) read_rec(j + 1);
+        // dz_0 per edge, for the sender-side sums of the projection adjoint (whole rows per warp)
+        for (int i = tid; i < ne * CPR; i += NT) {
+            const int rr = i / CPR, jj = i - rr * CPR;
+            *reinterpret_cast<uint4*>(A.dz1 + ((int64_t)e0 + rr) * H + 8 * jj) =
+                *reinterpret_cast<const uint4*>(z + tile_off(rr, 8 * jj, 128, S));
+        }
+        // receiver-side sums of dz_0 over each receiver's edges (dP, fixed edge order)
+        for (int it = tid; it < (r1 - r0) * CPR; it += NT) {
+            const int rr = it / CPR, c = (it % CPR) * 8;
+            const int32_t ea = it < NT ? ra0 : __ldg(rp + rr), eb = it < NT ? rb0 : __ldg(rp + rr + 1);
+            float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int32_t e = ea; e < eb; ++e) {
+                float z8[8];
+                ld_tile8(z, e, c, 128, S, z8);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s8[k] += z8[k];
+            }
+            float4* dp = reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + c);
+            dp[0] = make_float4(s8[0], s8[1], s8[2], s8[3]);
+            dp[1] = make_float4(s8[4], s8[5], s8[6], s8[7]);
+        }
+        // epilogue 2: de_in = g + D2, staged in the stage's h_0 slot (pair 1 and epilogue 1
+        // have read it)
+        ok = block_wait(c2d, par, tid);
+        if (!ok) break;
+        tc_fence_after();
+        {
+            float gv[CW], dh[CW];
+#pragma unroll
+            for (int i = 0; i < CW / 8; ++i) {
+                const uint32_t dw[4] = {gd[i].x, gd[i].y, gd[i].z, gd[i].w};
+                const float4 u0 = ga[2 * i], u1 = ga[2 * i + 1];
+                const float av[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float d0, d1;
+                    unpack_bf16x2(dw[k], d0, d1);
+                    gv[8 * i + 2 * k] = edge_g(w, av[2 * k], d0);
+                    gv[8 * i + 2 * k + 1] = edge_g(w, av[2 * k + 1], d1);
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj) accb[jj] += warp_colsum16(gv + 16 * jj, lane);
+            tmem_ld16(tD2 + lane_base + (uint32_t)c0, dh);
+            tmem_ld16(tD2 + lane_base + (uint32_t)(c0 + 16), dh + 16);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < CW; ++i) dh[i] = __fadd_rn(gv[i], dh[i]);
+            st_row_tile<CW>(hT, row, c0, S, dh);
+        }
+        tc_fence_before();
+        __syncwarp();   // reconverged before the aligned block barrier
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 read, de_in staged
+        if (!ok) break;
+        if (tid == 0) {   // pair 2's wgrad has read dz_0 and e: the next tile's e rows
+            ok0 = mbar_wait(c2w, par);
+            if (ok0 && nB < n_mine) issue_B();
+        }
+        for (int i = tid; i < ne * CPR; i += NT) {
+            const int rr = i / CPR, jj = i - rr * CPR;
+            *reinterpret_cast<uint4*>(A.de_in + ((int64_t)e0 + rr) * H + 8 * jj) =
+                *reinterpret_cast<const uint4*>(hT + tile_off(rr, 8 * jj, 128, S));
+        }
+        fence_proxy_async();   // generic accesses of the stage precede its TMA refill
+        __syncwarp();   // reconverged before the aligned block barrier
+        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // every thread is past its reads of stage st
+        if (!ok) break;
+        if (tid == 0 && nA < n_mine) issue_A();   // tile j + 2 into stage st
+    }
+    if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
+        if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
+        if (n2 > 0) {
+            mbar_wait(c2d, (uint32_t)(n2 - 1) & 1u);
+            mbar_wait(c2w, (uint32_t)(n2 - 1) & 1u);
+        }
+        for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
+        for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
+    }
+    __syncwarp();   // reconverged before the aligned block barrier
+    ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+    tc_fence_after();
+    float* part = A.part + (int64_t)blockIdx.x * A.pstride;
+    if (ok) {
+        if (n_mine > 0) {
+            flush_acc<CG>(tWa, H, H, q, lane, g, part);
+            flush_acc<CG>(tWb, H, H, q, lane, g, part + H * H);
+        } else {
+            for (int i = tid; i < 2 * H * H; i += NT) part[i] = 0.f;
+        }
+    }
+    colsum_store<H, NCH>(acc1, sRed, q, lane, c0, tid, NT, part + 2 * H * H);
+    colsum_store<H, NCH>(accb, sRed, q, lane, c0, tid, NT, part + 2 * H * H + H);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 4 * H);
 }
 
 // ------------------------------------------------------------------ k_bwd_node0
@@ -647,23 +985,29 @@ struct Node0Args {
 };
 
 // 128 rows x 4 column groups, one CTA per SM (TMEM: a 256-column input
-// gradient and the 256-column dW_0 accumulator). The epilogue reads only TMEM
-// and global memory, so the next tile's rows load while it runs.
+// gradient and the 256-column dW_0 accumulator). The epilogue reads only TMEM,
+// the dx' rows and its own FP32 staging tile, so the next tile's rows load while
+// it runs; da* and then dx_in pass through the staging tile and leave as whole
+// rows by TMA stores (rows past n_rows are clipped).
 constexpr int kN0NT = 512;
 struct Node0Smem {
-    static constexpr uint32_t w = 0, dz = 2 * kTile, xa = 3 * kTile;
-    static constexpr uint32_t bar = 5 * kTile;
+    static constexpr uint32_t w = 0, dz = 2 * kTile, xa = 3 * kTile, f = 5 * kTile;   // f: [128 x H] FP32
+    static constexpr uint32_t bar = f + 128 * H128 * 4;
     static constexpr uint32_t total = bar + 64 + 1024;
 };
+static_assert(Node0Smem::total <= 227 * 1024, "k_bwd_node0 shared memory");
 
 __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ CUtensorMap tm_dz,
-                                                       const __grid_constant__ CUtensorMap tm_xa, Node0Args A) {
+                                                       const __grid_constant__ CUtensorMap tm_xa,
+                                                       const __grid_constant__ CUtensorMap tm_da,
+                                                       const __grid_constant__ CUtensorMap tm_dxi, Node0Args A) {
     constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kN0NT;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     uint8_t* sW0 = sm + Node0Smem::w;
     uint8_t* sDz = sm + Node0Smem::dz;
     uint8_t* sXa = sm + Node0Smem::xa;
+    uint8_t* sF = sm + Node0Smem::f;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + Node0Smem::bar);
     uint64_t* bar = full + 1;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
@@ -724,7 +1068,11 @@ __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ 
                 const float4 u = __ldg(pg + i);
                 gx[4 * i] = u.x; gx[4 * i + 1] = u.y; gx[4 * i + 2] = u.z; gx[4 * i + 3] = u.w;
             }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) gx[i] = 0.f;
         }
+        if (tid == 0) bulk_wait_read_all();   // the previous tile's dx_in store has read the staging tile
         ok = block_wait(bar, ph, tid);
         if (!ok) break;
         mp = false;
@@ -735,25 +1083,40 @@ __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ 
         if (tid == 0 && t + gridDim.x < A.t1) issue(t + gridDim.x);
         float d[CW];
         ld_acc<CW>(tWork, q, c0, d);   // gradient of a* (first H inputs)
-        if (valid) {
-            float4* po = reinterpret_cast<float4*>(A.da + r * H + c0);
 #pragma unroll
-            for (int i = 0; i < CW / 4; ++i) po[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+        for (int i = 0; i < CW / 4; ++i)
+            st_f32x4_tile<H>(sF, row, c0 + 4 * i, make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]));
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int b = 0; b < H / 32; ++b) tma_store_2d(&tm_da, 32 * b, (int32_t)(t * 128), sF + b * 128 * 128);
+            bulk_commit();
         }
         ld_acc<CW>(tWork + H, q, c0, d);   // gradient of x (last H inputs) plus the residual branch
         tc_fence_before();
-        if (valid) {
-            float4* po = reinterpret_cast<float4*>(A.dx_in + r * H + c0);
 #pragma unroll
-            for (int i = 0; i < CW / 4; ++i)
-                po[i] = make_float4(gx[4 * i] + d[4 * i], gx[4 * i + 1] + d[4 * i + 1], gx[4 * i + 2] + d[4 * i + 2],
-                                    gx[4 * i + 3] + d[4 * i + 3]);
+        for (int i = 0; i < CW; ++i) d[i] = gx[i] + d[i];
+        if (tid == 0) bulk_wait_read_all();   // the da* store has read the staging tile
+        __syncwarp();
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < CW / 4; ++i)
+            st_f32x4_tile<H>(sF, row, c0 + 4 * i, make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]));
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int b = 0; b < H / 32; ++b) tma_store_2d(&tm_dxi, 32 * b, (int32_t)(t * 128), sF + b * 128 * 128);
+            bulk_commit();
         }
     }
+    if (tid == 0) bulk_wait_all();   // the stored rows are written before the CTA exits
     if (tid == 0 && !ok) {   // after a timeout: wait (bounded) for what this CTA started
         if (mp) mbar_wait(bar, ph);
         if (lp) mbar_wait(full, mp ? ph ^ 1 : ph);
     }
+    __syncwarp();   // reconverged before the aligned block barrier
     ok = __syncthreads_and(ok) != 0;
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
     if (ok) {
@@ -824,40 +1187,85 @@ B128Ws carve_b128(void* ws, const gnn_graph_dev& G, int Le, int Ln, bool need_a,
 // dz_{k-1} and the gradients of W_k, b_{k-1} for k = L-1 .. 1 over a chunk of
 // n_tiles tiles; returns the buffer that holds dz_0.
 int chain_backward(const gnn_mlp& W, const gnn_mlp& dW, B128Ws& w, int64_t n_tiles, int* cur, bool pairs,
-                   cudaStream_t s) {
-    return chain_backward_h128(W, dW, w.hs, w.hs_stride, w.dzs, w.part, kPstride, n_tiles, cur, s, pairs);
+                   cudaStream_t s, int k_last = 1) {
+    return chain_backward_h128(W, dW, w.hs, w.hs_stride, w.dzs, w.part, kPstride, n_tiles, cur, s, pairs, k_last);
 }
 
 // gamma, beta and the last bias of an MLP from the recomputation's partials
-int reduce_ln(const gnn_mlp& dW, const B128Ws& w, int grid, cudaStream_t s) {
+// [dgamma | dbeta | db_{L-1}]; without `beta` the beta gradient is left to the
+// kernel of the first Linear (the edge MLP's, which forms g again)
+int reduce_ln(const gnn_mlp& dW, const B128Ws& w, int grid, cudaStream_t s, bool beta = true) {
     constexpr int H = H128;
     RedSeg seg[3];
-    seg[0] = RedSeg{dW.gamma, H, 1, H, 0, 0};
-    seg[1] = RedSeg{dW.beta, H, 1, H, H, 0};
-    seg[2] = RedSeg{dW.b[dW.n_lin - 1], H, 1, H, 2 * H, 0};
-    return reduce_grads(seg, 3, w.part, kPstride, grid, s);
+    int n = 0;
+    seg[n++] = RedSeg{dW.gamma, H, 1, H, 0, 0};
+    if (beta) seg[n++] = RedSeg{dW.beta, H, 1, H, H, 0};
+    seg[n++] = RedSeg{dW.b[dW.n_lin - 1], H, 1, H, 2 * H, 0};
+    return reduce_grads(seg, n, w.part, kPstride, grid, s);
+}
+
+// Linear 1 and the first Linear's edge part of the edge MLP adjoint over tiles
+// [t0, t1) of a chunk (k_bwd_chain_edge0): dz_1 is in w.dzs[cur], h_0 in block 0
+// of w.hs.
+int chain_edge0(const gnn_graph_dev& G, const gnn_mp_params& W, const gnn_mp_params& dW, B128Ws& w, int64_t t0,
+                int64_t t1, int cur, const CUtensorMap& tm_e, const __nv_bfloat16* de_out, __nv_bfloat16* de_in,
+                cudaStream_t s) {
+    constexpr int H = H128;
+    const int64_t rows = (t1 - t0) * 128;
+    CUtensorMap tm_dz, tm_h;
+    int rc = make_row_tmap(&tm_dz, w.dzs[cur], rows, H);
+    if (rc) return rc;
+    if ((rc = make_row_tmap(&tm_h, w.hs, rows, H))) return rc;
+    ChainE0Args A{};
+    A.Wa = W.edge.W[1];
+    A.W1 = W.edge.W[0];
+    A.tile_meta = static_cast<const uint8_t*>(G.tile_meta);
+    A.t0 = t0;
+    A.n_tiles = t1 - t0;
+    A.de_out = de_out;
+    A.da = w.da;
+    A.de_in = de_in;
+    A.dz1 = w.dz1;
+    A.dP = w.dP;
+    A.part = w.part;
+    A.pstride = kPstride;
+    int grid;
+    if ((rc = persistent_grid(k_bwd_chain_edge0, kCE0NT, ChainE0Smem::total, 4 * H, t1 - t0, &grid))) return rc;
+    {
+        ProfScope _ps(s, "k_bwd_chain_edge0");
+        k_bwd_chain_edge0<<<grid, kCE0NT, ChainE0Smem::total, s>>>(tm_dz, tm_h, tm_e, A);
+    }
+    GNN_LAUNCH_CHECK("k_bwd_chain_edge0");
+    RedSeg seg[4];
+    seg[0] = RedSeg{dW.edge.W[1], H, H, H, 0, H};
+    seg[1] = RedSeg{dW.edge.W[0] + 2 * H, 3 * H, H, H, (int64_t)H * H, H};   // W1c columns of W1
+    seg[2] = RedSeg{dW.edge.b[0], H, 1, H, 2 * (int64_t)H * H, 0};
+    seg[3] = RedSeg{dW.edge.beta, H, 1, H, 2 * (int64_t)H * H + H, 0};
+    return reduce_grads(seg, 4, w.part, kPstride, grid, s);
 }
 
 }  // namespace
 
 int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
                         __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
-                        cudaStream_t s, bool pairs) {
+                        cudaStream_t s, bool pairs, int k_last) {
     constexpr int H = H128;
     GNN_REQUIRE(pstride >= 2 * H * H + 2 * H, GNN_EINVAL, "chain adjoint: partial stride too small");
+    GNN_REQUIRE(k_last >= 1, GNN_EINVAL, "chain adjoint: k_last %d", k_last);
     const int L = W.n_lin;
     int grid, grid2;
     int rc = persistent_grid(k_bwd_chain<false>, kChainNT, ChainSmem::total, 4 * H, n_tiles, &grid);
     if (rc) return rc;
     if ((rc = persistent_grid(k_bwd_chain2, kC2NT, Chain2Smem::total, 4 * H, n_tiles, &grid2))) return rc;
     const int64_t rows = n_tiles * 128;
-    for (int k = L - 1; k >= 1;) {
+    for (int k = L - 1; k >= k_last;) {
         CUtensorMap tm_dz, tm_h;
         if ((rc = make_row_tmap(&tm_dz, dzs[*cur], rows, H))) return rc;
         if ((rc = make_row_tmap(&tm_h, hs + (int64_t)(k - 1) * hs_stride, rows, H))) return rc;
-        if (pairs && k >= 2) {   // Linears k and k-1 in one pass
-            CUtensorMap tm_hb;
+        if (pairs && k - 1 >= k_last) {   // Linears k and k-1 in one pass
+            CUtensorMap tm_hb, tm_out;
             if ((rc = make_row_tmap(&tm_hb, hs + (int64_t)(k - 2) * hs_stride, rows, H))) return rc;
+            if ((rc = make_row_tmap(&tm_out, dzs[*cur ^ 1], rows, H))) return rc;
             Chain2Args A{};
             A.Wa = W.W[k];
             A.Wb = W.W[k - 1];
@@ -868,7 +1276,7 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
             A.pstride = pstride;
             {
                 ProfScope _ps(s, "k_bwd_chain2");
-                k_bwd_chain2<<<grid2, kC2NT, Chain2Smem::total, s>>>(tm_dz, tm_h, tm_hb, A);
+                k_bwd_chain2<<<grid2, kC2NT, Chain2Smem::total, s>>>(tm_dz, tm_h, tm_hb, tm_out, A);
             }
             GNN_LAUNCH_CHECK("k_bwd_chain2");
             RedSeg seg[4];
@@ -996,9 +1404,12 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
         A.pstride = kPstride;
         int grid;
         if ((rc = persistent_grid(k_bwd_node0, kN0NT, Node0Smem::total, 4 * H, t1 - t0, &grid))) return rc;
+        CUtensorMap tm_da, tm_dxi;
+        if ((rc = make_f32_tmap(&tm_da, w.da, NR, H))) return rc;
+        if ((rc = make_f32_tmap(&tm_dxi, dx_in, NR, H))) return rc;
         {
             ProfScope _ps(s, "k_bwd_node0");
-            k_bwd_node0<<<grid, kN0NT, Node0Smem::total, s>>>(tm_dz, tm_xa, A);
+            k_bwd_node0<<<grid, kN0NT, Node0Smem::total, s>>>(tm_dz, tm_xa, tm_da, tm_dxi, A);
         }
         GNN_LAUNCH_CHECK("k_bwd_node0");
         RedSeg seg[1] = {RedSeg{dW.node.W[0], 2 * H, H, 2 * H, 0, 2 * H}};
@@ -1014,6 +1425,9 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
                     "gnn_mp_backward: tile_meta must be a 16-byte aligned device array");
         CUtensorMap tm_e;
         if ((rc = make_row_tmap(&tm_e, e_in, E, H))) return rc;
+        // with an odd number of Linears after the first, the pairs leave Linear 1 alone: it
+        // runs with the first Linear's edge part in one pass (k_bwd_chain_edge0)
+        const bool merge_e0 = pairs && (Le - 1) % 2 == 1;
         for (int64_t t0 = 0; t0 < G.n_edge_tiles; t0 += w.chunk) {
             const int64_t t1 = std::min<int64_t>(G.n_edge_tiles, t0 + w.chunk);
             RecomputeSave o{};
@@ -1027,8 +1441,13 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
             o.part = w.part;
             o.pstride = kPstride;
             if ((rc = edge_recompute_save(G, cfg, W, e_in, w.pq, o, s))) return rc;
-            if ((rc = reduce_ln(dW.edge, w, o.grid, s))) return rc;
+            if ((rc = reduce_ln(dW.edge, w, o.grid, s, false))) return rc;
             int cur = 0;
+            if (merge_e0) {   // Linears L-1 .. 2 in pairs, then Linear 1 with the first Linear's edge part
+                if ((rc = chain_backward(W.edge, dW.edge, w, t1 - t0, &cur, pairs, s, 2))) return rc;
+                if ((rc = chain_edge0(G, W, dW, w, t0, t1, cur, tm_e, de_out, de_in, s))) return rc;
+                continue;
+            }
             if ((rc = chain_backward(W.edge, dW.edge, w, t1 - t0, &cur, pairs, s))) return rc;
             CUtensorMap tm_dz;
             if ((rc = make_row_tmap(&tm_dz, w.dzs[cur], (t1 - t0) * 128, H))) return rc;
@@ -1051,8 +1470,9 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
                 k_bwd_edge0<<<grid, kE0NT, Edge0Smem::total, s>>>(tm_dz, tm_e, A);
             }
             GNN_LAUNCH_CHECK("k_bwd_edge0");
-            RedSeg seg[1] = {RedSeg{dW.edge.W[0] + 2 * H, 3 * H, H, H, 0, H}};   // W1c columns of W1
-            if ((rc = reduce_grads(seg, 1, w.part, kPstride, grid, s))) return rc;
+            RedSeg seg[2] = {RedSeg{dW.edge.W[0] + 2 * H, 3 * H, H, H, 0, H},   // W1c columns of W1
+                             RedSeg{dW.edge.beta, H, 1, H, (int64_t)H * H, 0}};
+            if ((rc = reduce_grads(seg, 2, w.part, kPstride, grid, s))) return rc;
         }
     } else {
         GNN_CUDA_CHECK(cudaMemsetAsync(w.dP, 0, sizeof(float) * NR * H, s), "memset");

@@ -256,10 +256,10 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
                                              make_float2(er[i], er[i + 1]));
                 const float2 yb = __fadd2_rn(__ffma2_rn(xb, make_float2(gm.z, gm.w), make_float2(bt.z, bt.w)),
                                              make_float2(er[i + 2], er[i + 3]));
-                ev[c + i] = valid ? ya.x : 0.f;
-                ev[c + i + 1] = valid ? ya.y : 0.f;
-                ev[c + i + 2] = valid ? yb.x : 0.f;
-                ev[c + i + 3] = valid ? yb.y : 0.f;
+                ev[c + i] = ya.x;   // rows past the tile's edges are never read back
+                ev[c + i + 1] = ya.y;
+                ev[c + i + 2] = yb.x;
+                ev[c + i + 3] = yb.y;
             }
             st_tile8(sE, row, c, 128, kS, ev + c);
         }
@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
         if (leader && t + step < A.n_tiles) issue_ld(t + step, tile_hdr(t + step).z);
     }
     if (leader && ld_pending) mbar_wait(bar_ld + gi, ph_ld);   // after a timeout: bounded
+    __syncwarp();   // reconverged before the aligned block barrier
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -323,10 +324,11 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_fwd_tm(const __grid_constant__ 
 // LayerNorm is replaced by its adjoint: g = de' + da_i / d_ij (the adjoint of
 // Eq. 5b after the halo adjoint), dz = rstd (g gamma - mean(g gamma) - xhat
 // mean(g gamma xhat)), stored the same way (row (t - t0) * 128 + i), and the
-// column sums of g xhat, g and dz (the gamma, beta and last-bias gradients)
-// accumulate per warp over its rows by recursive halving across lanes; at the
-// end the eight warps' sums are added in warp order into the CTA's partials
-// [dgamma | dbeta | db_{L-1}].
+// column sums of g xhat and dz (the gamma and last-bias gradients) accumulate
+// per warp over its rows by recursive halving across lanes; at the end the
+// eight warps' sums are added in warp order into the CTA's partials
+// [dgamma | - | db_{L-1}]. The beta gradient (the column sums of g) is left to
+// the kernel of the first Linear, which forms g again.
 
 struct TmSaveArgs {
     const uint8_t* tile_meta;
@@ -397,9 +399,9 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
     uint32_t ph_ld = 0, ph_mma = 0;
     bool ok = true;
     // column sums over the warp's rows: lane l holds column 16 j + (l >> 1) of each 16-column block j
-    float accG[8], accB[8], accZ[8];
+    float accG[8], accZ[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) accG[j] = accB[j] = accZ[j] = 0.f;
+    for (int j = 0; j < 8; ++j) accG[j] = accZ[j] = 0.f;
 
     for (int64_t t = t_first; t < A.t1 && ok; t += step) {
         bool w_ok = leader ? mbar_wait(bar_ld + gi, ph_ld) : true;
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
                 mma_bf16(tAcc, desc_step(a0, kmajor_off(128, kS, k0)), desc_step(b0, kmajor_off(kH, kS, k0)), id,
                          k0 > 0 ? 1u : 0u);
             mma_commit(bar_mma + gi);
-            if (t + step < A.t1) {   // the group's next edge rows and their receivers' da rows into L2
+            if (t + step < A.t1) {   // the group's next edge rows, their de' rows and their receivers' da rows into L2
                 const int4 hn = tile_hdr(t + step);
                 if (hn.w > 0) prefetch_l2(A.e_in + (int64_t)hn.z * kH, (uint32_t)hn.w * kH * 2);
                 if (hn.y > hn.x) prefetch_l2(A.da + (int64_t)hn.x * kH, (uint32_t)(hn.y - hn.x) * kH * 4);
@@ -580,6 +582,11 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
             const float rstd = rsqrtf(fmaxf(tq * (1.f / kH) - mean * mean, 0.f) + A.eps);
             const float s1 = td * (1.f / kH);
             const float s2 = rstd * (tdv - mean * td) * (1.f / kH);
+            // xhat = (z + b - mean) rstd, dz = (g gamma) rstd + (xhat (-rstd s2) - rstd s1), in
+            // pairs; a row past the tile's edges takes rstd = 0, so its xhat and dz are 0 (its g is 0)
+            const float r = valid ? rstd : 0.f;
+            const float2 r2 = make_float2(r, r), nm2 = make_float2(-mean, -mean);
+            const float2 ks2 = make_float2(-r * s2, -r * s2), ks1 = make_float2(-r * s1, -r * s1);
 #pragma unroll
             for (int c = 0; c < kH; c += 16) {
                 float z[16], g[16], tg[16], dz[16];
@@ -587,13 +594,19 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
                 tmem_ld16(tG + lane_base + c, g);
                 tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float xh = valid ? (z[i] + bl[c + i] - mean) * rstd : 0.f;
-                    tg[i] = g[i] * xh;
-                    dz[i] = valid ? rstd * (g[i] * gam[c + i] - s1 - xh * s2) : 0.f;
+                for (int i = 0; i < 16; i += 2) {
+                    const float2 b2 = *reinterpret_cast<const float2*>(bl + c + i);
+                    const float2 gm2 = *reinterpret_cast<const float2*>(gam + c + i);
+                    const float2 g2 = make_float2(g[i], g[i + 1]);
+                    const float2 xh = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(z[i], z[i + 1]), b2), nm2), r2);
+                    const float2 t2 = __fmul2_rn(g2, xh);
+                    const float2 d2 = __ffma2_rn(__fmul2_rn(g2, gm2), r2, __ffma2_rn(xh, ks2, ks1));
+                    tg[i] = t2.x;
+                    tg[i + 1] = t2.y;
+                    dz[i] = d2.x;
+                    dz[i + 1] = d2.y;
                 }
                 accG[c / 16] += warp_colsum16(tg, lane);
-                accB[c / 16] += warp_colsum16(g, lane);
                 accZ[c / 16] += warp_colsum16(dz, lane);
                 st_tile8(sE, row, c, 128, kS, dz);
                 st_tile8(sE, row, c + 8, 128, kS, dz + 8);
@@ -612,27 +625,27 @@ __global__ void __launch_bounds__(kNT, 1) k_edge_save_tm(const __grid_constant__
     }
     if (leader && ld_pending) mbar_wait(bar_ld + gi, ph_ld);   // after a timeout: bounded
     if (leader) bulk_wait_all();                                // the scratch rows are written
+    __syncwarp();   // reconverged before the aligned block barrier
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     // the CTA's partials: the eight warps' column sums in warp order (the staging tiles are free)
-    float* red = reinterpret_cast<float*>(sm + L.e);   // [8 warps][3][H]
+    float* red = reinterpret_cast<float*>(sm + L.e);   // [8 warps][2][H]
     if ((lane & 1) == 0) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int c = 16 * j + (lane >> 1);
-            red[(warp * 3 + 0) * kH + c] = accG[j];
-            red[(warp * 3 + 1) * kH + c] = accB[j];
-            red[(warp * 3 + 2) * kH + c] = accZ[j];
+            red[(warp * 2 + 0) * kH + c] = accG[j];
+            red[(warp * 2 + 1) * kH + c] = accZ[j];
         }
     }
     __syncthreads();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
-    for (int i = tid; i < 3 * kH; i += kNT) {
+    for (int i = tid; i < 2 * kH; i += kNT) {
         const int k = i / kH, c = i % kH;
         float s = 0.f;
-        for (int wi = 0; wi < 8; ++wi) s += red[(wi * 3 + k) * kH + c];
-        part[i] = s;
+        for (int wi = 0; wi < 8; ++wi) s += red[(wi * 2 + k) * kH + c];
+        part[k == 0 ? c : 2 * kH + c] = s;   // dgamma, then db_{L-1} (dbeta: the first-Linear kernel)
     }
     tc_fence_before();
     __syncthreads();

@@ -1123,16 +1123,6 @@ __global__ void __launch_bounds__(RtCfg<H>::NT, 1)
 
 // ------------------------------------------------------------------ k_node_fwd
 
-// Four floats at (r, c..c+3) of an FP32 node-row tile in the layout of
-// make_f32_tmap boxes (the store counterpart of ld_f32x4_tile).
-template <int H>
-__device__ __forceinline__ void st_f32x4_tile(uint8_t* tile, int r, int c, float4 v) {
-    constexpr int BW = H < 32 ? H : 32, SB = BW * 4;
-    const uint32_t o = (uint32_t)r * SB + (uint32_t)(c % BW) * 4;
-    const uint32_t sw = o ^ (((o >> 7) & (uint32_t)(SB / 16 - 1)) << 4);
-    *reinterpret_cast<float4*>(tile + (uint32_t)(c / BW) * 128 * SB + sw) = v;
-}
-
 struct NodeFwdArgs {
     const float* a_star;
     const float* x;

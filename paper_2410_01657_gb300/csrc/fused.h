@@ -108,10 +108,11 @@ int backward_h128(const gnn_graph_dev& G, const gnn_mp_config& cfg, const gnn_mp
 // `pairs`, Linears k and k-1 share a pass (k_bwd_chain2, dz_{k-1} kept on chip)
 // while two remain, else one pass per Linear (k_bwd_chain); the results are the
 // same bit for bit. part holds pstride >= 2 H (H + 1) floats for each CTA of a
-// persistent grid (one CTA per SM).
+// persistent grid (one CTA per SM). k_last > 1 stops after Linear k_last (dz_{k_last - 1}
+// left in dzs[*cur]).
 int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, int64_t hs_stride,
                         __nv_bfloat16* const dzs[2], float* part, int64_t pstride, int64_t n_tiles, int* cur,
-                        cudaStream_t s, bool pairs = true);
+                        cudaStream_t s, bool pairs = true, int k_last = 1);
 // The same kernel on the first Linear of a row MLP whose input X is data: with
 // dz_0 and the BF16 copy of X in tile-padded scratch rows (row i of the scratch
 // is row row0 + i of X), writes dX = dz_0 W_0 (FP32 [n_rows x H], rows below

@@ -43,6 +43,7 @@ struct MlpDev {
 // subsequent tcgen05/shared-memory accesses.
 __device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, int tid) {
     const int mine = (tid == 0) ? (mbar_wait(bar, parity) ? 1 : 0) : 1;
+    __syncwarp();   // warp 0 reconverged before the aligned block barrier
     return __syncthreads_and(mine) != 0;
 }
 
@@ -170,6 +171,16 @@ __device__ __forceinline__ float4 ld_f32x4_tile(const uint8_t* tile, int r, int 
     const uint32_t o = (uint32_t)r * SB + (uint32_t)(c % BW) * 4;
     const uint32_t sw = o ^ (((o >> 7) & (uint32_t)(SB / 16 - 1)) << 4);
     return *reinterpret_cast<const float4*>(tile + (uint32_t)(c / BW) * 128 * SB + sw);
+}
+
+// Four floats at (r, c..c+3) of an FP32 node-row tile in the layout of
+// make_f32_tmap boxes (the store counterpart of ld_f32x4_tile).
+template <int H>
+__device__ __forceinline__ void st_f32x4_tile(uint8_t* tile, int r, int c, float4 v) {
+    constexpr int BW = H < 32 ? H : 32, SB = BW * 4;
+    const uint32_t o = (uint32_t)r * SB + (uint32_t)(c % BW) * 4;
+    const uint32_t sw = o ^ (((o >> 7) & (uint32_t)(SB / 16 - 1)) << 4);
+    *reinterpret_cast<float4*>(tile + (uint32_t)(c / BW) * 128 * SB + sw) = v;
 }
 
 // Issue the TMA loads of the FP32 node-row tile starting at row r0 (H/BW boxes).

@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(kNT, 1) k_rowdec_save_tm(const __grid_constant
         group_sync(gi);   // the staging tile is free for the next tile's X
     }
     if (leader) bulk_wait_all();   // the scratch rows are written
+    __syncwarp();   // reconverged before the aligned block barrier
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(kNT, 1) k_rowenc_save_tm(const __grid_constant
         }
     }
     if (leader) bulk_wait_all();   // the scratch rows are written
+    __syncwarp();   // reconverged before the aligned block barrier
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -377,14 +377,16 @@ def test_h128_tensor_memory_kernels_match_one_tile_kernels(n_hidden):
         assert rel_l2(a, b) < 1e-2
 
 
-@pytest.mark.parametrize("n_hidden", [1, 2])
+@pytest.mark.parametrize("n_hidden", [0, 1, 2])
 def test_h128_adjoint_two_linears_per_pass_match_one(n_hidden):
     # The layered H = 128 adjoint runs two Linears per pass (k_bwd_chain2, dz_{k-1}
-    # kept in shared memory) by default and one per pass with GNN_FLAG_ADJ_ONE_LINEAR
-    # (k_bwd_chain alone). Both use the same operands and roundings, so every output
-    # and gradient agrees bit for bit. The 12^3 p=3 brick gives each CTA tens of tiles,
-    # so the kernels' stage rings wrap many times; a workspace of 200 tiles per chunk adds
-    # chunk boundaries.
+    # kept in shared memory) by default, and when Linear 1 is left alone it runs it
+    # together with the first Linear's edge part (k_bwd_chain_edge0, dz_0 kept in
+    # shared memory; n_hidden 0 and 2); with GNN_FLAG_ADJ_ONE_LINEAR every Linear has
+    # its own pass (k_bwd_chain, then k_bwd_edge0). Both use the same operands,
+    # roundings and summation orders, so every output and gradient agrees bit for bit.
+    # The 12^3 p=3 brick gives each CTA tens of tiles, so the kernels' stage rings wrap
+    # many times; a workspace of 200 tiles per chunk adds chunk boundaries.
     H = 128
     part = MeshGraph((12, 12, 12), 3).partition(3, "rcb")
     G = part.to_device(DEV)

@@ -761,8 +761,7 @@ def main():
     if not args.no_e2e and wl["inputs"] == "encoders" and not fwd_only:
         torch.cuda.synchronize()
         ms_e, ms_e_mean, h2d, d2h, e2e_k = time_e2e(net, G, u, t, max(3, args.steps // 4), 2, dev)
-        enc_path = ("fused BF16 row MLPs" if Hw <= 64 else
-                    "encoders on the fused BF16 row MLP, decoder on the plain FP32 row MLP")
+        enc_path = "fused BF16 row MLPs"
         e2e = {"value": world * e_unpart * M / (ms_e * 1e-3), "unit": "edges/s", "ms_per_step": ms_e,
                "mean_ms_per_step": ms_e_mean, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "library_kernels_one_step": e2e_k,

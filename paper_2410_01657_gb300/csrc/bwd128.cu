@@ -673,15 +673,22 @@ __global__ void __launch_bounds__(kE0NT, 1) k_bwd_edge0(const __grid_constant__ 
 // that dz_0 never travels through the scratch. Per tile: MMA pair 1 (D1 =
 // dz_1 W_1, dW_1 += dz_1^T h_0), epilogue 1 (dz_0 = D1 ELU'(h_0) as BF16 into
 // the shared-memory slot dz_1 came in, its column sums for db_0), MMA pair 2
-// (D2 = dz_0 W1c, dW1c += dz_0^T e) while the block writes dz_0 per edge
-// (whole rows) and sums it over each receiver's edges (dP), epilogue 2 (de_in =
-// g + D2 with g = de' + da_i / d_ij, staged in the stage's h_0 slot and written
-// as whole rows). Operands, roundings and summation orders are those of the two
-// kernels, so the results are the same bit for bit. TMEM: D1, D2, dW_1, dW1c
-// (128 columns each). Two stages of {dz_1, h_0} rows; the e rows have one
-// stage, reloaded once pair 2's weight gradient has read them. The tile records
-// stay in global memory (brought into L2 two tiles ahead); each thread reads
-// its row's fields of the next record while the current tile runs.
+// (D2 = dz_0 W1c, dW1c += dz_0^T e), dz_0 per edge (whole rows) and its sums
+// over each receiver's edges (dP), epilogue 2 (de_in = g + D2 with g = de' +
+// da_i / d_ij, staged in the stage's h_0 slot and written as whole rows, the
+// column sums of g for the LayerNorm beta gradient).
+//
+// Two warp groups split the epilogues, so that epilogue 2 of tile j runs beside
+// epilogue 1 of tile j + 1: group X (warps 0-7) waits for pair 1, writes dz_0,
+// tells group Y's leader through an mbarrier (zr) that dz_0 is in place, issues
+// the next tile's pair 1 and then writes dz_0 per edge and dP; group Y (warps
+// 8-15) issues pair 2, runs epilogue 2, reloads the e tile once pair 2 has read
+// it and the stage once group X has said (mbarrier xd) that it has read it.
+// Each warp covers 64 columns of its 32 rows (TMEM lane quarter). Operands,
+// roundings and summation orders are those of the two separate kernels, so the
+// results are the same bit for bit. TMEM: D1, D2, dW_1, dW1c (128 columns
+// each). Two stages of {dz_1, h_0} rows; one stage of e rows. The tile records
+// stay in global memory (brought into L2 two tiles ahead).
 
 struct ChainE0Args {
     const float* Wa;             // W_1 [H x H] (FP32)
@@ -693,7 +700,7 @@ struct ChainE0Args {
     __nv_bfloat16* de_in;
     __nv_bfloat16* dz1;          // per-edge dz_0 [E x H]
     float* dP;                   // [n_rows x H]
-    float* part;                 // per-CTA: dW_1, dW1c [H x H], then db_0 [H]
+    float* part;                 // per-CTA: dW_1, dW1c [H x H], then db_0 and dbeta [H]
     int64_t pstride;
 };
 
@@ -702,17 +709,24 @@ struct ChainE0Smem {
     static constexpr uint32_t wa = 0, wb = kTile;
     static constexpr uint32_t a = 2 * kTile;          // stage s: dz_1 (then dz_0), h_0 (then de_in), at a + s * 2 * kTile
     static constexpr uint32_t e = a + 4 * kTile;      // e rows
-    static constexpr uint32_t red = a;                // 4 x H floats, after the tile loop
-    static constexpr uint32_t bar = e + kTile;        // fullA[2], fullB, c1, c2d, c2w, TMEM slot
-    static constexpr uint32_t total = bar + 64 + 1024;
+    static constexpr uint32_t red = a;                // 8 x H floats, after the tile loop
+    static constexpr uint32_t bar = e + kTile;        // fullA[2], fullB, c1, c2d, c2w, zr, xd, n1, TMEM slot
+    static constexpr uint32_t total = bar + 128 + 1024;
 };
 static_assert(ChainE0Smem::total <= 227 * 1024, "k_bwd_chain_edge0 shared memory");
+
+// One warp group's named barrier (X: 1, Y: 2; 256 threads), AND-ing a predicate;
+// the warp is reconverged first (the barrier is an aligned one).
+__device__ __forceinline__ bool ce0_group_and(bool v, bool isX) {
+    __syncwarp();
+    return named_and(v, isX ? 1 : 2, 256);
+}
 
 __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_constant__ CUtensorMap tm_dz,
                                                               const __grid_constant__ CUtensorMap tm_h,
                                                               const __grid_constant__ CUtensorMap tm_e,
                                                               ChainE0Args A) {
-    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kCE0NT, NCH = CW / 16, CPR = H / 8;
+    constexpr int H = H128, S = kS, CG = 4, CW = 64, NT = kCE0NT, NCH = CW / 16, CPR = H / 8, GT = 256;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     uint8_t* sWa = sm + ChainE0Smem::wa;
@@ -724,17 +738,22 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
     uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
     uint64_t* c2d = fullA + 4;     // pair 2's dgrad complete
     uint64_t* c2w = fullA + 5;     // pair 2's wgrad complete
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 6);
+    uint64_t* zr = fullA + 6;      // group X has written the tile's dz_0
+    uint64_t* xd = fullA + 7;      // group X has read the tile's stage
+    int64_t* sN1 = reinterpret_cast<int64_t*>(fullA + 8);   // pair 1 issues (for the final waits)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 9);
     auto sDz = [&](int st) { return sm + ChainE0Smem::a + st * 2 * kTile; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    const bool isX = warp < 8;
+    const int q = warp & 3, row = 32 * q + lane, c0 = 64 * ((warp >> 2) & 1), gt = tid & (GT - 1);
+    const bool leader = gt == 0;   // X: thread 0, Y: thread 256
     if (warp == 0) {
         tmem_alloc(tslot, 4 * H);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 6; ++i) mbar_init(fullA + i, 1);
+        for (int i = 0; i < 8; ++i) mbar_init(fullA + i, 1);
         fence_mbar_init();
     }
     load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
@@ -749,11 +768,10 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
                                ? (A.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };   // chunk-relative
     auto rec_of = [&](int64_t j) { return A.tile_meta + (A.t0 + tile_of(j)) * GNN_TILE_META_BYTES; };
-    // thread 0 only: loads and MMA pairs issued so far, whether it is still well, and
-    // the header of the tile whose e rows load next (read one e load ahead)
+    // leaders only: X issues pair 1 (n1); Y issues the loads (nA, nB) and pair 2 (n2)
     int64_t nA = 0, nB = 0, n1 = 0, n2 = 0;
     bool ok0 = true;
-    int4 hB = make_int4(0, 0, 0, 0);
+    int4 hB = make_int4(0, 0, 0, 0);   // Y: the header of the tile whose e rows load next
     auto issue_A = [&]() {   // dz_1 and h_0 rows of tile nA into stage nA % 2, its record into L2
         const int st = (int)(nA & 1);
         const int32_t y = (int32_t)(tile_of(nA) * 128);
@@ -783,188 +801,199 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
         mma_commit(c1);
         ++n1;
     };
-    if (tid == 0 && n_mine > 0) {
+    if (tid == 256 && n_mine > 0) {
         hB = ld_nc_v4s32(rec_of(0));
         while (nA < n_mine && nA < 2) issue_A();
         issue_B();
-        issue_pair1();
     }
-    // every thread: its row's fields of the next tile's record, read a tile ahead
-    int4 hn = make_int4(0, 0, 0, 0);
-    int segn = 0, rpa = 0, rpb = 0;
-    float wn = 0.f;
-    auto read_rec = [&](int64_t j) {
-        const uint8_t* r = rec_of(j);
-        hn = ld_nc_v4s32(r);
-        segn = __ldg(reinterpret_cast<const int16_t*>(r + 544) + row);
-        wn = __ldg(reinterpret_cast<const float*>(r + 1312) + row);
-        rpa = __ldg(reinterpret_cast<const int32_t*>(r + 16) + (tid >> 4));       // this thread's first
-        rpb = __ldg(reinterpret_cast<const int32_t*>(r + 16) + (tid >> 4) + 1);   // receiver of the dP sums
-    };
-    if (n_mine > 0) read_rec(0);
-    float acc1[NCH], accb[NCH];   // column sums of dz_0 (db_0) and of g (the LayerNorm beta gradient)
+    if (tid == 0 && n_mine > 0) issue_pair1();
+    float acc[NCH];   // X: column sums of dz_0 (db_0); Y: of g (the LayerNorm beta gradient)
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) acc1[j] = accb[j] = 0.f;
+    for (int j = 0; j < NCH; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int64_t j = 0; j < n_mine; ++j) {
-        const int st = (int)(j & 1);
-        const uint32_t par = (uint32_t)j & 1u;   // c1, c2d, c2w and fullB complete once per tile
-        const int32_t r0 = hn.x, r1 = hn.y, e0 = hn.z, ne = hn.w;
-        const int seg = segn, ra0 = rpa, rb0 = rpb;
-        const float w = wn;
-        const int32_t* rp = reinterpret_cast<const int32_t*>(rec_of(j) + 16);
-        const bool valid = row < ne;
-        // the inputs of g (epilogue 2), requested now
-        float4 ga[CW / 4];
-        uint4 gd[CW / 8];
-        if (valid) {
-            const float4* dar = reinterpret_cast<const float4*>(A.da + (int64_t)(r0 + seg) * H + c0);
+
+    if (isX) {
+        for (int64_t j = 0; j < n_mine; ++j) {
+            const int st = (int)(j & 1);
+            const uint32_t par = (uint32_t)j & 1u;   // c1, zr and xd complete once per tile
+            const uint8_t* rec = rec_of(j);
+            const int4 hd = ld_nc_v4s32(rec);
+            const int32_t* rp = reinterpret_cast<const int32_t*>(rec + 16);
+            // epilogue 1: dz_0 into the dz_1 slot of the stage, column sums for db_0
+            ok = ce0_group_and(leader ? mbar_wait(c1, par) : true, true);
+            if (!ok) break;
+            tc_fence_after();
+            uint8_t* z = sDz(st);
+            const uint8_t* hT = z + kTile;
 #pragma unroll
-            for (int i = 0; i < CW / 4; ++i) ga[i] = __ldg(dar + i);
-            if (A.de_out) {
-                const uint4* dp = reinterpret_cast<const uint4*>(A.de_out + ((int64_t)e0 + row) * H + c0);
+            for (int jj = 0; jj < NCH; ++jj) {
+                float dh[16], hv[16];
+                tmem_ld16(tD1 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+                ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
+                ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
+                tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < CW / 8; ++i) gd[i] = __ldg(dp + i);
-            } else {
-#pragma unroll
-                for (int i = 0; i < CW / 8; ++i) gd[i] = make_uint4(0u, 0u, 0u, 0u);
+                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
+                st_tile8(z, row, c0 + 16 * jj, 128, S, dh);
+                st_tile8(z, row, c0 + 16 * jj + 8, 128, S, dh + 8);
+                acc[jj] += warp_colsum16(dh, lane);
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < CW / 4; ++i) ga[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < CW / 8; ++i) gd[i] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        // epilogue 1: dz_0 into the dz_1 slot of the stage, column sums for db_0 (thread 0
-        // waits for pair 1, the block for thread 0)
-        ok = block_wait(c1, par, tid);
-        if (!ok) break;
-        tc_fence_after();
-        uint8_t* z = sDz(st);
-        uint8_t* hT = sDz(st) + kTile;
-#pragma unroll
-        for (int jj = 0; jj < NCH; ++jj) {
-            float dh[16], hv[16];
-            tmem_ld16(tD1 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
-            ld_tile8(hT, row, c0 + 16 * jj, 128, S, hv);
-            ld_tile8(hT, row, c0 + 16 * jj + 8, 128, S, hv + 8);
-            tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
-            st_tile8(z, row, c0 + 16 * jj, 128, S, dh);
-            st_tile8(z, row, c0 + 16 * jj + 8, 128, S, dh + 8);
-            acc1[jj] += warp_colsum16(dh, lane);
-        }
-        tc_fence_before();
-        fence_proxy_async();
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
-        if (!ok) break;
-        if (tid == 0) {   // pair 2 on dz_0; then the next tile's pair 1 (D1 has been read)
-            ok0 = mbar_wait(fullB, par);
-            if (ok0) {
-                tc_fence_after();
-                issue_dgrad(tD2, z, S, sWb, S, H, (uint32_t)H * S, H, H);
-                mma_commit(c2d);
-                issue_wgrad(tWb, z, S, 128u * S, sE, S, 128u * S, H, n2 > 0);
-                mma_commit(c2w);
-                ++n2;
+            tc_fence_before();
+            fence_proxy_async();
+            ce0_group_and(true, true);
+            if (leader) {   // dz_0 is in place for pair 2; then the next tile's pair 1 (D1 has been read)
+                mbar_arrive(zr);
                 if (j + 1 < n_mine) issue_pair1();
             }
-        }
-        if (j + 1 < n_mine) read_rec(j + 1);
-        // dz_0 per edge, for the sender-side sums of the projection adjoint (whole rows per warp)
-        for (int i = tid; i < ne * CPR; i += NT) {
-            const int rr = i / CPR, jj = i - rr * CPR;
-            *reinterpret_cast<uint4*>(A.dz1 + ((int64_t)e0 + rr) * H + 8 * jj) =
-                *reinterpret_cast<const uint4*>(z + tile_off(rr, 8 * jj, 128, S));
-        }
-        // receiver-side sums of dz_0 over each receiver's edges (dP, fixed edge order)
-        for (int it = tid; it < (r1 - r0) * CPR; it += NT) {
-            const int rr = it / CPR, c = (it % CPR) * 8;
-            const int32_t ea = it < NT ? ra0 : __ldg(rp + rr), eb = it < NT ? rb0 : __ldg(rp + rr + 1);
-            float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int32_t e = ea; e < eb; ++e) {
-                float z8[8];
-                ld_tile8(z, e, c, 128, S, z8);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) s8[k] += z8[k];
+            // dz_0 per edge, for the sender-side sums of the projection adjoint (whole rows per warp)
+            const int32_t r0 = hd.x, nr = hd.y - hd.x, e0 = hd.z, ne = hd.w;
+            for (int i = gt; i < ne * CPR; i += GT) {
+                const int rr = i / CPR, jj = i - rr * CPR;
+                *reinterpret_cast<uint4*>(A.dz1 + ((int64_t)e0 + rr) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(z + tile_off(rr, 8 * jj, 128, S));
             }
-            float4* dp = reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + c);
-            dp[0] = make_float4(s8[0], s8[1], s8[2], s8[3]);
-            dp[1] = make_float4(s8[4], s8[5], s8[6], s8[7]);
+            // receiver-side sums of dz_0 over each receiver's edges (dP, fixed edge order)
+            for (int it = gt; it < nr * CPR; it += GT) {
+                const int rr = it / CPR, c = (it % CPR) * 8;
+                const int32_t ea = __ldg(rp + rr), eb = __ldg(rp + rr + 1);
+                float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int32_t e = ea; e < eb; ++e) {
+                    float z8[8];
+                    ld_tile8(z, e, c, 128, S, z8);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) s8[k] += z8[k];
+                }
+                float4* dp = reinterpret_cast<float4*>(A.dP + (int64_t)(r0 + rr) * H + c);
+                dp[0] = make_float4(s8[0], s8[1], s8[2], s8[3]);
+                dp[1] = make_float4(s8[4], s8[5], s8[6], s8[7]);
+            }
+            ok = ce0_group_and(!leader || ok0, true);   // every X thread is past its reads of the stage
+            if (!ok) break;
+            if (leader) mbar_arrive(xd);
         }
-        // epilogue 2: de_in = g + D2, staged in the stage's h_0 slot (pair 1 and epilogue 1
-        // have read it)
-        ok = block_wait(c2d, par, tid);
-        if (!ok) break;
-        tc_fence_after();
-        {
-            float gv[CW], dh[CW];
-#pragma unroll
-            for (int i = 0; i < CW / 8; ++i) {
-                const uint32_t dw[4] = {gd[i].x, gd[i].y, gd[i].z, gd[i].w};
-                const float4 u0 = ga[2 * i], u1 = ga[2 * i + 1];
-                const float av[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float d0, d1;
-                    unpack_bf16x2(dw[k], d0, d1);
-                    gv[8 * i + 2 * k] = edge_g(w, av[2 * k], d0);
-                    gv[8 * i + 2 * k + 1] = edge_g(w, av[2 * k + 1], d1);
+        if (leader) *sN1 = n1;
+    } else {
+        for (int64_t j = 0; j < n_mine; ++j) {
+            const int st = (int)(j & 1);
+            const uint32_t par = (uint32_t)j & 1u;   // fullB, c2d, c2w complete once per tile
+            const uint8_t* rec = rec_of(j);
+            const int4 hd = ld_nc_v4s32(rec);
+            const int seg = __ldg(reinterpret_cast<const int16_t*>(rec + 544) + row);
+            const float w = __ldg(reinterpret_cast<const float*>(rec + 1312) + row);
+            const int32_t e0 = hd.z, ne = hd.w;
+            const bool valid = row < ne;
+            if (leader) {   // pair 2 once group X has written dz_0 and the e rows have landed
+                ok0 = ok0 && mbar_wait(zr, par) && mbar_wait(fullB, par);
+                if (ok0) {
+                    tc_fence_after();
+                    uint8_t* z = sDz(st);
+                    issue_dgrad(tD2, z, S, sWb, S, H, (uint32_t)H * S, H, H);
+                    mma_commit(c2d);
+                    issue_wgrad(tWb, z, S, 128u * S, sE, S, 128u * S, H, n2 > 0);
+                    mma_commit(c2w);
+                    ++n2;
                 }
             }
+            // the inputs of g, 16 columns at a time, one chunk ahead
+            const float4* dar = reinterpret_cast<const float4*>(A.da + (int64_t)(hd.x + (valid ? seg : 0)) * H + c0);
+            const bool has_de = valid && A.de_out;
+            const uint4* der = has_de ? reinterpret_cast<const uint4*>(A.de_out + ((int64_t)e0 + row) * H + c0) : nullptr;
+            float4 ga[2][4];
+            uint4 gd[2][2];
+            auto load_chunk = [&](int jj, int b) {
 #pragma unroll
-            for (int jj = 0; jj < NCH; ++jj) accb[jj] += warp_colsum16(gv + 16 * jj, lane);
-            tmem_ld16(tD2 + lane_base + (uint32_t)c0, dh);
-            tmem_ld16(tD2 + lane_base + (uint32_t)(c0 + 16), dh + 16);
-            tmem_ld_wait();
+                for (int i = 0; i < 4; ++i) ga[b][i] = valid ? __ldg(dar + 4 * jj + i) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < CW; ++i) dh[i] = __fadd_rn(gv[i], dh[i]);
-            st_row_tile<CW>(hT, row, c0, S, dh);
+                for (int i = 0; i < 2; ++i) gd[b][i] = has_de ? __ldg(der + 2 * jj + i) : make_uint4(0u, 0u, 0u, 0u);
+            };
+            load_chunk(0, 0);
+            ok = ce0_group_and(leader ? (ok0 && mbar_wait(c2d, par)) : true, false);
+            if (!ok) break;
+            tc_fence_after();
+            // epilogue 2: de_in = g + D2, staged in the stage's h_0 slot (pair 1 and epilogue 1 have read it)
+            uint8_t* hT = sDz(st) + kTile;
+#pragma unroll
+            for (int jj = 0; jj < NCH; ++jj) {
+                if (jj + 1 < NCH) load_chunk(jj + 1, (jj + 1) & 1);
+                const int b = jj & 1;
+                float gv[16], dh[16];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const uint32_t dw[4] = {gd[b][i].x, gd[b][i].y, gd[b][i].z, gd[b][i].w};
+                    const float4 u0 = ga[b][2 * i], u1 = ga[b][2 * i + 1];
+                    const float av[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float d0, d1;
+                        unpack_bf16x2(dw[k], d0, d1);
+                        gv[8 * i + 2 * k] = edge_g(w, av[2 * k], d0);
+                        gv[8 * i + 2 * k + 1] = edge_g(w, av[2 * k + 1], d1);
+                    }
+                }
+                acc[jj] += warp_colsum16(gv, lane);
+                tmem_ld16(tD2 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) dh[i] = __fadd_rn(gv[i], dh[i]);
+                st_tile8(hT, row, c0 + 16 * jj, 128, S, dh);
+                st_tile8(hT, row, c0 + 16 * jj + 8, 128, S, dh + 8);
+            }
+            tc_fence_before();
+            ce0_group_and(true, false);   // D2 read, de_in staged
+            if (leader) {   // pair 2's wgrad has read dz_0 and e: the next tile's e rows
+                ok0 = ok0 && mbar_wait(c2w, par);
+                if (ok0 && nB < n_mine) issue_B();
+            }
+            for (int i = gt; i < ne * CPR; i += GT) {
+                const int rr = i / CPR, jj = i - rr * CPR;
+                *reinterpret_cast<uint4*>(A.de_in + ((int64_t)e0 + rr) * H + 8 * jj) =
+                    *reinterpret_cast<const uint4*>(hT + tile_off(rr, 8 * jj, 128, S));
+            }
+            fence_proxy_async();   // generic accesses of the stage precede its TMA refill
+            ok = ce0_group_and(!leader || ok0, false);   // every Y thread is past its accesses of the stage
+            if (!ok) break;
+            if (leader && nA < n_mine) {   // tile j + 2 into stage st once group X has read it
+                ok0 = mbar_wait(xd, par);
+                if (ok0) issue_A();
+            }
         }
-        tc_fence_before();
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 read, de_in staged
-        if (!ok) break;
-        if (tid == 0) {   // pair 2's wgrad has read dz_0 and e: the next tile's e rows
-            ok0 = mbar_wait(c2w, par);
-            if (ok0 && nB < n_mine) issue_B();
-        }
-        for (int i = tid; i < ne * CPR; i += NT) {
-            const int rr = i / CPR, jj = i - rr * CPR;
-            *reinterpret_cast<uint4*>(A.de_in + ((int64_t)e0 + rr) * H + 8 * jj) =
-                *reinterpret_cast<const uint4*>(hT + tile_off(rr, 8 * jj, 128, S));
-        }
-        fence_proxy_async();   // generic accesses of the stage precede its TMA refill
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // every thread is past its reads of stage st
-        if (!ok) break;
-        if (tid == 0 && nA < n_mine) issue_A();   // tile j + 2 into stage st
     }
-    if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
-        if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
+    __syncwarp();
+    __syncthreads();
+    if (tid == 256) {   // bounded waits for what this CTA started and nobody waited for
+        const int64_t m1 = *sN1;
+        if (m1 > 0) mbar_wait(c1, (uint32_t)(m1 - 1) & 1u);
         if (n2 > 0) {
             mbar_wait(c2d, (uint32_t)(n2 - 1) & 1u);
             mbar_wait(c2w, (uint32_t)(n2 - 1) & 1u);
         }
-        for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
+        for (int64_t i = m1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
         for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
     }
-    __syncwarp();   // reconverged before the aligned block barrier
-    ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+    __syncwarp();
+    const bool all_ok = __syncthreads_and(ok && (!leader || ok0)) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
-    if (ok) {
+    if (all_ok) {
         if (n_mine > 0) {
-            flush_acc<CG>(tWa, H, H, q, lane, g, part);
-            flush_acc<CG>(tWb, H, H, q, lane, g, part + H * H);
+            flush_acc<CG>(tWa, H, H, q, lane, warp >> 2, part);
+            flush_acc<CG>(tWb, H, H, q, lane, warp >> 2, part + H * H);
         } else {
             for (int i = tid; i < 2 * H * H; i += NT) part[i] = 0.f;
         }
     }
-    colsum_store<H, NCH>(acc1, sRed, q, lane, c0, tid, NT, part + 2 * H * H);
-    colsum_store<H, NCH>(accb, sRed, q, lane, c0, tid, NT, part + 2 * H * H + H);
+    // column sums: warp (q, half) of a group holds columns c0 + 16 j + (lane >> 1) over its 32 rows;
+    // the four row quarters are added in order, db_0 from group X, dbeta from group Y
+    __syncthreads();
+    if ((lane & 1) == 0) {
+#pragma unroll
+        for (int jj = 0; jj < NCH; ++jj) sRed[(isX ? 0 : 4 * H) + q * H + c0 + 16 * jj + (lane >> 1)] = acc[jj];
+    }
+    __syncthreads();
+    for (int c = tid; c < 2 * H; c += NT) {
+        const float* r = sRed + (c < H ? 0 : 4 * H) + (c % H);
+        part[2 * H * H + c] = ((r[0] + r[H]) + r[2 * H]) + r[3 * H];
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -223,14 +223,20 @@ __global__ void __launch_bounds__(kChainNT, 1) k_bwd_chain(const __grid_constant
 // dW_k += dz_k^T h_{k-1}), epilogue 1 (dz_{k-1} = D1 ELU'(h_{k-1}) as BF16 into
 // the shared-memory slot dz_k came in, which pair 1 has finished reading, and
 // its column sums), MMA pair 2 (D2 = dz_{k-1} W_{k-1}, dW_{k-1} += dz_{k-1}^T
-// h_{k-2}), epilogue 2 (dz_{k-2} = D2 ELU'(h_{k-2}) to HBM, its column sums).
+// h_{k-2}), epilogue 2 (dz_{k-2} = D2 ELU'(h_{k-2}), its column sums, staged in
+// the stage's h_{k-1} slot and written to HBM as whole rows by a TMA store).
 // The operands and roundings are those of two k_bwd_chain passes, so the
 // results are the same bit for bit. TMEM: D1, D2, dW_k, dW_{k-1} (128 columns
-// each). Two stages of {dz_k, h_{k-1}} rows keep the next tile's load in flight;
-// h_{k-2} has one stage, reloaded as soon as epilogue 2 has read it into
-// registers and pair 2's weight-gradient MMA has read it; thread 0 issues tile
-// j+1's pair 1 right after tile j's pair 2. Pair 2 commits twice, so that
-// epilogue 2 starts once its dgrad is done, while the wgrad still runs.
+// each). Two stages of {dz_k, h_{k-1}} rows; h_{k-2} has one stage, reloaded as
+// soon as epilogue 2 has read it into registers and pair 2's weight gradient
+// has read it.
+// The two epilogues run on two warp groups, so that epilogue 2 of tile j runs
+// beside epilogue 1 of tile j + 1: group X (warps 0-7) waits for pair 1, writes
+// dz_{k-1}, tells group Y's leader through an mbarrier (zr) that the stage is
+// ready for pair 2 and no longer read by X, and issues the next tile's pair 1;
+// group Y (warps 8-15) issues pair 2, runs epilogue 2, reloads h_{k-2} and,
+// after the TMA store of dz_{k-2}, the stage. Each warp covers 64 columns of
+// its 32 rows (TMEM lane quarter).
 
 struct Chain2Args {
     const float* Wa;             // W_k [H x H] (FP32)
@@ -245,19 +251,22 @@ struct Chain2Args {
 constexpr int kC2NT = 512;
 struct Chain2Smem {
     static constexpr uint32_t wa = 0, wb = kTile;
-    static constexpr uint32_t a = 2 * kTile;          // stage s: dz_k (then dz_{k-1}), h_{k-1}, at a + s * 2 * kTile
+    static constexpr uint32_t a = 2 * kTile;          // stage s: dz_k (then dz_{k-1}), h_{k-1} (then dz_{k-2}), at a + s * 2 * kTile
     static constexpr uint32_t b = a + 4 * kTile;      // h_{k-2}
-    static constexpr uint32_t red = a;                // 4 x H floats, after the tile loop
-    static constexpr uint32_t bar = b + kTile;        // fullA[2], fullB, c1, c2d, c2w, TMEM slot
-    static constexpr uint32_t total = bar + 64 + 1024;
+    static constexpr uint32_t red = a;                // 8 x H floats, after the tile loop
+    static constexpr uint32_t bar = b + kTile;        // fullA[2], fullB, c1, c2d, c2w, zr[2], hbf, n1, TMEM slot
+    static constexpr uint32_t total = bar + 128 + 1024;
 };
 static_assert(Chain2Smem::total <= 227 * 1024, "k_bwd_chain2 shared memory");
+
+// One warp group's named barrier (X: 1, Y: 2; 256 threads), AND-ing a predicate.
+__device__ __forceinline__ bool wg_and(bool v, bool isX) { return named_and(v, isX ? 1 : 2, 256); }
 
 __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__ CUtensorMap tm_dz,
                                                          const __grid_constant__ CUtensorMap tm_ha,
                                                          const __grid_constant__ CUtensorMap tm_hb,
                                                          const __grid_constant__ CUtensorMap tm_out, Chain2Args A) {
-    constexpr int H = H128, S = kS, CG = 4, CW = 32, NT = kC2NT, NCH = CW / 16;
+    constexpr int H = H128, S = kS, CG = 4, CW = 64, NT = kC2NT, NCH = CW / 16, GT = 256;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = aligned_smem(smem_raw);
     uint8_t* sWa = sm + Chain2Smem::wa;
@@ -269,17 +278,23 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
     uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
     uint64_t* c2d = fullA + 4;     // pair 2's dgrad complete
     uint64_t* c2w = fullA + 5;     // pair 2's wgrad complete
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 6);
+    uint64_t* zr = fullA + 6;      // zr[j % 2]: group X has written tile j's dz_{k-1} and is done with its stage
+    uint64_t* hbf = fullA + 8;     // every group-Y thread has read the tile's h_{k-2} (256 arrivals)
+    int64_t* sN1 = reinterpret_cast<int64_t*>(fullA + 9);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 10);
     auto sDz = [&](int st) { return sm + Chain2Smem::a + st * 2 * kTile; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, g = warp >> 2, row = 32 * q + lane, c0 = g * CW;
+    const bool isX = warp < 8;
+    const int q = warp & 3, row = 32 * q + lane, c0 = 64 * ((warp >> 2) & 1), gt = tid & (GT - 1);
+    const bool leader = gt == 0;   // X: thread 0, Y: thread 256
     if (warp == 0) {
         tmem_alloc(tslot, 4 * H);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 6; ++i) mbar_init(fullA + i, 1);
+        for (int i = 0; i < 8; ++i) mbar_init(fullA + i, 1);
+        mbar_init(hbf, GT);
         fence_mbar_init();
     }
     load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
@@ -293,7 +308,7 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
     const int64_t n_mine = A.n_tiles > (int64_t)blockIdx.x
                                ? (A.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
     auto tile_of = [&](int64_t j) { return (int64_t)blockIdx.x + j * gridDim.x; };
-    // thread 0 only: loads and MMA pairs issued so far, and whether it is still well
+    // leaders only: X issues pair 1 (n1); Y issues the loads (nA, nB), pair 2 (n2) and the stores
     int64_t nA = 0, nB = 0, n1 = 0, n2 = 0;
     bool ok0 = true;
     auto issue_A = [&]() {   // dz_k and h_{k-1} rows of tile nA into stage nA % 2 (and its h_{k-2} into L2)
@@ -323,25 +338,26 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
         mma_commit(c1);
         ++n1;
     };
-    if (tid == 0 && n_mine > 0) {
+    if (tid == 256 && n_mine > 0) {
         while (nA < n_mine && nA < 2) issue_A();
         issue_B();
-        issue_pair1();
     }
-    float acc1[NCH], acc2[NCH];
+    if (tid == 0 && n_mine > 0) issue_pair1();
+    float acc[NCH];   // X: column sums of dz_{k-1} (db_{k-1}); Y: of dz_{k-2} (db_{k-2})
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) acc1[j] = acc2[j] = 0.f;
+    for (int j = 0; j < NCH; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int64_t j = 0; j < n_mine; ++j) {
-        const int st = (int)(j & 1);
-        const uint32_t par = (uint32_t)j & 1u;   // c1, c2 and fullB complete once per tile
-        // epilogue 1: dz_{k-1} into the dz_k slot of the stage, column sums for db_{k-1}
-        ok = ok && mbar_wait(c1, par);
-        __syncwarp();
-        tc_fence_after();
-        {
+
+    if (isX) {
+        for (int64_t j = 0; j < n_mine; ++j) {
+            const int st = (int)(j & 1);
+            const uint32_t par = (uint32_t)j & 1u;   // c1 completes once per tile
+            // epilogue 1: dz_{k-1} into the dz_k slot of the stage, column sums for db_{k-1}
+            ok = wg_and(leader ? mbar_wait(c1, par) : true, true);
+            if (!ok) break;
+            tc_fence_after();
             uint8_t* z = sDz(st);
-            const uint8_t* hT = sDz(st) + kTile;
+            const uint8_t* hT = z + kTile;
 #pragma unroll
             for (int jj = 0; jj < NCH; ++jj) {
                 float dh[16], hv[16];
@@ -353,95 +369,127 @@ __global__ void __launch_bounds__(kC2NT, 1) k_bwd_chain2(const __grid_constant__
                 for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
                 st_tile8(z, row, c0 + 16 * jj, 128, S, dh);
                 st_tile8(z, row, c0 + 16 * jj + 8, 128, S, dh + 8);
-                acc1[jj] += warp_colsum16(dh, lane);
+                acc[jj] += warp_colsum16(dh, lane);
             }
-        }
-        tc_fence_before();
-        fence_proxy_async();
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
-        if (!ok) break;
-        if (tid == 0) {   // pair 2 on dz_{k-1}; then the next tile's pair 1 (D1 has been read)
-            ok0 = mbar_wait(fullB, par);
-            if (ok0) {
-                tc_fence_after();
-                issue_dgrad(tD2, sDz(st), S, sWb, S, H, (uint32_t)H * S, H, H);
-                mma_commit(c2d);
-                issue_wgrad(tWb, sDz(st), S, 128u * S, sHb, S, 128u * S, H, n2 > 0);
-                mma_commit(c2w);
-                ++n2;
+            tc_fence_before();
+            fence_proxy_async();
+            ok = wg_and(!leader || ok0, true);   // every X thread is done with the stage
+            if (!ok) break;
+            if (leader) {   // dz_{k-1} is in place for pair 2; then the next tile's pair 1 (D1 has been read)
+                mbar_arrive(zr + st);
                 if (j + 1 < n_mine) issue_pair1();
             }
         }
-        // epilogue 2: dz_{k-2} to HBM, column sums for db_{k-2}
-        ok = ok && mbar_wait(c2d, par);
-        __syncwarp();
-        tc_fence_after();
-        float hb[CW];   // this thread's h_{k-2}, read before the stage is reloaded
+        if (leader) *sN1 = n1;
+    } else {
+        for (int64_t j = 0; j < n_mine; ++j) {
+            const int st = (int)(j & 1);
+            const uint32_t par = (uint32_t)j & 1u;   // fullB, c2d, c2w complete once per tile
+            if (leader) {   // pair 2 once group X has written dz_{k-1} and h_{k-2} has landed (zr alternates
+                            // between two barriers, so group X, at most two tiles ahead, cannot alias a phase)
+                ok0 = ok0 && mbar_wait(zr + st, (uint32_t)(j >> 1) & 1u) && mbar_wait(fullB, par);
+                if (ok0) {
+                    tc_fence_after();
+                    uint8_t* z = sDz(st);
+                    issue_dgrad(tD2, z, S, sWb, S, H, (uint32_t)H * S, H, H);
+                    mma_commit(c2d);
+                    issue_wgrad(tWb, z, S, 128u * S, sHb, S, 128u * S, H, n2 > 0);
+                    mma_commit(c2w);
+                    ++n2;
+                }
+            }
+            ok = wg_and(leader ? (ok0 && mbar_wait(c2d, par)) : true, false);
+            if (!ok) break;
+            tc_fence_after();
+            // this thread's h_{k-2} (64 columns, BF16 pairs), read before h_{k-2} is reloaded. The
+            // reads are released through an mbarrier that the leader acquires before the TMA
+            // reload: a block barrier does not order loads still in flight against the async
+            // proxy's writes (measured: with one, some rows took the next tile's h_{k-2})
+            uint4 hbw[CW / 8];
 #pragma unroll
-        for (int i = 0; i < CW; i += 8) ld_tile8(sHb, row, c0 + i, 128, S, hb + i);
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
-        if (!ok) break;
-        if (tid == 0) {   // the wgrad of pair 2 has read h_{k-2} and dz_{k-1}, so has every thread
-            ok0 = mbar_wait(c2w, par);
-            if (ok0 && nB < n_mine) issue_B();
-        }
-        __syncwarp();   // warp 0 reconverged before the aligned TMEM loads
-        {   // dz_{k-2} staged in the stage's h_{k-1} slot (pair 1 and epilogue 1 have read it)
+            for (int i = 0; i < CW / 8; ++i)
+                hbw[i] = *reinterpret_cast<const uint4*>(sHb + tile_off(row, c0 + 8 * i, 128, S));
+            fence_proxy_async();
+            mbar_arrive(hbf);
+            if (leader) {   // every Y thread has read h_{k-2} and the wgrad of pair 2 has too: the next tile's
+                ok0 = ok0 && mbar_wait(hbf, par) && mbar_wait(c2w, par);
+                if (ok0 && nB < n_mine) issue_B();
+            }
+            __syncwarp();   // the leader's warp reconverged before the aligned TMEM loads
+            // epilogue 2: dz_{k-2} staged in the stage's h_{k-1} slot (pair 1 and group X have read it)
             uint8_t* zt = sDz(st) + kTile;
 #pragma unroll
             for (int jj = 0; jj < NCH; ++jj) {
-                float dh[16];
+                float dh[16], hv[16];
                 tmem_ld16(tD2 + lane_base + (uint32_t)(c0 + 16 * jj), dh);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const uint4 u = hbw[2 * jj + i];
+                    unpack_bf16x2(u.x, hv[8 * i], hv[8 * i + 1]);
+                    unpack_bf16x2(u.y, hv[8 * i + 2], hv[8 * i + 3]);
+                    unpack_bf16x2(u.z, hv[8 * i + 4], hv[8 * i + 5]);
+                    unpack_bf16x2(u.w, hv[8 * i + 6], hv[8 * i + 7]);
+                }
                 tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hb[16 * jj + i]);
+                for (int i = 0; i < 16; ++i) dh[i] = elu1_bwd_from_out(dh[i], hv[i]);
                 st_tile8(zt, row, c0 + 16 * jj, 128, S, dh);
                 st_tile8(zt, row, c0 + 16 * jj + 8, 128, S, dh + 8);
-                acc2[jj] += warp_colsum16(dh, lane);
+                acc[jj] += warp_colsum16(dh, lane);
             }
-        }
-        tc_fence_before();
-        fence_proxy_async();   // the staged rows precede their TMA store and the stage's refill
-        __syncwarp();   // reconverged before the aligned block barrier
-        ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;   // D2 is read; stage st is free (c2w)
-        if (!ok) break;
-        if (tid == 0) {   // dz_{k-2} leaves as whole rows; tile j + 2 into stage st once the store has read it
+            tc_fence_before();
+            fence_proxy_async();   // the staged rows precede their TMA store and the stage's refill
+            ok = wg_and(!leader || ok0, false);   // D2 read, dz_{k-2} staged
+            if (!ok) break;
+            if (leader) {   // dz_{k-2} leaves as whole rows; tile j + 2 into stage st once the store has read it
 #pragma unroll
-            for (int kb = 0; kb < 2; ++kb)
-                tma_store_2d(&tm_out, kb * 64, (int32_t)(tile_of(j) * 128), sDz(st) + kTile + kb * 128 * S);
-            bulk_commit();
-            if (nA < n_mine) {
-                bulk_wait_read_all();
-                issue_A();
+                for (int kb = 0; kb < 2; ++kb)
+                    tma_store_2d(&tm_out, kb * 64, (int32_t)(tile_of(j) * 128), zt + kb * 128 * S);
+                bulk_commit();
+                if (nA < n_mine) {
+                    bulk_wait_read_all();
+                    issue_A();
+                }
             }
         }
     }
-    if (tid == 0) {   // bounded waits for what this CTA started and nobody waited for
-        if (n1 > 0) mbar_wait(c1, (uint32_t)(n1 - 1) & 1u);
+    __syncwarp();
+    __syncthreads();
+    if (tid == 256) {   // bounded waits for what this CTA started and nobody waited for
+        const int64_t m1 = *sN1;
+        if (m1 > 0) mbar_wait(c1, (uint32_t)(m1 - 1) & 1u);
         if (n2 > 0) {
             mbar_wait(c2d, (uint32_t)(n2 - 1) & 1u);
             mbar_wait(c2w, (uint32_t)(n2 - 1) & 1u);
         }
-        for (int64_t i = n1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
+        for (int64_t i = m1; i < nA; ++i) mbar_wait(fullA + (i & 1), (uint32_t)(i >> 1) & 1u);
         for (int64_t i = n2; i < nB; ++i) mbar_wait(fullB, (uint32_t)i & 1u);
+        bulk_wait_all();   // the stored dz rows are written
     }
-    if (tid == 0) bulk_wait_all();   // the stored dz rows are written, the stages free
-    __syncwarp();   // reconverged before the aligned block barrier
-    ok = __syncthreads_and(ok && (tid != 0 || ok0)) != 0;
+    __syncwarp();
+    const bool all_ok = __syncthreads_and(ok && (!leader || ok0)) != 0;
     tc_fence_after();
     float* part = A.part + (int64_t)blockIdx.x * A.pstride;
-    if (ok) {
+    if (all_ok) {
         if (n_mine > 0) {
-            flush_acc<CG>(tWa, H, H, q, lane, g, part);
-            flush_acc<CG>(tWb, H, H, q, lane, g, part + H * H);
+            flush_acc<CG>(tWa, H, H, q, lane, warp >> 2, part);
+            flush_acc<CG>(tWb, H, H, q, lane, warp >> 2, part + H * H);
         } else {
             for (int i = tid; i < 2 * H * H; i += NT) part[i] = 0.f;
         }
     }
-    colsum_store<H, NCH>(acc1, sRed, q, lane, c0, tid, NT, part + 2 * H * H);
-    colsum_store<H, NCH>(acc2, sRed, q, lane, c0, tid, NT, part + 2 * H * H + H);
+    // column sums: warp (q, half) of a group holds columns c0 + 16 j + (lane >> 1) over its 32 rows;
+    // the four row quarters are added in order, db_{k-1} from group X, db_{k-2} from group Y
+    __syncthreads();
+    if ((lane & 1) == 0) {
+#pragma unroll
+        for (int jj = 0; jj < NCH; ++jj) sRed[(isX ? 0 : 4 * H) + q * H + c0 + 16 * jj + (lane >> 1)] = acc[jj];
+    }
+    __syncthreads();
+    for (int c = tid; c < 2 * H; c += NT) {
+        const float* r = sRed + (c < H ? 0 : 4 * H) + (c % H);
+        part[2 * H * H + c] = ((r[0] + r[H]) + r[2 * H]) + r[3 * H];
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -710,17 +758,10 @@ struct ChainE0Smem {
     static constexpr uint32_t a = 2 * kTile;          // stage s: dz_1 (then dz_0), h_0 (then de_in), at a + s * 2 * kTile
     static constexpr uint32_t e = a + 4 * kTile;      // e rows
     static constexpr uint32_t red = a;                // 8 x H floats, after the tile loop
-    static constexpr uint32_t bar = e + kTile;        // fullA[2], fullB, c1, c2d, c2w, zr, xd, n1, TMEM slot
+    static constexpr uint32_t bar = e + kTile;        // fullA[2], fullB, c1, c2d, c2w, zr[2], xd, n1, TMEM slot
     static constexpr uint32_t total = bar + 128 + 1024;
 };
 static_assert(ChainE0Smem::total <= 227 * 1024, "k_bwd_chain_edge0 shared memory");
-
-// One warp group's named barrier (X: 1, Y: 2; 256 threads), AND-ing a predicate;
-// the warp is reconverged first (the barrier is an aligned one).
-__device__ __forceinline__ bool ce0_group_and(bool v, bool isX) {
-    __syncwarp();
-    return named_and(v, isX ? 1 : 2, 256);
-}
 
 __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_constant__ CUtensorMap tm_dz,
                                                               const __grid_constant__ CUtensorMap tm_h,
@@ -738,10 +779,10 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
     uint64_t* c1 = fullA + 3;      // MMA pair 1 complete
     uint64_t* c2d = fullA + 4;     // pair 2's dgrad complete
     uint64_t* c2w = fullA + 5;     // pair 2's wgrad complete
-    uint64_t* zr = fullA + 6;      // group X has written the tile's dz_0
-    uint64_t* xd = fullA + 7;      // group X has read the tile's stage
-    int64_t* sN1 = reinterpret_cast<int64_t*>(fullA + 8);   // pair 1 issues (for the final waits)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 9);
+    uint64_t* zr = fullA + 6;      // zr[j % 2]: group X has written tile j's dz_0
+    uint64_t* xd = fullA + 8;      // group X has read the tile's stage
+    int64_t* sN1 = reinterpret_cast<int64_t*>(fullA + 9);   // pair 1 issues (for the final waits)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fullA + 10);
     auto sDz = [&](int st) { return sm + ChainE0Smem::a + st * 2 * kTile; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -753,7 +794,7 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 8; ++i) mbar_init(fullA + i, 1);
+        for (int i = 0; i < 9; ++i) mbar_init(fullA + i, 1);
         fence_mbar_init();
     }
     load_weight(sWa, A.Wa, H, 0, H, H, tid, NT);
@@ -815,12 +856,12 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
     if (isX) {
         for (int64_t j = 0; j < n_mine; ++j) {
             const int st = (int)(j & 1);
-            const uint32_t par = (uint32_t)j & 1u;   // c1, zr and xd complete once per tile
+            const uint32_t par = (uint32_t)j & 1u;   // c1 and xd complete once per tile
             const uint8_t* rec = rec_of(j);
             const int4 hd = ld_nc_v4s32(rec);
             const int32_t* rp = reinterpret_cast<const int32_t*>(rec + 16);
             // epilogue 1: dz_0 into the dz_1 slot of the stage, column sums for db_0
-            ok = ce0_group_and(leader ? mbar_wait(c1, par) : true, true);
+            ok = wg_and(leader ? mbar_wait(c1, par) : true, true);
             if (!ok) break;
             tc_fence_after();
             uint8_t* z = sDz(st);
@@ -840,9 +881,9 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
             }
             tc_fence_before();
             fence_proxy_async();
-            ce0_group_and(true, true);
+            wg_and(true, true);
             if (leader) {   // dz_0 is in place for pair 2; then the next tile's pair 1 (D1 has been read)
-                mbar_arrive(zr);
+                mbar_arrive(zr + st);
                 if (j + 1 < n_mine) issue_pair1();
             }
             // dz_0 per edge, for the sender-side sums of the projection adjoint (whole rows per warp)
@@ -867,7 +908,7 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
                 dp[0] = make_float4(s8[0], s8[1], s8[2], s8[3]);
                 dp[1] = make_float4(s8[4], s8[5], s8[6], s8[7]);
             }
-            ok = ce0_group_and(!leader || ok0, true);   // every X thread is past its reads of the stage
+            ok = wg_and(!leader || ok0, true);   // every X thread is past its reads of the stage
             if (!ok) break;
             if (leader) mbar_arrive(xd);
         }
@@ -882,8 +923,9 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
             const float w = __ldg(reinterpret_cast<const float*>(rec + 1312) + row);
             const int32_t e0 = hd.z, ne = hd.w;
             const bool valid = row < ne;
-            if (leader) {   // pair 2 once group X has written dz_0 and the e rows have landed
-                ok0 = ok0 && mbar_wait(zr, par) && mbar_wait(fullB, par);
+            if (leader) {   // pair 2 once group X has written dz_0 and the e rows have landed (zr alternates
+                            // between two barriers, so group X, at most two tiles ahead, cannot alias a phase)
+                ok0 = ok0 && mbar_wait(zr + st, (uint32_t)(j >> 1) & 1u) && mbar_wait(fullB, par);
                 if (ok0) {
                     tc_fence_after();
                     uint8_t* z = sDz(st);
@@ -907,7 +949,7 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
                 for (int i = 0; i < 2; ++i) gd[b][i] = has_de ? __ldg(der + 2 * jj + i) : make_uint4(0u, 0u, 0u, 0u);
             };
             load_chunk(0, 0);
-            ok = ce0_group_and(leader ? (ok0 && mbar_wait(c2d, par)) : true, false);
+            ok = wg_and(leader ? (ok0 && mbar_wait(c2d, par)) : true, false);
             if (!ok) break;
             tc_fence_after();
             // epilogue 2: de_in = g + D2, staged in the stage's h_0 slot (pair 1 and epilogue 1 have read it)
@@ -939,7 +981,7 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
                 st_tile8(hT, row, c0 + 16 * jj + 8, 128, S, dh + 8);
             }
             tc_fence_before();
-            ce0_group_and(true, false);   // D2 read, de_in staged
+            wg_and(true, false);   // D2 read, de_in staged
             if (leader) {   // pair 2's wgrad has read dz_0 and e: the next tile's e rows
                 ok0 = ok0 && mbar_wait(c2w, par);
                 if (ok0 && nB < n_mine) issue_B();
@@ -950,7 +992,7 @@ __global__ void __launch_bounds__(kCE0NT, 1) k_bwd_chain_edge0(const __grid_cons
                     *reinterpret_cast<const uint4*>(hT + tile_off(rr, 8 * jj, 128, S));
             }
             fence_proxy_async();   // generic accesses of the stage precede its TMA refill
-            ok = ce0_group_and(!leader || ok0, false);   // every Y thread is past its accesses of the stage
+            ok = wg_and(!leader || ok0, false);   // every Y thread is past its accesses of the stage
             if (!ok) break;
             if (leader && nA < n_mine) {   // tile j + 2 into stage st once group X has read it
                 ok0 = mbar_wait(xd, par);
@@ -1110,6 +1152,7 @@ __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ 
         first = false;
         // both MMAs are done: the stage takes the next tile while the epilogue runs
         if (tid == 0 && t + gridDim.x < A.t1) issue(t + gridDim.x);
+        __syncwarp();   // warp 0 reconverged before the aligned TMEM loads
         float d[CW];
         ld_acc<CW>(tWork, q, c0, d);   // gradient of a* (first H inputs)
 #pragma unroll
@@ -1122,6 +1165,7 @@ __global__ void __launch_bounds__(kN0NT, 1) k_bwd_node0(const __grid_constant__ 
             for (int b = 0; b < H / 32; ++b) tma_store_2d(&tm_da, 32 * b, (int32_t)(t * 128), sF + b * 128 * 128);
             bulk_commit();
         }
+        __syncwarp();   // warp 0 reconverged before the aligned TMEM loads
         ld_acc<CW>(tWork + H, q, c0, d);   // gradient of x (last H inputs) plus the residual branch
         tc_fence_before();
 #pragma unroll

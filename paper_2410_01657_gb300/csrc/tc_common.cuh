@@ -73,14 +73,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Named barrier over `n` threads (a multiple of 32) of the CTA.
+// Named barrier over `n` threads (a multiple of 32) of the CTA. bar.sync is an
+// aligned barrier: every warp must reach it converged, so the warp is
+// reconverged first (a thread may come from code only it ran: a wait, an issue).
 __device__ __forceinline__ void named_sync(int id, int n) {
+    __syncwarp();
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Named barrier that also ANDs a predicate over the participating threads.
+// Named barrier that also ANDs a predicate over the participating threads
+// (reconverged first, as named_sync).
 __device__ __forceinline__ bool named_and(bool v, int id, int n) {
     uint32_t r;
+    __syncwarp();
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"

@@ -129,17 +129,9 @@ __device__ __forceinline__ void elu_to_tmem(uint32_t taddr, const float* v) {
     tmem_st16u(taddr, hb);
 }
 
-// One group's named barrier (ids 1, 2), optionally AND-ing a predicate. The
-// warp is reconverged first: the barrier is an aligned one, and the group's
-// leader may come from code that only it ran (a wait, an MMA issue).
-__device__ __forceinline__ void group_sync(int gi) {
-    __syncwarp();
-    named_sync(1 + gi, kGT);
-}
-__device__ __forceinline__ bool group_and(bool v, int gi) {
-    __syncwarp();
-    return named_and(v, 1 + gi, kGT);
-}
+// One group's named barrier (ids 1, 2), optionally AND-ing a predicate.
+__device__ __forceinline__ void group_sync(int gi) { named_sync(1 + gi, kGT); }
+__device__ __forceinline__ bool group_and(bool v, int gi) { return named_and(v, 1 + gi, kGT); }
 
 // The group's activation is in TMEM: order the stores before the MMA that reads
 // them, then the leader issues acc = h W^T.

@@ -413,8 +413,11 @@ def test_h128_adjoint_two_linears_per_pass_match_one(n_hidden):
         B.call("gnn_check", None)
         return [dxi, dei] + dparams
 
-    two, one = backward(0), backward(B.GNN_FLAG_ADJ_ONE_LINEAR)
-    for u, v in zip(two, one):
+    # the two-warp-group passes hand tiles between groups through mbarriers: a second run
+    # must give the same bits as the first (a race between the groups would not)
+    two, two_again, one = backward(0), backward(0), backward(B.GNN_FLAG_ADJ_ONE_LINEAR)
+    for u, w, v in zip(two, two_again, one):
+        assert torch.equal(u, w)
         assert torch.equal(u, v)
     ws = gnn.workspace(_ws_chunks(200, n_hidden + 2)(G, cfg, W), DEV)
     two_c, one_c = backward(0, ws), backward(B.GNN_FLAG_ADJ_ONE_LINEAR, ws)

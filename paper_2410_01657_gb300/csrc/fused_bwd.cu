@@ -998,6 +998,7 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
             const int64_t nr = std::min<int64_t>(128, A.n_rows - rn);
             prefetch_l2(A.dP + rn * H, (uint32_t)(nr * H * 4));
             prefetch_l2(A.x + rn * H, (uint32_t)(nr * H * 4));
+            if constexpr (H == 128) prefetch_l2(A.dx_in + rn * H, (uint32_t)(nr * H * 4));   // its update
         }
         const int64_t r = t * 128 + row;
         const bool valid = r < A.n_rows;
@@ -1155,7 +1156,7 @@ __global__ void __launch_bounds__(CfgP<H>::NT, H >= 128 ? 1 : 2) k_proj_bwd(Proj
             for (int i = 0; i < CW / 4; ++i)
                 sD[row * 32 + (((c0 / 4) + i) ^ (row & 7))] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
             __syncthreads();
-#pragma unroll 2
+#pragma unroll 4
             for (int i = 0; i < 8; ++i) {
                 const int rr = 8 * warp + i;
                 const int64_t rg = t * 128 + rr;
@@ -1227,7 +1228,18 @@ __global__ void k_reduce_grads(RedArgs A) {
     const int r = (int)(j / sg.cols), c = (int)(j % sg.cols);
     float acc = 0.f;
     const float* p = A.part + sg.src_off + (int64_t)r * sg.src_ld + c;
-    for (int b = 0; b < A.n_cta; ++b) acc += p[(int64_t)b * A.pstride];
+    // CTA partials in ascending order; the loads of 16 CTAs are requested together
+    // (the sum is one latency-bound pass over a few tens of MB)
+    constexpr int U = 16;
+    int b = 0;
+    for (; b + U <= A.n_cta; b += U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(p + (int64_t)(b + u) * A.pstride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += v[u];
+    }
+    for (; b < A.n_cta; ++b) acc += __ldg(p + (int64_t)b * A.pstride);
     sg.dst[(int64_t)r * sg.dst_ld + c] += acc;
 }
 

@@ -242,8 +242,7 @@ struct Chain2Args {
     const float* Wa;             // W_k [H x H] (FP32)
     const float* Wb;             // W_{k-1}
     const __nv_bfloat16* hb;     // h_{k-2} rows (prefetched into L2 two tiles ahead)
-    __nv_bfloat16* dz_out;       // dz_{k-2} rows (tile-padded)
-    int64_t n_tiles;
+    int64_t n_tiles;             // dz_{k-2} leaves through the tm_out tensor map (tile-padded rows)
     float* part;                 // per-CTA: dW_k, dW_{k-1} [H x H], then db_{k-1}, db_{k-2} [H]
     int64_t pstride;
 };
@@ -1343,7 +1342,6 @@ int chain_backward_h128(const gnn_mlp& W, const gnn_mlp& dW, __nv_bfloat16* hs, 
             A.Wa = W.W[k];
             A.Wb = W.W[k - 1];
             A.hb = hs + (int64_t)(k - 2) * hs_stride;
-            A.dz_out = dzs[*cur ^ 1];
             A.n_tiles = n_tiles;
             A.part = part;
             A.pstride = pstride;

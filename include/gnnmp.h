@@ -288,7 +288,8 @@ typedef struct gnn_mp_params {
 #define GNN_HALO_NONE 1   /* the paper's "None" mode: Eq. 5c-5d skipped (inconsistent)     */
 #define GNN_FLAG_NO_EDGE_OUT 1  /* forward: do not write e_out (last layer in inference)  */
 #define GNN_FLAG_ADJ_ONE_LINEAR 2  /* backward, BF16 at H = 128: one Linear per adjoint pass
-                                     instead of two (same results, bit for bit; for testing) */
+                                     instead of two, and the first Linear's edge part in a
+                                     pass of its own (same results, bit for bit; for testing) */
 
 /* Launch choices of the fused BF16 edge forward. Every choice computes the
  * same arithmetic; FP32 results agree to rounding (instruction pairing and

@@ -375,8 +375,12 @@ def _blas_threads() -> int:
 
 
 def workload_config_text(wl: dict, n_el, n_unpart, e_unpart, kind: str) -> str:
-    """The `config.workload` text of a workload (shared by both arms)."""
-    return (f"consistent NMP layers x{M} {kind}, {n_el}^3 {wl.get('cells', 'elements')}: {wl['desc']} "
+    """The `config.workload` text of a workload (shared by both arms); a brick size
+    given on the command line replaces the default one in the description."""
+    desc, pre = wl["desc"], f"{wl.get('nel')}^3 "
+    if n_el != wl.get("nel") and desc.startswith(pre):
+        desc = f"{n_el}^3 " + desc[len(pre):]
+    return (f"consistent NMP layers x{M} {kind}, {n_el}^3 {wl.get('cells', 'elements')}: {desc} "
             f"({n_unpart:,} nodes, {e_unpart:,} edges), H={wl['H']}, MLP {wl.get('nh', NH)} hidden")
 
 

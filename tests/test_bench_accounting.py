@@ -121,3 +121,12 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_workload_text_names_the_brick_that_ran():
+    wl = bench.WORKLOADS["c3"]
+    full = bench.workload_config_text(wl, wl["nel"], 1, 2, "fwd+bwd")
+    assert f"{wl['nel']}^3 elements: {wl['nel']}^3 elements p=7" in full
+    small = bench.workload_config_text(wl, 12, 614_125, 3_641_400, "fwd+bwd")
+    assert "12^3 elements: 12^3 elements p=7" in small and f"{wl['nel']}^3" not in small
+    assert "(614,125 nodes, 3,641,400 edges)" in small
